@@ -1,0 +1,444 @@
+"""FP64 oracle, part 2: the regularised solvers (Sections 1, 3.2, 4 and 5).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Every method works per Fourier frontal slice on the full spectrum of n slices,
+the way the paper's algorithms loop over i = 1..n.  Slices are coupled only
+through Frobenius norms (Parseval: ||X||_F^2 = (1/n) sum_s ||Xh[s]||^2) and the
+shared truncation index.
+
+Readings of points the paper leaves open (each also listed in the design notes):
+  * Eq. (disp): the residual is ||B - A * X_k||_F with the true A, and k is
+    the smallest admissible index with residual <= tau * delta.
+  * Eq. (kinit): for RT-tSVD the admissible k run from max(1, r - p) to r;
+    T-tSVD, tGKB and t-Lanczos start at k = 1.  If no admissible k meets the
+    bound the last one is returned with status NOT_CONVERGED.
+  * s_j^{-1} in Eq. (14) and its RT-tSVD analogue: a singular value at or
+    below max(l, m) * eps * sigma_max (sigma_max over all slices) is treated
+    as zero (its term is dropped), the usual numerical-rank convention.
+  * Algorithm 3 is run in block form: b Gaussian slices at a time, q power
+    iterations, each block orthonormalised by two classical Gram-Schmidt
+    passes against the basis so far and then column by column (two passes and
+    a Normalize per column).  With b = 1, q = 0 this reduces to Algorithm 3
+    (pinned in the tests against rtsvd_alg3, which follows Algorithm 3 as
+    printed).  The indicator eta and its stopping rule are Algorithm 3's.
+  * Algorithm 4's reorthogonalisation steps use two classical Gram-Schmidt
+    passes.
+  * tGKT: the projected Tikhonov problem min ||P_k y - z_1 e_1||^2 + mu^{-1}||y||^2
+    per slice, one scalar mu for all slices, mu found by bisection on log10(mu)
+    over the interval of Section 5 so that the residual equals tau * delta.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .talgebra import fft3, ifft3_real, fro2, fro2_hat, normalize_hat, tsvd_hat
+
+STATUS_OK = 0
+STATUS_NOT_CONVERGED = -5
+
+EPS64 = float(np.finfo(np.float64).eps)
+
+
+def _ct(M: np.ndarray) -> np.ndarray:
+    """Conjugate transpose of every slice of a stacked (n, a, b) array."""
+    return np.conj(np.swapaxes(M, -1, -2))
+
+
+def _dp_pick(res: dict, tau_delta: float, k_lo: int, k_hi: int):
+    """Smallest k in [k_lo, k_hi] with res[k] <= tau*delta (Eq. (disp))."""
+    for k in range(k_lo, k_hi + 1):
+        if res[k] <= tau_delta:
+            return k, STATUS_OK
+    return k_hi, STATUS_NOT_CONVERGED
+
+
+def _margin(res: dict, k: int, tau_delta: float) -> float:
+    """Relative distance of the DP test from a tie at the chosen k and at k-1."""
+    vals = [abs(res[k] - tau_delta)]
+    if (k - 1) in res:
+        vals.append(abs(res[k - 1] - tau_delta))
+    return float(min(vals) / tau_delta)
+
+
+def _inv_sigma(S: np.ndarray, dims: int) -> np.ndarray:
+    """1/sigma with the numerical-rank threshold max(l,m) * eps * sigma_max."""
+    tol = dims * EPS64 * (float(S.max()) if S.size else 0.0)
+    out = np.zeros_like(S)
+    keep = S > tol
+    out[keep] = 1.0 / S[keep]
+    return out
+
+
+# --------------------------------------------------------------------------
+# T-tSVD method (Section 4.1, Eqs. (11)-(14)).
+# --------------------------------------------------------------------------
+
+def ttsvd_solve(A, B, delta, tau, k_fixed=None):
+    n, l, m = A.shape
+    Ah, Bh = fft3(A), fft3(B)
+    U, S, V = tsvd_hat(Ah)
+    qn = S.shape[1]
+    beta = _ct(U) @ Bh                                   # (n, q, p)
+    b2 = np.sum(np.abs(Bh) ** 2)
+    captured = np.concatenate([[0.0], np.cumsum(np.sum(np.abs(beta) ** 2, axis=(0, 2)))])
+    res = {k: float(np.sqrt(max(b2 - captured[k], 0.0) / n)) for k in range(qn + 1)}
+    td = tau * delta
+    k, status = _dp_pick(res, td, 1, qn)
+    if k_fixed is not None:
+        k, status = k_fixed, STATUS_OK
+    alpha = _inv_sigma(S, max(l, m))[:, :, None] * beta
+    Xh = V[:, :, :k] @ alpha[:, :k, :]
+    return dict(X=ifft3_real(Xh), k=k, status=status, res=res, tau_delta=td,
+                margin=_margin(res, k, td), S=S)
+
+
+# --------------------------------------------------------------------------
+# R-tSVD, Algorithm 3 exactly as printed (one Gaussian slice per step).
+# --------------------------------------------------------------------------
+
+def rtsvd_alg3(A, Omega, eps, r_max=None):
+    """Algorithm 3: grows Q one lateral slice at a time until eta < eps^2.
+
+    Omega[:, :, r-1] (spatial, m x 1 x n) is the Gaussian slice G drawn at
+    step r.  Returns Fourier-domain Q (n, l, r), Bt (n, r, m), r, eta history.
+    """
+    n, l, m = A.shape
+    r_max = m if r_max is None else r_max
+    Ah = fft3(A)
+    eta = fro2(A)
+    etas = [eta]
+    Q, Bt = [], []
+    r = 0
+    while eta >= eps * eps and r < r_max:
+        r += 1
+        Gh = fft3(Omega[:, :, r - 1])                    # (n, m)
+        Zh = np.einsum("sij,sj->si", Ah, Gh)             # A * G
+        if r > 1:                                        # - Q_{r-1} * (Bt(r-1,:,:) * G)
+            tube = np.einsum("sj,sj->s", Bt[-1], Gh)
+            Zh = Zh - Q[-1] * tube[:, None]
+        Zh, _ = normalize_hat(Zh)
+        if r > 1:                                        # Z - sum_j Q_j * (Q_j^T * Z)
+            coef = [np.einsum("si,si->s", np.conj(Qj), Zh) for Qj in Q]
+            for Qj, cj in zip(Q, coef):
+                Zh = Zh - Qj * cj[:, None]
+        Zh, _ = normalize_hat(Zh)
+        Q.append(Zh)
+        Y = np.einsum("si,sij->sj", np.conj(Zh), Ah)     # Y = Z^T * A
+        Bt.append(Y)
+        eta = eta - fro2_hat(Y)
+        etas.append(eta)
+    Qa = np.stack(Q, axis=2) if Q else np.zeros((n, l, 0), complex)
+    Ba = np.stack(Bt, axis=1) if Bt else np.zeros((n, 0, m), complex)
+    return dict(Q=Qa, Bt=Ba, r=r, eta=eta, etas=etas)
+
+
+def _orth_block(Y: np.ndarray, Q: np.ndarray | None) -> np.ndarray:
+    """Two CGS passes of Y against Q, then column-by-column CGS2 + Normalize."""
+    Y = np.array(Y, dtype=np.complex128, copy=True)
+    if Q is not None and Q.shape[2] > 0:
+        QH = _ct(Q)
+        for _ in range(2):
+            Y = Y - Q @ (QH @ Y)
+    b = Y.shape[2]
+    for j in range(b):
+        if j > 0:
+            P = Y[:, :, :j]
+            PH = _ct(P)
+            for _ in range(2):
+                Y[:, :, j:j + 1] = Y[:, :, j:j + 1] - P @ (PH @ Y[:, :, j:j + 1])
+        Y[:, :, j], _ = normalize_hat(Y[:, :, j])
+    return Y
+
+
+def rtsvd_block(A, Omega, eps, b, q, r_max):
+    """Block form of Algorithm 3 with q power iterations (see module notes).
+
+    Returns Fourier-domain Q (n, l, r), BH = Bt^H (n, m, r), r, eta history.
+    """
+    n, l, m = A.shape
+    Ah = fft3(A)
+    AhH = _ct(Ah)
+    eta = fro2(A)
+    etas = [eta]
+    Q = np.zeros((n, l, 0), complex)
+    BH = np.zeros((n, m, 0), complex)
+    r = 0
+    while eta >= eps * eps and r < r_max:
+        bb = min(b, r_max - r)
+        Gh = fft3(Omega[:, :, r:r + bb])
+        Y = _orth_block(Ah @ Gh, Q)
+        for _ in range(q):
+            Z = _orth_block(AhH @ Y, None)
+            Y = _orth_block(Ah @ Z, Q)
+        BHb = AhH @ Y
+        eta = eta - fro2_hat(BHb)
+        etas.append(eta)
+        Q = np.concatenate([Q, Y], axis=2)
+        BH = np.concatenate([BH, BHb], axis=2)
+        r += bb
+    return dict(Q=Q, Bt=_ct(BH), r=r, eta=eta, etas=etas)
+
+
+# --------------------------------------------------------------------------
+# RT-tSVD method (Section 4.2 and Eq. (kinit)).
+# --------------------------------------------------------------------------
+
+def rtsvd_solve(A, B, Omega, delta, tau, eps, p_over, block=16, q_power=1,
+                r_max=None, form="block", k_fixed=None):
+    n, l, m = A.shape
+    r_max = min(l, m) if r_max is None else r_max
+    if form == "alg3":
+        fac = rtsvd_alg3(A, Omega, eps, r_max)
+    else:
+        fac = rtsvd_block(A, Omega, eps, block, q_power, r_max)
+    Q, Bt, r = fac["Q"], fac["Bt"], fac["r"]
+    Ah, Bh = fft3(A), fft3(B)
+    Ub, S, V = tsvd_hat(Bt)                               # full tSVD of Bt
+    d = _ct(Q) @ Bh                                       # (n, r, p)
+    beta = _ct(Ub) @ d                                    # U_k^T * B in Fourier
+    alpha = _inv_sigma(S, max(l, m))[:, :, None] * beta
+    k_init = max(1, r - p_over)
+    td = tau * delta
+    res = {}
+    for k in range(k_init, r + 1):
+        Xh = V[:, :, :k] @ alpha[:, :k, :]
+        res[k] = float(np.sqrt(fro2_hat(Bh - Ah @ Xh)))
+    k, status = _dp_pick(res, td, k_init, r)
+    if fac["eta"] >= eps * eps:
+        status = STATUS_NOT_CONVERGED
+    if k_fixed is not None:
+        k, status = k_fixed, STATUS_OK
+    Xh = V[:, :, :k] @ alpha[:, :k, :]
+    return dict(X=ifft3_real(Xh), k=k, r=r, k_init=k_init, status=status, res=res,
+                tau_delta=td, margin=_margin(res, k, td), eta=fac["eta"],
+                etas=fac["etas"], S=S, Q=Q, Bt=Bt)
+
+
+# --------------------------------------------------------------------------
+# tGKB (Algorithm 4) and the tGKB method (Eqs. (9tt), (solgkb)).
+# --------------------------------------------------------------------------
+
+def _reorth(v: np.ndarray, basis: list) -> np.ndarray:
+    """Two CGS passes of v (n, d) against the Fourier-domain vectors in basis."""
+    if not basis:
+        return v
+    Bm = np.stack(basis, axis=2)                          # (n, d, j)
+    for _ in range(2):
+        coef = np.einsum("sdj,sd->sj", np.conj(Bm), v)
+        v = v - np.einsum("sdj,sj->sd", Bm, coef)
+    return v
+
+
+def tgkb_hat(Ah: np.ndarray, bh: np.ndarray, k: int):
+    """k steps of Algorithm 4 on Fourier data.
+
+    Returns W (n, m, k), Q (n, l, k+1), c (n, k), z (n, k+1): the real
+    Fourier coefficients of the tubes c_i and z_i (Normalize makes them
+    non-negative reals per slice), i.e. the per-slice bidiagonal entries.
+    """
+    AhH = _ct(Ah)
+    q, z1 = normalize_hat(bh)
+    Q, W, c, z = [q], [], [], [z1]
+    w_prev = None
+    for i in range(k):
+        w = np.einsum("sij,sj->si", AhH, Q[i])
+        if w_prev is not None:
+            w = w - w_prev * z[i][:, None]
+        w = _reorth(w, W)
+        w, ci = normalize_hat(w)
+        W.append(w)
+        c.append(ci)
+        qn = np.einsum("sij,sj->si", Ah, w) - Q[i] * ci[:, None]
+        qn = _reorth(qn, Q)
+        qn, zn = normalize_hat(qn)
+        Q.append(qn)
+        z.append(zn)
+        w_prev = w
+    return dict(W=np.stack(W, axis=2) if W else np.zeros(Ah.shape[:1] + (Ah.shape[2], 0), complex),
+                Q=np.stack(Q, axis=2), c=np.stack(c, axis=1) if c else np.zeros((Ah.shape[0], 0)),
+                z=np.stack(z, axis=1))
+
+
+def bidiag(c_s: np.ndarray, z_s: np.ndarray, k: int) -> np.ndarray:
+    """Lower bidiagonal P_k ((k+1) x k) of one slice: c on the diagonal,
+    z_2..z_{k+1} below it (Section 4.3)."""
+    P = np.zeros((k + 1, k))
+    for i in range(k):
+        P[i, i] = c_s[i]
+        P[i + 1, i] = z_s[i + 1]
+    return P
+
+
+def _projected_ls(c, z, k):
+    """Per slice: min ||P_k y - z_1 e_1|| by least squares (Algorithm 5).
+
+    Returns y (n, k) and the per-slice residual norms (n,)."""
+    n = c.shape[0]
+    y = np.zeros((n, k))
+    phi = np.zeros(n)
+    for s in range(n):
+        P = bidiag(c[s], z[s], k)
+        rhs = np.zeros(k + 1)
+        rhs[0] = z[s, 0]
+        ys, *_ = np.linalg.lstsq(P, rhs, rcond=None)
+        y[s] = ys
+        phi[s] = np.linalg.norm(P @ ys - rhs)
+    return y, phi
+
+
+def tgkb_solve(A, B, delta, tau, k_max, k_fixed=None):
+    n, l, m = A.shape
+    k_max = min(k_max, min(l, m))
+    if k_fixed is not None:
+        k_max = k_fixed
+    Ah, Bh = fft3(A), fft3(B)
+    g = tgkb_hat(Ah, Bh[:, :, 0], k_max)
+    td = tau * delta
+    res = {}
+    k, status = k_max, STATUS_NOT_CONVERGED
+    for i in range(1, k_max + 1):
+        _, phi = _projected_ls(g["c"], g["z"], i)
+        res[i] = float(np.sqrt(np.sum(phi ** 2) / n))
+        if res[i] <= td and k_fixed is None:
+            k, status = i, STATUS_OK
+            break
+    if k_fixed is not None:
+        status = STATUS_OK
+    y, _ = _projected_ls(g["c"], g["z"], k)
+    Xh = np.einsum("sdj,sj->sd", g["W"][:, :, :k], y)[:, :, None]
+    return dict(X=ifft3_real(Xh), k=k, status=status, res=res, tau_delta=td,
+                margin=_margin(res, k, td), W=g["W"][:, :, :k], Q=g["Q"][:, :, :k + 1],
+                c=g["c"][:, :k], z=g["z"][:, :k + 1])
+
+
+# --------------------------------------------------------------------------
+# tGKT: Tikhonov regularisation of the tGKB-projected problem (Section 5).
+# --------------------------------------------------------------------------
+
+def tikhonov_residual(U1: np.ndarray, S: np.ndarray, z1: np.ndarray, mu: float, n: int) -> float:
+    """||P y_mu - z1 e1|| summed over slices (Parseval), from each slice's
+    thin SVD P = U S V^T: sum_j (z1 u_1j / (1 + mu s_j^2))^2 + z1^2 (1 - sum_j u_1j^2)."""
+    tot = 0.0
+    for s in range(U1.shape[0]):
+        f = z1[s] * U1[s] / (1.0 + mu * S[s] ** 2)
+        tot += np.sum(f ** 2) + z1[s] ** 2 * max(1.0 - np.sum(U1[s] ** 2), 0.0)
+    return float(np.sqrt(tot / n))
+
+
+def _bidiag_svds(c, z, k):
+    n = c.shape[0]
+    U1 = np.zeros((n, k))
+    S = np.zeros((n, k))
+    Vs = np.zeros((n, k, k))
+    for s in range(n):
+        U, sv, VT = np.linalg.svd(bidiag(c[s], z[s], k), full_matrices=False)
+        U1[s], S[s], Vs[s] = U[0], sv, VT.T
+    return U1, S, Vs
+
+
+def tikhonov_fixed_mu(g, mu):
+    """Projected Tikhonov solution X = W_k * Y_mu for a given mu, from the
+    output g of tgkb_solve (or of tgkb_hat plus k)."""
+    n = g["c"].shape[0]
+    k = g["c"].shape[1]
+    U1, S, Vs = _bidiag_svds(g["c"], g["z"], k)
+    z1 = g["z"][:, 0]
+    y = np.zeros((n, k))
+    for s in range(n):
+        y[s] = Vs[s] @ (S[s] / (S[s] ** 2 + 1.0 / mu) * z1[s] * U1[s])
+    Xh = np.einsum("sdj,sj->sd", g["W"], y)[:, :, None]
+    return ifft3_real(Xh), tikhonov_residual(U1, S, z1, mu, n)
+
+
+def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, max_iter=200):
+    n, l, m = A.shape
+    g = tgkb_solve(A, B, delta, tau, k_max)
+    k = g["k"]
+    c, z = g["c"], g["z"]
+    U1, S, Vs = _bidiag_svds(c, z, k)
+    z1 = z[:, 0]
+    td = tau * delta
+    lo, hi = np.log10(mu_lo), np.log10(mu_hi)
+    status = STATUS_OK
+    f = lambda t: tikhonov_residual(U1, S, z1, 10.0 ** t, n) - td
+    if f(hi) > 0.0:
+        t, status = hi, STATUS_NOT_CONVERGED
+    elif f(lo) <= 0.0:
+        t = lo
+    else:
+        it = 0
+        while hi - lo > log_tol and it < max_iter:
+            mid = 0.5 * (lo + hi)
+            if f(mid) > 0.0:
+                lo = mid
+            else:
+                hi = mid
+            it += 1
+        t = hi
+    mu = 10.0 ** t
+    y = np.zeros((n, k))
+    for s in range(n):
+        y[s] = Vs[s] @ (S[s] / (S[s] ** 2 + 1.0 / mu) * z1[s] * U1[s])
+    Xh = np.einsum("sdj,sj->sd", g["W"], y)[:, :, None]
+    return dict(X=ifft3_real(Xh), k=k, mu=mu, status=status, tau_delta=td,
+                residual=tikhonov_residual(U1, S, z1, mu, n), gkb=g)
+
+
+# --------------------------------------------------------------------------
+# t-Lanczos (Algorithm t-Lanc) and the t-Lanczos method (Eq. (9t)); symmetric A.
+# --------------------------------------------------------------------------
+
+def tlanczos_hat(Ah: np.ndarray, bh: np.ndarray, k: int):
+    """k steps of the symmetric t-Lanczos process with reorthogonalisation."""
+    q, z0 = normalize_hat(bh)
+    Q, c, z = [q], [], []
+    for i in range(k):
+        v = np.einsum("sij,sj->si", Ah, Q[i])
+        ci = np.einsum("si,si->s", np.conj(Q[i]), v)
+        v = v - Q[i] * ci[:, None]
+        if i > 0:
+            v = v - Q[i - 1] * z[i - 1][:, None]
+        v = _reorth(v, Q)
+        v, zi = normalize_hat(v)
+        Q.append(v)
+        c.append(ci)
+        z.append(zi)
+    return dict(Q=np.stack(Q, axis=2), c=np.stack(c, axis=1), z=np.stack(z, axis=1), z0=z0)
+
+
+def tridiag(c_s, z_s, k):
+    """T_k ((k+1) x k): c on the diagonal, z on both off-diagonals."""
+    T = np.zeros((k + 1, k), dtype=np.complex128)
+    for i in range(k):
+        T[i, i] = c_s[i]
+        T[i + 1, i] = z_s[i]
+        if i + 1 < k:
+            T[i, i + 1] = z_s[i]
+    return T
+
+
+def tlanczos_solve(A, B, delta, tau, k_max):
+    n, l, m = A.shape
+    k_max = min(k_max, m)
+    Ah, Bh = fft3(A), fft3(B)
+    g = tlanczos_hat(Ah, Bh[:, :, 0], k_max)
+    td = tau * delta
+    res, ys = {}, {}
+    k, status = k_max, STATUS_NOT_CONVERGED
+    for i in range(1, k_max + 1):
+        y = np.zeros((n, i), complex)
+        tot = 0.0
+        for s in range(n):
+            T = tridiag(g["c"][s], g["z"][s], i)
+            rhs = np.zeros(i + 1, complex)
+            rhs[0] = g["z0"][s]
+            y[s], *_ = np.linalg.lstsq(T, rhs, rcond=None)
+            tot += np.linalg.norm(T @ y[s] - rhs) ** 2
+        res[i] = float(np.sqrt(tot / n))
+        ys[i] = y
+        if res[i] <= td:
+            k, status = i, STATUS_OK
+            break
+    Xh = np.einsum("sdj,sj->sd", g["Q"][:, :, :k], ys[k])[:, :, None]
+    return dict(X=ifft3_real(Xh), k=k, status=status, res=res, tau_delta=td)

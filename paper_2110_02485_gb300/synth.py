@@ -1,0 +1,176 @@
+"""Seeded synthetic inputs for the t-product regularization problems.
+
+This module is shared by the CUDA path, its tests and the FP64 oracle.  It
+only *synthesises data*; none of the solvers' arithmetic lives here.  The one
+piece of algebra it contains is the forward blur used to make the data slice
+B = A * X_true + E: because the synthetic operator has the rank-one tube
+structure A(:,:,k) = c_k T, the product is written out in the spatial domain
+as T @ img @ Circ(c)^T (the circular convolution of Definition 2.1 applied to
+this structure), with no Fourier transform.
+
+Shapes follow the library's layout: a real third-order tensor with l x m
+frontal slices and n slices is stored frontal-slice-major as an array of shape
+(n, l, m), so element (i, j, k) of the paper lives at [k, i, j].  A lateral
+slice (l x 1 x n) is (n, l, 1); p lateral slices are (n, l, p).
+
+Recipes (Section 5 and the blur of Eq. (za), generalised as stated below):
+  * operator: T_ij = exp(-(i-j)^2 / (2 sigma^2)) / (sigma sqrt(2 pi)) for
+    |i-j| < band, else 0 (the band convention of Eq. (za): offsets
+    0..band-1); tube weights c_k = exp(-(k-1)^2 / (2 s^2)), k = 1..n;
+    A(:,:,k) = c_k T.
+  * true image: a sum of Gaussian bumps (centres U[0,N)^2, widths
+    U[N/32, N/8], amplitudes U[0.3, 1]) plus constant rectangles (corners
+    U[0,N), values U[0.2, 1]), clipped to [0, 1]; rows are mode 1 and columns
+    are tubes (mode 3), as the images of Examples 5.2-5.4 are stored.
+  * noise, Eq. (e1): E = nl * E0 / ||E0||_F * ||B_true||_F with E0 ~ N(0,1);
+    delta = ||E||_F is passed to the solvers as the noise bound of Eq. (errbd).
+  * Omega: the Gaussian test slices of Algorithm 3 drawn up front as a real
+    (n, m, r_max) tensor; lateral slice c is the c-th Gaussian slice.
+All draws use numpy's Philox bit generator with an explicit seed.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(seed))
+
+
+@dataclasses.dataclass(frozen=True)
+class BlurConfig:
+    """One synthetic deblurring workload (sizes and solver parameters)."""
+    name: str
+    N: int               # l = m = n = N
+    sigma: float         # Gaussian blur width of T
+    band: int            # T_ij != 0 iff |i-j| < band
+    s: float             # tube-weight width
+    bumps: int
+    rects: int
+    noise: float         # relative noise level (Eq. (e1))
+    tau: float           # discrepancy-principle factor (Eq. (disp))
+    p_over: int          # oversampling (rho in Section 4.2 / Eq. (kinit))
+    q_power: int         # power iterations of the block sketch
+    block: int           # sketch block size b
+    r_max: int           # cap on the sketch rank r
+    eps_rel: float       # R-tSVD tolerance as a fraction of ||A||_F
+    k_max: int           # tGKB step cap
+    mu_lo: float         # Tikhonov bisection interval (Section 5)
+    mu_hi: float
+    seed: int
+
+
+# Workloads.  The first is the small case the oracle finishes in seconds; the
+# second is the 256^3 image deblur that the throughput figure is quoted on;
+# the third is the 512^3 precision-form size.  eps_rel (the tolerance of
+# Algorithm 3 relative to ||A||_F; the paper tunes the absolute eps per example
+# by experiment, Table 0) is the largest value on the grid 10^(-j/10) for which
+# the oracle's RT-tSVD meets the discrepancy principle within [r - p, r]; at
+# 256^3 this gives r = 96, close to the paper's r = 99 for its 256^3 image.
+CONFIGS = {
+    "n32": BlurConfig("n32", 32, 1.5, 4, 2.0, 5, 2, 1e-2, 1.01, 5, 1, 1, 32,
+                      3e-2, 32, 1e1, 1e7, 43),
+    "n256": BlurConfig("n256", 256, 2.5, 8, 3.0, 20, 4, 1e-3, 1.1, 10, 1, 16,
+                       160, 2e-2, 100, 1e1, 1e7, 44),
+    "n256_hi": BlurConfig("n256_hi", 256, 2.5, 8, 3.0, 20, 4, 1e-2, 1.1, 10, 1,
+                          16, 160, 3e-2, 100, 1e1, 1e7, 44),
+    "n512": BlurConfig("n512", 512, 3.0, 12, 4.0, 20, 4, 1e-3, 1.1, 10, 1, 16,
+                       160, 3e-3, 100, 1e1, 1e7, 45),
+}
+
+
+def blur_factors(N: int, sigma: float, band: int, s: float, n: int | None = None):
+    """Return (T, c) in float64: the Toeplitz blur T (N x N) and tube weights c (n)."""
+    n = N if n is None else n
+    d = np.abs(np.arange(N)[:, None] - np.arange(N)[None, :])
+    T = np.where(d < band, np.exp(-(d.astype(np.float64) ** 2) / (2.0 * sigma * sigma)), 0.0)
+    T = T / (sigma * math.sqrt(2.0 * math.pi))
+    c = np.exp(-((np.arange(1, n + 1) - 1.0) ** 2) / (2.0 * s * s))
+    return T, c
+
+
+def blur_tensor(T: np.ndarray, c: np.ndarray, dtype=np.float32) -> np.ndarray:
+    """A(:,:,k) = c_k T stored as (n, l, m)."""
+    return (c[:, None, None] * T[None, :, :]).astype(dtype)
+
+
+def synthetic_image(rows: int, cols: int, n_bumps: int, n_rects: int,
+                    rng: np.random.Generator) -> np.ndarray:
+    N = max(rows, cols)
+    ii = np.arange(rows, dtype=np.float64)[:, None]
+    jj = np.arange(cols, dtype=np.float64)[None, :]
+    img = np.zeros((rows, cols))
+    for _ in range(n_bumps):
+        ci, cj = rng.uniform(0, rows), rng.uniform(0, cols)
+        w = rng.uniform(N / 32.0, N / 8.0)
+        amp = rng.uniform(0.3, 1.0)
+        img += amp * np.exp(-((ii - ci) ** 2 + (jj - cj) ** 2) / (2.0 * w * w))
+    for _ in range(n_rects):
+        r0, r1 = np.sort(rng.integers(0, rows, size=2))
+        c0, c1 = np.sort(rng.integers(0, cols, size=2))
+        img[r0:r1 + 1, c0:c1 + 1] += rng.uniform(0.2, 1.0)
+    return np.clip(img, 0.0, 1.0)
+
+
+def forward_blur(T: np.ndarray, c: np.ndarray, img: np.ndarray) -> np.ndarray:
+    """B_img = T @ img @ Circ(c)^T with Circ[k, k'] = c[(k - k') mod n].
+
+    img is (l, n): rows are mode 1, columns are tubes.  This is the spatial
+    form of A * X for A(:,:,k) = c_k T (Definition 2.1), used only to make data.
+    """
+    n = c.shape[0]
+    idx = (np.arange(n)[:, None] - np.arange(n)[None, :]) % n
+    circ = c[idx]
+    return T @ img @ circ.T
+
+
+def add_noise(B_true: np.ndarray, level: float, rng: np.random.Generator):
+    """Eq. (e1): returns (B, delta) with delta = ||E||_F."""
+    E0 = rng.standard_normal(B_true.shape)
+    E = level * E0 / np.linalg.norm(E0) * np.linalg.norm(B_true)
+    return B_true + E, float(np.linalg.norm(E))
+
+
+def lateral(img: np.ndarray) -> np.ndarray:
+    """(l, n) image -> (n, l, 1) lateral slice."""
+    return np.ascontiguousarray(img.T[:, :, None])
+
+
+def gaussian_tensor(shape, seed: int, dtype=np.float32) -> np.ndarray:
+    return rng_for(seed).standard_normal(shape).astype(dtype)
+
+
+def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | None = None,
+                 general: float = 0.0, with_omega: bool = True) -> dict:
+    """Build one deblurring problem.
+
+    general > 0 adds a dense Gaussian perturbation of relative size `general`
+    (in Frobenius norm) to A, so that the Fourier slices are no longer
+    multiples of one matrix.  B is always made from the unperturbed operator.
+    Returns float32 arrays A (n,N,N), B (n,N,1), X_true (n,N,1),
+    Omega (n,N,r_max) and float64 scalars delta, norm_A.
+    """
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    noise = cfg.noise if noise is None else noise
+    seed = cfg.seed if seed is None else seed
+    rng = rng_for(seed)
+    N = cfg.N
+    T, c = blur_factors(N, cfg.sigma, cfg.band, cfg.s)
+    A = blur_tensor(T, c)
+    if general > 0.0:
+        P = rng.standard_normal(A.shape)
+        A = (A.astype(np.float64) + general * P / np.linalg.norm(P) * np.linalg.norm(A)).astype(np.float32)
+    img = synthetic_image(N, N, cfg.bumps, cfg.rects, rng)
+    B_true = forward_blur(T, c, img)
+    B, delta = add_noise(B_true, noise, rng)
+    out = dict(cfg=cfg, A=A, B=lateral(B).astype(np.float32),
+               X_true=lateral(img).astype(np.float32), delta=delta, noise=noise,
+               T=T, c=c)
+    if with_omega:
+        out["Omega"] = rng.standard_normal((N, N, cfg.r_max)).astype(np.float32)
+    out["norm_A"] = float(np.sqrt(np.sum(A.astype(np.float64) ** 2)))
+    return out

@@ -1,0 +1,263 @@
+"""Pins for the oracle's solvers: Algorithm 3 and Theorems 4.1/4.2, the
+RT-tSVD and T-tSVD methods with the discrepancy principle (Eq. (disp)),
+Algorithm 4 and the tGKB method, the Tikhonov variant and t-Lanczos.
+
+Each pin checks the oracle against something other than itself: the
+block-circulant product of Definition 2.1 (no Fourier transform), explicit
+Krylov bases, dense per-slice solves, or an independent path of the paper.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_02485_gb300 import synth
+
+
+def rnd(shape, seed):
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+def spatial(Xh):
+    return O.ifft3_real(Xh)
+
+
+def small_blur(N=10, n=8, seed=3, noise=1e-2, general=0.0):
+    T, c = synth.blur_factors(N, 1.2, 3, 1.5, n=n)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    g = np.random.default_rng(seed)
+    if general:
+        P = g.standard_normal(A.shape)
+        A = A + general * P / np.linalg.norm(P) * np.linalg.norm(A)
+    img = synth.synthetic_image(N, n, 3, 1, g)
+    Bt = synth.lateral(synth.forward_blur(T, c, img))
+    E = g.standard_normal(Bt.shape)
+    E = noise * E / np.linalg.norm(E) * np.linalg.norm(Bt)
+    return A, Bt + E, float(np.linalg.norm(E))
+
+
+# ------------------------------------------------------ R-tSVD (Alg. 3) ----
+
+@pytest.mark.parametrize("form", ["alg3", "block"])
+def test_theorem_4_2_eta_is_the_approximation_error(form):
+    n, l, m = 6, 9, 7
+    A = rnd((n, l, m), 1)
+    Om = rnd((n, m, m), 2)
+    eps = 0.2 * np.sqrt(O.fro2(A))
+    if form == "alg3":
+        f = O.rtsvd_alg3(A, Om, eps)
+        step = 1
+    else:
+        f = O.rtsvd_block(A, Om, eps, b=2, q=1, r_max=m)
+        step = 2
+    assert f["eta"] < eps ** 2
+    for i, eta in enumerate(f["etas"]):
+        r = min(i * step, f["r"])
+        Q = spatial(f["Q"][:, :, :r])
+        Bt = spatial(f["Bt"][:, :r, :])
+        approx = O.tprod_bcirc(Q, Bt) if r else np.zeros_like(A)
+        assert np.isclose(eta, O.fro2(A - approx), rtol=1e-9, atol=1e-10 * O.fro2(A))
+    # Q is partially orthogonal: Q^T * Q = I (Section 2)
+    Q = spatial(f["Q"])
+    assert np.allclose(O.tprod_bcirc(O.ttranspose(Q), Q), O.tidentity(f["r"], n), atol=1e-10)
+
+
+def test_block_form_with_b1_q0_is_algorithm_3():
+    n, l, m = 5, 8, 6
+    A = rnd((n, l, m), 4)
+    Om = rnd((n, m, m), 5)
+    eps = 0.1 * np.sqrt(O.fro2(A))
+    a = O.rtsvd_alg3(A, Om, eps)
+    b = O.rtsvd_block(A, Om, eps, b=1, q=0, r_max=m)
+    assert a["r"] == b["r"]
+    assert np.allclose(a["Q"], b["Q"], atol=1e-9)
+    assert np.allclose(a["Bt"], b["Bt"], atol=1e-9)
+    assert np.allclose(a["etas"], b["etas"], rtol=1e-9)
+
+
+@pytest.mark.parametrize("q_power,block", [(0, 1), (1, 3), (2, 4)])
+def test_full_rank_rtsvd_equals_ttsvd_at_every_k(q_power, block):
+    """With r = m and A of full tubal rank the R-tSVD factorisation is exact,
+    so the RT-tSVD solution at any fixed k is the T-tSVD solution (Eq. (14))."""
+    A, B, delta = small_blur(N=8, n=6, general=0.05)
+    n, l, m = A.shape
+    Om = rnd((n, m, m), 6)
+    for k in [1, 3, 5, m]:
+        x1 = O.rtsvd_solve(A, B, Om, delta, 1.1, 0.0, m, block, q_power, r_max=m, k_fixed=k)
+        x2 = O.ttsvd_solve(A, B, delta, 1.1, k_fixed=k)
+        assert x1["r"] == m
+        assert np.allclose(x1["X"], x2["X"], atol=1e-8 * np.abs(x2["X"]).max())
+
+
+def test_rtsvd_discrepancy_residual_and_bracket():
+    A, B, delta = small_blur(N=10, n=8, general=0.02)
+    n, l, m = A.shape
+    Om = rnd((n, m, m), 7)
+    tau = 1.1
+    out = O.rtsvd_solve(A, B, Om, delta, tau, 0.02 * np.sqrt(O.fro2(A)), 3, 2, 1, r_max=m)
+    assert out["status"] == O.STATUS_OK
+    for k, rk in out["res"].items():          # residual is ||B - A*X_k|| with the true A
+        Xk = O.rtsvd_solve(A, B, Om, delta, tau, 0.02 * np.sqrt(O.fro2(A)), 3, 2, 1,
+                           r_max=m, k_fixed=k)["X"]
+        assert np.isclose(rk, np.sqrt(O.fro2(B - O.tprod_bcirc(A, Xk))), rtol=1e-9)
+    k = out["k"]
+    assert out["k_init"] == max(1, out["r"] - 3)
+    assert out["res"][k] <= tau * delta
+    assert all(out["res"][j] > tau * delta for j in range(out["k_init"], k))
+
+
+def test_ttsvd_discrepancy_bracket_with_brute_force_residual():
+    A, B, delta = small_blur()
+    tau = 1.1
+    out = O.ttsvd_solve(A, B, delta, tau)
+    k = out["k"]
+    r = lambda X: np.sqrt(O.fro2(B - O.tprod_bcirc(A, X)))
+    assert r(out["X"]) <= tau * delta * (1 + 1e-12)
+    if k > 1:
+        assert r(O.ttsvd_solve(A, B, delta, tau, k_fixed=k - 1)["X"]) > tau * delta
+    assert np.isclose(r(out["X"]), out["res"][k], rtol=1e-8)
+
+
+# ------------------------------------------------------------ tGKB ----
+
+def test_tgkb_decomposition_orthonormality_and_start():
+    n, l, m, k = 6, 9, 7, 4
+    A = rnd((n, l, m), 8)
+    B = rnd((n, l, 1), 9)
+    g = O.tgkb_hat(O.fft3(A), O.fft3(B)[:, :, 0], k)
+    W = spatial(g["W"])
+    Q = spatial(g["Q"])
+    # bidiagonal tensor P_k: tubes c_i on the diagonal and z_{i+1} below
+    Ph = np.zeros((n, k + 1, k), complex)
+    for s in range(n):
+        Ph[s] = O.bidiag(g["c"][s], g["z"][s], k)
+    P = spatial(Ph)
+    assert np.allclose(O.tprod_bcirc(A, W), O.tprod_bcirc(Q, P), atol=1e-10)      # Eq. (t-gkb)
+    assert np.allclose(O.tprod_bcirc(O.ttranspose(W), W), O.tidentity(k, n), atol=1e-10)
+    assert np.allclose(O.tprod_bcirc(O.ttranspose(Q), Q), O.tidentity(k + 1, n), atol=1e-10)
+    z1 = spatial(g["z"][:, 0].astype(complex)[:, None, None])
+    e1z1 = np.zeros((n, k + 1, 1))
+    e1z1[:, 0, 0] = z1[:, 0, 0]
+    assert np.allclose(O.tprod_bcirc(O.ttranspose(Q), B), e1z1, atol=1e-10)       # Q^T * B = e1 * z1
+    assert np.all(g["c"] >= 0) and np.all(g["z"] >= 0)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_tgkb_solution_is_the_krylov_least_squares_solution(k):
+    """Per Fourier slice, X_k minimises ||b - A x|| over the Krylov space
+    K_k(A^H A, A^H b) (Eq. (krylov1)), here built from explicit power vectors."""
+    A, B, delta = small_blur(N=9, n=5, general=0.3)
+    out = O.tgkb_solve(A, B, delta, 1.1, 50, k_fixed=k)
+    Ah, Bh = O.fft3(A), O.fft3(B)
+    Xh = np.zeros((A.shape[0], A.shape[2], 1), complex)
+    for s in range(A.shape[0]):
+        M, b = Ah[s], Bh[s, :, 0]
+        v = M.conj().T @ b
+        K = [v]
+        for _ in range(k - 1):
+            v = M.conj().T @ (M @ v)
+            K.append(v)
+        Kq, _ = np.linalg.qr(np.stack(K, axis=1))
+        y, *_ = np.linalg.lstsq(M @ Kq, b, rcond=None)
+        Xh[s, :, 0] = Kq @ y
+    assert np.allclose(out["X"], spatial(Xh), atol=1e-8 * np.abs(out["X"]).max())
+
+
+def test_tgkb_full_space_solves_the_system():
+    n, m = 4, 5
+    A = rnd((n, m, m), 10) + 3 * O.tidentity(m, n)
+    X = rnd((n, m, 1), 11)
+    B = O.tprod_bcirc(A, X)
+    out = O.tgkb_solve(A, B, 1e-14, 1.1, m, k_fixed=m)
+    assert np.allclose(out["X"], X, atol=1e-9)
+
+
+def test_tgkb_discrepancy_bracket_with_brute_force_residual():
+    A, B, delta = small_blur()
+    tau = 1.1
+    out = O.tgkb_solve(A, B, delta, tau, 20)
+    k = out["k"]
+    assert out["status"] == O.STATUS_OK
+    r = lambda X: np.sqrt(O.fro2(B - O.tprod_bcirc(A, X)))
+    assert np.isclose(r(out["X"]), out["res"][k], rtol=1e-8)
+    assert out["res"][k] <= tau * delta
+    if k > 1:
+        assert r(O.tgkb_solve(A, B, delta, tau, 20, k_fixed=k - 1)["X"]) > tau * delta
+
+
+# ------------------------------------------------------------ tGKT ----
+
+def test_tgkt_full_space_is_dense_tikhonov():
+    A, B, delta = small_blur(N=6, n=4, general=0.2)
+    n, l, m = A.shape
+    g = O.tgkb_solve(A, B, delta, 1.1, m, k_fixed=m)
+    Ah, Bh = O.fft3(A), O.fft3(B)
+    for mu in [0.3, 10.0, 1e3]:
+        X, _ = O.tikhonov_fixed_mu(g, mu)
+        Xh = np.zeros((n, m, 1), complex)
+        for s in range(n):
+            M = Ah[s]
+            Xh[s] = np.linalg.solve(M.conj().T @ M + np.eye(m) / mu, M.conj().T @ Bh[s])
+        assert np.allclose(X, spatial(Xh), atol=1e-8 * np.abs(X).max())
+
+
+def test_tgkt_residual_monotone_limit_and_root():
+    A, B, delta = small_blur()
+    tau = 1.1
+    out = O.tgkt_solve(A, B, delta, tau, 20, 1e-3, 1e9)
+    g = out["gkb"]
+    mus = np.logspace(-3, 9, 25)
+    res = [O.tikhonov_fixed_mu(g, mu)[1] for mu in mus]
+    assert all(res[i + 1] <= res[i] * (1 + 1e-12) for i in range(len(res) - 1))
+    X_inf, _ = O.tikhonov_fixed_mu(g, 1e14)
+    assert np.allclose(X_inf, g["X"], atol=1e-6 * np.abs(g["X"]).max())
+    assert out["status"] == O.STATUS_OK
+    assert np.isclose(out["residual"], tau * delta, rtol=1e-9)
+    # the residual reported is the true ||B - A * X_mu|| of the returned solution
+    assert np.isclose(np.sqrt(O.fro2(B - O.tprod_bcirc(A, out["X"]))), out["residual"], rtol=1e-7)
+
+
+# ---------------------------------------------------------- t-Lanczos ----
+
+def test_tlanczos_decomposition_on_a_symmetric_tensor():
+    n, m, k = 5, 7, 3
+    M = rnd((n, m, m), 12)
+    A = O.tprod(O.ttranspose(M), M)                # t-symmetric: A^T = A
+    assert np.allclose(O.ttranspose(A), A, atol=1e-12)
+    B = rnd((n, m, 1), 13)
+    g = O.tlanczos_hat(O.fft3(A), O.fft3(B)[:, :, 0], k)
+    Q = spatial(g["Q"])
+    Th = np.stack([O.tridiag(g["c"][s], g["z"][s], k) for s in range(n)])
+    T = spatial(Th)
+    assert np.allclose(O.tprod_bcirc(A, Q[:, :, :k]), O.tprod_bcirc(Q, T), atol=1e-9)   # Eq. (t-lanczos)
+    assert np.allclose(O.tprod_bcirc(O.ttranspose(Q), Q), O.tidentity(k + 1, n), atol=1e-9)
+
+
+def test_tlanczos_method_meets_the_discrepancy_principle():
+    n, m = 6, 8
+    M = rnd((n, m, m), 14)
+    A = O.tprod(O.ttranspose(M), M) + 0.5 * O.tidentity(m, n)
+    X = rnd((n, m, 1), 15)
+    B = O.tprod(A, X)
+    E = rnd(B.shape, 16)
+    E = 1e-2 * E / np.linalg.norm(E) * np.linalg.norm(B)
+    out = O.tlanczos_solve(A, B + E, np.linalg.norm(E), 1.1, m)
+    assert out["status"] == O.STATUS_OK
+    assert np.sqrt(O.fro2(B + E - O.tprod_bcirc(A, out["X"]))) <= 1.1 * np.linalg.norm(E) * (1 + 1e-9)
+
+
+# ------------------------------------------- small end-to-end workload ----
+
+def test_small_workload_end_to_end():
+    P = synth.blur_problem("n32")
+    cfg = P["cfg"]
+    A, B, Om = (P[k].astype(np.float64) for k in ("A", "B", "Omega"))
+    Xt = P["X_true"].astype(np.float64)
+    err = lambda X: np.linalg.norm(X - Xt) / np.linalg.norm(Xt)
+    t = O.ttsvd_solve(A, B, P["delta"], cfg.tau)
+    r = O.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.eps_rel * P["norm_A"], cfg.p_over,
+                      cfg.block, cfg.q_power, cfg.r_max)
+    g = O.tgkb_solve(A, B, P["delta"], cfg.tau, cfg.k_max)
+    for out in (t, r, g):
+        assert out["status"] == O.STATUS_OK
+        assert err(out["X"]) < 0.3
+    assert g["k"] < t["k"]                  # tGKB needs fewer steps than T-tSVD's k (Section 5)
