@@ -1,0 +1,186 @@
+/*
+ * tprod.h -- C ABI of the GB300 t-product regularization library (libtprod.so).
+ *
+ * Operations follow Ugwu & Reichel, "Tensor regularization by truncated
+ * iteration ... with a t-product" (arXiv 2110.02485):
+ *   - the t-product and its mode-3 DFT (Section 2, Definition 2.1),
+ *   - the RT-tSVD method (Algorithm 3, Section 4.2, Eq. (kinit)),
+ *   - the tGKB method (Algorithm 4, Eqs. (t-gkb), (9tt), (solgkb)),
+ *   - Tikhonov regularisation of the tGKB-projected problem (tGKT, Section 5),
+ * each with the discrepancy principle of Eq. (disp).
+ *
+ * Layouts (all row-major, all pointers DEVICE pointers owned by the caller):
+ *   real tensor  l x m x n   : array (n, l, m); element (i,j,k) at [k*l*m + i*m + j]
+ *   lateral slices l x p x n : array (n, l, p)
+ *   Fourier tensor           : half spectrum, h = n/2 + 1 slices of l x m
+ *                              complex values, interleaved (re, im), array (h, l, m)
+ * The element type of every real/complex array is set by `prec`:
+ *   TP_FP32 -> float / (float re, float im);  TP_FP64 -> double / (double, double).
+ *
+ * Streams: `stream` is a cudaStream_t passed as void*.  Every call only
+ * enqueues work on that stream and returns; results are ready when the stream
+ * reaches that point.  Solvers write their tp_info to DEVICE memory.
+ *
+ * Errors: argument and launch errors are returned synchronously (nothing is
+ * enqueued on an argument error).  Algorithmic outcomes (discrepancy principle
+ * not met within the caps, a wait that timed out) are written to
+ * info->status; X then holds the last candidate solution.
+ *
+ * Memory: the library never allocates device memory on these paths.  Solvers
+ * and tprod_gemm take a caller-provided workspace of at least the size that
+ * the matching *_workspace_bytes() query returns; ws must be 256-byte aligned.
+ */
+#ifndef TPROD_H
+#define TPROD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TP_OK = 0,
+    TP_ERR_ARG = -1,            /* invalid argument (sizes, pointers, precision)      */
+    TP_ERR_CUDA = -2,           /* a CUDA launch or attribute call failed              */
+    TP_ERR_WORKSPACE = -3,      /* workspace missing, misaligned or too small          */
+    TP_ERR_BREAKDOWN = -4,      /* reserved: exact breakdown reported by a solver      */
+    TP_ERR_NOT_CONVERGED = -5,  /* discrepancy principle not met within r_max / k_max  */
+    TP_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up                  */
+    TP_ERR_UNSUPPORTED = -7     /* valid request outside what this build supports      */
+} tp_status;
+
+typedef enum { TP_FP32 = 0, TP_FP64 = 1 } tp_precision;
+
+/* Result record of a solve, written to device memory. */
+typedef struct {
+    int status;         /* tp_status of the algorithm (TP_OK, TP_ERR_NOT_CONVERGED, ...)  */
+    int k;              /* truncation index / number of tGKB steps chosen                 */
+    int r;              /* RT-tSVD: sketch rank reached by Algorithm 3; tGKB: steps run   */
+    int sweeps;         /* RT-tSVD: Jacobi sweeps used (max over slices); else bisection  */
+    double residual;    /* ||B - A*X||_F of the returned X as the method measures it       */
+    double tau_delta;   /* tau * delta                                                     */
+    double eta;         /* RT-tSVD: final error indicator eta (Theorem 4.2); else unused  */
+    double mu;          /* tGKT: regularisation parameter; else 0                          */
+    double margin;      /* min over {k, k-1} of |res - tau*delta| / (tau*delta)            */
+    double norm_a2;     /* ||A||_F^2                                                       */
+} tp_info;
+
+/* ---------------------------------------------------------------- DFT -----
+ * tprod_fft: mode-3 DFT of a real tensor (Section 2: fft(A,[],3), the
+ * unnormalised transform x_s = sum_k x_k exp(-2 pi i s k / n)), keeping the
+ * h = n/2+1 non-redundant slices of the conjugate-symmetric result.
+ *   A    : real (n, l, m)            Ahat : complex (h, l, m)
+ * tprod_ifft: the inverse (with 1/n), reading a half spectrum and writing
+ * the real tensor; the imaginary parts of slices 0 and n/2 are ignored.
+ *   Xhat : complex (h, l, m)         X    : real (n, l, m)
+ * Both: l, m, n >= 1.  No workspace.
+ */
+tp_status tprod_fft(const void* A, int l, int m, int n, void* Ahat, int prec, void* stream);
+tp_status tprod_ifft(const void* Xhat, int l, int m, int n, void* X, int prec, void* stream);
+
+/* ---------------------------------------------------------- t-product -----
+ * tprod_gemm: C = op(A) * B, the t-product of Definition 2.1 computed as
+ * mode-3 DFT, one complex matrix product per Fourier slice, inverse DFT.
+ *   transA = 0: A is l x kk x n, array (n, l, kk);  C is l x m x n
+ *   transA = 1: op(A) = A^T, the t-transpose of Section 2 (each frontal slice
+ *               transposed, slices 2..n reversed); A is kk x l x n,
+ *               array (n, kk, l).
+ *   B : real (n, kk, m);  C : real (n, l, m)
+ * Workspace: tprod_gemm_workspace_bytes(l, kk, m, n, prec).
+ */
+size_t tprod_gemm_workspace_bytes(int l, int kk, int m, int n, int prec);
+tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m, int n,
+                     int transA, int prec, void* ws, size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------------- RT-tSVD ------
+ * rtsvd_truncated_solve: the RT-tSVD method of Section 4.2.
+ * Algorithm 3 in block form: Gaussian lateral slices are taken `block` at a
+ * time from Omega (slice c of Omega is the c-th Gaussian slice G), sketched
+ * with q_power power iterations, orthonormalised against the basis so far
+ * (two classical Gram-Schmidt passes, then column by column with Normalize),
+ * and the error indicator eta = ||A||_F^2 - ||Bt||_F^2 (Theorems 4.1-4.2) is
+ * updated per block until eta < eps^2 or r = r_max.  The full tSVD of Bt gives
+ * U_k = Q*U(:,1:k,:), S_k, V_k and X_k = V_k * S_k^{-1} * U_k^T * B; k is the
+ * smallest index in [max(1, r - p_over), r] (Eq. (kinit)) with
+ * ||B - A*X_k||_F <= tau*delta (Eq. (disp)), else k = r and status
+ * TP_ERR_NOT_CONVERGED.  Singular values at or below max(l,m)*eps*sigma_max
+ * are treated as zero.
+ *   A     : real (n, l, m)       B : real (n, l, 1)     X : real (n, m, 1)
+ *   Omega : real (n, m, r_max)   (Gaussian test slices, supplied by the caller)
+ * Limits: 1 <= block <= 32; r_max <= min(l, m); r_max <= 160 (FP32) or
+ * 112 (FP64); l, m <= 1024; p = 1.
+ */
+typedef struct {
+    double delta;       /* noise bound of Eq. (errbd)                                 */
+    double tau;         /* discrepancy factor tau > 1                                 */
+    double eps;         /* Algorithm 3 tolerance (absolute); if <= 0 use eps_rel      */
+    double eps_rel;     /* tolerance relative to ||A||_F, used when eps <= 0          */
+    int p_over;         /* oversampling rho of Eq. (kinit)                            */
+    int q_power;        /* power iterations per block (0 = Algorithm 3's sketch)      */
+    int block;          /* Gaussian slices per block (1 = Algorithm 3)                */
+    int r_max;          /* cap on the sketch rank                                     */
+    double* res_hist;   /* optional device array (r_max+1): ||B - A*X_k|| for
+                           k in [k_init, r]; other entries set to -1                 */
+} tp_rtsvd_params;
+
+size_t rtsvd_workspace_bytes(int l, int m, int n, int p, const tp_rtsvd_params* params, int prec);
+tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
+                                int l, int m, int n, int p, const tp_rtsvd_params* params,
+                                void* X, tp_info* d_info, int prec,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/* -------------------------------------------------------------- tGKB ------
+ * tgkb_solve: the tGKB method (Algorithm 4 with both reorthogonalisation
+ * steps done as two classical Gram-Schmidt passes).  After step i the
+ * projected problem min ||P_i * Y - e_1 * z_1||_F (Eq. (9tt)) is solved per
+ * Fourier slice (Givens QR of the lower-bidiagonal slice of P_i); the first i
+ * with residual <= tau*delta gives k and X_k = W_k * Y_k (Eq. (solgkb)).
+ * Normalize's breakdown branch (a zero Fourier slice) yields a zero vector
+ * and a zero coefficient.  The whole iteration is one persistent launch with
+ * one CTA per Fourier slice; its grid-wide wait is bounded (info->status
+ * TP_ERR_TIMEOUT if it gives up).
+ *   A : real (n, l, m)     B : real (n, l, 1)     X : real (n, m, 1)
+ * Limits: k_max <= min(l, m, 512); l, m <= 1024; p = 1.
+ */
+typedef struct {
+    double delta;       /* noise bound of Eq. (errbd)                                 */
+    double tau;         /* discrepancy factor                                         */
+    int k_max;          /* step cap                                                   */
+    double* res_hist;   /* optional device array (k_max+1): residual after step i     */
+} tp_tgkb_params;
+
+size_t tgkb_workspace_bytes(int l, int m, int n, int p, const tp_tgkb_params* params, int prec);
+tp_status tgkb_solve(const void* A, const void* B, int l, int m, int n, int p,
+                     const tp_tgkb_params* params, void* X, tp_info* d_info, int prec,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* -------------------------------------------------------------- tGKT ------
+ * tgkb_tikhonov_solve: tGKB as above fixes k; then per Fourier slice
+ *   y_mu = argmin ||P_k y - z_1 e_1||^2 + mu^{-1} ||y||^2
+ * with one scalar mu for all slices, chosen on log10(mu) in [mu_lo, mu_hi]
+ * (Section 5) so that ||B - A*X_mu||_F = tau*delta, to a bracket width of
+ * log_tol in log10(mu).  If even mu_hi leaves the residual above tau*delta,
+ * mu = mu_hi and status TP_ERR_NOT_CONVERGED; if mu_lo already meets it,
+ * mu = mu_lo.  X = W_k * Y_mu.
+ */
+typedef struct {
+    tp_tgkb_params gkb;
+    double mu_lo, mu_hi;   /* search interval, 0 < mu_lo < mu_hi                       */
+    double log_tol;        /* bracket width in log10(mu); <= 0 selects 1e-12           */
+} tp_tik_params;
+
+size_t tgkb_tikhonov_workspace_bytes(int l, int m, int n, int p, const tp_tik_params* params, int prec);
+tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n, int p,
+                              const tp_tik_params* params, void* X, tp_info* d_info, int prec,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------ misc -------- */
+const char* tp_status_string(int status);
+int tp_version(void);                 /* 100 * major + minor                        */
+int tp_kernel_launches(void);         /* kernels enqueued by this library so far    */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPROD_H */

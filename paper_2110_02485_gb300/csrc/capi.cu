@@ -1,0 +1,172 @@
+// extern "C" entry points of libtprod (declared in include/tprod.h).
+#include "common.cuh"
+#include "internal.h"
+
+namespace tp {
+
+int g_launches = 0;
+
+template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_params*);
+template <typename T>
+tp_status rt_solve(const T*, const T*, const T*, int, int, int, int, const tp_rtsvd_params*, T*, tp_info*, void*,
+                   size_t, cudaStream_t);
+template <typename T> size_t gk_ws_bytes(int, int, int, int, const tp_tgkb_params*);
+template <typename T>
+tp_status gk_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
+                   cudaStream_t);
+template <typename T> size_t tik_ws_bytes(int, int, int, int, const tp_tik_params*);
+template <typename T>
+tp_status tik_solve(const T*, const T*, int, int, int, int, const tp_tik_params*, T*, tp_info*, void*, size_t,
+                    cudaStream_t);
+
+static bool dims_ok(int l, int m, int n, int prec) {
+    if (l < 1 || m < 1 || n < 1) return false;
+    if (prec != TP_FP32 && prec != TP_FP64) return false;
+    if (n > (prec == TP_FP32 ? 1024 : 512)) return false;
+    return (long)l * m * n < (1L << 40);
+}
+
+template <typename T>
+static tp_status fft_t(const void* A, int l, int m, int n, void* Ahat, cudaStream_t st) {
+    return rdft<T>((const T*)A, Ahat, n, l, m, m, (long)l * m, nullptr, nullptr, st);
+}
+template <typename T>
+static tp_status ifft_t(const void* Xh, int l, int m, int n, void* X, cudaStream_t st) {
+    return irdft<T>(Xh, (T*)X, n, l, m, m, (long)l * m, nullptr, st);
+}
+
+static size_t gemm_ws(int l, int kk, int m, int n, size_t c) {
+    const size_t h = n / 2 + 1;
+    return align256(h * l * kk * c) + align256(h * kk * m * c) + align256(h * l * m * c);
+}
+
+template <typename T>
+static tp_status gemm_t(const void* A, const void* B, void* C, int l, int kk, int m, int n, int transA, void* ws,
+                        cudaStream_t st) {
+    const int h = n / 2 + 1;
+    const size_t c = 2 * sizeof(T);
+    char* p = (char*)ws;
+    void* Ah = p;
+    void* Bh = p + align256((size_t)h * l * kk * c);
+    void* Ch = (char*)Bh + align256((size_t)h * kk * m * c);
+    // A is (n, l, kk) or, transposed, (n, kk, l)
+    const int ar = transA ? kk : l, ac = transA ? l : kk;
+    tp_status e = rdft<T>((const T*)A, Ah, n, ar, ac, ac, (long)ar * ac, nullptr, nullptr, st);
+    if (e != TP_OK) return e;
+    e = rdft<T>((const T*)B, Bh, n, kk, m, m, (long)kk * m, nullptr, nullptr, st);
+    if (e != TP_OK) return e;
+    e = cgemm<T>(h, l, m, kk, nullptr, nullptr, nullptr, 1, 0, Ah, ac, (long)ar * ac, transA ? OP_C : OP_N, Bh, m,
+                 (long)kk * m, OP_N, 0, 0, Ch, m, (long)l * m, nullptr, st);
+    if (e != TP_OK) return e;
+    return irdft<T>(Ch, (T*)C, n, l, m, m, (long)l * m, nullptr, st);
+}
+
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" {
+
+tp_status tprod_fft(const void* A, int l, int m, int n, void* Ahat, int prec, void* stream) {
+    if (!A || !Ahat || !dims_ok(l, m, n, prec)) return TP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == TP_FP32 ? fft_t<float>(A, l, m, n, Ahat, st) : fft_t<double>(A, l, m, n, Ahat, st);
+}
+
+tp_status tprod_ifft(const void* Xhat, int l, int m, int n, void* X, int prec, void* stream) {
+    if (!Xhat || !X || !dims_ok(l, m, n, prec)) return TP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == TP_FP32 ? ifft_t<float>(Xhat, l, m, n, X, st) : ifft_t<double>(Xhat, l, m, n, X, st);
+}
+
+size_t tprod_gemm_workspace_bytes(int l, int kk, int m, int n, int prec) {
+    if (!dims_ok(l, kk, n, prec) || m < 1) return 0;
+    return gemm_ws(l, kk, m, n, prec == TP_FP32 ? 8 : 16);
+}
+
+tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m, int n, int transA, int prec,
+                     void* ws, size_t ws_bytes, void* stream) {
+    if (!A || !B || !C || !dims_ok(l, kk, n, prec) || !dims_ok(kk, m, n, prec)) return TP_ERR_ARG;
+    if (transA != 0 && transA != 1) return TP_ERR_ARG;
+    if (l > 65535 * 128) return TP_ERR_ARG;
+    const size_t need = gemm_ws(l, kk, m, n, prec == TP_FP32 ? 8 : 16);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < need) return TP_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == TP_FP32 ? gemm_t<float>(A, B, C, l, kk, m, n, transA, ws, st)
+                           : gemm_t<double>(A, B, C, l, kk, m, n, transA, ws, st);
+}
+
+size_t rtsvd_workspace_bytes(int l, int m, int n, int p, const tp_rtsvd_params* params, int prec) {
+    if (prec == TP_FP32) return rt_ws_bytes<float>(l, m, n, p, params);
+    if (prec == TP_FP64) return rt_ws_bytes<double>(l, m, n, p, params);
+    return 0;
+}
+
+tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega, int l, int m, int n, int p,
+                                const tp_rtsvd_params* params, void* X, tp_info* d_info, int prec, void* ws,
+                                size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return rt_solve<float>((const float*)A, (const float*)B, (const float*)Omega, l, m, n, p, params, (float*)X,
+                               d_info, ws, ws_bytes, st);
+    if (prec == TP_FP64)
+        return rt_solve<double>((const double*)A, (const double*)B, (const double*)Omega, l, m, n, p, params,
+                                (double*)X, d_info, ws, ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+size_t tgkb_workspace_bytes(int l, int m, int n, int p, const tp_tgkb_params* params, int prec) {
+    if (prec == TP_FP32) return gk_ws_bytes<float>(l, m, n, p, params);
+    if (prec == TP_FP64) return gk_ws_bytes<double>(l, m, n, p, params);
+    return 0;
+}
+
+tp_status tgkb_solve(const void* A, const void* B, int l, int m, int n, int p, const tp_tgkb_params* params, void* X,
+                     tp_info* d_info, int prec, void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return gk_solve<float>((const float*)A, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws, ws_bytes,
+                               st);
+    if (prec == TP_FP64)
+        return gk_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
+                                ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+size_t tgkb_tikhonov_workspace_bytes(int l, int m, int n, int p, const tp_tik_params* params, int prec) {
+    if (prec == TP_FP32) return tik_ws_bytes<float>(l, m, n, p, params);
+    if (prec == TP_FP64) return tik_ws_bytes<double>(l, m, n, p, params);
+    return 0;
+}
+
+tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n, int p, const tp_tik_params* params,
+                              void* X, tp_info* d_info, int prec, void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return tik_solve<float>((const float*)A, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws,
+                                ws_bytes, st);
+    if (prec == TP_FP64)
+        return tik_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
+                                 ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+const char* tp_status_string(int status) {
+    switch (status) {
+        case TP_OK: return "ok";
+        case TP_ERR_ARG: return "invalid argument";
+        case TP_ERR_CUDA: return "CUDA launch or attribute call failed";
+        case TP_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case TP_ERR_BREAKDOWN: return "breakdown";
+        case TP_ERR_NOT_CONVERGED: return "discrepancy principle not met within the cap";
+        case TP_ERR_TIMEOUT: return "bounded device-side wait gave up";
+        case TP_ERR_UNSUPPORTED: return "request not supported by this build or device";
+        default: return "unknown status";
+    }
+}
+
+int tp_version(void) { return 100; }
+
+int tp_kernel_launches(void) { return g_launches; }
+
+}  // extern "C"

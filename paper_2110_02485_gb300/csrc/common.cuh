@@ -1,0 +1,80 @@
+// Shared device helpers for the t-product library: complex arithmetic on
+// float2/double2, warp and block reductions, launch bookkeeping.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "tprod.h"
+
+namespace tp {
+
+template <typename T> struct C2;
+template <> struct C2<float> { typedef float2 type; };
+template <> struct C2<double> { typedef double2 type; };
+template <typename T> using cplx = typename C2<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T x, T y) {
+    cplx<T> r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename V> __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// acc += a * b
+template <typename V> __device__ __forceinline__ void cfma(V& acc, V a, V b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename V> __device__ __forceinline__ void cfmac(V& acc, V a, V b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(a.x) s) { a.x *= s; a.y *= s; return a; }
+template <typename V> __device__ __forceinline__ double cabs2d(V a) {
+    return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+}
+
+template <typename S> __device__ __forceinline__ S warp_sum(S v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of one value per thread over the block; every thread gets the result.
+// `red` must hold blockDim.x/32 doubles.  Contains two __syncthreads().
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    return t;
+}
+
+template <typename T> struct Eps;
+template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+
+// Parseval weight of half-spectrum slice s for transform length n.
+__host__ __device__ __forceinline__ double parseval_w(int s, int n) {
+    return (s == 0 || 2 * s == n) ? 1.0 : 2.0;
+}
+
+}  // namespace tp

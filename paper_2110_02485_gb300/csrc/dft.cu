@@ -1,0 +1,277 @@
+// Mode-3 DFT along the tubes of a frontal-slice-major tensor (Section 2:
+// fft(A,[],3) and its inverse), real data <-> half spectrum.
+//
+// One CTA owns 32 tubes and all n of their entries: slice k of the 32 tubes
+// is one coalesced row read, the transform runs in shared memory, and each
+// output slice is one coalesced 32-element row write.  For power-of-two n two
+// real tubes are packed into one complex sequence (x_a + i x_b), transformed by
+// an in-place radix-2 decimation-in-time FFT and separated again; for other n
+// the DFT sum is evaluated directly from a table of the n roots of unity.
+// The forward kernel can also emit one float64 partial sum of squares per CTA
+// (used for ||A||_F^2).
+#include "common.cuh"
+#include "internal.h"
+
+namespace tp {
+
+constexpr int DFT_TILE = 32;
+constexpr int DFT_THREADS = 256;
+
+template <typename T> __device__ __forceinline__ void sincospi_t(T x, T* s, T* c);
+template <> __device__ __forceinline__ void sincospi_t<float>(float x, float* s, float* c) { sincospif(x, s, c); }
+template <> __device__ __forceinline__ void sincospi_t<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+
+__device__ __forceinline__ long tube_off(long t, int cols, long ld) {
+    long r = t / cols;
+    return r * ld + (t - r * cols);
+}
+__device__ __forceinline__ int bitrev(int x, int logn) {
+    return logn ? (int)(__brev((unsigned)x) >> (32 - logn)) : 0;
+}
+
+// exp(sign * 2 pi i m / n) for m < count
+template <typename T>
+__device__ void fill_roots(cplx<T>* tw, int count, int n, T sign) {
+    for (int m = threadIdx.x; m < count; m += blockDim.x) {
+        T s, c;
+        sincospi_t<T>((T)(2 * m) / (T)n, &s, &c);
+        tw[m] = mk<T>(c, sign * s);
+    }
+}
+
+// In-place radix-2 DIT over the 16 packed sequences z[k*16 + p] (input in
+// bit-reversed order, output natural).  tw holds exp(+-2 pi i m / n), m < n/2.
+template <typename T>
+__device__ void fft16_inplace(cplx<T>* z, const cplx<T>* tw, int n) {
+    for (int lh = 0; (1 << (lh + 1)) <= n; ++lh) {
+        const int half = 1 << lh, step = n >> (lh + 1);
+        for (int e = threadIdx.x; e < (n >> 1) * 16; e += blockDim.x) {
+            const int p = e & 15, bf = e >> 4;
+            const int j = bf & (half - 1), grp = bf >> lh;
+            const int i1 = (grp << (lh + 1)) + j, i2 = i1 + half;
+            cplx<T> a = z[i1 * 16 + p];
+            cplx<T> b = cmul(z[i2 * 16 + p], tw[j * step]);
+            z[i1 * 16 + p] = cadd(a, b);
+            z[i2 * 16 + p] = csub(a, b);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ void store_partial(double v, double* sumsq) {
+    __shared__ double red[DFT_THREADS / 32];
+    double t = block_sum(v, red);
+    if (sumsq && threadIdx.x == 0) sumsq[blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DFT_THREADS)
+k_rdft_pow2(const T* __restrict__ X, cplx<T>* __restrict__ Xh, int n, int logn, long tubes, int cols,
+            long ld, long ss, double* sumsq, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* z = (cplx<T>*)smraw;
+    cplx<T>* tw = z + (size_t)n * 16;
+    T* zf = (T*)z;
+    const long t0 = (long)blockIdx.x * DFT_TILE;
+    fill_roots<T>(tw, n / 2, n, (T)-1);
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
+        const int k = e >> 5, tt = e & 31;
+        const long t = t0 + tt;
+        T v = (T)0;
+        if (t < tubes) v = X[(long)k * ss + tube_off(t, cols, ld)];
+        acc += (double)v * (double)v;
+        zf[((size_t)bitrev(k, logn) * 16 + (tt & 15)) * 2 + (tt >> 4)] = v;
+    }
+    __syncthreads();
+    fft16_inplace<T>(z, tw, n);
+    const int h = n / 2 + 1;
+    for (int e = threadIdx.x; e < h * DFT_TILE; e += blockDim.x) {
+        const int s = e >> 5, tt = e & 31;
+        const long t = t0 + tt;
+        if (t >= tubes) continue;
+        const int p = tt & 15;
+        cplx<T> zs = z[s * 16 + p];
+        cplx<T> zc = cconj(z[((n - s) & (n - 1)) * 16 + p]);
+        cplx<T> o;
+        if (tt < 16) o = mk<T>((zs.x + zc.x) * (T)0.5, (zs.y + zc.y) * (T)0.5);
+        else o = mk<T>((zs.y - zc.y) * (T)0.5, -(zs.x - zc.x) * (T)0.5);
+        Xh[(long)s * tubes + t] = o;
+    }
+    store_partial<T>(acc, sumsq);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DFT_THREADS)
+k_rdft_direct(const T* __restrict__ X, cplx<T>* __restrict__ Xh, int n, long tubes, int cols,
+              long ld, long ss, double* sumsq, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = (cplx<T>*)smraw;
+    T* x = (T*)(tw + n);
+    const long t0 = (long)blockIdx.x * DFT_TILE;
+    fill_roots<T>(tw, n, n, (T)-1);
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
+        const int k = e >> 5, tt = e & 31;
+        const long t = t0 + tt;
+        T v = (T)0;
+        if (t < tubes) v = X[(long)k * ss + tube_off(t, cols, ld)];
+        acc += (double)v * (double)v;
+        x[e] = v;
+    }
+    __syncthreads();
+    const int h = n / 2 + 1;
+    for (int e = threadIdx.x; e < h * DFT_TILE; e += blockDim.x) {
+        const int s = e >> 5, tt = e & 31;
+        const long t = t0 + tt;
+        cplx<T> o = mk<T>(0, 0);
+        int idx = 0;
+        for (int k = 0; k < n; ++k) {
+            const T v = x[k * DFT_TILE + tt];
+            o.x = fma(v, tw[idx].x, o.x);
+            o.y = fma(v, tw[idx].y, o.y);
+            idx += s;
+            if (idx >= n) idx -= n;
+        }
+        if (t < tubes) Xh[(long)s * tubes + t] = o;
+    }
+    store_partial<T>(acc, sumsq);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DFT_THREADS)
+k_irdft_pow2(const cplx<T>* __restrict__ Xh, T* __restrict__ X, int n, int logn, long tubes, int cols,
+             long ld, long ss, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* z = (cplx<T>*)smraw;
+    cplx<T>* tw = z + (size_t)n * 16;
+    const long t0 = (long)blockIdx.x * DFT_TILE;
+    fill_roots<T>(tw, n / 2, n, (T)1);
+    const int h = n / 2 + 1;
+    for (int e = threadIdx.x; e < h * 16; e += blockDim.x) {
+        const int s = e >> 4, p = e & 15;
+        const long ta = t0 + p, tb = t0 + p + 16;
+        cplx<T> xa = mk<T>(0, 0), xb = mk<T>(0, 0);
+        if (ta < tubes) xa = Xh[(long)s * tubes + ta];
+        if (tb < tubes) xb = Xh[(long)s * tubes + tb];
+        const bool self = (s == 0) || (2 * s == n);
+        if (self) { xa.y = 0; xb.y = 0; }
+        z[bitrev(s, logn) * 16 + p] = mk<T>(xa.x - xb.y, xa.y + xb.x);
+        if (!self) z[bitrev(n - s, logn) * 16 + p] = mk<T>(xa.x + xb.y, xb.x - xa.y);
+    }
+    __syncthreads();
+    fft16_inplace<T>(z, tw, n);
+    const T inv = (T)1 / (T)n;
+    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
+        const int k = e >> 5, tt = e & 31;
+        const long t = t0 + tt;
+        if (t >= tubes) continue;
+        cplx<T> v = z[k * 16 + (tt & 15)];
+        X[(long)k * ss + tube_off(t, cols, ld)] = (tt < 16 ? v.x : v.y) * inv;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DFT_THREADS)
+k_irdft_direct(const cplx<T>* __restrict__ Xh, T* __restrict__ X, int n, long tubes, int cols,
+               long ld, long ss, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = (cplx<T>*)smraw;
+    cplx<T>* xs = tw + n;
+    const long t0 = (long)blockIdx.x * DFT_TILE;
+    fill_roots<T>(tw, n, n, (T)1);
+    const int h = n / 2 + 1;
+    for (int e = threadIdx.x; e < h * DFT_TILE; e += blockDim.x) {
+        const int s = e >> 5, tt = e & 31;
+        const long t = t0 + tt;
+        cplx<T> v = mk<T>(0, 0);
+        if (t < tubes) v = Xh[(long)s * tubes + t];
+        if (s == 0 || 2 * s == n) v.y = 0;
+        xs[e] = v;
+    }
+    __syncthreads();
+    const T inv = (T)1 / (T)n;
+    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
+        const int k = e >> 5, tt = e & 31;
+        const long t = t0 + tt;
+        T acc = xs[tt].x;  // slice 0
+        int idx = k;
+        for (int s = 1; s < h; ++s) {
+            const cplx<T> v = xs[s * DFT_TILE + tt];
+            const T wgt = (2 * s == n) ? (T)1 : (T)2;
+            acc += wgt * (v.x * tw[idx].x - v.y * tw[idx].y);
+            idx += k;
+            if (idx >= n) idx -= n;
+        }
+        if (t < tubes) X[(long)k * ss + tube_off(t, cols, ld)] = acc * inv;
+    }
+}
+
+static inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+static inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+int rdft_parts(int rows, int cols) { return (int)(((long)rows * cols + DFT_TILE - 1) / DFT_TILE); }
+
+size_t rdft_smem(int n, size_t elem) {
+    const size_t c = 2 * elem;
+    if (is_pow2(n)) return ((size_t)n * 16 + n / 2) * c;
+    const size_t fwd = (size_t)n * c + (size_t)n * DFT_TILE * elem;
+    const size_t inv = (size_t)n * c + (size_t)(n / 2 + 1) * DFT_TILE * c;
+    return fwd > inv ? fwd : inv;
+}
+
+template <typename K>
+static tp_status prep(K kern, size_t smem) {
+    if (smem > 48 * 1024)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return TP_ERR_CUDA;
+    return TP_OK;
+}
+
+template <typename T>
+tp_status rdft(const T* X, void* Xh, int n, int rows, int cols, long ld, long ss, double* sumsq,
+               const int* skip, cudaStream_t st) {
+    const long tubes = (long)rows * cols;
+    if (tubes == 0) return TP_OK;
+    const unsigned grid = (unsigned)((tubes + DFT_TILE - 1) / DFT_TILE);
+    const size_t smem = rdft_smem(n, sizeof(T));
+    if (is_pow2(n)) {
+        if (prep(k_rdft_pow2<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        k_rdft_pow2<T><<<grid, DFT_THREADS, smem, st>>>(X, (cplx<T>*)Xh, n, ilog2(n), tubes, cols, ld, ss,
+                                                         sumsq, skip);
+    } else {
+        if (prep(k_rdft_direct<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        k_rdft_direct<T><<<grid, DFT_THREADS, smem, st>>>(X, (cplx<T>*)Xh, n, tubes, cols, ld, ss, sumsq, skip);
+    }
+    return last_launch();
+}
+
+template <typename T>
+tp_status irdft(const void* Xh, T* X, int n, int rows, int cols, long ld, long ss, const int* skip,
+                cudaStream_t st) {
+    const long tubes = (long)rows * cols;
+    if (tubes == 0) return TP_OK;
+    const unsigned grid = (unsigned)((tubes + DFT_TILE - 1) / DFT_TILE);
+    const size_t smem = rdft_smem(n, sizeof(T));
+    if (is_pow2(n)) {
+        if (prep(k_irdft_pow2<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        k_irdft_pow2<T><<<grid, DFT_THREADS, smem, st>>>((const cplx<T>*)Xh, X, n, ilog2(n), tubes, cols, ld,
+                                                          ss, skip);
+    } else {
+        if (prep(k_irdft_direct<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        k_irdft_direct<T><<<grid, DFT_THREADS, smem, st>>>((const cplx<T>*)Xh, X, n, tubes, cols, ld, ss, skip);
+    }
+    return last_launch();
+}
+
+template tp_status rdft<float>(const float*, void*, int, int, int, long, long, double*, const int*, cudaStream_t);
+template tp_status rdft<double>(const double*, void*, int, int, int, long, long, double*, const int*, cudaStream_t);
+template tp_status irdft<float>(const void*, float*, int, int, int, long, long, const int*, cudaStream_t);
+template tp_status irdft<double>(const void*, double*, int, int, int, long, long, const int*, cudaStream_t);
+
+}  // namespace tp

@@ -1,0 +1,624 @@
+// tGKB (Algorithm 4) and the tGKB / Tikhonov-tGKB methods on the half spectrum.
+//
+// Every t-operation of Algorithm 4 is facewise in the Fourier domain, so each
+// Fourier slice runs its own Golub-Kahan bidiagonalisation; the slices are
+// coupled only by the discrepancy test, whose residual is the Parseval sum of
+// the per-slice least-squares residuals.  The whole iteration is one
+// persistent cooperative launch with one CTA per slice: after each step a CTA
+// publishes its residual and waits (bounded) until all slices have done the
+// step, then every CTA evaluates the same fixed-order sum and so takes the
+// same stop decision.  Normalize's coefficients are non-negative reals per
+// slice, so the projected problem of each slice is a real lower-bidiagonal
+// least-squares problem, solved incrementally by Givens rotations (float64).
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tp {
+
+constexpr int GKB_THREADS = 256;
+constexpr int GKB_KMAX = 512;
+
+struct GkbShared {
+    double res[GKB_KMAX + 1];   // global residual after step i
+    double rho[GKB_KMAX], theta[GKB_KMAX + 1], phi[GKB_KMAX];
+    double y[GKB_KMAX];
+};
+
+template <typename T>
+__device__ void mv_h(const cplx<T>* __restrict__ A, int l, int m, const cplx<T>* q, cplx<T>* u) {
+    // u[j] = sum_i conj(A[i][j]) q[i]
+    for (int j0 = threadIdx.x; j0 < m; j0 += 4 * blockDim.x) {
+        cplx<T> acc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = mk<T>(0, 0);
+        int i = 0;
+        for (; i + 4 <= l; i += 4) {
+            cplx<T> a[4][4];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = j0 + c * blockDim.x;
+                    a[rr][c] = j < m ? A[(long)(i + rr) * m + j] : mk<T>(0, 0);
+                }
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const cplx<T> qv = q[i + rr];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cfmac(acc[c], a[rr][c], qv);
+            }
+        }
+        for (; i < l; ++i) {
+            const cplx<T> qv = q[i];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + c * blockDim.x;
+                if (j < m) cfmac(acc[c], A[(long)i * m + j], qv);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = j0 + c * blockDim.x;
+            if (j < m) u[j] = acc[c];
+        }
+    }
+}
+
+template <typename T>
+__device__ void mv_n(const cplx<T>* __restrict__ A, int l, int m, const cplx<T>* w, cplx<T>* u) {
+    // u[i] = sum_j A[i][j] w[j]; one warp per row, two rows at a time
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp * 2; i < l; i += 2 * nw) {
+        cplx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+        const bool two = (i + 1) < l;
+        for (int j = lane; j < m; j += 32) {
+            const cplx<T> wv = w[j];
+            cfma(a0, A[(long)i * m + j], wv);
+            if (two) cfma(a1, A[(long)(i + 1) * m + j], wv);
+        }
+        a0.x = warp_sum(a0.x);
+        a0.y = warp_sum(a0.y);
+        a1.x = warp_sum(a1.x);
+        a1.y = warp_sum(a1.y);
+        if (lane == 0) {
+            u[i] = a0;
+            if (two) u[i + 1] = a1;
+        }
+    }
+}
+
+// Two classical Gram-Schmidt passes of u (length L, shared) against cnt basis
+// vectors stored contiguously (stride L) in global memory.
+template <typename T>
+__device__ void reorth(cplx<T>* u, const cplx<T>* basis, int cnt, int L, cplx<T>* cf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (cnt <= 0) return;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = warp; i < cnt; i += nw) {
+            cplx<T> acc = mk<T>(0, 0);
+            const cplx<T>* bv = basis + (long)i * L;
+            for (int e = lane; e < L; e += 32) cfmac(acc, bv[e], u[e]);
+            acc.x = warp_sum(acc.x);
+            acc.y = warp_sum(acc.y);
+            if (lane == 0) cf[i] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < L; e += blockDim.x) {
+            cplx<T> acc = mk<T>(0, 0);
+            for (int i = 0; i < cnt; ++i) cfma(acc, basis[(long)i * L + e], cf[i]);
+            u[e] = csub(u[e], acc);
+        }
+        __syncthreads();
+    }
+}
+
+// Normalize (per slice): returns ||u|| and scales u to unit length (zero stays zero).
+template <typename T>
+__device__ double normalize_vec(cplx<T>* u, int L, double* red, double* bc) {
+    double p = 0.0;
+    for (int e = threadIdx.x; e < L; e += blockDim.x) p += cabs2d(u[e]);
+    p = block_sum(p, red);
+    if (threadIdx.x == 0) *bc = p;
+    __syncthreads();
+    const double nrm2 = *bc;
+    const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+    for (int e = threadIdx.x; e < L; e += blockDim.x) {
+        const cplx<T> v = u[e];
+        u[e] = mk<T>((T)((double)v.x * inv), (T)((double)v.y * inv));
+    }
+    __syncthreads();
+    return sqrt(nrm2);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Persistent tGKB.  Outputs per slice: W (k_max x m), Q (k_max+1 x l),
+// c (k_max), z (k_max+1), Xhat (m) for the chosen k; State k/status; info.
+template <typename T>
+__global__ void __launch_bounds__(GKB_THREADS)
+k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l, int m, int n, int h, int k_max,
+      double tau_delta, cplx<T>* Wb, cplx<T>* Qb, double* cc, double* zz, double* res2, unsigned* counters,
+      cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info) {
+    typedef cplx<T> V;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int L = l > m ? l : m;
+    V* q = (V*)smraw;           // l
+    V* w = q + l;               // m
+    V* u = w + m;               // L
+    V* cf = u + L;              // k_max + 1
+    __shared__ GkbShared S;
+    __shared__ double red[GKB_THREADS / 32];
+    __shared__ double bc;
+    __shared__ int flag_done, flag_timeout;
+    const int s = blockIdx.x, tid = threadIdx.x;
+    const V* A = Ahat + (long)s * l * m;
+    V* W = Wb + (long)s * k_max * m;
+    V* Qv = Qb + (long)s * (k_max + 1) * l;
+    double* cs_ = cc + (long)s * k_max;
+    double* zs_ = zz + (long)s * (k_max + 1);
+    const double ws = parseval_w(s, n);
+
+    for (int e = tid; e < l; e += blockDim.x) u[e] = Bhat[(long)s * l + e];
+    for (int e = tid; e < m; e += blockDim.x) w[e] = mk<T>(0, 0);
+    __syncthreads();
+    const double z1 = normalize_vec<T>(u, l, red, &bc);
+    for (int e = tid; e < l; e += blockDim.x) {
+        q[e] = u[e];
+        Qv[e] = u[e];
+    }
+    if (tid == 0) {
+        zs_[0] = z1;
+        flag_done = 0;
+        flag_timeout = 0;
+    }
+    __syncthreads();
+
+    // Givens state (thread 0): rhobar, phibar, previous rotation, orphan residual
+    double phibar = z1, cs_prev = 1.0, sn_prev = 0.0, orphan = 0.0;
+    double zprev = z1;
+    int k = k_max;
+    for (int i = 1; i <= k_max; ++i) {
+        // W_i = A^T * Q_i - W_{i-1} * z_i ; reorthogonalise ; Normalize -> c_i
+        mv_h<T>(A, l, m, q, u);
+        __syncthreads();
+        for (int e = tid; e < m; e += blockDim.x) u[e] = csub(u[e], cscale(w[e], (T)zprev));
+        __syncthreads();
+        reorth<T>(u, W, i - 1, m, cf);
+        const double ci = normalize_vec<T>(u, m, red, &bc);
+        for (int e = tid; e < m; e += blockDim.x) {
+            w[e] = u[e];
+            W[(long)(i - 1) * m + e] = u[e];
+        }
+        __syncthreads();
+        // Q_{i+1} = A * W_i - Q_i * c_i ; reorthogonalise ; Normalize -> z_{i+1}
+        mv_n<T>(A, l, m, w, u);
+        __syncthreads();
+        for (int e = tid; e < l; e += blockDim.x) u[e] = csub(u[e], cscale(q[e], (T)ci));
+        __syncthreads();
+        reorth<T>(u, Qv, i, l, cf);
+        const double zi = normalize_vec<T>(u, l, red, &bc);
+        for (int e = tid; e < l; e += blockDim.x) {
+            q[e] = u[e];
+            Qv[(long)i * l + e] = u[e];
+        }
+        if (tid == 0) {
+            cs_[i - 1] = ci;
+            zs_[i] = zi;
+            // Givens QR of the lower-bidiagonal slice: column i has c_i on the
+            // diagonal, z_{i+1} below it.
+            const double rhobar = (i == 1) ? ci : cs_prev * ci;
+            S.theta[i - 1] = (i == 1) ? 0.0 : sn_prev * ci;   // R(i-1, i)
+            const double rho = hypot(rhobar, zi);
+            double c = 1.0, sn = 0.0;
+            if (rho > 0.0) {
+                c = rhobar / rho;
+                sn = zi / rho;
+                S.phi[i - 1] = c * phibar;
+                phibar = -sn * phibar;
+            } else {  // zero column: its right-hand side entry stays unmatched
+                S.phi[i - 1] = 0.0;
+                orphan += phibar * phibar;
+                phibar = 0.0;
+            }
+            S.rho[i - 1] = rho;
+            cs_prev = c;
+            sn_prev = sn;
+            res2[(long)i * h + s] = ws * (orphan + phibar * phibar);
+            __threadfence();
+            atomicAdd(&counters[i], 1u);
+            // wait for every slice to finish step i (bounded)
+            const long long t0 = clock64();
+            while (ld_acquire(&counters[i]) < (unsigned)h) {
+                if (clock64() - t0 > spin_cycles) {
+                    flag_timeout = 1;
+                    break;
+                }
+            }
+            __threadfence();
+            if (!flag_timeout) {
+                double tot = 0.0;
+                for (int s2 = 0; s2 < h; ++s2) tot += __ldcg(&res2[(long)i * h + s2]);
+                S.res[i] = sqrt(tot / (double)n);
+                if (S.res[i] <= tau_delta) flag_done = 1;
+            }
+        }
+        zprev = zi;
+        __syncthreads();
+        if (flag_timeout || flag_done) {
+            k = i;
+            break;
+        }
+    }
+    // back substitution R y = phi (rho on the diagonal, theta above it)
+    if (tid == 0) {
+        for (int j = k - 1; j >= 0; --j) {
+            double v = S.phi[j];
+            if (j + 1 < k) v -= S.theta[j + 1] * S.y[j + 1];
+            S.y[j] = S.rho[j] > 0.0 ? v / S.rho[j] : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < m; e += blockDim.x) {
+        double xr = 0.0, xi = 0.0;
+        for (int j = 0; j < k; ++j) {
+            const V v = W[(long)j * m + e];
+            xr += (double)v.x * S.y[j];
+            xi += (double)v.y * S.y[j];
+        }
+        Xhat[(long)s * m + e] = mk<T>((T)xr, (T)xi);
+    }
+    if (s == 0 && tid == 0) {
+        int status = flag_timeout ? TP_ERR_TIMEOUT : (flag_done ? TP_OK : TP_ERR_NOT_CONVERGED);
+        st->k = k;
+        st->status = status;
+        const double res_k = flag_timeout ? -1.0 : S.res[k];
+        double margin = fabs(res_k - tau_delta) / tau_delta;
+        if (k >= 2) margin = fmin(margin, fabs(S.res[k - 1] - tau_delta) / tau_delta);
+        if (res_hist) {
+            res_hist[0] = -1.0;
+            for (int j = 1; j <= k_max; ++j) res_hist[j] = j <= k ? S.res[j] : -1.0;
+        }
+        if (write_info) {
+            tp_info o;
+            o.status = status;
+            o.k = k;
+            o.r = k;
+            o.sweeps = 0;
+            o.residual = res_k;
+            o.tau_delta = tau_delta;
+            o.eta = 0.0;
+            o.mu = 0.0;
+            o.margin = margin;
+            o.norm_a2 = 0.0;
+            *info = o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tikhonov on the projected problem of each slice:
+//   min ||P y - z1 e1||^2 + lam^2 ||y||^2,  lam^2 = 1/mu,
+// solved by Givens QR of [P; lam I] (two rotations per column); returns the
+// data residual ||P y - z1 e1||^2 and optionally y.
+// ---------------------------------------------------------------------------
+__device__ double damped_bidiag(const double* c, const double* z, int k, double lam, double* y, double* scr,
+                               int kcap) {
+    // scr: 4 * kcap doubles of per-thread scratch (rho, theta, phi, y)
+    double* rho = scr;
+    double* theta = scr + kcap;
+    double* phi = scr + 2 * kcap;
+    double* yy = y ? y : scr + 3 * kcap;
+    double rhobar = k > 0 ? c[0] : 0.0, phibar = z[0];
+    for (int j = 0; j < k; ++j) {
+        const double rh = hypot(rhobar, lam);          // eliminate the damping row
+        const double c1 = rh > 0.0 ? rhobar / rh : 1.0;
+        const double ph = c1 * phibar;
+        const double rj = hypot(rh, z[j + 1]);         // eliminate z_{j+2}
+        double cs = 1.0, sn = 0.0;
+        if (rj > 0.0) {
+            cs = rh / rj;
+            sn = z[j + 1] / rj;
+        }
+        rho[j] = rj;
+        phi[j] = cs * ph;
+        phibar = -sn * ph;
+        if (j + 1 < k) {
+            theta[j + 1] = sn * c[j + 1];
+            rhobar = cs * c[j + 1];
+        }
+    }
+    for (int j = k - 1; j >= 0; --j) {
+        double v = phi[j];
+        if (j + 1 < k) v -= theta[j + 1] * yy[j + 1];
+        yy[j] = rho[j] > 0.0 ? v / rho[j] : 0.0;
+    }
+    // data residual: r_1 = c_1 y_1 - z_1, r_j = z_j y_{j-1} + c_j y_j, r_{k+1} = z_{k+1} y_k
+    double r2 = 0.0;
+    for (int j = 0; j <= k; ++j) {
+        double v = (j < k ? c[j] * yy[j] : 0.0) + (j > 0 ? z[j] * yy[j - 1] : 0.0);
+        if (j == 0) v -= z[0];
+        r2 += v * v;
+    }
+    return r2;
+}
+
+struct TikState {
+    double lo, hi, t;
+    int done, status, round;
+};
+
+constexpr int TIK_P = 64;
+
+// f at TIK_P points of the current bracket for every slice: out[p*h + s]
+__global__ void __launch_bounds__(TIK_P)
+k_tik_eval(const double* cc, const double* zz, int k_max, const State* st, const TikState* ts, int h, int n,
+           double* out, double* scratch) {
+    if (ts->done) return;
+    const int s = blockIdx.x, p = threadIdx.x, k = st->k;
+    double t;
+    if (p == 0) t = ts->lo;
+    else if (p == TIK_P - 1) t = ts->hi;
+    else t = ts->lo + (ts->hi - ts->lo) * (double)p / (double)(TIK_P - 1);
+    const double lam = sqrt(pow(10.0, -t));
+    double* scr = scratch + ((long)p * h + s) * 4 * k_max;
+    const double r2 = damped_bidiag(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, nullptr, scr, k_max);
+    out[(long)p * h + s] = parseval_w(s, n) * r2;
+}
+
+__global__ void __launch_bounds__(TIK_P)
+k_tik_select(const double* out, int h, int n, double tau_delta, double log_tol, TikState* ts) {
+    if (ts->done) return;
+    __shared__ double f[TIK_P];
+    const int p = threadIdx.x;
+    double a = 0.0;
+    for (int s = 0; s < h; ++s) a += out[(long)p * h + s];
+    f[p] = sqrt(a / (double)n) - tau_delta;
+    __syncthreads();
+    if (p != 0) return;
+    const double lo = ts->lo, hi = ts->hi;
+    if (ts->round == 0) {
+        if (f[TIK_P - 1] > 0.0) {  // even mu_hi leaves the residual above tau*delta
+            ts->t = hi;
+            ts->status = TP_ERR_NOT_CONVERGED;
+            ts->done = 1;
+            return;
+        }
+        if (f[0] <= 0.0) {
+            ts->t = lo;
+            ts->done = 1;
+            return;
+        }
+    }
+    int ps = TIK_P - 1;
+    for (int i = 1; i < TIK_P; ++i)
+        if (f[i] <= 0.0) {
+            ps = i;
+            break;
+        }
+    auto pt = [&](int i) {
+        return i == 0 ? lo : (i == TIK_P - 1 ? hi : lo + (hi - lo) * (double)i / (double)(TIK_P - 1));
+    };
+    ts->lo = pt(ps - 1);
+    ts->hi = pt(ps);
+    ts->round += 1;
+    if (ts->hi - ts->lo <= log_tol) {
+        ts->t = ts->hi;
+        ts->done = 1;
+    }
+}
+
+// final: y_mu per slice, Xhat = W y, residual; info
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_tik_final(const double* cc, const double* zz, int k_max, const cplx<T>* Wb, int m, const State* st,
+            const TikState* ts, int n, double* out, cplx<T>* Xhat, double* scratch) {
+    __shared__ double y[GKB_KMAX];
+    const int s = blockIdx.x, k = st->k;
+    const double mu = pow(10.0, ts->t);
+    if (threadIdx.x == 0) {
+        const double r2 = damped_bidiag(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, sqrt(1.0 / mu), y,
+                                        scratch + (long)s * 4 * k_max, k_max);
+        out[s] = parseval_w(s, n) * r2;
+    }
+    __syncthreads();
+    const cplx<T>* W = Wb + (long)s * k_max * m;
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        double xr = 0.0, xi = 0.0;
+        for (int j = 0; j < k; ++j) {
+            const cplx<T> v = W[(long)j * m + e];
+            xr += (double)v.x * y[j];
+            xi += (double)v.y * y[j];
+        }
+        Xhat[(long)s * m + e] = mk<T>((T)xr, (T)xi);
+    }
+}
+
+__global__ void k_tik_info(const double* out, int h, int n, const State* st, const TikState* ts, double tau_delta,
+                           tp_info* info) {
+    if (threadIdx.x != 0) return;
+    double a = 0.0;
+    for (int s = 0; s < h; ++s) a += out[s];
+    tp_info o;
+    o.status = st->status == TP_ERR_TIMEOUT ? TP_ERR_TIMEOUT : ts->status;
+    o.k = st->k;
+    o.r = st->k;
+    o.sweeps = ts->round;
+    o.residual = sqrt(a / (double)n);
+    o.tau_delta = tau_delta;
+    o.eta = 0.0;
+    o.mu = pow(10.0, ts->t);
+    o.margin = fabs(o.residual - tau_delta) / tau_delta;
+    o.norm_a2 = 0.0;
+    *info = o;
+}
+
+__global__ void k_tik_init(TikState* ts, double lo, double hi) {
+    ts->lo = lo;
+    ts->hi = hi;
+    ts->t = hi;
+    ts->done = 0;
+    ts->status = TP_OK;
+    ts->round = 0;
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+struct GkWs {
+    State* st;
+    TikState* ts;
+    unsigned* counters;
+    double *res2, *cc, *zz, *tout, *tscr;
+    cplx<T> *Ahat, *Bhat, *W, *Q, *Xhat;
+    size_t bytes;
+};
+
+template <typename T>
+static GkWs<T> gk_carve(void* base, int l, int m, int n, int k_max) {
+    typedef cplx<T> V;
+    const long h = n / 2 + 1;
+    Carver c(base, 0);
+    GkWs<T> w;
+    w.st = c.take<State>(1);
+    w.ts = c.take<TikState>(1);
+    w.counters = c.take<unsigned>(k_max + 1);
+    w.res2 = c.take<double>((long)(k_max + 1) * h);
+    w.cc = c.take<double>(h * k_max);
+    w.zz = c.take<double>(h * (k_max + 1));
+    w.tout = c.take<double>((long)TIK_P * h);
+    w.tscr = c.take<double>((long)TIK_P * h * 4 * k_max);
+    w.Ahat = c.take<V>(h * l * m);
+    w.Bhat = c.take<V>(h * l);
+    w.W = c.take<V>(h * (long)k_max * m);
+    w.Q = c.take<V>(h * (long)(k_max + 1) * l);
+    w.Xhat = c.take<V>(h * m);
+    w.bytes = c.off;
+    return w;
+}
+
+template <typename T>
+static tp_status gk_check(int l, int m, int n, int p, const tp_tgkb_params* P) {
+    if (!P || l < 1 || m < 1 || n < 1 || p != 1) return TP_ERR_ARG;
+    if (l > 1024 || m > 1024 || n > (sizeof(T) == 4 ? 1024 : 512)) return TP_ERR_ARG;
+    const int mn = l < m ? l : m;
+    if (P->k_max < 1 || P->k_max > mn || P->k_max > GKB_KMAX) return TP_ERR_ARG;
+    if (!(P->tau > 0.0) || !(P->delta >= 0.0)) return TP_ERR_ARG;
+    return TP_OK;
+}
+
+template <typename T>
+size_t gk_ws_bytes(int l, int m, int n, int p, const tp_tgkb_params* P) {
+    if (gk_check<T>(l, m, n, p, P) != TP_OK) return 0;
+    return gk_carve<T>(nullptr, l, m, n, P->k_max).bytes;
+}
+
+#define TRY(x)                      \
+    do {                            \
+        tp_status _e = (x);         \
+        if (_e != TP_OK) return _e; \
+    } while (0)
+
+template <typename T>
+static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tgkb_params* P, GkWs<T>& w,
+                        tp_info* info, int write_info, cudaStream_t st) {
+    const int h = n / 2 + 1, k_max = P->k_max;
+    const long lm = (long)l * m;
+    if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (k_max + 1), st) != cudaSuccess) return TP_ERR_CUDA;
+    TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, nullptr, nullptr, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, nullptr, nullptr, st));
+    const int L = l > m ? l : m;
+    const size_t smem = ((size_t)l + m + L + k_max + 1) * sizeof(cplx<T>);
+    auto kern = k_gkb<T>;
+    if (smem > 48 * 1024)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return TP_ERR_CUDA;
+    int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TP_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TP_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return TP_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GKB_THREADS, smem) != cudaSuccess)
+        return TP_ERR_CUDA;
+    if (!coop || (long)per_sm * nsm < h) return TP_ERR_UNSUPPORTED;
+    const cplx<T>* Ahat = w.Ahat;
+    const cplx<T>* Bhat = w.Bhat;
+    int l_ = l, m_ = m, n_ = n, h_ = h, k_ = k_max, wi = write_info;
+    double td = P->tau * P->delta;
+    long long spin = 4000000000LL;  // ~2 s at the GB300 SM clock
+    double* rh = P->res_hist;
+    void* args[] = {(void*)&Ahat, (void*)&Bhat, &l_, &m_, &n_, &h_, &k_, &td, (void*)&w.W, (void*)&w.Q,
+                    (void*)&w.cc, (void*)&w.zz, (void*)&w.res2, (void*)&w.counters, (void*)&w.Xhat,
+                    (void*)&w.st, (void*)&info, (void*)&rh, &spin, &wi};
+    if (cudaLaunchCooperativeKernel((const void*)kern, dim3(h), dim3(GKB_THREADS), args, smem, st) != cudaSuccess)
+        return TP_ERR_CUDA;
+    return last_launch();
+}
+
+template <typename T>
+tp_status gk_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_tgkb_params* P, T* X,
+                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+    TRY(gk_check<T>(l, m, n, p, P));
+    if (!A || !B || !X || !info) return TP_ERR_ARG;
+    GkWs<T> w = gk_carve<T>(ws, l, m, n, P->k_max);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
+    TRY(gk_run<T>(A, B, l, m, n, P, w, info, 1, st));
+    TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));
+    return TP_OK;
+}
+
+template <typename T>
+size_t tik_ws_bytes(int l, int m, int n, int p, const tp_tik_params* P) {
+    if (!P) return 0;
+    return gk_ws_bytes<T>(l, m, n, p, &P->gkb);
+}
+
+template <typename T>
+tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_tik_params* P, T* X,
+                    tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!P) return TP_ERR_ARG;
+    TRY(gk_check<T>(l, m, n, p, &P->gkb));
+    if (!(P->mu_lo > 0.0) || !(P->mu_hi > P->mu_lo)) return TP_ERR_ARG;
+    if (!A || !B || !X || !info) return TP_ERR_ARG;
+    GkWs<T> w = gk_carve<T>(ws, l, m, n, P->gkb.k_max);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
+    TRY(gk_run<T>(A, B, l, m, n, &P->gkb, w, info, 0, st));
+    const int h = n / 2 + 1, k_max = P->gkb.k_max;
+    const double lo = log10(P->mu_lo), hi = log10(P->mu_hi);
+    const double tol = P->log_tol > 0.0 ? P->log_tol : 1e-12;
+    const double td = P->gkb.tau * P->gkb.delta;
+    k_tik_init<<<1, 1, 0, st>>>(w.ts, lo, hi);
+    TRY(last_launch());
+    int rounds = 1;
+    for (double width = hi - lo; width > tol && rounds < 40; width /= (TIK_P - 1)) ++rounds;
+    for (int it = 0; it < rounds; ++it) {
+        k_tik_eval<<<h, TIK_P, 0, st>>>(w.cc, w.zz, k_max, w.st, w.ts, h, n, w.tout, w.tscr);
+        TRY(last_launch());
+        k_tik_select<<<1, TIK_P, 0, st>>>(w.tout, h, n, td, tol, w.ts);
+        TRY(last_launch());
+    }
+    k_tik_final<T><<<h, 256, 0, st>>>(w.cc, w.zz, k_max, w.W, m, w.st, w.ts, n, w.tout, w.Xhat, w.tscr);
+    TRY(last_launch());
+    k_tik_info<<<1, 32, 0, st>>>(w.tout, h, n, w.st, w.ts, td, info);
+    TRY(last_launch());
+    TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));
+    return TP_OK;
+}
+
+template size_t gk_ws_bytes<float>(int, int, int, int, const tp_tgkb_params*);
+template size_t gk_ws_bytes<double>(int, int, int, int, const tp_tgkb_params*);
+template size_t tik_ws_bytes<float>(int, int, int, int, const tp_tik_params*);
+template size_t tik_ws_bytes<double>(int, int, int, int, const tp_tik_params*);
+template tp_status gk_solve<float>(const float*, const float*, int, int, int, int, const tp_tgkb_params*, float*,
+                                   tp_info*, void*, size_t, cudaStream_t);
+template tp_status gk_solve<double>(const double*, const double*, int, int, int, int, const tp_tgkb_params*,
+                                    double*, tp_info*, void*, size_t, cudaStream_t);
+template tp_status tik_solve<float>(const float*, const float*, int, int, int, int, const tp_tik_params*, float*,
+                                    tp_info*, void*, size_t, cudaStream_t);
+template tp_status tik_solve<double>(const double*, const double*, int, int, int, int, const tp_tik_params*,
+                                     double*, tp_info*, void*, size_t, cudaStream_t);
+
+}  // namespace tp

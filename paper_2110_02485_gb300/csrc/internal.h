@@ -1,0 +1,74 @@
+// Host-side launchers shared between the translation units of libtprod.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "tprod.h"
+
+namespace tp {
+
+extern int g_launches;  // kernels enqueued by the library (reported by tp_kernel_launches)
+
+inline tp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TP_OK : TP_ERR_CUDA; }
+inline tp_status last_launch() {
+    ++g_launches;
+    return cuda_status(cudaGetLastError());
+}
+
+// Real <-> half-spectrum mode-3 DFT over a batch of tubes.  A "tube set" is
+// rows x cols tubes; tube (r, c) of slice k sits at base + k*ss + r*ld + c.
+// The spectrum is (h, rows, cols) contiguous.  sumsq (optional, device) gets
+// one float64 partial sum of squares per CTA; nparts returns their count.
+template <typename T>
+tp_status rdft(const T* X, void* Xh, int n, int rows, int cols, long ld, long ss,
+               double* sumsq, const int* skip, cudaStream_t st);
+template <typename T>
+tp_status irdft(const void* Xh, T* X, int n, int rows, int cols, long ld, long ss,
+                const int* skip, cudaStream_t st);
+int rdft_parts(int rows, int cols);
+size_t rdft_smem(int n, size_t elem);
+
+// Batched complex matrix product over slices:
+//   C[s] = alpha * op(A[s]) * op(B[s]) + beta * C[s]
+// op bits: 1 = transpose, 2 = conjugate.  Row-major operands with leading
+// dimensions and slice strides in complex elements.  dM/dN/dK (optional,
+// device) cap the effective sizes at run time.  skip (optional, device):
+// the launch does nothing when *skip != 0.
+enum { OP_N = 0, OP_T = 1, OP_R = 2, OP_C = 3 };
+template <typename T>
+tp_status cgemm(int batch, int M, int N, int K, const int* dM, const int* dN, const int* dK,
+                double alpha_re, double alpha_im, const void* A, long lda, long sA, int opA,
+                const void* B, long ldb, long sB, int opB, double beta_re, double beta_im,
+                void* C, long ldc, long sC, const int* skip, cudaStream_t st);
+
+// Device-side bookkeeping shared by a solve.
+struct State {
+    double norm_a2;   // ||A||_F^2
+    double eps2;      // eps^2 of Algorithm 3
+    double eta;       // error indicator
+    double norm_b2;   // ||B||_F^2
+    double sigma_max;
+    int done;         // sketch finished
+    int r;            // sketch rank reached
+    int k;            // truncation index
+    int status;
+    int sweeps;
+    int pad[3];
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carver {
+    char* base;
+    size_t off;
+    size_t cap;
+    explicit Carver(void* p, size_t c) : base((char*)p), off(0), cap(c) {}
+    template <typename U> U* take(size_t count) {
+        U* p = base ? (U*)(base + off) : nullptr;
+        off = align256(off + count * sizeof(U));
+        return p;
+    }
+};
+
+}  // namespace tp

@@ -1,0 +1,265 @@
+"""ctypes binding of libtprod (include/tprod.h).
+
+Argument marshalling only: every step of every call runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors (float32 or float64,
+contiguous); the current torch stream is used; workspaces come from torch's
+caching allocator.  There is no CPU path: a missing library or a non-CUDA
+tensor raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libtprod.so")
+
+TP_OK, TP_ERR_ARG, TP_ERR_CUDA, TP_ERR_WORKSPACE = 0, -1, -2, -3
+TP_ERR_BREAKDOWN, TP_ERR_NOT_CONVERGED, TP_ERR_TIMEOUT, TP_ERR_UNSUPPORTED = -4, -5, -6, -7
+TP_FP32, TP_FP64 = 0, 1
+
+
+class TpInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("k", ctypes.c_int), ("r", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("residual", ctypes.c_double), ("tau_delta", ctypes.c_double), ("eta", ctypes.c_double),
+                ("mu", ctypes.c_double), ("margin", ctypes.c_double), ("norm_a2", ctypes.c_double)]
+
+
+class RtsvdParams(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double), ("eps", ctypes.c_double),
+                ("eps_rel", ctypes.c_double), ("p_over", ctypes.c_int), ("q_power", ctypes.c_int),
+                ("block", ctypes.c_int), ("r_max", ctypes.c_int), ("res_hist", ctypes.c_void_p)]
+
+
+class TgkbParams(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double), ("k_max", ctypes.c_int),
+                ("res_hist", ctypes.c_void_p)]
+
+
+class TikParams(ctypes.Structure):
+    _fields_ = [("gkb", TgkbParams), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
+                ("log_tol", ctypes.c_double)]
+
+
+# every symbol include/tprod.h declares
+EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm", "rtsvd_workspace_bytes",
+           "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
+           "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches")
+
+_lib = None
+
+
+class TprodError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn}: {status_string(status)} ({status})")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libtprod.so (built by paper_2110_02485_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libtprod.so not built ({p}); run `python -m paper_2110_02485_gb300.build`")
+    L = ctypes.CDLL(p)
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    L.tprod_fft.argtypes = [vp, i, i, i, vp, i, vp]
+    L.tprod_ifft.argtypes = [vp, i, i, i, vp, i, vp]
+    L.tprod_gemm_workspace_bytes.argtypes = [i, i, i, i, i]
+    L.tprod_gemm_workspace_bytes.restype = sz
+    L.tprod_gemm.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, sz, vp]
+    L.rtsvd_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(RtsvdParams), i]
+    L.rtsvd_workspace_bytes.restype = sz
+    L.rtsvd_truncated_solve.argtypes = [vp, vp, vp, i, i, i, i, ctypes.POINTER(RtsvdParams), vp, vp, i, vp, sz, vp]
+    L.tgkb_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TgkbParams), i]
+    L.tgkb_workspace_bytes.restype = sz
+    L.tgkb_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TgkbParams), vp, vp, i, vp, sz, vp]
+    L.tgkb_tikhonov_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TikParams), i]
+    L.tgkb_tikhonov_workspace_bytes.restype = sz
+    L.tgkb_tikhonov_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TikParams), vp, vp, i, vp, sz, vp]
+    L.tp_status_string.argtypes = [i]
+    L.tp_status_string.restype = ctypes.c_char_p
+    L.tp_version.restype = i
+    L.tp_kernel_launches.restype = i
+    for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
+              "tgkb_tikhonov_solve"):
+        getattr(L, f).restype = i
+    _lib = L
+    return L
+
+
+def status_string(st: int) -> str:
+    return load().tp_status_string(int(st)).decode()
+
+
+def kernel_launches() -> int:
+    return int(load().tp_kernel_launches())
+
+
+def _check(fn: str, st: int):
+    if st != TP_OK:
+        raise TprodError(fn, st)
+
+
+def _prec(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return TP_FP32
+    if t.dtype == torch.float64:
+        return TP_FP64
+    raise TypeError(f"unsupported dtype {t.dtype} (float32 or float64)")
+
+
+def _dev(*ts: torch.Tensor):
+    for t in ts:
+        if not t.is_cuda:
+            raise TypeError("tprod works on CUDA tensors only (no CPU path)")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device=device)
+
+
+def _aligned(ws: torch.Tensor) -> tuple[ctypes.c_void_p, int]:
+    p = ws.data_ptr()
+    a = (p + 255) & ~255
+    return ctypes.c_void_p(a), ws.numel() - (a - p)
+
+
+def _cplx_dtype(t: torch.Tensor):
+    return torch.complex64 if t.dtype == torch.float32 else torch.complex128
+
+
+def fft(A: torch.Tensor) -> torch.Tensor:
+    """Half-spectrum mode-3 DFT: A (n, l, m) real -> (n//2+1, l, m) complex."""
+    _dev(A)
+    n, l, m = A.shape
+    out = torch.empty((n // 2 + 1, l, m), dtype=_cplx_dtype(A), device=A.device)
+    _check("tprod_fft", load().tprod_fft(_ptr(A), l, m, n, _ptr(out), _prec(A), _stream()))
+    return out
+
+
+def ifft(Xh: torch.Tensor, n: int) -> torch.Tensor:
+    """Inverse of fft: (n//2+1, l, m) complex -> (n, l, m) real."""
+    _dev(Xh)
+    h, l, m = Xh.shape
+    if h != n // 2 + 1:
+        raise ValueError("spectrum has the wrong number of slices for n")
+    real = torch.float32 if Xh.dtype == torch.complex64 else torch.float64
+    out = torch.empty((n, l, m), dtype=real, device=Xh.device)
+    prec = TP_FP32 if real == torch.float32 else TP_FP64
+    _check("tprod_ifft", load().tprod_ifft(_ptr(Xh), l, m, n, _ptr(out), prec, _stream()))
+    return out
+
+
+def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False) -> torch.Tensor:
+    """t-product op(A) * B.  A (n, l, kk) [or (n, kk, l) with transA], B (n, kk, m)."""
+    _dev(A, B)
+    if A.dtype != B.dtype:
+        raise TypeError("A and B must share a dtype")
+    n, a1, a2 = A.shape
+    nb, kk, m = B.shape
+    l = a2 if transA else a1
+    if nb != n or (a1 if transA else a2) != kk:
+        raise ValueError("shape mismatch")
+    prec = _prec(A)
+    C = torch.empty((n, l, m), dtype=A.dtype, device=A.device)
+    L = load()
+    ws = _workspace(L.tprod_gemm_workspace_bytes(l, kk, m, n, prec), A.device)
+    wp, wn = _aligned(ws)
+    _check("tprod_gemm", L.tprod_gemm(_ptr(A), _ptr(B), _ptr(C), l, kk, m, n, int(transA), prec, wp, wn, _stream()))
+    return C
+
+
+def _info_dict(buf: torch.Tensor) -> dict:
+    raw = bytes(buf.cpu().numpy().tobytes())
+    o = TpInfo.from_buffer_copy(raw[:ctypes.sizeof(TpInfo)])
+    return {f: getattr(o, f) for f, _ in TpInfo._fields_}
+
+
+def _info_buf(device):
+    return torch.zeros(ctypes.sizeof(TpInfo), dtype=torch.uint8, device=device)
+
+
+def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None, eps=0.0, eps_rel=0.0,
+                res_hist=False, sync=True):
+    """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist])."""
+    _dev(A, B, Omega)
+    n, l, m = A.shape
+    r_max = min(l, m) if r_max is None else r_max
+    prec = _prec(A)
+    X = torch.empty((n, m, 1), dtype=A.dtype, device=A.device)
+    hist = torch.empty(r_max + 1, dtype=torch.float64, device=A.device) if res_hist else None
+    P = RtsvdParams(float(delta), float(tau), float(eps), float(eps_rel), int(p_over), int(q_power), int(block),
+                    int(r_max), hist.data_ptr() if hist is not None else None)
+    L = load()
+    nb = L.rtsvd_workspace_bytes(l, m, n, 1, ctypes.byref(P), prec)
+    if nb == 0:
+        raise TprodError("rtsvd_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, A.device)
+    wp, wn = _aligned(ws)
+    info = _info_buf(A.device)
+    _check("rtsvd_truncated_solve", L.rtsvd_truncated_solve(_ptr(A), _ptr(B), _ptr(Omega), l, m, n, 1,
+                                                            ctypes.byref(P), _ptr(X), _ptr(info), prec, wp, wn,
+                                                            _stream()))
+    if not sync:
+        return X, info, hist
+    out = (X, _info_dict(info))
+    return out + ((hist.cpu().numpy(),) if res_hist else ())
+
+
+def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True):
+    """tGKB method (Algorithm 4 + Eq. (solgkb)).  Returns (X, info[, res_hist])."""
+    _dev(A, B)
+    n, l, m = A.shape
+    prec = _prec(A)
+    X = torch.empty((n, m, 1), dtype=A.dtype, device=A.device)
+    hist = torch.empty(k_max + 1, dtype=torch.float64, device=A.device) if res_hist else None
+    P = TgkbParams(float(delta), float(tau), int(k_max), hist.data_ptr() if hist is not None else None)
+    L = load()
+    nb = L.tgkb_workspace_bytes(l, m, n, 1, ctypes.byref(P), prec)
+    if nb == 0:
+        raise TprodError("tgkb_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, A.device)
+    wp, wn = _aligned(ws)
+    info = _info_buf(A.device)
+    _check("tgkb_solve", L.tgkb_solve(_ptr(A), _ptr(B), l, m, n, 1, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp,
+                                      wn, _stream()))
+    if not sync:
+        return X, info, hist
+    out = (X, _info_dict(info))
+    return out + ((hist.cpu().numpy(),) if res_hist else ())
+
+
+def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True):
+    """Tikhonov-tGKB (Section 5).  Returns (X, info)."""
+    _dev(A, B)
+    n, l, m = A.shape
+    prec = _prec(A)
+    X = torch.empty((n, m, 1), dtype=A.dtype, device=A.device)
+    P = TikParams(TgkbParams(float(delta), float(tau), int(k_max), None), float(mu_lo), float(mu_hi),
+                  float(log_tol))
+    L = load()
+    nb = L.tgkb_tikhonov_workspace_bytes(l, m, n, 1, ctypes.byref(P), prec)
+    if nb == 0:
+        raise TprodError("tgkb_tikhonov_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, A.device)
+    wp, wn = _aligned(ws)
+    info = _info_buf(A.device)
+    _check("tgkb_tikhonov_solve", L.tgkb_tikhonov_solve(_ptr(A), _ptr(B), l, m, n, 1, ctypes.byref(P), _ptr(X),
+                                                        _ptr(info), prec, wp, wn, _stream()))
+    if not sync:
+        return X, info
+    return X, _info_dict(info)

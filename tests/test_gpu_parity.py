@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every case feeds both sides the same seeded inputs.  The GPU runs in FP64
+(to show it computes the same algorithm: agreement to ~1e-10) and in FP32
+(the product precision: tolerances derived in the design notes).  Truncation
+indices are integers decided by a floating-point threshold; they must match
+exactly unless the oracle's margin puts the decision inside the rounding
+band of the GPU precision.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2110_02485_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# relative Frobenius tolerances on X against the FP64 oracle
+TOL_X = {torch.float64: 1e-9, torch.float32: 2e-4}
+# decisions closer than this (relative) to tau*delta may legitimately differ
+TIE = {torch.float64: 1e-9, torch.float32: 1e-4}
+
+
+@pytest.fixture(scope="session")
+def tp():
+    from paper_2110_02485_gb300 import build, tprod
+    build.build()
+    tprod.load()
+    assert torch.cuda.is_available()
+    return tprod
+
+
+def dev(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def rnd(shape, seed):
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+# ----------------------------------------------------------------- DFT ----
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,l,m", [(1, 3, 5), (2, 4, 4), (3, 7, 2), (5, 6, 9), (8, 33, 3), (17, 5, 13),
+                                   (32, 16, 40), (96, 9, 7), (256, 3, 70), (512, 2, 33)])
+def test_fft_matches_oracle(tp, dtype, n, l, m):
+    A = rnd((n, l, m), n * 7 + l)
+    A_dev = dev(A, dtype)
+    Ah = tp.fft(A_dev).cpu().numpy()
+    ref = O.fft3(A_dev.cpu().double().numpy())[: n // 2 + 1]
+    scale = np.abs(ref).max()
+    tol = 1e-13 if dtype == torch.float64 else 2e-6 * (1 + np.log2(n))
+    assert Ah.shape == ref.shape
+    assert np.abs(Ah - ref).max() <= tol * scale
+    X = tp.ifft(tp.fft(A_dev), n).cpu().numpy()
+    assert np.abs(X - A_dev.cpu().numpy()).max() <= tol * np.abs(A).max()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_ifft_of_a_spectrum_ignores_imaginary_dc_and_nyquist(tp, dtype):
+    n, l, m = 8, 3, 4
+    g = np.random.default_rng(1)
+    Xh = g.standard_normal((n // 2 + 1, l, m)) + 1j * g.standard_normal((n // 2 + 1, l, m))
+    cd = torch.complex64 if dtype == torch.float32 else torch.complex128
+    X = tp.ifft(torch.from_numpy(Xh).to("cuda", cd), n).cpu().numpy()
+    full = np.concatenate([Xh, np.conj(Xh[1:n // 2][::-1])], axis=0)
+    full[0] = full[0].real
+    full[n // 2] = full[n // 2].real
+    ref = O.ifft3_real(full)
+    tol = 1e-13 if dtype == torch.float64 else 2e-6
+    assert np.abs(X - ref).max() <= tol * np.abs(ref).max()
+
+
+# ----------------------------------------------------------- t-product ----
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,l,kk,m,trans", [(1, 3, 4, 2, 0), (6, 5, 3, 7, 0), (7, 4, 6, 3, 1), (16, 70, 33, 20, 0),
+                                            (9, 130, 17, 3, 1), (32, 64, 64, 64, 0)])
+def test_tprod_matches_oracle(tp, dtype, n, l, kk, m, trans):
+    A = rnd((n, kk, l) if trans else (n, l, kk), 3 + n)
+    B = rnd((n, kk, m), 4 + n)
+    C = tp.tprod(dev(A, dtype), dev(B, dtype), transA=bool(trans)).cpu().numpy()
+    Ad = dev(A, dtype).cpu().double().numpy()
+    Bd = dev(B, dtype).cpu().double().numpy()
+    ref = O.tprod(O.ttranspose(Ad) if trans else Ad, Bd)
+    tol = 1e-12 if dtype == torch.float64 else 5e-6 * np.sqrt(kk)
+    assert rel(C, ref) <= tol
+
+
+# --------------------------------------------------------------- solvers ----
+
+def problem(N, n=None, seed=5, noise=1e-2, general=0.02, l=None):
+    n = N if n is None else n
+    l = N if l is None else l
+    T, c = synth.blur_factors(N, 1.3, 3, 1.5, n=n)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    g = np.random.default_rng(seed)
+    P = g.standard_normal(A.shape)
+    A = A + general * P / np.linalg.norm(P) * np.linalg.norm(A)
+    if l > N:  # tall slices: extra rows
+        A = np.concatenate([A, 0.3 * g.standard_normal((n, l - N, N))], axis=1)
+    img = synth.synthetic_image(N, n, 3, 1, g)
+    Bt = O.tprod_bcirc(A, synth.lateral(img)) if N <= 24 else None
+    if Bt is None:
+        Bt = O.tprod(A, synth.lateral(img))
+    E = g.standard_normal(Bt.shape)
+    E = noise * E / np.linalg.norm(E) * np.linalg.norm(Bt)
+    return A.astype(np.float32), (Bt + E).astype(np.float32), float(np.linalg.norm(E))
+
+
+def exact_k_required(out, dtype):
+    return out["margin"] > TIE[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,block,q,p_over,eps_rel", [(12, 8, 1, 0, 3, 0.02), (16, 16, 4, 1, 3, 0.01),
+                                                        (20, 17, 3, 2, 4, 0.01), (24, 12, 5, 1, 2, 0.005)])
+def test_rtsvd_matches_oracle(tp, dtype, N, n, block, q, p_over, eps_rel):
+    A, B, delta = problem(N, n)
+    Om = rnd((n, N, N), 11).astype(np.float32)
+    tau = 1.1
+    ref = O.rtsvd_solve(A.astype(np.float64), B.astype(np.float64), Om.astype(np.float64), delta, tau,
+                        eps_rel * np.sqrt(O.fro2(A.astype(np.float64))), p_over, block, q, r_max=N)
+    X, info, hist = tp.rtsvd_solve(dev(A, dtype), dev(B, dtype), dev(Om, dtype), delta, tau, p_over, block, q,
+                                   r_max=N, eps_rel=eps_rel, res_hist=True)
+    X = X.cpu().numpy()
+    assert info["r"] == ref["r"]
+    if exact_k_required(ref, dtype):
+        assert info["k"] == ref["k"]
+        assert info["status"] == ref["status"]
+        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+    for k, rk in ref["res"].items():
+        assert abs(hist[k] - rk) <= (1e-9 if dtype == torch.float64 else 1e-4) * rk
+    assert np.isclose(info["norm_a2"], O.fro2(A.astype(np.float64)), rtol=1e-6 if dtype == torch.float32 else 1e-12)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,k_max,l", [(12, 8, 12, None), (16, 17, 16, None), (20, 16, 10, 28), (32, 32, 32, None)])
+def test_tgkb_matches_oracle(tp, dtype, N, n, k_max, l):
+    A, B, delta = problem(N, n, l=l)
+    tau = 1.1
+    ref = O.tgkb_solve(A.astype(np.float64), B.astype(np.float64), delta, tau, k_max)
+    X, info, hist = tp.tgkb_solve(dev(A, dtype), dev(B, dtype), delta, tau, k_max, res_hist=True)
+    X = X.cpu().numpy()
+    if exact_k_required(ref, dtype):
+        assert info["k"] == ref["k"]
+        assert info["status"] == ref["status"]
+        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+    for i, ri in ref["res"].items():
+        if i <= info["k"]:
+            assert abs(hist[i] - ri) <= (1e-9 if dtype == torch.float64 else 1e-4) * ri
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,k_max,lo,hi", [(12, 8, 12, 1e-3, 1e9), (16, 17, 16, 1e-2, 1e8), (32, 32, 32, 1e-1, 1e9)])
+def test_tgkt_matches_oracle(tp, dtype, N, n, k_max, lo, hi):
+    A, B, delta = problem(N, n)
+    tau = 1.1
+    ref = O.tgkt_solve(A.astype(np.float64), B.astype(np.float64), delta, tau, k_max, lo, hi)
+    X, info = tp.tgkt_solve(dev(A, dtype), dev(B, dtype), delta, tau, k_max, lo, hi)
+    X = X.cpu().numpy()
+    g = ref["gkb"]
+    if exact_k_required(g, dtype):
+        assert info["k"] == ref["k"]
+        assert info["status"] == ref["status"]
+        assert abs(np.log10(info["mu"]) - np.log10(ref["mu"])) <= (1e-9 if dtype == torch.float64 else 1e-3)
+        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+        assert abs(info["residual"] - ref["residual"]) <= (1e-9 if dtype == torch.float64 else 1e-4) * ref["residual"]
+
+
+# ------------------------------------------------------------ edge cases ----
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_tgkb_cap_reports_not_converged(tp, dtype):
+    A, B, delta = problem(16, 8)
+    X, info = tp.tgkb_solve(dev(A, dtype), dev(B, dtype), delta * 1e-6, 1.1, 3)
+    ref = O.tgkb_solve(A.astype(np.float64), B.astype(np.float64), delta * 1e-6, 1.1, 3)
+    assert info["status"] == O.STATUS_NOT_CONVERGED == ref["status"]
+    assert info["k"] == 3 == ref["k"]
+    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype] * 10
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_rtsvd_rmax_cap_reports_not_converged(tp, dtype):
+    A, B, delta = problem(16, 8)
+    Om = rnd((8, 16, 6), 3).astype(np.float32)
+    X, info = tp.rtsvd_solve(dev(A, dtype), dev(B, dtype), dev(Om, dtype), delta, 1.1, 2, 2, 1, r_max=6,
+                             eps_rel=1e-6)
+    ref = O.rtsvd_solve(A.astype(np.float64), B.astype(np.float64), Om.astype(np.float64), delta, 1.1,
+                        1e-6 * np.sqrt(O.fro2(A.astype(np.float64))), 2, 2, 1, r_max=6)
+    assert info["r"] == 6 == ref["r"]
+    assert info["status"] == O.STATUS_NOT_CONVERGED == ref["status"]
+    assert info["k"] == ref["k"]
+    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype] * 10
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_zero_fourier_slices_break_down_cleanly(tp, dtype):
+    """Constant tubes make every Fourier slice but the first exactly zero:
+    Normalize breaks down there (zero coefficient) and the solvers must still
+    agree with the oracle."""
+    n, N = 6, 10
+    A = np.tile(rnd((1, N, N), 21) + 3 * np.eye(N), (n, 1, 1))
+    B = np.tile(rnd((1, N, 1), 22), (n, 1, 1))
+    ref = O.tgkb_solve(A, B, 1e-3, 1.1, N)
+    X, info = tp.tgkb_solve(dev(A, dtype), dev(B, dtype), 1e-3, 1.1, N)
+    assert info["k"] == ref["k"]
+    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype] * 10
+    Om = rnd((n, N, N), 23)
+    refr = O.rtsvd_solve(A, B, Om, 1e-3, 1.1, 1e-3 * np.sqrt(O.fro2(A)), 2, 2, 1, r_max=N)
+    Xr, infor = tp.rtsvd_solve(dev(A, dtype), dev(B, dtype), dev(Om, dtype), 1e-3, 1.1, 2, 2, 1, r_max=N,
+                               eps_rel=1e-3)
+    assert infor["r"] == refr["r"] and infor["k"] == refr["k"]
+    assert rel(Xr.cpu().numpy(), refr["X"]) <= TOL_X[dtype] * 10
+
+
+def test_invalid_arguments_raise(tp):
+    A = torch.zeros((4, 5, 5), device="cuda")
+    B = torch.zeros((4, 5, 1), device="cuda")
+    with pytest.raises(tp.TprodError):
+        tp.tgkb_solve(A, B, 1.0, 1.1, 0)
+    with pytest.raises(tp.TprodError):
+        tp.rtsvd_solve(A, B, torch.zeros((4, 5, 5), device="cuda"), 1.0, 1.1, 2, block=64, r_max=5, eps_rel=0.1)
