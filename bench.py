@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Throughput of the t-product regularization hot path on GB300.
+
+One step solves one synthetic 256^3 image-deblurring problem (the blur and
+image recipe of the paper's Section 5, scaled as documented in the design
+notes) with all three methods of the hot path: RT-tSVD (Algorithm 3 + the
+discrepancy principle), tGKB (Algorithm 4) and Tikhonov-tGKB.  Each solve
+starts from the raw spatial tensors A, B (and the Gaussian slices Omega) and
+includes every mode-3 DFT.  `value` = solves per second over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own independent problem (different seed;
+weak scaling, no data-path collective).  The reference arm times the FP64
+numpy oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RT-tSVD / tGKB solves/s at N=256,512 on 1 GB300; % roofline; BF16 vs FP32 at rel-err"
+UNIT = "solves/s"
+SOLVES_PER_STEP = 3
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 SIMT peak derived from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="n256")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for nm, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gkb_bytes(h, l, m, k, esize):
+    """Algorithmic DRAM-level bytes of the persistent tGKB kernel for k steps:
+    per step two passes over A-hat, two CGS passes (coefficients + update)
+    over the W and Q bases, and the two new basis vectors written."""
+    c = 2 * esize
+    tot = 0
+    for i in range(1, k + 1):
+        tot += 2 * c * h * l * m + 4 * c * h * ((i - 1) * m + i * l) + c * h * (l + m)
+    return tot
+
+
+def class_work(cfg, infos, esize=4):
+    """Algorithmic work per step by kernel class: (amount, unit, bound)."""
+    N = cfg.N
+    h, l, m, n = N // 2 + 1, N, N, N
+    c = 2 * esize
+    rt, gk, tk = infos
+    r, k_rt, b, q = rt["r"], rt["k"], cfg.block, cfg.q_power
+    nblk = -(-r // b)
+    gemm = nblk * (2 * q + 2) * 8.0 * h * l * m * b            # sketch, power iterations, projection
+    gemm += 8.0 * h * r * l + 8.0 * h * m * r * r + 8.0 * h * r * l * m + 8.0 * h * m * k_rt
+    dft_bytes = 3 * (esize * n * l * m + c * h * l * m)        # A transformed by each of the three solves
+    gkbb = gkb_bytes(h, l, m, gk["k"], esize) + gkb_bytes(h, l, m, tk["k"], esize)
+    orth = 0.0
+    for blk in range(nblk):
+        rp = blk * b
+        per = 32.0 * l * rp * b + 16.0 * l * b * b             # two CGS passes vs basis + in-block CGS2
+        orth += h * per * (q + 1) + h * (16.0 * l * b * b) * q + h * (32.0 * m * rp * b + 16.0 * m * b * b)
+    svd = h * rt.get("sweeps", 8) * (r * (r - 1) / 2) * 7 * r * 8.0
+    return {"gemm": (gemm / 1e12, "TFLOP", "alu"), "dft": (dft_bytes / 1e9, "GB", "hbm"),
+            "gkb": (gkbb / 1e9, "GB", "hbm"), "orth": (orth / 1e12, "TFLOP", "alu"),
+            "svd": (svd / 1e12, "TFLOP", "alu")}
+
+
+def run_ours(a, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2110_02485_gb300 import build, synth, tprod
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    tprod.load()
+    cfg = synth.CONFIGS[a.config]
+    P = synth.blur_problem(cfg, seed=cfg.seed + rank)
+    dev = lambda x: torch.from_numpy(x).cuda()
+    A, B, Om = dev(P["A"]), dev(P["B"]), dev(P["Omega"])
+    delta = P["delta"]
+
+    def step(A, B, Om):
+        X1, i1, _ = tprod.rtsvd_solve(A, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                                      eps_rel=cfg.eps_rel, sync=False)
+        X2, i2, _ = tprod.tgkb_solve(A, B, delta, cfg.tau, cfg.k_max, sync=False)
+        X3, i3 = tprod.tgkt_solve(A, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False)
+        return (X1, X2, X3), (i1, i2, i3)
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    for _ in range(a.warmup):
+        step(A, B, Om)
+    torch.cuda.synchronize()
+    # one instrumented step: device time per kernel class, and the solve records
+    tprod.timing_enable(tprod.KERNEL_CLASSES)
+    _, infos_dev = step(A, B, Om)
+    per_class = tprod.timing_read()
+    tprod.timing_enable([])
+    infos = [tprod._info_dict(x) for x in infos_dev]
+    dominant = max(per_class, key=lambda k: per_class[k][0])
+
+    # timed region: K steps, L2 flushed between steps, device time by CUDA events
+    launches0 = tprod.kernel_launches()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    tprod.timing_enable([dominant])
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    t_wall = time.perf_counter()
+    for _ in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(A, B, Om)
+        e1.record()
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    dom_ms, dom_launches = tprod.timing_read()[dominant]
+    tprod.timing_enable([])
+    clk = clocks.stop()
+    launches = tprod.kernel_launches() - launches0
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * SOLVES_PER_STEP * a.steps / (ms / 1e3)
+
+    # end to end through the public API: pinned host inputs in, solutions out
+    e2e = None
+    if not a.no_e2e:
+        Ah, Bh, Oh = (torch.from_numpy(P[k]).pin_memory() for k in ("A", "B", "Omega"))
+        Ad, Bd, Od = torch.empty_like(A), torch.empty_like(B), torch.empty_like(Om)
+        outs = [torch.empty((cfg.N, cfg.N, 1), dtype=torch.float32).pin_memory() for _ in range(3)]
+        h2d = sum(x.numel() * x.element_size() for x in (Ah, Bh, Oh))
+        d2h = sum(x.numel() * x.element_size() for x in outs)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs2 = []
+        for _ in range(a.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            Ad.copy_(Ah, non_blocking=True)
+            Bd.copy_(Bh, non_blocking=True)
+            Od.copy_(Oh, non_blocking=True)
+            Xs, _ = step(Ad, Bd, Od)
+            for o, x in zip(outs, Xs):
+                o.copy_(x, non_blocking=True)
+            e1.record()
+            evs2.append((e0, e1))
+        torch.cuda.synchronize()
+        ms2 = sum(e0.elapsed_time(e1) for e0, e1 in evs2)
+        if world > 1:
+            t = torch.tensor([ms2], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms2 = float(t.item())
+        e2e = {"value": world * SOLVES_PER_STEP * a.steps / (ms2 / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    hbm, bf16, src = peaks()
+    work = class_work(cfg, infos)
+    roof = None
+    if dominant in work and dom_launches:
+        amount, unit, bound = work[dominant]
+        secs = dom_ms / 1e3 / a.steps  # device seconds of this class per step
+        if bound == "hbm":
+            ach = amount / secs
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "kernel_class": dominant, "peak_source": src,
+                    "avg_launch_ms": dom_ms / dom_launches}
+        else:
+            ach = amount / secs
+            roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_SIMT_TFLOPS, "traffic": None, "kernel_class": dominant,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                    "avg_launch_ms": dom_ms / dom_launches}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{cfg.name}: {cfg.N}x{cfg.N}x{cfg.N} blur, 1 RHS, noise {cfg.noise:g}; "
+                                  "one RT-tSVD + one tGKB + one Tikhonov-tGKB solve per step",
+                      "N": cfg.N, "solves_per_step": SOLVES_PER_STEP, "l2": "flushed between steps (512 MB write)",
+                      "parallelism": f"replicas x{world}"},
+           "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+           "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
+           "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
+                          "tgkb": {k: infos[1][k] for k in ("k", "status")},
+                          "tgkt": {k: infos[2][k] for k in ("k", "status", "mu")}},
+           "wall_s_timed": t_wall}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, P)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_solve(method, cfg, P):
+    import oracle as O
+    A, B = P["A"].astype(np.float64), P["B"].astype(np.float64)
+    if method == "rtsvd":
+        Om = P["Omega"].astype(np.float64)
+        return O.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.eps_rel * np.sqrt(O.fro2(A)), cfg.p_over,
+                             cfg.block, cfg.q_power, cfg.r_max)
+    if method == "tgkb":
+        return O.tgkb_solve(A, B, P["delta"], cfg.tau, cfg.k_max)
+    return O.tgkt_solve(A, B, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)
+
+
+def cpu_threads():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return os.cpu_count()
+
+
+def cpu_baseline(cfg, P):
+    """The FP64 oracle as it stands, on a bounded sample: one RT-tSVD and one
+    tGKB solve of the same problem."""
+    t = time.perf_counter()
+    oracle_solve("rtsvd", cfg, P)
+    oracle_solve("tgkb", cfg, P)
+    dt = time.perf_counter() - t
+    return {"value": 2 / dt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"one RT-tSVD + one tGKB solve of the {cfg.name} problem (FP64 numpy, {dt:.1f} s)"}
+
+
+def run_reference(a, rank, world):
+    """FP64 oracle on the host cores; each step is one full solve, cycling
+    through the three methods."""
+    if rank != 0:
+        return
+    from paper_2110_02485_gb300 import synth
+    cfg = synth.CONFIGS[a.config]
+    P = synth.blur_problem(cfg, seed=cfg.seed)
+    small = synth.blur_problem("n32")
+    for i in range(a.warmup):  # warm the interpreter and BLAS on the small case
+        oracle_solve(("rtsvd", "tgkb", "tgkt")[i % 3], small["cfg"], small)
+    methods = ("rtsvd", "tgkb", "tgkt")
+    t = time.perf_counter()
+    for i in range(a.steps):
+        oracle_solve(methods[i % 3], cfg, P)
+    dt = time.perf_counter() - t
+    v = a.steps / dt
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{cfg.name}: one oracle solve per step, methods cycled", "N": cfg.N},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                            "sample": f"{a.steps} full solves of the {cfg.name} problem"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = args_()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

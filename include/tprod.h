@@ -180,6 +180,28 @@ const char* tp_status_string(int status);
 int tp_version(void);                 /* 100 * major + minor                        */
 int tp_kernel_launches(void);         /* kernels enqueued by this library so far    */
 
+/* Optional device timing per kernel class, for benchmarks (off by default).
+ * tp_timing_enable(mask): bit c of mask enables class c; every later launch
+ * of an enabled class is bracketed by CUDA events on its stream (a few
+ * microseconds of host time per launch).  mask = 0 disables.
+ * tp_timing_read(ms, launches, nclasses): waits for the recorded events,
+ * writes per class the summed device time (ms) and launch count, clears the
+ * record, and returns the number of classes (TP_KC_COUNT) or a negative
+ * tp_status.  Not for use while a stream is being captured. */
+enum {
+    TP_KC_DFT = 0,      /* mode-3 DFT / inverse DFT                               */
+    TP_KC_GEMM = 1,     /* batched complex products over Fourier slices           */
+    TP_KC_ORTH = 2,     /* block orthonormalisation (Algorithm 3 steps 5-9)       */
+    TP_KC_SVD = 3,      /* one-sided Jacobi SVD of the projected factor           */
+    TP_KC_GKB = 4,      /* persistent tGKB iteration (Algorithm 4)                */
+    TP_KC_DP = 5,       /* discrepancy-principle scans and reductions             */
+    TP_KC_TIK = 6,      /* Tikhonov parameter search and solution                 */
+    TP_KC_MISC = 7,     /* small bookkeeping kernels                              */
+    TP_KC_COUNT = 8
+};
+int tp_timing_enable(int class_mask);
+int tp_timing_read(double* ms, int* launches, int nclasses);
+
 #ifdef __cplusplus
 }
 #endif

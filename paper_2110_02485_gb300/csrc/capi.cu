@@ -2,9 +2,55 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <vector>
+
 namespace tp {
 
 int g_launches = 0;
+
+// ---- optional per-class device timing -------------------------------------
+namespace {
+struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+};
+int g_mask = 0;
+std::vector<cudaEvent_t> g_pool;   // free events
+std::vector<Rec> g_recs;           // recorded launches
+int g_open_cls = -1;
+cudaEvent_t g_open = nullptr;
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+void prof_begin(int cls, cudaStream_t st) {
+    if (!(g_mask >> cls & 1)) return;
+    g_open = take_event();
+    g_open_cls = g_open ? cls : -1;
+    if (g_open) cudaEventRecord(g_open, st);
+}
+
+void prof_end(int cls, cudaStream_t st) {
+    if (g_open_cls != cls || !g_open) return;
+    cudaEvent_t e = take_event();
+    if (e) {
+        cudaEventRecord(e, st);
+        g_recs.push_back({cls, g_open, e});
+    } else {
+        g_pool.push_back(g_open);
+    }
+    g_open = nullptr;
+    g_open_cls = -1;
+}
 
 template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_params*);
 template <typename T>
@@ -168,5 +214,32 @@ const char* tp_status_string(int status) {
 int tp_version(void) { return 100; }
 
 int tp_kernel_launches(void) { return g_launches; }
+
+int tp_timing_enable(int class_mask) {
+    g_mask = class_mask & ((1 << TP_KC_COUNT) - 1);
+    return TP_OK;
+}
+
+int tp_timing_read(double* ms, int* launches, int nclasses) {
+    if (!ms || !launches || nclasses < 1) return TP_ERR_ARG;
+    for (int c = 0; c < nclasses; ++c) {
+        ms[c] = 0.0;
+        launches[c] = 0;
+    }
+    int rc = TP_KC_COUNT;
+    for (const Rec& r : g_recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            rc = TP_ERR_CUDA;
+        if (r.cls < nclasses) {
+            ms[r.cls] += t;
+            launches[r.cls] += 1;
+        }
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    return rc;
+}
 
 }  // extern "C"

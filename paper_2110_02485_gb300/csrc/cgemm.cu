@@ -158,9 +158,10 @@ static tp_status launch(int batch, int M, int N, int K, const int* dM, const int
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return TP_ERR_CUDA;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+    prof_begin(TP_KC_GEMM, st);
     kern<<<grid, NT, smem, st>>>(M, N, K, dM, dN, dK, alpha, (const cplx<T>*)A, lda, sA, opA,
                                  (const cplx<T>*)B, ldb, sB, opB, beta, (cplx<T>*)C, ldc, sC, skip);
-    return last_launch();
+    return launched(TP_KC_GEMM, st);
 }
 
 template <typename T>

@@ -242,13 +242,15 @@ tp_status rdft(const T* X, void* Xh, int n, int rows, int cols, long ld, long ss
     const size_t smem = rdft_smem(n, sizeof(T));
     if (is_pow2(n)) {
         if (prep(k_rdft_pow2<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        prof_begin(TP_KC_DFT, st);
         k_rdft_pow2<T><<<grid, DFT_THREADS, smem, st>>>(X, (cplx<T>*)Xh, n, ilog2(n), tubes, cols, ld, ss,
                                                          sumsq, skip);
     } else {
         if (prep(k_rdft_direct<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        prof_begin(TP_KC_DFT, st);
         k_rdft_direct<T><<<grid, DFT_THREADS, smem, st>>>(X, (cplx<T>*)Xh, n, tubes, cols, ld, ss, sumsq, skip);
     }
-    return last_launch();
+    return launched(TP_KC_DFT, st);
 }
 
 template <typename T>
@@ -260,13 +262,15 @@ tp_status irdft(const void* Xh, T* X, int n, int rows, int cols, long ld, long s
     const size_t smem = rdft_smem(n, sizeof(T));
     if (is_pow2(n)) {
         if (prep(k_irdft_pow2<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        prof_begin(TP_KC_DFT, st);
         k_irdft_pow2<T><<<grid, DFT_THREADS, smem, st>>>((const cplx<T>*)Xh, X, n, ilog2(n), tubes, cols, ld,
                                                           ss, skip);
     } else {
         if (prep(k_irdft_direct<T>, smem) != TP_OK) return TP_ERR_CUDA;
+        prof_begin(TP_KC_DFT, st);
         k_irdft_direct<T><<<grid, DFT_THREADS, smem, st>>>((const cplx<T>*)Xh, X, n, tubes, cols, ld, ss, skip);
     }
-    return last_launch();
+    return launched(TP_KC_DFT, st);
 }
 
 template tp_status rdft<float>(const float*, void*, int, int, int, long, long, double*, const int*, cudaStream_t);

@@ -553,9 +553,10 @@ static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tg
     void* args[] = {(void*)&Ahat, (void*)&Bhat, &l_, &m_, &n_, &h_, &k_, &td, (void*)&w.W, (void*)&w.Q,
                     (void*)&w.cc, (void*)&w.zz, (void*)&w.res2, (void*)&w.counters, (void*)&w.Xhat,
                     (void*)&w.st, (void*)&info, (void*)&rh, &spin, &wi};
+    prof_begin(TP_KC_GKB, st);
     if (cudaLaunchCooperativeKernel((const void*)kern, dim3(h), dim3(GKB_THREADS), args, smem, st) != cudaSuccess)
         return TP_ERR_CUDA;
-    return last_launch();
+    return launched(TP_KC_GKB, st);
 }
 
 template <typename T>
@@ -590,20 +591,25 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     const double lo = log10(P->mu_lo), hi = log10(P->mu_hi);
     const double tol = P->log_tol > 0.0 ? P->log_tol : 1e-12;
     const double td = P->gkb.tau * P->gkb.delta;
+    prof_begin(TP_KC_TIK, st);
     k_tik_init<<<1, 1, 0, st>>>(w.ts, lo, hi);
-    TRY(last_launch());
+    TRY(launched(TP_KC_TIK, st));
     int rounds = 1;
     for (double width = hi - lo; width > tol && rounds < 40; width /= (TIK_P - 1)) ++rounds;
     for (int it = 0; it < rounds; ++it) {
+        prof_begin(TP_KC_TIK, st);
         k_tik_eval<<<h, TIK_P, 0, st>>>(w.cc, w.zz, k_max, w.st, w.ts, h, n, w.tout, w.tscr);
-        TRY(last_launch());
+        TRY(launched(TP_KC_TIK, st));
+        prof_begin(TP_KC_TIK, st);
         k_tik_select<<<1, TIK_P, 0, st>>>(w.tout, h, n, td, tol, w.ts);
-        TRY(last_launch());
+        TRY(launched(TP_KC_TIK, st));
     }
+    prof_begin(TP_KC_TIK, st);
     k_tik_final<T><<<h, 256, 0, st>>>(w.cc, w.zz, k_max, w.W, m, w.st, w.ts, n, w.tout, w.Xhat, w.tscr);
-    TRY(last_launch());
+    TRY(launched(TP_KC_TIK, st));
+    prof_begin(TP_KC_TIK, st);
     k_tik_info<<<1, 32, 0, st>>>(w.tout, h, n, w.st, w.ts, td, info);
-    TRY(last_launch());
+    TRY(launched(TP_KC_TIK, st));
     TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));
     return TP_OK;
 }

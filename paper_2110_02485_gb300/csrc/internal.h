@@ -11,8 +11,15 @@ namespace tp {
 extern int g_launches;  // kernels enqueued by the library (reported by tp_kernel_launches)
 
 inline tp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TP_OK : TP_ERR_CUDA; }
-inline tp_status last_launch() {
+
+// Optional per-kernel-class device timing (tp_timing_enable / tp_timing_read):
+// prof_begin records a start event before a launch of an enabled class and
+// launched() records the matching end event.
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+inline tp_status launched(int cls, cudaStream_t st) {
     ++g_launches;
+    prof_end(cls, st);
     return cuda_status(cudaGetLastError());
 }
 

@@ -172,8 +172,9 @@ static tp_status orth(int h, cplx<T>* Y, long sY, int L, int b, const cplx<T>* Q
     if (smem > 48 * 1024)
         if (cudaFuncSetAttribute(k_orth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return TP_ERR_CUDA;
+    prof_begin(TP_KC_ORTH, st);
     k_orth<T><<<h, ORTH_THREADS, smem, st>>>(Y, sY, L, b, Qb, sQ, r_prev, Qout, R, ldr, sR, r_rows, normsq, skip);
-    return last_launch();
+    return launched(TP_KC_ORTH, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -546,8 +547,9 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
 
     TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, w.partsA, nullptr, st));
     TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, w.partsB, nullptr, st));
+    prof_begin(TP_KC_MISC, st);
     k_rt_init<<<1, 256, 0, st>>>(w.st, w.partsA, rdft_parts(l, m), w.partsB, rdft_parts(l, 1), P->eps, P->eps_rel, n);
-    TRY(last_launch());
+    TRY(launched(TP_KC_MISC, st));
 
     const int nblk = (r_max + b - 1) / b;
     for (int blk = 0; blk < nblk; ++blk) {
@@ -574,8 +576,9 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
                      (long)m * bb, done, st));
         TRY(orth<T>(h, w.BHb, (long)m * bb, m, bb, w.QG, (long)r_max * m, r0, w.QG, w.R, r_max,
                     (long)r_max * r_max, r_max, w.normsq, done, st));
+        prof_begin(TP_KC_MISC, st);
         k_eta_update<<<1, 256, 0, st>>>(w.st, w.normsq, h, n, r0 + bb);
-        TRY(last_launch());
+        TRY(launched(TP_KC_MISC, st));
     }
     const int* dr = &w.st->r;
     // d = Q^H b
@@ -587,13 +590,15 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
             if (cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess)
                 return TP_ERR_CUDA;
+        prof_begin(TP_KC_SVD, st);
         k_jacobi<T><<<h, JAC_THREADS, smem, st>>>(w.R, r_max, (long)r_max * r_max, w.st, w.d, r_max, w.sigma, r_max,
                                                     w.UR, r_max, (long)r_max * r_max, w.dprime, r_max, 60,
                                                     &w.st->sweeps);
-        TRY(last_launch());
+        TRY(launched(TP_KC_SVD, st));
     }
+    prof_begin(TP_KC_MISC, st);
     k_alpha<T><<<h, 256, 0, st>>>(w.sigma, r_max, w.dprime, r_max, w.alpha, r_max, w.st, h, l > m ? l : m, r_max);
-    TRY(last_launch());
+    TRY(launched(TP_KC_MISC, st));
     // V = QG^T-as-matrix * U_R ;  K^T = V^T A^T (vector-major K = A V)
     TRY(cgemm<T>(h, m, r_max, r_max, 0, dr, dr, 1, 0, w.QG, m, (long)r_max * m, OP_T, w.UR, r_max,
                  (long)r_max * r_max, OP_N, 0, 0, w.Vt, r_max, (long)m * r_max, nullptr, st));
@@ -601,13 +606,15 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
                  w.KhT, l, (long)r_max * l, nullptr, st));
     {
         const size_t smem = (size_t)(256 / 32) * (r_max + 1) * sizeof(double);
+        prof_begin(TP_KC_DP, st);
         k_dp_scan<T><<<h, 256, smem, st>>>(w.KhT, (long)r_max * l, w.alpha, r_max, w.Bhat, l, w.st, l, w.dpout,
                                            r_max + 1);
-        TRY(last_launch());
+        TRY(launched(TP_KC_DP, st));
     }
+    prof_begin(TP_KC_DP, st);
     k_dp_reduce<<<1, 256, (r_max + 1) * sizeof(double), st>>>(w.dpout, r_max + 1, h, n, w.st, P->p_over,
                                                               P->tau * P->delta, info, P->res_hist, r_max);
-    TRY(last_launch());
+    TRY(launched(TP_KC_DP, st));
     TRY(cgemm<T>(h, m, 1, r_max, 0, 0, &w.st->k, 1, 0, w.Vt, r_max, (long)m * r_max, OP_N, w.alpha, 1, r_max, OP_N,
                  0, 0, w.Xhat, 1, m, nullptr, st));
     TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));

@@ -45,7 +45,10 @@ class TikParams(ctypes.Structure):
 # every symbol include/tprod.h declares
 EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm", "rtsvd_workspace_bytes",
            "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
-           "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches")
+           "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
+           "tp_timing_read")
+
+KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
 _lib = None
 
@@ -84,6 +87,10 @@ def load(path: str | None = None):
     L.tp_status_string.restype = ctypes.c_char_p
     L.tp_version.restype = i
     L.tp_kernel_launches.restype = i
+    L.tp_timing_enable.argtypes = [i]
+    L.tp_timing_enable.restype = i
+    L.tp_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), i]
+    L.tp_timing_read.restype = i
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
               "tgkb_tikhonov_solve"):
         getattr(L, f).restype = i
@@ -97,6 +104,25 @@ def status_string(st: int) -> str:
 
 def kernel_launches() -> int:
     return int(load().tp_kernel_launches())
+
+
+def timing_enable(classes) -> None:
+    """Bracket every later launch of the named kernel classes with CUDA events."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << KERNEL_CLASSES.index(c)
+    load().tp_timing_enable(mask)
+
+
+def timing_read() -> dict:
+    """{class: (total device ms, launches)} since the last read; clears the record."""
+    n = len(KERNEL_CLASSES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    rc = load().tp_timing_read(ms, cnt, n)
+    if rc < 0:
+        raise TprodError("tp_timing_read", rc)
+    return {c: (ms[i], cnt[i]) for i, c in enumerate(KERNEL_CLASSES)}
 
 
 def _check(fn: str, st: int):

@@ -113,6 +113,14 @@ def problem(N, n=None, seed=5, noise=1e-2, general=0.02, l=None):
     return A.astype(np.float32), (Bt + E).astype(np.float32), float(np.linalg.norm(E))
 
 
+def res_tol(res, B, dtype):
+    """Residual-norm tolerance: relative part plus the rounding floor of
+    forming b - A x in the working precision (u * ||B||)."""
+    if dtype == torch.float64:
+        return 1e-9 * res + 1e-13 * np.linalg.norm(B)
+    return 1e-4 * res + 4e-6 * np.linalg.norm(B)
+
+
 def exact_k_required(out, dtype):
     return out["margin"] > TIE[dtype]
 
@@ -135,7 +143,7 @@ def test_rtsvd_matches_oracle(tp, dtype, N, n, block, q, p_over, eps_rel):
         assert info["status"] == ref["status"]
         assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
     for k, rk in ref["res"].items():
-        assert abs(hist[k] - rk) <= (1e-9 if dtype == torch.float64 else 1e-4) * rk
+        assert abs(hist[k] - rk) <= res_tol(rk, B, dtype)
     assert np.isclose(info["norm_a2"], O.fro2(A.astype(np.float64)), rtol=1e-6 if dtype == torch.float32 else 1e-12)
 
 
@@ -153,7 +161,7 @@ def test_tgkb_matches_oracle(tp, dtype, N, n, k_max, l):
         assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
     for i, ri in ref["res"].items():
         if i <= info["k"]:
-            assert abs(hist[i] - ri) <= (1e-9 if dtype == torch.float64 else 1e-4) * ri
+            assert abs(hist[i] - ri) <= res_tol(ri, B, dtype)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -201,10 +209,10 @@ def test_rtsvd_rmax_cap_reports_not_converged(tp, dtype):
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_zero_fourier_slices_break_down_cleanly(tp, dtype):
-    """Constant tubes make every Fourier slice but the first exactly zero:
-    Normalize breaks down there (zero coefficient) and the solvers must still
-    agree with the oracle."""
-    n, N = 6, 10
+    """Constant tubes make every Fourier slice but the first exactly zero (for
+    a power-of-two n both FFTs produce exact zeros): Normalize breaks down
+    there (zero coefficient) and the solvers must still agree with the oracle."""
+    n, N = 8, 10
     A = np.tile(rnd((1, N, N), 21) + 3 * np.eye(N), (n, 1, 1))
     B = np.tile(rnd((1, N, 1), 22), (n, 1, 1))
     ref = O.tgkb_solve(A, B, 1e-3, 1.1, N)
