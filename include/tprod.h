@@ -93,6 +93,26 @@ size_t tprod_gemm_workspace_bytes(int l, int kk, int m, int n, int prec);
 tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m, int n,
                      int transA, int prec, void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------- t-product, no allocation -----
+ * tprod_gemm_noalloc: the same product as tprod_gemm, for callers that cannot
+ * allocate device memory or pass a workspace (for example code inside a host
+ * framework whose device memory belongs to an allocator it cannot reach, or a
+ * latency-critical path that must not call cudaMalloc, which can block and
+ * synchronise the device).  The paper has no counterpart: this is a service
+ * of the library, not a step of the method.
+ * The scratch is a static device array of 16 MiB inside the library, held by
+ * every GPU that loads the library until the process exits.  A problem whose
+ * three spectra need more than that returns TP_ERR_WORKSPACE and enqueues
+ * nothing; the need is align256(h*l*kk*c) + align256(h*kk*m*c) +
+ * align256(h*l*m*c) bytes, h = n/2+1, c = 8 (FP32) or 16 (FP64).
+ * The first call on each device looks up the array's device address (with
+ * that device current); make it before any stream capture.  Calls share the
+ * array, so calls that overlap on the GPU race; nothing needs clearing
+ * between calls.  Arguments and layouts as tprod_gemm.
+ */
+tp_status tprod_gemm_noalloc(const void* A, const void* B, void* C, int l, int kk, int m, int n,
+                             int transA, int prec, void* stream);
+
 /* ----------------------------------------------------------- RT-tSVD ------
  * rtsvd_truncated_solve: the RT-tSVD method of Section 4.2.
  * Algorithm 3 in block form: Gaussian lateral slices are taken `block` at a

@@ -46,7 +46,7 @@ class TikParams(ctypes.Structure):
 EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm", "rtsvd_workspace_bytes",
            "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
            "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
-           "tp_timing_read")
+           "tp_timing_read", "tprod_gemm_noalloc")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -91,8 +91,9 @@ def load(path: str | None = None):
     L.tp_timing_enable.restype = i
     L.tp_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), i]
     L.tp_timing_read.restype = i
+    L.tprod_gemm_noalloc.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
-              "tgkb_tikhonov_solve"):
+              "tgkb_tikhonov_solve", "tprod_gemm_noalloc"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -206,6 +207,25 @@ def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False) -> torch.Tenso
     ws = _workspace(L.tprod_gemm_workspace_bytes(l, kk, m, n, prec), A.device)
     wp, wn = _aligned(ws)
     _check("tprod_gemm", L.tprod_gemm(_ptr(A), _ptr(B), _ptr(C), l, kk, m, n, int(transA), prec, wp, wn, _stream()))
+    return C
+
+
+def tprod_noalloc(A: torch.Tensor, B: torch.Tensor, transA: bool = False) -> torch.Tensor:
+    """t-product computed in the library's fixed 16 MiB scratch (no workspace).
+
+    For callers that cannot allocate device memory for a workspace; the output
+    tensor is still the caller's.  Raises TprodError(TP_ERR_WORKSPACE) when
+    the problem does not fit the scratch.
+    """
+    _dev(A, B)
+    n, a1, a2 = A.shape
+    nb, kk, m = B.shape
+    l = a2 if transA else a1
+    if nb != n or (a1 if transA else a2) != kk or A.dtype != B.dtype:
+        raise ValueError("shape or dtype mismatch")
+    C = torch.empty((n, l, m), dtype=A.dtype, device=A.device)
+    _check("tprod_gemm_noalloc", load().tprod_gemm_noalloc(_ptr(A), _ptr(B), _ptr(C), l, kk, m, n, int(transA),
+                                                           _prec(A), _stream()))
     return C
 
 
