@@ -2,6 +2,8 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 namespace tp {
@@ -50,6 +52,18 @@ void prof_end(int cls, cudaStream_t st) {
     }
     g_open = nullptr;
     g_open_cls = -1;
+}
+
+tp_status smem_optin(const void* kern, size_t bytes) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(kern);
+    if (it != done.end() && it->second >= bytes) return TP_OK;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return TP_ERR_CUDA;
+    done[kern] = bytes;
+    return TP_OK;
 }
 
 template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_params*);

@@ -154,9 +154,7 @@ static tp_status launch(int batch, int M, int N, int K, const int* dM, const int
     constexpr int NT = (BM / TM) * (BN / TN);
     const size_t smem = (size_t)2 * BK * ((BM + 1) + (BN + 1)) * sizeof(cplx<T>);
     auto kern = k_cgemm<T, BM, BN, BK, TM, TN>;
-    if (smem > 48 * 1024)
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return TP_ERR_CUDA;
+    if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     prof_begin(TP_KC_GEMM, st);
     kern<<<grid, NT, smem, st>>>(M, N, K, dM, dN, dK, alpha, (const cplx<T>*)A, lda, sA, opA,

@@ -68,6 +68,27 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return t;
 }
 
+// Sum of one value per thread over the block, accumulated in the working
+// precision within warps and in float64 across warps (one warp combines the
+// partials); every thread gets the result.  red: 33 doubles.  Two barriers.
+template <typename S>
+__device__ __forceinline__ double block_sum_t(S v, double* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = (double)v;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < nw ? red[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <typename V> __device__ __forceinline__ decltype(V().x) cabs2(V a) { return a.x * a.x + a.y * a.y; }
+
 template <typename T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };

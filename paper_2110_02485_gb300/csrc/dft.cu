@@ -227,9 +227,7 @@ size_t rdft_smem(int n, size_t elem) {
 
 template <typename K>
 static tp_status prep(K kern, size_t smem) {
-    if (smem > 48 * 1024)
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return TP_ERR_CUDA;
+    if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
     return TP_OK;
 }
 

@@ -12,12 +12,14 @@
 // least-squares problem, solved incrementally by Givens rotations (float64).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace tp {
 
-constexpr int GKB_THREADS = 256;
+constexpr int GKB_THREADS = 512;
 constexpr int GKB_KMAX = 512;
 
 struct GkbShared {
@@ -89,47 +91,39 @@ __device__ void mv_n(const cplx<T>* __restrict__ A, int l, int m, const cplx<T>*
     }
 }
 
-// Two classical Gram-Schmidt passes of u (length L, shared) against cnt basis
-// vectors stored contiguously (stride L) in global memory.
-template <typename T>
-__device__ void reorth(cplx<T>* u, const cplx<T>* basis, int cnt, int L, cplx<T>* cf) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (cnt <= 0) return;
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int i = warp; i < cnt; i += nw) {
-            cplx<T> acc = mk<T>(0, 0);
-            const cplx<T>* bv = basis + (long)i * L;
-            for (int e = lane; e < L; e += 32) cfmac(acc, bv[e], u[e]);
-            acc.x = warp_sum(acc.x);
-            acc.y = warp_sum(acc.y);
-            if (lane == 0) cf[i] = acc;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < L; e += blockDim.x) {
-            cplx<T> acc = mk<T>(0, 0);
-            for (int i = 0; i < cnt; ++i) cfma(acc, basis[(long)i * L + e], cf[i]);
-            u[e] = csub(u[e], acc);
-        }
-        __syncthreads();
-    }
-}
-
 // Normalize (per slice): returns ||u|| and scales u to unit length (zero stays zero).
 template <typename T>
 __device__ double normalize_vec(cplx<T>* u, int L, double* red, double* bc) {
-    double p = 0.0;
-    for (int e = threadIdx.x; e < L; e += blockDim.x) p += cabs2d(u[e]);
-    p = block_sum(p, red);
-    if (threadIdx.x == 0) *bc = p;
+    T p = 0;
+    for (int e = threadIdx.x; e < L; e += blockDim.x) p += cabs2(u[e]);
+    // block sum in the working precision (one warp combines the warp partials)
+    p = warp_sum(p);
+    T* redt = (T*)red;
     __syncthreads();
-    const double nrm2 = *bc;
-    const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
-    for (int e = threadIdx.x; e < L; e += blockDim.x) {
-        const cplx<T> v = u[e];
-        u[e] = mk<T>((T)((double)v.x * inv), (T)((double)v.y * inv));
+    if ((threadIdx.x & 31) == 0) redt[threadIdx.x >> 5] = p;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T t = threadIdx.x < (blockDim.x >> 5) ? redt[threadIdx.x] : (T)0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) red[32] = (double)t;
     }
     __syncthreads();
-    return sqrt(nrm2);
+    const double nrm2 = red[32];  // every thread gets the sum
+    // 1/||u|| in the working precision (float64 divide/sqrt are slow here);
+    // float64 only when the float value would not be finite
+    const T n2t = (T)nrm2;
+    const T invt = n2t > (T)0 ? (T)1 / sqrt(n2t) : (T)0;
+    if (isfinite(invt) && (n2t > (T)0 || nrm2 == 0.0)) {
+        for (int e = threadIdx.x; e < L; e += blockDim.x) u[e] = cscale(u[e], invt);
+    } else {
+        const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+        for (int e = threadIdx.x; e < L; e += blockDim.x) {
+            const cplx<T> v = u[e];
+            u[e] = mk<T>((T)((double)v.x * inv), (T)((double)v.y * inv));
+        }
+    }
+    __syncthreads();
+    return (double)sqrt(n2t > (T)0 ? n2t : (T)0) + (n2t > (T)0 ? 0.0 : sqrt(nrm2));
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -138,13 +132,192 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
+// ---- streaming matrix-vector products over one Fourier slice --------------
+// 16-byte vector loads straight from global memory (the slice is contiguous),
+// eight rows in flight per thread, one CTA barrier per product.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; static constexpr int VW = 2; };
+template <> struct Vec16<double> { typedef double2 type; static constexpr int VW = 1; };
+
+template <typename T>
+__device__ __forceinline__ void unpack(const typename Vec16<T>::type& x, cplx<T>* o);
+template <> __device__ __forceinline__ void unpack<float>(const float4& x, float2* o) {
+    o[0] = make_float2(x.x, x.y);
+    o[1] = make_float2(x.z, x.w);
+}
+template <> __device__ __forceinline__ void unpack<double>(const double2& x, double2* o) { o[0] = x; }
+
+// u = A^H q - z * w.  Requires m / VW <= blockDim (one vector column per
+// thread); rg = blockDim / (m / VW) row groups; part holds blockDim * VW entries.
+template <typename T>
+__device__ void mv_h_vec(const cplx<T>* __restrict__ A, int l, int m, const cplx<T>* q, const cplx<T>* w, T z,
+                         cplx<T>* u, cplx<T>* part) {
+    typedef cplx<T> V;
+    typedef typename Vec16<T>::type LV;
+    constexpr int VW = Vec16<T>::VW, UR = 8;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    const int mv = m / VW, rg = NT / mv;
+    const int g = tid / mv, cv = tid - g * mv;
+    const LV* Av = (const LV*)A + cv;
+    V acc[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] = mk<T>(0, 0);
+    if (g < rg) {
+        int i = g;
+        for (; i + (UR - 1) * rg < l; i += UR * rg) {
+            LV a[UR];
+#pragma unroll
+            for (int rr = 0; rr < UR; ++rr) a[rr] = __ldcg(Av + (long)(i + rr * rg) * mv);
+#pragma unroll
+            for (int rr = 0; rr < UR; ++rr) {
+                const V qv = q[i + rr * rg];
+                V e[VW];
+                unpack<T>(a[rr], e);
+#pragma unroll
+                for (int v = 0; v < VW; ++v) cfmac(acc[v], e[v], qv);
+            }
+        }
+        for (; i < l; i += rg) {
+            const V qv = q[i];
+            V e[VW];
+            unpack<T>(__ldcg(Av + (long)i * mv), e);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) cfmac(acc[v], e[v], qv);
+        }
+#pragma unroll
+        for (int v = 0; v < VW; ++v) part[g * m + cv * VW + v] = acc[v];
+    }
+    __syncthreads();
+    for (int j = tid; j < m; j += NT) {
+        V t = mk<T>(0, 0);
+        for (int p = 0; p < rg; ++p) t = cadd(t, part[p * m + j]);
+        u[j] = csub(t, cscale(w[j], z));
+    }
+    __syncthreads();
+}
+
+// u = A w - c * q   (one warp per row, four rows at a time, 4 vector columns per lane per pass)
+template <typename T>
+__device__ void mv_n_vec(const cplx<T>* __restrict__ A, int l, int m, const cplx<T>* w, const cplx<T>* q, T cq,
+                         cplx<T>* u) {
+    typedef cplx<T> V;
+    typedef typename Vec16<T>::type LV;
+    constexpr int VW = Vec16<T>::VW, CH = 4, RW = 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int mv = m / VW;
+    const LV* Av = (const LV*)A;
+    for (int i = warp * RW; i < l; i += RW * nw) {
+        V sacc[RW];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) sacc[r] = mk<T>(0, 0);
+        for (int t0 = 0; t0 * 32 < mv; t0 += CH) {
+            LV a[RW][CH];
+#pragma unroll
+            for (int r = 0; r < RW; ++r)
+#pragma unroll
+                for (int tt = 0; tt < CH; ++tt) {
+                    const int cvv = lane + 32 * (t0 + tt);
+                    if (cvv < mv && i + r < l) a[r][tt] = __ldcg(Av + (long)(i + r) * mv + cvv);
+                }
+#pragma unroll
+            for (int tt = 0; tt < CH; ++tt) {
+                const int cvv = lane + 32 * (t0 + tt);
+                if (cvv < mv) {
+                    V wv[VW];
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) wv[v] = w[cvv * VW + v];
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) {
+                        if (i + r < l) {
+                            V e[VW];
+                            unpack<T>(a[r][tt], e);
+#pragma unroll
+                            for (int v = 0; v < VW; ++v) cfma(sacc[r], e[v], wv[v]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            sacc[r].x = warp_sum(sacc[r].x);
+            sacc[r].y = warp_sum(sacc[r].y);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int r = 0; r < RW; ++r)
+                if (i + r < l) u[i + r] = csub(sacc[r], cscale(q[i + r], cq));
+    }
+    __syncthreads();
+}
+
+// Two classical Gram-Schmidt passes of u (length L, shared) against cnt basis
+// vectors of stride L: the first kc live in shared memory (sb), the rest in
+// global memory (gb).  Loads of each phase are unrolled so that many are in
+// flight.  part: 4*L scratch.
+template <typename T>
+__device__ __forceinline__ const cplx<T>* bvec(const cplx<T>* sb, const cplx<T>* gb, int kc, int i, int L) {
+    return (i < kc ? sb : gb) + (long)i * L;
+}
+
+template <typename T>
+__device__ void reorth2(cplx<T>* u, const cplx<T>* sb, const cplx<T>* __restrict__ gb, int kc, int cnt, int L,
+                        cplx<T>* cf, cplx<T>* part) {
+    typedef cplx<T> V;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, NT = blockDim.x;
+    if (cnt <= 0) return;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = warp; i < cnt; i += nw) {
+            const V* bv = bvec<T>(sb, gb, kc, i, L);
+            V acc = mk<T>(0, 0);
+            int e = lane;
+            for (; e + 96 < L; e += 128) {
+                const V b0 = bv[e], b1 = bv[e + 32], b2 = bv[e + 64], b3 = bv[e + 96];
+                cfmac(acc, b0, u[e]);
+                cfmac(acc, b1, u[e + 32]);
+                cfmac(acc, b2, u[e + 64]);
+                cfmac(acc, b3, u[e + 96]);
+            }
+            for (; e < L; e += 32) cfmac(acc, bv[e], u[e]);
+            acc.x = warp_sum(acc.x);
+            acc.y = warp_sum(acc.y);
+            if (lane == 0) cf[i] = acc;
+        }
+        __syncthreads();
+        // u -= sum_i basis_i cf_i, the basis split over G groups of threads
+        const int G = (NT / L) >= 4 ? 4 : ((NT / L) >= 2 ? 2 : 1);
+        for (int idx = threadIdx.x; idx < L * G; idx += NT) {
+            const int g = idx / L, e = idx - g * L;
+            V acc = mk<T>(0, 0);
+            int i = g;
+            for (; i + 3 * G < cnt; i += 4 * G) {
+                const V b0 = bvec<T>(sb, gb, kc, i, L)[e], b1 = bvec<T>(sb, gb, kc, i + G, L)[e];
+                const V b2 = bvec<T>(sb, gb, kc, i + 2 * G, L)[e], b3 = bvec<T>(sb, gb, kc, i + 3 * G, L)[e];
+                cfma(acc, b0, cf[i]);
+                cfma(acc, b1, cf[i + G]);
+                cfma(acc, b2, cf[i + 2 * G]);
+                cfma(acc, b3, cf[i + 3 * G]);
+            }
+            for (; i < cnt; i += G) cfma(acc, bvec<T>(sb, gb, kc, i, L)[e], cf[i]);
+            part[g * L + e] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < L; e += NT) {
+            V t = u[e];
+            for (int g = 0; g < G; ++g) t = csub(t, part[g * L + e]);
+            u[e] = t;
+        }
+        __syncthreads();
+    }
+}
+
 // Persistent tGKB.  Outputs per slice: W (k_max x m), Q (k_max+1 x l),
 // c (k_max), z (k_max+1), Xhat (m) for the chosen k; State k/status; info.
-template <typename T>
-__global__ void __launch_bounds__(GKB_THREADS)
+template <typename T, bool VEC, int NT>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2)
 k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l, int m, int n, int h, int k_max,
       double tau_delta, cplx<T>* Wb, cplx<T>* Qb, double* cc, double* zz, double* res2, unsigned* counters,
-      cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info) {
+      cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info, int kc) {
     typedef cplx<T> V;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = l > m ? l : m;
@@ -152,8 +325,12 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
     V* w = q + l;               // m
     V* u = w + m;               // L
     V* cf = u + L;              // k_max + 1
+    V* part = cf + k_max + 1;   // max(4 L, NT * VW)
+    const int part_n = (4 * L > NT * (16 / (int)sizeof(V))) ? 4 * L : NT * (16 / (int)sizeof(V));
+    V* Wc = part + part_n;      // kc cached vectors of W (m each)
+    V* Qc = Wc + (long)kc * m;  // kc cached vectors of Q (l each)
     __shared__ GkbShared S;
-    __shared__ double red[GKB_THREADS / 32];
+    __shared__ double red[33];
     __shared__ double bc;
     __shared__ int flag_done, flag_timeout;
     const int s = blockIdx.x, tid = threadIdx.x;
@@ -171,6 +348,7 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
     for (int e = tid; e < l; e += blockDim.x) {
         q[e] = u[e];
         Qv[e] = u[e];
+        if (kc > 0) Qc[e] = u[e];
     }
     if (tid == 0) {
         zs_[0] = z1;
@@ -179,33 +357,43 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
     }
     __syncthreads();
 
-    // Givens state (thread 0): rhobar, phibar, previous rotation, orphan residual
+    // Givens state (thread 0): phibar, previous rotation, orphan residual
     double phibar = z1, cs_prev = 1.0, sn_prev = 0.0, orphan = 0.0;
     double zprev = z1;
     int k = k_max;
     for (int i = 1; i <= k_max; ++i) {
         // W_i = A^T * Q_i - W_{i-1} * z_i ; reorthogonalise ; Normalize -> c_i
-        mv_h<T>(A, l, m, q, u);
-        __syncthreads();
-        for (int e = tid; e < m; e += blockDim.x) u[e] = csub(u[e], cscale(w[e], (T)zprev));
-        __syncthreads();
-        reorth<T>(u, W, i - 1, m, cf);
+        if (VEC) {
+            mv_h_vec<T>(A, l, m, q, w, (T)zprev, u, part);
+        } else {
+            mv_h<T>(A, l, m, q, u);
+            __syncthreads();
+            for (int e = tid; e < m; e += blockDim.x) u[e] = csub(u[e], cscale(w[e], (T)zprev));
+            __syncthreads();
+        }
+        reorth2<T>(u, Wc, W, kc, i - 1, m, cf, part);
         const double ci = normalize_vec<T>(u, m, red, &bc);
         for (int e = tid; e < m; e += blockDim.x) {
             w[e] = u[e];
             W[(long)(i - 1) * m + e] = u[e];
+            if (i - 1 < kc) Wc[(long)(i - 1) * m + e] = u[e];
         }
         __syncthreads();
         // Q_{i+1} = A * W_i - Q_i * c_i ; reorthogonalise ; Normalize -> z_{i+1}
-        mv_n<T>(A, l, m, w, u);
-        __syncthreads();
-        for (int e = tid; e < l; e += blockDim.x) u[e] = csub(u[e], cscale(q[e], (T)ci));
-        __syncthreads();
-        reorth<T>(u, Qv, i, l, cf);
+        if (VEC) {
+            mv_n_vec<T>(A, l, m, w, q, (T)ci, u);
+        } else {
+            mv_n<T>(A, l, m, w, u);
+            __syncthreads();
+            for (int e = tid; e < l; e += blockDim.x) u[e] = csub(u[e], cscale(q[e], (T)ci));
+            __syncthreads();
+        }
+        reorth2<T>(u, Qc, Qv, kc, i, l, cf, part);
         const double zi = normalize_vec<T>(u, l, red, &bc);
         for (int e = tid; e < l; e += blockDim.x) {
             q[e] = u[e];
             Qv[(long)i * l + e] = u[e];
+            if (i < kc) Qc[(long)i * l + e] = u[e];
         }
         if (tid == 0) {
             cs_[i - 1] = ci;
@@ -241,9 +429,14 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
                 }
             }
             __threadfence();
-            if (!flag_timeout) {
-                double tot = 0.0;
-                for (int s2 = 0; s2 < h; ++s2) tot += __ldcg(&res2[(long)i * h + s2]);
+        }
+        __syncthreads();
+        // residual of step i: the same fixed-order sum over slices in every CTA
+        if (tid < 32 && !flag_timeout) {
+            double tot = 0.0;
+            for (int s2 = tid; s2 < h; s2 += 32) tot += __ldcg(&res2[(long)i * h + s2]);
+            tot = warp_sum(tot);
+            if (tid == 0) {
                 S.res[i] = sqrt(tot / (double)n);
                 if (S.res[i] <= tau_delta) flag_done = 1;
             }
@@ -307,41 +500,49 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
 // solved by Givens QR of [P; lam I] (two rotations per column); returns the
 // data residual ||P y - z1 e1||^2 and optionally y.
 // ---------------------------------------------------------------------------
-__device__ double damped_bidiag(const double* c, const double* z, int k, double lam, double* y, double* scr,
-                               int kcap) {
-    // scr: 4 * kcap doubles of per-thread scratch (rho, theta, phi, y)
-    double* rho = scr;
-    double* theta = scr + kcap;
-    double* phi = scr + 2 * kcap;
-    double* yy = y ? y : scr + 3 * kcap;
-    double rhobar = k > 0 ? c[0] : 0.0, phibar = z[0];
+template <typename R>
+__device__ double damped_bidiag(const double* c, const double* z, int k, R lam, R* y, R* scr, int kcap, int stride) {
+    // scr: per-thread scratch of 4 arrays (rho, theta, phi, y) of kcap entries,
+    // entry j of an array at scr[j * stride] (stride = threads sharing the
+    // buffer, so that neighbouring threads touch neighbouring addresses).
+    // Working precision R: the bidiagonal entries come from R-precision vectors.
+    struct Strided {
+        R* p;
+        int st;
+        __device__ R& operator[](int j) const { return p[(long)j * st]; }
+    };
+    const long a = (long)kcap * stride;
+    Strided rho{scr, stride}, theta{scr + a, stride}, phi{scr + 2 * a, stride};
+    Strided yy = y ? Strided{y, 1} : Strided{scr + 3 * a, stride};
+    R rhobar = k > 0 ? (R)c[0] : (R)0, phibar = (R)z[0];
     for (int j = 0; j < k; ++j) {
-        const double rh = hypot(rhobar, lam);          // eliminate the damping row
-        const double c1 = rh > 0.0 ? rhobar / rh : 1.0;
-        const double ph = c1 * phibar;
-        const double rj = hypot(rh, z[j + 1]);         // eliminate z_{j+2}
-        double cs = 1.0, sn = 0.0;
-        if (rj > 0.0) {
+        const R rh = hypot(rhobar, lam);          // eliminate the damping row
+        const R c1 = rh > (R)0 ? rhobar / rh : (R)1;
+        const R ph = c1 * phibar;
+        const R zj = (R)z[j + 1];
+        const R rj = hypot(rh, zj);               // eliminate z_{j+2}
+        R cs = 1, sn = 0;
+        if (rj > (R)0) {
             cs = rh / rj;
-            sn = z[j + 1] / rj;
+            sn = zj / rj;
         }
         rho[j] = rj;
         phi[j] = cs * ph;
         phibar = -sn * ph;
         if (j + 1 < k) {
-            theta[j + 1] = sn * c[j + 1];
-            rhobar = cs * c[j + 1];
+            theta[j + 1] = sn * (R)c[j + 1];
+            rhobar = cs * (R)c[j + 1];
         }
     }
     for (int j = k - 1; j >= 0; --j) {
-        double v = phi[j];
+        R v = phi[j];
         if (j + 1 < k) v -= theta[j + 1] * yy[j + 1];
-        yy[j] = rho[j] > 0.0 ? v / rho[j] : 0.0;
+        yy[j] = rho[j] > (R)0 ? v / rho[j] : (R)0;
     }
     // data residual: r_1 = c_1 y_1 - z_1, r_j = z_j y_{j-1} + c_j y_j, r_{k+1} = z_{k+1} y_k
     double r2 = 0.0;
     for (int j = 0; j <= k; ++j) {
-        double v = (j < k ? c[j] * yy[j] : 0.0) + (j > 0 ? z[j] * yy[j - 1] : 0.0);
+        double v = (j < k ? c[j] * (double)yy[j] : 0.0) + (j > 0 ? z[j] * (double)yy[j - 1] : 0.0);
         if (j == 0) v -= z[0];
         r2 += v * v;
     }
@@ -353,21 +554,23 @@ struct TikState {
     int done, status, round;
 };
 
-constexpr int TIK_P = 64;
+constexpr int TIK_P = 256;
 
 // f at TIK_P points of the current bracket for every slice: out[p*h + s]
+template <typename R>
 __global__ void __launch_bounds__(TIK_P)
 k_tik_eval(const double* cc, const double* zz, int k_max, const State* st, const TikState* ts, int h, int n,
-           double* out, double* scratch) {
+           double* out, R* scratch) {
     if (ts->done) return;
     const int s = blockIdx.x, p = threadIdx.x, k = st->k;
     double t;
     if (p == 0) t = ts->lo;
     else if (p == TIK_P - 1) t = ts->hi;
     else t = ts->lo + (ts->hi - ts->lo) * (double)p / (double)(TIK_P - 1);
-    const double lam = sqrt(pow(10.0, -t));
-    double* scr = scratch + ((long)p * h + s) * 4 * k_max;
-    const double r2 = damped_bidiag(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, nullptr, scr, k_max);
+    const R lam = (R)sqrt(pow(10.0, -t));
+    R* scr = scratch + (long)s * TIK_P * 4 * k_max + p;
+    const double r2 = damped_bidiag<R>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, nullptr, scr, k_max,
+                                       TIK_P);
     out[(long)p * h + s] = parseval_w(s, n) * r2;
 }
 
@@ -417,13 +620,13 @@ k_tik_select(const double* out, int h, int n, double tau_delta, double log_tol, 
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_tik_final(const double* cc, const double* zz, int k_max, const cplx<T>* Wb, int m, const State* st,
-            const TikState* ts, int n, double* out, cplx<T>* Xhat, double* scratch) {
-    __shared__ double y[GKB_KMAX];
+            const TikState* ts, int n, double* out, cplx<T>* Xhat, T* scratch) {
+    __shared__ T y[GKB_KMAX];
     const int s = blockIdx.x, k = st->k;
     const double mu = pow(10.0, ts->t);
     if (threadIdx.x == 0) {
-        const double r2 = damped_bidiag(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, sqrt(1.0 / mu), y,
-                                        scratch + (long)s * 4 * k_max, k_max);
+        const double r2 = damped_bidiag<T>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, (T)sqrt(1.0 / mu), y,
+                                           scratch + (long)s * TIK_P * 4 * k_max, k_max, 1);
         out[s] = parseval_w(s, n) * r2;
     }
     __syncthreads();
@@ -432,8 +635,8 @@ k_tik_final(const double* cc, const double* zz, int k_max, const cplx<T>* Wb, in
         double xr = 0.0, xi = 0.0;
         for (int j = 0; j < k; ++j) {
             const cplx<T> v = W[(long)j * m + e];
-            xr += (double)v.x * y[j];
-            xi += (double)v.y * y[j];
+            xr += (double)v.x * (double)y[j];
+            xi += (double)v.y * (double)y[j];
         }
         Xhat[(long)s * m + e] = mk<T>((T)xr, (T)xi);
     }
@@ -473,7 +676,8 @@ struct GkWs {
     State* st;
     TikState* ts;
     unsigned* counters;
-    double *res2, *cc, *zz, *tout, *tscr;
+    double *res2, *cc, *zz, *tout;
+    T* tscr;
     cplx<T> *Ahat, *Bhat, *W, *Q, *Xhat;
     size_t bytes;
 };
@@ -491,7 +695,7 @@ static GkWs<T> gk_carve(void* base, int l, int m, int n, int k_max) {
     w.cc = c.take<double>(h * k_max);
     w.zz = c.take<double>(h * (k_max + 1));
     w.tout = c.take<double>((long)TIK_P * h);
-    w.tscr = c.take<double>((long)TIK_P * h * 4 * k_max);
+    w.tscr = c.take<T>((long)TIK_P * h * 4 * k_max);
     w.Ahat = c.take<V>(h * l * m);
     w.Bhat = c.take<V>(h * l);
     w.W = c.take<V>(h * (long)k_max * m);
@@ -532,16 +736,31 @@ static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tg
     TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, nullptr, nullptr, st));
     TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, nullptr, nullptr, st));
     const int L = l > m ? l : m;
-    const size_t smem = ((size_t)l + m + L + k_max + 1) * sizeof(cplx<T>);
-    auto kern = k_gkb<T>;
-    if (smem > 48 * 1024)
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return TP_ERR_CUDA;
     int dev = 0, nsm = 0, per_sm = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return TP_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GKB_THREADS, smem) != cudaSuccess)
+    // One CTA per Fourier slice, all resident (cooperative launch): 1024
+    // threads when one CTA per SM suffices, else 512.  Vector loads need
+    // 16-byte aligned rows.  Spare shared memory caches the first kc vectors
+    // of both Krylov bases.
+    const size_t vb = sizeof(cplx<T>);
+    const int nt = (h <= nsm) ? 1024 : 512;
+    const bool vec = ((size_t)m * vb) % 16 == 0 && (size_t)m * vb / 16 <= (size_t)nt;
+    const size_t part_n = std::max<size_t>(4 * (size_t)L, 16 / vb * (size_t)nt);
+    const size_t base_bytes = ((size_t)l + m + L + k_max + 1 + part_n) * vb;
+    const size_t static_bytes = 24 * 1024;  // GkbShared and small arrays
+    const size_t per_cta = (size_t)(228 * 1024) / (size_t)((h + nsm - 1) / nsm) - 2048;
+    const size_t avail = per_cta > base_bytes + static_bytes ? per_cta - base_bytes - static_bytes : 0;
+    // A shared-memory cache of the bases measured slower: it takes the L1
+    // capacity that the streaming loads of A-hat need in flight.
+    const int kc = 0 * (int)std::min<size_t>((size_t)k_max + 1, avail / (((size_t)l + m) * vb));
+    const size_t smem = base_bytes + (size_t)kc * ((size_t)l + m) * vb;
+    const void* kern;
+    if (nt == 1024) kern = vec ? (const void*)k_gkb<T, true, 1024> : (const void*)k_gkb<T, false, 1024>;
+    else kern = vec ? (const void*)k_gkb<T, true, 512> : (const void*)k_gkb<T, false, 512>;
+    if (smem_optin(kern, smem) != TP_OK) return TP_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess)
         return TP_ERR_CUDA;
     if (!coop || (long)per_sm * nsm < h) return TP_ERR_UNSUPPORTED;
     const cplx<T>* Ahat = w.Ahat;
@@ -550,11 +769,12 @@ static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tg
     double td = P->tau * P->delta;
     long long spin = 4000000000LL;  // ~2 s at the GB300 SM clock
     double* rh = P->res_hist;
+    int kc_ = kc;
     void* args[] = {(void*)&Ahat, (void*)&Bhat, &l_, &m_, &n_, &h_, &k_, &td, (void*)&w.W, (void*)&w.Q,
                     (void*)&w.cc, (void*)&w.zz, (void*)&w.res2, (void*)&w.counters, (void*)&w.Xhat,
-                    (void*)&w.st, (void*)&info, (void*)&rh, &spin, &wi};
+                    (void*)&w.st, (void*)&info, (void*)&rh, &spin, &wi, &kc_};
     prof_begin(TP_KC_GKB, st);
-    if (cudaLaunchCooperativeKernel((const void*)kern, dim3(h), dim3(GKB_THREADS), args, smem, st) != cudaSuccess)
+    if (cudaLaunchCooperativeKernel(kern, dim3(h), dim3(nt), args, smem, st) != cudaSuccess)
         return TP_ERR_CUDA;
     return launched(TP_KC_GKB, st);
 }
@@ -598,7 +818,7 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     for (double width = hi - lo; width > tol && rounds < 40; width /= (TIK_P - 1)) ++rounds;
     for (int it = 0; it < rounds; ++it) {
         prof_begin(TP_KC_TIK, st);
-        k_tik_eval<<<h, TIK_P, 0, st>>>(w.cc, w.zz, k_max, w.st, w.ts, h, n, w.tout, w.tscr);
+        k_tik_eval<T><<<h, TIK_P, 0, st>>>(w.cc, w.zz, k_max, w.st, w.ts, h, n, w.tout, w.tscr);
         TRY(launched(TP_KC_TIK, st));
         prof_begin(TP_KC_TIK, st);
         k_tik_select<<<1, TIK_P, 0, st>>>(w.tout, h, n, td, tol, w.ts);

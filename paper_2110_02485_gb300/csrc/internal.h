@@ -17,6 +17,10 @@ inline tp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TP_OK : 
 // launched() records the matching end event.
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
+// Opt a kernel into `bytes` of dynamic shared memory.  Always needed when
+// static + dynamic shared memory exceeds 48 KB; cached per kernel.
+tp_status smem_optin(const void* kern, size_t bytes);
+
 inline tp_status launched(int cls, cudaStream_t st) {
     ++g_launches;
     prof_end(cls, st);

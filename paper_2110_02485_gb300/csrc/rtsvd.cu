@@ -18,131 +18,249 @@
 
 namespace tp {
 
-constexpr int ORTH_THREADS = 256;
-constexpr int JAC_THREADS = 512;
+constexpr int JAC_THREADS = 1024;
 constexpr int MAX_BLOCK = 32;
 
 // ---------------------------------------------------------------------------
-// Block orthonormalisation (Algorithm 3, steps 5-9, in block form):
-//   Y <- Y - Q (Q^H Y)   twice   (classical Gram-Schmidt against the basis)
-//   then column by column: two CGS passes against the earlier block columns
-//   and Normalize (a zero column stays zero).
-// Y is L x b row-major per slice.  Optionally writes the result into the
-// basis array (rows r_prev .. r_prev+b-1, vector-major), the R coefficients
-// (rows 0..r_prev+b-1, columns r_prev.. of a row-major r_max x r_max matrix),
-// and the float64 squared norm of the input block.
+// Block orthonormalisation (Algorithm 3, Normalize + reorthogonalisation, in
+// block form), one CTA of 1024 threads per Fourier slice:
+//   1. Y <- Y - Q (Q^H Y), twice (classical Gram-Schmidt against the basis);
+//   2. Y = Q_new R by shifted Cholesky-QR3 (Fukaya et al., 2020): one Cholesky
+//      QR of the Gram matrix shifted by 11 (L b + b(b+1)) u ||Y||_F^2, then two
+//      plain Cholesky QR passes.  R is upper triangular with a positive real
+//      diagonal, so in exact arithmetic Q_new is the Gram-Schmidt basis (the
+//      QR factorisation with that normalisation is unique); a zero column
+//      (zero pivot) stays zero, as Normalize's breakdown branch gives.
+// Y is L x b row-major per slice (b <= BB).  Optional outputs: the basis rows
+// r_prev .. r_prev+b-1 (vector-major), the block column of R (coefficients
+// against the earlier basis above, the in-block R below, zeros further down to
+// row r_rows), and the float64 squared norm of the input block.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(ORTH_THREADS)
+constexpr int ORTH2_GROUPS = 4;  // column groups in the update phase
+// threads per CTA: as many as the register footprint of BB accumulators allows
+template <typename T, int BB> struct OrthThreads {
+    static constexpr int v = (sizeof(T) == 8 && BB == 32) ? 256 : 512;
+};
+
+// Reduce-scatter of BB complex values over a warp: returns the warp sum of
+// column (BB == 32 ? lane : lane >> 1).
+template <typename V, int BB>
+__device__ __forceinline__ V warp_reduce_scatter(V (&v)[BB]) {
+    const int lane = threadIdx.x & 31;
+    int cnt = BB;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (cnt > 1) {
+            const bool hi = (lane & o) != 0;
+            const int half = cnt >> 1;
+#pragma unroll
+            for (int t = 0; t < BB / 2; ++t) {
+                if (t < half) {
+                    V keep = hi ? v[half + t] : v[t];
+                    V send = hi ? v[t] : v[half + t];
+                    send.x = __shfl_xor_sync(0xffffffffu, send.x, o);
+                    send.y = __shfl_xor_sync(0xffffffffu, send.y, o);
+                    v[t] = cadd(keep, send);
+                }
+            }
+            cnt = half;
+        } else {
+            V send = v[0];
+            send.x = __shfl_xor_sync(0xffffffffu, send.x, o);
+            send.y = __shfl_xor_sync(0xffffffffu, send.y, o);
+            v[0] = cadd(v[0], send);
+        }
+    }
+    return v[0];
+}
+
+template <typename T, int BB>
+__global__ void __launch_bounds__(OrthThreads<T, BB>::v)
 k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev, cplx<T>* Qout,
        cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip) {
     typedef cplx<T> V;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* Ys = (V*)smraw;                  // Ys[j*L + row]
-    V* Cs = Ys + (size_t)b * L;         // r_prev x b, summed over both passes
-    V* Cp = Cs + (size_t)r_prev * b;    // r_prev x b, this pass
-    V* cb = Cp + (size_t)r_prev * b;    // MAX_BLOCK
-    V* Rb = cb + MAX_BLOCK;             // b x b
-    __shared__ double red[ORTH_THREADS / 32];
-    __shared__ double bcast;
-    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    V* Ys = (V*)smraw;                      // Ys[j*L + row], BB columns (unused ones zero)
+    V* Cs = Ys + (size_t)BB * L;            // r_prev x BB, summed over both passes
+    V* Cp = Cs + (size_t)r_prev * BB;       // r_prev x BB, this pass
+    V* G = Cp + (size_t)r_prev * BB;        // BB x BB Gram / Cholesky work
+    V* Rk = G + BB * BB;                    // this pass's R
+    V* Ra = Rk + BB * BB;                   // accumulated in-block R
+    V* Rt = Ra + BB * BB;                   // scratch for the product
+    __shared__ double red[33];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = OrthThreads<T, BB>::v / 32;
     Y += (long)s * sY;
 
-    double nn = 0.0;
-    for (int e = tid; e < L * b; e += blockDim.x) {
-        const int row = e / b, j = e - row * b;
-        const V v = Y[e];
-        Ys[(size_t)j * L + row] = v;
-        nn += cabs2d(v);
+    T nn = 0;
+    for (int e = tid; e < L * BB; e += blockDim.x) {
+        const int j = e / L, row = e - j * L;
+        V v = mk<T>(0, 0);
+        if (j < b) v = Y[(long)row * b + j];
+        Ys[e] = v;
+        nn += cabs2(v);
     }
-    for (int e = tid; e < b * b; e += blockDim.x) Rb[e] = mk<T>(0, 0);
-    nn = block_sum(nn, red);
-    if (normsq && tid == 0) normsq[s] = nn;
+    for (int e = tid; e < BB * BB; e += blockDim.x) Ra[e] = mk<T>((e / BB) == (e % BB) ? (T)1 : (T)0, 0);
+    const double nnd = block_sum_t(nn, red);
+    if (normsq && tid == 0) normsq[s] = nnd;
 
+    // 1. two CGS passes against the basis
     if (r_prev > 0) {
         const V* Q = Qb + (long)s * sQ;
         for (int pass = 0; pass < 2; ++pass) {
-            for (int i = warp; i < r_prev; i += nw) {
-                V acc[MAX_BLOCK];
+            // two basis vectors per warp share every shared-memory read of Y
+            for (int i0 = 2 * warp; i0 < r_prev; i0 += 2 * NW) {
+                const bool two = i0 + 1 < r_prev;
+                V acc0[BB], acc1[BB];
 #pragma unroll
-                for (int j = 0; j < MAX_BLOCK; ++j) acc[j] = mk<T>(0, 0);
-                for (int row = lane; row < L; row += 32) {
-                    const V q = Q[(long)i * L + row];
+                for (int j = 0; j < BB; ++j) acc0[j] = acc1[j] = mk<T>(0, 0);
+                const V* qa = Q + (long)i0 * L;
+                const V* qb = two ? qa + L : qa;
+                int row = lane;
+                for (; row + 32 < L; row += 64) {
+                    const V a0 = qa[row], a1 = qa[row + 32];
+                    V b0 = qb[row], b1 = qb[row + 32];
+                    if (!two) b0 = b1 = mk<T>(0, 0);
 #pragma unroll
-                    for (int j = 0; j < MAX_BLOCK; ++j)
-                        if (j < b) cfmac(acc[j], q, Ys[(size_t)j * L + row]);
-                }
-#pragma unroll
-                for (int j = 0; j < MAX_BLOCK; ++j) {
-                    if (j < b) {
-                        acc[j].x = warp_sum(acc[j].x);
-                        acc[j].y = warp_sum(acc[j].y);
+                    for (int j = 0; j < BB; ++j) {
+                        const V y0 = Ys[j * L + row], y1 = Ys[j * L + row + 32];
+                        cfmac(acc0[j], a0, y0);
+                        cfmac(acc1[j], b0, y0);
+                        cfmac(acc0[j], a1, y1);
+                        cfmac(acc1[j], b1, y1);
                     }
                 }
-                if (lane == 0)
-                    for (int j = 0; j < b; ++j) Cp[(size_t)i * b + j] = acc[j];
+                for (; row < L; row += 32) {
+                    const V a0 = qa[row];
+                    const V b0 = two ? qb[row] : mk<T>(0, 0);
+#pragma unroll
+                    for (int j = 0; j < BB; ++j) {
+                        const V y0 = Ys[j * L + row];
+                        cfmac(acc0[j], a0, y0);
+                        cfmac(acc1[j], b0, y0);
+                    }
+                }
+                const int col = (BB == 32) ? lane : (lane >> 1);
+                const V t0 = warp_reduce_scatter<V, BB>(acc0);
+                if ((BB == 32 || (lane & 1) == 0)) Cp[(size_t)i0 * BB + col] = t0;
+                const V t1 = warp_reduce_scatter<V, BB>(acc1);
+                if (two && (BB == 32 || (lane & 1) == 0)) Cp[(size_t)(i0 + 1) * BB + col] = t1;
             }
             __syncthreads();
-            for (int row = tid; row < L; row += blockDim.x) {
-                V acc[MAX_BLOCK];
+            constexpr int CPG = BB / ORTH2_GROUPS;
+            for (int e = tid; e < L * ORTH2_GROUPS; e += blockDim.x) {
+                const int g = e / L, row = e - g * L;
+                V acc[CPG];
 #pragma unroll
-                for (int j = 0; j < MAX_BLOCK; ++j) acc[j] = mk<T>(0, 0);
-                for (int i = 0; i < r_prev; ++i) {
+                for (int c = 0; c < CPG; ++c) acc[c] = mk<T>(0, 0);
+                int i = 0;
+                for (; i + 3 < r_prev; i += 4) {  // four loads in flight per thread
+                    const V q0 = Q[(long)i * L + row], q1 = Q[(long)(i + 1) * L + row];
+                    const V q2 = Q[(long)(i + 2) * L + row], q3 = Q[(long)(i + 3) * L + row];
+#pragma unroll
+                    for (int c = 0; c < CPG; ++c) {
+                        const V* cp = Cp + (size_t)i * BB + g * CPG + c;
+                        cfma(acc[c], q0, cp[0]);
+                        cfma(acc[c], q1, cp[BB]);
+                        cfma(acc[c], q2, cp[2 * BB]);
+                        cfma(acc[c], q3, cp[3 * BB]);
+                    }
+                }
+                for (; i < r_prev; ++i) {
                     const V q = Q[(long)i * L + row];
 #pragma unroll
-                    for (int j = 0; j < MAX_BLOCK; ++j)
-                        if (j < b) cfma(acc[j], q, Cp[(size_t)i * b + j]);
+                    for (int c = 0; c < CPG; ++c) cfma(acc[c], q, Cp[(size_t)i * BB + g * CPG + c]);
                 }
 #pragma unroll
-                for (int j = 0; j < MAX_BLOCK; ++j)
-                    if (j < b) Ys[(size_t)j * L + row] = csub(Ys[(size_t)j * L + row], acc[j]);
+                for (int c = 0; c < CPG; ++c) {
+                    V* y = Ys + (g * CPG + c) * L + row;
+                    *y = csub(*y, acc[c]);
+                }
             }
-            for (int e = tid; e < r_prev * b; e += blockDim.x) Cs[e] = pass ? cadd(Cs[e], Cp[e]) : Cp[e];
+            for (int e = tid; e < r_prev * BB; e += blockDim.x) Cs[e] = pass ? cadd(Cs[e], Cp[e]) : Cp[e];
             __syncthreads();
         }
     }
 
-    for (int j = 0; j < b; ++j) {
-        V* yj = Ys + (size_t)j * L;
-        if (j > 0) {
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int i = warp; i < j; i += nw) {
-                    V acc = mk<T>(0, 0);
-                    const V* yi = Ys + (size_t)i * L;
-                    for (int row = lane; row < L; row += 32) cfmac(acc, yi[row], yj[row]);
-                    acc.x = warp_sum(acc.x);
-                    acc.y = warp_sum(acc.y);
-                    if (lane == 0) cb[i] = acc;
+    // 2. shifted Cholesky-QR3 of the block
+    T y2p = 0;
+    for (int e = tid; e < L * BB; e += blockDim.x) y2p += cabs2(Ys[e]);
+    const double y2 = block_sum_t(y2p, red);
+    const double shift = 11.0 * ((double)L * b + (double)b * (b + 1)) * Eps<T>::v * y2;
+    for (int pass = 0; pass < 3; ++pass) {
+        // Gram matrix (upper triangle incl. diagonal)
+        for (int p = warp; p < BB * BB; p += NW) {
+            const int i = p / BB, j = p - i * BB;
+            if (i > j) continue;
+            V acc = mk<T>(0, 0);
+            for (int row = lane; row < L; row += 32) cfmac(acc, Ys[i * L + row], Ys[j * L + row]);
+            acc.x = warp_sum(acc.x);
+            acc.y = warp_sum(acc.y);
+            if (lane == 0) G[i * BB + j] = acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // upper Cholesky G = R^H R in registers: lane j holds column j.
+            // A zero pivot gives a zero row of R (a zero column stays zero).
+            const int j = lane;
+            V g[BB];
+#pragma unroll
+            for (int i = 0; i < BB; ++i) g[i] = (j < BB && i <= j) ? G[i * BB + j] : mk<T>(0, 0);
+            if (pass == 0 && j < BB) g[j].x += (T)shift;
+#pragma unroll
+            for (int k = 0; k < BB; ++k) {
+                const T d2 = __shfl_sync(0xffffffffu, g[k].x, k);
+                const T d = (k < b && d2 > (T)0) ? sqrt(d2) : (T)0;
+                V rkj = mk<T>(0, 0);
+                if (j < BB && j >= k && d > (T)0) rkj = (j == k) ? mk<T>(d, 0) : mk<T>(g[k].x / d, g[k].y / d);
+                if (j < BB) Rk[k * BB + j] = rkj;
+#pragma unroll
+                for (int i = k + 1; i < BB; ++i) {
+                    V rki;
+                    rki.x = __shfl_sync(0xffffffffu, rkj.x, i);
+                    rki.y = __shfl_sync(0xffffffffu, rkj.y, i);
+                    if (i <= j) g[i] = csub(g[i], cmul(cconj(rki), rkj));
                 }
-                __syncthreads();
-                for (int row = tid; row < L; row += blockDim.x) {
+            }
+            __syncwarp();
+            // Ra <- Rk * Ra (upper triangular), lane j -> column j
+            if (j < BB) {
+                V col[BB];
+#pragma unroll
+                for (int i = 0; i < BB; ++i) {
                     V acc = mk<T>(0, 0);
-                    for (int i = 0; i < j; ++i) cfma(acc, Ys[(size_t)i * L + row], cb[i]);
-                    yj[row] = csub(yj[row], acc);
+#pragma unroll
+                    for (int t = 0; t < BB; ++t)
+                        if (t >= i && t <= j) cfma(acc, Rk[i * BB + t], Ra[t * BB + j]);
+                    col[i] = (i <= j) ? acc : mk<T>(0, 0);
                 }
-                if (tid < j) Rb[tid * b + j] = cadd(Rb[tid * b + j], cb[tid]);
-                __syncthreads();
+                __syncwarp(BB == 32 ? 0xffffffffu : 0x0000ffffu);
+#pragma unroll
+                for (int i = 0; i < BB; ++i) Ra[i * BB + j] = col[i];
             }
         }
-        double p = 0.0;
-        for (int row = tid; row < L; row += blockDim.x) p += cabs2d(yj[row]);
-        p = block_sum(p, red);
-        if (tid == 0) bcast = p;
         __syncthreads();
-        const double nrm2 = bcast;
-        const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+        // Y <- Y R^{-1}: per row, forward substitution over the columns
         for (int row = tid; row < L; row += blockDim.x) {
-            const V v = yj[row];
-            yj[row] = mk<T>((T)((double)v.x * inv), (T)((double)v.y * inv));
+            V x[BB];
+#pragma unroll
+            for (int jj = 0; jj < BB; ++jj) {
+                V y = Ys[jj * L + row];
+#pragma unroll
+                for (int i = 0; i < jj; ++i) y = csub(y, cmul(x[i], Rk[i * BB + jj]));
+                const T d = Rk[jj * BB + jj].x;
+                x[jj] = d > (T)0 ? mk<T>(y.x / d, y.y / d) : mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int jj = 0; jj < BB; ++jj) Ys[jj * L + row] = x[jj];
         }
-        if (tid == 0) Rb[j * b + j] = mk<T>((T)sqrt(nrm2), 0);
         __syncthreads();
     }
 
     for (int e = tid; e < L * b; e += blockDim.x) {
         const int row = e / b, j = e - row * b;
-        Y[e] = Ys[(size_t)j * L + row];
+        Y[e] = Ys[j * L + row];
     }
     if (Qout) {
         V* Qo = Qout + (long)s * sQ + (long)r_prev * L;
@@ -153,15 +271,16 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
         for (int e = tid; e < r_rows * b; e += blockDim.x) {
             const int i = e / b, j = e - i * b;
             V v = mk<T>(0, 0);  // rows below this block stay zero: R is block upper triangular
-            if (i < r_prev) v = Cs[(size_t)i * b + j];
-            else if (i < r_prev + b) v = Rb[(i - r_prev) * b + j];
+            if (i < r_prev) v = Cs[(size_t)i * BB + j];
+            else if (i < r_prev + b) v = Ra[(i - r_prev) * BB + j];
             Rs[(long)i * ldr + r_prev + j] = v;
         }
     }
 }
 
 static size_t orth_smem(int L, int b, int r_prev, size_t c) {
-    return ((size_t)b * L + 2 * (size_t)r_prev * b + MAX_BLOCK + (size_t)b * b) * c;
+    const size_t BB = b <= 16 ? 16 : 32;
+    return ((size_t)BB * L + 2 * (size_t)r_prev * BB + 4 * BB * BB) * c;
 }
 
 template <typename T>
@@ -169,11 +288,11 @@ static tp_status orth(int h, cplx<T>* Y, long sY, int L, int b, const cplx<T>* Q
                       cplx<T>* Qout, cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip,
                       cudaStream_t st) {
     const size_t smem = orth_smem(L, b, r_prev, sizeof(cplx<T>));
-    if (smem > 48 * 1024)
-        if (cudaFuncSetAttribute(k_orth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return TP_ERR_CUDA;
+    auto kern = b <= 16 ? k_orth<T, 16> : k_orth<T, 32>;
+    const int nt = b <= 16 ? OrthThreads<T, 16>::v : OrthThreads<T, 32>::v;
+    if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
     prof_begin(TP_KC_ORTH, st);
-    k_orth<T><<<h, ORTH_THREADS, smem, st>>>(Y, sY, L, b, Qb, sQ, r_prev, Qout, R, ldr, sR, r_rows, normsq, skip);
+    kern<<<h, nt, smem, st>>>(Y, sY, L, b, Qb, sQ, r_prev, Qout, R, ldr, sR, r_rows, normsq, skip);
     return launched(TP_KC_ORTH, st);
 }
 
@@ -230,6 +349,8 @@ __global__ void __launch_bounds__(JAC_THREADS)
 k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, const cplx<T>* __restrict__ d, long sd,
          T* sigma, long ssig, cplx<T>* UR, long ldu, long sU, cplx<T>* dprime, long sdp, int max_sweeps,
          int* sweeps_out) {
+    // one half-warp (16 lanes) per column pair: a round of r/2 <= 64 disjoint
+    // pairs runs in one pass over the 64 half-warps of the CTA
     typedef cplx<T> V;
     const int r = st->r;
     if (r <= 0) return;
@@ -240,6 +361,7 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     int* perm = (int*)(sg + r);
     __shared__ int rot_count;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
     R += (long)s * sR;
     for (int e = tid; e < r * r; e += blockDim.x) {
         const int i = e / r, j = e - i * r;
@@ -255,45 +377,50 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
         if (tid == 0) rot_count = 0;
         __syncthreads();
         for (int t = 0; t < rr - 1; ++t) {
-            for (int kp = warp; kp < rr / 2; kp += nw) {
-                int p, q;
+            for (int base = 0; base < rr / 2; base += nslots) {
+                const int kp = base + slot;
+                int p = 0, q = 0;
                 if (kp == 0) {
                     p = 0;
                     q = 1 + t;
-                } else {
+                } else if (kp < rr / 2) {
                     p = 1 + (t + kp) % (rr - 1);
                     q = 1 + (t - kp + (rr - 1)) % (rr - 1);
                 }
                 if (p > q) { const int x = p; p = q; q = x; }
-                if (q >= r) continue;
+                const bool valid = kp < rr / 2 && q < r && p != q;
                 V* cp = Rs + (size_t)p * r;
                 V* cq = Rs + (size_t)q * r;
                 T a = 0, bq = 0;
                 V g = mk<T>(0, 0);
-                for (int i = lane; i < r; i += 32) {
-                    const V x = cp[i], y = cq[i];
-                    a += x.x * x.x + x.y * x.y;
-                    bq += y.x * y.x + y.y * y.y;
-                    cfmac(g, x, y);
+                if (valid)
+                    for (int i = hl; i < r; i += 16) {
+                        const V x = cp[i], y = cq[i];
+                        a += x.x * x.x + x.y * x.y;
+                        bq += y.x * y.x + y.y * y.y;
+                        cfmac(g, x, y);
+                    }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    bq += __shfl_xor_sync(0xffffffffu, bq, o);
+                    g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
+                    g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
                 }
-                a = warp_sum(a);
-                bq = warp_sum(bq);
-                g.x = warp_sum(g.x);
-                g.y = warp_sum(g.y);
                 const T ag = sqrt(g.x * g.x + g.y * g.y);
-                if (ag > (T)0 && ag > tol * sqrt(a) * sqrt(bq)) {
+                if (valid && ag > (T)0 && ag > tol * sqrt(a) * sqrt(bq)) {
                     const T zeta = (bq - a) / ((T)2 * ag);
                     const T tt = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
                     const T c = (T)1 / sqrt((T)1 + tt * tt), sn = c * tt;
                     const V e = mk<T>(g.x / ag, g.y / ag);
                     const V ec = cconj(e);
-                    for (int i = lane; i < r; i += 32) {
+                    for (int i = hl; i < r; i += 16) {
                         const V x = cp[i];
                         const V ey = cmul(ec, cq[i]);
                         cp[i] = mk<T>(c * x.x - sn * ey.x, c * x.y - sn * ey.y);
                         cq[i] = mk<T>(sn * x.x + c * ey.x, sn * x.y + c * ey.y);
                     }
-                    if (lane == 0) {
+                    if (hl == 0) {
                         const V x = dp[p];
                         const V ey = cmul(e, dp[q]);
                         dp[p] = mk<T>(c * x.x - sn * ey.x, c * x.y - sn * ey.y);
@@ -586,10 +713,7 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
                  r_max, nullptr, st));
     {
         const size_t smem = jacobi_smem(r_max, sizeof(cplx<T>));
-        if (smem > 48 * 1024)
-            if (cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-                return TP_ERR_CUDA;
+        if (smem_optin((const void*)k_jacobi<T>, smem) != TP_OK) return TP_ERR_CUDA;
         prof_begin(TP_KC_SVD, st);
         k_jacobi<T><<<h, JAC_THREADS, smem, st>>>(w.R, r_max, (long)r_max * r_max, w.st, w.d, r_max, w.sigma, r_max,
                                                     w.UR, r_max, (long)r_max * r_max, w.dprime, r_max, 60,
