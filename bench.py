@@ -133,8 +133,11 @@ def class_work(cfg, infos, esize=4):
     orth = 0.0
     for blk in range(nblk):
         rp = blk * b
-        per = 32.0 * l * rp * b + 16.0 * l * b * b             # two CGS passes vs basis + in-block CGS2
-        orth += h * per * (q + 1) + h * (16.0 * l * b * b) * q + h * (32.0 * m * rp * b + 16.0 * m * b * b)
+        # two CGS passes against the basis (32 flop per complex coefficient and update) for the q+1 sketch
+        # blocks and the projection block; in-block Cholesky QR at 8*L*b^2 flop per pass (Gram + solve), two
+        # passes for kept blocks, one for the q intermediate blocks on each side
+        orth += h * ((q + 1) * 32.0 * l * rp * b + (q * 8.0 + 16.0) * l * b * b)
+        orth += h * (q * 8.0 * m * b * b + 32.0 * m * rp * b + 16.0 * m * b * b)
     svd = h * rt.get("sweeps", 8) * (r * (r - 1) / 2) * 7 * r * 8.0
     return {"gemm": (gemm / 1e12, "TFLOP", "alu"), "dft": (dft_bytes / 1e9, "GB", "hbm"),
             "gkb": (gkbb / 1e9, "GB", "hbm"), "orth": (orth / 1e12, "TFLOP", "alu"),

@@ -77,7 +77,7 @@ __device__ __forceinline__ V warp_reduce_scatter(V (&v)[BB]) {
 template <typename T, int BB>
 __global__ void __launch_bounds__(OrthThreads<T, BB>::v)
 k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev, cplx<T>* Qout,
-       cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip) {
+       cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip, int final_pass) {
     typedef cplx<T> V;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -183,12 +183,24 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
         }
     }
 
-    // 2. shifted Cholesky-QR3 of the block
+    // 2. Cholesky QR of the block: CholQR2 when the first Gram matrix is well
+    //    conditioned, otherwise shifted CholQR3 (a shifted first pass, then two
+    //    plain passes).  G holds the Gram matrix, Rk this pass's R, Rt = Rk^-1,
+    //    Ra the accumulated in-block R (only when R is an output).
+    __shared__ int passes, need_shift;
+    __shared__ T invd[BB];
+    // Intermediate blocks (inside the power iteration) only need a
+    // well-conditioned basis of the right subspace: one Cholesky QR pass.
+    // Blocks that are kept (Q, QG, R) get two.
+    if (tid == 0) {
+        passes = final_pass ? 2 : 1;
+        need_shift = 0;
+    }
     T y2p = 0;
     for (int e = tid; e < L * BB; e += blockDim.x) y2p += cabs2(Ys[e]);
-    const double y2 = block_sum_t(y2p, red);
+    const double y2 = block_sum_t(y2p, red);  // its barriers also publish `passes`
     const double shift = 11.0 * ((double)L * b + (double)b * (b + 1)) * Eps<T>::v * y2;
-    for (int pass = 0; pass < 3; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
         // Gram matrix (upper triangle incl. diagonal)
         for (int p = warp; p < BB * BB; p += NW) {
             const int i = p / BB, j = p - i * BB;
@@ -201,47 +213,66 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
         }
         __syncthreads();
         if (warp == 0) {
-            // upper Cholesky G = R^H R in registers: lane j holds column j.
-            // A zero pivot gives a zero row of R (a zero column stays zero).
-            const int j = lane;
-            V g[BB];
-#pragma unroll
-            for (int i = 0; i < BB; ++i) g[i] = (j < BB && i <= j) ? G[i * BB + j] : mk<T>(0, 0);
-            if (pass == 0 && j < BB) g[j].x += (T)shift;
-#pragma unroll
-            for (int k = 0; k < BB; ++k) {
-                const T d2 = __shfl_sync(0xffffffffu, g[k].x, k);
-                const T d = (k < b && d2 > (T)0) ? sqrt(d2) : (T)0;
-                V rkj = mk<T>(0, 0);
-                if (j < BB && j >= k && d > (T)0) rkj = (j == k) ? mk<T>(d, 0) : mk<T>(g[k].x / d, g[k].y / d);
-                if (j < BB) Rk[k * BB + j] = rkj;
-#pragma unroll
-                for (int i = k + 1; i < BB; ++i) {
-                    V rki;
-                    rki.x = __shfl_sync(0xffffffffu, rkj.x, i);
-                    rki.y = __shfl_sync(0xffffffffu, rkj.y, i);
-                    if (i <= j) g[i] = csub(g[i], cmul(cconj(rki), rkj));
+            // Cholesky G (+ shift) = R^H R by the first warp: at step k the
+            // lanes form row k of R, then update the trailing Gram entries as
+            // independent (i, j) pairs.  A zero pivot gives a zero row (a zero
+            // column stays zero).  The first pass retries with the shift when a
+            // pivot falls below 100 u of the largest diagonal entry.
+            T dmax = 0;
+            for (int k = 0; k < BB; ++k) dmax = fmax(dmax, G[k * BB + k].x);
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                const bool shifted = attempt == 1;
+                if (shifted) {
+                    // restore the Gram matrix from its untouched copy in Rt, add the shift
+                    for (int e = lane; e < BB * BB; e += 32) G[e] = Rt[e];
+                    __syncwarp();
+                    if (lane < BB) G[lane * BB + lane].x += (T)shift;
+                } else {
+                    for (int e = lane; e < BB * BB; e += 32) Rt[e] = G[e];
+                }
+                __syncwarp();
+                bool bad = false;
+                for (int k = 0; k < BB; ++k) {
+                    const T d2 = G[k * BB + k].x;
+                    if (k < b && d2 < (T)(100.0 * Eps<T>::v) * dmax) bad = true;
+                    const T d = (k < b && d2 > (T)0) ? sqrt(d2) : (T)0;
+                    const T id = d > (T)0 ? (T)1 / d : (T)0;
+                    const int j = lane;
+                    if (j < BB) {
+                        V v = mk<T>(0, 0);
+                        if (j > k) v = cscale(G[k * BB + j], id);
+                        else if (j == k) v = mk<T>(d, 0);
+                        Rk[k * BB + j] = v;
+                    }
+                    if (lane == 0) invd[k] = id;
+                    __syncwarp();
+                    const int mrem = BB - k - 1;
+                    for (int pi = lane; pi < mrem * mrem; pi += 32) {
+                        const int i = k + 1 + pi / mrem, jj = k + 1 + pi % mrem;
+                        if (jj >= i) G[i * BB + jj] = csub(G[i * BB + jj], cmul(cconj(Rk[k * BB + i]), Rk[k * BB + jj]));
+                    }
+                    __syncwarp();
+                }
+                if (pass > 0 || shifted || !bad || y2 == 0.0) break;
+                if (lane == 0) {
+                    need_shift = 1;
+                    passes += 1;
                 }
             }
-            __syncwarp();
-            // Ra <- Rk * Ra (upper triangular), lane j -> column j
-            if (j < BB) {
-                V col[BB];
-#pragma unroll
-                for (int i = 0; i < BB; ++i) {
+            // Ra <- Rk * Ra when the in-block R is an output (entries spread over lanes)
+            if (R) {
+                for (int e = lane; e < BB * BB; e += 32) {
+                    const int i = e / BB, jj = e - i * BB;
                     V acc = mk<T>(0, 0);
-#pragma unroll
-                    for (int t = 0; t < BB; ++t)
-                        if (t >= i && t <= j) cfma(acc, Rk[i * BB + t], Ra[t * BB + j]);
-                    col[i] = (i <= j) ? acc : mk<T>(0, 0);
+                    for (int t = i; t <= jj; ++t) cfma(acc, Rk[i * BB + t], Ra[t * BB + jj]);
+                    Rt[e] = (i <= jj) ? acc : mk<T>(0, 0);
                 }
-                __syncwarp(BB == 32 ? 0xffffffffu : 0x0000ffffu);
-#pragma unroll
-                for (int i = 0; i < BB; ++i) Ra[i * BB + j] = col[i];
+                __syncwarp();
+                for (int e = lane; e < BB * BB; e += 32) Ra[e] = Rt[e];
             }
         }
         __syncthreads();
-        // Y <- Y R^{-1}: per row, forward substitution over the columns
+        // Y <- Y R^{-1}: per row, forward substitution (diagonal reciprocals precomputed)
         for (int row = tid; row < L; row += blockDim.x) {
             V x[BB];
 #pragma unroll
@@ -249,8 +280,7 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                 V y = Ys[jj * L + row];
 #pragma unroll
                 for (int i = 0; i < jj; ++i) y = csub(y, cmul(x[i], Rk[i * BB + jj]));
-                const T d = Rk[jj * BB + jj].x;
-                x[jj] = d > (T)0 ? mk<T>(y.x / d, y.y / d) : mk<T>(0, 0);
+                x[jj] = cscale(y, invd[jj]);
             }
 #pragma unroll
             for (int jj = 0; jj < BB; ++jj) Ys[jj * L + row] = x[jj];
@@ -287,12 +317,13 @@ template <typename T>
 static tp_status orth(int h, cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev,
                       cplx<T>* Qout, cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip,
                       cudaStream_t st) {
+    const int final_pass = (Qout != nullptr || R != nullptr) ? 1 : 0;
     const size_t smem = orth_smem(L, b, r_prev, sizeof(cplx<T>));
     auto kern = b <= 16 ? k_orth<T, 16> : k_orth<T, 32>;
     const int nt = b <= 16 ? OrthThreads<T, 16>::v : OrthThreads<T, 32>::v;
     if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
     prof_begin(TP_KC_ORTH, st);
-    kern<<<h, nt, smem, st>>>(Y, sY, L, b, Qb, sQ, r_prev, Qout, R, ldr, sR, r_rows, normsq, skip);
+    kern<<<h, nt, smem, st>>>(Y, sY, L, b, Qb, sQ, r_prev, Qout, R, ldr, sR, r_rows, normsq, skip, final_pass);
     return launched(TP_KC_ORTH, st);
 }
 
@@ -360,6 +391,7 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     double* sg = (double*)(dp + r);
     int* perm = (int*)(sg + r);
     __shared__ int rot_count;
+    __shared__ int max_off;  // bit pattern of the largest |g| / sqrt(a b) of a sweep (non-negative float)
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
     R += (long)s * sR;
@@ -373,8 +405,15 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     const int rr = r + (r & 1);
     const T tol = (T)(4.0 * sqrt((double)r) * Eps<T>::v);
     int sweep = 0;
+    // Convergence is quadratic once the columns are nearly orthogonal: a sweep
+    // whose largest relative off-diagonal is below sqrt(tol) leaves residues
+    // below tol, so the sweep after it (which would only confirm) is skipped.
+    const float stop_off = (float)sqrt((double)tol);
     for (; sweep < max_sweeps; ++sweep) {
-        if (tid == 0) rot_count = 0;
+        if (tid == 0) {
+            rot_count = 0;
+            max_off = 0;
+        }
         __syncthreads();
         for (int t = 0; t < rr - 1; ++t) {
             for (int base = 0; base < rr / 2; base += nslots) {
@@ -408,6 +447,10 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
                     g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
                 }
                 const T ag = sqrt(g.x * g.x + g.y * g.y);
+                if (valid && hl == 0 && a > (T)0 && bq > (T)0) {
+                    const float rel = (float)(ag / (sqrt(a) * sqrt(bq)));
+                    atomicMax(&max_off, __float_as_int(rel));
+                }
                 if (valid && ag > (T)0 && ag > tol * sqrt(a) * sqrt(bq)) {
                     const T zeta = (bq - a) / ((T)2 * ag);
                     const T tt = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
@@ -432,8 +475,13 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
             __syncthreads();
         }
         const int rc = rot_count;
+        const float mo = __int_as_float(max_off);
         __syncthreads();
         if (rc == 0) break;
+        if (mo < stop_off) {
+            ++sweep;  // count this sweep
+            break;
+        }
     }
     for (int j = warp; j < r; j += nw) {
         double a = 0.0;
