@@ -38,6 +38,29 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel class from the
+# ncu capture summarised in profiles/; reported only while the kernel source is the one that was captured.
+NCU_TRAFFIC = {
+    "gkb": {"bytes": 81.3e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
+            "sha256": "bda0ffc1bd562b6765d4e38d71361e66bc33dd782150b1b1085318b0839db6b2",
+            "profile": "profiles/k_gkb_n256.md"},
+}
+
+
+def ncu_traffic(cls):
+    import hashlib
+    rec = NCU_TRAFFIC.get(cls)
+    if not rec:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+                return None
+    except OSError:
+        return None
+    return rec["bytes"]
+
+
 def args_():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -252,8 +275,10 @@ def run_ours(a, rank, world, local):
         secs = dom_ms / 1e3 / a.steps  # device seconds of this class per step
         if bound == "hbm":
             ach = amount / secs
+            tr = ncu_traffic(dominant)
             roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": None, "kernel_class": dominant, "peak_source": src,
+                    "traffic": tr, "traffic_source": NCU_TRAFFIC[dominant]["profile"] if tr else None,
+                    "algorithmic_bytes_per_launch": amount * 1e9 * a.steps / dom_launches, "kernel_class": dominant, "peak_source": src,
                     "avg_launch_ms": dom_ms / dom_launches}
         else:
             ach = amount / secs
