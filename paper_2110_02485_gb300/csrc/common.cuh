@@ -87,6 +87,39 @@ __device__ __forceinline__ double block_sum_t(S v, double* red) {
     return red[32];
 }
 
+// Reduce-scatter of BB (a power of two <= 32) complex values over a warp:
+// returns the warp sum of entry lane / (32 / BB); the halving steps pick the
+// entry index from the high lane bits.
+template <typename V, int BB>
+__device__ __forceinline__ V warp_reduce_scatter(V (&v)[BB]) {
+    const int lane = threadIdx.x & 31;
+    int cnt = BB;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (cnt > 1) {
+            const bool hi = (lane & o) != 0;
+            const int half = cnt >> 1;
+#pragma unroll
+            for (int t = 0; t < BB / 2; ++t) {
+                if (t < half) {
+                    V keep = hi ? v[half + t] : v[t];
+                    V send = hi ? v[t] : v[half + t];
+                    send.x = __shfl_xor_sync(0xffffffffu, send.x, o);
+                    send.y = __shfl_xor_sync(0xffffffffu, send.y, o);
+                    v[t] = cadd(keep, send);
+                }
+            }
+            cnt = half;
+        } else {
+            V send = v[0];
+            send.x = __shfl_xor_sync(0xffffffffu, send.x, o);
+            send.y = __shfl_xor_sync(0xffffffffu, send.y, o);
+            v[0] = cadd(v[0], send);
+        }
+    }
+    return v[0];
+}
+
 template <typename V> __device__ __forceinline__ decltype(V().x) cabs2(V a) { return a.x * a.x + a.y * a.y; }
 
 template <typename T> struct Eps;

@@ -9,6 +9,10 @@
 // the DFT sum is evaluated directly from a table of the n roots of unity.
 // The forward kernel can also emit one float64 partial sum of squares per CTA
 // (used for ||A||_F^2).
+//
+// A thread always handles the same tube (DFT_THREADS is a multiple of
+// DFT_TILE), so its tube offset is computed once; squares are summed per
+// thread in the working precision and combined in float64 across the CTA.
 #include "common.cuh"
 #include "internal.h"
 
@@ -59,11 +63,14 @@ __device__ void fft16_inplace(cplx<T>* z, const cplx<T>* tw, int n) {
 }
 
 template <typename T>
-__device__ void store_partial(double v, double* sumsq) {
-    __shared__ double red[DFT_THREADS / 32];
-    double t = block_sum(v, red);
-    if (sumsq && threadIdx.x == 0) sumsq[blockIdx.x] = t;
+__device__ void store_partial(T v, double* sumsq) {
+    if (!sumsq) return;
+    __shared__ double red[33];
+    const double t = block_sum_t(v, red);
+    if (threadIdx.x == 0) sumsq[blockIdx.x] = t;
 }
+
+static_assert(DFT_THREADS % DFT_TILE == 0, "a thread must keep one tube");
 
 template <typename T>
 __global__ void __launch_bounds__(DFT_THREADS)
@@ -76,13 +83,14 @@ k_rdft_pow2(const T* __restrict__ X, cplx<T>* __restrict__ Xh, int n, int logn, 
     T* zf = (T*)z;
     const long t0 = (long)blockIdx.x * DFT_TILE;
     fill_roots<T>(tw, n / 2, n, (T)-1);
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
-        const int k = e >> 5, tt = e & 31;
-        const long t = t0 + tt;
-        T v = (T)0;
-        if (t < tubes) v = X[(long)k * ss + tube_off(t, cols, ld)];
-        acc += (double)v * (double)v;
+    const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
+    const bool live = t0 + tt < tubes;
+    const T* xt = X + (live ? tube_off(t0 + tt, cols, ld) : 0);
+    T acc = 0;
+#pragma unroll 8
+    for (int k = k0; k < n; k += kst) {
+        const T v = live ? xt[(long)k * ss] : (T)0;
+        acc = fma(v, v, acc);
         zf[((size_t)bitrev(k, logn) * 16 + (tt & 15)) * 2 + (tt >> 4)] = v;
     }
     __syncthreads();
@@ -113,14 +121,15 @@ k_rdft_direct(const T* __restrict__ X, cplx<T>* __restrict__ Xh, int n, long tub
     T* x = (T*)(tw + n);
     const long t0 = (long)blockIdx.x * DFT_TILE;
     fill_roots<T>(tw, n, n, (T)-1);
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
-        const int k = e >> 5, tt = e & 31;
-        const long t = t0 + tt;
-        T v = (T)0;
-        if (t < tubes) v = X[(long)k * ss + tube_off(t, cols, ld)];
-        acc += (double)v * (double)v;
-        x[e] = v;
+    const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
+    const bool live = t0 + tt < tubes;
+    const T* xt = X + (live ? tube_off(t0 + tt, cols, ld) : 0);
+    T acc = 0;
+#pragma unroll 4
+    for (int k = k0; k < n; k += kst) {
+        const T v = live ? xt[(long)k * ss] : (T)0;
+        acc = fma(v, v, acc);
+        x[k * DFT_TILE + tt] = v;
     }
     __syncthreads();
     const int h = n / 2 + 1;
@@ -166,12 +175,14 @@ k_irdft_pow2(const cplx<T>* __restrict__ Xh, T* __restrict__ X, int n, int logn,
     __syncthreads();
     fft16_inplace<T>(z, tw, n);
     const T inv = (T)1 / (T)n;
-    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
-        const int k = e >> 5, tt = e & 31;
-        const long t = t0 + tt;
-        if (t >= tubes) continue;
-        cplx<T> v = z[k * 16 + (tt & 15)];
-        X[(long)k * ss + tube_off(t, cols, ld)] = (tt < 16 ? v.x : v.y) * inv;
+    const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
+    if (t0 + tt < tubes) {
+        T* xt = X + tube_off(t0 + tt, cols, ld);
+#pragma unroll 8
+        for (int k = k0; k < n; k += kst) {
+            const cplx<T> v = z[k * 16 + (tt & 15)];
+            xt[(long)k * ss] = (tt < 16 ? v.x : v.y) * inv;
+        }
     }
 }
 
@@ -196,9 +207,10 @@ k_irdft_direct(const cplx<T>* __restrict__ Xh, T* __restrict__ X, int n, long tu
     }
     __syncthreads();
     const T inv = (T)1 / (T)n;
-    for (int e = threadIdx.x; e < n * DFT_TILE; e += blockDim.x) {
-        const int k = e >> 5, tt = e & 31;
-        const long t = t0 + tt;
+    const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
+    const bool live = t0 + tt < tubes;
+    T* xt = X + (live ? tube_off(t0 + tt, cols, ld) : 0);
+    for (int k = k0; k < n; k += kst) {
         T acc = xs[tt].x;  // slice 0
         int idx = k;
         for (int s = 1; s < h; ++s) {
@@ -208,7 +220,7 @@ k_irdft_direct(const cplx<T>* __restrict__ Xh, T* __restrict__ X, int n, long tu
             idx += k;
             if (idx >= n) idx -= n;
         }
-        if (t < tubes) X[(long)k * ss + tube_off(t, cols, ld)] = acc * inv;
+        if (live) xt[(long)k * ss] = acc * inv;
     }
 }
 

@@ -91,40 +91,63 @@ __device__ void mv_n(const cplx<T>* __restrict__ A, int l, int m, const cplx<T>*
     }
 }
 
-// Normalize (per slice): returns ||u|| and scales u to unit length (zero stays zero).
+// Normalize (per slice): scales u (length L, shared) to unit length and
+// returns ||u|| in the working precision; a zero vector stays zero (its norm,
+// 0, is the breakdown coefficient).  Squares are summed in the working
+// precision; one thread forms the norm and its reciprocal, so no other thread
+// executes float64 instructions (on GB300 one float64 instruction costs as
+// much issue time as 64 float32 ones).  Only when the reciprocal is not finite
+// for a positive sum (a sum too small for 1/sqrt in the working precision)
+// does the scaling go through float64.
+template <typename T> struct NormBc {
+    double invd;
+    T nrm, inv;
+    int mode;
+};
+
 template <typename T>
-__device__ double normalize_vec(cplx<T>* u, int L, double* red, double* bc) {
+__device__ T normalize_vec(cplx<T>* u, int L, double* red, NormBc<T>* nb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T p = 0;
     for (int e = threadIdx.x; e < L; e += blockDim.x) p += cabs2(u[e]);
-    // block sum in the working precision (one warp combines the warp partials)
     p = warp_sum(p);
     T* redt = (T*)red;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) redt[threadIdx.x >> 5] = p;
+    if (lane == 0) redt[warp] = p;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        T t = threadIdx.x < (blockDim.x >> 5) ? redt[threadIdx.x] : (T)0;
+    if (warp == 0) {
+        T t = lane < nw ? redt[lane] : (T)0;
         t = warp_sum(t);
-        if (threadIdx.x == 0) red[32] = (double)t;
+        if (lane == 0) {
+            const T inv = t > (T)0 ? (T)1 / sqrt(t) : (T)0;
+            nb->nrm = sqrt(t);
+            nb->inv = inv;
+            nb->mode = (t > (T)0 && !isfinite(inv)) ? 1 : 0;
+            if (nb->mode) nb->invd = 1.0 / sqrt((double)t);
+        }
     }
     __syncthreads();
-    const double nrm2 = red[32];  // every thread gets the sum
-    // 1/||u|| in the working precision (float64 divide/sqrt are slow here);
-    // float64 only when the float value would not be finite
-    const T n2t = (T)nrm2;
-    const T invt = n2t > (T)0 ? (T)1 / sqrt(n2t) : (T)0;
-    if (isfinite(invt) && (n2t > (T)0 || nrm2 == 0.0)) {
-        for (int e = threadIdx.x; e < L; e += blockDim.x) u[e] = cscale(u[e], invt);
+    const T nrm = nb->nrm;
+    if (nb->mode == 0) {
+        const T inv = nb->inv;
+        for (int e = threadIdx.x; e < L; e += blockDim.x) u[e] = cscale(u[e], inv);
     } else {
-        const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+        const double inv = nb->invd;
         for (int e = threadIdx.x; e < L; e += blockDim.x) {
             const cplx<T> v = u[e];
             u[e] = mk<T>((T)((double)v.x * inv), (T)((double)v.y * inv));
         }
     }
     __syncthreads();
-    return (double)sqrt(n2t > (T)0 ? n2t : (T)0) + (n2t > (T)0 ? 0.0 : sqrt(nrm2));
+    return nrm;
 }
+
+// sqrt(a^2 + b^2) for the Givens rotations: the arguments are norms of
+// working-precision vectors, so for float data the plain form cannot overflow
+// in float64; double data needs the scaled hypot.
+template <typename T> __device__ __forceinline__ double givens_norm(double a, double b);
+template <> __device__ __forceinline__ double givens_norm<float>(double a, double b) { return sqrt(fma(a, a, b * b)); }
+template <> __device__ __forceinline__ double givens_norm<double>(double a, double b) { return hypot(a, b); }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -196,57 +219,43 @@ __device__ void mv_h_vec(const cplx<T>* __restrict__ A, int l, int m, const cplx
     __syncthreads();
 }
 
-// u = A w - c * q   (one warp per row, four rows at a time, 4 vector columns per lane per pass)
+// u = A w - c * q.  A warp takes RB = 4 consecutive rows, each lane a set of
+// vector columns; the lanes accumulate partial sums of the four rows and one
+// reduce-scatter at the end gives lane j*8 the sum of row j.
 template <typename T>
 __device__ void mv_n_vec(const cplx<T>* __restrict__ A, int l, int m, const cplx<T>* w, const cplx<T>* q, T cq,
                          cplx<T>* u) {
     typedef cplx<T> V;
     typedef typename Vec16<T>::type LV;
-    constexpr int VW = Vec16<T>::VW, CH = 4, RW = 2;
+    constexpr int VW = Vec16<T>::VW, RB = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int mv = m / VW;
     const LV* Av = (const LV*)A;
-    for (int i = warp * RW; i < l; i += RW * nw) {
-        V sacc[RW];
+    for (int i0 = warp * RB; i0 < l; i0 += nw * RB) {
+        V acc[RB];
 #pragma unroll
-        for (int r = 0; r < RW; ++r) sacc[r] = mk<T>(0, 0);
-        for (int t0 = 0; t0 * 32 < mv; t0 += CH) {
-            LV a[RW][CH];
+        for (int r = 0; r < RB; ++r) acc[r] = mk<T>(0, 0);
+        for (int cv = lane; cv < mv; cv += 32) {
+            V wv[VW];
 #pragma unroll
-            for (int r = 0; r < RW; ++r)
+            for (int v = 0; v < VW; ++v) wv[v] = w[cv * VW + v];
+            LV a[RB];
 #pragma unroll
-                for (int tt = 0; tt < CH; ++tt) {
-                    const int cvv = lane + 32 * (t0 + tt);
-                    if (cvv < mv && i + r < l) a[r][tt] = __ldcg(Av + (long)(i + r) * mv + cvv);
-                }
+            for (int r = 0; r < RB; ++r)
+                if (i0 + r < l) a[r] = __ldcg(Av + (long)(i0 + r) * mv + cv);
 #pragma unroll
-            for (int tt = 0; tt < CH; ++tt) {
-                const int cvv = lane + 32 * (t0 + tt);
-                if (cvv < mv) {
-                    V wv[VW];
+            for (int r = 0; r < RB; ++r) {
+                if (i0 + r < l) {
+                    V e[VW];
+                    unpack<T>(a[r], e);
 #pragma unroll
-                    for (int v = 0; v < VW; ++v) wv[v] = w[cvv * VW + v];
-#pragma unroll
-                    for (int r = 0; r < RW; ++r) {
-                        if (i + r < l) {
-                            V e[VW];
-                            unpack<T>(a[r][tt], e);
-#pragma unroll
-                            for (int v = 0; v < VW; ++v) cfma(sacc[r], e[v], wv[v]);
-                        }
-                    }
+                    for (int v = 0; v < VW; ++v) cfma(acc[r], e[v], wv[v]);
                 }
             }
         }
-#pragma unroll
-        for (int r = 0; r < RW; ++r) {
-            sacc[r].x = warp_sum(sacc[r].x);
-            sacc[r].y = warp_sum(sacc[r].y);
-        }
-        if (lane == 0)
-#pragma unroll
-            for (int r = 0; r < RW; ++r)
-                if (i + r < l) u[i + r] = csub(sacc[r], cscale(q[i + r], cq));
+        const V sum = warp_reduce_scatter<V, RB>(acc);
+        const int i = i0 + (lane >> 3);
+        if ((lane & 7) == 0 && i < l) u[i] = csub(sum, cscale(q[i], cq));
     }
     __syncthreads();
 }
@@ -316,7 +325,7 @@ __device__ void reorth2(cplx<T>* u, const cplx<T>* sb, const cplx<T>* __restrict
 template <typename T, bool VEC, int NT>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2)
 k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l, int m, int n, int h, int k_max,
-      double tau_delta, cplx<T>* Wb, cplx<T>* Qb, double* cc, double* zz, double* res2, unsigned* counters,
+      double tau_delta, cplx<T>* Wb, cplx<T>* Qb, T* cc, T* zz, double* res2, unsigned* counters,
       cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info, int kc) {
     typedef cplx<T> V;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -331,20 +340,21 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
     V* Qc = Wc + (long)kc * m;  // kc cached vectors of Q (l each)
     __shared__ GkbShared S;
     __shared__ double red[33];
-    __shared__ double bc;
+    __shared__ NormBc<T> nb;
+    __shared__ T yt[GKB_KMAX];
     __shared__ int flag_done, flag_timeout;
     const int s = blockIdx.x, tid = threadIdx.x;
     const V* A = Ahat + (long)s * l * m;
     V* W = Wb + (long)s * k_max * m;
     V* Qv = Qb + (long)s * (k_max + 1) * l;
-    double* cs_ = cc + (long)s * k_max;
-    double* zs_ = zz + (long)s * (k_max + 1);
+    T* cs_ = cc + (long)s * k_max;
+    T* zs_ = zz + (long)s * (k_max + 1);
     const double ws = parseval_w(s, n);
 
     for (int e = tid; e < l; e += blockDim.x) u[e] = Bhat[(long)s * l + e];
     for (int e = tid; e < m; e += blockDim.x) w[e] = mk<T>(0, 0);
     __syncthreads();
-    const double z1 = normalize_vec<T>(u, l, red, &bc);
+    const T z1 = normalize_vec<T>(u, l, red, &nb);
     for (int e = tid; e < l; e += blockDim.x) {
         q[e] = u[e];
         Qv[e] = u[e];
@@ -359,20 +369,20 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
 
     // Givens state (thread 0): phibar, previous rotation, orphan residual
     double phibar = z1, cs_prev = 1.0, sn_prev = 0.0, orphan = 0.0;
-    double zprev = z1;
+    T zprev = z1;
     int k = k_max;
     for (int i = 1; i <= k_max; ++i) {
         // W_i = A^T * Q_i - W_{i-1} * z_i ; reorthogonalise ; Normalize -> c_i
         if (VEC) {
-            mv_h_vec<T>(A, l, m, q, w, (T)zprev, u, part);
+            mv_h_vec<T>(A, l, m, q, w, zprev, u, part);
         } else {
             mv_h<T>(A, l, m, q, u);
             __syncthreads();
-            for (int e = tid; e < m; e += blockDim.x) u[e] = csub(u[e], cscale(w[e], (T)zprev));
+            for (int e = tid; e < m; e += blockDim.x) u[e] = csub(u[e], cscale(w[e], zprev));
             __syncthreads();
         }
         reorth2<T>(u, Wc, W, kc, i - 1, m, cf, part);
-        const double ci = normalize_vec<T>(u, m, red, &bc);
+        const T ci = normalize_vec<T>(u, m, red, &nb);
         for (int e = tid; e < m; e += blockDim.x) {
             w[e] = u[e];
             W[(long)(i - 1) * m + e] = u[e];
@@ -381,15 +391,15 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
         __syncthreads();
         // Q_{i+1} = A * W_i - Q_i * c_i ; reorthogonalise ; Normalize -> z_{i+1}
         if (VEC) {
-            mv_n_vec<T>(A, l, m, w, q, (T)ci, u);
+            mv_n_vec<T>(A, l, m, w, q, ci, u);
         } else {
             mv_n<T>(A, l, m, w, u);
             __syncthreads();
-            for (int e = tid; e < l; e += blockDim.x) u[e] = csub(u[e], cscale(q[e], (T)ci));
+            for (int e = tid; e < l; e += blockDim.x) u[e] = csub(u[e], cscale(q[e], ci));
             __syncthreads();
         }
         reorth2<T>(u, Qc, Qv, kc, i, l, cf, part);
-        const double zi = normalize_vec<T>(u, l, red, &bc);
+        const T zi = normalize_vec<T>(u, l, red, &nb);
         for (int e = tid; e < l; e += blockDim.x) {
             q[e] = u[e];
             Qv[(long)i * l + e] = u[e];
@@ -400,13 +410,15 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
             zs_[i] = zi;
             // Givens QR of the lower-bidiagonal slice: column i has c_i on the
             // diagonal, z_{i+1} below it.
-            const double rhobar = (i == 1) ? ci : cs_prev * ci;
-            S.theta[i - 1] = (i == 1) ? 0.0 : sn_prev * ci;   // R(i-1, i)
-            const double rho = hypot(rhobar, zi);
+            const double cid = ci, zid = zi;
+            const double rhobar = (i == 1) ? cid : cs_prev * cid;
+            S.theta[i - 1] = (i == 1) ? 0.0 : sn_prev * cid;   // R(i-1, i)
+            const double rho = givens_norm<T>(rhobar, zid);
             double c = 1.0, sn = 0.0;
             if (rho > 0.0) {
-                c = rhobar / rho;
-                sn = zi / rho;
+                const double irho = 1.0 / rho;
+                c = rhobar * irho;
+                sn = zid * irho;
                 S.phi[i - 1] = c * phibar;
                 phibar = -sn * phibar;
             } else {  // zero column: its right-hand side entry stays unmatched
@@ -454,17 +466,19 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
             double v = S.phi[j];
             if (j + 1 < k) v -= S.theta[j + 1] * S.y[j + 1];
             S.y[j] = S.rho[j] > 0.0 ? v / S.rho[j] : 0.0;
+            yt[j] = (T)S.y[j];
         }
     }
     __syncthreads();
+    // X-hat = W y in the working precision
     for (int e = tid; e < m; e += blockDim.x) {
-        double xr = 0.0, xi = 0.0;
+        V x = mk<T>(0, 0);
         for (int j = 0; j < k; ++j) {
             const V v = W[(long)j * m + e];
-            xr += (double)v.x * S.y[j];
-            xi += (double)v.y * S.y[j];
+            x.x = fma(v.x, yt[j], x.x);
+            x.y = fma(v.y, yt[j], x.y);
         }
-        Xhat[(long)s * m + e] = mk<T>((T)xr, (T)xi);
+        Xhat[(long)s * m + e] = x;
     }
     if (s == 0 && tid == 0) {
         int status = flag_timeout ? TP_ERR_TIMEOUT : (flag_done ? TP_OK : TP_ERR_NOT_CONVERGED);
@@ -501,7 +515,7 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
 // data residual ||P y - z1 e1||^2 and optionally y.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ double damped_bidiag(const double* c, const double* z, int k, R lam, R* y, R* scr, int kcap, int stride) {
+__device__ R damped_bidiag(const R* c, const R* z, int k, R lam, R* y, R* scr, int kcap, int stride) {
     // scr: per-thread scratch of 4 arrays (rho, theta, phi, y) of kcap entries,
     // entry j of an array at scr[j * stride] (stride = threads sharing the
     // buffer, so that neighbouring threads touch neighbouring addresses).
@@ -514,12 +528,12 @@ __device__ double damped_bidiag(const double* c, const double* z, int k, R lam, 
     const long a = (long)kcap * stride;
     Strided rho{scr, stride}, theta{scr + a, stride}, phi{scr + 2 * a, stride};
     Strided yy = y ? Strided{y, 1} : Strided{scr + 3 * a, stride};
-    R rhobar = k > 0 ? (R)c[0] : (R)0, phibar = (R)z[0];
+    R rhobar = k > 0 ? c[0] : (R)0, phibar = z[0];
     for (int j = 0; j < k; ++j) {
         const R rh = hypot(rhobar, lam);          // eliminate the damping row
         const R c1 = rh > (R)0 ? rhobar / rh : (R)1;
         const R ph = c1 * phibar;
-        const R zj = (R)z[j + 1];
+        const R zj = z[j + 1];
         const R rj = hypot(rh, zj);               // eliminate z_{j+2}
         R cs = 1, sn = 0;
         if (rj > (R)0) {
@@ -530,8 +544,8 @@ __device__ double damped_bidiag(const double* c, const double* z, int k, R lam, 
         phi[j] = cs * ph;
         phibar = -sn * ph;
         if (j + 1 < k) {
-            theta[j + 1] = sn * (R)c[j + 1];
-            rhobar = cs * (R)c[j + 1];
+            theta[j + 1] = sn * c[j + 1];
+            rhobar = cs * c[j + 1];
         }
     }
     for (int j = k - 1; j >= 0; --j) {
@@ -540,11 +554,11 @@ __device__ double damped_bidiag(const double* c, const double* z, int k, R lam, 
         yy[j] = rho[j] > (R)0 ? v / rho[j] : (R)0;
     }
     // data residual: r_1 = c_1 y_1 - z_1, r_j = z_j y_{j-1} + c_j y_j, r_{k+1} = z_{k+1} y_k
-    double r2 = 0.0;
+    R r2 = 0;
     for (int j = 0; j <= k; ++j) {
-        double v = (j < k ? c[j] * (double)yy[j] : 0.0) + (j > 0 ? z[j] * (double)yy[j - 1] : 0.0);
+        R v = (j < k ? c[j] * yy[j] : (R)0) + (j > 0 ? z[j] * yy[j - 1] : (R)0);
         if (j == 0) v -= z[0];
-        r2 += v * v;
+        r2 = fma(v, v, r2);
     }
     return r2;
 }
@@ -552,101 +566,145 @@ __device__ double damped_bidiag(const double* c, const double* z, int k, R lam, 
 struct TikState {
     double lo, hi, t;
     int done, status, round;
+    unsigned arrived;
 };
 
 constexpr int TIK_P = 256;
+static_assert(TIK_P <= 256, "fill_lam forms p-th powers from eight squarings");
 
-// f at TIK_P points of the current bracket for every slice: out[p*h + s]
+// lam_p = 10^(-t_p / 2) at the TIK_P points t_p = lo + (hi - lo) p / (TIK_P - 1)
+// of the current bracket: 10^(-lo/2) times the p-th power of
+// 10^(-(hi - lo) / (2 (TIK_P - 1))), the power from the binary digits of p
+// (float64, then rounded to the working precision).  All TIK_P threads call it.
 template <typename R>
-__global__ void __launch_bounds__(TIK_P)
-k_tik_eval(const double* cc, const double* zz, int k_max, const State* st, const TikState* ts, int h, int n,
-           double* out, R* scratch) {
-    if (ts->done) return;
-    const int s = blockIdx.x, p = threadIdx.x, k = st->k;
-    double t;
-    if (p == 0) t = ts->lo;
-    else if (p == TIK_P - 1) t = ts->hi;
-    else t = ts->lo + (ts->hi - ts->lo) * (double)p / (double)(TIK_P - 1);
-    const R lam = (R)sqrt(pow(10.0, -t));
-    R* scr = scratch + (long)s * TIK_P * 4 * k_max + p;
-    const double r2 = damped_bidiag<R>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, nullptr, scr, k_max,
-                                       TIK_P);
-    out[(long)p * h + s] = parseval_w(s, n) * r2;
+__device__ void fill_lam(const TikState* ts, R* lam) {
+    __shared__ double pw[9];
+    if (threadIdx.x == 0) {
+        pw[8] = pow(10.0, -0.5 * ts->lo);
+        double b = pow(10.0, -0.5 * (ts->hi - ts->lo) / (double)(TIK_P - 1));
+        for (int i = 0; i < 8; ++i) {
+            pw[i] = b;
+            b *= b;
+        }
+    }
+    __syncthreads();
+    const int p = threadIdx.x;
+    double v = pw[8];
+    for (int i = 0; i < 8; ++i)
+        if ((p >> i) & 1) v *= pw[i];
+    lam[p] = (R)v;
 }
 
-__global__ void __launch_bounds__(TIK_P)
-k_tik_select(const double* out, int h, int n, double tau_delta, double log_tol, TikState* ts) {
-    if (ts->done) return;
-    __shared__ double f[TIK_P];
+// New bracket from the residuals at the TIK_P points (one CTA of TIK_P
+// threads): the first point whose residual is at most tau*delta closes it.
+// The slice sum runs in a fixed order with Kahan compensation in the working
+// precision; "above" means sum/n > (tau delta)^2, i.e. residual > tau*delta.
+template <typename R>
+__device__ void tik_select(const R* out, int h, R thr, double log_tol, TikState* ts, R* lamv) {
+    __shared__ unsigned char above[TIK_P];
     const int p = threadIdx.x;
-    double a = 0.0;
-    for (int s = 0; s < h; ++s) a += out[(long)p * h + s];
-    f[p] = sqrt(a / (double)n) - tau_delta;
+    R a = 0, comp = 0;
+    for (int s = 0; s < h; ++s) {
+        const R y = __ldcg(&out[(long)s * TIK_P + p]) - comp;
+        const R t = a + y;
+        comp = (t - a) - y;
+        a = t;
+    }
+    above[p] = a > thr ? 1 : 0;
     __syncthreads();
-    if (p != 0) return;
-    const double lo = ts->lo, hi = ts->hi;
-    if (ts->round == 0) {
-        if (f[TIK_P - 1] > 0.0) {  // even mu_hi leaves the residual above tau*delta
-            ts->t = hi;
-            ts->status = TP_ERR_NOT_CONVERGED;
-            ts->done = 1;
-            return;
+    if (p == 0) {
+        const double lo = ts->lo, hi = ts->hi;
+        bool fin = false;
+        if (ts->round == 0) {
+            if (above[TIK_P - 1]) {  // even mu_hi leaves the residual above tau*delta
+                ts->t = hi;
+                ts->status = TP_ERR_NOT_CONVERGED;
+                fin = true;
+            } else if (!above[0]) {
+                ts->t = lo;
+                fin = true;
+            }
         }
-        if (f[0] <= 0.0) {
-            ts->t = lo;
-            ts->done = 1;
-            return;
+        if (!fin) {
+            int ps = TIK_P - 1;
+            for (int i = 1; i < TIK_P; ++i)
+                if (!above[i]) {
+                    ps = i;
+                    break;
+                }
+            auto pt = [&](int i) {
+                return i == 0 ? lo : (i == TIK_P - 1 ? hi : lo + (hi - lo) * (double)i / (double)(TIK_P - 1));
+            };
+            ts->lo = pt(ps - 1);
+            ts->hi = pt(ps);
+            ts->round += 1;
+            if (ts->hi - ts->lo <= log_tol) {
+                ts->t = ts->hi;
+                fin = true;
+            }
         }
+        ts->done = fin ? 1 : 0;
+        ts->arrived = 0;
     }
-    int ps = TIK_P - 1;
-    for (int i = 1; i < TIK_P; ++i)
-        if (f[i] <= 0.0) {
-            ps = i;
-            break;
-        }
-    auto pt = [&](int i) {
-        return i == 0 ? lo : (i == TIK_P - 1 ? hi : lo + (hi - lo) * (double)i / (double)(TIK_P - 1));
-    };
-    ts->lo = pt(ps - 1);
-    ts->hi = pt(ps);
-    ts->round += 1;
-    if (ts->hi - ts->lo <= log_tol) {
-        ts->t = ts->hi;
-        ts->done = 1;
-    }
+    __syncthreads();
+    if (!ts->done) fill_lam<R>(ts, lamv);
+}
+
+// One multisection round: the data residual at the TIK_P points of the
+// bracket for every slice (out[s*TIK_P + p]); the last CTA to finish selects
+// the next bracket.
+template <typename R>
+__global__ void __launch_bounds__(TIK_P)
+k_tik_round(const R* cc, const R* zz, int k_max, const State* st, TikState* ts, R* lamv, int h, int n, R* out,
+            R* scratch, R thr, double log_tol) {
+    if (ts->done) return;
+    __shared__ int last;
+    const int s = blockIdx.x, p = threadIdx.x, k = st->k;
+    const R lam = lamv[p];
+    R* scr = scratch + (long)s * TIK_P * 4 * k_max + p;
+    const R r2 = damped_bidiag<R>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, nullptr, scr, k_max,
+                                  TIK_P);
+    out[(long)s * TIK_P + p] = ((s == 0 || 2 * s == n) ? (R)1 : (R)2) * r2;
+    __threadfence();
+    __syncthreads();
+    if (p == 0) last = atomicAdd(&ts->arrived, 1u) == (unsigned)(h - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    tik_select<R>(out, h, thr, log_tol, ts, lamv);
 }
 
 // final: y_mu per slice, Xhat = W y, residual; info
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_tik_final(const double* cc, const double* zz, int k_max, const cplx<T>* Wb, int m, const State* st,
-            const TikState* ts, int n, double* out, cplx<T>* Xhat, T* scratch) {
+k_tik_final(const T* cc, const T* zz, int k_max, const cplx<T>* Wb, int m, const State* st,
+            const TikState* ts, int n, double* fout, cplx<T>* Xhat, T* scratch) {
     __shared__ T y[GKB_KMAX];
     const int s = blockIdx.x, k = st->k;
-    const double mu = pow(10.0, ts->t);
     if (threadIdx.x == 0) {
-        const double r2 = damped_bidiag<T>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, (T)sqrt(1.0 / mu), y,
-                                           scratch + (long)s * TIK_P * 4 * k_max, k_max, 1);
-        out[s] = parseval_w(s, n) * r2;
+        const T lam = (T)pow(10.0, -0.5 * ts->t);
+        const T r2 = damped_bidiag<T>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, y,
+                                      scratch + (long)s * TIK_P * 4 * k_max, k_max, 1);
+        fout[s] = parseval_w(s, n) * (double)r2;
     }
     __syncthreads();
     const cplx<T>* W = Wb + (long)s * k_max * m;
     for (int e = threadIdx.x; e < m; e += blockDim.x) {
-        double xr = 0.0, xi = 0.0;
+        cplx<T> x = mk<T>(0, 0);
         for (int j = 0; j < k; ++j) {
             const cplx<T> v = W[(long)j * m + e];
-            xr += (double)v.x * (double)y[j];
-            xi += (double)v.y * (double)y[j];
+            x.x = fma(v.x, y[j], x.x);
+            x.y = fma(v.y, y[j], x.y);
         }
-        Xhat[(long)s * m + e] = mk<T>((T)xr, (T)xi);
+        Xhat[(long)s * m + e] = x;
     }
 }
 
-__global__ void k_tik_info(const double* out, int h, int n, const State* st, const TikState* ts, double tau_delta,
+__global__ void k_tik_info(const double* fout, int h, int n, const State* st, const TikState* ts, double tau_delta,
                            tp_info* info) {
     if (threadIdx.x != 0) return;
     double a = 0.0;
-    for (int s = 0; s < h; ++s) a += out[s];
+    for (int s = 0; s < h; ++s) a += fout[s];
     tp_info o;
     o.status = st->status == TP_ERR_TIMEOUT ? TP_ERR_TIMEOUT : ts->status;
     o.k = st->k;
@@ -661,13 +719,19 @@ __global__ void k_tik_info(const double* out, int h, int n, const State* st, con
     *info = o;
 }
 
-__global__ void k_tik_init(TikState* ts, double lo, double hi) {
-    ts->lo = lo;
-    ts->hi = hi;
-    ts->t = hi;
-    ts->done = 0;
-    ts->status = TP_OK;
-    ts->round = 0;
+template <typename R>
+__global__ void __launch_bounds__(TIK_P) k_tik_init(TikState* ts, R* lamv, double lo, double hi) {
+    if (threadIdx.x == 0) {
+        ts->lo = lo;
+        ts->hi = hi;
+        ts->t = hi;
+        ts->done = 0;
+        ts->status = TP_OK;
+        ts->round = 0;
+        ts->arrived = 0;
+    }
+    __syncthreads();
+    fill_lam<R>(ts, lamv);
 }
 
 // ---------------------------------------------------------------------------
@@ -676,8 +740,8 @@ struct GkWs {
     State* st;
     TikState* ts;
     unsigned* counters;
-    double *res2, *cc, *zz, *tout;
-    T* tscr;
+    double *res2, *fout;
+    T *cc, *zz, *tout, *lam, *tscr;
     cplx<T> *Ahat, *Bhat, *W, *Q, *Xhat;
     size_t bytes;
 };
@@ -692,9 +756,11 @@ static GkWs<T> gk_carve(void* base, int l, int m, int n, int k_max) {
     w.ts = c.take<TikState>(1);
     w.counters = c.take<unsigned>(k_max + 1);
     w.res2 = c.take<double>((long)(k_max + 1) * h);
-    w.cc = c.take<double>(h * k_max);
-    w.zz = c.take<double>(h * (k_max + 1));
-    w.tout = c.take<double>((long)TIK_P * h);
+    w.fout = c.take<double>(h);
+    w.cc = c.take<T>(h * k_max);
+    w.zz = c.take<T>(h * (k_max + 1));
+    w.tout = c.take<T>((long)TIK_P * h);
+    w.lam = c.take<T>(TIK_P);
     w.tscr = c.take<T>((long)TIK_P * h * 4 * k_max);
     w.Ahat = c.take<V>(h * l * m);
     w.Bhat = c.take<V>(h * l);
@@ -811,24 +877,22 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     const double lo = log10(P->mu_lo), hi = log10(P->mu_hi);
     const double tol = P->log_tol > 0.0 ? P->log_tol : 1e-12;
     const double td = P->gkb.tau * P->gkb.delta;
+    const T thr = (T)((double)n * td * td);
     prof_begin(TP_KC_TIK, st);
-    k_tik_init<<<1, 1, 0, st>>>(w.ts, lo, hi);
+    k_tik_init<T><<<1, TIK_P, 0, st>>>(w.ts, w.lam, lo, hi);
     TRY(launched(TP_KC_TIK, st));
     int rounds = 1;
     for (double width = hi - lo; width > tol && rounds < 40; width /= (TIK_P - 1)) ++rounds;
     for (int it = 0; it < rounds; ++it) {
         prof_begin(TP_KC_TIK, st);
-        k_tik_eval<T><<<h, TIK_P, 0, st>>>(w.cc, w.zz, k_max, w.st, w.ts, h, n, w.tout, w.tscr);
-        TRY(launched(TP_KC_TIK, st));
-        prof_begin(TP_KC_TIK, st);
-        k_tik_select<<<1, TIK_P, 0, st>>>(w.tout, h, n, td, tol, w.ts);
+        k_tik_round<T><<<h, TIK_P, 0, st>>>(w.cc, w.zz, k_max, w.st, w.ts, w.lam, h, n, w.tout, w.tscr, thr, tol);
         TRY(launched(TP_KC_TIK, st));
     }
     prof_begin(TP_KC_TIK, st);
-    k_tik_final<T><<<h, 256, 0, st>>>(w.cc, w.zz, k_max, w.W, m, w.st, w.ts, n, w.tout, w.Xhat, w.tscr);
+    k_tik_final<T><<<h, 256, 0, st>>>(w.cc, w.zz, k_max, w.W, m, w.st, w.ts, n, w.fout, w.Xhat, w.tscr);
     TRY(launched(TP_KC_TIK, st));
     prof_begin(TP_KC_TIK, st);
-    k_tik_info<<<1, 32, 0, st>>>(w.tout, h, n, w.st, w.ts, td, info);
+    k_tik_info<<<1, 32, 0, st>>>(w.fout, h, n, w.st, w.ts, td, info);
     TRY(launched(TP_KC_TIK, st));
     TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));
     return TP_OK;

@@ -42,38 +42,6 @@ template <typename T, int BB> struct OrthThreads {
     static constexpr int v = (sizeof(T) == 8 && BB == 32) ? 256 : 512;
 };
 
-// Reduce-scatter of BB complex values over a warp: returns the warp sum of
-// column (BB == 32 ? lane : lane >> 1).
-template <typename V, int BB>
-__device__ __forceinline__ V warp_reduce_scatter(V (&v)[BB]) {
-    const int lane = threadIdx.x & 31;
-    int cnt = BB;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        if (cnt > 1) {
-            const bool hi = (lane & o) != 0;
-            const int half = cnt >> 1;
-#pragma unroll
-            for (int t = 0; t < BB / 2; ++t) {
-                if (t < half) {
-                    V keep = hi ? v[half + t] : v[t];
-                    V send = hi ? v[t] : v[half + t];
-                    send.x = __shfl_xor_sync(0xffffffffu, send.x, o);
-                    send.y = __shfl_xor_sync(0xffffffffu, send.y, o);
-                    v[t] = cadd(keep, send);
-                }
-            }
-            cnt = half;
-        } else {
-            V send = v[0];
-            send.x = __shfl_xor_sync(0xffffffffu, send.x, o);
-            send.y = __shfl_xor_sync(0xffffffffu, send.y, o);
-            v[0] = cadd(v[0], send);
-        }
-    }
-    return v[0];
-}
-
 template <typename T, int BB>
 __global__ void __launch_bounds__(OrthThreads<T, BB>::v)
 k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev, cplx<T>* Qout,
@@ -371,44 +339,50 @@ __global__ void k_eta_update(State* st, const double* normsq, int h, int n, int 
 
 // ---------------------------------------------------------------------------
 // One-sided Jacobi SVD of R (r x r) per slice, rotations from the right
-// (cyclic round-robin ordering, r/2 disjoint pairs per round, one warp per
-// pair).  Tracks d' = J^H d.  Outputs, sorted by decreasing sigma:
+// (cyclic round-robin ordering, r/2 disjoint pairs per round, one half-warp
+// per pair).  Tracks d' = J^H d.  Outputs, sorted by decreasing sigma:
 // sigma (r), U_R (r x r row-major, columns normalised), d'.
+//
+// A pair (p, q) with Gram entries a = |x|^2, b = |y|^2, g = x^H y is rotated
+// when |g| > tol sqrt(a b) (tol = 4 sqrt(r) u): with e = g/|g|,
+// zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// c = 1/sqrt(1 + t^2), s = c t, the columns become x' = c x - s conj(e) y and
+// y' = s x + c conj(e) y, which makes them orthogonal.
+// Convergence is quadratic once the columns are nearly orthogonal: a sweep
+// whose largest relative off-diagonal |g|/sqrt(a b) is below sqrt(tol) leaves
+// residues below tol, so the sweep after it (which would only confirm) is
+// skipped.
 // ---------------------------------------------------------------------------
+
+// Pair (p, q) of slot kp in round t of the round-robin ordering of rr (even)
+// columns; valid only when q < r.
+__device__ __forceinline__ bool rr_pair(int t, int kp, int rr, int r, int& p, int& q) {
+    p = 0;
+    q = 0;
+    if (kp == 0) {
+        q = 1 + t;
+    } else if (kp < rr / 2) {
+        p = 1 + (t + kp) % (rr - 1);
+        q = 1 + (t - kp + (rr - 1)) % (rr - 1);
+    }
+    if (p > q) {
+        const int x = p;
+        p = q;
+        q = x;
+    }
+    return kp < rr / 2 && q < r && p != q;
+}
+
+// Sweeps in shared memory with IEEE arithmetic (any precision).
 template <typename T>
-__global__ void __launch_bounds__(JAC_THREADS)
-k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, const cplx<T>* __restrict__ d, long sd,
-         T* sigma, long ssig, cplx<T>* UR, long ldu, long sU, cplx<T>* dprime, long sdp, int max_sweeps,
-         int* sweeps_out) {
-    // one half-warp (16 lanes) per column pair: a round of r/2 <= 64 disjoint
-    // pairs runs in one pass over the 64 half-warps of the CTA
+__device__ int jacobi_sweeps_smem(cplx<T>* Rs, cplx<T>* dp, int r, int max_sweeps, T tol) {
     typedef cplx<T> V;
-    const int r = st->r;
-    if (r <= 0) return;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* Rs = (V*)smraw;                       // column j at Rs[j*r]
-    V* dp = Rs + (size_t)r * r;
-    double* sg = (double*)(dp + r);
-    int* perm = (int*)(sg + r);
     __shared__ int rot_count;
     __shared__ int max_off;  // bit pattern of the largest |g| / sqrt(a b) of a sweep (non-negative float)
-    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
-    R += (long)s * sR;
-    for (int e = tid; e < r * r; e += blockDim.x) {
-        const int i = e / r, j = e - i * r;
-        Rs[(size_t)j * r + i] = R[(long)i * ldr + j];
-    }
-    for (int i = tid; i < r; i += blockDim.x) dp[i] = d[(long)s * sd + i];
-    __syncthreads();
-
+    const int tid = threadIdx.x, hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
     const int rr = r + (r & 1);
-    const T tol = (T)(4.0 * sqrt((double)r) * Eps<T>::v);
-    int sweep = 0;
-    // Convergence is quadratic once the columns are nearly orthogonal: a sweep
-    // whose largest relative off-diagonal is below sqrt(tol) leaves residues
-    // below tol, so the sweep after it (which would only confirm) is skipped.
     const float stop_off = (float)sqrt((double)tol);
+    int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (tid == 0) {
             rot_count = 0;
@@ -417,17 +391,8 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
         __syncthreads();
         for (int t = 0; t < rr - 1; ++t) {
             for (int base = 0; base < rr / 2; base += nslots) {
-                const int kp = base + slot;
-                int p = 0, q = 0;
-                if (kp == 0) {
-                    p = 0;
-                    q = 1 + t;
-                } else if (kp < rr / 2) {
-                    p = 1 + (t + kp) % (rr - 1);
-                    q = 1 + (t - kp + (rr - 1)) % (rr - 1);
-                }
-                if (p > q) { const int x = p; p = q; q = x; }
-                const bool valid = kp < rr / 2 && q < r && p != q;
+                int p, q;
+                const bool valid = rr_pair(t, base + slot, rr, r, p, q);
                 V* cp = Rs + (size_t)p * r;
                 V* cq = Rs + (size_t)q * r;
                 T a = 0, bq = 0;
@@ -477,12 +442,142 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
         const int rc = rot_count;
         const float mo = __int_as_float(max_off);
         __syncthreads();
-        if (rc == 0) break;
-        if (mo < stop_off) {
-            ++sweep;  // count this sweep
-            break;
-        }
+        if (rc == 0 || mo < stop_off) return sweep + 1;
     }
+    return sweep;  // sweeps executed
+}
+
+// 1/sqrt(x) for normal positive x: one Newton-Raphson step on the hardware
+// approximation, y <- y (3 - x y^2) / 2, which brings it to about one ulp.
+__device__ __forceinline__ float rsqrt_nr(float x) {
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
+
+// Float32 sweeps with the two columns of a pair held in registers (r <= 16
+// EPL): the Gram entries and the rotation read and write shared memory once
+// per element, the rotation parameters come from Newton-refined reciprocal
+// square roots (c^2 + s^2 = 1 to about an ulp), and the per-round "any
+// rotation" flag rides on the round's barrier.
+template <int EPL>
+__device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int r, int max_sweeps, float tol) {
+    __shared__ int max_off2;  // bit pattern of the largest (|g|^2 / (a b)) of a sweep
+    const int tid = threadIdx.x, lane = tid & 31, hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
+    const int rr = r + (r & 1);
+    const float tol2 = tol * tol;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) max_off2 = 0;
+        int any = 0;
+        float mo2 = 0.f;
+        for (int t = 0; t < rr - 1; ++t) {
+            for (int base = 0; base < rr / 2; base += nslots) {
+                int p, q;
+                const bool valid = rr_pair(t, base + slot, rr, r, p, q);
+                float2* cp = Rs + (size_t)p * r;
+                float2* cq = Rs + (size_t)q * r;
+                float2 x[EPL], y[EPL];
+                float a = 0.f, b = 0.f;
+                float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    const int i = hl + 16 * e;
+                    if (valid && i < r) {
+                        x[e] = cp[i];
+                        y[e] = cq[i];
+                    } else {
+                        x[e] = y[e] = make_float2(0.f, 0.f);
+                    }
+                    a = fmaf(x[e].x, x[e].x, fmaf(x[e].y, x[e].y, a));
+                    b = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, b));
+                    cfmac(g, x[e], y[e]);
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
+                    g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
+                }
+                const float ag2 = fmaf(g.x, g.x, g.y * g.y), ab = a * b;
+                if (valid && ab > 0.f) mo2 = fmaxf(mo2, __fdividef(ag2, ab));
+                const bool rot = valid && a > 0.f && b > 0.f && ag2 >= 1.17549435e-38f && ag2 > tol2 * ab;
+                if (rot) {
+                    const float rg = rsqrt_nr(ag2);  // 1/|g|
+                    const float2 ec = make_float2(g.x * rg, -g.y * rg);
+                    const float zeta = (b - a) * 0.5f * rg;
+                    const float tt = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                    const float c = rsqrt_nr(fmaf(tt, tt, 1.f)), sn = c * tt;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        const int i = hl + 16 * e;
+                        if (i < r) {
+                            const float2 ey = cmul(ec, y[e]);
+                            cp[i] = make_float2(c * x[e].x - sn * ey.x, c * x[e].y - sn * ey.y);
+                            cq[i] = make_float2(sn * x[e].x + c * ey.x, sn * x[e].y + c * ey.y);
+                        }
+                    }
+                    if (hl == 0) {
+                        const float2 xv = dp[p];
+                        const float2 ey = cmul(cconj(ec), dp[q]);
+                        dp[p] = make_float2(c * xv.x - sn * ey.x, c * xv.y - sn * ey.y);
+                        dp[q] = make_float2(sn * xv.x + c * ey.x, sn * xv.y + c * ey.y);
+                    }
+                }
+                any |= rot ? 1 : 0;
+            }
+            any = __syncthreads_or(any);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mo2 = fmaxf(mo2, __shfl_xor_sync(0xffffffffu, mo2, o));
+        if (lane == 0) atomicMax(&max_off2, __float_as_int(mo2));
+        __syncthreads();
+        const float mo = __int_as_float(max_off2);
+        __syncthreads();
+        // no rotation, or the largest relative off-diagonal below sqrt(tol)
+        if (!any || mo < tol) return sweep + 1;
+    }
+    return sweep;  // sweeps executed
+}
+
+template <typename T> struct JacobiSweeps {
+    static __device__ int run(cplx<T>* Rs, cplx<T>* dp, int r, int max_sweeps, T tol) {
+        return jacobi_sweeps_smem<T>(Rs, dp, r, max_sweeps, tol);
+    }
+};
+template <> struct JacobiSweeps<float> {
+    static __device__ int run(float2* Rs, float2* dp, int r, int max_sweeps, float tol) {
+        if (r <= 64) return jacobi_sweeps_reg<4>(Rs, dp, r, max_sweeps, tol);
+        if (r <= 96) return jacobi_sweeps_reg<6>(Rs, dp, r, max_sweeps, tol);
+        if (r <= 128) return jacobi_sweeps_reg<8>(Rs, dp, r, max_sweeps, tol);
+        return jacobi_sweeps_smem<float>(Rs, dp, r, max_sweeps, tol);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(JAC_THREADS)
+k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, const cplx<T>* __restrict__ d, long sd,
+         T* sigma, long ssig, cplx<T>* UR, long ldu, long sU, cplx<T>* dprime, long sdp, int max_sweeps,
+         int* sweeps_out) {
+    typedef cplx<T> V;
+    const int r = st->r;
+    if (r <= 0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* Rs = (V*)smraw;                       // column j at Rs[j*r]
+    V* dp = Rs + (size_t)r * r;
+    double* sg = (double*)(dp + r);
+    int* perm = (int*)(sg + r);
+    __shared__ T tol_s;
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    R += (long)s * sR;
+    for (int e = tid; e < r * r; e += blockDim.x) {
+        const int i = e / r, j = e - i * r;
+        Rs[(size_t)j * r + i] = R[(long)i * ldr + j];
+    }
+    for (int i = tid; i < r; i += blockDim.x) dp[i] = d[(long)s * sd + i];
+    if (tid == 0) tol_s = (T)(4.0 * sqrt((double)r) * Eps<T>::v);
+    __syncthreads();
+    const int sweep = JacobiSweeps<T>::run(Rs, dp, r, max_sweeps, tol_s);
     for (int j = warp; j < r; j += nw) {
         double a = 0.0;
         for (int i = lane; i < r; i += 32) a += cabs2d(Rs[(size_t)j * r + i]);
@@ -510,7 +605,7 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
         const V x = Rs[(size_t)j * r + i];
         U[(long)i * ldu + jr] = sv > 0.0 ? mk<T>((T)(x.x / sv), (T)(x.y / sv)) : mk<T>(0, 0);
     }
-    if (tid == 0) atomicMax(sweeps_out, sweep + (sweep < max_sweeps ? 1 : 0));
+    if (tid == 0) atomicMax(sweeps_out, sweep);
 }
 
 static size_t jacobi_smem(int r, size_t c) {
