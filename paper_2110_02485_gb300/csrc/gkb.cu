@@ -19,7 +19,6 @@
 
 namespace tp {
 
-constexpr int GKB_THREADS = 512;
 constexpr int GKB_KMAX = 512;
 
 struct GkbShared {

@@ -708,6 +708,7 @@ __global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st,
             break;
         }
     if (st->eta >= st->eps2) status = TP_ERR_NOT_CONVERGED;
+    if (st->status == TP_ERR_TIMEOUT) status = TP_ERR_TIMEOUT;  // a bounded wait of a product ran out
     double margin = fabs(res[k] - tau_delta) / tau_delta;
     if (k - 1 >= k_init) margin = fmin(margin, fabs(res[k - 1] - tau_delta) / tau_delta);
     st->k = k;
@@ -735,10 +736,31 @@ template <typename T>
 struct RtWs {
     State* st;
     double *partsA, *partsB, *normsq, *dpout;
-    cplx<T> *Ahat, *Bhat, *G, *Y, *Z, *Q, *BHb, *QG, *R, *d, *UR, *dprime, *alpha, *Vt, *KhT, *Xhat;
+    cplx<T> *Ahat, *AhT, *Bhat, *G, *Y, *Z, *Q, *BHb, *QG, *R, *d, *UR, *dprime, *alpha, *Vt, *KhT, *Xhat;
     T* sigma;
     size_t bytes;
 };
+
+// A-hat^T per slice (m x l), so that the float32 products A-hat^H Y read rows
+// (conj(A-hat^T) Y) on the tensor cores.  32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ctranspose(const cplx<T>* __restrict__ A, cplx<T>* __restrict__ AT, int l,
+                                                    int m) {
+    __shared__ cplx<T> tile[32][33];
+    const long s = blockIdx.z;
+    const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    A += s * l * m;
+    AT += s * l * m;
+    for (int y = ty; y < 32; y += 8) {
+        const int i = i0 + y, j = j0 + tx;
+        if (i < l && j < m) tile[y][tx] = A[(long)i * m + j];
+    }
+    __syncthreads();
+    for (int y = ty; y < 32; y += 8) {
+        const int j = j0 + y, i = i0 + tx;
+        if (i < l && j < m) AT[(long)j * l + i] = tile[tx][y];
+    }
+}
 
 template <typename T>
 static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max) {
@@ -752,6 +774,7 @@ static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max) {
     w.normsq = c.take<double>(h);
     w.dpout = c.take<double>(h * (r_max + 1));
     w.Ahat = c.take<V>(h * l * m);
+    w.AhT = sizeof(T) == 4 ? c.take<V>(h * l * m) : nullptr;  // float32 only: tensor-core products
     w.Bhat = c.take<V>(h * l);
     w.G = c.take<V>(h * m * b);
     w.Y = c.take<V>(h * l * b);
@@ -816,6 +839,16 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     const int* done = &w.st->done;
 
     TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, w.partsA, nullptr, st));
+    if (w.AhT) {
+        prof_begin(TP_KC_GEMM, st);
+        k_ctranspose<T><<<dim3((unsigned)((m + 31) / 32), (unsigned)((l + 31) / 32), (unsigned)h), 256, 0, st>>>(
+            w.Ahat, w.AhT, l, m);
+        TRY(launched(TP_KC_GEMM, st));
+    }
+    // A-hat^H Y: conj(A-hat^T) Y from the transposed copy when there is one
+    const cplx<T>* AH = w.AhT ? w.AhT : w.Ahat;
+    const long ldah = w.AhT ? l : m;
+    const int op_h = w.AhT ? OP_R : OP_C;
     TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, w.partsB, nullptr, st));
     prof_begin(TP_KC_MISC, st);
     k_rt_init<<<1, 256, 0, st>>>(w.st, w.partsA, rdft_parts(l, m), w.partsB, rdft_parts(l, 1), P->eps, P->eps_rel, n);
@@ -827,23 +860,23 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
         // Gaussian block -> Fourier, sketch, power iterations, orthonormalise
         TRY(rdft<T>(Om + r0, w.G, n, m, bb, r_max, (long)m * r_max, nullptr, done, st));
         TRY(cgemm<T>(h, l, bb, m, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_N, w.G, bb, (long)m * bb, OP_N, 0, 0, w.Y, bb,
-                     (long)l * bb, done, st));
+                     (long)l * bb, done, st, &w.st->status));
         const bool last_y = (P->q_power == 0);
         TRY(orth<T>(h, w.Y, (long)l * bb, l, bb, w.Q, (long)r_max * l, r0, last_y ? w.Q : nullptr, nullptr, 0, 0, 0,
                     nullptr, done, st));
         for (int it = 0; it < P->q_power; ++it) {
-            TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_C, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.Z, bb,
-                         (long)m * bb, done, st));
+            TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, AH, ldah, lm, op_h, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.Z, bb,
+                         (long)m * bb, done, st, &w.st->status));
             TRY(orth<T>(h, w.Z, (long)m * bb, m, bb, nullptr, 0, 0, nullptr, nullptr, 0, 0, 0, nullptr, done, st));
             TRY(cgemm<T>(h, l, bb, m, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_N, w.Z, bb, (long)m * bb, OP_N, 0, 0, w.Y, bb,
-                         (long)l * bb, done, st));
+                         (long)l * bb, done, st, &w.st->status));
             const bool last = (it + 1 == P->q_power);
             TRY(orth<T>(h, w.Y, (long)l * bb, l, bb, w.Q, (long)r_max * l, r0, last ? w.Q : nullptr, nullptr, 0, 0,
                         0, nullptr, done, st));
         }
         // Bt(block)^H = A^H Y; its QR against the earlier columns extends QG and R
-        TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_C, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.BHb, bb,
-                     (long)m * bb, done, st));
+        TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, AH, ldah, lm, op_h, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.BHb, bb,
+                     (long)m * bb, done, st, &w.st->status));
         TRY(orth<T>(h, w.BHb, (long)m * bb, m, bb, w.QG, (long)r_max * m, r0, w.QG, w.R, r_max,
                     (long)r_max * r_max, r_max, w.normsq, done, st));
         prof_begin(TP_KC_MISC, st);

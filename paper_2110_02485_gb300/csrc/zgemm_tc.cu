@@ -1,0 +1,489 @@
+// Batched complex matrix product C[s] = op(A[s]) B[s] on the fifth-generation
+// tensor cores (tcgen05.mma, kind::tf32) with float32 accuracy.
+//
+// This is the sketch and projection product of the block RT-tSVD (Algorithm 3
+// in block form: Y = A-hat Omega-hat, Z = A-hat^H Y per Fourier slice), whose
+// right-hand side has few columns (the block size b <= 32) while A-hat is a
+// full slice.  The complex product is written as a real one:
+//   op = N:  rows i of A, reduction over (j, re/im), A used in place;
+//   op = C:  rows (j, re/im) of A^T, reduction over i, A transposed while it
+//            is staged in shared memory,
+// with the right-hand side expanded into a real matrix of 2 b columns whose
+// signs produce the real and imaginary parts (conjugation included).
+//
+// Accuracy: each float32 operand x is split as x = hi + lo with hi = tf32(x)
+// and lo = tf32(x - hi) (round to nearest); the product keeps
+// hi*hi + hi*lo + lo*hi (the "3xTF32" scheme), so the relative error of each
+// term is about 2^-22, the same order as float32 products.  The right-hand
+// side's hi and lo rows are stacked, so one MMA of N = 4 b' forms hi*hi and
+// hi*lo and a second of N = 2 b' adds lo*hi (b' = b rounded up to 8).
+//
+// Layout and pipeline: one CTA per (slice, 128-row tile), three roles that
+// meet only at mbarriers, over a ring of stages:
+//   warp 8 (one thread): TMA loads of the raw A and B tiles of a stage
+//        (3-D tensor maps: columns, rows, slices; zero fill past the edges);
+//   warps 0-7: the hi/lo split.  For op = N the TMA writes A with the 128-byte
+//        swizzle, which is the tensor core's K-major SWIZZLE_128B layout, so
+//        the split is element-wise in place (hi) plus a lo copy; for op = C the
+//        raw tile (rows i) is transposed into the no-swizzle K-major layout
+//        (8 rows x 16 bytes per core matrix).  The real right-hand side is
+//        built from the raw B rows;
+//   warp 9 (one thread): the MMAs of a stage, committed to the stage's
+//        "empty" barrier, which hands the buffers back to the TMA thread.
+// The accumulator (128 lanes x 4 b' float32 columns) lives in tensor memory;
+// warps 0-7 read it back with tcgen05.ld once the last commit lands.
+// op = R (conj(A) B, A row-major) uses the op = N kernel with the signs of
+// the right-hand side flipped; the RT-tSVD forms A-hat^H Y this way from a
+// transposed copy of A-hat, so every large product takes the swizzled path.
+// Every wait is bounded; on a timeout the kernel records TP_ERR_TIMEOUT,
+// waits (bounded) for its MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tp {
+namespace {
+
+constexpr int TC_M = 128;                 // MMA rows per CTA
+constexpr int TC_KT = 32;                 // real reduction length per stage (4 MMA K-steps of 8)
+constexpr int TC_CONV_WARPS = 8;          // warps 0-7 split; in the epilogue warp w reads TMEM lanes 32 (w % 4)..
+constexpr int TC_CONV_THREADS = 32 * TC_CONV_WARPS;
+constexpr int TC_PROD_WARP = TC_CONV_WARPS, TC_MMA_WARP = TC_CONV_WARPS + 1;
+constexpr int TC_THREADS = 32 * (TC_CONV_WARPS + 2);
+constexpr int TC_A_BYTES = TC_M * TC_KT * 4;      // one A tile (16 KB)
+constexpr uint32_t TC_LBO_A = (TC_M / 8) * 128;  // no-swizzle K-major: next core matrix along K
+constexpr uint32_t TC_SBO = 128;                  // no-swizzle: next core matrix along M / N
+constexpr uint32_t TC_SBO_SW = 1024;              // 128-byte swizzle: next 8-row group
+constexpr int TC_SMEM_LIMIT = 225 * 1024;
+constexpr long long TC_SPIN = 2000000000LL;       // ~1 s at the GB300 SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// x rounded to tf32 (10 stored mantissa bits), to nearest with ties away from
+// zero: add half an ulp of the kept part to the magnitude bits, clear the rest
+// (a carry into the exponent is the correct rounding; finite inputs only).
+__device__ __forceinline__ float tf32_rna(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ void split3(float x, float& hi, float& lo) {
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - hi);
+}
+__device__ __forceinline__ void split3(float4 x, float4& hi, float4& lo) {
+    split3(x.x, hi.x, lo.x);
+    split3(x.y, hi.y, lo.y);
+    split3(x.z, hi.z, lo.z);
+    split3(x.w, hi.w, lo.w);
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, layout type (0 none, 2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
+}
+// Instruction descriptor, kind::tf32: D float32, A and B tf32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        :
+        : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity.  False on timeout (which
+// also raises *abort) or when another role has raised *abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    while (!mbar_try(a, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > TC_SPIN) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// Bounded wait that ignores the abort flag (used to drain work in flight).
+__device__ __forceinline__ void mbar_drain(uint32_t a, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(a, parity))
+        if (clock64() - t0 > TC_SPIN) return;
+}
+__device__ __forceinline__ void mbar_init_n(uint32_t a, unsigned n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 8 consecutive float32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    // the registers are valid only after wait::ld; threading them through the
+    // wait keeps every use behind it
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle tile whose core
+// matrices advance by `lbo` along K and by 128 bytes along the rows.
+__device__ __forceinline__ uint32_t kmaj_off(int row, int k, uint32_t lbo) {
+    return (uint32_t)(k >> 2) * lbo + (uint32_t)(row >> 3) * TC_SBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
+}
+
+__device__ __forceinline__ float pick4(const float4& v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// Stage buffers: raw A (TMA), hi A (op C only; op N splits in place), lo A,
+// raw B rows (TMA), and the real right-hand side B_op.
+template <int OPA, int NCP> struct TcCfg {
+    static constexpr int NB = 4 * NCP;                  // B_op rows: (re, im) x (hi, lo)
+    static constexpr uint32_t LBO_B = (NB / 8) * 128;
+    static constexpr int KB = OPA == OP_N ? TC_KT / 2 : TC_KT;  // B rows per stage
+    static constexpr int A_RAW = 0;
+    static constexpr int A_HI = OPA == OP_N ? 0 : TC_A_BYTES;
+    static constexpr int A_LO = OPA == OP_N ? TC_A_BYTES : 2 * TC_A_BYTES;
+    static constexpr int B_RAW = A_LO + TC_A_BYTES;
+    static constexpr int B_RAW_BYTES = KB * NCP * 8;
+    static constexpr int B_OP = B_RAW + B_RAW_BYTES;
+    static constexpr int STAGE = B_OP + NB * TC_KT * 4;  // a multiple of 1024
+    static constexpr int NS = (TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE;
+    static constexpr size_t SMEM = (size_t)NS * STAGE + 1024;  // + alignment slack
+    static constexpr uint32_t TX = TC_A_BYTES + B_RAW_BYTES;   // bytes the two TMA boxes deliver
+    static constexpr uint32_t NCOLS = NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
+};
+
+// Split one stage (warps 0-7).  CONJ (op = R): right-hand side signs of conj(A) B.
+template <int OPA, bool CONJ, int NCP>
+__device__ __forceinline__ void split_stage(unsigned char* st) {
+    typedef TcCfg<OPA, NCP> G;
+    const int t = threadIdx.x;
+    const float2* rb = (const float2*)(st + G::B_RAW);
+    float* Bs = (float*)(st + G::B_OP);
+    if (OPA == OP_N) {
+        // element-wise on the swizzled tile: hi in place, lo at the same offset
+        float4* a = (float4*)(st + G::A_RAW);
+        float4* alo = (float4*)(st + G::A_LO);
+#pragma unroll 4
+        for (int i = t; i < TC_A_BYTES / 16; i += TC_CONV_THREADS) {
+            float4 hi, lo;
+            split3(a[i], hi, lo);
+            a[i] = hi;
+            alo[i] = lo;
+        }
+        // A B:       re row (Br, -Bi), im row (Bi,  Br)
+        // conj(A) B: re row (Br,  Bi), im row (Bi, -Br)
+        for (int e = t; e < G::KB * NCP; e += TC_CONV_THREADS) {
+            const int jj = e / NCP, c = e - jj * NCP;
+            const float2 x = rb[e];
+            float rh, rl, ih, il;
+            split3(x.x, rh, rl);
+            split3(x.y, ih, il);
+            const int k = 2 * jj;
+            const float sa = CONJ ? 1.f : -1.f, sb = CONJ ? -1.f : 1.f;
+            *(float2*)((char*)Bs + kmaj_off(c, k, G::LBO_B)) = make_float2(rh, sa * ih);
+            *(float2*)((char*)Bs + kmaj_off(NCP + c, k, G::LBO_B)) = make_float2(ih, sb * rh);
+            *(float2*)((char*)Bs + kmaj_off(2 * NCP + c, k, G::LBO_B)) = make_float2(rl, sa * il);
+            *(float2*)((char*)Bs + kmaj_off(3 * NCP + c, k, G::LBO_B)) = make_float2(il, sb * rl);
+        }
+    } else {
+        // raw rows i (128 floats each) -> rows (j, re/im) of the K-major tiles, 4 x 4 blocks
+        const float* ra = (const float*)(st + G::A_RAW);
+        float* Ahi = (float*)(st + G::A_HI);
+        float* Alo = (float*)(st + G::A_LO);
+#pragma unroll 1
+        for (int b = t; b < (TC_M / 4) * (TC_KT / 4); b += TC_CONV_THREADS) {
+            const int m4 = b & 31, i4 = b >> 5;
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = *(const float4*)(ra + (4 * i4 + q) * 128 + 4 * m4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = (u + (m4 >> 1)) & 3;  // rotate the first row with the thread: no bank conflicts
+                const float4 w = make_float4(pick4(v[0], e), pick4(v[1], e), pick4(v[2], e), pick4(v[3], e));
+                float4 hi, lo;
+                split3(w, hi, lo);
+                const uint32_t off = kmaj_off(4 * m4 + e, 4 * i4, TC_LBO_A);
+                *(float4*)((char*)Ahi + off) = hi;
+                *(float4*)((char*)Alo + off) = lo;
+            }
+        }
+        for (int e = t; e < G::KB * NCP; e += TC_CONV_THREADS) {
+            const int ii = e / NCP, c = e - ii * NCP;
+            const float2 x = rb[e];
+            float rh, rl, ih, il;
+            split3(x.x, rh, rl);
+            split3(x.y, ih, il);
+            *(float*)((char*)Bs + kmaj_off(c, ii, G::LBO_B)) = rh;
+            *(float*)((char*)Bs + kmaj_off(NCP + c, ii, G::LBO_B)) = ih;
+            *(float*)((char*)Bs + kmaj_off(2 * NCP + c, ii, G::LBO_B)) = rl;
+            *(float*)((char*)Bs + kmaj_off(3 * NCP + c, ii, G::LBO_B)) = il;
+        }
+    }
+}
+
+template <int OPA, bool CONJ, int NCP>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           float2* __restrict__ C, long ldc, long sC, int Mc, int Nc, int Kc, const int* skip, int* err) {
+    typedef TcCfg<OPA, NCP> G;
+    if (skip && *skip) return;
+    extern __shared__ unsigned char sm_raw[];
+    __shared__ __align__(8) uint64_t full[G::NS], conv[G::NS], empty[G::NS], accf;
+    __shared__ uint32_t tmem_s;
+    __shared__ int abort_s;
+    volatile int* abort = &abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int sl = blockIdx.y, row0 = blockIdx.x * TC_M;
+    C += (long)sl * sC;
+    const int Mr = OPA == OP_N ? Mc : 2 * Mc;
+    const int Kr = OPA == OP_N ? 2 * Kc : Kc;
+    const int nkt = (Kr + TC_KT - 1) / TC_KT;
+    // stage ring at a 1024-byte boundary (the 128-byte swizzle repeats every 1024 bytes)
+    const uint32_t sbase = (smem_u32(sm_raw) + 1023u) & ~1023u;
+    unsigned char* sgen = sm_raw + (sbase - smem_u32(sm_raw));
+
+    if (tid == 0) {
+        for (int i = 0; i < G::NS; ++i) {
+            mbar_init_n(smem_u32(&full[i]), 1);
+            mbar_init_n(smem_u32(&conv[i]), TC_CONV_WARPS);
+            mbar_init_n(smem_u32(&empty[i]), 1);
+        }
+        mbar_init_n(smem_u32(&accf), 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                     "r"(G::NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_s;
+
+    if (warp == TC_PROD_WARP) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kt = 0; kt < nkt; ++kt) {
+                const int st = kt % G::NS;
+                if (kt >= G::NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((kt / G::NS - 1) & 1), abort)) break;
+                const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
+                const uint32_t fb = smem_u32(&full[st]);
+                mbar_expect_tx(fb, G::TX);
+                if (OPA == OP_N) tma_load_3d(buf + G::A_RAW, &tmA, kt * TC_KT, row0, sl, fb);
+                else tma_load_3d(buf + G::A_RAW, &tmA, row0, kt * TC_KT, sl, fb);
+                tma_load_3d(buf + G::B_RAW, &tmB, 0, kt * G::KB, sl, fb);
+                issued = kt + 1;
+            }
+            // drain: every TMA write lands before the CTA can end
+            for (int kt = issued - G::NS > 0 ? issued - G::NS : 0; kt < issued; ++kt)
+                mbar_drain(smem_u32(&full[kt % G::NS]), (uint32_t)((kt / G::NS) & 1));
+        }
+    } else if (warp == TC_MMA_WARP) {
+        if (lane == 0) {
+            const uint32_t id_full = idesc_tf32(TC_M, G::NB), id_half = idesc_tf32(TC_M, 2 * NCP);
+            int issued = 0;
+            for (int kt = 0; kt < nkt; ++kt) {
+                const int st = kt % G::NS;
+                if (!mbar_wait(smem_u32(&conv[st]), (uint32_t)((kt / G::NS) & 1), abort)) break;
+                tc_fence_after();
+                const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
+#pragma unroll
+                for (int ks = 0; ks < TC_KT / 8; ++ks) {
+                    uint64_t dah, dal;
+                    if (OPA == OP_N) {  // 128-byte swizzled K-major: K advances 32 bytes inside the atom
+                        dah = sdesc(buf + G::A_HI + ks * 32, 16, TC_SBO_SW, 2);
+                        dal = sdesc(buf + G::A_LO + ks * 32, 16, TC_SBO_SW, 2);
+                    } else {
+                        dah = sdesc(buf + G::A_HI + ks * 2 * TC_LBO_A, TC_LBO_A, TC_SBO);
+                        dal = sdesc(buf + G::A_LO + ks * 2 * TC_LBO_A, TC_LBO_A, TC_SBO);
+                    }
+                    const uint64_t db = sdesc(buf + G::B_OP + ks * 2 * G::LBO_B, G::LBO_B, TC_SBO);
+                    mma_tf32(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);  // hi*hi | hi*lo
+                    mma_tf32(tmem, dal, db, id_half, 1u);                            // += lo*hi
+                }
+                mma_commit(smem_u32(&empty[st]));
+                issued = kt + 1;
+            }
+            if (issued == nkt) {
+                mma_commit(smem_u32(&accf));
+            } else if (issued > 0) {  // aborted: let the MMAs in flight finish
+                mbar_drain(smem_u32(&empty[(issued - 1) % G::NS]), (uint32_t)(((issued - 1) / G::NS) & 1));
+            }
+        }
+    } else {
+        // warps 0-7: split each stage, then the epilogue
+        for (int kt = 0; kt < nkt; ++kt) {
+            const int st = kt % G::NS;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / G::NS) & 1), abort)) break;
+            split_stage<OPA, CONJ, NCP>(sgen + st * G::STAGE);
+            fence_async_smem();  // generic-proxy writes -> tensor-core reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&conv[st]));
+        }
+        const bool ok = mbar_wait(smem_u32(&accf), 0u, abort);
+        if (__all_sync(0xffffffffu, ok)) {
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+            const int r = row0 + 32 * (warp & 3) + lane;  // real row of the MMA
+            for (int c0 = 8 * (warp >> 2); c0 < NCP; c0 += 16) {
+                // columns c0..c0+7 of the four groups: re (hi*hi + lo*hi), im (...), re (hi*lo), im (hi*lo)
+                float d[4][8];
+#pragma unroll
+                for (int g = 0; g < 4; ++g) tmem_ld8(ta + (uint32_t)(g * NCP + c0), d[g]);
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    const int c = c0 + cc;
+                    const float re = d[0][cc] + d[2][cc];
+                    const float im = d[1][cc] + d[3][cc];
+                    if (OPA == OP_N) {
+                        if (r < Mr && c < Nc) C[(long)r * ldc + c] = make_float2(re, im);
+                    } else {
+                        // rows 2j (re of A) and 2j+1 (im of A) sit in neighbouring lanes
+                        const float pim = __shfl_xor_sync(0xffffffffu, im, 1);
+                        const float v = (lane & 1) ? (pim - re) : (re + pim);
+                        if (r < Mr && c < Nc) ((float*)C)[((long)(r >> 1) * ldc + c) * 2 + (r & 1)] = v;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && abort_s && err) atomicExch(err, (int)TP_ERR_TIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::NCOLS) : "memory");
+    }
+}
+
+typedef PFN_cuTensorMapEncodeTiled_v12000 EncodeFn;
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)p;
+    });
+    return fn;
+}
+
+// 3-D float32 tensor map over (columns, rows, slices) with the given box.
+bool make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t slices, uint64_t row_bytes,
+              uint64_t slice_bytes, uint32_t box_c, uint32_t box_r, bool swz) {
+    EncodeFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {cols, rows, slices};
+    const cuuint64_t strides[2] = {row_bytes, slice_bytes};
+    const cuuint32_t box[3] = {box_c, box_r, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int OPA, bool CONJ, int NCP>
+tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, const void* B, long ldb,
+                    long sB, void* C, long ldc, long sC, const int* skip, int* err, cudaStream_t st) {
+    typedef TcCfg<OPA, NCP> G;
+    CUtensorMap ma, mb;
+    // A: op N rows i of 2K floats (box 32 x 128, swizzled); op C rows i of 2M floats (box 128 x 32)
+    const bool oka = OPA == OP_N ? make_map(&ma, A, 2 * (uint64_t)K, M, batch, 8 * (uint64_t)lda,
+                                            8 * (uint64_t)sA, TC_KT, TC_M, true)
+                                 : make_map(&ma, A, 2 * (uint64_t)M, K, batch, 8 * (uint64_t)lda,
+                                            8 * (uint64_t)sA, TC_M, TC_KT, false);
+    const bool okb =
+        make_map(&mb, B, 2 * (uint64_t)N, K, batch, 8 * (uint64_t)ldb, 8 * (uint64_t)sB, 2 * NCP, G::KB, false);
+    if (!oka || !okb) return TP_ERR_UNSUPPORTED;
+    auto kern = k_zgemm_tc<OPA, CONJ, NCP>;
+    if (smem_optin((const void*)kern, G::SMEM) != TP_OK) return TP_ERR_CUDA;
+    const int Mr = OPA == OP_N ? M : 2 * M;
+    dim3 grid((unsigned)((Mr + TC_M - 1) / TC_M), (unsigned)batch);
+    prof_begin(TP_KC_GEMM, st);
+    kern<<<grid, TC_THREADS, G::SMEM, st>>>(ma, mb, (float2*)C, ldc, sC, M, N, K, skip, err);
+    return launched(TP_KC_GEMM, st);
+}
+
+}  // namespace
+
+// Returns TP_ERR_UNSUPPORTED (nothing enqueued) when the shape or alignment
+// does not fit this kernel; the caller then uses the SIMT product.
+tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B, long ldb,
+                   long sB, void* C, long ldc, long sC, const int* skip, int* err, cudaStream_t st) {
+    if (opA != OP_N && opA != OP_R && opA != OP_C) return TP_ERR_UNSUPPORTED;
+    if (batch < 1 || batch > 65535 || M < 1 || N < 1 || N > 32 || K < 1) return TP_ERR_UNSUPPORTED;
+    // tensor maps: 16-byte aligned bases and 16-byte multiples for the row and slice strides
+    if ((lda & 1) || (sA & 1) || (ldb & 1) || (sB & 1) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+        return TP_ERR_UNSUPPORTED;
+    if ((opA == OP_C ? 2 * M : M) > 65535 * TC_M) return TP_ERR_UNSUPPORTED;
+    const int ncp = (N + 7) & ~7;
+#define TC_GO(OP, CJ, NC) launch_tc<OP, CJ, NC>(batch, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, skip, err, st)
+#define TC_SWITCH(OP, CJ)                          \
+    switch (ncp) {                                 \
+        case 8: return TC_GO(OP, CJ, 8);           \
+        case 16: return TC_GO(OP, CJ, 16);         \
+        case 24: return TC_GO(OP, CJ, 24);         \
+        default: return TC_GO(OP, CJ, 32);         \
+    }
+    if (opA == OP_N) TC_SWITCH(OP_N, false)
+    if (opA == OP_R) TC_SWITCH(OP_N, true)
+    TC_SWITCH(OP_C, false)
+#undef TC_SWITCH
+#undef TC_GO
+}
+
+}  // namespace tp

@@ -92,6 +92,23 @@ def test_tprod_matches_oracle(tp, dtype, n, l, kk, m, trans):
     assert rel(C, ref) <= tol
 
 
+@pytest.mark.parametrize("n,l,kk,m,trans", [(8, 256, 256, 16, 0), (8, 256, 256, 16, 1), (5, 128, 40, 8, 0),
+                                            (4, 100, 62, 24, 1), (3, 200, 98, 32, 0), (6, 64, 2, 2, 0),
+                                            (3, 1, 2, 2, 1), (4, 300, 130, 14, 1), (2, 150, 66, 6, 0),
+                                            (7, 37, 300, 10, 1)])
+def test_tprod_tensor_core_shapes(tp, n, l, kk, m, trans):
+    """Float32 products with at most 32 columns and even leading dimensions run
+    on the tensor cores (3xTF32); ragged row, reduction and column counts
+    included.  Their error must stay at the float32 level."""
+    A = rnd((n, kk, l) if trans else (n, l, kk), 30 + n)
+    B = rnd((n, kk, m), 40 + n)
+    C = tp.tprod(dev(A, torch.float32), dev(B, torch.float32), transA=bool(trans)).cpu().numpy()
+    Ad = dev(A, torch.float32).cpu().double().numpy()
+    Bd = dev(B, torch.float32).cpu().double().numpy()
+    ref = O.tprod(O.ttranspose(Ad) if trans else Ad, Bd)
+    assert rel(C, ref) <= 5e-6 * np.sqrt(kk)
+
+
 # --------------------------------------------------------------- solvers ----
 
 def problem(N, n=None, seed=5, noise=1e-2, general=0.02, l=None):
