@@ -11,10 +11,13 @@
 // with the right-hand side expanded into a real matrix of 2 b columns whose
 // signs produce the real and imaginary parts (conjugation included).
 //
-// Accuracy: each float32 operand x is split as x = hi + lo with hi = tf32(x)
-// and lo = tf32(x - hi) (round to nearest); the product keeps
-// hi*hi + hi*lo + lo*hi (the "3xTF32" scheme), so the relative error of each
-// term is about 2^-22, the same order as float32 products.  The right-hand
+// Accuracy: each float32 operand x is split as x = hi + lo and the product
+// keeps hi*hi + hi*lo + lo*hi (the "3xTF32" scheme).  The tensor core reads a
+// float32 operand as tf32 by ignoring its 13 low mantissa bits, so for the
+// large operand (A) with op = N or R hi is the float32 tile itself, left in
+// place, and lo = rna(x - trunc(x)) is the only value written; otherwise
+// hi = rna(x), lo = rna(x - hi).  Relative error of a term: at most about
+// 2^-21, the order of float32 products.  The right-hand
 // side's hi and lo rows are stacked, so one MMA of N = 4 b' forms hi*hi and
 // hi*lo and a second of N = 2 b' adds lo*hi (b' = b rounded up to 8).
 //
@@ -79,6 +82,10 @@ __device__ __forceinline__ void split3(float4 x, float4& hi, float4& lo) {
     split3(x.y, hi.y, lo.y);
     split3(x.z, hi.z, lo.z);
     split3(x.w, hi.w, lo.w);
+}
+// The part of x below its tf32 truncation, rounded to tf32.
+__device__ __forceinline__ float tf32_rest(float x) {
+    return tf32_rna(x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u));
 }
 
 // Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
@@ -193,7 +200,12 @@ template <int OPA, int NCP> struct TcCfg {
     static constexpr int B_RAW_BYTES = KB * NCP * 8;
     static constexpr int B_OP = B_RAW + B_RAW_BYTES;
     static constexpr int STAGE = B_OP + NB * TC_KT * 4;  // a multiple of 1024
-    static constexpr int NS = (TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE;
+    // two CTAs per SM when two stages fit in half the shared memory (the TMA
+    // stream of one CTA does not fill an SM's share of L2 bandwidth), else one
+    // CTA with up to four stages
+    static constexpr int NS = 2 * STAGE + 1024 <= TC_SMEM_LIMIT / 2
+                                  ? 2
+                                  : ((TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE);
     static constexpr size_t SMEM = (size_t)NS * STAGE + 1024;  // + alignment slack
     static constexpr uint32_t TX = TC_A_BYTES + B_RAW_BYTES;   // bytes the two TMA boxes deliver
     static constexpr uint32_t NCOLS = NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
@@ -207,15 +219,13 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
     const float2* rb = (const float2*)(st + G::B_RAW);
     float* Bs = (float*)(st + G::B_OP);
     if (OPA == OP_N) {
-        // element-wise on the swizzled tile: hi in place, lo at the same offset
-        float4* a = (float4*)(st + G::A_RAW);
+        // element-wise on the swizzled tile: hi is the tile itself, lo at the same offset
+        const float4* a = (const float4*)(st + G::A_RAW);
         float4* alo = (float4*)(st + G::A_LO);
 #pragma unroll 4
         for (int i = t; i < TC_A_BYTES / 16; i += TC_CONV_THREADS) {
-            float4 hi, lo;
-            split3(a[i], hi, lo);
-            a[i] = hi;
-            alo[i] = lo;
+            const float4 v = a[i];
+            alo[i] = make_float4(tf32_rest(v.x), tf32_rest(v.y), tf32_rest(v.z), tf32_rest(v.w));
         }
         // A B:       re row (Br, -Bi), im row (Bi,  Br)
         // conj(A) B: re row (Br,  Bi), im row (Bi, -Br)
@@ -225,12 +235,14 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
             float rh, rl, ih, il;
             split3(x.x, rh, rl);
             split3(x.y, ih, il);
-            const int k = 2 * jj;
             const float sa = CONJ ? 1.f : -1.f, sb = CONJ ? -1.f : 1.f;
-            *(float2*)((char*)Bs + kmaj_off(c, k, G::LBO_B)) = make_float2(rh, sa * ih);
-            *(float2*)((char*)Bs + kmaj_off(NCP + c, k, G::LBO_B)) = make_float2(ih, sb * rh);
-            *(float2*)((char*)Bs + kmaj_off(2 * NCP + c, k, G::LBO_B)) = make_float2(rl, sa * il);
-            *(float2*)((char*)Bs + kmaj_off(3 * NCP + c, k, G::LBO_B)) = make_float2(il, sb * rl);
+            // rows c, NCP + c, 2 NCP + c, 3 NCP + c: NCP / 8 core matrices apart
+            char* p = (char*)Bs + kmaj_off(c, 2 * jj, G::LBO_B);
+            constexpr int RS = (NCP / 8) * TC_SBO;
+            *(float2*)(p) = make_float2(rh, sa * ih);
+            *(float2*)(p + RS) = make_float2(ih, sb * rh);
+            *(float2*)(p + 2 * RS) = make_float2(rl, sa * il);
+            *(float2*)(p + 3 * RS) = make_float2(il, sb * rl);
         }
     } else {
         // raw rows i (128 floats each) -> rows (j, re/im) of the K-major tiles, 4 x 4 blocks
@@ -260,16 +272,18 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
             float rh, rl, ih, il;
             split3(x.x, rh, rl);
             split3(x.y, ih, il);
-            *(float*)((char*)Bs + kmaj_off(c, ii, G::LBO_B)) = rh;
-            *(float*)((char*)Bs + kmaj_off(NCP + c, ii, G::LBO_B)) = ih;
-            *(float*)((char*)Bs + kmaj_off(2 * NCP + c, ii, G::LBO_B)) = rl;
-            *(float*)((char*)Bs + kmaj_off(3 * NCP + c, ii, G::LBO_B)) = il;
+            char* p = (char*)Bs + kmaj_off(c, ii, G::LBO_B);
+            constexpr int RS = (NCP / 8) * TC_SBO;
+            *(float*)(p) = rh;
+            *(float*)(p + RS) = ih;
+            *(float*)(p + 2 * RS) = rl;
+            *(float*)(p + 3 * RS) = il;
         }
     }
 }
 
 template <int OPA, bool CONJ, int NCP>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
 k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            float2* __restrict__ C, long ldc, long sC, int Mc, int Nc, int Kc, const int* skip, int* err) {
     typedef TcCfg<OPA, NCP> G;
