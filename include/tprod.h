@@ -50,7 +50,20 @@ typedef enum {
     TP_ERR_UNSUPPORTED = -7     /* valid request outside what this build supports      */
 } tp_status;
 
-typedef enum { TP_FP32 = 0, TP_FP64 = 1 } tp_precision;
+/* Arithmetic precision of a call.
+ *   TP_FP32: float data; every product float32-accurate (the tensor-core
+ *            products with at most 32 columns use the 3xTF32 split).
+ *   TP_FP64: double data, double arithmetic (CUDA cores).
+ *   TP_TF32: float data; the tensor-core products (tprod_gemm with at most 32
+ *            columns, and the block sketch and power-iteration products of
+ *            rtsvd_truncated_solve) take one tf32 product each (10-bit
+ *            mantissa inputs, float32 accumulation) instead of the 3xTF32
+ *            split; the re-projection B^H = A^H Y of each block and
+ *            everything else stay as TP_FP32.  The reduced-precision form of
+ *            the RT-tSVD sketch (Algorithm 3's products), accepted by
+ *            tprod_gemm, rtsvd_truncated_solve and their workspace queries;
+ *            any other entry point rejects it with TP_ERR_ARG (or returns 0). */
+typedef enum { TP_FP32 = 0, TP_FP64 = 1, TP_TF32 = 2 } tp_precision;
 
 /* Result record of a solve, written to device memory. */
 typedef struct {

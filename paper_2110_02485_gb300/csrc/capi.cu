@@ -69,7 +69,7 @@ tp_status smem_optin(const void* kern, size_t bytes) {
 template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_params*);
 template <typename T>
 tp_status rt_solve(const T*, const T*, const T*, int, int, int, int, const tp_rtsvd_params*, T*, tp_info*, void*,
-                   size_t, cudaStream_t);
+                   size_t, cudaStream_t, int);
 template <typename T> size_t gk_ws_bytes(int, int, int, int, const tp_tgkb_params*);
 template <typename T>
 tp_status gk_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
@@ -102,7 +102,7 @@ static size_t gemm_ws(int l, int kk, int m, int n, size_t c) {
 
 template <typename T>
 static tp_status gemm_t(const void* A, const void* B, void* C, int l, int kk, int m, int n, int transA, void* ws,
-                        cudaStream_t st) {
+                        cudaStream_t st, int tc_passes = 3) {
     const int h = n / 2 + 1;
     const size_t c = 2 * sizeof(T);
     char* p = (char*)ws;
@@ -116,7 +116,7 @@ static tp_status gemm_t(const void* A, const void* B, void* C, int l, int kk, in
     e = rdft<T>((const T*)B, Bh, n, kk, m, m, (long)kk * m, nullptr, nullptr, st);
     if (e != TP_OK) return e;
     e = cgemm<T>(h, l, m, kk, nullptr, nullptr, nullptr, 1, 0, Ah, ac, (long)ar * ac, transA ? OP_C : OP_N, Bh, m,
-                 (long)kk * m, OP_N, 0, 0, Ch, m, (long)l * m, nullptr, st);
+                 (long)kk * m, OP_N, 0, 0, Ch, m, (long)l * m, nullptr, st, nullptr, tc_passes);
     if (e != TP_OK) return e;
     return irdft<T>(Ch, (T*)C, n, l, m, m, (long)l * m, nullptr, st);
 }
@@ -139,24 +139,31 @@ tp_status tprod_ifft(const void* Xhat, int l, int m, int n, void* X, int prec, v
     return prec == TP_FP32 ? ifft_t<float>(Xhat, l, m, n, X, st) : ifft_t<double>(Xhat, l, m, n, X, st);
 }
 
+// TP_TF32: float32 data; only the tensor-core products differ (one tf32 product).
+static int data_prec(int prec) { return prec == TP_TF32 ? TP_FP32 : prec; }
+
 size_t tprod_gemm_workspace_bytes(int l, int kk, int m, int n, int prec) {
+    prec = data_prec(prec);
     if (!dims_ok(l, kk, n, prec) || m < 1) return 0;
     return gemm_ws(l, kk, m, n, prec == TP_FP32 ? 8 : 16);
 }
 
 tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m, int n, int transA, int prec,
                      void* ws, size_t ws_bytes, void* stream) {
+    const int passes = prec == TP_TF32 ? 1 : 3;
+    prec = data_prec(prec);
     if (!A || !B || !C || !dims_ok(l, kk, n, prec) || !dims_ok(kk, m, n, prec)) return TP_ERR_ARG;
     if (transA != 0 && transA != 1) return TP_ERR_ARG;
     if (l > 65535 * 128) return TP_ERR_ARG;
     const size_t need = gemm_ws(l, kk, m, n, prec == TP_FP32 ? 8 : 16);
     if (!ws || ((size_t)ws & 255) || ws_bytes < need) return TP_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
-    return prec == TP_FP32 ? gemm_t<float>(A, B, C, l, kk, m, n, transA, ws, st)
+    return prec == TP_FP32 ? gemm_t<float>(A, B, C, l, kk, m, n, transA, ws, st, passes)
                            : gemm_t<double>(A, B, C, l, kk, m, n, transA, ws, st);
 }
 
 size_t rtsvd_workspace_bytes(int l, int m, int n, int p, const tp_rtsvd_params* params, int prec) {
+    prec = data_prec(prec);
     if (prec == TP_FP32) return rt_ws_bytes<float>(l, m, n, p, params);
     if (prec == TP_FP64) return rt_ws_bytes<double>(l, m, n, p, params);
     return 0;
@@ -166,12 +173,12 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
                                 const tp_rtsvd_params* params, void* X, tp_info* d_info, int prec, void* ws,
                                 size_t ws_bytes, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == TP_FP32)
+    if (prec == TP_FP32 || prec == TP_TF32)
         return rt_solve<float>((const float*)A, (const float*)B, (const float*)Omega, l, m, n, p, params, (float*)X,
-                               d_info, ws, ws_bytes, st);
+                               d_info, ws, ws_bytes, st, prec == TP_TF32 ? 1 : 3);
     if (prec == TP_FP64)
         return rt_solve<double>((const double*)A, (const double*)B, (const double*)Omega, l, m, n, p, params,
-                                (double*)X, d_info, ws, ws_bytes, st);
+                                (double*)X, d_info, ws, ws_bytes, st, 3);
     return TP_ERR_ARG;
 }
 

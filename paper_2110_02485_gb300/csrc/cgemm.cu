@@ -166,12 +166,13 @@ template <typename T>
 tp_status cgemm(int batch, int M, int N, int K, const int* dM, const int* dN, const int* dK, double alpha_re,
                 double alpha_im, const void* A, long lda, long sA, int opA, const void* B, long ldb, long sB,
                 int opB, double beta_re, double beta_im, void* C, long ldc, long sC, const int* skip,
-                cudaStream_t st, int* err) {
+                cudaStream_t st, int* err, int tc_passes) {
     if (batch <= 0 || M <= 0 || N <= 0) return TP_OK;
     if (batch > 65535 || (M + 127) / 128 > 65535) return TP_ERR_ARG;
     if (sizeof(T) == 4 && alpha_re == 1.0 && alpha_im == 0.0 && beta_re == 0.0 && beta_im == 0.0 && opB == OP_N &&
         !dM && !dN && !dK && K > 0) {
-        const tp_status e = zgemm_tc(batch, M, N, K, A, lda, sA, opA, B, ldb, sB, C, ldc, sC, skip, err, st);
+        const tp_status e =
+            zgemm_tc(batch, M, N, K, A, lda, sA, opA, B, ldb, sB, C, ldc, sC, skip, err, tc_passes, st);
         if (e != TP_ERR_UNSUPPORTED) return e;
     }
     const cplx<T> al = mk<T>((T)alpha_re, (T)alpha_im), be = mk<T>((T)beta_re, (T)beta_im);
@@ -184,9 +185,9 @@ tp_status cgemm(int batch, int M, int N, int K, const int* dM, const int* dN, co
 
 template tp_status cgemm<float>(int, int, int, int, const int*, const int*, const int*, double, double, const void*,
                                 long, long, int, const void*, long, long, int, double, double, void*, long, long,
-                                const int*, cudaStream_t, int*);
+                                const int*, cudaStream_t, int*, int);
 template tp_status cgemm<double>(int, int, int, int, const int*, const int*, const int*, double, double,
                                  const void*, long, long, int, const void*, long, long, int, double, double, void*,
-                                 long, long, const int*, cudaStream_t, int*);
+                                 long, long, const int*, cudaStream_t, int*, int);
 
 }  // namespace tp

@@ -48,19 +48,23 @@ size_t rdft_smem(int n, size_t elem);
 // the launch does nothing when *skip != 0.
 enum { OP_N = 0, OP_T = 1, OP_R = 2, OP_C = 3 };
 // Float32 products with alpha = 1, beta = 0, op(B) = B, at most 32 columns,
-// no run-time size caps and 16-byte aligned rows of A run on the tensor cores
-// (zgemm_tc, 3xTF32); err (optional, device) receives TP_ERR_TIMEOUT if one of
-// that kernel's bounded waits runs out.
+// no run-time size caps and 16-byte aligned operands run on the tensor cores
+// (zgemm_tc): tc_passes = 3 (3xTF32, float32 accuracy) or 1 (one tf32
+// product, the TF32 precision form).  err (optional, device) receives
+// TP_ERR_TIMEOUT if one of that kernel's bounded waits runs out.
 template <typename T>
 tp_status cgemm(int batch, int M, int N, int K, const int* dM, const int* dN, const int* dK,
                 double alpha_re, double alpha_im, const void* A, long lda, long sA, int opA,
                 const void* B, long ldb, long sB, int opB, double beta_re, double beta_im,
-                void* C, long ldc, long sC, const int* skip, cudaStream_t st, int* err = nullptr);
+                void* C, long ldc, long sC, const int* skip, cudaStream_t st, int* err = nullptr,
+                int tc_passes = 3);
 
 // Tensor-core complex product C[s] = op(A[s]) B[s] (op = N, R or C), float32
-// data; TP_ERR_UNSUPPORTED (nothing enqueued) when the shape does not fit.
+// data, passes 3 or 1; TP_ERR_UNSUPPORTED (nothing enqueued) when the shape
+// does not fit.
 tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B,
-                   long ldb, long sB, void* C, long ldc, long sC, const int* skip, int* err, cudaStream_t st);
+                   long ldb, long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes,
+                   cudaStream_t st);
 
 // Device-side bookkeeping shared by a solve.
 struct State {

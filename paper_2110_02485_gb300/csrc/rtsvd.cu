@@ -73,10 +73,12 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
     const double nnd = block_sum_t(nn, red);
     if (normsq && tid == 0) normsq[s] = nnd;
 
-    // 1. two CGS passes against the basis
+    // 1. two CGS passes against the basis (one for intermediate blocks of the
+    //    power iteration: the kept block after them gets two)
     if (r_prev > 0) {
         const V* Q = Qb + (long)s * sQ;
-        for (int pass = 0; pass < 2; ++pass) {
+        const int dpasses = final_pass ? 2 : 1;
+        for (int pass = 0; pass < dpasses; ++pass) {
             // two basis vectors per warp share every shared-memory read of Y
             for (int i0 = 2 * warp; i0 < r_prev; i0 += 2 * NW) {
                 const bool two = i0 + 1 < r_prev;
@@ -776,7 +778,7 @@ static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max) {
     w.Ahat = c.take<V>(h * l * m);
     w.AhT = sizeof(T) == 4 ? c.take<V>(h * l * m) : nullptr;  // float32 only: tensor-core products
     w.Bhat = c.take<V>(h * l);
-    w.G = c.take<V>(h * m * b);
+    w.G = c.take<V>(h * m * r_max);  // all Gaussian slices, transformed once
     w.Y = c.take<V>(h * l * b);
     w.Z = c.take<V>(h * m * b);
     w.Q = c.take<V>(h * r_max * l);
@@ -829,7 +831,7 @@ size_t rt_ws_bytes(int l, int m, int n, int p, const tp_rtsvd_params* P) {
 
 template <typename T>
 tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int p, const tp_rtsvd_params* P, T* X,
-                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st, int tc_passes) {
     TRY(rt_check<T>(l, m, n, p, P));
     if (!A || !B || !Om || !X || !info) return TP_ERR_ARG;
     const int b = P->block, r_max = P->r_max, h = n / 2 + 1;
@@ -854,29 +856,32 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     k_rt_init<<<1, 256, 0, st>>>(w.st, w.partsA, rdft_parts(l, m), w.partsB, rdft_parts(l, 1), P->eps, P->eps_rel, n);
     TRY(launched(TP_KC_MISC, st));
 
+    // all Gaussian slices -> Fourier in one launch (blocks the sketch never
+    // reaches are transformed too; one full launch beats a latency-bound
+    // launch per block)
+    TRY(rdft<T>(Om, w.G, n, m, r_max, r_max, (long)m * r_max, nullptr, nullptr, st));
     const int nblk = (r_max + b - 1) / b;
     for (int blk = 0; blk < nblk; ++blk) {
         const int r0 = blk * b, bb = (b < r_max - r0) ? b : r_max - r0;
-        // Gaussian block -> Fourier, sketch, power iterations, orthonormalise
-        TRY(rdft<T>(Om + r0, w.G, n, m, bb, r_max, (long)m * r_max, nullptr, done, st));
-        TRY(cgemm<T>(h, l, bb, m, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_N, w.G, bb, (long)m * bb, OP_N, 0, 0, w.Y, bb,
-                     (long)l * bb, done, st, &w.st->status));
+        // sketch, power iterations, orthonormalise
+        TRY(cgemm<T>(h, l, bb, m, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_N, w.G + r0, r_max, (long)m * r_max, OP_N, 0, 0,
+                     w.Y, bb, (long)l * bb, done, st, &w.st->status, tc_passes));
         const bool last_y = (P->q_power == 0);
         TRY(orth<T>(h, w.Y, (long)l * bb, l, bb, w.Q, (long)r_max * l, r0, last_y ? w.Q : nullptr, nullptr, 0, 0, 0,
                     nullptr, done, st));
         for (int it = 0; it < P->q_power; ++it) {
             TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, AH, ldah, lm, op_h, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.Z, bb,
-                         (long)m * bb, done, st, &w.st->status));
+                         (long)m * bb, done, st, &w.st->status, tc_passes));
             TRY(orth<T>(h, w.Z, (long)m * bb, m, bb, nullptr, 0, 0, nullptr, nullptr, 0, 0, 0, nullptr, done, st));
             TRY(cgemm<T>(h, l, bb, m, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_N, w.Z, bb, (long)m * bb, OP_N, 0, 0, w.Y, bb,
-                         (long)l * bb, done, st, &w.st->status));
+                         (long)l * bb, done, st, &w.st->status, tc_passes));
             const bool last = (it + 1 == P->q_power);
             TRY(orth<T>(h, w.Y, (long)l * bb, l, bb, w.Q, (long)r_max * l, r0, last ? w.Q : nullptr, nullptr, 0, 0,
                         0, nullptr, done, st));
         }
         // Bt(block)^H = A^H Y; its QR against the earlier columns extends QG and R
         TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, AH, ldah, lm, op_h, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.BHb, bb,
-                     (long)m * bb, done, st, &w.st->status));
+                     (long)m * bb, done, st, &w.st->status, 3));  // the re-projection stays float32-accurate
         TRY(orth<T>(h, w.BHb, (long)m * bb, m, bb, w.QG, (long)r_max * m, r0, w.QG, w.R, r_max,
                     (long)r_max * r_max, r_max, w.normsq, done, st));
         prof_begin(TP_KC_MISC, st);
@@ -924,8 +929,8 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
 template size_t rt_ws_bytes<float>(int, int, int, int, const tp_rtsvd_params*);
 template size_t rt_ws_bytes<double>(int, int, int, int, const tp_rtsvd_params*);
 template tp_status rt_solve<float>(const float*, const float*, const float*, int, int, int, int,
-                                   const tp_rtsvd_params*, float*, tp_info*, void*, size_t, cudaStream_t);
+                                   const tp_rtsvd_params*, float*, tp_info*, void*, size_t, cudaStream_t, int);
 template tp_status rt_solve<double>(const double*, const double*, const double*, int, int, int, int,
-                                    const tp_rtsvd_params*, double*, tp_info*, void*, size_t, cudaStream_t);
+                                    const tp_rtsvd_params*, double*, tp_info*, void*, size_t, cudaStream_t, int);
 
 }  // namespace tp

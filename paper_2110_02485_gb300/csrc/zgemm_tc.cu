@@ -187,16 +187,18 @@ __device__ __forceinline__ float pick4(const float4& v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
 
-// Stage buffers: raw A (TMA), hi A (op C only; op N splits in place), lo A,
-// raw B rows (TMA), and the real right-hand side B_op.
-template <int OPA, int NCP> struct TcCfg {
-    static constexpr int NB = 4 * NCP;                  // B_op rows: (re, im) x (hi, lo)
+// Stage buffers: raw A (TMA), hi A (op C only; op N uses the raw tile), lo A
+// (3xTF32 only), raw B rows (TMA), and the real right-hand side B_op.  NP = 3
+// (hi*hi + hi*lo + lo*hi, float32 accuracy) or 1 (hi*hi, the TF32 precision
+// form).
+template <int OPA, int NCP, int NP> struct TcCfg {
+    static constexpr int NB = (NP == 3 ? 4 : 2) * NCP;  // B_op rows: (re, im) x (hi[, lo])
     static constexpr uint32_t LBO_B = (NB / 8) * 128;
     static constexpr int KB = OPA == OP_N ? TC_KT / 2 : TC_KT;  // B rows per stage
     static constexpr int A_RAW = 0;
     static constexpr int A_HI = OPA == OP_N ? 0 : TC_A_BYTES;
-    static constexpr int A_LO = OPA == OP_N ? TC_A_BYTES : 2 * TC_A_BYTES;
-    static constexpr int B_RAW = A_LO + TC_A_BYTES;
+    static constexpr int A_LO = A_HI + TC_A_BYTES;  // used when NP == 3
+    static constexpr int B_RAW = (NP == 3 ? A_LO : A_HI) + TC_A_BYTES;
     static constexpr int B_RAW_BYTES = KB * NCP * 8;
     static constexpr int B_OP = B_RAW + B_RAW_BYTES;
     static constexpr int STAGE = B_OP + NB * TC_KT * 4;  // a multiple of 1024
@@ -212,20 +214,23 @@ template <int OPA, int NCP> struct TcCfg {
 };
 
 // Split one stage (warps 0-7).  CONJ (op = R): right-hand side signs of conj(A) B.
-template <int OPA, bool CONJ, int NCP>
+template <int OPA, bool CONJ, int NCP, int NP>
 __device__ __forceinline__ void split_stage(unsigned char* st) {
-    typedef TcCfg<OPA, NCP> G;
+    typedef TcCfg<OPA, NCP, NP> G;
     const int t = threadIdx.x;
     const float2* rb = (const float2*)(st + G::B_RAW);
     float* Bs = (float*)(st + G::B_OP);
+    constexpr int RS = (NCP / 8) * TC_SBO;  // rows c, NCP + c, ...: NCP / 8 core matrices apart
     if (OPA == OP_N) {
-        // element-wise on the swizzled tile: hi is the tile itself, lo at the same offset
-        const float4* a = (const float4*)(st + G::A_RAW);
-        float4* alo = (float4*)(st + G::A_LO);
+        if (NP == 3) {
+            // element-wise on the swizzled tile: hi is the tile itself, lo at the same offset
+            const float4* a = (const float4*)(st + G::A_RAW);
+            float4* alo = (float4*)(st + G::A_LO);
 #pragma unroll 4
-        for (int i = t; i < TC_A_BYTES / 16; i += TC_CONV_THREADS) {
-            const float4 v = a[i];
-            alo[i] = make_float4(tf32_rest(v.x), tf32_rest(v.y), tf32_rest(v.z), tf32_rest(v.w));
+            for (int i = t; i < TC_A_BYTES / 16; i += TC_CONV_THREADS) {
+                const float4 v = a[i];
+                alo[i] = make_float4(tf32_rest(v.x), tf32_rest(v.y), tf32_rest(v.z), tf32_rest(v.w));
+            }
         }
         // A B:       re row (Br, -Bi), im row (Bi,  Br)
         // conj(A) B: re row (Br,  Bi), im row (Bi, -Br)
@@ -236,13 +241,13 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
             split3(x.x, rh, rl);
             split3(x.y, ih, il);
             const float sa = CONJ ? 1.f : -1.f, sb = CONJ ? -1.f : 1.f;
-            // rows c, NCP + c, 2 NCP + c, 3 NCP + c: NCP / 8 core matrices apart
             char* p = (char*)Bs + kmaj_off(c, 2 * jj, G::LBO_B);
-            constexpr int RS = (NCP / 8) * TC_SBO;
             *(float2*)(p) = make_float2(rh, sa * ih);
             *(float2*)(p + RS) = make_float2(ih, sb * rh);
-            *(float2*)(p + 2 * RS) = make_float2(rl, sa * il);
-            *(float2*)(p + 3 * RS) = make_float2(il, sb * rl);
+            if (NP == 3) {
+                *(float2*)(p + 2 * RS) = make_float2(rl, sa * il);
+                *(float2*)(p + 3 * RS) = make_float2(il, sb * rl);
+            }
         }
     } else {
         // raw rows i (128 floats each) -> rows (j, re/im) of the K-major tiles, 4 x 4 blocks
@@ -263,7 +268,7 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
                 split3(w, hi, lo);
                 const uint32_t off = kmaj_off(4 * m4 + e, 4 * i4, TC_LBO_A);
                 *(float4*)((char*)Ahi + off) = hi;
-                *(float4*)((char*)Alo + off) = lo;
+                if (NP == 3) *(float4*)((char*)Alo + off) = lo;
             }
         }
         for (int e = t; e < G::KB * NCP; e += TC_CONV_THREADS) {
@@ -273,20 +278,21 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
             split3(x.x, rh, rl);
             split3(x.y, ih, il);
             char* p = (char*)Bs + kmaj_off(c, ii, G::LBO_B);
-            constexpr int RS = (NCP / 8) * TC_SBO;
             *(float*)(p) = rh;
             *(float*)(p + RS) = ih;
-            *(float*)(p + 2 * RS) = rl;
-            *(float*)(p + 3 * RS) = il;
+            if (NP == 3) {
+                *(float*)(p + 2 * RS) = rl;
+                *(float*)(p + 3 * RS) = il;
+            }
         }
     }
 }
 
-template <int OPA, bool CONJ, int NCP>
+template <int OPA, bool CONJ, int NCP, int NP>
 __global__ void __launch_bounds__(TC_THREADS, 2)
 k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            float2* __restrict__ C, long ldc, long sC, int Mc, int Nc, int Kc, const int* skip, int* err) {
-    typedef TcCfg<OPA, NCP> G;
+    typedef TcCfg<OPA, NCP, NP> G;
     if (skip && *skip) return;
     extern __shared__ unsigned char sm_raw[];
     __shared__ __align__(8) uint64_t full[G::NS], conv[G::NS], empty[G::NS], accf;
@@ -362,8 +368,8 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                         dal = sdesc(buf + G::A_LO + ks * 2 * TC_LBO_A, TC_LBO_A, TC_SBO);
                     }
                     const uint64_t db = sdesc(buf + G::B_OP + ks * 2 * G::LBO_B, G::LBO_B, TC_SBO);
-                    mma_tf32(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);  // hi*hi | hi*lo
-                    mma_tf32(tmem, dal, db, id_half, 1u);                            // += lo*hi
+                    mma_tf32(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);  // hi*hi [| hi*lo]
+                    if (NP == 3) mma_tf32(tmem, dal, db, id_half, 1u);              // += lo*hi
                 }
                 mma_commit(smem_u32(&empty[st]));
                 issued = kt + 1;
@@ -379,7 +385,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         for (int kt = 0; kt < nkt; ++kt) {
             const int st = kt % G::NS;
             if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / G::NS) & 1), abort)) break;
-            split_stage<OPA, CONJ, NCP>(sgen + st * G::STAGE);
+            split_stage<OPA, CONJ, NCP, NP>(sgen + st * G::STAGE);
             fence_async_smem();  // generic-proxy writes -> tensor-core reads
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&conv[st]));
@@ -393,12 +399,12 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 // columns c0..c0+7 of the four groups: re (hi*hi + lo*hi), im (...), re (hi*lo), im (hi*lo)
                 float d[4][8];
 #pragma unroll
-                for (int g = 0; g < 4; ++g) tmem_ld8(ta + (uint32_t)(g * NCP + c0), d[g]);
+                for (int g = 0; g < (NP == 3 ? 4 : 2); ++g) tmem_ld8(ta + (uint32_t)(g * NCP + c0), d[g]);
 #pragma unroll
                 for (int cc = 0; cc < 8; ++cc) {
                     const int c = c0 + cc;
-                    const float re = d[0][cc] + d[2][cc];
-                    const float im = d[1][cc] + d[3][cc];
+                    const float re = NP == 3 ? d[0][cc] + d[2][cc] : d[0][cc];
+                    const float im = NP == 3 ? d[1][cc] + d[3][cc] : d[1][cc];
                     if (OPA == OP_N) {
                         if (r < Mr && c < Nc) C[(long)r * ldc + c] = make_float2(re, im);
                     } else {
@@ -450,10 +456,10 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, 
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int OPA, bool CONJ, int NCP>
+template <int OPA, bool CONJ, int NCP, int NP>
 tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, const void* B, long ldb,
                     long sB, void* C, long ldc, long sC, const int* skip, int* err, cudaStream_t st) {
-    typedef TcCfg<OPA, NCP> G;
+    typedef TcCfg<OPA, NCP, NP> G;
     CUtensorMap ma, mb;
     // A: op N rows i of 2K floats (box 32 x 128, swizzled); op C rows i of 2M floats (box 128 x 32)
     const bool oka = OPA == OP_N ? make_map(&ma, A, 2 * (uint64_t)K, M, batch, 8 * (uint64_t)lda,
@@ -463,7 +469,7 @@ tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, lon
     const bool okb =
         make_map(&mb, B, 2 * (uint64_t)N, K, batch, 8 * (uint64_t)ldb, 8 * (uint64_t)sB, 2 * NCP, G::KB, false);
     if (!oka || !okb) return TP_ERR_UNSUPPORTED;
-    auto kern = k_zgemm_tc<OPA, CONJ, NCP>;
+    auto kern = k_zgemm_tc<OPA, CONJ, NCP, NP>;
     if (smem_optin((const void*)kern, G::SMEM) != TP_OK) return TP_ERR_CUDA;
     const int Mr = OPA == OP_N ? M : 2 * M;
     dim3 grid((unsigned)((Mr + TC_M - 1) / TC_M), (unsigned)batch);
@@ -477,25 +483,32 @@ tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, lon
 // Returns TP_ERR_UNSUPPORTED (nothing enqueued) when the shape or alignment
 // does not fit this kernel; the caller then uses the SIMT product.
 tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B, long ldb,
-                   long sB, void* C, long ldc, long sC, const int* skip, int* err, cudaStream_t st) {
+                   long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes, cudaStream_t st) {
     if (opA != OP_N && opA != OP_R && opA != OP_C) return TP_ERR_UNSUPPORTED;
+    if (passes != 1 && passes != 3) return TP_ERR_UNSUPPORTED;
     if (batch < 1 || batch > 65535 || M < 1 || N < 1 || N > 32 || K < 1) return TP_ERR_UNSUPPORTED;
     // tensor maps: 16-byte aligned bases and 16-byte multiples for the row and slice strides
     if ((lda & 1) || (sA & 1) || (ldb & 1) || (sB & 1) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
         return TP_ERR_UNSUPPORTED;
     if ((opA == OP_C ? 2 * M : M) > 65535 * TC_M) return TP_ERR_UNSUPPORTED;
     const int ncp = (N + 7) & ~7;
-#define TC_GO(OP, CJ, NC) launch_tc<OP, CJ, NC>(batch, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, skip, err, st)
-#define TC_SWITCH(OP, CJ)                          \
-    switch (ncp) {                                 \
-        case 8: return TC_GO(OP, CJ, 8);           \
-        case 16: return TC_GO(OP, CJ, 16);         \
-        case 24: return TC_GO(OP, CJ, 24);         \
-        default: return TC_GO(OP, CJ, 32);         \
+#define TC_GO(OP, CJ, NC, P) \
+    launch_tc<OP, CJ, NC, P>(batch, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, skip, err, st)
+#define TC_SWITCH(OP, CJ, P)                          \
+    switch (ncp) {                                    \
+        case 8: return TC_GO(OP, CJ, 8, P);           \
+        case 16: return TC_GO(OP, CJ, 16, P);         \
+        case 24: return TC_GO(OP, CJ, 24, P);         \
+        default: return TC_GO(OP, CJ, 32, P);         \
     }
-    if (opA == OP_N) TC_SWITCH(OP_N, false)
-    if (opA == OP_R) TC_SWITCH(OP_N, true)
-    TC_SWITCH(OP_C, false)
+    if (passes == 3) {
+        if (opA == OP_N) TC_SWITCH(OP_N, false, 3)
+        if (opA == OP_R) TC_SWITCH(OP_N, true, 3)
+        TC_SWITCH(OP_C, false, 3)
+    }
+    if (opA == OP_N) TC_SWITCH(OP_N, false, 1)
+    if (opA == OP_R) TC_SWITCH(OP_N, true, 1)
+    TC_SWITCH(OP_C, false, 1)
 #undef TC_SWITCH
 #undef TC_GO
 }

@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 TP_OK, TP_ERR_ARG, TP_ERR_CUDA, TP_ERR_WORKSPACE = 0, -1, -2, -3
 TP_ERR_BREAKDOWN, TP_ERR_NOT_CONVERGED, TP_ERR_TIMEOUT, TP_ERR_UNSUPPORTED = -4, -5, -6, -7
-TP_FP32, TP_FP64 = 0, 1
+TP_FP32, TP_FP64, TP_TF32 = 0, 1, 2
 
 
 class TpInfo(ctypes.Structure):
@@ -191,8 +191,11 @@ def ifft(Xh: torch.Tensor, n: int) -> torch.Tensor:
     return out
 
 
-def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False) -> torch.Tensor:
-    """t-product op(A) * B.  A (n, l, kk) [or (n, kk, l) with transA], B (n, kk, m)."""
+def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False, tf32: bool = False) -> torch.Tensor:
+    """t-product op(A) * B.  A (n, l, kk) [or (n, kk, l) with transA], B (n, kk, m).
+
+    tf32=True (float32 only): the TP_TF32 precision form (one tf32 product on
+    the tensor cores instead of the float32-accurate split)."""
     _dev(A, B)
     if A.dtype != B.dtype:
         raise TypeError("A and B must share a dtype")
@@ -202,6 +205,10 @@ def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False) -> torch.Tenso
     if nb != n or (a1 if transA else a2) != kk:
         raise ValueError("shape mismatch")
     prec = _prec(A)
+    if tf32:
+        if prec != TP_FP32:
+            raise TypeError("tf32 needs float32 tensors")
+        prec = TP_TF32
     C = torch.empty((n, l, m), dtype=A.dtype, device=A.device)
     L = load()
     ws = _workspace(L.tprod_gemm_workspace_bytes(l, kk, m, n, prec), A.device)
@@ -240,12 +247,19 @@ def _info_buf(device):
 
 
 def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None, eps=0.0, eps_rel=0.0,
-                res_hist=False, sync=True):
-    """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist])."""
+                res_hist=False, sync=True, tf32=False):
+    """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist]).
+
+    tf32=True (float32 only): the TP_TF32 precision form of the block sketch
+    and projection products."""
     _dev(A, B, Omega)
     n, l, m = A.shape
     r_max = min(l, m) if r_max is None else r_max
     prec = _prec(A)
+    if tf32:
+        if prec != TP_FP32:
+            raise TypeError("tf32 needs float32 tensors")
+        prec = TP_TF32
     X = torch.empty((n, m, 1), dtype=A.dtype, device=A.device)
     hist = torch.empty(r_max + 1, dtype=torch.float64, device=A.device) if res_hist else None
     P = RtsvdParams(float(delta), float(tau), float(eps), float(eps_rel), int(p_over), int(q_power), int(block),

@@ -1,0 +1,60 @@
+"""Write n256_oracle.json: the FP64 oracle's results on the 256^3 deblurring
+workload that bench.py times (synth.CONFIGS["n256"], the seed of rank 0), for
+the full-size GPU parity test (tests/test_gpu_full_size.py).
+
+Calls only the oracle and the seeded input generator.  About a minute and a
+half of CPU:
+
+    python tests/golden/make_n256.py
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle as O  # noqa: E402
+from paper_2110_02485_gb300 import synth  # noqa: E402
+
+N_SAMPLES = 1024
+
+
+def sample_index(N: int) -> np.ndarray:
+    """Seeded flat indices into an (N, N, 1) solution (the same on both sides)."""
+    return np.random.default_rng(2024).choice(N * N, size=N_SAMPLES, replace=False)
+
+
+def main() -> None:
+    cfg = synth.CONFIGS["n256"]
+    P = synth.blur_problem(cfg, seed=cfg.seed)
+    A, B, Om = (P[k].astype(np.float64) for k in ("A", "B", "Omega"))
+    idx = sample_index(cfg.N)
+    out = {"config": "n256", "seed": cfg.seed, "delta": P["delta"], "sample_index": idx.tolist()}
+
+    def pack(r, extra):
+        X = r["X"].reshape(-1)
+        d = {"k": int(r["k"]), "status": int(r["status"]), "tau_delta": float(r["tau_delta"]),
+             "x_norm": float(np.linalg.norm(X)),
+             "x_samples": X[idx].tolist()}
+        d.update(extra)
+        return d
+
+    r1 = O.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.eps_rel * np.sqrt(O.fro2(A)), cfg.p_over, cfg.block,
+                       cfg.q_power, cfg.r_max)
+    out["rtsvd"] = pack(r1, {"r": int(r1["r"]), "residual": float(r1["res"][r1["k"]]), "margin": float(r1["margin"]),
+                             "res": {str(k): v for k, v in r1["res"].items()}})
+    r2 = O.tgkb_solve(A, B, P["delta"], cfg.tau, cfg.k_max)
+    out["tgkb"] = pack(r2, {"residual": float(r2["res"][r2["k"]]), "margin": float(r2["margin"]),
+                            "res": {str(k): v for k, v in r2["res"].items()}})
+    r3 = O.tgkt_solve(A, B, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)
+    out["tgkt"] = pack(r3, {"mu": float(r3["mu"]), "residual": float(r3["residual"])})
+    with open(os.path.join(HERE, "n256_oracle.json"), "w") as f:
+        json.dump(out, f)
+    print({m: {k: out[m].get(k) for k in ("k", "status", "margin", "mu")} for m in ("rtsvd", "tgkb", "tgkt")})
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,114 @@
+"""Parity at the full 256^3 bench workload, in the launch configuration that
+bench.py times (the same generator, seed, parameters and float32 path).
+
+The oracle's results on this workload are stored in tests/golden/n256_oracle.json
+by tests/golden/make_n256.py (which calls only the oracle).  The GPU must pick
+the same truncation indices (the stored margins are far from the tie band),
+match the oracle's solution on 1024 seeded sample entries and in norm, and
+report residuals that an independent float64 evaluation of ||B - A*X||
+reproduces.  The TF32 precision form of the RT-tSVD is held to the
+spec bound for the reduced-precision sketch (3e-3 relative).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_02485_gb300 import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def tp():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2110_02485_gb300 import tprod
+    tprod.load()
+    return tprod
+
+
+@pytest.fixture(scope="module")
+def work():
+    with open(os.path.join(HERE, "golden", "n256_oracle.json")) as f:
+        gold = json.load(f)
+    cfg = synth.CONFIGS["n256"]
+    P = synth.blur_problem(cfg, seed=gold["seed"])
+    assert abs(P["delta"] - gold["delta"]) <= 1e-12 * gold["delta"]
+    return cfg, P, gold
+
+
+def dev(x):
+    return torch.from_numpy(x).cuda()
+
+
+def sample_err(X, ref, idx):
+    """Largest sampled deviation, relative to the largest sampled entry."""
+    x = X.reshape(-1)[np.asarray(idx)]
+    r = np.asarray(ref["x_samples"])
+    return float(np.max(np.abs(x - r)) / np.max(np.abs(r)))
+
+
+def true_residual(P, X):
+    """||B - A*X||_F in float64 from the float32 inputs (independent of the GPU)."""
+    A, B = P["A"].astype(np.float64), P["B"].astype(np.float64)
+    return float(np.sqrt(O.fro2(B - O.tprod(A, X.astype(np.float64)))))
+
+
+def check(info, X, ref, P, idx, tol_x):
+    assert info["k"] == ref["k"]
+    assert info["status"] == ref["status"] == 0
+    assert sample_err(X, ref, idx) <= tol_x
+    assert abs(np.linalg.norm(X) - ref["x_norm"]) <= tol_x * ref["x_norm"]
+    res = true_residual(P, X)
+    assert res <= ref["tau_delta"] * (1 + 1e-4)             # the discrepancy principle holds
+    assert abs(info["residual"] - res) <= 1e-4 * res         # and the reported residual is the true one
+
+
+def test_rtsvd_n256(tp, work):
+    cfg, P, gold = work
+    ref = gold["rtsvd"]
+    assert ref["margin"] > 1e-3
+    X, info = tp.rtsvd_solve(dev(P["A"]), dev(P["B"]), dev(P["Omega"]), P["delta"], cfg.tau, cfg.p_over, cfg.block,
+                             cfg.q_power, cfg.r_max, eps_rel=cfg.eps_rel)
+    X = X.cpu().numpy()
+    assert info["r"] == ref["r"]
+    check(info, X, ref, P, gold["sample_index"], 2e-4)
+
+
+def test_rtsvd_n256_tf32_form(tp, work):
+    cfg, P, gold = work
+    ref = gold["rtsvd"]
+    X, info = tp.rtsvd_solve(dev(P["A"]), dev(P["B"]), dev(P["Omega"]), P["delta"], cfg.tau, cfg.p_over, cfg.block,
+                             cfg.q_power, cfg.r_max, eps_rel=cfg.eps_rel, tf32=True)
+    X = X.cpu().numpy()
+    assert info["status"] == 0
+    assert sample_err(X, ref, gold["sample_index"]) <= 3e-3
+    assert abs(np.linalg.norm(X) - ref["x_norm"]) <= 3e-3 * ref["x_norm"]
+    assert true_residual(P, X) <= ref["tau_delta"] * (1 + 1e-3)
+
+
+def test_tgkb_n256(tp, work):
+    cfg, P, gold = work
+    ref = gold["tgkb"]
+    assert ref["margin"] > 1e-3
+    X, info = tp.tgkb_solve(dev(P["A"]), dev(P["B"]), P["delta"], cfg.tau, cfg.k_max)
+    check(info, X.cpu().numpy(), ref, P, gold["sample_index"], 1e-4)
+
+
+def test_tgkt_n256(tp, work):
+    cfg, P, gold = work
+    ref = gold["tgkt"]
+    X, info = tp.tgkt_solve(dev(P["A"]), dev(P["B"]), P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)
+    X = X.cpu().numpy()
+    assert info["k"] == ref["k"] and info["status"] == ref["status"] == 0
+    assert abs(np.log10(info["mu"]) - np.log10(ref["mu"])) <= 1e-3
+    assert sample_err(X, ref, gold["sample_index"]) <= 1e-4
+    res = true_residual(P, X)
+    assert abs(res - ref["tau_delta"]) <= 1e-3 * ref["tau_delta"]   # mu puts the residual on tau*delta

@@ -109,6 +109,23 @@ def test_tprod_tensor_core_shapes(tp, n, l, kk, m, trans):
     assert rel(C, ref) <= 5e-6 * np.sqrt(kk)
 
 
+@pytest.mark.parametrize("n,l,kk,m,trans", [(8, 256, 256, 16, 0), (5, 100, 62, 8, 1), (4, 130, 40, 24, 0)])
+def test_tprod_tf32_form(tp, n, l, kk, m, trans):
+    """TP_TF32 (one tf32 product on the tensor cores): error at the tf32 level
+    (inputs rounded to 10 mantissa bits), inside 2e-3, and well above the
+    float32 form's on the same inputs, so the form is really in effect."""
+    A = rnd((n, kk, l) if trans else (n, l, kk), 50 + n)
+    B = rnd((n, kk, m), 60 + n)
+    Ad = dev(A, torch.float32).cpu().double().numpy()
+    Bd = dev(B, torch.float32).cpu().double().numpy()
+    ref = O.tprod(O.ttranspose(Ad) if trans else Ad, Bd)
+    c32 = tp.tprod(dev(A, torch.float32), dev(B, torch.float32), transA=bool(trans)).cpu().numpy()
+    ctf = tp.tprod(dev(A, torch.float32), dev(B, torch.float32), transA=bool(trans), tf32=True).cpu().numpy()
+    e32, etf = rel(c32, ref), rel(ctf, ref)
+    assert etf <= 2e-3
+    assert etf > 10 * e32
+
+
 # --------------------------------------------------------------- solvers ----
 
 def problem(N, n=None, seed=5, noise=1e-2, general=0.02, l=None):
