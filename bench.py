@@ -70,6 +70,7 @@ def args_():
     p.add_argument("--config", default="n256")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-precision", action="store_true", help="skip the TF32-vs-FP32 RT-tSVD comparison")
     return p.parse_args()
 
 
@@ -267,6 +268,12 @@ def run_ours(a, rank, world, local):
         e2e = {"value": world * SOLVES_PER_STEP * a.steps / (ms2 / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # precision form: RT-tSVD alone, float32 vs TF32 sketch, device time and
+    # error against the oracle's stored solution samples for this workload
+    prec_form = None
+    if not a.no_precision and rank == 0:
+        prec_form = precision_form(a, cfg, P, A, B, Om, flush, tprod, torch)
+
     hbm, bf16, src = peaks()
     work = class_work(cfg, infos)
     roof = None
@@ -295,6 +302,7 @@ def run_ours(a, rank, world, local):
                       "N": cfg.N, "solves_per_step": SOLVES_PER_STEP, "l2": "flushed between steps (512 MB write)",
                       "parallelism": f"replicas x{world}"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+           "precision_form": prec_form,
            "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
            "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
                           "tgkb": {k: infos[1][k] for k in ("k", "status")},
@@ -306,6 +314,47 @@ def run_ours(a, rank, world, local):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
+    """RT-tSVD solves/s with the float32 and the TF32 sketch on the same
+    workload (L2 flushed between solves, CUDA events), with each solution's
+    sampled error against the oracle's (tests/golden/n256_oracle.json, written
+    by an oracle-only script; read, not run)."""
+    gold_path = os.path.join(ROOT, "tests", "golden", f"{cfg.name}_oracle.json")
+    gold = None
+    if os.path.exists(gold_path):
+        with open(gold_path) as f:
+            gold = json.load(f)
+    out = {}
+    reps = max(3, min(a.steps, 20))
+    for name, tf32 in (("fp32", False), ("tf32", True)):
+        def solve():
+            return tprod.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                                     eps_rel=cfg.eps_rel, sync=False, tf32=tf32)
+        for _ in range(2):
+            solve()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            X, info, _ = solve()
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        info = tprod._info_dict(info)
+        rec = {"solves_per_s": reps / (ms / 1e3), "ms_per_solve": ms / reps, "k": info["k"], "r": info["r"]}
+        if gold is not None:
+            x = X.cpu().numpy().reshape(-1)[np.asarray(gold["sample_index"])]
+            ref = np.asarray(gold["rtsvd"]["x_samples"])
+            rec["rel_err_vs_oracle_samples"] = float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+            rec["k_matches_oracle"] = info["k"] == gold["rtsvd"]["k"]
+        out[name] = rec
+    out["note"] = ("TF32: sketch and power-iteration products with one tf32 tensor-core product; "
+                   "re-projection and the rest float32")
+    return out
 
 
 def oracle_solve(method, cfg, P):

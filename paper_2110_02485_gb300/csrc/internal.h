@@ -61,10 +61,12 @@ tp_status cgemm(int batch, int M, int N, int K, const int* dM, const int* dN, co
 
 // Tensor-core complex product C[s] = op(A[s]) B[s] (op = N, R or C), float32
 // data, passes 3 or 1; TP_ERR_UNSUPPORTED (nothing enqueued) when the shape
-// does not fit.
+// does not fit.  trans_out (op N / R): write C^T (C[c * ldc + row]).  ncap
+// (optional, device) with c0: the launch does nothing when c0 >= *ncap (a
+// column chunk past a run-time column count; B and C already offset by c0).
 tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B,
                    long ldb, long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes,
-                   cudaStream_t st);
+                   cudaStream_t st, int trans_out = 0, const int* ncap = nullptr, int c0 = 0);
 
 // Device-side bookkeeping shared by a solve.
 struct State {

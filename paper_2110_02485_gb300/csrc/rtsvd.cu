@@ -169,7 +169,8 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
     T y2p = 0;
     for (int e = tid; e < L * BB; e += blockDim.x) y2p += cabs2(Ys[e]);
     const double y2 = block_sum_t(y2p, red);  // its barriers also publish `passes`
-    const double shift = 11.0 * ((double)L * b + (double)b * (b + 1)) * Eps<T>::v * y2;
+    // the Cholesky warp alone needs the shift (float64 arithmetic is slow here)
+    const double shift = warp == 0 ? 11.0 * ((double)L * b + (double)b * (b + 1)) * Eps<T>::v * y2 : 0.0;
     for (int pass = 0; pass < passes; ++pass) {
         // Gram matrix (upper triangle incl. diagonal)
         for (int p = warp; p < BB * BB; p += NW) {
@@ -219,7 +220,8 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                     const int mrem = BB - k - 1;
                     for (int pi = lane; pi < mrem * mrem; pi += 32) {
                         const int i = k + 1 + pi / mrem, jj = k + 1 + pi % mrem;
-                        if (jj >= i) G[i * BB + jj] = csub(G[i * BB + jj], cmul(cconj(Rk[k * BB + i]), Rk[k * BB + jj]));
+                        if (jj >= i)
+                            G[i * BB + jj] = csub(G[i * BB + jj], cmul(cconj(Rk[k * BB + i]), Rk[k * BB + jj]));
                     }
                     __syncwarp();
                 }
@@ -229,20 +231,11 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                     passes += 1;
                 }
             }
-            // Ra <- Rk * Ra when the in-block R is an output (entries spread over lanes)
-            if (R) {
-                for (int e = lane; e < BB * BB; e += 32) {
-                    const int i = e / BB, jj = e - i * BB;
-                    V acc = mk<T>(0, 0);
-                    for (int t = i; t <= jj; ++t) cfma(acc, Rk[i * BB + t], Ra[t * BB + jj]);
-                    Rt[e] = (i <= jj) ? acc : mk<T>(0, 0);
-                }
-                __syncwarp();
-                for (int e = lane; e < BB * BB; e += 32) Ra[e] = Rt[e];
-            }
         }
         __syncthreads();
-        // Y <- Y R^{-1}: per row, forward substitution (diagonal reciprocals precomputed)
+        // Y <- Y R^{-1}: per row, forward substitution (diagonal reciprocals
+        // precomputed); the threads beyond the rows meanwhile form the
+        // accumulated in-block R' = Rk Ra when R is an output
         for (int row = tid; row < L; row += blockDim.x) {
             V x[BB];
 #pragma unroll
@@ -255,7 +248,21 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
 #pragma unroll
             for (int jj = 0; jj < BB; ++jj) Ys[jj * L + row] = x[jj];
         }
+        if (R) {
+            const int nthr = (int)blockDim.x, t0 = L < nthr ? L : 0;  // threads idle in the solve when L < blockDim
+            for (int e = tid - t0; e >= 0 && e < BB * BB; e += nthr - t0) {
+                const int i = e / BB, jj = e - i * BB;
+                V acc = mk<T>(0, 0);
+                for (int t = i; t <= jj; ++t) cfma(acc, Rk[i * BB + t], Ra[t * BB + jj]);
+                Rt[e] = (i <= jj) ? acc : mk<T>(0, 0);
+            }
+        }
         __syncthreads();
+        if (R) {  // the product becomes the accumulated R (swap the two buffers)
+            V* tmp = Ra;
+            Ra = Rt;
+            Rt = tmp;
+        }
     }
 
     for (int e = tid; e < L * b; e += blockDim.x) {
@@ -458,38 +465,66 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 
 // Float32 sweeps with the two columns of a pair held in registers (r <= 16
 // EPL): the Gram entries and the rotation read and write shared memory once
-// per element, the rotation parameters come from Newton-refined reciprocal
-// square roots (c^2 + s^2 = 1 to about an ulp), and the per-round "any
-// rotation" flag rides on the round's barrier.
-template <int EPL>
+// per element (as 16-byte pairs of entries when r is even), the rotation
+// parameters come from Newton-refined reciprocal square roots (c^2 + s^2 = 1
+// to about an ulp), the pair indices of the round-robin ordering advance by
+// one per round (no integer division), and the per-round "any rotation" flag
+// rides on the round's barrier.
+template <int EPL, bool V2>
 __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int r, int max_sweeps, float tol) {
     __shared__ int max_off2;  // bit pattern of the largest (|g|^2 / (a b)) of a sweep
     const int tid = threadIdx.x, lane = tid & 31, hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
-    const int rr = r + (r & 1);
+    const int rr = r + (r & 1), npair = rr / 2;
     const float tol2 = tol * tol;
+    // element e of this lane: index hl + 16 e, or with pairs (V2) 2 (hl + 16 (e / 2)) + e % 2
+    auto idx = [&](int e) { return V2 ? 2 * (hl + 16 * (e >> 1)) + (e & 1) : hl + 16 * e; };
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (tid == 0) max_off2 = 0;
         int any = 0;
         float mo2 = 0.f;
-        for (int t = 0; t < rr - 1; ++t) {
-            for (int base = 0; base < rr / 2; base += nslots) {
-                int p, q;
-                const bool valid = rr_pair(t, base + slot, rr, r, p, q);
+        for (int base = 0; base < npair; base += nslots) {
+            const int kp = base + slot;
+            // round 0 of slot kp: (0, 1) for kp = 0, else (1 + kp, 1 + (rr - 1 - kp) % (rr - 1))
+            int pa = kp == 0 ? 0 : 1 + kp;
+            int pb = kp == 0 ? 1 : 1 + (rr - 1 - kp);
+            if (pa > rr - 1) pa -= rr - 1;
+            if (pb > rr - 1) pb -= rr - 1;
+            for (int t = 0; t < rr - 1; ++t) {
+                const int p = min(pa, pb), q = max(pa, pb);
+                const bool valid = kp < npair && q < r && p != q;
                 float2* cp = Rs + (size_t)p * r;
                 float2* cq = Rs + (size_t)q * r;
                 float2 x[EPL], y[EPL];
+                if (V2) {
+#pragma unroll
+                    for (int v = 0; v < EPL / 2; ++v) {
+                        const int i = 2 * (hl + 16 * v);
+                        float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), yv = xv;
+                        if (valid && i < r) {
+                            xv = *(const float4*)(cp + i);
+                            yv = *(const float4*)(cq + i);
+                        }
+                        x[2 * v] = make_float2(xv.x, xv.y);
+                        x[2 * v + 1] = make_float2(xv.z, xv.w);
+                        y[2 * v] = make_float2(yv.x, yv.y);
+                        y[2 * v + 1] = make_float2(yv.z, yv.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        const int i = idx(e);
+                        x[e] = y[e] = make_float2(0.f, 0.f);
+                        if (valid && i < r) {
+                            x[e] = cp[i];
+                            y[e] = cq[i];
+                        }
+                    }
+                }
                 float a = 0.f, b = 0.f;
                 float2 g = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int e = 0; e < EPL; ++e) {
-                    const int i = hl + 16 * e;
-                    if (valid && i < r) {
-                        x[e] = cp[i];
-                        y[e] = cq[i];
-                    } else {
-                        x[e] = y[e] = make_float2(0.f, 0.f);
-                    }
                     a = fmaf(x[e].x, x[e].x, fmaf(x[e].y, x[e].y, a));
                     b = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, b));
                     cfmac(g, x[e], y[e]);
@@ -510,13 +545,32 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int r, int max_sweeps, 
                     const float zeta = (b - a) * 0.5f * rg;
                     const float tt = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
                     const float c = rsqrt_nr(fmaf(tt, tt, 1.f)), sn = c * tt;
+                    float2 xn[EPL], yn[EPL];
 #pragma unroll
                     for (int e = 0; e < EPL; ++e) {
-                        const int i = hl + 16 * e;
-                        if (i < r) {
-                            const float2 ey = cmul(ec, y[e]);
-                            cp[i] = make_float2(c * x[e].x - sn * ey.x, c * x[e].y - sn * ey.y);
-                            cq[i] = make_float2(sn * x[e].x + c * ey.x, sn * x[e].y + c * ey.y);
+                        const float2 ey = cmul(ec, y[e]);
+                        xn[e] = make_float2(c * x[e].x - sn * ey.x, c * x[e].y - sn * ey.y);
+                        yn[e] = make_float2(sn * x[e].x + c * ey.x, sn * x[e].y + c * ey.y);
+                    }
+                    if (V2) {
+#pragma unroll
+                        for (int v = 0; v < EPL / 2; ++v) {
+                            const int i = 2 * (hl + 16 * v);
+                            if (i < r) {
+                                *(float4*)(cp + i) = make_float4(xn[2 * v].x, xn[2 * v].y, xn[2 * v + 1].x,
+                                                                 xn[2 * v + 1].y);
+                                *(float4*)(cq + i) = make_float4(yn[2 * v].x, yn[2 * v].y, yn[2 * v + 1].x,
+                                                                 yn[2 * v + 1].y);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const int i = idx(e);
+                            if (i < r) {
+                                cp[i] = xn[e];
+                                cq[i] = yn[e];
+                            }
                         }
                     }
                     if (hl == 0) {
@@ -527,8 +581,11 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int r, int max_sweeps, 
                     }
                 }
                 any |= rot ? 1 : 0;
+                any = __syncthreads_or(any);
+                // next round: both indices of a slot advance by one (kp = 0 keeps p = 0)
+                if (kp != 0) pa = pa == rr - 1 ? 1 : pa + 1;
+                pb = pb == rr - 1 ? 1 : pb + 1;
             }
-            any = __syncthreads_or(any);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mo2 = fmaxf(mo2, __shfl_xor_sync(0xffffffffu, mo2, o));
@@ -549,9 +606,13 @@ template <typename T> struct JacobiSweeps {
 };
 template <> struct JacobiSweeps<float> {
     static __device__ int run(float2* Rs, float2* dp, int r, int max_sweeps, float tol) {
-        if (r <= 64) return jacobi_sweeps_reg<4>(Rs, dp, r, max_sweeps, tol);
-        if (r <= 96) return jacobi_sweeps_reg<6>(Rs, dp, r, max_sweeps, tol);
-        if (r <= 128) return jacobi_sweeps_reg<8>(Rs, dp, r, max_sweeps, tol);
+        const bool v2 = (r & 1) == 0;  // 16-byte pairs of entries need an even column length
+        if (r <= 64) return v2 ? jacobi_sweeps_reg<4, true>(Rs, dp, r, max_sweeps, tol)
+                               : jacobi_sweeps_reg<4, false>(Rs, dp, r, max_sweeps, tol);
+        if (r <= 96) return v2 ? jacobi_sweeps_reg<6, true>(Rs, dp, r, max_sweeps, tol)
+                               : jacobi_sweeps_reg<6, false>(Rs, dp, r, max_sweeps, tol);
+        if (r <= 128) return v2 ? jacobi_sweeps_reg<8, true>(Rs, dp, r, max_sweeps, tol)
+                                : jacobi_sweeps_reg<8, false>(Rs, dp, r, max_sweeps, tol);
         return jacobi_sweeps_smem<float>(Rs, dp, r, max_sweeps, tol);
     }
 };
@@ -567,7 +628,7 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     extern __shared__ __align__(16) unsigned char smraw[];
     V* Rs = (V*)smraw;                       // column j at Rs[j*r]
     V* dp = Rs + (size_t)r * r;
-    double* sg = (double*)(dp + r);
+    T* sg = (T*)(dp + r);  // column norms (sigma), working precision
     int* perm = (int*)(sg + r);
     __shared__ T tol_s;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -581,31 +642,31 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     __syncthreads();
     const int sweep = JacobiSweeps<T>::run(Rs, dp, r, max_sweeps, tol_s);
     for (int j = warp; j < r; j += nw) {
-        double a = 0.0;
-        for (int i = lane; i < r; i += 32) a += cabs2d(Rs[(size_t)j * r + i]);
+        T a = 0;  // column norms in the working precision (float64 only on lane 0)
+        for (int i = lane; i < r; i += 32) a += cabs2(Rs[(size_t)j * r + i]);
         a = warp_sum(a);
         if (lane == 0) sg[j] = sqrt(a);
     }
     __syncthreads();
     for (int j = tid; j < r; j += blockDim.x) {
         int rank = 0;
-        const double v = sg[j];
+        const T v = sg[j];
         for (int i = 0; i < r; ++i) rank += (sg[i] > v) || (sg[i] == v && i < j);
         perm[rank] = j;
     }
     __syncthreads();
     for (int jr = tid; jr < r; jr += blockDim.x) {
         const int j = perm[jr];
-        sigma[(long)s * ssig + jr] = (T)sg[j];
+        sigma[(long)s * ssig + jr] = sg[j];
         dprime[(long)s * sdp + jr] = dp[j];
     }
     V* U = UR + (long)s * sU;
     for (int e = tid; e < r * r; e += blockDim.x) {
         const int i = e / r, jr = e - i * r;
         const int j = perm[jr];
-        const double sv = sg[j];
+        const T sv = sg[j];
         const V x = Rs[(size_t)j * r + i];
-        U[(long)i * ldu + jr] = sv > 0.0 ? mk<T>((T)(x.x / sv), (T)(x.y / sv)) : mk<T>(0, 0);
+        U[(long)i * ldu + jr] = sv > (T)0 ? cscale(x, (T)1 / sv) : mk<T>(0, 0);
     }
     if (tid == 0) atomicMax(sweeps_out, sweep);
 }
@@ -647,43 +708,47 @@ __global__ void k_alpha(const T* sigma, long ssig, const cplx<T>* dprime, long s
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_dp_scan(const cplx<T>* __restrict__ KhT, long sK, const cplx<T>* __restrict__ alpha, long sa,
-          const cplx<T>* __restrict__ bhat, long sb, const State* st, int l, double* out, long so) {
+          const cplx<T>* __restrict__ bhat, long sb, const State* st, int l, int p_over, double* out, long so) {
+    // Residual b - sum_{j<k} K_j alpha_j of one slice for every k; its squared
+    // norm is formed only for the candidates k >= k_init = max(1, r - p) (the
+    // others are written as 0): per thread and per warp in the working
+    // precision, across warps in float64.
     typedef cplx<T> V;
     constexpr int RPT = 4;  // rows per thread (l <= 1024)
     extern __shared__ __align__(16) unsigned char smraw[];
     double* wsum = (double*)smraw;  // [8][r+1]
     const int r = st->r, s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
+    const int k_init = max(1, r - p_over);
     KhT += (long)s * sK;
     V res[RPT];
-    double part = 0.0;
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
         const int i = tid + u * blockDim.x;
         res[u] = (i < l) ? bhat[(long)s * sb + i] : mk<T>(0, 0);
-        part += cabs2d(res[u]);
     }
-    part = warp_sum(part);
-    if (lane == 0) wsum[warp * (r + 1)] = part;
-    for (int j = 0; j < r; ++j) {
-        const V a = alpha[(long)s * sa + j];
-        part = 0.0;
+    for (int j = 0; j <= r; ++j) {
+        if (j > 0) {
+            const V a = alpha[(long)s * sa + j - 1];
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            const int i = tid + u * blockDim.x;
-            if (i < l) {
-                const V kv = KhT[(long)j * l + i];
-                res[u] = csub(res[u], cmul(kv, a));
-                part += cabs2d(res[u]);
+            for (int u = 0; u < RPT; ++u) {
+                const int i = tid + u * blockDim.x;
+                if (i < l) res[u] = csub(res[u], cmul(KhT[(long)(j - 1) * l + i], a));
             }
         }
-        part = warp_sum(part);
-        if (lane == 0) wsum[warp * (r + 1) + j + 1] = part;
+        if (j >= k_init) {
+            T part = 0;
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) part += cabs2(res[u]);
+            part = warp_sum(part);
+            if (lane == 0) wsum[warp * (r + 1) + j] = (double)part;
+        }
     }
     __syncthreads();
     for (int j = tid; j <= r; j += blockDim.x) {
         double a = 0.0;
-        for (int w = 0; w < nw; ++w) a += wsum[w * (r + 1) + j];
+        if (j >= k_init)
+            for (int w = 0; w < nw; ++w) a += wsum[w * (r + 1) + j];
         out[(long)s * so + j] = a;
     }
 }
@@ -694,14 +759,14 @@ __global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st,
                             tp_info* info, double* res_hist, int r_max) {
     extern __shared__ double res[];
     const int r = st->r;
-    for (int k = threadIdx.x; k <= r; k += blockDim.x) {
+    const int k_init = max(1, r - p_over);  // only the candidates k_init..r are needed
+    for (int k = k_init + threadIdx.x; k <= r; k += blockDim.x) {
         double a = 0.0;
         for (int s = 0; s < h; ++s) a += parseval_w(s, n) * out[(long)s * so + k];
         res[k] = sqrt(fmax(a, 0.0) / (double)n);
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    const int k_init = max(1, r - p_over);
     int k = r, status = TP_ERR_NOT_CONVERGED;
     for (int j = k_init; j <= r; ++j)
         if (res[j] <= tau_delta) {
@@ -907,13 +972,28 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     // V = QG^T-as-matrix * U_R ;  K^T = V^T A^T (vector-major K = A V)
     TRY(cgemm<T>(h, m, r_max, r_max, 0, dr, dr, 1, 0, w.QG, m, (long)r_max * m, OP_T, w.UR, r_max,
                  (long)r_max * r_max, OP_N, 0, 0, w.Vt, r_max, (long)m * r_max, nullptr, st));
-    TRY(cgemm<T>(h, r_max, l, m, dr, 0, 0, 1, 0, w.Vt, r_max, (long)m * r_max, OP_T, w.Ahat, m, lm, OP_T, 0, 0,
-                 w.KhT, l, (long)r_max * l, nullptr, st));
+    // float32: K = A-hat V on the tensor cores in column chunks of 32, written
+    // transposed; chunks past the sketch rank r are skipped on the device
+    bool k_done = false;
+    if (sizeof(T) == 4) {
+        tp_status e = TP_OK;
+        for (int c0 = 0; c0 < r_max && e == TP_OK; c0 += 32) {
+            const int nc = r_max - c0 < 32 ? r_max - c0 : 32;
+            e = zgemm_tc(h, l, nc, m, w.Ahat, m, lm, OP_N, w.Vt + c0, r_max, (long)m * r_max, w.KhT + (long)c0 * l,
+                         l, (long)r_max * l, nullptr, &w.st->status, 3, st, 1, dr, c0);
+            if (c0 == 0 && e == TP_ERR_UNSUPPORTED) break;  // shape not taken: the SIMT product below
+            TRY(e);
+            k_done = e == TP_OK;
+        }
+    }
+    if (!k_done)
+        TRY(cgemm<T>(h, r_max, l, m, dr, 0, 0, 1, 0, w.Vt, r_max, (long)m * r_max, OP_T, w.Ahat, m, lm, OP_T, 0, 0,
+                     w.KhT, l, (long)r_max * l, nullptr, st));
     {
         const size_t smem = (size_t)(256 / 32) * (r_max + 1) * sizeof(double);
         prof_begin(TP_KC_DP, st);
-        k_dp_scan<T><<<h, 256, smem, st>>>(w.KhT, (long)r_max * l, w.alpha, r_max, w.Bhat, l, w.st, l, w.dpout,
-                                           r_max + 1);
+        k_dp_scan<T><<<h, 256, smem, st>>>(w.KhT, (long)r_max * l, w.alpha, r_max, w.Bhat, l, w.st, l, P->p_over,
+                                           w.dpout, r_max + 1);
         TRY(launched(TP_KC_DP, st));
     }
     prof_begin(TP_KC_DP, st);

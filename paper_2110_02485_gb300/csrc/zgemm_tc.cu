@@ -291,9 +291,11 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
 template <int OPA, bool CONJ, int NCP, int NP>
 __global__ void __launch_bounds__(TC_THREADS, 2)
 k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-           float2* __restrict__ C, long ldc, long sC, int Mc, int Nc, int Kc, const int* skip, int* err) {
+           float2* __restrict__ C, long ldc, long sC, int Mc, int Nc, int Kc, const int* skip, int* err,
+           int trans_out, const int* ncap, int c0) {
     typedef TcCfg<OPA, NCP, NP> G;
     if (skip && *skip) return;
+    if (ncap && c0 >= *ncap) return;  // a column chunk past the run-time column count
     extern __shared__ unsigned char sm_raw[];
     __shared__ __align__(8) uint64_t full[G::NS], conv[G::NS], empty[G::NS], accf;
     __shared__ uint32_t tmem_s;
@@ -406,7 +408,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     const float re = NP == 3 ? d[0][cc] + d[2][cc] : d[0][cc];
                     const float im = NP == 3 ? d[1][cc] + d[3][cc] : d[1][cc];
                     if (OPA == OP_N) {
-                        if (r < Mr && c < Nc) C[(long)r * ldc + c] = make_float2(re, im);
+                        if (r < Mr && c < Nc) C[trans_out ? (long)c * ldc + r : (long)r * ldc + c] = make_float2(re, im);
                     } else {
                         // rows 2j (re of A) and 2j+1 (im of A) sit in neighbouring lanes
                         const float pim = __shfl_xor_sync(0xffffffffu, im, 1);
@@ -458,7 +460,8 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, 
 
 template <int OPA, bool CONJ, int NCP, int NP>
 tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, const void* B, long ldb,
-                    long sB, void* C, long ldc, long sC, const int* skip, int* err, cudaStream_t st) {
+                    long sB, void* C, long ldc, long sC, const int* skip, int* err, int trans_out, const int* ncap,
+                    int c0, cudaStream_t st) {
     typedef TcCfg<OPA, NCP, NP> G;
     CUtensorMap ma, mb;
     // A: op N rows i of 2K floats (box 32 x 128, swizzled); op C rows i of 2M floats (box 128 x 32)
@@ -474,7 +477,7 @@ tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, lon
     const int Mr = OPA == OP_N ? M : 2 * M;
     dim3 grid((unsigned)((Mr + TC_M - 1) / TC_M), (unsigned)batch);
     prof_begin(TP_KC_GEMM, st);
-    kern<<<grid, TC_THREADS, G::SMEM, st>>>(ma, mb, (float2*)C, ldc, sC, M, N, K, skip, err);
+    kern<<<grid, TC_THREADS, G::SMEM, st>>>(ma, mb, (float2*)C, ldc, sC, M, N, K, skip, err, trans_out, ncap, c0);
     return launched(TP_KC_GEMM, st);
 }
 
@@ -483,17 +486,20 @@ tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, lon
 // Returns TP_ERR_UNSUPPORTED (nothing enqueued) when the shape or alignment
 // does not fit this kernel; the caller then uses the SIMT product.
 tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B, long ldb,
-                   long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes, cudaStream_t st) {
+                   long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes, cudaStream_t st,
+                   int trans_out, const int* ncap, int c0) {
     if (opA != OP_N && opA != OP_R && opA != OP_C) return TP_ERR_UNSUPPORTED;
     if (passes != 1 && passes != 3) return TP_ERR_UNSUPPORTED;
+    if (trans_out && opA == OP_C) return TP_ERR_UNSUPPORTED;
     if (batch < 1 || batch > 65535 || M < 1 || N < 1 || N > 32 || K < 1) return TP_ERR_UNSUPPORTED;
     // tensor maps: 16-byte aligned bases and 16-byte multiples for the row and slice strides
     if ((lda & 1) || (sA & 1) || (ldb & 1) || (sB & 1) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
         return TP_ERR_UNSUPPORTED;
     if ((opA == OP_C ? 2 * M : M) > 65535 * TC_M) return TP_ERR_UNSUPPORTED;
     const int ncp = (N + 7) & ~7;
-#define TC_GO(OP, CJ, NC, P) \
-    launch_tc<OP, CJ, NC, P>(batch, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, skip, err, st)
+#define TC_GO(OP, CJ, NC, P)                                                                                  \
+    launch_tc<OP, CJ, NC, P>(batch, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, skip, err, trans_out, ncap, \
+                             c0, st)
 #define TC_SWITCH(OP, CJ, P)                          \
     switch (ncp) {                                    \
         case 8: return TC_GO(OP, CJ, 8, P);           \
