@@ -234,7 +234,8 @@ __device__ void mv_n_vec(const cplx<T>* __restrict__ A, int l, int m, const cplx
         V acc[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) acc[r] = mk<T>(0, 0);
-        for (int cv = lane; cv < mv; cv += 32) {
+#pragma unroll 2
+        for (int cv = lane; cv < mv; cv += 32) {  // two iterations' loads in flight
             V wv[VW];
 #pragma unroll
             for (int v = 0; v < VW; ++v) wv[v] = w[cv * VW + v];
@@ -269,11 +270,19 @@ __device__ __forceinline__ const cplx<T>* bvec(const cplx<T>* sb, const cplx<T>*
 }
 
 template <typename T>
-__device__ void reorth2(cplx<T>* u, const cplx<T>* sb, const cplx<T>* __restrict__ gb, int kc, int cnt, int L,
-                        cplx<T>* cf, cplx<T>* part) {
+__device__ decltype(cplx<T>().x) reorth2(cplx<T>* u, const cplx<T>* sb, const cplx<T>* __restrict__ gb, int kc,
+                                         int cnt, int L, cplx<T>* cf, cplx<T>* part) {
+    // Returns this thread's partial sum of |u_e|^2 over its entries
+    // e = threadIdx.x + j blockDim.x of the result (for normalize_into); the
+    // last update is not followed by a barrier.
     typedef cplx<T> V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, NT = blockDim.x;
-    if (cnt <= 0) return;
+    if (cnt <= 0) {
+        T p = 0;
+        for (int e = threadIdx.x; e < L; e += NT) p += cabs2(u[e]);
+        return p;
+    }
+    T p = 0;
     for (int pass = 0; pass < 2; ++pass) {
         for (int i = warp; i < cnt; i += nw) {
             const V* bv = bvec<T>(sb, gb, kc, i, L);
@@ -310,13 +319,64 @@ __device__ void reorth2(cplx<T>* u, const cplx<T>* sb, const cplx<T>* __restrict
             part[g * L + e] = acc;
         }
         __syncthreads();
+        p = 0;
         for (int e = threadIdx.x; e < L; e += NT) {
             V t = u[e];
             for (int g = 0; g < G; ++g) t = csub(t, part[g * L + e]);
             u[e] = t;
+            p += cabs2(t);
         }
-        __syncthreads();
+        if (pass == 0) __syncthreads();
     }
+    return p;
+}
+
+// Normalize u (length L, shared) given each thread's partial sum of squares
+// over its entries e = threadIdx.x + j blockDim.x (as reorth2 returns it):
+// writes u / ||u|| to dst (shared) and, if given, dstg (global), and returns
+// ||u|| in the working precision; a zero vector gives zeros and norm 0.  One
+// thread forms the norm and its reciprocal (float64 only when the
+// working-precision reciprocal of a positive sum is not finite).
+template <typename T>
+__device__ T normalize_into(const cplx<T>* u, int L, T p, double* red, NormBc<T>* nb, cplx<T>* dst,
+                            cplx<T>* dstg) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    p = warp_sum(p);
+    T* redt = (T*)red;
+    __syncthreads();  // u complete; redt free
+    if (lane == 0) redt[warp] = p;
+    __syncthreads();
+    if (warp == 0) {
+        T t = lane < nw ? redt[lane] : (T)0;
+        t = warp_sum(t);
+        if (lane == 0) {
+            const T inv = t > (T)0 ? (T)1 / sqrt(t) : (T)0;
+            nb->nrm = sqrt(t);
+            nb->inv = inv;
+            nb->mode = (t > (T)0 && !isfinite(inv)) ? 1 : 0;
+            if (nb->mode) nb->invd = 1.0 / sqrt((double)t);
+        }
+    }
+    __syncthreads();
+    const T nrm = nb->nrm;
+    if (nb->mode == 0) {
+        const T inv = nb->inv;
+        for (int e = threadIdx.x; e < L; e += blockDim.x) {
+            const cplx<T> v = cscale(u[e], inv);
+            dst[e] = v;
+            if (dstg) dstg[e] = v;
+        }
+    } else {
+        const double inv = nb->invd;
+        for (int e = threadIdx.x; e < L; e += blockDim.x) {
+            const cplx<T> x = u[e];
+            const cplx<T> v = mk<T>((T)((double)x.x * inv), (T)((double)x.y * inv));
+            dst[e] = v;
+            if (dstg) dstg[e] = v;
+        }
+    }
+    __syncthreads();
+    return nrm;
 }
 
 // Persistent tGKB.  Outputs per slice: W (k_max x m), Q (k_max+1 x l),
@@ -366,28 +426,62 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
     }
     __syncthreads();
 
+    const double td2n = (double)n * tau_delta * tau_delta;
     // Givens state (thread 0): phibar, previous rotation, orphan residual
     double phibar = z1, cs_prev = 1.0, sn_prev = 0.0, orphan = 0.0;
     T zprev = z1;
     int k = k_max;
-    for (int i = 1; i <= k_max; ++i) {
-        // W_i = A^T * Q_i - W_{i-1} * z_i ; reorthogonalise ; Normalize -> c_i
-        if (VEC) {
-            mv_h_vec<T>(A, l, m, q, w, zprev, u, part);
-        } else {
-            mv_h<T>(A, l, m, q, u);
-            __syncthreads();
-            for (int e = tid; e < m; e += blockDim.x) u[e] = csub(u[e], cscale(w[e], zprev));
-            __syncthreads();
+    // Step i publishes its residual and goes on; the discrepancy test of step
+    // i-1 is taken after step i's first product (which hides the grid-wide
+    // wait), and a stop discards step i before it writes anything.
+    for (int i = 1; i <= k_max + 1; ++i) {
+        const bool step = i <= k_max;
+        // W_i = A^T * Q_i - W_{i-1} * z_i
+        if (step) {
+            if (VEC) {
+                mv_h_vec<T>(A, l, m, q, w, zprev, u, part);
+            } else {
+                mv_h<T>(A, l, m, q, u);
+                __syncthreads();
+                for (int e = tid; e < m; e += blockDim.x) u[e] = csub(u[e], cscale(w[e], zprev));
+                __syncthreads();
+            }
         }
-        reorth2<T>(u, Wc, W, kc, i - 1, m, cf, part);
-        const T ci = normalize_vec<T>(u, m, red, &nb);
-        for (int e = tid; e < m; e += blockDim.x) {
-            w[e] = u[e];
-            W[(long)(i - 1) * m + e] = u[e];
-            if (i - 1 < kc) Wc[(long)(i - 1) * m + e] = u[e];
+        if (i >= 2) {
+            if (tid == 0) {
+                // wait for every slice to finish step i-1 (bounded)
+                const long long t0 = clock64();
+                while (ld_acquire(&counters[i - 1]) < (unsigned)h) {
+                    if (clock64() - t0 > spin_cycles) {
+                        flag_timeout = 1;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            // squared residual of step i-1 (times n): the same fixed-order sum
+            // over slices in every CTA; compared with n (tau delta)^2
+            if (tid < 32 && !flag_timeout) {
+                double tot = 0.0;
+                for (int s2 = tid; s2 < h; s2 += 32) tot += __ldcg(&res2[(long)(i - 1) * h + s2]);
+                tot = warp_sum(tot);
+                if (tid == 0) {
+                    S.res[i - 1] = tot;
+                    if (tot <= td2n) flag_done = 1;
+                }
+            }
+            __syncthreads();
+            if (flag_timeout || flag_done) {
+                k = i - 1;
+                break;
+            }
         }
-        __syncthreads();
+        if (!step) break;
+        // reorthogonalise ; Normalize -> c_i, w = W_i
+        const T pw = reorth2<T>(u, Wc, W, kc, i - 1, m, cf, part);
+        const T ci = normalize_into<T>(u, m, pw, red, &nb, w, W + (long)(i - 1) * m);
+        if (i - 1 < kc)
+            for (int e = tid; e < m; e += blockDim.x) Wc[(long)(i - 1) * m + e] = w[e];
         // Q_{i+1} = A * W_i - Q_i * c_i ; reorthogonalise ; Normalize -> z_{i+1}
         if (VEC) {
             mv_n_vec<T>(A, l, m, w, q, ci, u);
@@ -397,13 +491,10 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
             for (int e = tid; e < l; e += blockDim.x) u[e] = csub(u[e], cscale(q[e], ci));
             __syncthreads();
         }
-        reorth2<T>(u, Qc, Qv, kc, i, l, cf, part);
-        const T zi = normalize_vec<T>(u, l, red, &nb);
-        for (int e = tid; e < l; e += blockDim.x) {
-            q[e] = u[e];
-            Qv[(long)i * l + e] = u[e];
-            if (i < kc) Qc[(long)i * l + e] = u[e];
-        }
+        const T pq = reorth2<T>(u, Qc, Qv, kc, i, l, cf, part);
+        const T zi = normalize_into<T>(u, l, pq, red, &nb, q, Qv + (long)i * l);
+        if (i < kc)
+            for (int e = tid; e < l; e += blockDim.x) Qc[(long)i * l + e] = q[e];
         if (tid == 0) {
             cs_[i - 1] = ci;
             zs_[i] = zi;
@@ -429,38 +520,15 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
             cs_prev = c;
             sn_prev = sn;
             res2[(long)i * h + s] = ws * (orphan + phibar * phibar);
-            __threadfence();
-            atomicAdd(&counters[i], 1u);
-            // wait for every slice to finish step i (bounded)
-            const long long t0 = clock64();
-            while (ld_acquire(&counters[i]) < (unsigned)h) {
-                if (clock64() - t0 > spin_cycles) {
-                    flag_timeout = 1;
-                    break;
-                }
-            }
-            __threadfence();
-        }
-        __syncthreads();
-        // residual of step i: the same fixed-order sum over slices in every CTA
-        if (tid < 32 && !flag_timeout) {
-            double tot = 0.0;
-            for (int s2 = tid; s2 < h; s2 += 32) tot += __ldcg(&res2[(long)i * h + s2]);
-            tot = warp_sum(tot);
-            if (tid == 0) {
-                S.res[i] = sqrt(tot / (double)n);
-                if (S.res[i] <= tau_delta) flag_done = 1;
-            }
+            // step i done here (release: the residual above is visible first); the test comes after the next product
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&counters[i]) : "memory");
         }
         zprev = zi;
-        __syncthreads();
-        if (flag_timeout || flag_done) {
-            k = i;
-            break;
-        }
     }
-    // back substitution R y = phi (rho on the diagonal, theta above it)
+    // back substitution R y = phi (rho on the diagonal, theta above it); the
+    // residuals from their squares (times n)
     if (tid == 0) {
+        for (int j = 1; j <= k; ++j) S.res[j] = sqrt(S.res[j] / (double)n);
         for (int j = k - 1; j >= 0; --j) {
             double v = S.phi[j];
             if (j + 1 < k) v -= S.theta[j + 1] * S.y[j + 1];
