@@ -41,9 +41,12 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel class from the
 # ncu capture summarised in profiles/; reported only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
-    "gkb": {"bytes": 81.3e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
-            "sha256": "bda0ffc1bd562b6765d4e38d71361e66bc33dd782150b1b1085318b0839db6b2",
+    "gkb": {"bytes": 70.72e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
+            "sha256": "67c65259b651158aaff3a47343ec38df16c0817077894b51ea3ddea5f1b55de6",
             "profile": "profiles/k_gkb_n256.md"},
+    "orth": {"bytes": 7.47e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
+             "sha256": "bd999f56804f7f3bc4a26ff3062e63ffab0947a6b446dbce076efa61b67dd496",
+             "profile": "profiles/k_orth_n256.md"},
 }
 
 
@@ -289,8 +292,10 @@ def run_ours(a, rank, world, local):
                     "avg_launch_ms": dom_ms / dom_launches}
         else:
             ach = amount / secs
+            tr = ncu_traffic(dominant)
             roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_SIMT_TFLOPS, "traffic": None, "kernel_class": dominant,
+                    "frac": ach / FP32_SIMT_TFLOPS, "traffic": tr,
+                    "traffic_source": NCU_TRAFFIC[dominant]["profile"] if tr else None, "kernel_class": dominant,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                     "avg_launch_ms": dom_ms / dom_launches}
 
