@@ -42,6 +42,83 @@ template <typename T, int BB> struct OrthThreads {
     static constexpr int v = (sizeof(T) == 8 && BB == 32) ? 256 : 512;
 };
 
+// 1/sqrt(x) for positive normal x: one Newton-Raphson step on the hardware
+// approximation (float), y <- y (3 - x y^2) / 2, about one ulp.
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+
+// Cholesky factor of a 16 x 16 Hermitian Gram matrix (upper triangle of G in
+// shared memory) by one warp, the matrix in registers: lane j (and j + 16)
+// holds column j.  The step loop is not unrolled (a one-shot straight-line
+// body would be bound by instruction fetch); at step k the lanes pick their
+// row-k entry by a select tree on the bits of k, the pivot comes from lane k
+// by a shuffle (its reciprocal square root Newton-refined),
+// row k of R is formed lane-wise and each of its entries is broadcast by
+// shuffles for the trailing update.  Rows k >= b and zero pivots give zero
+// rows (a zero column stays zero).  On the first pass (may_shift) a pivot
+// below 100 u of the largest diagonal entry restarts on G + shift I and asks
+// for one more pass (shifted CholQR3).  Writes R (row-major) and 1/diag.
+template <typename T>
+__device__ void chol16_reg(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shift, bool may_shift,
+                           int* need_shift, int* passes) {
+    typedef cplx<T> V;
+    const int lane = threadIdx.x & 31, j = lane & 15;
+    T dmax = G[j * 16 + j].x;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+#pragma unroll 1
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        V col[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            col[i] = i <= j ? G[i * 16 + j] : mk<T>(0, 0);
+            if (attempt == 1 && i == j) col[i].x += shift;
+        }
+        bool bad = false;
+#pragma unroll 1
+        for (int k = 0; k < 16; ++k) {
+            // col[k] by a 4-level select tree on the bits of k
+            V t8[8], t4[4], t2[2];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) t8[i] = (k & 1) ? col[2 * i + 1] : col[2 * i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) t4[i] = (k & 2) ? t8[2 * i + 1] : t8[2 * i];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) t2[i] = (k & 4) ? t4[2 * i + 1] : t4[2 * i];
+            const V ck = (k & 8) ? t2[1] : t2[0];
+            const T d2 = __shfl_sync(0xffffffffu, ck.x, k);
+            if (k < b && d2 < (T)(100.0 * Eps<T>::v) * dmax) bad = true;
+            T d = 0, id = 0;
+            if (k < b && d2 > (T)0) {
+                id = rsqrt_t<T>(d2);
+                d = d2 * id;
+            }
+            V r = mk<T>(0, 0);
+            if (j > k) r = cscale(ck, id);
+            else if (j == k) r = mk<T>(d, 0);
+            if (lane < 16) Rk[k * 16 + j] = r;
+            if (lane == 0) invd[k] = id;
+#pragma unroll
+            for (int i = 1; i < 16; ++i) {
+                V ri;
+                ri.x = __shfl_sync(0xffffffffu, r.x, i);
+                ri.y = __shfl_sync(0xffffffffu, r.y, i);
+                if (i > k && i <= j) col[i] = csub(col[i], cmul(cconj(ri), r));
+            }
+        }
+        if (!may_shift || attempt == 1 || !bad || dmax == (T)0) break;
+        if (lane == 0) {
+            *need_shift = 1;
+            *passes += 1;
+        }
+    }
+    __syncwarp();
+}
+
 template <typename T, int BB>
 __global__ void __launch_bounds__(OrthThreads<T, BB>::v)
 k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev, cplx<T>* Qout,
@@ -183,7 +260,9 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
             if (lane == 0) G[i * BB + j] = acc;
         }
         __syncthreads();
-        if (warp == 0) {
+        if (warp == 0 && BB == 16 && sizeof(T) == 4) {
+            chol16_reg<T>(G, Rk, invd, b, (T)shift, pass == 0, &need_shift, &passes);
+        } else if (warp == 0) {
             // Cholesky G (+ shift) = R^H R by the first warp: at step k the
             // lanes form row k of R, then update the trailing Gram entries as
             // independent (i, j) pairs.  A zero pivot gives a zero row (a zero
@@ -217,10 +296,14 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                     }
                     if (lane == 0) invd[k] = id;
                     __syncwarp();
-                    const int mrem = BB - k - 1;
-                    for (int pi = lane; pi < mrem * mrem; pi += 32) {
-                        const int i = k + 1 + pi / mrem, jj = k + 1 + pi % mrem;
-                        if (jj >= i)
+                    // trailing update G[i][jj] -= conj(R[k][i]) R[k][jj], k < i <= jj:
+                    // a half-warp (BB = 16) or a warp (BB = 32) per row i, lane
+                    // offset jj - i (no integer division)
+                    constexpr int RW = BB == 16 ? 16 : 32;
+                    const int rsub = lane / RW, jo = lane % RW;
+                    for (int i = k + 1 + rsub; i < BB; i += 32 / RW) {
+                        const int jj = i + jo;
+                        if (jj < BB)
                             G[i * BB + jj] = csub(G[i * BB + jj], cmul(cconj(Rk[k * BB + i]), Rk[k * BB + jj]));
                     }
                     __syncwarp();
