@@ -105,6 +105,59 @@ def test_rtsvd_discrepancy_residual_and_bracket():
     assert all(out["res"][j] > tau * delta for j in range(out["k_init"], k))
 
 
+def small_blur_multi(p=3, N=10, n=8, seed=13, noise=1e-2, general=0.02):
+    """p lateral slices (different images) blurred by one operator, with noise
+    of total relative level `noise` (delta = ||E||_F over all slices)."""
+    T, c = synth.blur_factors(N, 1.2, 3, 1.5, n=n)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    g = np.random.default_rng(seed)
+    P = g.standard_normal(A.shape)
+    A = A + general * P / np.linalg.norm(P) * np.linalg.norm(A)
+    Xt = np.concatenate([synth.lateral(synth.synthetic_image(N, n, 3, 1, g)) for _ in range(p)], axis=2)
+    Bt = O.tprod_bcirc(A, Xt)
+    E = g.standard_normal(Bt.shape)
+    E = noise * E / np.linalg.norm(E) * np.linalg.norm(Bt)
+    return A, Bt + E, float(np.linalg.norm(E))
+
+
+def test_rtsvd_several_lateral_slices_share_k_and_match_columnwise():
+    """Reading for B with p lateral slices (problem (I6)): one factorisation,
+    one truncation index k from ||B - A*X_k||_F <= tau delta with delta the
+    norm of all of E.  At any fixed k the solution is the column-wise one
+    (X_k = V_k S_k^-1 U_k^T * B is linear in B), and the reported residual is
+    the Frobenius norm over all slices, checked through the block-circulant
+    product."""
+    A, B, delta = small_blur_multi(p=3)
+    n, l, m = A.shape
+    Om = rnd((n, m, m), 8)
+    tau, eps = 1.1, 0.02 * np.sqrt(O.fro2(A))
+    out = O.rtsvd_solve(A, B, Om, delta, tau, eps, 3, 2, 1, r_max=m)
+    assert out["status"] == O.STATUS_OK
+    k = out["k"]
+    for c in range(3):
+        xc = O.rtsvd_solve(A, B[:, :, c:c + 1], Om, delta, tau, eps, 3, 2, 1, r_max=m, k_fixed=k)["X"]
+        assert np.allclose(out["X"][:, :, c:c + 1], xc, atol=1e-10 * np.abs(xc).max())
+    for j, rj in out["res"].items():
+        Xj = O.rtsvd_solve(A, B, Om, delta, tau, eps, 3, 2, 1, r_max=m, k_fixed=j)["X"]
+        assert np.isclose(rj, np.sqrt(O.fro2(B - O.tprod_bcirc(A, Xj))), rtol=1e-9)
+    assert out["res"][k] <= tau * delta
+    assert all(out["res"][j] > tau * delta for j in range(out["k_init"], k))
+
+
+def test_rtsvd_duplicated_lateral_slice_gives_the_single_slice_answer():
+    """B = [b, b] with delta scaled by sqrt(2) is the single-slice problem twice:
+    same k, and both solution slices equal the single-slice solution."""
+    A, B, delta = small_blur(N=10, n=8, general=0.02)
+    n, l, m = A.shape
+    Om = rnd((n, m, m), 9)
+    tau, eps = 1.1, 0.02 * np.sqrt(O.fro2(A))
+    one = O.rtsvd_solve(A, B, Om, delta, tau, eps, 3, 2, 1, r_max=m)
+    two = O.rtsvd_solve(A, np.concatenate([B, B], axis=2), Om, np.sqrt(2.0) * delta, tau, eps, 3, 2, 1, r_max=m)
+    assert two["k"] == one["k"] and two["r"] == one["r"]
+    for c in range(2):
+        assert np.allclose(two["X"][:, :, c:c + 1], one["X"], atol=1e-10 * np.abs(one["X"]).max())
+
+
 def test_ttsvd_discrepancy_bracket_with_brute_force_residual():
     A, B, delta = small_blur()
     tau = 1.1
