@@ -131,18 +131,22 @@ tp_status tprod_gemm_noalloc(const void* A, const void* B, void* C, int l, int k
  * Algorithm 3 in block form: Gaussian lateral slices are taken `block` at a
  * time from Omega (slice c of Omega is the c-th Gaussian slice G), sketched
  * with q_power power iterations, orthonormalised against the basis so far
- * (two classical Gram-Schmidt passes, then column by column with Normalize),
- * and the error indicator eta = ||A||_F^2 - ||Bt||_F^2 (Theorems 4.1-4.2) is
- * updated per block until eta < eps^2 or r = r_max.  The full tSVD of Bt gives
+ * (two classical Gram-Schmidt passes, then a Cholesky QR of the block, whose
+ * basis equals the column-by-column Gram-Schmidt one up to rounding), and the
+ * error indicator eta = ||A||_F^2 - ||Bt||_F^2 (Theorems 4.1-4.2) is updated
+ * per block until eta < eps^2 or r = r_max.  The full tSVD of Bt gives
  * U_k = Q*U(:,1:k,:), S_k, V_k and X_k = V_k * S_k^{-1} * U_k^T * B; k is the
  * smallest index in [max(1, r - p_over), r] (Eq. (kinit)) with
  * ||B - A*X_k||_F <= tau*delta (Eq. (disp)), else k = r and status
  * TP_ERR_NOT_CONVERGED.  Singular values at or below max(l,m)*eps*sigma_max
- * are treated as zero.
- *   A     : real (n, l, m)       B : real (n, l, 1)     X : real (n, m, 1)
+ * are treated as zero.  With p > 1 lateral slices (problem (I6)) the slices
+ * share the factorisation and one k, chosen from the Frobenius norm of the
+ * residual over all slices (delta then bounds the norm of all of E).
+ *   A     : real (n, l, m)       B : real (n, l, p)     X : real (n, m, p)
  *   Omega : real (n, m, r_max)   (Gaussian test slices, supplied by the caller)
  * Limits: 1 <= block <= 32; r_max <= min(l, m); r_max <= 160 (FP32) or
- * 112 (FP64); l, m <= 1024; p = 1.
+ * 112 (FP64); l, m <= 1024; 1 <= p <= 64, and the small SVD's working set,
+ * (r_max^2 + r_max p) complex entries, must fit in 227 KB of shared memory.
  */
 typedef struct {
     double delta;       /* noise bound of Eq. (errbd)                                 */

@@ -467,7 +467,7 @@ __device__ __forceinline__ bool rr_pair(int t, int kp, int rr, int r, int& p, in
 
 // Sweeps in shared memory with IEEE arithmetic (any precision).
 template <typename T>
-__device__ int jacobi_sweeps_smem(cplx<T>* Rs, cplx<T>* dp, int r, int max_sweeps, T tol) {
+__device__ int jacobi_sweeps_smem(cplx<T>* Rs, cplx<T>* dp, int np, int r, int max_sweeps, T tol) {
     typedef cplx<T> V;
     __shared__ int rot_count;
     __shared__ int max_off;  // bit pattern of the largest |g| / sqrt(a b) of a sweep (non-negative float)
@@ -520,13 +520,13 @@ __device__ int jacobi_sweeps_smem(cplx<T>* Rs, cplx<T>* dp, int r, int max_sweep
                         cp[i] = mk<T>(c * x.x - sn * ey.x, c * x.y - sn * ey.y);
                         cq[i] = mk<T>(sn * x.x + c * ey.x, sn * x.y + c * ey.y);
                     }
-                    if (hl == 0) {
-                        const V x = dp[p];
-                        const V ey = cmul(e, dp[q]);
-                        dp[p] = mk<T>(c * x.x - sn * ey.x, c * x.y - sn * ey.y);
-                        dp[q] = mk<T>(sn * x.x + c * ey.x, sn * x.y + c * ey.y);
-                        atomicAdd(&rot_count, 1);
+                    for (int cc = hl; cc < np; cc += 16) {  // the rows p, q of d' (np right-hand sides)
+                        const V x = dp[p * np + cc];
+                        const V ey = cmul(e, dp[q * np + cc]);
+                        dp[p * np + cc] = mk<T>(c * x.x - sn * ey.x, c * x.y - sn * ey.y);
+                        dp[q * np + cc] = mk<T>(sn * x.x + c * ey.x, sn * x.y + c * ey.y);
                     }
+                    if (hl == 0) atomicAdd(&rot_count, 1);
                 }
             }
             __syncthreads();
@@ -554,7 +554,7 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 // one per round (no integer division), and the per-round "any rotation" flag
 // rides on the round's barrier.
 template <int EPL, bool V2>
-__device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int r, int max_sweeps, float tol) {
+__device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol) {
     __shared__ int max_off2;  // bit pattern of the largest (|g|^2 / (a b)) of a sweep
     const int tid = threadIdx.x, lane = tid & 31, hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
     const int rr = r + (r & 1), npair = rr / 2;
@@ -656,11 +656,11 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int r, int max_sweeps, 
                             }
                         }
                     }
-                    if (hl == 0) {
-                        const float2 xv = dp[p];
-                        const float2 ey = cmul(cconj(ec), dp[q]);
-                        dp[p] = make_float2(c * xv.x - sn * ey.x, c * xv.y - sn * ey.y);
-                        dp[q] = make_float2(sn * xv.x + c * ey.x, sn * xv.y + c * ey.y);
+                    for (int cc = hl; cc < np; cc += 16) {  // the rows p, q of d' (np right-hand sides)
+                        const float2 xv = dp[p * np + cc];
+                        const float2 ey = cmul(cconj(ec), dp[q * np + cc]);
+                        dp[p * np + cc] = make_float2(c * xv.x - sn * ey.x, c * xv.y - sn * ey.y);
+                        dp[q * np + cc] = make_float2(sn * xv.x + c * ey.x, sn * xv.y + c * ey.y);
                     }
                 }
                 any |= rot ? 1 : 0;
@@ -683,35 +683,36 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int r, int max_sweeps, 
 }
 
 template <typename T> struct JacobiSweeps {
-    static __device__ int run(cplx<T>* Rs, cplx<T>* dp, int r, int max_sweeps, T tol) {
-        return jacobi_sweeps_smem<T>(Rs, dp, r, max_sweeps, tol);
+    static __device__ int run(cplx<T>* Rs, cplx<T>* dp, int np, int r, int max_sweeps, T tol) {
+        return jacobi_sweeps_smem<T>(Rs, dp, np, r, max_sweeps, tol);
     }
 };
 template <> struct JacobiSweeps<float> {
-    static __device__ int run(float2* Rs, float2* dp, int r, int max_sweeps, float tol) {
+    static __device__ int run(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol) {
         const bool v2 = (r & 1) == 0;  // 16-byte pairs of entries need an even column length
-        if (r <= 64) return v2 ? jacobi_sweeps_reg<4, true>(Rs, dp, r, max_sweeps, tol)
-                               : jacobi_sweeps_reg<4, false>(Rs, dp, r, max_sweeps, tol);
-        if (r <= 96) return v2 ? jacobi_sweeps_reg<6, true>(Rs, dp, r, max_sweeps, tol)
-                               : jacobi_sweeps_reg<6, false>(Rs, dp, r, max_sweeps, tol);
-        if (r <= 128) return v2 ? jacobi_sweeps_reg<8, true>(Rs, dp, r, max_sweeps, tol)
-                                : jacobi_sweeps_reg<8, false>(Rs, dp, r, max_sweeps, tol);
-        return jacobi_sweeps_smem<float>(Rs, dp, r, max_sweeps, tol);
+        if (r <= 64) return v2 ? jacobi_sweeps_reg<4, true>(Rs, dp, np, r, max_sweeps, tol)
+                               : jacobi_sweeps_reg<4, false>(Rs, dp, np, r, max_sweeps, tol);
+        if (r <= 96) return v2 ? jacobi_sweeps_reg<6, true>(Rs, dp, np, r, max_sweeps, tol)
+                               : jacobi_sweeps_reg<6, false>(Rs, dp, np, r, max_sweeps, tol);
+        if (r <= 128) return v2 ? jacobi_sweeps_reg<8, true>(Rs, dp, np, r, max_sweeps, tol)
+                                : jacobi_sweeps_reg<8, false>(Rs, dp, np, r, max_sweeps, tol);
+        return jacobi_sweeps_smem<float>(Rs, dp, np, r, max_sweeps, tol);
     }
 };
 
 template <typename T>
 __global__ void __launch_bounds__(JAC_THREADS)
 k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, const cplx<T>* __restrict__ d, long sd,
-         T* sigma, long ssig, cplx<T>* UR, long ldu, long sU, cplx<T>* dprime, long sdp, int max_sweeps,
+         int np, T* sigma, long ssig, cplx<T>* UR, long ldu, long sU, cplx<T>* dprime, long sdp, int max_sweeps,
          int* sweeps_out) {
+    // d and d' are r x np (np right-hand sides, row-major) per slice
     typedef cplx<T> V;
     const int r = st->r;
     if (r <= 0) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* Rs = (V*)smraw;                       // column j at Rs[j*r]
     V* dp = Rs + (size_t)r * r;
-    T* sg = (T*)(dp + r);  // column norms (sigma), working precision
+    T* sg = (T*)(dp + (size_t)r * np);  // column norms (sigma), working precision
     int* perm = (int*)(sg + r);
     __shared__ T tol_s;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -720,10 +721,10 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
         const int i = e / r, j = e - i * r;
         Rs[(size_t)j * r + i] = R[(long)i * ldr + j];
     }
-    for (int i = tid; i < r; i += blockDim.x) dp[i] = d[(long)s * sd + i];
+    for (int i = tid; i < r * np; i += blockDim.x) dp[i] = d[(long)s * sd + i];
     if (tid == 0) tol_s = (T)(4.0 * sqrt((double)r) * Eps<T>::v);
     __syncthreads();
-    const int sweep = JacobiSweeps<T>::run(Rs, dp, r, max_sweeps, tol_s);
+    const int sweep = JacobiSweeps<T>::run(Rs, dp, np, r, max_sweeps, tol_s);
     for (int j = warp; j < r; j += nw) {
         T a = 0;  // column norms in the working precision (float64 only on lane 0)
         for (int i = lane; i < r; i += 32) a += cabs2(Rs[(size_t)j * r + i]);
@@ -738,10 +739,11 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
         perm[rank] = j;
     }
     __syncthreads();
-    for (int jr = tid; jr < r; jr += blockDim.x) {
+    for (int e = tid; e < r * np; e += blockDim.x) {
+        const int jr = e / np, cc = e - jr * np;
         const int j = perm[jr];
-        sigma[(long)s * ssig + jr] = sg[j];
-        dprime[(long)s * sdp + jr] = dp[j];
+        if (cc == 0) sigma[(long)s * ssig + jr] = sg[j];
+        dprime[(long)s * sdp + e] = dp[j * np + cc];
     }
     V* U = UR + (long)s * sU;
     for (int e = tid; e < r * r; e += blockDim.x) {
@@ -754,14 +756,14 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     if (tid == 0) atomicMax(sweeps_out, sweep);
 }
 
-static size_t jacobi_smem(int r, size_t c) {
-    return (size_t)r * r * c + (size_t)r * c + (size_t)r * sizeof(double) + (size_t)r * sizeof(int);
+static size_t jacobi_smem(int r, size_t c, int np) {
+    return (size_t)r * r * c + (size_t)r * np * c + (size_t)r * sizeof(double) + (size_t)r * sizeof(int);
 }
 
 // alpha_j = d'_j / sigma_j, dropping sigma_j <= dims * eps * sigma_max.
 template <typename T>
 __global__ void k_alpha(const T* sigma, long ssig, const cplx<T>* dprime, long sdp, cplx<T>* alpha, long sa,
-                        const State* st, int h, int dims, int r_max) {
+                        const State* st, int h, int dims, int r_max, int np) {
     __shared__ double red[32];
     const int r = st->r, s = blockIdx.x;
     double mx = 0.0;
@@ -773,16 +775,17 @@ __global__ void k_alpha(const T* sigma, long ssig, const cplx<T>* dprime, long s
     double gmax = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gmax = fmax(gmax, red[w]);
     const double tol = (double)dims * Eps<T>::v * gmax;
-    for (int j = threadIdx.x; j < r_max; j += blockDim.x) {
+    for (int e = threadIdx.x; e < r_max * np; e += blockDim.x) {  // alpha, d' are r_max x np
+        const int j = e / np;
         cplx<T> a = mk<T>(0, 0);
         if (j < r) {
             const double sv = (double)sigma[(long)s * ssig + j];
             if (sv > tol) {
-                const cplx<T> v = dprime[(long)s * sdp + j];
+                const cplx<T> v = dprime[(long)s * sdp + e];
                 a = mk<T>((T)(v.x / sv), (T)(v.y / sv));
             }
         }
-        alpha[(long)s * sa + j] = a;
+        alpha[(long)s * sa + e] = a;
     }
 }
 
@@ -791,11 +794,13 @@ __global__ void k_alpha(const T* sigma, long ssig, const cplx<T>* dprime, long s
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_dp_scan(const cplx<T>* __restrict__ KhT, long sK, const cplx<T>* __restrict__ alpha, long sa,
-          const cplx<T>* __restrict__ bhat, long sb, const State* st, int l, int p_over, double* out, long so) {
-    // Residual b - sum_{j<k} K_j alpha_j of one slice for every k; its squared
-    // norm is formed only for the candidates k >= k_init = max(1, r - p) (the
-    // others are written as 0): per thread and per warp in the working
-    // precision, across warps in float64.
+          const cplx<T>* __restrict__ bhat, long sb, const State* st, int l, int np, int p_over, double* out,
+          long so) {
+    // Residual B - sum_{j<k} K_j alpha_j of one slice for every k (np
+    // right-hand sides, alpha and B row-major with np columns); its squared
+    // Frobenius norm is formed only for the candidates k >= k_init =
+    // max(1, r - p) (the others are written as 0): per thread and per warp in
+    // the working precision, across warps in float64.
     typedef cplx<T> V;
     constexpr int RPT = 4;  // rows per thread (l <= 1024)
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -804,27 +809,29 @@ k_dp_scan(const cplx<T>* __restrict__ KhT, long sK, const cplx<T>* __restrict__ 
     const int nw = blockDim.x >> 5;
     const int k_init = max(1, r - p_over);
     KhT += (long)s * sK;
-    V res[RPT];
+    for (int c = 0; c < np; ++c) {
+        V res[RPT];
 #pragma unroll
-    for (int u = 0; u < RPT; ++u) {
-        const int i = tid + u * blockDim.x;
-        res[u] = (i < l) ? bhat[(long)s * sb + i] : mk<T>(0, 0);
-    }
-    for (int j = 0; j <= r; ++j) {
-        if (j > 0) {
-            const V a = alpha[(long)s * sa + j - 1];
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                const int i = tid + u * blockDim.x;
-                if (i < l) res[u] = csub(res[u], cmul(KhT[(long)(j - 1) * l + i], a));
-            }
+        for (int u = 0; u < RPT; ++u) {
+            const int i = tid + u * blockDim.x;
+            res[u] = (i < l) ? bhat[(long)s * sb + (long)i * np + c] : mk<T>(0, 0);
         }
-        if (j >= k_init) {
-            T part = 0;
+        for (int j = 0; j <= r; ++j) {
+            if (j > 0) {
+                const V a = alpha[(long)s * sa + (long)(j - 1) * np + c];
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) part += cabs2(res[u]);
-            part = warp_sum(part);
-            if (lane == 0) wsum[warp * (r + 1) + j] = (double)part;
+                for (int u = 0; u < RPT; ++u) {
+                    const int i = tid + u * blockDim.x;
+                    if (i < l) res[u] = csub(res[u], cmul(KhT[(long)(j - 1) * l + i], a));
+                }
+            }
+            if (j >= k_init) {
+                T part = 0;
+#pragma unroll
+                for (int u = 0; u < RPT; ++u) part += cabs2(res[u]);
+                part = warp_sum(part);
+                if (lane == 0) wsum[warp * (r + 1) + j] = (c == 0 ? 0.0 : wsum[warp * (r + 1) + j]) + (double)part;
+            }
         }
     }
     __syncthreads();
@@ -913,19 +920,19 @@ __global__ void __launch_bounds__(256) k_ctranspose(const cplx<T>* __restrict__ 
 }
 
 template <typename T>
-static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max) {
+static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max, int p) {
     typedef cplx<T> V;
     const long h = n / 2 + 1;
     Carver c(base, 0);
     RtWs<T> w;
     w.st = c.take<State>(1);
     w.partsA = c.take<double>(rdft_parts(l, m));
-    w.partsB = c.take<double>(rdft_parts(l, 1));
+    w.partsB = c.take<double>(rdft_parts(l, p));
     w.normsq = c.take<double>(h);
     w.dpout = c.take<double>(h * (r_max + 1));
     w.Ahat = c.take<V>(h * l * m);
     w.AhT = sizeof(T) == 4 ? c.take<V>(h * l * m) : nullptr;  // float32 only: tensor-core products
-    w.Bhat = c.take<V>(h * l);
+    w.Bhat = c.take<V>(h * l * p);
     w.G = c.take<V>(h * m * r_max);  // all Gaussian slices, transformed once
     w.Y = c.take<V>(h * l * b);
     w.Z = c.take<V>(h * m * b);
@@ -933,31 +940,33 @@ static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max) {
     w.BHb = c.take<V>(h * m * b);
     w.QG = c.take<V>(h * r_max * m);
     w.R = c.take<V>(h * r_max * r_max);
-    w.d = c.take<V>(h * r_max);
+    w.d = c.take<V>(h * r_max * p);
     w.UR = c.take<V>(h * r_max * r_max);
-    w.dprime = c.take<V>(h * r_max);
-    w.alpha = c.take<V>(h * r_max);
+    w.dprime = c.take<V>(h * r_max * p);
+    w.alpha = c.take<V>(h * r_max * p);
     w.Vt = c.take<V>(h * m * r_max);
     w.KhT = c.take<V>(h * r_max * l);
-    w.Xhat = c.take<V>(h * m);
+    w.Xhat = c.take<V>(h * m * p);
     w.sigma = c.take<T>(h * r_max);
     w.bytes = c.off;
     return w;
 }
 
-static int jac_rmax(size_t elem) {
-    // largest r whose Jacobi working set fits in 227 KB of shared memory
+static int jac_rmax(size_t elem, int p) {
+    // largest r whose Jacobi working set (p right-hand sides) fits in 227 KB of shared memory
     int r = 1;
-    while (jacobi_smem(r + 1, 2 * elem) <= 227 * 1024) ++r;
+    while (jacobi_smem(r + 1, 2 * elem, p) <= 227 * 1024) ++r;
     return r;
 }
 
+constexpr int RT_MAX_RHS = 64;  // lateral slices of B per RT-tSVD call
+
 template <typename T>
 static tp_status rt_check(int l, int m, int n, int p, const tp_rtsvd_params* P) {
-    if (!P || l < 1 || m < 1 || n < 1 || p != 1) return TP_ERR_ARG;
+    if (!P || l < 1 || m < 1 || n < 1 || p < 1 || p > RT_MAX_RHS) return TP_ERR_ARG;
     if (l > 1024 || m > 1024 || n > (sizeof(T) == 4 ? 1024 : 512)) return TP_ERR_ARG;
     if (P->block < 1 || P->block > MAX_BLOCK || P->r_max < 1 || P->r_max > (l < m ? l : m)) return TP_ERR_ARG;
-    if (P->r_max > (sizeof(T) == 4 ? 160 : 112) || P->r_max > jac_rmax(sizeof(T))) return TP_ERR_ARG;
+    if (P->r_max > (sizeof(T) == 4 ? 160 : 112) || P->r_max > jac_rmax(sizeof(T), p)) return TP_ERR_ARG;
     if (!(P->tau > 0.0) || !(P->delta >= 0.0) || P->p_over < 0 || P->q_power < 0) return TP_ERR_ARG;
     if (!(P->eps > 0.0) && !(P->eps_rel > 0.0)) return TP_ERR_ARG;
     const int Lmax = l > m ? l : m;
@@ -968,7 +977,7 @@ static tp_status rt_check(int l, int m, int n, int p, const tp_rtsvd_params* P) 
 template <typename T>
 size_t rt_ws_bytes(int l, int m, int n, int p, const tp_rtsvd_params* P) {
     if (rt_check<T>(l, m, n, p, P) != TP_OK) return 0;
-    return rt_carve<T>(nullptr, l, m, n, P->block, P->r_max).bytes;
+    return rt_carve<T>(nullptr, l, m, n, P->block, P->r_max, p).bytes;
 }
 
 #define TRY(x)                              \
@@ -983,7 +992,7 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     TRY(rt_check<T>(l, m, n, p, P));
     if (!A || !B || !Om || !X || !info) return TP_ERR_ARG;
     const int b = P->block, r_max = P->r_max, h = n / 2 + 1;
-    RtWs<T> w = rt_carve<T>(ws, l, m, n, b, r_max);
+    RtWs<T> w = rt_carve<T>(ws, l, m, n, b, r_max, p);
     if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
     const long lm = (long)l * m;
     const int* done = &w.st->done;
@@ -999,9 +1008,9 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     const cplx<T>* AH = w.AhT ? w.AhT : w.Ahat;
     const long ldah = w.AhT ? l : m;
     const int op_h = w.AhT ? OP_R : OP_C;
-    TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, w.partsB, nullptr, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, p, p, (long)l * p, w.partsB, nullptr, st));
     prof_begin(TP_KC_MISC, st);
-    k_rt_init<<<1, 256, 0, st>>>(w.st, w.partsA, rdft_parts(l, m), w.partsB, rdft_parts(l, 1), P->eps, P->eps_rel, n);
+    k_rt_init<<<1, 256, 0, st>>>(w.st, w.partsA, rdft_parts(l, m), w.partsB, rdft_parts(l, p), P->eps, P->eps_rel, n);
     TRY(launched(TP_KC_MISC, st));
 
     // all Gaussian slices -> Fourier in one launch (blocks the sketch never
@@ -1037,20 +1046,21 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
         TRY(launched(TP_KC_MISC, st));
     }
     const int* dr = &w.st->r;
-    // d = Q^H b
-    TRY(cgemm<T>(h, r_max, 1, l, dr, 0, 0, 1, 0, w.Q, l, (long)r_max * l, OP_R, w.Bhat, 1, l, OP_N, 0, 0, w.d, 1,
-                 r_max, nullptr, st));
+    // d = Q^H B (r_max x p per slice)
+    const long rp = (long)r_max * p;
+    TRY(cgemm<T>(h, r_max, p, l, dr, 0, 0, 1, 0, w.Q, l, (long)r_max * l, OP_R, w.Bhat, p, (long)l * p, OP_N, 0, 0,
+                 w.d, p, rp, nullptr, st));
     {
-        const size_t smem = jacobi_smem(r_max, sizeof(cplx<T>));
+        const size_t smem = jacobi_smem(r_max, sizeof(cplx<T>), p);
         if (smem_optin((const void*)k_jacobi<T>, smem) != TP_OK) return TP_ERR_CUDA;
         prof_begin(TP_KC_SVD, st);
-        k_jacobi<T><<<h, JAC_THREADS, smem, st>>>(w.R, r_max, (long)r_max * r_max, w.st, w.d, r_max, w.sigma, r_max,
-                                                    w.UR, r_max, (long)r_max * r_max, w.dprime, r_max, 60,
+        k_jacobi<T><<<h, JAC_THREADS, smem, st>>>(w.R, r_max, (long)r_max * r_max, w.st, w.d, rp, p, w.sigma, r_max,
+                                                    w.UR, r_max, (long)r_max * r_max, w.dprime, rp, 60,
                                                     &w.st->sweeps);
         TRY(launched(TP_KC_SVD, st));
     }
     prof_begin(TP_KC_MISC, st);
-    k_alpha<T><<<h, 256, 0, st>>>(w.sigma, r_max, w.dprime, r_max, w.alpha, r_max, w.st, h, l > m ? l : m, r_max);
+    k_alpha<T><<<h, 256, 0, st>>>(w.sigma, r_max, w.dprime, rp, w.alpha, rp, w.st, h, l > m ? l : m, r_max, p);
     TRY(launched(TP_KC_MISC, st));
     // V = QG^T-as-matrix * U_R ;  K^T = V^T A^T (vector-major K = A V)
     TRY(cgemm<T>(h, m, r_max, r_max, 0, dr, dr, 1, 0, w.QG, m, (long)r_max * m, OP_T, w.UR, r_max,
@@ -1075,17 +1085,17 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     {
         const size_t smem = (size_t)(256 / 32) * (r_max + 1) * sizeof(double);
         prof_begin(TP_KC_DP, st);
-        k_dp_scan<T><<<h, 256, smem, st>>>(w.KhT, (long)r_max * l, w.alpha, r_max, w.Bhat, l, w.st, l, P->p_over,
-                                           w.dpout, r_max + 1);
+        k_dp_scan<T><<<h, 256, smem, st>>>(w.KhT, (long)r_max * l, w.alpha, rp, w.Bhat, (long)l * p, w.st, l, p,
+                                           P->p_over, w.dpout, r_max + 1);
         TRY(launched(TP_KC_DP, st));
     }
     prof_begin(TP_KC_DP, st);
     k_dp_reduce<<<1, 256, (r_max + 1) * sizeof(double), st>>>(w.dpout, r_max + 1, h, n, w.st, P->p_over,
                                                               P->tau * P->delta, info, P->res_hist, r_max);
     TRY(launched(TP_KC_DP, st));
-    TRY(cgemm<T>(h, m, 1, r_max, 0, 0, &w.st->k, 1, 0, w.Vt, r_max, (long)m * r_max, OP_N, w.alpha, 1, r_max, OP_N,
-                 0, 0, w.Xhat, 1, m, nullptr, st));
-    TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));
+    TRY(cgemm<T>(h, m, p, r_max, 0, 0, &w.st->k, 1, 0, w.Vt, r_max, (long)m * r_max, OP_N, w.alpha, p, rp, OP_N,
+                 0, 0, w.Xhat, p, (long)m * p, nullptr, st));
+    TRY(irdft<T>(w.Xhat, X, n, m, p, p, (long)m * p, nullptr, st));
     return TP_OK;
 }
 

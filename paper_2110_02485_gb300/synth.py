@@ -144,13 +144,16 @@ def gaussian_tensor(shape, seed: int, dtype=np.float32) -> np.ndarray:
 
 
 def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | None = None,
-                 general: float = 0.0, with_omega: bool = True) -> dict:
+                 general: float = 0.0, with_omega: bool = True, frames: int = 1) -> dict:
     """Build one deblurring problem.
 
     general > 0 adds a dense Gaussian perturbation of relative size `general`
     (in Frobenius norm) to A, so that the Fourier slices are no longer
     multiples of one matrix.  B is always made from the unperturbed operator.
-    Returns float32 arrays A (n,N,N), B (n,N,1), X_true (n,N,1),
+    frames > 1 blurs that many independent images with the same operator and
+    stacks them as lateral slices (the several-right-hand-side problem (I6));
+    the noise level and delta then refer to all frames together.
+    Returns float32 arrays A (n,N,N), B (n,N,frames), X_true (n,N,frames),
     Omega (n,N,r_max) and float64 scalars delta, norm_A.
     """
     if isinstance(cfg, str):
@@ -164,12 +167,13 @@ def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | 
     if general > 0.0:
         P = rng.standard_normal(A.shape)
         A = (A.astype(np.float64) + general * P / np.linalg.norm(P) * np.linalg.norm(A)).astype(np.float32)
-    img = synthetic_image(N, N, cfg.bumps, cfg.rects, rng)
-    B_true = forward_blur(T, c, img)
-    B, delta = add_noise(B_true, noise, rng)
-    out = dict(cfg=cfg, A=A, B=lateral(B).astype(np.float32),
-               X_true=lateral(img).astype(np.float32), delta=delta, noise=noise,
-               T=T, c=c)
+    imgs = [synthetic_image(N, N, cfg.bumps, cfg.rects, rng) for _ in range(frames)]
+    B_true = np.stack([forward_blur(T, c, img) for img in imgs])
+    B, delta = add_noise(B_true if frames > 1 else B_true[0], noise, rng)
+    B = B.reshape(frames, N, N)
+    out = dict(cfg=cfg, A=A, B=np.concatenate([lateral(b) for b in B], axis=2).astype(np.float32),
+               X_true=np.concatenate([lateral(img) for img in imgs], axis=2).astype(np.float32), delta=delta,
+               noise=noise, T=T, c=c)
     if with_omega:
         out["Omega"] = rng.standard_normal((N, N, cfg.r_max)).astype(np.float32)
     out["norm_A"] = float(np.sqrt(np.sum(A.astype(np.float64) ** 2)))

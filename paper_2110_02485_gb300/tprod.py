@@ -250,28 +250,30 @@ def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None
                 res_hist=False, sync=True, tf32=False):
     """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist]).
 
-    tf32=True (float32 only): the TP_TF32 precision form of the block sketch
-    and projection products."""
+    B is (n, l, p): p > 1 lateral slices share one factorisation and one k
+    (problem (I6)).  tf32=True (float32 only): the TP_TF32 precision form of
+    the block sketch and projection products."""
     _dev(A, B, Omega)
     n, l, m = A.shape
+    p = B.shape[2]
     r_max = min(l, m) if r_max is None else r_max
     prec = _prec(A)
     if tf32:
         if prec != TP_FP32:
             raise TypeError("tf32 needs float32 tensors")
         prec = TP_TF32
-    X = torch.empty((n, m, 1), dtype=A.dtype, device=A.device)
+    X = torch.empty((n, m, p), dtype=A.dtype, device=A.device)
     hist = torch.empty(r_max + 1, dtype=torch.float64, device=A.device) if res_hist else None
     P = RtsvdParams(float(delta), float(tau), float(eps), float(eps_rel), int(p_over), int(q_power), int(block),
                     int(r_max), hist.data_ptr() if hist is not None else None)
     L = load()
-    nb = L.rtsvd_workspace_bytes(l, m, n, 1, ctypes.byref(P), prec)
+    nb = L.rtsvd_workspace_bytes(l, m, n, p, ctypes.byref(P), prec)
     if nb == 0:
         raise TprodError("rtsvd_workspace_bytes", TP_ERR_ARG)
     ws = _workspace(nb, A.device)
     wp, wn = _aligned(ws)
     info = _info_buf(A.device)
-    _check("rtsvd_truncated_solve", L.rtsvd_truncated_solve(_ptr(A), _ptr(B), _ptr(Omega), l, m, n, 1,
+    _check("rtsvd_truncated_solve", L.rtsvd_truncated_solve(_ptr(A), _ptr(B), _ptr(Omega), l, m, n, p,
                                                             ctypes.byref(P), _ptr(X), _ptr(info), prec, wp, wn,
                                                             _stream()))
     if not sync:

@@ -60,3 +60,20 @@ def test_product_path_has_no_cpu_fallback():
     from paper_2110_02485_gb300 import tprod
     with pytest.raises(TypeError):
         tprod.fft(torch.zeros(4, 3, 3))
+
+
+def test_rtsvd_lateral_slice_limits(lib):
+    """Workspace sizing (host only) accepts 1 <= p <= 64 lateral slices of B,
+    grows with p, and refuses an r_max whose small SVD working set
+    (r_max^2 + r_max p complex entries) would not fit in shared memory."""
+    from paper_2110_02485_gb300 import build, tprod
+    L = tprod.load(build.build())
+    P = tprod.RtsvdParams(1.0, 1.1, 0.1, 0.0, 2, 1, 16, 64, None)
+    sizes = [L.rtsvd_workspace_bytes(256, 256, 256, p, ctypes.byref(P), tprod.TP_FP32) for p in (1, 2, 17, 64)]
+    assert all(s > 0 for s in sizes) and sizes == sorted(sizes) and sizes[0] < sizes[-1]
+    for p in (0, 65, -1):
+        assert L.rtsvd_workspace_bytes(256, 256, 256, p, ctypes.byref(P), tprod.TP_FP32) == 0
+    # FP32 at r_max = 160: 160^2 + 160 p complex64 entries fit for p = 1, not for p = 64
+    P.r_max = 160
+    assert L.rtsvd_workspace_bytes(256, 256, 256, 1, ctypes.byref(P), tprod.TP_FP32) > 0
+    assert L.rtsvd_workspace_bytes(256, 256, 256, 64, ctypes.byref(P), tprod.TP_FP32) == 0

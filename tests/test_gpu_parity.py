@@ -128,7 +128,9 @@ def test_tprod_tf32_form(tp, n, l, kk, m, trans):
 
 # --------------------------------------------------------------- solvers ----
 
-def problem(N, n=None, seed=5, noise=1e-2, general=0.02, l=None):
+def problem(N, n=None, seed=5, noise=1e-2, general=0.02, l=None, p=1):
+    """Blurred synthetic images plus noise; p > 1 stacks p images as lateral
+    slices of B (delta = ||E||_F over all of them)."""
     n = N if n is None else n
     l = N if l is None else l
     T, c = synth.blur_factors(N, 1.3, 3, 1.5, n=n)
@@ -138,10 +140,10 @@ def problem(N, n=None, seed=5, noise=1e-2, general=0.02, l=None):
     A = A + general * P / np.linalg.norm(P) * np.linalg.norm(A)
     if l > N:  # tall slices: extra rows
         A = np.concatenate([A, 0.3 * g.standard_normal((n, l - N, N))], axis=1)
-    img = synth.synthetic_image(N, n, 3, 1, g)
-    Bt = O.tprod_bcirc(A, synth.lateral(img)) if N <= 24 else None
+    Xt = np.concatenate([synth.lateral(synth.synthetic_image(N, n, 3, 1, g)) for _ in range(p)], axis=2)
+    Bt = O.tprod_bcirc(A, Xt) if N <= 24 else None
     if Bt is None:
-        Bt = O.tprod(A, synth.lateral(img))
+        Bt = O.tprod(A, Xt)
     E = g.standard_normal(Bt.shape)
     E = noise * E / np.linalg.norm(E) * np.linalg.norm(Bt)
     return A.astype(np.float32), (Bt + E).astype(np.float32), float(np.linalg.norm(E))
@@ -179,6 +181,37 @@ def test_rtsvd_matches_oracle(tp, dtype, N, n, block, q, p_over, eps_rel):
     for k, rk in ref["res"].items():
         assert abs(hist[k] - rk) <= res_tol(rk, B, dtype)
     assert np.isclose(info["norm_a2"], O.fro2(A.astype(np.float64)), rtol=1e-6 if dtype == torch.float32 else 1e-12)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,block,p,r_max", [(12, 8, 4, 2, 12), (16, 9, 3, 5, 16), (20, 16, 8, 17, 20),
+                                               (24, 6, 16, 64, 24)])
+def test_rtsvd_several_lateral_slices_match_oracle(tp, dtype, N, n, block, p, r_max):
+    """Problem (I6): p lateral slices share the factorisation and one k chosen
+    from the Frobenius residual over all slices."""
+    A, B, delta = problem(N, n, seed=7 + p, p=p)
+    assert B.shape == (n, N, p)
+    Om = rnd((n, N, r_max), 12).astype(np.float32)
+    tau, p_over, eps_rel = 1.1, 3, 0.01
+    ref = O.rtsvd_solve(A.astype(np.float64), B.astype(np.float64), Om.astype(np.float64), delta, tau,
+                        eps_rel * np.sqrt(O.fro2(A.astype(np.float64))), p_over, block, 1, r_max=r_max)
+    X, info, hist = tp.rtsvd_solve(dev(A, dtype), dev(B, dtype), dev(Om, dtype), delta, tau, p_over, block, 1,
+                                   r_max=r_max, eps_rel=eps_rel, res_hist=True)
+    X = X.cpu().numpy()
+    assert X.shape == (n, N, p)
+    assert info["r"] == ref["r"]
+    for k, rk in ref["res"].items():
+        assert abs(hist[k] - rk) <= res_tol(rk, B, dtype)
+    if exact_k_required(ref, dtype):
+        assert info["k"] == ref["k"]
+        assert info["status"] == ref["status"]
+        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+        # slice j of the joint solve is the k-term filtered solution of slice j alone
+        j = p // 2
+        Xj = O.rtsvd_solve(A.astype(np.float64), B[:, :, j:j + 1].astype(np.float64), Om.astype(np.float64),
+                           delta, tau, eps_rel * np.sqrt(O.fro2(A.astype(np.float64))), p_over, block, 1,
+                           r_max=r_max, k_fixed=ref["k"])["X"]
+        assert rel(X[:, :, j:j + 1], Xj) <= TOL_X[dtype] * 10
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
