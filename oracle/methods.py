@@ -312,6 +312,18 @@ def tgkb_solve(A, B, delta, tau, k_max, k_fixed=None):
                 c=g["c"][:, :k], z=g["z"][:, :k + 1])
 
 
+def tgkb_p_solve(A, B, deltas, tau, k_max):
+    """tGKB_p (Section 1 and Section 4.3): problem (I6) with p lateral slices
+    B_j, each with its own noise bound ||E_j||_F <= delta_j, solved by
+    applying the tGKB method to every slice separately; slice j gets its own
+    number of steps k_j.  Returns X (n, m, p) and the per-slice records."""
+    n, l, p = B.shape
+    deltas = np.broadcast_to(np.asarray(deltas, dtype=np.float64), (p,))
+    outs = [tgkb_solve(A, B[:, :, j:j + 1], float(deltas[j]), tau, k_max) for j in range(p)]
+    X = np.concatenate([o["X"] for o in outs], axis=2)
+    return dict(X=X, k=[o["k"] for o in outs], status=[o["status"] for o in outs], per_slice=outs)
+
+
 # --------------------------------------------------------------------------
 # tGKT: Tikhonov regularisation of the tGKB-projected problem (Section 5).
 # --------------------------------------------------------------------------

@@ -237,6 +237,64 @@ def test_tgkb_discrepancy_bracket_with_brute_force_residual():
         assert r(O.tgkb_solve(A, B, delta, tau, 20, k_fixed=k - 1)["X"]) > tau * delta
 
 
+def slice_noise(A, Xt, levels, seed):
+    """B = A*Xt + E with slice j's noise of relative level levels[j];
+    returns B and delta_j = ||E_j||_F."""
+    Bt = O.tprod_bcirc(A, Xt)
+    g = np.random.default_rng(seed)
+    B, deltas = Bt.copy(), []
+    for j, lev in enumerate(levels):
+        E = g.standard_normal(Bt[:, :, j].shape)
+        E = lev * E / np.linalg.norm(E) * np.linalg.norm(Bt[:, :, j])
+        B[:, :, j] += E
+        deltas.append(float(np.linalg.norm(E)))
+    return B, deltas
+
+
+def test_tgkb_p_each_slice_meets_its_own_discrepancy_bound():
+    """tGKB_p (problem (I6) with ||E_j|| <= delta_j): slice j stops at the
+    first k_j whose residual ||B_j - A*X_j||_F, formed here through the
+    block-circulant product, is <= tau delta_j; different noise levels give
+    different k_j."""
+    A, _, _ = small_blur_multi(p=3)
+    Xt = np.concatenate([synth.lateral(synth.synthetic_image(10, 8, 3, 1, np.random.default_rng(40 + j)))
+                         for j in range(3)], axis=2)
+    B, deltas = slice_noise(A, Xt, [1e-1, 1e-2, 1e-3], 41)
+    tau = 1.1
+    out = O.tgkb_p_solve(A, B, deltas, tau, 10)
+    assert out["X"].shape == (8, 10, 3)
+    r = lambda X, j: np.sqrt(O.fro2(B[:, :, j:j + 1] - O.tprod_bcirc(A, X)))
+    for j in range(3):
+        kj = out["k"][j]
+        assert out["status"][j] == O.STATUS_OK
+        assert r(out["X"][:, :, j:j + 1], j) <= tau * deltas[j] * (1 + 1e-12)
+        if kj > 1:
+            prev = O.tgkb_solve(A, B[:, :, j:j + 1], deltas[j], tau, 10, k_fixed=kj - 1)["X"]
+            assert r(prev, j) > tau * deltas[j]
+    assert out["k"][0] < out["k"][1] < out["k"][2]
+
+
+def test_tgkb_p_slices_are_independent_and_homogeneous():
+    """Changing one slice leaves the others' k_j and X_j alone; scaling B_j
+    and delta_j by a > 0 scales X_j by a with the same k_j (the method is
+    positively homogeneous: Normalize divides the scale out)."""
+    A, B, delta = small_blur_multi(p=3)
+    d = [delta / np.sqrt(3.0)] * 3
+    tau = 1.1
+    out = O.tgkb_p_solve(A, B, d, tau, 10)
+    B2 = B.copy()
+    B2[:, :, 2] = 3.0 * B[:, :, 2] + 0.5
+    out2 = O.tgkb_p_solve(A, B2, [d[0], d[1], 3.0 * d[2]], tau, 10)
+    for j in range(2):
+        assert out2["k"][j] == out["k"][j]
+        assert np.array_equal(out2["X"][:, :, j], out["X"][:, :, j])
+    B3 = B.copy()
+    B3[:, :, 1] *= 7.5
+    out3 = O.tgkb_p_solve(A, B3, [d[0], 7.5 * d[1], d[2]], tau, 10)
+    assert out3["k"] == out["k"]
+    assert np.allclose(out3["X"][:, :, 1], 7.5 * out["X"][:, :, 1], rtol=0, atol=1e-11 * np.abs(out3["X"]).max())
+
+
 # ------------------------------------------------------------ tGKT ----
 
 def test_tgkt_full_space_is_dense_tikhonov():
