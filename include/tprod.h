@@ -177,14 +177,25 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
  * and a zero coefficient.  The whole iteration is one persistent launch with
  * one CTA per Fourier slice; its grid-wide wait is bounded (info->status
  * TP_ERR_TIMEOUT if it gives up).
- *   A : real (n, l, m)     B : real (n, l, 1)     X : real (n, m, 1)
- * Limits: k_max <= min(l, m, 512); l, m <= 1024; p = 1.
+ * With p > 1 lateral slices this is the tGKB_p method (Sections 1 and 4.3,
+ * problem (I6) with ||E_j||_F <= delta_j): every slice B_j is solved on its
+ * own, with its own bound delta_j and its own number of steps k_j.  Groups
+ * of 8 slices go through the iteration together in one launch, sharing the
+ * two products with A of each step; shapes that launch does not take (float
+ * data with odd m, or too little shared memory) run one launch per slice.
+ *   A : real (n, l, m)     B : real (n, l, p)     X : real (n, m, p)
+ *   d_info : p device records, record j for slice j
+ * Limits: k_max <= min(l, m, 512); l, m <= 1024; 1 <= p <= 1024.
  */
 typedef struct {
-    double delta;       /* noise bound of Eq. (errbd)                                 */
+    double delta;       /* noise bound of Eq. (errbd); with p > 1, the bound of every
+                           slice unless delta_p is given                               */
     double tau;         /* discrepancy factor                                         */
     int k_max;          /* step cap                                                   */
-    double* res_hist;   /* optional device array (k_max+1): residual after step i     */
+    double* res_hist;   /* optional device array, (k_max+1) entries per lateral slice
+                           (slice-major): residual after step i, -1 where not formed   */
+    const double* delta_p; /* optional HOST array of p bounds delta_j (p > 1); read
+                              before the call returns                                  */
 } tp_tgkb_params;
 
 size_t tgkb_workspace_bytes(int l, int m, int n, int p, const tp_tgkb_params* params, int prec);
@@ -199,7 +210,8 @@ tp_status tgkb_solve(const void* A, const void* B, int l, int m, int n, int p,
  * (Section 5) so that ||B - A*X_mu||_F = tau*delta, to a bracket width of
  * log_tol in log10(mu).  If even mu_hi leaves the residual above tau*delta,
  * mu = mu_hi and status TP_ERR_NOT_CONVERGED; if mu_lo already meets it,
- * mu = mu_lo.  X = W_k * Y_mu.
+ * mu = mu_lo.  X = W_k * Y_mu.  One lateral slice (p = 1; gkb.delta_p is
+ * ignored).
  */
 typedef struct {
     tp_tgkb_params gkb;

@@ -131,4 +131,30 @@ __host__ __device__ __forceinline__ double parseval_w(int s, int n) {
     return (s == 0 || 2 * s == n) ? 1.0 : 2.0;
 }
 
+// sqrt(a^2 + b^2) for Givens rotations whose arguments are norms of
+// working-precision vectors: for float data the plain form cannot overflow in
+// float64; double data needs the scaled hypot.
+template <typename T> __device__ __forceinline__ double givens_norm(double a, double b);
+template <> __device__ __forceinline__ double givens_norm<float>(double a, double b) { return sqrt(fma(a, a, b * b)); }
+template <> __device__ __forceinline__ double givens_norm<double>(double a, double b) { return hypot(a, b); }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// 16-byte loads of complex data: two float2 or one double2 per load.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; static constexpr int VW = 2; };
+template <> struct Vec16<double> { typedef double2 type; static constexpr int VW = 1; };
+
+template <typename T>
+__device__ __forceinline__ void unpack(const typename Vec16<T>::type& x, cplx<T>* o);
+template <> __device__ __forceinline__ void unpack<float>(const float4& x, float2* o) {
+    o[0] = make_float2(x.x, x.y);
+    o[1] = make_float2(x.z, x.w);
+}
+template <> __device__ __forceinline__ void unpack<double>(const double2& x, double2* o) { o[0] = x; }
+
 }  // namespace tp

@@ -20,6 +20,7 @@
 namespace tp {
 
 constexpr int GKB_KMAX = 512;
+constexpr int GKB_MAX_RHS = 1024;  // lateral slices of B per tgkb_solve call
 
 struct GkbShared {
     double res[GKB_KMAX + 1];   // global residual after step i
@@ -141,33 +142,9 @@ __device__ T normalize_vec(cplx<T>* u, int L, double* red, NormBc<T>* nb) {
     return nrm;
 }
 
-// sqrt(a^2 + b^2) for the Givens rotations: the arguments are norms of
-// working-precision vectors, so for float data the plain form cannot overflow
-// in float64; double data needs the scaled hypot.
-template <typename T> __device__ __forceinline__ double givens_norm(double a, double b);
-template <> __device__ __forceinline__ double givens_norm<float>(double a, double b) { return sqrt(fma(a, a, b * b)); }
-template <> __device__ __forceinline__ double givens_norm<double>(double a, double b) { return hypot(a, b); }
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // ---- streaming matrix-vector products over one Fourier slice --------------
 // 16-byte vector loads straight from global memory (the slice is contiguous),
 // eight rows in flight per thread, one CTA barrier per product.
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { typedef float4 type; static constexpr int VW = 2; };
-template <> struct Vec16<double> { typedef double2 type; static constexpr int VW = 1; };
-
-template <typename T>
-__device__ __forceinline__ void unpack(const typename Vec16<T>::type& x, cplx<T>* o);
-template <> __device__ __forceinline__ void unpack<float>(const float4& x, float2* o) {
-    o[0] = make_float2(x.x, x.y);
-    o[1] = make_float2(x.z, x.w);
-}
-template <> __device__ __forceinline__ void unpack<double>(const double2& x, double2* o) { o[0] = x; }
 
 // u = A^H q - z * w.  Requires m / VW <= blockDim (one vector column per
 // thread); rg = blockDim / (m / VW) row groups; part holds blockDim * VW entries.
@@ -385,7 +362,10 @@ template <typename T, bool VEC, int NT>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2)
 k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l, int m, int n, int h, int k_max,
       double tau_delta, cplx<T>* Wb, cplx<T>* Qb, T* cc, T* zz, double* res2, unsigned* counters,
-      cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info, int kc) {
+      cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info, int kc,
+      int bs) {
+    // bs: column stride of Bhat and Xhat (the lateral slice count of B; the
+    // pointers already point at this slice's column)
     typedef cplx<T> V;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = l > m ? l : m;
@@ -410,7 +390,7 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
     T* zs_ = zz + (long)s * (k_max + 1);
     const double ws = parseval_w(s, n);
 
-    for (int e = tid; e < l; e += blockDim.x) u[e] = Bhat[(long)s * l + e];
+    for (int e = tid; e < l; e += blockDim.x) u[e] = Bhat[((long)s * l + e) * bs];
     for (int e = tid; e < m; e += blockDim.x) w[e] = mk<T>(0, 0);
     __syncthreads();
     const T z1 = normalize_vec<T>(u, l, red, &nb);
@@ -545,7 +525,7 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
             x.x = fma(v.x, yt[j], x.x);
             x.y = fma(v.y, yt[j], x.y);
         }
-        Xhat[(long)s * m + e] = x;
+        Xhat[((long)s * m + e) * bs] = x;
     }
     if (s == 0 && tid == 0) {
         int status = flag_timeout ? TP_ERR_TIMEOUT : (flag_done ? TP_OK : TP_ERR_NOT_CONVERGED);
@@ -809,49 +789,57 @@ struct GkWs {
     unsigned* counters;
     double *res2, *fout;
     T *cc, *zz, *tout, *lam, *tscr;
+    double* gv;  // Givens data of the batched kernel (p > 1)
     cplx<T> *Ahat, *Bhat, *W, *Q, *Xhat;
     size_t bytes;
 };
 
 template <typename T>
-static GkWs<T> gk_carve(void* base, int l, int m, int n, int k_max) {
+static GkWs<T> gk_carve(void* base, int l, int m, int n, int k_max, int p) {
+    // p > 1: bases and step residuals for one group of GKM_PB lateral slices
+    // (groups run one after another), B-hat and X-hat for all p
     typedef cplx<T> V;
     const long h = n / 2 + 1;
+    const long pb = p > 1 ? GKM_PB : 1;
     Carver c(base, 0);
     GkWs<T> w;
     w.st = c.take<State>(1);
     w.ts = c.take<TikState>(1);
     w.counters = c.take<unsigned>(k_max + 1);
-    w.res2 = c.take<double>((long)(k_max + 1) * h);
+    w.res2 = c.take<double>((long)(k_max + 1) * h * pb);
     w.fout = c.take<double>(h);
     w.cc = c.take<T>(h * k_max);
     w.zz = c.take<T>(h * (k_max + 1));
     w.tout = c.take<T>((long)TIK_P * h);
     w.lam = c.take<T>(TIK_P);
     w.tscr = c.take<T>((long)TIK_P * h * 4 * k_max);
+    w.gv = p > 1 ? c.take<double>(h * pb * 3 * k_max) : nullptr;
     w.Ahat = c.take<V>(h * l * m);
-    w.Bhat = c.take<V>(h * l);
-    w.W = c.take<V>(h * (long)k_max * m);
-    w.Q = c.take<V>(h * (long)(k_max + 1) * l);
-    w.Xhat = c.take<V>(h * m);
+    w.Bhat = c.take<V>(h * l * p);
+    w.W = c.take<V>(h * pb * k_max * m);
+    w.Q = c.take<V>(h * pb * (k_max + 1) * l);
+    w.Xhat = c.take<V>(h * m * p);
     w.bytes = c.off;
     return w;
 }
 
 template <typename T>
 static tp_status gk_check(int l, int m, int n, int p, const tp_tgkb_params* P) {
-    if (!P || l < 1 || m < 1 || n < 1 || p != 1) return TP_ERR_ARG;
+    if (!P || l < 1 || m < 1 || n < 1 || p < 1 || p > GKB_MAX_RHS) return TP_ERR_ARG;
     if (l > 1024 || m > 1024 || n > (sizeof(T) == 4 ? 1024 : 512)) return TP_ERR_ARG;
     const int mn = l < m ? l : m;
     if (P->k_max < 1 || P->k_max > mn || P->k_max > GKB_KMAX) return TP_ERR_ARG;
     if (!(P->tau > 0.0) || !(P->delta >= 0.0)) return TP_ERR_ARG;
+    if (P->delta_p)
+        for (int j = 0; j < p; ++j)
+            if (!(P->delta_p[j] >= 0.0) || !isfinite(P->delta_p[j])) return TP_ERR_ARG;
     return TP_OK;
 }
 
 template <typename T>
 size_t gk_ws_bytes(int l, int m, int n, int p, const tp_tgkb_params* P) {
     if (gk_check<T>(l, m, n, p, P) != TP_OK) return 0;
-    return gk_carve<T>(nullptr, l, m, n, P->k_max).bytes;
+    return gk_carve<T>(nullptr, l, m, n, P->k_max, p).bytes;
 }
 
 #define TRY(x)                      \
@@ -860,14 +848,13 @@ size_t gk_ws_bytes(int l, int m, int n, int p, const tp_tgkb_params* P) {
         if (_e != TP_OK) return _e; \
     } while (0)
 
+// One single-slice tGKB launch: column bs-strided B-hat of one lateral slice
+// (Bhat_j, already offset) to its X-hat column (Xhat_j).
 template <typename T>
-static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tgkb_params* P, GkWs<T>& w,
-                        tp_info* info, int write_info, cudaStream_t st) {
-    const int h = n / 2 + 1, k_max = P->k_max;
-    const long lm = (long)l * m;
+static tp_status gk_single(const GkWs<T>& w, const cplx<T>* Bhat_j, cplx<T>* Xhat_j, int bs, int l, int m, int n,
+                           int k_max, double td, tp_info* info, double* res_hist, int write_info, cudaStream_t st) {
+    const int h = n / 2 + 1;
     if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (k_max + 1), st) != cudaSuccess) return TP_ERR_CUDA;
-    TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, nullptr, nullptr, st));
-    TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, nullptr, nullptr, st));
     const int L = l > m ? l : m;
     int dev = 0, nsm = 0, per_sm = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TP_ERR_CUDA;
@@ -897,15 +884,12 @@ static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tg
         return TP_ERR_CUDA;
     if (!coop || (long)per_sm * nsm < h) return TP_ERR_UNSUPPORTED;
     const cplx<T>* Ahat = w.Ahat;
-    const cplx<T>* Bhat = w.Bhat;
-    int l_ = l, m_ = m, n_ = n, h_ = h, k_ = k_max, wi = write_info;
-    double td = P->tau * P->delta;
+    int l_ = l, m_ = m, n_ = n, h_ = h, k_ = k_max, wi = write_info, bs_ = bs;
     long long spin = 4000000000LL;  // ~2 s at the GB300 SM clock
-    double* rh = P->res_hist;
     int kc_ = kc;
-    void* args[] = {(void*)&Ahat, (void*)&Bhat, &l_, &m_, &n_, &h_, &k_, &td, (void*)&w.W, (void*)&w.Q,
-                    (void*)&w.cc, (void*)&w.zz, (void*)&w.res2, (void*)&w.counters, (void*)&w.Xhat,
-                    (void*)&w.st, (void*)&info, (void*)&rh, &spin, &wi, &kc_};
+    void* args[] = {(void*)&Ahat, (void*)&Bhat_j, &l_, &m_, &n_, &h_, &k_, &td, (void*)&w.W, (void*)&w.Q,
+                    (void*)&w.cc, (void*)&w.zz, (void*)&w.res2, (void*)&w.counters, (void*)&Xhat_j,
+                    (void*)&w.st, (void*)&info, (void*)&res_hist, &spin, &wi, &kc_, &bs_};
     prof_begin(TP_KC_GKB, st);
     if (cudaLaunchCooperativeKernel(kern, dim3(h), dim3(nt), args, smem, st) != cudaSuccess)
         return TP_ERR_CUDA;
@@ -913,31 +897,95 @@ static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tg
 }
 
 template <typename T>
+static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tgkb_params* P, GkWs<T>& w,
+                        tp_info* info, int write_info, cudaStream_t st) {
+    const long lm = (long)l * m;
+    TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, nullptr, nullptr, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, nullptr, nullptr, st));
+    return gk_single<T>(w, w.Bhat, w.Xhat, 1, l, m, n, P->k_max, P->tau * P->delta, info, P->res_hist, write_info,
+                        st);
+}
+
+// tGKB_p: p lateral slices, each with its own delta_j and k_j.  Groups of
+// GKM_PB slices share the products with A in one batched launch; shapes that
+// the batched kernel does not take run one single-slice launch per slice.
+template <typename T>
+static tp_status gk_run_p(const T* A, const T* B, int l, int m, int n, int p, const tp_tgkb_params* P, GkWs<T>& w,
+                          tp_info* info, cudaStream_t st) {
+    const int h = n / 2 + 1, k_max = P->k_max;
+    TRY(rdft<T>(A, w.Ahat, n, l, m, m, (long)l * m, nullptr, nullptr, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, p, p, (long)l * p, nullptr, nullptr, st));
+    auto td_of = [&](int j) { return P->tau * (P->delta_p ? P->delta_p[j] : P->delta); };
+    int nt = 0;
+    size_t smem = 0;
+    const tp_status cfg = gkm_config<T>(l, m, n, k_max, &nt, &smem);
+    if (cfg == TP_OK) {
+        for (int j0 = 0; j0 < p; j0 += GKM_PB) {
+            GkmArgs a;
+            a.Ahat = w.Ahat;
+            a.Bhat = w.Bhat;
+            a.Wb = w.W;
+            a.Qb = w.Q;
+            a.Xhat = w.Xhat;
+            a.gv = w.gv;
+            a.res2 = w.res2;
+            a.counters = w.counters;
+            a.info = info;
+            a.res_hist = P->res_hist;
+            a.spin = 4000000000LL;  // ~2 s at the GB300 SM clock
+            a.l = l;
+            a.m = m;
+            a.n = n;
+            a.h = h;
+            a.k_max = k_max;
+            a.p = p;
+            a.j0 = j0;
+            a.pb = std::min(GKM_PB, p - j0);
+            for (int j = 0; j < GKM_PB; ++j) {
+                const double td = j < a.pb ? td_of(j0 + j) : 0.0;
+                a.td[j] = td;
+                a.td2n[j] = (double)n * td * td;
+            }
+            TRY(gkm_launch<T>(a, nt, smem, st));
+        }
+        return TP_OK;
+    }
+    if (cfg != TP_ERR_UNSUPPORTED) return cfg;
+    const cplx<T>* Bh = w.Bhat;
+    cplx<T>* Xh = w.Xhat;
+    for (int j = 0; j < p; ++j)
+        TRY(gk_single<T>(w, Bh + j, Xh + j, p, l, m, n, k_max, td_of(j), info + j,
+                         P->res_hist ? P->res_hist + (long)j * (k_max + 1) : nullptr, 1, st));
+    return TP_OK;
+}
+
+template <typename T>
 tp_status gk_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_tgkb_params* P, T* X,
                    tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
     TRY(gk_check<T>(l, m, n, p, P));
     if (!A || !B || !X || !info) return TP_ERR_ARG;
-    GkWs<T> w = gk_carve<T>(ws, l, m, n, P->k_max);
+    GkWs<T> w = gk_carve<T>(ws, l, m, n, P->k_max, p);
     if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
-    TRY(gk_run<T>(A, B, l, m, n, P, w, info, 1, st));
-    TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));
+    if (p == 1) TRY(gk_run<T>(A, B, l, m, n, P, w, info, 1, st));
+    else TRY(gk_run_p<T>(A, B, l, m, n, p, P, w, info, st));
+    TRY(irdft<T>(w.Xhat, X, n, m, p, p, (long)m * p, nullptr, st));
     return TP_OK;
 }
 
 template <typename T>
 size_t tik_ws_bytes(int l, int m, int n, int p, const tp_tik_params* P) {
-    if (!P) return 0;
+    if (!P || p != 1) return 0;  // Tikhonov-tGKB: one lateral slice
     return gk_ws_bytes<T>(l, m, n, p, &P->gkb);
 }
 
 template <typename T>
 tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_tik_params* P, T* X,
                     tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
-    if (!P) return TP_ERR_ARG;
+    if (!P || p != 1) return TP_ERR_ARG;
     TRY(gk_check<T>(l, m, n, p, &P->gkb));
     if (!(P->mu_lo > 0.0) || !(P->mu_hi > P->mu_lo)) return TP_ERR_ARG;
     if (!A || !B || !X || !info) return TP_ERR_ARG;
-    GkWs<T> w = gk_carve<T>(ws, l, m, n, P->gkb.k_max);
+    GkWs<T> w = gk_carve<T>(ws, l, m, n, P->gkb.k_max, 1);
     if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
     TRY(gk_run<T>(A, B, l, m, n, &P->gkb, w, info, 0, st));
     const int h = n / 2 + 1, k_max = P->gkb.k_max;

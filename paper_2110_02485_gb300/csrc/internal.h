@@ -68,6 +68,35 @@ tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long
                    long ldb, long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes,
                    cudaStream_t st, int trans_out = 0, const int* ncap = nullptr, int c0 = 0);
 
+// Batched tGKB (tGKB_p): one cooperative launch carries GKM_PB lateral
+// slices of B (columns j0 .. j0+pb-1) through Algorithm 4 in lockstep.
+// Complex arrays are cplx<T>: Ahat (h, l, m), Bhat (h, l, p), Wb (h, PB,
+// k_max, m), Qb (h, PB, k_max+1, l), Xhat (h, m, p); gv (h, PB, 3, k_max)
+// Givens data; res2 (k_max+1, PB, h); counters (k_max+1, zeroed by the
+// launcher); info: p records; res_hist (optional): (p, k_max+1).
+constexpr int GKM_PB = 8;
+struct GkmArgs {
+    const void* Ahat;
+    const void* Bhat;
+    void* Wb;
+    void* Qb;
+    void* Xhat;
+    double* gv;
+    double* res2;
+    unsigned* counters;
+    tp_info* info;
+    double* res_hist;
+    long long spin;  // bound of each grid-wide wait, in SM clock cycles
+    int l, m, n, h, k_max, p, j0, pb;
+    double td[GKM_PB];    // tau * delta_j
+    double td2n[GKM_PB];  // n (tau delta_j)^2, compared with the Parseval sums
+};
+// Launch configuration of the batched kernel for these sizes (threads per
+// CTA, dynamic shared memory); TP_ERR_UNSUPPORTED when its CTAs cannot all be
+// resident or the rows of A are not 16-byte multiples.  Enqueues nothing.
+template <typename T> tp_status gkm_config(int l, int m, int n, int k_max, int* nt, size_t* smem);
+template <typename T> tp_status gkm_launch(const GkmArgs& a, int nt, size_t smem, cudaStream_t st);
+
 // Device-side bookkeeping shared by a solve.
 struct State {
     double norm_a2;   // ||A||_F^2

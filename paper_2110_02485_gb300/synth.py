@@ -172,6 +172,7 @@ def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | 
     B, delta = add_noise(B_true if frames > 1 else B_true[0], noise, rng)
     B = B.reshape(frames, N, N)
     out = dict(cfg=cfg, A=A, B=np.concatenate([lateral(b) for b in B], axis=2).astype(np.float32),
+               B_true=np.concatenate([lateral(b) for b in B_true], axis=2),
                X_true=np.concatenate([lateral(img) for img in imgs], axis=2).astype(np.float32), delta=delta,
                noise=noise, T=T, c=c)
     if with_omega:

@@ -34,7 +34,7 @@ class RtsvdParams(ctypes.Structure):
 
 class TgkbParams(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double), ("k_max", ctypes.c_int),
-                ("res_hist", ctypes.c_void_p)]
+                ("res_hist", ctypes.c_void_p), ("delta_p", ctypes.c_void_p)]
 
 
 class TikParams(ctypes.Structure):
@@ -242,8 +242,15 @@ def _info_dict(buf: torch.Tensor) -> dict:
     return {f: getattr(o, f) for f, _ in TpInfo._fields_}
 
 
-def _info_buf(device):
-    return torch.zeros(ctypes.sizeof(TpInfo), dtype=torch.uint8, device=device)
+def _info_list(buf: torch.Tensor, p: int) -> list:
+    raw = bytes(buf.cpu().numpy().tobytes())
+    sz = ctypes.sizeof(TpInfo)
+    recs = [TpInfo.from_buffer_copy(raw[j * sz:(j + 1) * sz]) for j in range(p)]
+    return [{f: getattr(o, f) for f, _ in TpInfo._fields_} for o in recs]
+
+
+def _info_buf(device, count=1):
+    return torch.zeros(count * ctypes.sizeof(TpInfo), dtype=torch.uint8, device=device)
 
 
 def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None, eps=0.0, eps_rel=0.0,
@@ -282,26 +289,40 @@ def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None
     return out + ((hist.cpu().numpy(),) if res_hist else ())
 
 
-def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True):
-    """tGKB method (Algorithm 4 + Eq. (solgkb)).  Returns (X, info[, res_hist])."""
+def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None):
+    """tGKB method (Algorithm 4 + Eq. (solgkb)).  Returns (X, info[, res_hist]).
+
+    B is (n, l, p); p > 1 is the tGKB_p method: every lateral slice j is
+    solved on its own with bound deltas[j] (default: delta for all) and its own
+    k_j; info is then a list of p records and res_hist a (p, k_max+1) array."""
     _dev(A, B)
     n, l, m = A.shape
+    p = B.shape[2]
     prec = _prec(A)
-    X = torch.empty((n, m, 1), dtype=A.dtype, device=A.device)
-    hist = torch.empty(k_max + 1, dtype=torch.float64, device=A.device) if res_hist else None
-    P = TgkbParams(float(delta), float(tau), int(k_max), hist.data_ptr() if hist is not None else None)
+    X = torch.empty((n, m, p), dtype=A.dtype, device=A.device)
+    hist = torch.empty((p, k_max + 1), dtype=torch.float64, device=A.device) if res_hist else None
+    dp = None
+    if deltas is not None:
+        dl = [float(d) for d in deltas]
+        if len(dl) != p:
+            raise ValueError("deltas needs one bound per lateral slice")
+        dp = (ctypes.c_double * p)(*dl)
+    P = TgkbParams(float(delta), float(tau), int(k_max), hist.data_ptr() if hist is not None else None,
+                   ctypes.cast(dp, ctypes.c_void_p) if dp is not None else None)
     L = load()
-    nb = L.tgkb_workspace_bytes(l, m, n, 1, ctypes.byref(P), prec)
+    nb = L.tgkb_workspace_bytes(l, m, n, p, ctypes.byref(P), prec)
     if nb == 0:
         raise TprodError("tgkb_workspace_bytes", TP_ERR_ARG)
     ws = _workspace(nb, A.device)
     wp, wn = _aligned(ws)
-    info = _info_buf(A.device)
-    _check("tgkb_solve", L.tgkb_solve(_ptr(A), _ptr(B), l, m, n, 1, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp,
+    info = _info_buf(A.device, p)
+    _check("tgkb_solve", L.tgkb_solve(_ptr(A), _ptr(B), l, m, n, p, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp,
                                       wn, _stream()))
+    if p == 1 and hist is not None:
+        hist = hist[0]
     if not sync:
         return X, info, hist
-    out = (X, _info_dict(info))
+    out = (X, _info_dict(info) if p == 1 else _info_list(info, p))
     return out + ((hist.cpu().numpy(),) if res_hist else ())
 
 

@@ -231,6 +231,71 @@ def test_tgkb_matches_oracle(tp, dtype, N, n, k_max, l):
             assert abs(hist[i] - ri) <= res_tol(ri, B, dtype)
 
 
+def problem_p(N, n, levels, seed=21, general=0.02):
+    """Blur operator, len(levels) synthetic images as lateral slices, slice j
+    with noise of relative level levels[j]; returns A, B, delta_j."""
+    T, c = synth.blur_factors(N, 1.3, 3, 1.5, n=n)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    g = np.random.default_rng(seed)
+    P = g.standard_normal(A.shape)
+    A = A + general * P / np.linalg.norm(P) * np.linalg.norm(A)
+    Xt = np.concatenate([synth.lateral(synth.synthetic_image(N, n, 3, 1, g)) for _ in levels], axis=2)
+    Bt = O.tprod(A, Xt)
+    B, deltas = Bt.copy(), []
+    for j, lev in enumerate(levels):
+        E = g.standard_normal(Bt[:, :, j].shape)
+        E = lev * E / np.linalg.norm(E) * np.linalg.norm(Bt[:, :, j])
+        B[:, :, j] += E
+        deltas.append(float(np.linalg.norm(E)))
+    return A.astype(np.float32), B.astype(np.float32), deltas
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,p,k_max", [(12, 8, 3, 12), (16, 9, 8, 16), (20, 16, 11, 20), (13, 10, 5, 13),
+                                         (32, 32, 9, 32)])
+def test_tgkb_p_matches_oracle(tp, dtype, N, n, p, k_max):
+    """tGKB_p: every lateral slice with its own delta_j and k_j, against the
+    oracle's per-slice tGKB.  Float data with odd m (N = 13) runs the
+    one-launch-per-slice form, the rest the batched launch (groups of 8)."""
+    levels = [(1e-1, 1e-2, 1e-3, 3e-2, 3e-3)[j % 5] for j in range(p)]
+    A, B, deltas = problem_p(N, n, levels, seed=N + p)
+    tau = 1.1
+    ref = O.tgkb_p_solve(A.astype(np.float64), B.astype(np.float64), deltas, tau, k_max)
+    X, infos, hist = tp.tgkb_solve(dev(A, dtype), dev(B, dtype), 0.0, tau, k_max, res_hist=True, deltas=deltas)
+    X = X.cpu().numpy()
+    assert X.shape == (n, N, p) and len(infos) == p and hist.shape == (p, k_max + 1)
+    for j in range(p):
+        r, info = ref["per_slice"][j], infos[j]
+        assert info["tau_delta"] == pytest.approx(tau * deltas[j], rel=1e-15)
+        for i, ri in r["res"].items():
+            if i <= info["k"]:
+                assert abs(hist[j, i] - ri) <= res_tol(ri, B[:, :, j:j + 1], dtype)
+        assert all(hist[j, i] == -1.0 for i in range(info["k"] + 1, k_max + 1))
+        if exact_k_required(r, dtype):
+            assert info["k"] == r["k"], j
+            assert info["status"] == r["status"]
+            assert rel(X[:, :, j], r["X"][:, :, 0]) <= TOL_X[dtype] * 10
+            assert abs(info["residual"] - r["res"][r["k"]]) <= res_tol(r["res"][r["k"]], B[:, :, j:j + 1], dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_tgkb_p_common_delta_and_cap(tp, dtype):
+    """tGKB_p with one delta for every slice (delta_p not given) and a step cap
+    that some slices reach (NOT_CONVERGED) while others stop earlier."""
+    A, B, deltas = problem_p(16, 8, [1e-1, 1e-3, 1e-1, 1e-3, 1e-2, 1e-1], seed=3)
+    tau, k_max = 1.1, 4
+    d = float(np.median(deltas))
+    ref = O.tgkb_p_solve(A.astype(np.float64), B.astype(np.float64), [d] * 6, tau, k_max)
+    X, infos = tp.tgkb_solve(dev(A, dtype), dev(B, dtype), d, tau, k_max)
+    X = X.cpu().numpy()
+    assert {r["status"] for r in ref["per_slice"]} == {O.STATUS_OK, O.STATUS_NOT_CONVERGED}
+    for j in range(6):
+        r = ref["per_slice"][j]
+        if exact_k_required(r, dtype):
+            assert infos[j]["k"] == r["k"] and infos[j]["status"] == r["status"]
+            assert rel(X[:, :, j], r["X"][:, :, 0]) <= TOL_X[dtype] * 10
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("N,n,k_max,lo,hi", [(12, 8, 12, 1e-3, 1e9), (16, 17, 16, 1e-2, 1e8), (32, 32, 32, 1e-1, 1e9)])
 def test_tgkt_matches_oracle(tp, dtype, N, n, k_max, lo, hi):
