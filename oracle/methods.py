@@ -219,6 +219,22 @@ def rtsvd_solve(A, B, Omega, delta, tau, eps, p_over, block=16, q_power=1,
 # tGKB (Algorithm 4) and the tGKB method (Eqs. (9tt), (solgkb)).
 # --------------------------------------------------------------------------
 
+def rtsvd_adjoint(out: dict, G: np.ndarray) -> np.ndarray:
+    """Adjoint of the linear map B -> X_k of an rtsvd_solve result, at its k:
+    X_k = V_k S_k^{-1} U_k^T * B (Section 4.2, with U_k = Q * U-tilde_k from the
+    full tSVD of B-tilde), so dL/dB = U_k S_k^{-1} V_k^T * G for G = dL/dX_k,
+    the t-transpose of the filter (Section 2: the t-product's adjoint is the
+    t-transpose).  Fourier slice by slice; singular values the solve dropped
+    (_inv_sigma) are dropped here too."""
+    Q, Bt, k = out["Q"], out["Bt"], out["k"]
+    Ub, S, V = tsvd_hat(Bt)
+    l, m = Q.shape[1], V.shape[1]
+    inv = _inv_sigma(S, max(l, m))[:, :k]
+    Uk = Q @ Ub[:, :, :k]                                 # (n, l, k)
+    t = _ct(V[:, :, :k]) @ fft3(G)                        # (n, k, p)
+    return ifft3_real(Uk @ (inv[:, :, None] * t))
+
+
 def _reorth(v: np.ndarray, basis: list) -> np.ndarray:
     """Two CGS passes of v (n, d) against the Fourier-domain vectors in basis."""
     if not basis:

@@ -89,6 +89,16 @@ def test_transpose_identity_and_definition():
     assert np.allclose(Ath, np.conj(np.swapaxes(Ah, 1, 2)), atol=1e-12)
 
 
+def test_tproduct_adjoint_is_the_t_transpose():
+    """<G, A * B> = <A^T * G, B> = <G * B^T, A>: the t-transpose is the adjoint
+    of the t-product in both arguments (the gradient rules of the t-product)."""
+    g = np.random.default_rng(12)
+    A, B, G = g.standard_normal((5, 3, 4)), g.standard_normal((5, 4, 2)), g.standard_normal((5, 3, 2))
+    lhs = np.sum(G * O.tprod_bcirc(A, B))
+    assert np.isclose(lhs, np.sum(O.tprod_bcirc(O.ttranspose(A), G) * B), rtol=1e-12)
+    assert np.isclose(lhs, np.sum(O.tprod_bcirc(G, O.ttranspose(B)) * A), rtol=1e-12)
+
+
 def test_identity_tensor():
     A = rnd((5, 3, 4), 8)
     assert np.allclose(O.tprod(O.tidentity(3, 5), A), A, atol=1e-13)

@@ -158,6 +158,29 @@ def test_rtsvd_duplicated_lateral_slice_gives_the_single_slice_answer():
         assert np.allclose(two["X"][:, :, c:c + 1], one["X"], atol=1e-10 * np.abs(one["X"]).max())
 
 
+def test_rtsvd_adjoint_satisfies_the_adjoint_identity():
+    """At fixed k, B -> X_k is linear; its adjoint must satisfy
+    <G, X_k(E)> = <adjoint(G), E> for any E and G (real inner products), the
+    forward side computed by the solver itself on E.  Also pinned: the
+    adjoint of a p-slice G is the slice-wise adjoint."""
+    A, B, delta = small_blur_multi(p=2)
+    n, l, m = A.shape
+    Om = rnd((n, m, m), 10)
+    tau, eps = 1.1, 0.02 * np.sqrt(O.fro2(A))
+    out = O.rtsvd_solve(A, B, Om, delta, tau, eps, 3, 2, 1, r_max=m)
+    k = out["k"]
+    g = np.random.default_rng(77)
+    for _ in range(3):
+        E = g.standard_normal((n, l, 2))
+        G = g.standard_normal((n, m, 2))
+        XE = O.rtsvd_solve(A, E, Om, delta, tau, eps, 3, 2, 1, r_max=m, k_fixed=k)["X"]
+        adj = O.rtsvd_adjoint(out, G)
+        assert adj.shape == (n, l, 2)
+        assert np.isclose(np.sum(G * XE), np.sum(adj * E), rtol=1e-10)
+    one = O.rtsvd_adjoint(out, G[:, :, 1:2])
+    assert np.allclose(adj[:, :, 1:2], one, rtol=0, atol=1e-12 * np.abs(one).max())
+
+
 def test_ttsvd_discrepancy_bracket_with_brute_force_residual():
     A, B, delta = small_blur()
     tau = 1.1
