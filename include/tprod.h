@@ -93,18 +93,20 @@ tp_status tprod_fft(const void* A, int l, int m, int n, void* Ahat, int prec, vo
 tp_status tprod_ifft(const void* Xhat, int l, int m, int n, void* X, int prec, void* stream);
 
 /* ---------------------------------------------------------- t-product -----
- * tprod_gemm: C = op(A) * B, the t-product of Definition 2.1 computed as
+ * tprod_gemm: C = op(A) * op(B), the t-product of Definition 2.1 computed as
  * mode-3 DFT, one complex matrix product per Fourier slice, inverse DFT.
- *   transA = 0: A is l x kk x n, array (n, l, kk);  C is l x m x n
- *   transA = 1: op(A) = A^T, the t-transpose of Section 2 (each frontal slice
- *               transposed, slices 2..n reversed); A is kk x l x n,
- *               array (n, kk, l).
- *   B : real (n, kk, m);  C : real (n, l, m)
+ * op(X) = X^T is the t-transpose of Section 2 (each frontal slice transposed,
+ * slices 2..n reversed), the adjoint of the t-product: for C = A * B,
+ * dL/dA = G * B^T and dL/dB = A^T * G.  trans bit 0 selects op(A), bit 1
+ * op(B):
+ *   bit 0 clear: A is l x kk x n, array (n, l, kk);  set: A is kk x l x n, (n, kk, l)
+ *   bit 1 clear: B is kk x m x n, array (n, kk, m);  set: B is m x kk x n, (n, m, kk)
+ *   C : real (n, l, m)
  * Workspace: tprod_gemm_workspace_bytes(l, kk, m, n, prec).
  */
 size_t tprod_gemm_workspace_bytes(int l, int kk, int m, int n, int prec);
 tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m, int n,
-                     int transA, int prec, void* ws, size_t ws_bytes, void* stream);
+                     int trans, int prec, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------- t-product, no allocation -----
  * tprod_gemm_noalloc: the same product as tprod_gemm, for callers that cannot
@@ -121,7 +123,8 @@ tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m
  * The first call on each device looks up the array's device address (with
  * that device current); make it before any stream capture.  Calls share the
  * array, so calls that overlap on the GPU race; nothing needs clearing
- * between calls.  Arguments and layouts as tprod_gemm.
+ * between calls.  Arguments and layouts as tprod_gemm with trans bit 1
+ * clear (transA = 0 or 1).
  */
 tp_status tprod_gemm_noalloc(const void* A, const void* B, void* C, int l, int kk, int m, int n,
                              int transA, int prec, void* stream);
@@ -166,6 +169,27 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
                                 int l, int m, int n, int p, const tp_rtsvd_params* params,
                                 void* X, tp_info* d_info, int prec,
                                 void* ws, size_t ws_bytes, void* stream);
+
+/* rtsvd_adjoint: the adjoint of the map B -> X_k of the last
+ * rtsvd_truncated_solve made with this workspace and the same arguments
+ * (A, Omega, l, m, n, p, params, prec), for differentiation.  With k held at
+ * the value that solve chose, X_k = V_k * S_k^{-1} * U_k^T * B is linear in
+ * B, and for G = dL/dX_k
+ *   dL/dB = U_k * S_k^{-1} * V_k^T * G,
+ * the t-transpose of the filter (the adjoint of the t-product is the
+ * t-transpose, Section 2).  It is formed from what the solve left in the
+ * workspace: per Fourier slice U_k = Q Q^H K_k S_k^{-1} with K = A-hat V
+ * (U-tilde_k = B-tilde V_k S_k^{-1}), so
+ *   dB-hat = Q Q^H K_k S_k^{-2} V_k^H G-hat,
+ * with the terms of singular values the solve treated as zero dropped.  The
+ * paper has no counterpart; it is a service for gradient-based use.
+ *   G : real (n, m, p)      dB : real (n, l, p)
+ * The workspace must be untouched since that solve; the call overwrites the
+ * solve's B-hat, d, alpha and X-hat scratch, not the factorisation, so it can
+ * be repeated.  prec as for the solve (TP_TF32 computes as TP_FP32).
+ */
+tp_status rtsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_rtsvd_params* params,
+                        void* dB, int prec, void* ws, size_t ws_bytes, void* stream);
 
 /* -------------------------------------------------------------- tGKB ------
  * tgkb_solve: the tGKB method (Algorithm 4 with both reorthogonalisation

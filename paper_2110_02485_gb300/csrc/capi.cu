@@ -70,6 +70,8 @@ template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_para
 template <typename T>
 tp_status rt_solve(const T*, const T*, const T*, int, int, int, int, const tp_rtsvd_params*, T*, tp_info*, void*,
                    size_t, cudaStream_t, int);
+template <typename T>
+tp_status rt_adjoint(const T*, int, int, int, int, const tp_rtsvd_params*, T*, void*, size_t, cudaStream_t);
 template <typename T> size_t gk_ws_bytes(int, int, int, int, const tp_tgkb_params*);
 template <typename T>
 tp_status gk_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
@@ -101,7 +103,7 @@ static size_t gemm_ws(int l, int kk, int m, int n, size_t c) {
 }
 
 template <typename T>
-static tp_status gemm_t(const void* A, const void* B, void* C, int l, int kk, int m, int n, int transA, void* ws,
+static tp_status gemm_t(const void* A, const void* B, void* C, int l, int kk, int m, int n, int trans, void* ws,
                         cudaStream_t st, int tc_passes = 3) {
     const int h = n / 2 + 1;
     const size_t c = 2 * sizeof(T);
@@ -109,14 +111,17 @@ static tp_status gemm_t(const void* A, const void* B, void* C, int l, int kk, in
     void* Ah = p;
     void* Bh = p + align256((size_t)h * l * kk * c);
     void* Ch = (char*)Bh + align256((size_t)h * kk * m * c);
-    // A is (n, l, kk) or, transposed, (n, kk, l)
-    const int ar = transA ? kk : l, ac = transA ? l : kk;
+    // A is (n, l, kk) or, t-transposed, (n, kk, l); B is (n, kk, m) or (n, m, kk).
+    // The t-transpose is the conjugate transpose of every Fourier slice.
+    const bool tA = trans & 1, tB = trans & 2;
+    const int ar = tA ? kk : l, ac = tA ? l : kk;
+    const int br = tB ? m : kk, bc = tB ? kk : m;
     tp_status e = rdft<T>((const T*)A, Ah, n, ar, ac, ac, (long)ar * ac, nullptr, nullptr, st);
     if (e != TP_OK) return e;
-    e = rdft<T>((const T*)B, Bh, n, kk, m, m, (long)kk * m, nullptr, nullptr, st);
+    e = rdft<T>((const T*)B, Bh, n, br, bc, bc, (long)br * bc, nullptr, nullptr, st);
     if (e != TP_OK) return e;
-    e = cgemm<T>(h, l, m, kk, nullptr, nullptr, nullptr, 1, 0, Ah, ac, (long)ar * ac, transA ? OP_C : OP_N, Bh, m,
-                 (long)kk * m, OP_N, 0, 0, Ch, m, (long)l * m, nullptr, st, nullptr, tc_passes);
+    e = cgemm<T>(h, l, m, kk, nullptr, nullptr, nullptr, 1, 0, Ah, ac, (long)ar * ac, tA ? OP_C : OP_N, Bh, bc,
+                 (long)br * bc, tB ? OP_C : OP_N, 0, 0, Ch, m, (long)l * m, nullptr, st, nullptr, tc_passes);
     if (e != TP_OK) return e;
     return irdft<T>(Ch, (T*)C, n, l, m, m, (long)l * m, nullptr, st);
 }
@@ -148,18 +153,18 @@ size_t tprod_gemm_workspace_bytes(int l, int kk, int m, int n, int prec) {
     return gemm_ws(l, kk, m, n, prec == TP_FP32 ? 8 : 16);
 }
 
-tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m, int n, int transA, int prec,
+tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m, int n, int trans, int prec,
                      void* ws, size_t ws_bytes, void* stream) {
     const int passes = prec == TP_TF32 ? 1 : 3;
     prec = data_prec(prec);
     if (!A || !B || !C || !dims_ok(l, kk, n, prec) || !dims_ok(kk, m, n, prec)) return TP_ERR_ARG;
-    if (transA != 0 && transA != 1) return TP_ERR_ARG;
+    if (trans < 0 || trans > 3) return TP_ERR_ARG;
     if (l > 65535 * 128) return TP_ERR_ARG;
     const size_t need = gemm_ws(l, kk, m, n, prec == TP_FP32 ? 8 : 16);
     if (!ws || ((size_t)ws & 255) || ws_bytes < need) return TP_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
-    return prec == TP_FP32 ? gemm_t<float>(A, B, C, l, kk, m, n, transA, ws, st, passes)
-                           : gemm_t<double>(A, B, C, l, kk, m, n, transA, ws, st);
+    return prec == TP_FP32 ? gemm_t<float>(A, B, C, l, kk, m, n, trans, ws, st, passes)
+                           : gemm_t<double>(A, B, C, l, kk, m, n, trans, ws, st);
 }
 
 size_t rtsvd_workspace_bytes(int l, int m, int n, int p, const tp_rtsvd_params* params, int prec) {
@@ -179,6 +184,15 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
     if (prec == TP_FP64)
         return rt_solve<double>((const double*)A, (const double*)B, (const double*)Omega, l, m, n, p, params,
                                 (double*)X, d_info, ws, ws_bytes, st, 3);
+    return TP_ERR_ARG;
+}
+
+tp_status rtsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_rtsvd_params* params, void* dB,
+                        int prec, void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32 || prec == TP_TF32)
+        return rt_adjoint<float>((const float*)G, l, m, n, p, params, (float*)dB, ws, ws_bytes, st);
+    if (prec == TP_FP64) return rt_adjoint<double>((const double*)G, l, m, n, p, params, (double*)dB, ws, ws_bytes, st);
     return TP_ERR_ARG;
 }
 

@@ -760,10 +760,11 @@ static size_t jacobi_smem(int r, size_t c, int np) {
     return (size_t)r * r * c + (size_t)r * np * c + (size_t)r * sizeof(double) + (size_t)r * sizeof(int);
 }
 
-// alpha_j = d'_j / sigma_j, dropping sigma_j <= dims * eps * sigma_max.
+// alpha_j = d'_j / sigma_j^pw (pw = 1: the solution coefficients; pw = 2:
+// the adjoint's), dropping sigma_j <= dims * eps * sigma_max.
 template <typename T>
 __global__ void k_alpha(const T* sigma, long ssig, const cplx<T>* dprime, long sdp, cplx<T>* alpha, long sa,
-                        const State* st, int h, int dims, int r_max, int np) {
+                        const State* st, int h, int dims, int r_max, int np, int pw = 1) {
     __shared__ double red[32];
     const int r = st->r, s = blockIdx.x;
     double mx = 0.0;
@@ -782,7 +783,8 @@ __global__ void k_alpha(const T* sigma, long ssig, const cplx<T>* dprime, long s
             const double sv = (double)sigma[(long)s * ssig + j];
             if (sv > tol) {
                 const cplx<T> v = dprime[(long)s * sdp + e];
-                a = mk<T>((T)(v.x / sv), (T)(v.y / sv));
+                const double dv = pw == 2 ? sv * sv : sv;
+                a = mk<T>((T)(v.x / dv), (T)(v.y / dv));
             }
         }
         alpha[(long)s * sa + e] = a;
@@ -1099,6 +1101,42 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     return TP_OK;
 }
 
+// Adjoint of B -> X_k for the factorisation and k that the last rt_solve
+// left in ws (same arguments).  Per Fourier slice, with K = A-hat V-tilde:
+//   dB-hat = Q Q^H K_k S_k^{-2} V_k^H G-hat
+// (U-tilde_k = B-tilde V_k S_k^{-1} = Q^H K_k S_k^{-1}).
+template <typename T>
+tp_status rt_adjoint(const T* G, int l, int m, int n, int p, const tp_rtsvd_params* P, T* dB, void* ws,
+                     size_t ws_bytes, cudaStream_t st) {
+    TRY(rt_check<T>(l, m, n, p, P));
+    if (!G || !dB) return TP_ERR_ARG;
+    const int r_max = P->r_max, h = n / 2 + 1;
+    RtWs<T> w = rt_carve<T>(ws, l, m, n, P->block, r_max, p);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
+    const long rp = (long)r_max * p;
+    const int* dr = &w.st->r;
+    const int* dk = &w.st->k;
+    TRY(rdft<T>(G, w.Xhat, n, m, p, p, (long)m * p, nullptr, nullptr, st));
+    // t = V_k^H G-hat (k x p), then t_j / sigma_j^2
+    TRY(cgemm<T>(h, r_max, p, m, dk, 0, 0, 1, 0, w.Vt, r_max, (long)m * r_max, OP_C, w.Xhat, p, (long)m * p, OP_N, 0,
+                 0, w.alpha, p, rp, nullptr, st));
+    prof_begin(TP_KC_MISC, st);
+    k_alpha<T><<<h, 256, 0, st>>>(w.sigma, r_max, w.alpha, rp, w.alpha, rp, w.st, h, l > m ? l : m, r_max, p, 2);
+    TRY(launched(TP_KC_MISC, st));
+    // y = K_k t (K stored transposed), z = Q^H y, dB-hat = Q z
+    TRY(cgemm<T>(h, l, p, r_max, 0, 0, dk, 1, 0, w.KhT, l, (long)r_max * l, OP_T, w.alpha, p, rp, OP_N, 0, 0, w.Bhat,
+                 p, (long)l * p, nullptr, st));
+    TRY(cgemm<T>(h, r_max, p, l, dr, 0, 0, 1, 0, w.Q, l, (long)r_max * l, OP_R, w.Bhat, p, (long)l * p, OP_N, 0, 0,
+                 w.d, p, rp, nullptr, st));
+    TRY(cgemm<T>(h, l, p, r_max, 0, 0, dr, 1, 0, w.Q, l, (long)r_max * l, OP_T, w.d, p, rp, OP_N, 0, 0, w.Bhat, p,
+                 (long)l * p, nullptr, st));
+    return irdft<T>(w.Bhat, dB, n, l, p, p, (long)l * p, nullptr, st);
+}
+
+template tp_status rt_adjoint<float>(const float*, int, int, int, int, const tp_rtsvd_params*, float*, void*, size_t,
+                                     cudaStream_t);
+template tp_status rt_adjoint<double>(const double*, int, int, int, int, const tp_rtsvd_params*, double*, void*,
+                                      size_t, cudaStream_t);
 template size_t rt_ws_bytes<float>(int, int, int, int, const tp_rtsvd_params*);
 template size_t rt_ws_bytes<double>(int, int, int, int, const tp_rtsvd_params*);
 template tp_status rt_solve<float>(const float*, const float*, const float*, int, int, int, int,

@@ -46,7 +46,7 @@ class TikParams(ctypes.Structure):
 EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm", "rtsvd_workspace_bytes",
            "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
            "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
-           "tp_timing_read", "tprod_gemm_noalloc")
+           "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -77,6 +77,7 @@ def load(path: str | None = None):
     L.rtsvd_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(RtsvdParams), i]
     L.rtsvd_workspace_bytes.restype = sz
     L.rtsvd_truncated_solve.argtypes = [vp, vp, vp, i, i, i, i, ctypes.POINTER(RtsvdParams), vp, vp, i, vp, sz, vp]
+    L.rtsvd_adjoint.argtypes = [vp, i, i, i, i, ctypes.POINTER(RtsvdParams), vp, i, vp, sz, vp]
     L.tgkb_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TgkbParams), i]
     L.tgkb_workspace_bytes.restype = sz
     L.tgkb_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TgkbParams), vp, vp, i, vp, sz, vp]
@@ -191,8 +192,10 @@ def ifft(Xh: torch.Tensor, n: int) -> torch.Tensor:
     return out
 
 
-def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False, tf32: bool = False) -> torch.Tensor:
-    """t-product op(A) * B.  A (n, l, kk) [or (n, kk, l) with transA], B (n, kk, m).
+def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False, tf32: bool = False,
+          transB: bool = False) -> torch.Tensor:
+    """t-product op(A) * op(B), op = the t-transpose when asked.  A (n, l, kk)
+    [or (n, kk, l) with transA], B (n, kk, m) [or (n, m, kk) with transB].
 
     tf32=True (float32 only): the TP_TF32 precision form (one tf32 product on
     the tensor cores instead of the float32-accurate split)."""
@@ -200,8 +203,9 @@ def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False, tf32: bool = F
     if A.dtype != B.dtype:
         raise TypeError("A and B must share a dtype")
     n, a1, a2 = A.shape
-    nb, kk, m = B.shape
+    nb, b1, b2 = B.shape
     l = a2 if transA else a1
+    kk, m = (b2, b1) if transB else (b1, b2)
     if nb != n or (a1 if transA else a2) != kk:
         raise ValueError("shape mismatch")
     prec = _prec(A)
@@ -213,8 +217,33 @@ def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False, tf32: bool = F
     L = load()
     ws = _workspace(L.tprod_gemm_workspace_bytes(l, kk, m, n, prec), A.device)
     wp, wn = _aligned(ws)
-    _check("tprod_gemm", L.tprod_gemm(_ptr(A), _ptr(B), _ptr(C), l, kk, m, n, int(transA), prec, wp, wn, _stream()))
+    trans = int(bool(transA)) | (2 if transB else 0)
+    _check("tprod_gemm", L.tprod_gemm(_ptr(A), _ptr(B), _ptr(C), l, kk, m, n, trans, prec, wp, wn, _stream()))
     return C
+
+
+class TProd(torch.autograd.Function):
+    """C = A * B with the adjoint of the t-product as its backward:
+    dL/dA = G * B^T and dL/dB = A^T * G (Section 2's t-transpose), both on the
+    GPU through tprod_gemm."""
+
+    @staticmethod
+    def forward(ctx, A, B):
+        ctx.save_for_backward(A, B)
+        return tprod(A, B)
+
+    @staticmethod
+    def backward(ctx, G):
+        A, B = ctx.saved_tensors
+        G = G.contiguous()
+        dA = tprod(G, B, transB=True) if ctx.needs_input_grad[0] else None
+        dB = tprod(A, G, transA=True) if ctx.needs_input_grad[1] else None
+        return dA, dB
+
+
+def tprod_ad(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """Differentiable t-product (torch.autograd)."""
+    return TProd.apply(A, B)
 
 
 def tprod_noalloc(A: torch.Tensor, B: torch.Tensor, transA: bool = False) -> torch.Tensor:
@@ -253,13 +282,36 @@ def _info_buf(device, count=1):
     return torch.zeros(count * ctypes.sizeof(TpInfo), dtype=torch.uint8, device=device)
 
 
+class RtsvdFactor:
+    """What rtsvd_solve(..., keep=True) leaves for rtsvd_adjoint: the solve's
+    own workspace (factorisation and k) and its arguments."""
+
+    def __init__(self, ws, P, hist, l, m, n, p, prec, device, dtype):
+        self.ws, self.P, self.hist = ws, P, hist
+        self.l, self.m, self.n, self.p = l, m, n, p
+        self.prec, self.device, self.dtype = prec, device, dtype
+
+
+def rtsvd_adjoint(fac: RtsvdFactor, G: torch.Tensor) -> torch.Tensor:
+    """dL/dB = U_k S_k^{-1} V_k^T * G for the solve that made `fac` (k fixed)."""
+    _dev(G)
+    if tuple(G.shape) != (fac.n, fac.m, fac.p) or G.dtype != fac.dtype:
+        raise ValueError("G must match the solution X of the solve")
+    dB = torch.empty((fac.n, fac.l, fac.p), dtype=fac.dtype, device=fac.device)
+    wp, wn = _aligned(fac.ws)
+    _check("rtsvd_adjoint", load().rtsvd_adjoint(_ptr(G), fac.l, fac.m, fac.n, fac.p, ctypes.byref(fac.P), _ptr(dB),
+                                                 fac.prec, wp, wn, _stream()))
+    return dB
+
+
 def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None, eps=0.0, eps_rel=0.0,
-                res_hist=False, sync=True, tf32=False):
-    """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist]).
+                res_hist=False, sync=True, tf32=False, keep=False):
+    """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist][, factor]).
 
     B is (n, l, p): p > 1 lateral slices share one factorisation and one k
     (problem (I6)).  tf32=True (float32 only): the TP_TF32 precision form of
-    the block sketch and projection products."""
+    the block sketch and projection products.  keep=True also returns an
+    RtsvdFactor for rtsvd_adjoint."""
     _dev(A, B, Omega)
     n, l, m = A.shape
     p = B.shape[2]
@@ -283,10 +335,31 @@ def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None
     _check("rtsvd_truncated_solve", L.rtsvd_truncated_solve(_ptr(A), _ptr(B), _ptr(Omega), l, m, n, p,
                                                             ctypes.byref(P), _ptr(X), _ptr(info), prec, wp, wn,
                                                             _stream()))
+    fac = (RtsvdFactor(ws, P, hist, l, m, n, p, prec, A.device, A.dtype),) if keep else ()
     if not sync:
-        return X, info, hist
+        return (X, info, hist) + fac
     out = (X, _info_dict(info))
-    return out + ((hist.cpu().numpy(),) if res_hist else ())
+    return out + ((hist.cpu().numpy(),) if res_hist else ()) + fac
+
+
+class RtsvdSolve(torch.autograd.Function):
+    """X_k = RT-tSVD solution of A * X = B, differentiable in B with k held at
+    the value the discrepancy principle chose (the adjoint is rtsvd_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, B, A, Omega, kw):
+        X, _, _, fac = rtsvd_solve(A, B, Omega, sync=False, keep=True, **kw)
+        ctx.fac = fac
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        return rtsvd_adjoint(ctx.fac, G.contiguous()), None, None, None
+
+
+def rtsvd_solve_ad(A, B, Omega, delta, tau, p_over, **kw):
+    """Differentiable (in B) RT-tSVD solve: returns X only."""
+    return RtsvdSolve.apply(B, A, Omega, dict(delta=delta, tau=tau, p_over=p_over, **kw))
 
 
 def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None):

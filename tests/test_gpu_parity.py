@@ -92,6 +92,92 @@ def test_tprod_matches_oracle(tp, dtype, n, l, kk, m, trans):
     assert rel(C, ref) <= tol
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,l,kk,m,trans", [(7, 4, 6, 3, 2), (5, 9, 4, 6, 3), (16, 70, 33, 20, 2), (1, 2, 3, 4, 3)])
+def test_tprod_transposed_b_matches_oracle(tp, dtype, n, l, kk, m, trans):
+    """op(B) = B^T (trans bit 1), with or without op(A) = A^T: the adjoint products."""
+    A = rnd((n, kk, l) if trans & 1 else (n, l, kk), 5 + n)
+    B = rnd((n, m, kk) if trans & 2 else (n, kk, m), 6 + n)
+    C = tp.tprod(dev(A, dtype), dev(B, dtype), transA=bool(trans & 1), transB=bool(trans & 2)).cpu().numpy()
+    Ad = dev(A, dtype).cpu().double().numpy()
+    Bd = dev(B, dtype).cpu().double().numpy()
+    ref = O.tprod(O.ttranspose(Ad) if trans & 1 else Ad, O.ttranspose(Bd) if trans & 2 else Bd)
+    tol = 1e-12 if dtype == torch.float64 else 5e-6 * np.sqrt(kk)
+    assert rel(C, ref) <= tol
+
+
+def test_tprod_autograd_gradcheck(tp):
+    """The t-product's backward (G * B^T, A^T * G on the GPU) against float64
+    central differences of the forward (torch.autograd.gradcheck)."""
+    g = torch.Generator(device="cpu").manual_seed(3)
+    A = torch.randn(5, 3, 4, generator=g, dtype=torch.float64).cuda().requires_grad_()
+    B = torch.randn(5, 4, 2, generator=g, dtype=torch.float64).cuda().requires_grad_()
+    assert torch.autograd.gradcheck(tp.tprod_ad, (A, B), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,p", [(12, 8, 1), (16, 9, 3), (20, 16, 2)])
+def test_rtsvd_adjoint_matches_oracle(tp, dtype, N, n, p):
+    """dL/dB = U_k S_k^{-1} V_k^T * G of the GPU solve's factorisation against
+    the oracle's, at the same k."""
+    A, B, delta = problem(N, n, seed=30 + p, p=p)
+    Om = rnd((n, N, N), 13).astype(np.float32)
+    tau, eps_rel = 1.1, 0.01
+    ref = O.rtsvd_solve(A.astype(np.float64), B.astype(np.float64), Om.astype(np.float64), delta, tau,
+                        eps_rel * np.sqrt(O.fro2(A.astype(np.float64))), 3, 4, 1, r_max=N)
+    X, info, fac = tp.rtsvd_solve(dev(A, dtype), dev(B, dtype), dev(Om, dtype), delta, tau, 3, 4, 1, r_max=N,
+                                  eps_rel=eps_rel, keep=True)
+    if not exact_k_required(ref, dtype):
+        pytest.skip("truncation index inside the rounding band")
+    assert info["k"] == ref["k"]
+    G = rnd((n, N, p), 40 + p)
+    dB = tp.rtsvd_adjoint(fac, dev(G, dtype)).cpu().numpy()
+    want = O.rtsvd_adjoint(ref, dev(G, dtype).cpu().double().numpy())
+    assert dB.shape == (n, N, p)
+    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 2e-3)
+    # repeatable: the factorisation is not overwritten
+    dB2 = tp.rtsvd_adjoint(fac, dev(G, dtype)).cpu().numpy()
+    assert np.array_equal(dB, dB2)
+
+
+def test_rtsvd_adjoint_central_differences(tp):
+    """Float64 central differences of L(B) = <W, X_k(B)> through the C ABI
+    against <dL/dB, E> from the adjoint (k unchanged under the perturbation;
+    X_k is linear in B at fixed k, so the difference quotient is exact up to
+    rounding)."""
+    A, B, delta = problem(16, 9, seed=8, p=2)
+    Om = rnd((9, 16, 16), 14)
+    dt = torch.float64
+    kw = dict(r_max=16, eps_rel=0.01)
+    X, info, fac = tp.rtsvd_solve(dev(A, dt), dev(B, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, keep=True, **kw)
+    g = np.random.default_rng(9)
+    W = g.standard_normal(X.shape)
+    dB = tp.rtsvd_adjoint(fac, dev(W, dt)).cpu().numpy()
+    h = 1e-6 * np.linalg.norm(B)
+    for _ in range(8):
+        E = g.standard_normal(B.shape)
+        E /= np.linalg.norm(E)
+        Xp, ip = tp.rtsvd_solve(dev(A, dt), dev(B + h * E, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, **kw)
+        Xm, im = tp.rtsvd_solve(dev(A, dt), dev(B - h * E, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, **kw)
+        assert ip["k"] == im["k"] == info["k"]
+        fd = (np.sum(W * Xp.cpu().numpy()) - np.sum(W * Xm.cpu().numpy())) / (2 * h)
+        assert abs(fd - np.sum(dB * E)) <= 1e-7 * max(abs(fd), np.linalg.norm(dB))
+
+
+def test_rtsvd_autograd_backward_is_the_adjoint(tp):
+    """torch.autograd through RtsvdSolve gives rtsvd_adjoint's dL/dB."""
+    A, B, delta = problem(12, 8, seed=4, p=2)
+    Om = rnd((8, 12, 12), 15)
+    dt = torch.float64
+    Bt = dev(B, dt).requires_grad_()
+    X = tp.rtsvd_solve_ad(dev(A, dt), Bt, dev(Om, dt), delta, 1.1, 3, block=4, r_max=12, eps_rel=0.01)
+    W = dev(np.random.default_rng(5).standard_normal(X.shape), dt)
+    (W * X).sum().backward()
+    _, _, fac = tp.rtsvd_solve(dev(A, dt), dev(B, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, r_max=12, eps_rel=0.01,
+                               keep=True)
+    assert torch.allclose(Bt.grad, tp.rtsvd_adjoint(fac, W), rtol=0, atol=1e-12 * float(Bt.grad.abs().max()))
+
+
 @pytest.mark.parametrize("n,l,kk,m,trans", [(8, 256, 256, 16, 0), (8, 256, 256, 16, 1), (5, 128, 40, 8, 0),
                                             (4, 100, 62, 24, 1), (3, 200, 98, 32, 0), (6, 64, 2, 2, 0),
                                             (3, 1, 2, 2, 1), (4, 300, 130, 14, 1), (2, 150, 66, 6, 0),
