@@ -340,6 +340,53 @@ def tgkb_p_solve(A, B, deltas, tau, k_max):
     return dict(X=X, k=[o["k"] for o in outs], status=[o["status"] for o in outs], per_slice=outs)
 
 
+def nested_tgkb_p_solve(A, B, deltas, eta, k_max, k_init=2):
+    """nested_tGKB_p (Algorithm 6): one t-Krylov basis, grown by Algorithm 4
+    from the first lateral slice B_1, serves all p slices in turn.  For slice
+    j the projected problem min ||P_k Y - Q_{k+1}^T * B_j||_F is solved in the
+    current basis; while its residual is >= eta delta_j the basis is extended
+    by one more step (k <- k + 1: the subspaces are nested, so "go to step 2"
+    continues the same process rather than restarting it), and slice j + 1
+    starts from the k that slice j ended with.  The first test is made at
+    k = k_init.  k stops at k_max (status NOT_CONVERGED for a slice still
+    above its bound there).  The residual tested is the projected one, as
+    printed; the part of B_j outside the span of Q_{k+1} is not in it."""
+    n, l, p = B.shape
+    m = A.shape[2]
+    k_max = min(k_max, min(l, m))
+    deltas = np.broadcast_to(np.asarray(deltas, dtype=np.float64), (p,))
+    Ah, Bh = fft3(A), fft3(B)
+    g = tgkb_hat(Ah, Bh[:, :, 0], k_max)       # the process to k_max; its first k steps are the k-step process
+    k = min(k_init, k_max)
+    X = np.zeros((n, m, p), dtype=complex)
+    ks, status, res_all = [], [], []
+    for j in range(p):
+        res = {}
+        while True:
+            Qk = g["Q"][:, :, :k + 1]
+            rhs = np.einsum("sdi,sd->si", np.conj(Qk), Bh[:, :, j])     # Q_{k+1}^H b_j per slice
+            y = np.zeros((n, k), dtype=complex)
+            r2 = 0.0
+            for s in range(n):
+                P = bidiag(g["c"][s], g["z"][s], k)
+                ys, *_ = np.linalg.lstsq(P, rhs[s], rcond=None)
+                y[s] = ys
+                r2 += float(np.sum(np.abs(P @ ys - rhs[s]) ** 2))
+            res[k] = float(np.sqrt(r2 / n))
+            if res[k] < eta * deltas[j]:
+                st = STATUS_OK
+                break
+            if k >= k_max:
+                st = STATUS_NOT_CONVERGED
+                break
+            k += 1
+        X[:, :, j] = np.einsum("sdi,si->sd", g["W"][:, :, :k], y)
+        ks.append(k)
+        status.append(st)
+        res_all.append(res)
+    return dict(X=ifft3_real(X), k=ks, status=status, res=res_all, W=g["W"], Q=g["Q"])
+
+
 # --------------------------------------------------------------------------
 # tGKT: Tikhonov regularisation of the tGKB-projected problem (Section 5).
 # --------------------------------------------------------------------------

@@ -318,6 +318,42 @@ def test_tgkb_p_slices_are_independent_and_homogeneous():
     assert np.allclose(out3["X"][:, :, 1], 7.5 * out["X"][:, :, 1], rtol=0, atol=1e-11 * np.abs(out3["X"]).max())
 
 
+def test_nested_tgkb_p_first_slice_is_tgkb_and_residuals_split():
+    """Algorithm 6: slice 1 is the tGKB solution at its k (a different code
+    path: Q_{k+1}^T * B_1 = e_1 z_1 there); every slice's true residual splits
+    into the tested projected residual and the part of B_j outside the span
+    of Q_{k+1} (Pythagoras, both sides brute force through the block-circulant
+    product); k never decreases and starts at k_init = 2."""
+    A, B, delta = small_blur_multi(p=3)
+    d = [delta / np.sqrt(3.0)] * 3
+    eta = 1.1
+    out = O.nested_tgkb_p_solve(A, B, d, eta, 10)
+    k = out["k"]
+    assert k == sorted(k) and k[0] >= 2 and all(st == O.STATUS_OK for st in out["status"])
+    x1 = O.tgkb_solve(A, B[:, :, :1], d[0], eta, 10, k_fixed=k[0])["X"]
+    assert np.allclose(out["X"][:, :, :1], x1, rtol=0, atol=1e-10 * np.abs(x1).max())
+    n = A.shape[0]
+    for j in range(3):
+        kj = k[j]
+        Qh = out["Q"][:, :, :kj + 1]
+        bh = O.fft3(B[:, :, j:j + 1])[:, :, 0]
+        outside = O.ifft3_real((bh - np.einsum("sdi,si->sd", Qh, np.einsum("sdi,sd->si", np.conj(Qh), bh)))[:, :, None])
+        true2 = O.fro2(B[:, :, j:j + 1] - O.tprod_bcirc(A, out["X"][:, :, j:j + 1]))
+        assert np.isclose(true2, out["res"][j][kj] ** 2 + O.fro2(outside), rtol=1e-9)
+        assert out["res"][j][kj] < eta * d[j]
+
+
+def test_nested_tgkb_p_duplicate_and_loose_slices_do_not_grow_the_basis():
+    """A repeated slice with the same bound reuses k and gives the same
+    solution; a slice whose bound is already met keeps k unchanged."""
+    A, B, delta = small_blur_multi(p=2)
+    d0 = delta / np.sqrt(2.0)
+    Bd = np.concatenate([B[:, :, :1], B[:, :, :1], B[:, :, 1:2]], axis=2)
+    out = O.nested_tgkb_p_solve(A, Bd, [d0, d0, 1e6], 1.1, 10)
+    assert out["k"][1] == out["k"][0] == out["k"][2]
+    assert np.allclose(out["X"][:, :, 1], out["X"][:, :, 0], rtol=0, atol=1e-12 * np.abs(out["X"]).max())
+
+
 # ------------------------------------------------------------ tGKT ----
 
 def test_tgkt_full_space_is_dense_tikhonov():
