@@ -425,6 +425,16 @@ def batched_form(a, cfg, flush, tprod, torch, frames=16):
     ginfo = tprod._info_list(ginfo, frames)
     ghist = ghist.cpu().numpy()
     ks = [g["k"] for g in ginfo]
+    def nested():
+        return tprod.nested_tgkb_solve(A, B, dj, cfg.tau, cfg.k_max, res_hist=True, sync=False)
+
+    ms_n, (_, ninfo, nhist) = timed(nested)
+    ninfo = tprod._info_list(ninfo, frames)
+    nhist = nhist.cpu().numpy()
+    nk = [g["k"] for g in ninfo]
+    out["nested_tgkb_p"] = {"rhs_per_s": frames / (ms_n / 1e3), "ms_per_call": ms_n, "k_final": max(nk),
+                            "all_ok": all(g["status"] == 0 for g in ninfo),
+                            "projected_dp_met": all(nhist[j, nk[j]] < cfg.tau * dj[j] for j in range(frames))}
     out["tgkb_p"] = {"rhs_per_s": frames / (ms_gj / 1e3), "ms_per_call": ms_gj,
                      "per_frame_calls_rhs_per_s": frames / (ms_gs / 1e3), "k_min": min(ks), "k_max": max(ks),
                      "all_ok": all(g["status"] == 0 for g in ginfo),

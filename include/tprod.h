@@ -227,6 +227,29 @@ tp_status tgkb_solve(const void* A, const void* B, int l, int m, int n, int p,
                      const tp_tgkb_params* params, void* X, tp_info* d_info, int prec,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------ nested_tGKB_p ----
+ * nested_tgkb_solve: the nested_tGKB_p method (Algorithm 6) for p lateral
+ * slices.  One t-Krylov basis, grown by Algorithm 4 from B_1 (both
+ * reorthogonalisations as in tgkb_solve), serves the slices in turn: slice j
+ * solves its projected problem min ||P_k * Y - Q_{k+1}^T * B_j||_F in the
+ * present basis; while that residual is >= tau * delta_j the basis is
+ * extended by one step (the subspaces are nested: the same process goes on),
+ * and slice j+1 starts from the k that slice j ended with.  The first test is
+ * made at k = 2 (Algorithm 6's k_init).  The residual tested is the projected
+ * one, as Algorithm 6 prints it.  params as for tgkb_solve (tau is Algorithm
+ * 6's eta; delta_p optional); at k = k_max a slice above its bound is
+ * accepted with TP_ERR_NOT_CONVERGED.  One persistent launch (one CTA per
+ * Fourier slice, bounded grid-wide waits).
+ *   A : real (n, l, m)     B : real (n, l, p)     X : real (n, m, p)
+ *   d_info : p device records; res_hist (optional): (p, k_max+1), -1 where a
+ *   slice was not tested.
+ * Limits as tgkb_solve.
+ */
+size_t nested_tgkb_workspace_bytes(int l, int m, int n, int p, const tp_tgkb_params* params, int prec);
+tp_status nested_tgkb_solve(const void* A, const void* B, int l, int m, int n, int p,
+                            const tp_tgkb_params* params, void* X, tp_info* d_info, int prec,
+                            void* ws, size_t ws_bytes, void* stream);
+
 /* -------------------------------------------------------------- tGKT ------
  * tgkb_tikhonov_solve: tGKB as above fixes k; then per Fourier slice
  *   y_mu = argmin ||P_k y - z_1 e_1||^2 + mu^{-1} ||y||^2

@@ -76,6 +76,10 @@ template <typename T> size_t gk_ws_bytes(int, int, int, int, const tp_tgkb_param
 template <typename T>
 tp_status gk_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
                    cudaStream_t);
+template <typename T> size_t gkn_ws_bytes(int, int, int, int, const tp_tgkb_params*);
+template <typename T>
+tp_status gkn_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
+                    cudaStream_t);
 template <typename T> size_t tik_ws_bytes(int, int, int, int, const tp_tik_params*);
 template <typename T>
 tp_status tik_solve(const T*, const T*, int, int, int, int, const tp_tik_params*, T*, tp_info*, void*, size_t,
@@ -211,6 +215,24 @@ tp_status tgkb_solve(const void* A, const void* B, int l, int m, int n, int p, c
     if (prec == TP_FP64)
         return gk_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
                                 ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+size_t nested_tgkb_workspace_bytes(int l, int m, int n, int p, const tp_tgkb_params* params, int prec) {
+    if (prec == TP_FP32) return gkn_ws_bytes<float>(l, m, n, p, params);
+    if (prec == TP_FP64) return gkn_ws_bytes<double>(l, m, n, p, params);
+    return 0;
+}
+
+tp_status nested_tgkb_solve(const void* A, const void* B, int l, int m, int n, int p, const tp_tgkb_params* params,
+                            void* X, tp_info* d_info, int prec, void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return gkn_solve<float>((const float*)A, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws, ws_bytes,
+                                st);
+    if (prec == TP_FP64)
+        return gkn_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
+                                 ws_bytes, st);
     return TP_ERR_ARG;
 }
 

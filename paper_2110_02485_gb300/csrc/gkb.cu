@@ -556,6 +556,318 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
 }
 
 // ---------------------------------------------------------------------------
+// nested_tGKB_p (Algorithm 6): one Krylov basis, grown by Algorithm 4 from the
+// first lateral slice, serves the p slices in turn.  Slice j's projected
+// problem min ||P_k y - Q_{k+1}^H b_j|| is solved with the Givens QR of the
+// common bidiagonal P_k: the rotation of every step is kept (per Fourier
+// slice), the current slice's right-hand side coefficients are rotated as the
+// basis grows, and the next slice replays the stored rotations on its own
+// coefficients.  Tests are not lagged: after each published residual every
+// CTA waits (bounded) for all Fourier slices, then all take the same
+// decision.  Events (a residual after a step, a new slice's first residual)
+// index the counters.
+struct GknArgs {
+    const void* Ahat;
+    const void* Bhat;     // (h, l, p)
+    void* Wb;             // (h, k_max, m)
+    void* Qb;             // (h, k_max+1, l)
+    void* Xhat;           // (h, m, p)
+    double* phi;          // (h, k_max, 2): rotated right-hand side of the current slice
+    double* rot;          // (h, k_max, 3): cs, sn, rho of each step's rotation
+    double* res2;         // (k_max + p + 1, h)
+    unsigned* counters;   // k_max + p + 1, zeroed by the launcher
+    const double* td;     // p values eta * delta_j (device)
+    tp_info* info;        // p records
+    double* res_hist;     // optional (p, k_max+1)
+    long long spin;
+    int l, m, n, h, k_max, p, k_init;
+};
+
+struct GknShared {
+    double theta[GKB_KMAX + 1];
+    double cs_prev, sn_prev, orphan, res_prev, tot;
+    double2 phibar;
+    int k, j, e, timeout, have_prev;
+};
+
+// Complex dot q^H b over the CTA (working precision per thread and warp,
+// float64 across warps); every thread gets the result.  red: 64 doubles.
+template <typename T>
+__device__ double2 block_dot(const cplx<T>* q, const cplx<T>* b, int L, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    cplx<T> acc = mk<T>(0, 0);
+    for (int e = threadIdx.x; e < L; e += blockDim.x) cfmac(acc, q[e], b[e]);
+    acc.x = warp_sum(acc.x);
+    acc.y = warp_sum(acc.y);
+    __syncthreads();
+    if (lane == 0) {
+        red[warp] = (double)acc.x;
+        red[32 + warp] = (double)acc.y;
+    }
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    for (int i = 0; i < nw; ++i) {
+        r.x += red[i];
+        r.y += red[32 + i];
+    }
+    __syncthreads();
+    return r;
+}
+
+template <typename T, bool VEC, int NT>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2) k_gkb_nested(const GknArgs a) {
+    typedef cplx<T> V;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int l = a.l, m = a.m, n = a.n, h = a.h, k_max = a.k_max, p = a.p;
+    const int L = l > m ? l : m;
+    V* q = (V*)smraw;           // l
+    V* w = q + l;               // m
+    V* u = w + m;               // L
+    V* bj = u + L;              // l: the current lateral slice
+    V* cf = bj + l;             // k_max + 1
+    V* part = cf + k_max + 1;   // max(4 L, NT * VW)
+    __shared__ GknShared S;
+    __shared__ double red[64];
+    __shared__ NormBc<T> nb;
+    __shared__ V yt[GKB_KMAX];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+    const V* A = (const V*)a.Ahat + (long)s * l * m;
+    const V* Bh = (const V*)a.Bhat;
+    V* W = (V*)a.Wb + (long)s * k_max * m;
+    V* Qv = (V*)a.Qb + (long)s * (k_max + 1) * l;
+    V* Xh = (V*)a.Xhat;
+    double* phi = a.phi + (long)s * k_max * 2;
+    double* rot = a.rot + (long)s * k_max * 3;
+    const double ws = parseval_w(s, n);
+    const int k_first = a.k_init < k_max ? a.k_init : k_max;
+
+    for (int e = tid; e < l; e += NT) {
+        const V b = Bh[((long)s * l + e) * p];
+        u[e] = b;
+        bj[e] = b;
+    }
+    for (int e = tid; e < m; e += NT) w[e] = mk<T>(0, 0);
+    if (s == 0 && a.res_hist)
+        for (int e = tid; e < p * (k_max + 1); e += NT) a.res_hist[e] = -1.0;
+    __syncthreads();
+    const T z1 = normalize_vec<T>(u, l, red, &nb);
+    for (int e = tid; e < l; e += NT) {
+        q[e] = u[e];
+        Qv[e] = u[e];
+    }
+    if (tid == 0) {
+        S.cs_prev = 1.0;
+        S.sn_prev = 0.0;
+        S.orphan = 0.0;
+        S.phibar = make_double2((double)z1, 0.0);  // q_1^H b_1 = z_1
+        S.k = 0;
+        S.j = 0;
+        S.e = 0;
+        S.timeout = 0;
+        S.have_prev = 0;
+    }
+    __syncthreads();
+    T zprev = z1;
+
+    for (;;) {
+        if (S.k < k_max) {
+            // one more step of Algorithm 4: W_i, c_i, Q_{i+1}, z_{i+1}
+            const int i = S.k + 1;
+            if (VEC) {
+                mv_h_vec<T>(A, l, m, q, w, zprev, u, part);
+            } else {
+                mv_h<T>(A, l, m, q, u);
+                __syncthreads();
+                for (int e = tid; e < m; e += NT) u[e] = csub(u[e], cscale(w[e], zprev));
+                __syncthreads();
+            }
+            const T pw = reorth2<T>(u, nullptr, W, 0, i - 1, m, cf, part);
+            const T ci = normalize_into<T>(u, m, pw, red, &nb, w, W + (long)(i - 1) * m);
+            if (VEC) {
+                mv_n_vec<T>(A, l, m, w, q, ci, u);
+            } else {
+                mv_n<T>(A, l, m, w, u);
+                __syncthreads();
+                for (int e = tid; e < l; e += NT) u[e] = csub(u[e], cscale(q[e], ci));
+                __syncthreads();
+            }
+            const T pq = reorth2<T>(u, nullptr, Qv, 0, i, l, cf, part);
+            const T zi = normalize_into<T>(u, l, pq, red, &nb, q, Qv + (long)i * l);
+            const double2 cn = block_dot<T>(q, bj, l, red);  // q_{i+1}^H b_j
+            if (tid == 0) {
+                // Givens QR of column i of the bidiagonal (c_i on the diagonal,
+                // z_{i+1} below), applied to the current right-hand side
+                const double cid = ci, zid = zi;
+                const double rhobar = (i == 1) ? cid : S.cs_prev * cid;
+                S.theta[i - 1] = (i == 1) ? 0.0 : S.sn_prev * cid;  // R(i-1, i)
+                const double rho = givens_norm<T>(rhobar, zid);
+                double c = 1.0, sn = 0.0;
+                const double2 pb = S.phibar;
+                if (rho > 0.0) {
+                    const double irho = 1.0 / rho;
+                    c = rhobar * irho;
+                    sn = zid * irho;
+                    phi[2 * (i - 1)] = c * pb.x + sn * cn.x;
+                    phi[2 * (i - 1) + 1] = c * pb.y + sn * cn.y;
+                    S.phibar = make_double2(-sn * pb.x + c * cn.x, -sn * pb.y + c * cn.y);
+                } else {  // zero column: its right-hand side entry stays unmatched
+                    phi[2 * (i - 1)] = 0.0;
+                    phi[2 * (i - 1) + 1] = 0.0;
+                    S.orphan += pb.x * pb.x + pb.y * pb.y;
+                    S.phibar = cn;
+                }
+                rot[3 * (i - 1)] = c;
+                rot[3 * (i - 1) + 1] = sn;
+                rot[3 * (i - 1) + 2] = rho;
+                S.cs_prev = c;
+                S.sn_prev = sn;
+                S.k = i;
+            }
+            zprev = zi;
+            __syncthreads();
+        }
+        const int kk = S.k;
+        if (kk < k_first) continue;
+        bool finished = false;
+        // the test of the current slice at this k, then of every following
+        // slice that the present basis already satisfies
+        for (;;) {
+            if (tid == 0) {
+                const double2 pb = S.phibar;
+                a.res2[(long)S.e * h + s] = ws * (S.orphan + pb.x * pb.x + pb.y * pb.y);
+                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.counters[S.e]) : "memory");
+                const long long t0 = clock64();
+                while (ld_acquire(&a.counters[S.e]) < (unsigned)h) {
+                    if (clock64() - t0 > a.spin) {
+                        S.timeout = 1;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {  // the same fixed-order sum in every CTA
+                double tot = 0.0;
+                if (!S.timeout)
+                    for (int s2 = lane; s2 < h; s2 += 32) tot += __ldcg(&a.res2[(long)S.e * h + s2]);
+                tot = warp_sum(tot);
+                if (lane == 0) {
+                    S.tot = tot;
+                    ++S.e;
+                }
+            }
+            __syncthreads();
+            const int j = S.j;
+            const double tdj = a.td[j], tot = S.tot;
+            const bool met = !S.timeout && tot < (double)n * tdj * tdj;
+            if (s == 0 && tid == 0 && a.res_hist && !S.timeout) a.res_hist[(long)j * (k_max + 1) + kk] = sqrt(tot / n);
+            if (!met && !S.timeout && kk < k_max) {
+                if (tid == 0) {
+                    S.res_prev = tot;
+                    S.have_prev = 1;
+                }
+                __syncthreads();
+                break;  // extend the basis
+            }
+            // accept slice j at k = kk: back substitution R y = phi (complex
+            // right-hand side), then X-hat_j = W_k y
+            if (tid == 0) {
+                double2 yn = make_double2(0.0, 0.0);
+                for (int t = kk - 1; t >= 0; --t) {
+                    double vx = phi[2 * t], vy = phi[2 * t + 1];
+                    if (t + 1 < kk) {
+                        vx -= S.theta[t + 1] * yn.x;
+                        vy -= S.theta[t + 1] * yn.y;
+                    }
+                    const double rho = rot[3 * t + 2];
+                    yn = rho > 0.0 ? make_double2(vx / rho, vy / rho) : make_double2(0.0, 0.0);
+                    yt[t] = mk<T>((T)yn.x, (T)yn.y);
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < m; e += NT) {
+                V x = mk<T>(0, 0);
+                for (int t = 0; t < kk; ++t) cfma(x, W[(long)t * m + e], yt[t]);
+                Xh[((long)s * m + e) * p + j] = x;
+            }
+            if (s == 0 && tid == 0) {
+                const int status = S.timeout ? TP_ERR_TIMEOUT : (met ? TP_OK : TP_ERR_NOT_CONVERGED);
+                const double res_k = S.timeout ? -1.0 : sqrt(tot / n);
+                double margin = fabs(res_k - tdj) / tdj;
+                if (S.have_prev && !S.timeout) margin = fmin(margin, fabs(sqrt(S.res_prev / n) - tdj) / tdj);
+                tp_info o;
+                o.status = status;
+                o.k = kk;
+                o.r = kk;
+                o.sweeps = 0;
+                o.residual = res_k;
+                o.tau_delta = tdj;
+                o.eta = 0.0;
+                o.mu = 0.0;
+                o.margin = margin;
+                o.norm_a2 = 0.0;
+                a.info[j] = o;
+            }
+            __syncthreads();
+            if (j + 1 == p || S.timeout) {
+                if (S.timeout) {  // the slices not reached: zero solutions, status TIMEOUT
+                    for (int jj = j + 1; jj < p; ++jj) {
+                        for (int e = tid; e < m; e += NT) Xh[((long)s * m + e) * p + jj] = mk<T>(0, 0);
+                        if (s == 0 && tid == 0) {
+                            tp_info o = {};
+                            o.status = TP_ERR_TIMEOUT;
+                            o.k = kk;
+                            o.r = kk;
+                            o.residual = -1.0;
+                            o.tau_delta = a.td[jj];
+                            a.info[jj] = o;
+                        }
+                    }
+                }
+                finished = true;
+                break;
+            }
+            // next slice: its coefficients against Q_{k+1}, rotated by the
+            // stored rotations of steps 1..k
+            for (int e = tid; e < l; e += NT) bj[e] = Bh[((long)s * l + e) * p + j + 1];
+            __syncthreads();
+            for (int t = warp; t <= kk; t += nw) {
+                const V* qt = Qv + (long)t * l;
+                V acc = mk<T>(0, 0);
+                for (int e = lane; e < l; e += 32) cfmac(acc, __ldcg(qt + e), bj[e]);
+                acc.x = warp_sum(acc.x);
+                acc.y = warp_sum(acc.y);
+                if (lane == 0) cf[t] = acc;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double2 pb = make_double2((double)cf[0].x, (double)cf[0].y);
+                double orphan = 0.0;
+                for (int t = 0; t < kk; ++t) {
+                    const double c = rot[3 * t], sn = rot[3 * t + 1], rho = rot[3 * t + 2];
+                    const double2 cn = make_double2((double)cf[t + 1].x, (double)cf[t + 1].y);
+                    if (rho > 0.0) {
+                        phi[2 * t] = c * pb.x + sn * cn.x;
+                        phi[2 * t + 1] = c * pb.y + sn * cn.y;
+                        pb = make_double2(-sn * pb.x + c * cn.x, -sn * pb.y + c * cn.y);
+                    } else {
+                        phi[2 * t] = 0.0;
+                        phi[2 * t + 1] = 0.0;
+                        orphan += pb.x * pb.x + pb.y * pb.y;
+                        pb = cn;
+                    }
+                }
+                S.phibar = pb;
+                S.orphan = orphan;
+                S.j = j + 1;
+                S.have_prev = 0;
+            }
+            __syncthreads();
+        }
+        if (finished) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Tikhonov on the projected problem of each slice:
 //   min ||P y - z1 e1||^2 + lam^2 ||y||^2,  lam^2 = 1/mu,
 // solved by Givens QR of [P; lam I] (two rotations per column); returns the
@@ -972,6 +1284,111 @@ tp_status gk_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_
     return TP_OK;
 }
 
+// ---- nested_tGKB_p host side ----------------------------------------------
+template <typename T>
+struct GknWs {
+    unsigned* counters;
+    double *res2, *phi, *rot, *td;
+    cplx<T> *Ahat, *Bhat, *W, *Q, *Xhat;
+    size_t bytes;
+};
+
+template <typename T>
+static GknWs<T> gkn_carve(void* base, int l, int m, int n, int k_max, int p) {
+    typedef cplx<T> V;
+    const long h = n / 2 + 1, ev = (long)k_max + p + 1;
+    Carver c(base, 0);
+    GknWs<T> w;
+    w.counters = c.take<unsigned>(ev);
+    w.res2 = c.take<double>(ev * h);
+    w.phi = c.take<double>(h * k_max * 2);
+    w.rot = c.take<double>(h * k_max * 3);
+    w.td = c.take<double>(p);
+    w.Ahat = c.take<V>(h * l * m);
+    w.Bhat = c.take<V>(h * l * p);
+    w.W = c.take<V>(h * (long)k_max * m);
+    w.Q = c.take<V>(h * (long)(k_max + 1) * l);
+    w.Xhat = c.take<V>(h * m * p);
+    w.bytes = c.off;
+    return w;
+}
+
+template <typename T>
+size_t gkn_ws_bytes(int l, int m, int n, int p, const tp_tgkb_params* P) {
+    if (gk_check<T>(l, m, n, p, P) != TP_OK) return 0;
+    return gkn_carve<T>(nullptr, l, m, n, P->k_max, p).bytes;
+}
+
+struct TdChunk {
+    double v[128];
+};
+__global__ void k_fill_td(double* dst, TdChunk c, int cnt) {
+    if ((int)threadIdx.x < cnt) dst[threadIdx.x] = c.v[threadIdx.x];
+}
+
+template <typename T>
+tp_status gkn_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_tgkb_params* P, T* X,
+                    tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+    TRY(gk_check<T>(l, m, n, p, P));
+    if (!A || !B || !X || !info) return TP_ERR_ARG;
+    const int h = n / 2 + 1, k_max = P->k_max, L = l > m ? l : m;
+    GknWs<T> w = gkn_carve<T>(ws, l, m, n, k_max, p);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
+    int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TP_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TP_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return TP_ERR_CUDA;
+    const size_t vb = sizeof(cplx<T>);
+    const int nt = (h <= nsm) ? 1024 : 512;
+    const bool vec = ((size_t)m * vb) % 16 == 0 && (size_t)m * vb / 16 <= (size_t)nt;
+    const size_t part_n = std::max<size_t>(4 * (size_t)L, 16 / vb * (size_t)nt);
+    const size_t smem = ((size_t)l + m + L + l + k_max + 1 + part_n) * vb;
+    const void* kern;
+    if (nt == 1024) kern = vec ? (const void*)k_gkb_nested<T, true, 1024> : (const void*)k_gkb_nested<T, false, 1024>;
+    else kern = vec ? (const void*)k_gkb_nested<T, true, 512> : (const void*)k_gkb_nested<T, false, 512>;
+    if (smem_optin(kern, smem) != TP_OK) return TP_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess) return TP_ERR_CUDA;
+    if (!coop || (long)per_sm * nsm < h) return TP_ERR_UNSUPPORTED;
+    if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * ((size_t)k_max + p + 1), st) != cudaSuccess)
+        return TP_ERR_CUDA;
+    for (int j0 = 0; j0 < p; j0 += 128) {  // eta delta_j, passed by value
+        TdChunk c;
+        const int cnt = std::min(128, p - j0);
+        for (int j = 0; j < cnt; ++j) c.v[j] = P->tau * (P->delta_p ? P->delta_p[j0 + j] : P->delta);
+        prof_begin(TP_KC_MISC, st);
+        k_fill_td<<<1, 128, 0, st>>>(w.td + j0, c, cnt);
+        TRY(launched(TP_KC_MISC, st));
+    }
+    TRY(rdft<T>(A, w.Ahat, n, l, m, m, (long)l * m, nullptr, nullptr, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, p, p, (long)l * p, nullptr, nullptr, st));
+    GknArgs g;
+    g.Ahat = w.Ahat;
+    g.Bhat = w.Bhat;
+    g.Wb = w.W;
+    g.Qb = w.Q;
+    g.Xhat = w.Xhat;
+    g.phi = w.phi;
+    g.rot = w.rot;
+    g.res2 = w.res2;
+    g.counters = w.counters;
+    g.td = w.td;
+    g.info = info;
+    g.res_hist = P->res_hist;
+    g.spin = 4000000000LL;  // ~2 s at the GB300 SM clock
+    g.l = l;
+    g.m = m;
+    g.n = n;
+    g.h = h;
+    g.k_max = k_max;
+    g.p = p;
+    g.k_init = 2;  // Algorithm 6's k_init
+    void* args[] = {(void*)&g};
+    prof_begin(TP_KC_GKB, st);
+    if (cudaLaunchCooperativeKernel(kern, dim3(h), dim3(nt), args, smem, st) != cudaSuccess) return TP_ERR_CUDA;
+    TRY(launched(TP_KC_GKB, st));
+    return irdft<T>(w.Xhat, X, n, m, p, p, (long)m * p, nullptr, st);
+}
+
 template <typename T>
 size_t tik_ws_bytes(int l, int m, int n, int p, const tp_tik_params* P) {
     if (!P || p != 1) return 0;  // Tikhonov-tGKB: one lateral slice
@@ -1015,6 +1432,12 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
 
 template size_t gk_ws_bytes<float>(int, int, int, int, const tp_tgkb_params*);
 template size_t gk_ws_bytes<double>(int, int, int, int, const tp_tgkb_params*);
+template size_t gkn_ws_bytes<float>(int, int, int, int, const tp_tgkb_params*);
+template size_t gkn_ws_bytes<double>(int, int, int, int, const tp_tgkb_params*);
+template tp_status gkn_solve<float>(const float*, const float*, int, int, int, int, const tp_tgkb_params*, float*,
+                                    tp_info*, void*, size_t, cudaStream_t);
+template tp_status gkn_solve<double>(const double*, const double*, int, int, int, int, const tp_tgkb_params*,
+                                     double*, tp_info*, void*, size_t, cudaStream_t);
 template size_t tik_ws_bytes<float>(int, int, int, int, const tp_tik_params*);
 template size_t tik_ws_bytes<double>(int, int, int, int, const tp_tik_params*);
 template tp_status gk_solve<float>(const float*, const float*, int, int, int, int, const tp_tgkb_params*, float*,

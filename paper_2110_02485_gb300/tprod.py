@@ -46,7 +46,8 @@ class TikParams(ctypes.Structure):
 EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm", "rtsvd_workspace_bytes",
            "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
            "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
-           "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint")
+           "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
+           "nested_tgkb_solve")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -81,6 +82,9 @@ def load(path: str | None = None):
     L.tgkb_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TgkbParams), i]
     L.tgkb_workspace_bytes.restype = sz
     L.tgkb_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TgkbParams), vp, vp, i, vp, sz, vp]
+    L.nested_tgkb_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TgkbParams), i]
+    L.nested_tgkb_workspace_bytes.restype = sz
+    L.nested_tgkb_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TgkbParams), vp, vp, i, vp, sz, vp]
     L.tgkb_tikhonov_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TikParams), i]
     L.tgkb_tikhonov_workspace_bytes.restype = sz
     L.tgkb_tikhonov_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TikParams), vp, vp, i, vp, sz, vp]
@@ -396,6 +400,36 @@ def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None):
     if not sync:
         return X, info, hist
     out = (X, _info_dict(info) if p == 1 else _info_list(info, p))
+    return out + ((hist.cpu().numpy(),) if res_hist else ())
+
+
+def nested_tgkb_solve(A, B, deltas, eta, k_max, res_hist=False, sync=True):
+    """nested_tGKB_p (Algorithm 6): one Krylov basis from B[:, :, 0] serves
+    every lateral slice in turn.  Returns (X, infos[, res_hist (p, k_max+1)])."""
+    _dev(A, B)
+    n, l, m = A.shape
+    p = B.shape[2]
+    prec = _prec(A)
+    X = torch.empty((n, m, p), dtype=A.dtype, device=A.device)
+    hist = torch.empty((p, k_max + 1), dtype=torch.float64, device=A.device) if res_hist else None
+    dl = [float(d) for d in deltas]
+    if len(dl) != p:
+        raise ValueError("deltas needs one bound per lateral slice")
+    dp = (ctypes.c_double * p)(*dl)
+    P = TgkbParams(0.0, float(eta), int(k_max), hist.data_ptr() if hist is not None else None,
+                   ctypes.cast(dp, ctypes.c_void_p))
+    L = load()
+    nb = L.nested_tgkb_workspace_bytes(l, m, n, p, ctypes.byref(P), prec)
+    if nb == 0:
+        raise TprodError("nested_tgkb_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, A.device)
+    wp, wn = _aligned(ws)
+    info = _info_buf(A.device, p)
+    _check("nested_tgkb_solve", L.nested_tgkb_solve(_ptr(A), _ptr(B), l, m, n, p, ctypes.byref(P), _ptr(X),
+                                                    _ptr(info), prec, wp, wn, _stream()))
+    if not sync:
+        return X, info, hist
+    out = (X, _info_list(info, p))
     return out + ((hist.cpu().numpy(),) if res_hist else ())
 
 

@@ -365,6 +365,36 @@ def test_tgkb_p_matches_oracle(tp, dtype, N, n, p, k_max):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,p,k_max,levels", [(12, 8, 3, 12, (1e-2, 1e-2, 1e-2)), (16, 9, 5, 16, (3e-2, 1e-2, 1e-3, 1e-1, 3e-3)),
+                                                (20, 16, 4, 20, (1e-1, 1e-2, 3e-3, 1e-3)), (13, 10, 3, 13, (1e-2, 1e-3, 1e-2)),
+                                                (24, 12, 6, 5, (1e-2, 1e-3, 1e-3, 1e-4, 1e-1, 1e-2))])
+def test_nested_tgkb_p_matches_oracle(tp, dtype, N, n, p, k_max, levels):
+    """nested_tGKB_p (Algorithm 6) against the oracle: the k each slice ends
+    with, its status, its solution, and the projected residuals it tested.
+    The last case caps k (k_max = 5) so that slices end NOT_CONVERGED."""
+    A, B, deltas = problem_p(N, n, list(levels), seed=N + 3 * p + (3 if N == 20 else 0))
+    eta = 1.1
+    ref = O.nested_tgkb_p_solve(A.astype(np.float64), B.astype(np.float64), deltas, eta, k_max)
+    X, infos, hist = tp.nested_tgkb_solve(dev(A, dtype), dev(B, dtype), deltas, eta, k_max, res_hist=True)
+    X = X.cpu().numpy()
+    assert X.shape == (n, N, p) and hist.shape == (p, k_max + 1)
+    # exact k only while every decision so far sits outside the rounding band
+    for j in range(p):
+        tdj = eta * deltas[j]
+        if min(abs(r - tdj) / tdj for jj in range(j + 1) for r in ref["res"][jj].values()) <= TIE[dtype]:
+            break
+        assert infos[j]["k"] == ref["k"][j], j
+        assert infos[j]["status"] == ref["status"][j]
+        assert rel(X[:, :, j], ref["X"][:, :, j]) <= TOL_X[dtype] * 10
+        for k, rk in ref["res"][j].items():
+            assert abs(hist[j, k] - rk) <= res_tol(rk, B[:, :, j:j + 1], dtype)
+        untested = [k for k in range(k_max + 1) if k not in ref["res"][j]]
+        assert all(hist[j, k] == -1.0 for k in untested)
+    if k_max == 5:
+        assert O.STATUS_NOT_CONVERGED in ref["status"]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_tgkb_p_common_delta_and_cap(tp, dtype):
     """tGKB_p with one delta for every slice (delta_p not given) and a step cap
     that some slices reach (NOT_CONVERGED) while others stop earlier."""
