@@ -87,11 +87,24 @@ k_rdft_pow2(const T* __restrict__ X, cplx<T>* __restrict__ Xh, int n, int logn, 
     const bool live = t0 + tt < tubes;
     const T* xt = X + (live ? tube_off(t0 + tt, cols, ld) : 0);
     T acc = 0;
-#pragma unroll 8
-    for (int k = k0; k < n; k += kst) {
-        const T v = live ? xt[(long)k * ss] : (T)0;
-        acc = fma(v, v, acc);
-        zf[((size_t)bitrev(k, logn) * 16 + (tt & 15)) * 2 + (tt >> 4)] = v;
+    // LB loads in flight per thread before any is used (the tube entries are
+    // one strided row each: the kernel is bound by how many rows are in flight)
+    constexpr int LB = sizeof(T) == 4 ? 32 : 16;
+    for (int kb = k0; kb < n; kb += LB * kst) {
+        T v[LB];
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int k = kb + j * kst;
+            v[j] = (live && k < n) ? __ldcs(xt + (long)k * ss) : (T)0;
+        }
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int k = kb + j * kst;
+            if (k < n) {
+                acc = fma(v[j], v[j], acc);
+                zf[((size_t)bitrev(k, logn) * 16 + (tt & 15)) * 2 + (tt >> 4)] = v[j];
+            }
+        }
     }
     __syncthreads();
     fft16_inplace<T>(z, tw, n);
@@ -161,16 +174,29 @@ k_irdft_pow2(const cplx<T>* __restrict__ Xh, T* __restrict__ X, int n, int logn,
     const long t0 = (long)blockIdx.x * DFT_TILE;
     fill_roots<T>(tw, n / 2, n, (T)1);
     const int h = n / 2 + 1;
-    for (int e = threadIdx.x; e < h * 16; e += blockDim.x) {
-        const int s = e >> 4, p = e & 15;
-        const long ta = t0 + p, tb = t0 + p + 16;
-        cplx<T> xa = mk<T>(0, 0), xb = mk<T>(0, 0);
-        if (ta < tubes) xa = Xh[(long)s * tubes + ta];
-        if (tb < tubes) xb = Xh[(long)s * tubes + tb];
-        const bool self = (s == 0) || (2 * s == n);
-        if (self) { xa.y = 0; xb.y = 0; }
-        z[bitrev(s, logn) * 16 + p] = mk<T>(xa.x - xb.y, xa.y + xb.x);
-        if (!self) z[bitrev(n - s, logn) * 16 + p] = mk<T>(xa.x + xb.y, xb.x - xa.y);
+    // LB pairs of spectrum loads in flight per thread before any is used
+    constexpr int LB = sizeof(T) == 4 ? 8 : 4;
+    for (int e0 = threadIdx.x; e0 < h * 16; e0 += LB * blockDim.x) {
+        cplx<T> xa[LB], xb[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int s = e >> 4, p = e & 15;
+            const long ta = t0 + p, tb = t0 + p + 16;
+            xa[u] = (e < h * 16 && ta < tubes) ? Xh[(long)s * tubes + ta] : mk<T>(0, 0);
+            xb[u] = (e < h * 16 && tb < tubes) ? Xh[(long)s * tubes + tb] : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= h * 16) break;
+            const int s = e >> 4, p = e & 15;
+            cplx<T> a = xa[u], b = xb[u];
+            const bool self = (s == 0) || (2 * s == n);
+            if (self) { a.y = 0; b.y = 0; }
+            z[bitrev(s, logn) * 16 + p] = mk<T>(a.x - b.y, a.y + b.x);
+            if (!self) z[bitrev(n - s, logn) * 16 + p] = mk<T>(a.x + b.y, b.x - a.y);
+        }
     }
     __syncthreads();
     fft16_inplace<T>(z, tw, n);
