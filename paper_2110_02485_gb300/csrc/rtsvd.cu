@@ -18,7 +18,7 @@
 
 namespace tp {
 
-constexpr int JAC_THREADS = 1024;
+constexpr int JAC_THREADS = 512;
 constexpr int MAX_BLOCK = 32;
 
 // ---------------------------------------------------------------------------
@@ -52,13 +52,14 @@ template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
 
 // Cholesky factor of a 16 x 16 Hermitian Gram matrix (upper triangle of G in
-// shared memory) by one warp, the matrix in registers: lane j (and j + 16)
-// holds column j.  The step loop is not unrolled (a one-shot straight-line
-// body would be bound by instruction fetch); at step k the lanes pick their
-// row-k entry by a select tree on the bits of k, the pivot comes from lane k
-// by a shuffle (its reciprocal square root Newton-refined),
-// row k of R is formed lane-wise and each of its entries is broadcast by
-// shuffles for the trailing update.  Rows k >= b and zero pivots give zero
+// shared memory) by one warp, the matrix in registers: lanes j and j + 16
+// hold the even and the odd rows of column j.  The step loop is not unrolled
+// (a one-shot straight-line body would be bound by instruction fetch); at
+// step k the lanes pick an entry by a select tree on the bits of k / 2, the
+// lane holding row k of the column passes it on by a shuffle, the pivot comes
+// from lane k (its reciprocal square root Newton-refined), row k of R is
+// formed lane-wise and the entries each lane needs are broadcast by shuffles
+// for the trailing update.  Rows k >= b and zero pivots give zero
 // rows (a zero column stays zero).  On the first pass (may_shift) a pivot
 // below 100 u of the largest diagonal entry restarts on G + shift I and asks
 // for one more pass (shifted CholQR3).  Writes R (row-major) and 1/diag.
@@ -66,30 +67,36 @@ template <typename T>
 __device__ void chol16_reg(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shift, bool may_shift,
                            int* need_shift, int* passes) {
     typedef cplx<T> V;
-    const int lane = threadIdx.x & 31, j = lane & 15;
+    // lane = 16 h + j holds the entries i = 2 t + h (t < 8) of column j: the
+    // two half-warps split the rows by parity, so each lane selects from and
+    // updates eight entries and fetches eight entries of row k of R
+    const int lane = threadIdx.x & 31, j = lane & 15, hpar = lane >> 4;
     T dmax = G[j * 16 + j].x;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
 #pragma unroll 1
     for (int attempt = 0; attempt < 2; ++attempt) {
-        V col[16];
+        V col[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            col[i] = i <= j ? G[i * 16 + j] : mk<T>(0, 0);
-            if (attempt == 1 && i == j) col[i].x += shift;
+        for (int t = 0; t < 8; ++t) {
+            const int i = 2 * t + hpar;
+            col[t] = i <= j ? G[i * 16 + j] : mk<T>(0, 0);
+            if (attempt == 1 && i == j) col[t].x += shift;
         }
         bool bad = false;
 #pragma unroll 1
         for (int k = 0; k < 16; ++k) {
-            // col[k] by a 4-level select tree on the bits of k
-            V t8[8], t4[4], t2[2];
+            const int tk = k >> 1;
+            V t4[4], t2[2];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) t8[i] = (k & 1) ? col[2 * i + 1] : col[2 * i];
+            for (int i = 0; i < 4; ++i) t4[i] = (tk & 1) ? col[2 * i + 1] : col[2 * i];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) t4[i] = (k & 2) ? t8[2 * i + 1] : t8[2 * i];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) t2[i] = (k & 4) ? t4[2 * i + 1] : t4[2 * i];
-            const V ck = (k & 8) ? t2[1] : t2[0];
+            for (int i = 0; i < 2; ++i) t2[i] = (tk & 2) ? t4[2 * i + 1] : t4[2 * i];
+            const V mine = (tk & 4) ? t2[1] : t2[0];  // entry 2 tk + hpar of column j
+            const int src = ((k & 1) << 4) + j;        // the lane of this column that holds entry k
+            V ck;
+            ck.x = __shfl_sync(0xffffffffu, mine.x, src);
+            ck.y = __shfl_sync(0xffffffffu, mine.y, src);
             const T d2 = __shfl_sync(0xffffffffu, ck.x, k);
             if (k < b && d2 < (T)(100.0 * Eps<T>::v) * dmax) bad = true;
             T d = 0, id = 0;
@@ -103,11 +110,12 @@ __device__ void chol16_reg(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shif
             if (lane < 16) Rk[k * 16 + j] = r;
             if (lane == 0) invd[k] = id;
 #pragma unroll
-            for (int i = 1; i < 16; ++i) {
+            for (int t = 0; t < 8; ++t) {
+                const int i = 2 * t + hpar;
                 V ri;
                 ri.x = __shfl_sync(0xffffffffu, r.x, i);
                 ri.y = __shfl_sync(0xffffffffu, r.y, i);
-                if (i > k && i <= j) col[i] = csub(col[i], cmul(cconj(ri), r));
+                if (i > k && i <= j) col[t] = csub(col[t], cmul(cconj(ri), r));
             }
         }
         if (!may_shift || attempt == 1 || !bad || dmax == (T)0) break;
@@ -431,8 +439,9 @@ __global__ void k_eta_update(State* st, const double* normsq, int h, int n, int 
 
 // ---------------------------------------------------------------------------
 // One-sided Jacobi SVD of R (r x r) per slice, rotations from the right
-// (cyclic round-robin ordering, r/2 disjoint pairs per round, one half-warp
-// per pair).  Tracks d' = J^H d.  Outputs, sorted by decreasing sigma:
+// (cyclic round-robin ordering, r/2 disjoint pairs per round, a group of
+// lanes per pair: 8 in the float32 register form, 16 in the shared-memory
+// form).  Tracks d' = J^H d.  Outputs, sorted by decreasing sigma:
 // sigma (r), U_R (r x r row-major, columns normalised), d'.
 //
 // A pair (p, q) with Gram entries a = |x|^2, b = |y|^2, g = x^H y is rotated
@@ -546,21 +555,23 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
     return y * fmaf(-0.5f * x * y, y, 1.5f);
 }
 
-// Float32 sweeps with the two columns of a pair held in registers (r <= 16
-// EPL): the Gram entries and the rotation read and write shared memory once
-// per element (as 16-byte pairs of entries when r is even), the rotation
-// parameters come from Newton-refined reciprocal square roots (c^2 + s^2 = 1
-// to about an ulp), the pair indices of the round-robin ordering advance by
+// Float32 sweeps with the two columns of a pair held in registers by GL = 8
+// lanes (r <= GL EPL; fewer lanes per pair than a half-warp amortise the
+// rotation's scalar work and shuffles over more entries per lane, and the
+// CTA needs only 512 threads): the Gram entries and the rotation read and
+// write shared memory once per element (as 16-byte pairs of entries when r
+// is even), the rotation parameters come from Newton-refined reciprocal
+// square roots (c^2 + s^2 = 1 to about an ulp), the pair indices of the round-robin ordering advance by
 // one per round (no integer division), and the per-round "any rotation" flag
 // rides on the round's barrier.
-template <int EPL, bool V2>
+template <int EPL, bool V2, int GL = 8>
 __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol) {
     __shared__ int max_off2;  // bit pattern of the largest (|g|^2 / (a b)) of a sweep
-    const int tid = threadIdx.x, lane = tid & 31, hl = tid & 15, slot = tid >> 4, nslots = blockDim.x >> 4;
+    const int tid = threadIdx.x, lane = tid & 31, hl = tid & (GL - 1), slot = tid / GL, nslots = blockDim.x / GL;
     const int rr = r + (r & 1), npair = rr / 2;
     const float tol2 = tol * tol;
-    // element e of this lane: index hl + 16 e, or with pairs (V2) 2 (hl + 16 (e / 2)) + e % 2
-    auto idx = [&](int e) { return V2 ? 2 * (hl + 16 * (e >> 1)) + (e & 1) : hl + 16 * e; };
+    // element e of this lane: index hl + GL e, or with pairs (V2) 2 (hl + GL (e / 2)) + e % 2
+    auto idx = [&](int e) { return V2 ? 2 * (hl + GL * (e >> 1)) + (e & 1) : hl + GL * e; };
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (tid == 0) max_off2 = 0;
@@ -582,7 +593,7 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
                 if (V2) {
 #pragma unroll
                     for (int v = 0; v < EPL / 2; ++v) {
-                        const int i = 2 * (hl + 16 * v);
+                        const int i = 2 * (hl + GL * v);
                         float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), yv = xv;
                         if (valid && i < r) {
                             xv = *(const float4*)(cp + i);
@@ -613,7 +624,7 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
                     cfmac(g, x[e], y[e]);
                 }
 #pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
+                for (int o = GL / 2; o > 0; o >>= 1) {
                     a += __shfl_xor_sync(0xffffffffu, a, o);
                     b += __shfl_xor_sync(0xffffffffu, b, o);
                     g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
@@ -638,7 +649,7 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
                     if (V2) {
 #pragma unroll
                         for (int v = 0; v < EPL / 2; ++v) {
-                            const int i = 2 * (hl + 16 * v);
+                            const int i = 2 * (hl + GL * v);
                             if (i < r) {
                                 *(float4*)(cp + i) = make_float4(xn[2 * v].x, xn[2 * v].y, xn[2 * v + 1].x,
                                                                  xn[2 * v + 1].y);
@@ -656,7 +667,7 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
                             }
                         }
                     }
-                    for (int cc = hl; cc < np; cc += 16) {  // the rows p, q of d' (np right-hand sides)
+                    for (int cc = hl; cc < np; cc += GL) {  // the rows p, q of d' (np right-hand sides)
                         const float2 xv = dp[p * np + cc];
                         const float2 ey = cmul(cconj(ec), dp[q * np + cc]);
                         dp[p * np + cc] = make_float2(c * xv.x - sn * ey.x, c * xv.y - sn * ey.y);
@@ -690,12 +701,14 @@ template <typename T> struct JacobiSweeps {
 template <> struct JacobiSweeps<float> {
     static __device__ int run(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol) {
         const bool v2 = (r & 1) == 0;  // 16-byte pairs of entries need an even column length
-        if (r <= 64) return v2 ? jacobi_sweeps_reg<4, true>(Rs, dp, np, r, max_sweeps, tol)
+        if (r <= 32) return v2 ? jacobi_sweeps_reg<4, true>(Rs, dp, np, r, max_sweeps, tol)
                                : jacobi_sweeps_reg<4, false>(Rs, dp, np, r, max_sweeps, tol);
-        if (r <= 96) return v2 ? jacobi_sweeps_reg<6, true>(Rs, dp, np, r, max_sweeps, tol)
-                               : jacobi_sweeps_reg<6, false>(Rs, dp, np, r, max_sweeps, tol);
-        if (r <= 128) return v2 ? jacobi_sweeps_reg<8, true>(Rs, dp, np, r, max_sweeps, tol)
-                                : jacobi_sweeps_reg<8, false>(Rs, dp, np, r, max_sweeps, tol);
+        if (r <= 64) return v2 ? jacobi_sweeps_reg<8, true>(Rs, dp, np, r, max_sweeps, tol)
+                               : jacobi_sweeps_reg<8, false>(Rs, dp, np, r, max_sweeps, tol);
+        if (r <= 96) return v2 ? jacobi_sweeps_reg<12, true>(Rs, dp, np, r, max_sweeps, tol)
+                               : jacobi_sweeps_reg<12, false>(Rs, dp, np, r, max_sweeps, tol);
+        if (r <= 128) return v2 ? jacobi_sweeps_reg<16, true>(Rs, dp, np, r, max_sweeps, tol)
+                                : jacobi_sweeps_reg<16, false>(Rs, dp, np, r, max_sweeps, tol);
         return jacobi_sweeps_smem<float>(Rs, dp, np, r, max_sweeps, tol);
     }
 };
