@@ -279,11 +279,15 @@ int tp_kernel_launches(void);         /* kernels enqueued by this library so far
 /* Optional device timing per kernel class, for benchmarks (off by default).
  * tp_timing_enable(mask): bit c of mask enables class c; every later launch
  * of an enabled class is bracketed by CUDA events on its stream (a few
- * microseconds of host time per launch).  mask = 0 disables.
+ * microseconds of host time per launch).  mask = 0 disables.  Inside a
+ * stream capture the events become external event-record nodes of the graph,
+ * so each replay records them again.
  * tp_timing_read(ms, launches, nclasses): waits for the recorded events,
- * writes per class the summed device time (ms) and launch count, clears the
- * record, and returns the number of classes (TP_KC_COUNT) or a negative
- * tp_status.  Not for use while a stream is being captured. */
+ * writes per class the summed device time (ms) and launch count (for
+ * captured events: those of the latest replay), clears the record, and
+ * returns the number of classes (TP_KC_COUNT) or a negative tp_status.  Not
+ * for use while a stream is being captured; read once per capture (the
+ * events go back to the library's pool). */
 enum {
     TP_KC_DFT = 0,      /* mode-3 DFT / inverse DFT                               */
     TP_KC_GEMM = 1,     /* batched complex products over Fourier slices           */

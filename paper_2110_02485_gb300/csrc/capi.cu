@@ -34,18 +34,28 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+// Records e on st; inside a stream capture the record becomes a node of the
+// graph (an external event record), so that every replay records it again.
+static void record(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
 void prof_begin(int cls, cudaStream_t st) {
     if (!(g_mask >> cls & 1)) return;
     g_open = take_event();
     g_open_cls = g_open ? cls : -1;
-    if (g_open) cudaEventRecord(g_open, st);
+    if (g_open) record(g_open, st);
 }
 
 void prof_end(int cls, cudaStream_t st) {
     if (g_open_cls != cls || !g_open) return;
     cudaEvent_t e = take_event();
     if (e) {
-        cudaEventRecord(e, st);
+        record(e, st);
         g_recs.push_back({cls, g_open, e});
     } else {
         g_pool.push_back(g_open);

@@ -226,6 +226,33 @@ def tprod(A: torch.Tensor, B: torch.Tensor, transA: bool = False, tf32: bool = F
     return C
 
 
+class Captured:
+    """A sequence of this library's calls recorded once as a CUDA graph and
+    replayed: the same kernels on the same buffers, without the per-launch
+    host work and with shorter gaps between dependent kernels.  `fn` must
+    enqueue only (sync=False calls) on fixed tensors; `outputs` holds what it
+    returned during capture, rewritten by every replay.  Workspaces are
+    allocated during capture from the graph's private pool and stay with it."""
+
+    def __init__(self, fn, warmup: int = 2):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        n0 = kernel_launches()
+        with torch.cuda.graph(self.graph):
+            self.outputs = fn()
+        self.launches = kernel_launches() - n0  # kernels of this library in one replay
+
+    def replay(self):
+        self.graph.replay()
+        return self.outputs
+
+
 class TProd(torch.autograd.Function):
     """C = A * B with the adjoint of the t-product as its backward:
     dL/dA = G * B^T and dL/dB = A^T * G (Section 2's t-transpose), both on the
