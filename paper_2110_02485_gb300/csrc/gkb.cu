@@ -963,11 +963,19 @@ __device__ void tik_select(const R* out, int h, R thr, double log_tol, TikState*
     __shared__ unsigned char above[TIK_P];
     const int p = threadIdx.x;
     R a = 0, comp = 0;
-    for (int s = 0; s < h; ++s) {
-        const R y = __ldcg(&out[(long)s * TIK_P + p]) - comp;
-        const R t = a + y;
-        comp = (t - a) - y;
-        a = t;
+    constexpr int SB = 16;  // slice values loaded ahead of the (ordered) Kahan additions
+    for (int s0 = 0; s0 < h; s0 += SB) {
+        R v[SB];
+#pragma unroll
+        for (int u = 0; u < SB; ++u) v[u] = s0 + u < h ? __ldcg(&out[(long)(s0 + u) * TIK_P + p]) : (R)0;
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            if (s0 + u >= h) break;
+            const R y = v[u] - comp;
+            const R t = a + y;
+            comp = (t - a) - y;
+            a = t;
+        }
     }
     above[p] = a > thr ? 1 : 0;
     __syncthreads();
@@ -1009,6 +1017,53 @@ __device__ void tik_select(const R* out, int h, R thr, double log_tol, TikState*
     if (!ts->done) fill_lam<R>(ts, lamv);
 }
 
+// The data residual ||P y - z_1 e_1||^2 of the damped problem, as
+// damped_bidiag computes it, with the Givens data of the forward sweep in
+// shared memory (entry j of thread p at [j * TIK_P + p]) and the residual
+// entries formed during the back substitution (y is not stored).
+template <typename R>
+__device__ R damped_resid_smem(const R* c, const R* z, int k, R lam, R* rho, R* theta, R* phi) {
+    const int p = threadIdx.x;
+    R rhobar = k > 0 ? c[0] : (R)0, phibar = z[0];
+    for (int j = 0; j < k; ++j) {
+        const R rh = sqrt(fma(rhobar, rhobar, lam * lam));  // eliminate the damping row
+        const R c1 = rh > (R)0 ? rhobar / rh : (R)1;
+        const R ph = c1 * phibar;
+        const R zj = z[j + 1];
+        const R rj = sqrt(fma(rh, rh, zj * zj));           // eliminate z_{j+2}
+        R cs = 1, sn = 0;
+        if (rj > (R)0) {
+            const R ir = (R)1 / rj;
+            cs = rh * ir;
+            sn = zj * ir;
+        }
+        rho[j * TIK_P + p] = rj;
+        phi[j * TIK_P + p] = cs * ph;
+        phibar = -sn * ph;
+        if (j + 1 < k) {
+            theta[(j + 1) * TIK_P + p] = sn * c[j + 1];
+            rhobar = cs * c[j + 1];
+        }
+    }
+    // back substitution; residual entries r_k = z_k y_{k-1},
+    // r_j = z_j y_{j-1} + c_j y_j, r_0 = c_0 y_0 - z_0
+    R r2 = 0, ynext = 0;
+    for (int j = k - 1; j >= 0; --j) {
+        R v = phi[j * TIK_P + p];
+        if (j + 1 < k) v -= theta[(j + 1) * TIK_P + p] * ynext;
+        const R rr = rho[j * TIK_P + p];
+        const R y = rr > (R)0 ? v / rr : (R)0;
+        const R e = z[j + 1] * y + (j + 1 < k ? c[j + 1] * ynext : (R)0);
+        r2 = fma(e, e, r2);
+        ynext = y;
+    }
+    const R e0 = (k > 0 ? c[0] * ynext : (R)0) - z[0];
+    return fma(e0, e0, r2);
+}
+
+// Largest k whose Givens data fit in the round kernel's shared memory.
+template <typename R> constexpr int tik_smem_k() { return (int)(160 * 1024 / (3 * TIK_P * sizeof(R))); }
+
 // One multisection round: the data residual at the TIK_P points of the
 // bracket for every slice (out[s*TIK_P + p]); the last CTA to finish selects
 // the next bracket.
@@ -1017,12 +1072,20 @@ __global__ void __launch_bounds__(TIK_P)
 k_tik_round(const R* cc, const R* zz, int k_max, const State* st, TikState* ts, R* lamv, int h, int n, R* out,
             R* scratch, R thr, double log_tol) {
     if (ts->done) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int last;
     const int s = blockIdx.x, p = threadIdx.x, k = st->k;
     const R lam = lamv[p];
-    R* scr = scratch + (long)s * TIK_P * 4 * k_max + p;
-    const R r2 = damped_bidiag<R>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, nullptr, scr, k_max,
-                                  TIK_P);
+    R r2;
+    if (k <= tik_smem_k<R>()) {
+        R* sm = (R*)smraw;
+        r2 = damped_resid_smem<R>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, sm, sm + k * TIK_P,
+                                  sm + 2 * k * TIK_P);
+    } else {
+        R* scr = scratch + (long)s * TIK_P * 4 * k_max + p;
+        r2 = damped_bidiag<R>(cc + (long)s * k_max, zz + (long)s * (k_max + 1), k, lam, nullptr, scr, k_max,
+                              TIK_P);
+    }
     out[(long)s * TIK_P + p] = ((s == 0 || 2 * s == n) ? (R)1 : (R)2) * r2;
     __threadfence();
     __syncthreads();
@@ -1061,9 +1124,10 @@ k_tik_final(const T* cc, const T* zz, int k_max, const cplx<T>* Wb, int m, const
 
 __global__ void k_tik_info(const double* fout, int h, int n, const State* st, const TikState* ts, double tau_delta,
                            tp_info* info) {
+    double a = 0.0;  // lanes take every 32nd slice, then a fixed-order warp sum
+    for (int s = threadIdx.x; s < h; s += 32) a += fout[s];
+    a = warp_sum(a);
     if (threadIdx.x != 0) return;
-    double a = 0.0;
-    for (int s = 0; s < h; ++s) a += fout[s];
     tp_info o;
     o.status = st->status == TP_ERR_TIMEOUT ? TP_ERR_TIMEOUT : ts->status;
     o.k = st->k;
@@ -1415,9 +1479,13 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     TRY(launched(TP_KC_TIK, st));
     int rounds = 1;
     for (double width = hi - lo; width > tol && rounds < 40; width /= (TIK_P - 1)) ++rounds;
+    // shared memory for the Givens data of up to tik_smem_k steps (k is known
+    // on the device only; larger k use the global scratch)
+    const size_t tsm = (size_t)3 * TIK_P * sizeof(T) * (size_t)std::min(k_max, tik_smem_k<T>());
+    if (smem_optin((const void*)k_tik_round<T>, tsm) != TP_OK) return TP_ERR_CUDA;
     for (int it = 0; it < rounds; ++it) {
         prof_begin(TP_KC_TIK, st);
-        k_tik_round<T><<<h, TIK_P, 0, st>>>(w.cc, w.zz, k_max, w.st, w.ts, w.lam, h, n, w.tout, w.tscr, thr, tol);
+        k_tik_round<T><<<h, TIK_P, tsm, st>>>(w.cc, w.zz, k_max, w.st, w.ts, w.lam, h, n, w.tout, w.tscr, thr, tol);
         TRY(launched(TP_KC_TIK, st));
     }
     prof_begin(TP_KC_TIK, st);

@@ -865,10 +865,14 @@ __global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st,
     extern __shared__ double res[];
     const int r = st->r;
     const int k_init = max(1, r - p_over);  // only the candidates k_init..r are needed
-    for (int k = k_init + threadIdx.x; k <= r; k += blockDim.x) {
+    // one warp per candidate k: lanes take every 32nd slice (their loads all
+    // in flight), then a fixed-order warp sum
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = k_init + warp; k <= r; k += nw) {
         double a = 0.0;
-        for (int s = 0; s < h; ++s) a += parseval_w(s, n) * out[(long)s * so + k];
-        res[k] = sqrt(fmax(a, 0.0) / (double)n);
+        for (int s = lane; s < h; s += 32) a += parseval_w(s, n) * out[(long)s * so + k];
+        a = warp_sum(a);
+        if (lane == 0) res[k] = sqrt(fmax(a, 0.0) / (double)n);
     }
     __syncthreads();
     if (threadIdx.x != 0) return;

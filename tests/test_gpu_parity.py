@@ -482,3 +482,31 @@ def test_invalid_arguments_raise(tp):
         tp.tgkb_solve(A, B, 1.0, 1.1, 0)
     with pytest.raises(tp.TprodError):
         tp.rtsvd_solve(A, B, torch.zeros((4, 5, 5), device="cuda"), 1.0, 1.1, 2, block=64, r_max=5, eps_rel=0.1)
+
+
+def test_captured_graph_replay_matches_plain_calls(tp):
+    """A solve recorded as a CUDA graph (tprod.Captured) and replayed gives
+    the plain call's results bit for bit, and its kernels are this
+    library's (counted at capture)."""
+    A, B, delta = problem(16, 8, seed=2)
+    Om = rnd((8, 16, 16), 3).astype(np.float32)
+    dt = torch.float32
+    Ad, Bd, Od = dev(A, dt), dev(B, dt), dev(Om, dt)
+
+    def step():
+        X1, i1, _ = tp.rtsvd_solve(Ad, Bd, Od, delta, 1.1, 3, 4, 1, r_max=16, eps_rel=0.01, sync=False)
+        X2, i2, _ = tp.tgkb_solve(Ad, Bd, delta, 1.1, 16, sync=False)
+        X3, i3 = tp.tgkt_solve(Ad, Bd, delta, 1.1, 16, 1e-2, 1e8, sync=False)
+        return (X1, X2, X3), (i1, i2, i3)
+
+    ref, rinfo = step()
+    ref = [x.clone() for x in ref]
+    rinfo = [tp._info_dict(i) for i in rinfo]
+    g = tp.Captured(step)
+    assert g.launches > 10
+    for _ in range(2):
+        Xs, infos = g.replay()
+        torch.cuda.synchronize()
+        assert all(torch.equal(a, b) for a, b in zip(Xs, ref))
+        assert [tp._info_dict(i) for i in infos] == rinfo
+
