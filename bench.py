@@ -41,12 +41,15 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel class from the
 # ncu capture summarised in profiles/; reported only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
-    "gkb": {"bytes": 70.72e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
-            "sha256": "67c65259b651158aaff3a47343ec38df16c0817077894b51ea3ddea5f1b55de6",
+    "gkb": {"bytes": 70.34e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
+            "sha256": "d85596a36827e76cb4388b4d5f609484371bd2df422638449294cfd640685c19",
             "profile": "profiles/k_gkb_n256.md"},
     "orth": {"bytes": 7.47e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
-             "sha256": "bd999f56804f7f3bc4a26ff3062e63ffab0947a6b446dbce076efa61b67dd496",
+             "sha256": "7b0b45474f80a53269444e78f45e65268255325a83e763bbeb7a21407d79f01e",
              "profile": "profiles/k_orth_n256.md"},
+    "svd": {"bytes": 9.68e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
+            "sha256": "7b0b45474f80a53269444e78f45e65268255325a83e763bbeb7a21407d79f01e",
+            "profile": "profiles/k_jacobi_n256.md"},
 }
 
 
