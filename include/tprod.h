@@ -191,6 +191,29 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
 tp_status rtsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_rtsvd_params* params,
                         void* dB, int prec, void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------ T-tSVD ------
+ * ttsvd_solve: the T-tSVD method (Section 4.1, Eqs. (11)-(14)): the full tSVD
+ * of A and X_s = sum_{i<=s} V_i * s_i^{-1} * U_i^T * B with the smallest s
+ * whose residual ||B - A*X_s||_F <= tau*delta (Eq. (disp); else s = the last
+ * index and TP_ERR_NOT_CONVERGED).  Computed by the RT-tSVD path with the
+ * t-identity as the sketching tensor and r = min(l, m) (the sketch then spans
+ * the whole range of A, and B-tilde has A's singular values), no power
+ * iterations, the scan of Eq. (disp) from s = 1.  Singular values at or below
+ * max(l,m)*eps*sigma_max are treated as zero.  B (n, l, p), X (n, m, p); p > 1
+ * slices share one s (as rtsvd_truncated_solve).
+ * Limits: min(l, m) <= 160 (FP32) or 112 (FP64), and as rtsvd_truncated_solve.
+ */
+typedef struct {
+    double delta;       /* noise bound of Eq. (errbd)                                 */
+    double tau;         /* discrepancy factor                                         */
+    double* res_hist;   /* optional device array (min(l,m)+1): residual at each s    */
+} tp_ttsvd_params;
+
+size_t ttsvd_workspace_bytes(int l, int m, int n, int p, const tp_ttsvd_params* params, int prec);
+tp_status ttsvd_solve(const void* A, const void* B, int l, int m, int n, int p,
+                      const tp_ttsvd_params* params, void* X, tp_info* d_info, int prec,
+                      void* ws, size_t ws_bytes, void* stream);
+
 /* -------------------------------------------------------------- tGKB ------
  * tgkb_solve: the tGKB method (Algorithm 4 with both reorthogonalisation
  * steps done as two classical Gram-Schmidt passes).  After step i the

@@ -82,6 +82,10 @@ tp_status rt_solve(const T*, const T*, const T*, int, int, int, int, const tp_rt
                    size_t, cudaStream_t, int);
 template <typename T>
 tp_status rt_adjoint(const T*, int, int, int, int, const tp_rtsvd_params*, T*, void*, size_t, cudaStream_t);
+template <typename T> size_t tt_ws_bytes(int, int, int, int, const tp_ttsvd_params*);
+template <typename T>
+tp_status tt_solve(const T*, const T*, int, int, int, int, const tp_ttsvd_params*, T*, tp_info*, void*, size_t,
+                   cudaStream_t);
 template <typename T> size_t gk_ws_bytes(int, int, int, int, const tp_tgkb_params*);
 template <typename T>
 tp_status gk_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
@@ -207,6 +211,24 @@ tp_status rtsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_rtsv
     if (prec == TP_FP32 || prec == TP_TF32)
         return rt_adjoint<float>((const float*)G, l, m, n, p, params, (float*)dB, ws, ws_bytes, st);
     if (prec == TP_FP64) return rt_adjoint<double>((const double*)G, l, m, n, p, params, (double*)dB, ws, ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+size_t ttsvd_workspace_bytes(int l, int m, int n, int p, const tp_ttsvd_params* params, int prec) {
+    if (prec == TP_FP32) return tt_ws_bytes<float>(l, m, n, p, params);
+    if (prec == TP_FP64) return tt_ws_bytes<double>(l, m, n, p, params);
+    return 0;
+}
+
+tp_status ttsvd_solve(const void* A, const void* B, int l, int m, int n, int p, const tp_ttsvd_params* params,
+                      void* X, tp_info* d_info, int prec, void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return tt_solve<float>((const float*)A, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws, ws_bytes,
+                               st);
+    if (prec == TP_FP64)
+        return tt_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
+                                ws_bytes, st);
     return TP_ERR_ARG;
 }
 

@@ -414,7 +414,8 @@ __global__ void k_rt_init(State* st, const double* partsA, int nA, const double*
         st->norm_a2 = a2;
         st->norm_b2 = b2;
         st->eta = a2;
-        st->eps2 = eps > 0.0 ? eps * eps : eps_rel * eps_rel * a2;
+        // eps < 0: sketch to r_max whatever eta (the T-tSVD form); eps2 = -1 never stops it
+        st->eps2 = eps > 0.0 ? eps * eps : (eps < 0.0 ? -1.0 : eps_rel * eps_rel * a2);
         st->done = (st->eta < st->eps2) ? 1 : 0;
         st->r = 0;
         st->k = 0;
@@ -883,7 +884,7 @@ __global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st,
             status = TP_OK;
             break;
         }
-    if (st->eta >= st->eps2) status = TP_ERR_NOT_CONVERGED;
+    if (st->eps2 >= 0.0 && st->eta >= st->eps2) status = TP_ERR_NOT_CONVERGED;
     if (st->status == TP_ERR_TIMEOUT) status = TP_ERR_TIMEOUT;  // a bounded wait of a product ran out
     double margin = fabs(res[k] - tau_delta) / tau_delta;
     if (k - 1 >= k_init) margin = fmin(margin, fabs(res[k - 1] - tau_delta) / tau_delta);
@@ -981,13 +982,13 @@ static int jac_rmax(size_t elem, int p) {
 constexpr int RT_MAX_RHS = 64;  // lateral slices of B per RT-tSVD call
 
 template <typename T>
-static tp_status rt_check(int l, int m, int n, int p, const tp_rtsvd_params* P) {
+static tp_status rt_check(int l, int m, int n, int p, const tp_rtsvd_params* P, bool full = false) {
     if (!P || l < 1 || m < 1 || n < 1 || p < 1 || p > RT_MAX_RHS) return TP_ERR_ARG;
     if (l > 1024 || m > 1024 || n > (sizeof(T) == 4 ? 1024 : 512)) return TP_ERR_ARG;
     if (P->block < 1 || P->block > MAX_BLOCK || P->r_max < 1 || P->r_max > (l < m ? l : m)) return TP_ERR_ARG;
     if (P->r_max > (sizeof(T) == 4 ? 160 : 112) || P->r_max > jac_rmax(sizeof(T), p)) return TP_ERR_ARG;
     if (!(P->tau > 0.0) || !(P->delta >= 0.0) || P->p_over < 0 || P->q_power < 0) return TP_ERR_ARG;
-    if (!(P->eps > 0.0) && !(P->eps_rel > 0.0)) return TP_ERR_ARG;
+    if (!full && !(P->eps > 0.0) && !(P->eps_rel > 0.0)) return TP_ERR_ARG;
     const int Lmax = l > m ? l : m;
     if (orth_smem(Lmax, P->block, P->r_max, 2 * sizeof(T)) > 227 * 1024) return TP_ERR_ARG;
     return TP_OK;
@@ -1006,9 +1007,10 @@ size_t rt_ws_bytes(int l, int m, int n, int p, const tp_rtsvd_params* P) {
     } while (0)
 
 template <typename T>
-tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int p, const tp_rtsvd_params* P, T* X,
-                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st, int tc_passes) {
-    TRY(rt_check<T>(l, m, n, p, P));
+static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m, int n, int p,
+                               const tp_rtsvd_params* P, T* X, tp_info* info, void* ws, size_t ws_bytes,
+                               cudaStream_t st, int tc_passes, bool full) {
+    TRY(rt_check<T>(l, m, n, p, P, full));
     if (!A || !B || !Om || !X || !info) return TP_ERR_ARG;
     const int b = P->block, r_max = P->r_max, h = n / 2 + 1;
     RtWs<T> w = rt_carve<T>(ws, l, m, n, b, r_max, p);
@@ -1118,6 +1120,12 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
     return TP_OK;
 }
 
+template <typename T>
+tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int p, const tp_rtsvd_params* P, T* X,
+                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st, int tc_passes) {
+    return rt_solve_impl<T>(A, B, Om, l, m, n, p, P, X, info, ws, ws_bytes, st, tc_passes, false);
+}
+
 // Adjoint of B -> X_k for the factorisation and k that the last rt_solve
 // left in ws (same arguments).  Per Fourier slice, with K = A-hat V-tilde:
 //   dB-hat = Q Q^H K_k S_k^{-2} V_k^H G-hat
@@ -1150,6 +1158,70 @@ tp_status rt_adjoint(const T* G, int l, int m, int n, int p, const tp_rtsvd_para
     return irdft<T>(w.Bhat, dB, n, l, p, p, (long)l * p, nullptr, st);
 }
 
+// ---------------------------------------------------------------------------
+// T-tSVD method (Section 4.1, Eqs. (11)-(14)) through the RT-tSVD path: with
+// the t-identity as the sketching tensor (Omega(:,:,1) = I, the other frontal
+// slices zero, so every Fourier slice of Omega is I) and r = min(l, m), the
+// block sketch spans the whole range of every A-hat slice, B-tilde = Q^H A-hat
+// has the singular values of A-hat, and the discrepancy scan from k = 1
+// (p = r in Eq. (kinit)) is Eq. (14)'s choice of s.  No power iterations.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_tidentity(T* Om, int m, int r) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * r; e += gridDim.x * blockDim.x) {
+        const int i = e / r, j = e - i * r;
+        Om[e] = i == j ? (T)1 : (T)0;  // frontal slice 1; the other slices are zeroed by a memset
+    }
+}
+
+template <typename T>
+static tp_rtsvd_params tt_params(int l, int m, const tp_ttsvd_params* P) {
+    tp_rtsvd_params R;
+    R.delta = P->delta;
+    R.tau = P->tau;
+    R.eps = -1.0;  // sketch to r = min(l, m) whatever the error indicator
+    R.eps_rel = 0.0;
+    R.r_max = l < m ? l : m;
+    R.p_over = R.r_max;
+    R.q_power = 0;
+    R.block = 16;
+    R.res_hist = P->res_hist;
+    return R;
+}
+
+template <typename T>
+size_t tt_ws_bytes(int l, int m, int n, int p, const tp_ttsvd_params* P) {
+    if (!P) return 0;
+    const tp_rtsvd_params R = tt_params<T>(l, m, P);
+    if (rt_check<T>(l, m, n, p, &R, true) != TP_OK) return 0;
+    const size_t rb = rt_carve<T>(nullptr, l, m, n, R.block, R.r_max, p).bytes;
+    return align256(rb) + align256((size_t)n * m * R.r_max * sizeof(T));
+}
+
+template <typename T>
+tp_status tt_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_ttsvd_params* P, T* X,
+                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!P) return TP_ERR_ARG;
+    const tp_rtsvd_params R = tt_params<T>(l, m, P);
+    TRY(rt_check<T>(l, m, n, p, &R, true));
+    if (!A || !B || !X || !info) return TP_ERR_ARG;
+    const size_t rb = align256(rt_carve<T>(nullptr, l, m, n, R.block, R.r_max, p).bytes);
+    const size_t ob = (size_t)n * m * R.r_max * sizeof(T);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < rb + align256(ob)) return TP_ERR_WORKSPACE;
+    T* Om = (T*)((char*)ws + rb);
+    if (cudaMemsetAsync(Om, 0, ob, st) != cudaSuccess) return TP_ERR_CUDA;
+    prof_begin(TP_KC_MISC, st);
+    k_tidentity<T><<<(m * R.r_max + 255) / 256, 256, 0, st>>>(Om, m, R.r_max);
+    TRY(launched(TP_KC_MISC, st));
+    return rt_solve_impl<T>(A, B, Om, l, m, n, p, &R, X, info, ws, rb, st, 3, true);
+}
+
+template size_t tt_ws_bytes<float>(int, int, int, int, const tp_ttsvd_params*);
+template size_t tt_ws_bytes<double>(int, int, int, int, const tp_ttsvd_params*);
+template tp_status tt_solve<float>(const float*, const float*, int, int, int, int, const tp_ttsvd_params*, float*,
+                                   tp_info*, void*, size_t, cudaStream_t);
+template tp_status tt_solve<double>(const double*, const double*, int, int, int, int, const tp_ttsvd_params*,
+                                    double*, tp_info*, void*, size_t, cudaStream_t);
 template tp_status rt_adjoint<float>(const float*, int, int, int, int, const tp_rtsvd_params*, float*, void*, size_t,
                                      cudaStream_t);
 template tp_status rt_adjoint<double>(const double*, int, int, int, int, const tp_rtsvd_params*, double*, void*,

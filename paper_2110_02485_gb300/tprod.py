@@ -32,6 +32,10 @@ class RtsvdParams(ctypes.Structure):
                 ("block", ctypes.c_int), ("r_max", ctypes.c_int), ("res_hist", ctypes.c_void_p)]
 
 
+class TtsvdParams(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double), ("res_hist", ctypes.c_void_p)]
+
+
 class TgkbParams(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double), ("k_max", ctypes.c_int),
                 ("res_hist", ctypes.c_void_p), ("delta_p", ctypes.c_void_p)]
@@ -47,7 +51,7 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
            "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
            "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
-           "nested_tgkb_solve")
+           "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -79,6 +83,9 @@ def load(path: str | None = None):
     L.rtsvd_workspace_bytes.restype = sz
     L.rtsvd_truncated_solve.argtypes = [vp, vp, vp, i, i, i, i, ctypes.POINTER(RtsvdParams), vp, vp, i, vp, sz, vp]
     L.rtsvd_adjoint.argtypes = [vp, i, i, i, i, ctypes.POINTER(RtsvdParams), vp, i, vp, sz, vp]
+    L.ttsvd_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TtsvdParams), i]
+    L.ttsvd_workspace_bytes.restype = sz
+    L.ttsvd_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TtsvdParams), vp, vp, i, vp, sz, vp]
     L.tgkb_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TgkbParams), i]
     L.tgkb_workspace_bytes.restype = sz
     L.tgkb_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TgkbParams), vp, vp, i, vp, sz, vp]
@@ -391,6 +398,30 @@ class RtsvdSolve(torch.autograd.Function):
 def rtsvd_solve_ad(A, B, Omega, delta, tau, p_over, **kw):
     """Differentiable (in B) RT-tSVD solve: returns X only."""
     return RtsvdSolve.apply(B, A, Omega, dict(delta=delta, tau=tau, p_over=p_over, **kw))
+
+
+def ttsvd_solve(A, B, delta, tau, res_hist=False, sync=True):
+    """T-tSVD method (Section 4.1).  Returns (X, info[, res_hist])."""
+    _dev(A, B)
+    n, l, m = A.shape
+    p = B.shape[2]
+    prec = _prec(A)
+    X = torch.empty((n, m, p), dtype=A.dtype, device=A.device)
+    hist = torch.empty(min(l, m) + 1, dtype=torch.float64, device=A.device) if res_hist else None
+    P = TtsvdParams(float(delta), float(tau), hist.data_ptr() if hist is not None else None)
+    L = load()
+    nb = L.ttsvd_workspace_bytes(l, m, n, p, ctypes.byref(P), prec)
+    if nb == 0:
+        raise TprodError("ttsvd_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, A.device)
+    wp, wn = _aligned(ws)
+    info = _info_buf(A.device)
+    _check("ttsvd_solve", L.ttsvd_solve(_ptr(A), _ptr(B), l, m, n, p, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp,
+                                        wn, _stream()))
+    if not sync:
+        return X, info, hist
+    out = (X, _info_dict(info))
+    return out + ((hist.cpu().numpy(),) if res_hist else ())
 
 
 def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None):

@@ -301,6 +301,32 @@ def test_rtsvd_several_lateral_slices_match_oracle(tp, dtype, N, n, block, p, r_
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,l,p", [(12, 8, None, 1), (16, 9, None, 1), (20, 16, 28, 1), (24, 6, None, 3),
+                                     (40, 8, None, 1)])
+def test_ttsvd_matches_oracle(tp, dtype, N, n, l, p):
+    """T-tSVD (Section 4.1) through the RT-tSVD path with the t-identity sketch
+    against the oracle's full tSVD: the truncation index, the solution and the
+    residual at every s."""
+    A, B, delta = problem(N, n, seed=11 + N, l=l, p=p)
+    tau = 1.1
+    ref = O.ttsvd_solve(A.astype(np.float64), B.astype(np.float64), delta, tau)
+    X, info, hist = tp.ttsvd_solve(dev(A, dtype), dev(B, dtype), delta, tau, res_hist=True)
+    X = X.cpu().numpy()
+    assert X.shape == (n, N, p)
+    assert info["r"] == min(A.shape[1], A.shape[2])
+    # the oracle forms the residual as sqrt(||B||^2 - ||U_s^T B||^2), which
+    # cancels to about sqrt(u) ||B|| near full rank: compare above that floor
+    floor = 1e-6 * np.linalg.norm(B)
+    for k, rk in ref["res"].items():
+        if k >= 1 and rk > floor:
+            assert abs(hist[k] - rk) <= res_tol(rk, B, dtype), k
+    if exact_k_required(ref, dtype):
+        assert info["k"] == ref["k"]
+        assert info["status"] == ref["status"]
+        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("N,n,k_max,l", [(12, 8, 12, None), (16, 17, 16, None), (20, 16, 10, 28), (32, 32, 32, None)])
 def test_tgkb_matches_oracle(tp, dtype, N, n, k_max, l):
     A, B, delta = problem(N, n, l=l)
