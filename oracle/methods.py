@@ -328,6 +328,27 @@ def tgkb_solve(A, B, delta, tau, k_max, k_fixed=None):
                 c=g["c"][:, :k], z=g["z"][:, :k + 1])
 
 
+def ritz_triplets(A, B, k):
+    """The analogues of Ritz triplets from k steps of Algorithm 4 (Section 4.3,
+    Eq. (16)-(solgkbb)): per Fourier slice the SVD P_k = U_P S V_P^T of the
+    (k+1) x k lower bidiagonal, and the triplets (s_i, Q_{k+1} U_P e_i,
+    W_k V_P e_i), largest first.  Returns the Fourier factors Uh (n, l, k),
+    S (n, k), Vh (n, m, k) and the spatial tensors U (n, l, k), s (n, k)
+    tubes, V (n, m, k)."""
+    Ah, Bh = fft3(A), fft3(B)
+    g = tgkb_hat(Ah, Bh[:, :, 0], k)
+    n = A.shape[0]
+    Uh = np.zeros((n, A.shape[1], k), dtype=complex)
+    Vh = np.zeros((n, A.shape[2], k), dtype=complex)
+    S = np.zeros((n, k))
+    for s in range(n):
+        Us, ss, Vts = np.linalg.svd(bidiag(g["c"][s], g["z"][s], k), full_matrices=False)
+        S[s] = ss
+        Uh[s] = g["Q"][s][:, :k + 1] @ Us
+        Vh[s] = g["W"][s][:, :k] @ Vts.T
+    return dict(Uh=Uh, S=S, Vh=Vh, U=ifft3_real(Uh), s=ifft3_real(S[:, None, :])[:, 0, :], V=ifft3_real(Vh), gkb=g)
+
+
 def tgkb_p_solve(A, B, deltas, tau, k_max):
     """tGKB_p (Section 1 and Section 4.3): problem (I6) with p lateral slices
     B_j, each with its own noise bound ||E_j||_F <= delta_j, solved by

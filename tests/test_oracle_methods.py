@@ -260,6 +260,29 @@ def test_tgkb_discrepancy_bracket_with_brute_force_residual():
         assert r(O.tgkb_solve(A, B, delta, tau, 20, k_fixed=k - 1)["X"]) > tau * delta
 
 
+def test_ritz_triplets_relations_and_full_rank_limit():
+    """Section 4.3's triplets from k tGKB steps: A-hat V_i = U_i s_i exactly in
+    every Fourier slice (from A W_k = Q_{k+1} P_k), orthonormal U and V; the
+    tGKB solution rebuilt from them (Eq. (solgkbb)) is the tGKB solution; and
+    with k = min(l, m) the singular values are those of the full tSVD."""
+    A, B, delta = small_blur(N=10, n=6, general=0.05)
+    n, l, m = A.shape
+    k = 5
+    t = O.ritz_triplets(A, B, k)
+    Ah = O.fft3(A)
+    for s in range(n):
+        assert np.allclose(Ah[s] @ t["Vh"][s], t["Uh"][s] * t["S"][s][None, :], atol=1e-10)
+        assert np.allclose(t["Uh"][s].conj().T @ t["Uh"][s], np.eye(k), atol=1e-10)
+        assert np.allclose(t["Vh"][s].conj().T @ t["Vh"][s], np.eye(k), atol=1e-10)
+    Bh = O.fft3(B)
+    Xh = np.stack([t["Vh"][s] @ ((t["Uh"][s].conj().T @ Bh[s]) / t["S"][s][:, None]) for s in range(n)])
+    ref = O.tgkb_solve(A, B, delta, 1.1, k, k_fixed=k)["X"]
+    assert np.allclose(O.ifft3_real(Xh), ref, atol=1e-10 * np.abs(ref).max())
+    full = O.ritz_triplets(A, B, min(l, m))
+    _, S_exact, _ = O.tsvd_hat(Ah)
+    assert np.allclose(full["S"], S_exact[:, :min(l, m)], rtol=1e-8, atol=1e-12)
+
+
 def slice_noise(A, Xt, levels, seed):
     """B = A*Xt + E with slice j's noise of relative level levels[j];
     returns B and delta_j = ||E_j||_F."""
