@@ -273,6 +273,22 @@ tp_status nested_tgkb_solve(const void* A, const void* B, int l, int m, int n, i
                             const tp_tgkb_params* params, void* X, tp_info* d_info, int prec,
                             void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------- tGKB t-singular triplets --
+ * tgkb_triplets: the analogues of Ritz triplets of Section 4.3: k steps of
+ * Algorithm 4 from B (no discrepancy stop), then per Fourier slice the SVD
+ * P_k = U_P S V_P^T of the (k+1) x k lower bidiagonal, and the triplets
+ * (s_i, Q_{k+1} * U_i, W_k * V_i), i = 1..k, largest first in every slice:
+ * approximations of the k largest t-singular triplets of A, from which
+ * Eq. (solgkbb) rebuilds the tGKB solution.
+ *   A : real (n, l, m)   B : real (n, l, 1)
+ *   U : real (n, l, k)   S : real (n, k), tube i in column i   V : real (n, m, k)
+ * Limits as tgkb_solve, and (k+1)^2 complex entries twice in 227 KB of
+ * shared memory (k <= 118 in FP32, 83 in FP64).
+ */
+size_t tgkb_triplets_workspace_bytes(int l, int m, int n, int k, int prec);
+tp_status tgkb_triplets(const void* A, const void* B, int l, int m, int n, int k, void* U, void* S, void* V,
+                        int prec, void* ws, size_t ws_bytes, void* stream);
+
 /* -------------------------------------------------------------- tGKT ------
  * tgkb_tikhonov_solve: tGKB as above fixes k; then per Fourier slice
  *   y_mu = argmin ||P_k y - z_1 e_1||^2 + mu^{-1} ||y||^2

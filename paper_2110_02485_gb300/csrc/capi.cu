@@ -94,6 +94,9 @@ template <typename T> size_t gkn_ws_bytes(int, int, int, int, const tp_tgkb_para
 template <typename T>
 tp_status gkn_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
                     cudaStream_t);
+template <typename T> size_t tri_ws_bytes(int, int, int, int);
+template <typename T>
+tp_status tri_solve(const T*, const T*, int, int, int, int, T*, T*, T*, void*, size_t, cudaStream_t);
 template <typename T> size_t tik_ws_bytes(int, int, int, int, const tp_tik_params*);
 template <typename T>
 tp_status tik_solve(const T*, const T*, int, int, int, int, const tp_tik_params*, T*, tp_info*, void*, size_t,
@@ -265,6 +268,24 @@ tp_status nested_tgkb_solve(const void* A, const void* B, int l, int m, int n, i
     if (prec == TP_FP64)
         return gkn_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
                                  ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+size_t tgkb_triplets_workspace_bytes(int l, int m, int n, int k, int prec) {
+    if (prec == TP_FP32) return tri_ws_bytes<float>(l, m, n, k);
+    if (prec == TP_FP64) return tri_ws_bytes<double>(l, m, n, k);
+    return 0;
+}
+
+tp_status tgkb_triplets(const void* A, const void* B, int l, int m, int n, int k, void* U, void* S, void* V, int prec,
+                        void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return tri_solve<float>((const float*)A, (const float*)B, l, m, n, k, (float*)U, (float*)S, (float*)V, ws,
+                                ws_bytes, st);
+    if (prec == TP_FP64)
+        return tri_solve<double>((const double*)A, (const double*)B, l, m, n, k, (double*)U, (double*)S, (double*)V,
+                                 ws, ws_bytes, st);
     return TP_ERR_ARG;
 }
 

@@ -1453,6 +1453,121 @@ tp_status gkn_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     return irdft<T>(w.Xhat, X, n, m, p, p, (long)m * p, nullptr, st);
 }
 
+// ---- t-singular triplets from tGKB (Section 4.3, Eq. (solgkbb)) --------------
+// k steps of Algorithm 4 from B; per Fourier slice the SVD of the (k+1) x k
+// lower bidiagonal P_k (one-sided Jacobi on [P_k | 0], the rotations carried
+// along an identity so that J comes out as well), then U = Q_{k+1} U_P and
+// V = W_k V_P, and the inverse DFTs of U, the singular tubes and V.
+template <typename T>
+__global__ void k_bidiag(const T* cc, const T* zz, int k_max, const State* gst, cplx<T>* R, cplx<T>* D, int r,
+                         State* st2) {
+    const int s = blockIdx.x, ka = gst->k;  // the steps actually made (fewer after an exact breakdown)
+    cplx<T>* Rs = R + (long)s * r * r;
+    cplx<T>* Ds = D + (long)s * r * r;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int i = e / r, j = e - i * r;
+        T v = 0;
+        if (j < ka) {
+            if (i == j) v = cc[(long)s * k_max + j];
+            else if (i == j + 1) v = zz[(long)s * (k_max + 1) + j + 1];
+        }
+        Rs[e] = mk<T>(v, 0);
+        Ds[e] = mk<T>(i == j ? (T)1 : (T)0, 0);
+    }
+    if (s == 0 && threadIdx.x == 0) {
+        st2->r = r;
+        st2->sweeps = 0;
+    }
+}
+
+template <typename T>
+__global__ void k_sigma_tubes(const T* sigma, int r, int k, cplx<T>* Sh) {
+    const int s = blockIdx.x;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) Sh[(long)s * k + i] = mk<T>(sigma[(long)s * r + i], 0);
+}
+
+template <typename T>
+struct TriWs {
+    GkWs<T> g;
+    State* st2;
+    tp_info* info;
+    T* sigma;
+    cplx<T> *R, *D, *UR, *dprime, *Uh, *Vh, *Sh;
+    size_t bytes;
+};
+
+template <typename T>
+static TriWs<T> tri_carve(void* base, int l, int m, int n, int k) {
+    typedef cplx<T> V;
+    TriWs<T> w;
+    w.g = gk_carve<T>(base, l, m, n, k, 1);
+    const long h = n / 2 + 1, r = k + 1;
+    Carver c(base ? (char*)base + w.g.bytes : nullptr, 0);
+    w.st2 = c.take<State>(1);
+    w.info = c.take<tp_info>(1);
+    w.sigma = c.take<T>(h * r);
+    w.R = c.take<V>(h * r * r);
+    w.D = c.take<V>(h * r * r);
+    w.UR = c.take<V>(h * r * r);
+    w.dprime = c.take<V>(h * r * r);
+    w.Uh = c.take<V>(h * l * k);
+    w.Vh = c.take<V>(h * m * k);
+    w.Sh = c.take<V>(h * k);
+    w.bytes = w.g.bytes + c.off;
+    return w;
+}
+
+template <typename T>
+static tp_status tri_check(int l, int m, int n, int k) {
+    tp_tgkb_params P = {0.0, 1.0, k, nullptr, nullptr};
+    if (gk_check<T>(l, m, n, 1, &P) != TP_OK) return TP_ERR_ARG;
+    // the Jacobi working set (r^2 + r^2 complex entries, r = k + 1) in shared memory
+    if ((size_t)2 * (k + 1) * (k + 1) * sizeof(cplx<T>) + (size_t)(k + 1) * 12 > 227 * 1024) return TP_ERR_ARG;
+    return TP_OK;
+}
+
+template <typename T>
+size_t tri_ws_bytes(int l, int m, int n, int k) {
+    if (tri_check<T>(l, m, n, k) != TP_OK) return 0;
+    return tri_carve<T>(nullptr, l, m, n, k).bytes;
+}
+
+template <typename T>
+tp_status tri_solve(const T* A, const T* B, int l, int m, int n, int k, T* U, T* S, T* V, void* ws, size_t ws_bytes,
+                    cudaStream_t st) {
+    TRY(tri_check<T>(l, m, n, k));
+    if (!A || !B || !U || !S || !V) return TP_ERR_ARG;
+    TriWs<T> w = tri_carve<T>(ws, l, m, n, k);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
+    const int h = n / 2 + 1, r = k + 1;
+    // k steps of Algorithm 4 (delta = 0: no discrepancy stop before k)
+    tp_tgkb_params P = {0.0, 1.0, k, nullptr, nullptr};
+    TRY(gk_run<T>(A, B, l, m, n, &P, w.g, w.info, 0, st));
+    prof_begin(TP_KC_MISC, st);
+    k_bidiag<T><<<h, 256, 0, st>>>(w.g.cc, w.g.zz, k, w.g.st, w.R, w.D, r, w.st2);
+    TRY(launched(TP_KC_MISC, st));
+    TRY(jacobi_svd<T>(h, w.R, r, (long)r * r, w.st2, w.D, (long)r * r, r, w.sigma, r, w.UR, r, (long)r * r, w.dprime,
+                      (long)r * r, r, &w.st2->sweeps, st));
+    // U = Q_{k+1} U_P(:, 1:k);  V = W_k V_P(1:k, 1:k) with V_P = d'^H
+    TRY(cgemm<T>(h, l, k, r, nullptr, nullptr, nullptr, 1, 0, w.g.Q, l, (long)(k + 1) * l, OP_T, w.UR, r,
+                 (long)r * r, OP_N, 0, 0, w.Uh, k, (long)l * k, nullptr, st));
+    TRY(cgemm<T>(h, m, k, k, nullptr, nullptr, nullptr, 1, 0, w.g.W, m, (long)k * m, OP_T, w.dprime, r,
+                 (long)r * r, OP_C, 0, 0, w.Vh, k, (long)m * k, nullptr, st));
+    prof_begin(TP_KC_MISC, st);
+    k_sigma_tubes<T><<<h, 64, 0, st>>>(w.sigma, r, k, w.Sh);
+    TRY(launched(TP_KC_MISC, st));
+    TRY(irdft<T>(w.Uh, U, n, l, k, k, (long)l * k, nullptr, st));
+    TRY(irdft<T>(w.Vh, V, n, m, k, k, (long)m * k, nullptr, st));
+    return irdft<T>(w.Sh, S, n, 1, k, k, k, nullptr, st);
+}
+
+template size_t tri_ws_bytes<float>(int, int, int, int);
+template size_t tri_ws_bytes<double>(int, int, int, int);
+template tp_status tri_solve<float>(const float*, const float*, int, int, int, int, float*, float*, float*, void*,
+                                    size_t, cudaStream_t);
+template tp_status tri_solve<double>(const double*, const double*, int, int, int, int, double*, double*, double*,
+                                     void*, size_t, cudaStream_t);
+
 template <typename T>
 size_t tik_ws_bytes(int l, int m, int n, int p, const tp_tik_params* P) {
     if (!P || p != 1) return 0;  // Tikhonov-tGKB: one lateral slice

@@ -114,6 +114,16 @@ struct State {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// One-sided Jacobi SVD of h square factors R (r x r complex, row-major, r =
+// st->r <= r_max) per CTA, the np columns of d (r x np row-major) rotated
+// along: sigma sorted decreasing, U_R (columns normalised) and d' = J^H d with
+// rows in sorted order.  TP_ERR_UNSUPPORTED when the working set exceeds
+// shared memory.
+template <typename T>
+tp_status jacobi_svd(int h, const void* R, long ldr, long sR, const State* st, const void* d, long sd, int np,
+                     T* sigma, long ssig, void* UR, long ldu, long sU, void* dprime, long sdp, int r_max,
+                     int* sweeps, cudaStream_t stream);
+
 struct Carver {
     char* base;
     size_t off;

@@ -774,6 +774,25 @@ static size_t jacobi_smem(int r, size_t c, int np) {
     return (size_t)r * r * c + (size_t)r * np * c + (size_t)r * sizeof(double) + (size_t)r * sizeof(int);
 }
 
+// The one-sided Jacobi SVD of h square r x r factors (r from st->r, at most
+// r_max), with np right-hand sides rotated along; see k_jacobi.
+template <typename T>
+tp_status jacobi_svd(int h, const void* R, long ldr, long sR, const State* st, const void* d, long sd, int np,
+                     T* sigma, long ssig, void* UR, long ldu, long sU, void* dprime, long sdp, int r_max,
+                     int* sweeps, cudaStream_t stream) {
+    const size_t smem = jacobi_smem(r_max, sizeof(cplx<T>), np);
+    if (smem > 227 * 1024) return TP_ERR_UNSUPPORTED;
+    if (smem_optin((const void*)k_jacobi<T>, smem) != TP_OK) return TP_ERR_CUDA;
+    prof_begin(TP_KC_SVD, stream);
+    k_jacobi<T><<<h, JAC_THREADS, smem, stream>>>((const cplx<T>*)R, ldr, sR, st, (const cplx<T>*)d, sd, np, sigma,
+                                                  ssig, (cplx<T>*)UR, ldu, sU, (cplx<T>*)dprime, sdp, 60, sweeps);
+    return launched(TP_KC_SVD, stream);
+}
+template tp_status jacobi_svd<float>(int, const void*, long, long, const State*, const void*, long, int, float*, long,
+                                     void*, long, long, void*, long, int, int*, cudaStream_t);
+template tp_status jacobi_svd<double>(int, const void*, long, long, const State*, const void*, long, int, double*,
+                                      long, void*, long, long, void*, long, int, int*, cudaStream_t);
+
 // alpha_j = d'_j / sigma_j^pw (pw = 1: the solution coefficients; pw = 2:
 // the adjoint's), dropping sigma_j <= dims * eps * sigma_max.
 template <typename T>

@@ -51,7 +51,8 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
            "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
            "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
-           "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve")
+           "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve", "tgkb_triplets_workspace_bytes",
+           "tgkb_triplets")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -92,6 +93,9 @@ def load(path: str | None = None):
     L.nested_tgkb_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TgkbParams), i]
     L.nested_tgkb_workspace_bytes.restype = sz
     L.nested_tgkb_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TgkbParams), vp, vp, i, vp, sz, vp]
+    L.tgkb_triplets_workspace_bytes.argtypes = [i, i, i, i, i]
+    L.tgkb_triplets_workspace_bytes.restype = sz
+    L.tgkb_triplets.argtypes = [vp, vp, i, i, i, i, vp, vp, vp, i, vp, sz, vp]
     L.tgkb_tikhonov_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TikParams), i]
     L.tgkb_tikhonov_workspace_bytes.restype = sz
     L.tgkb_tikhonov_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TikParams), vp, vp, i, vp, sz, vp]
@@ -489,6 +493,26 @@ def nested_tgkb_solve(A, B, deltas, eta, k_max, res_hist=False, sync=True):
         return X, info, hist
     out = (X, _info_list(info, p))
     return out + ((hist.cpu().numpy(),) if res_hist else ())
+
+
+def tgkb_triplets(A, B, k):
+    """t-singular triplets from k tGKB steps (Section 4.3): returns U (n, l, k),
+    S (n, k) (tube i in column i), V (n, m, k)."""
+    _dev(A, B)
+    n, l, m = A.shape
+    prec = _prec(A)
+    U = torch.empty((n, l, k), dtype=A.dtype, device=A.device)
+    S = torch.empty((n, k), dtype=A.dtype, device=A.device)
+    V = torch.empty((n, m, k), dtype=A.dtype, device=A.device)
+    L = load()
+    nb = L.tgkb_triplets_workspace_bytes(l, m, n, int(k), prec)
+    if nb == 0:
+        raise TprodError("tgkb_triplets_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, A.device)
+    wp, wn = _aligned(ws)
+    _check("tgkb_triplets", L.tgkb_triplets(_ptr(A), _ptr(B), l, m, n, int(k), _ptr(U), _ptr(S), _ptr(V), prec, wp,
+                                            wn, _stream()))
+    return U, S, V
 
 
 def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True):
