@@ -262,42 +262,66 @@ def run_ours(a, rank, world, local):
         ms = float(t.item())
     value = world * SOLVES_PER_STEP * a.steps / (ms / 1e3)
 
-    # end to end through the public API: pinned host inputs in, solutions out
+    # end to end through the public API: pinned host inputs in, solutions out.
+    # Two sets of device inputs: the copy of step i+1's inputs (a second
+    # stream) overlaps step i's solves; the whole loop is timed, with every
+    # step's H2D copy, L2 flush, solves and D2H of the three solutions in it.
     e2e = None
     if not a.no_e2e:
         Ah, Bh, Oh = (torch.from_numpy(P[k]).pin_memory() for k in ("A", "B", "Omega"))
-        Ad, Bd, Od = torch.empty_like(A), torch.empty_like(B), torch.empty_like(Om)
+        sets = [tuple(torch.empty_like(x) for x in (A, B, Om)) for _ in range(2)]
         outs = [torch.empty((cfg.N, cfg.N, 1), dtype=torch.float32).pin_memory() for _ in range(3)]
         h2d = sum(x.numel() * x.element_size() for x in (Ah, Bh, Oh))
         d2h = sum(x.numel() * x.element_size() for x in outs)
-        Ad.copy_(Ah)
-        Bd.copy_(Bh)
-        Od.copy_(Oh)
-        g2 = None if a.no_graph else tprod.Captured(lambda: step(Ad, Bd, Od), warmup=0)
+        for dst in sets:
+            for d_, h_ in zip(dst, (Ah, Bh, Oh)):
+                d_.copy_(h_)
+        if a.no_graph:
+            runs = [lambda d=d: step(*d) for d in sets]
+        else:
+            caps = [tprod.Captured(lambda d=d: step(*d), warmup=0) for d in sets]
+            runs = [c.replay for c in caps]
+        comp = torch.cuda.current_stream()
+        copy_stream = torch.cuda.Stream()
+        copied = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
+
+        def h2d_copy(j):
+            with torch.cuda.stream(copy_stream):
+                for d_, h_ in zip(sets[j], (Ah, Bh, Oh)):
+                    d_.copy_(h_, non_blocking=True)
+                copied[j].record(copy_stream)
+
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        evs2 = []
-        for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(comp)
+        copy_stream.wait_event(e0)
+        h2d_copy(0)
+        for i in range(a.steps):
+            j = i % 2
+            if i + 1 < a.steps:
+                if i >= 1:
+                    copy_stream.wait_event(done[1 - j])  # step i-1 has finished with that set
+                h2d_copy(1 - j)
             flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            Ad.copy_(Ah, non_blocking=True)
-            Bd.copy_(Bh, non_blocking=True)
-            Od.copy_(Oh, non_blocking=True)
-            Xs, _ = g2.replay() if g2 else step(Ad, Bd, Od)
+            comp.wait_event(copied[j])
+            Xs, _ = runs[j]()
             for o, x in zip(outs, Xs):
                 o.copy_(x, non_blocking=True)
-            e1.record()
-            evs2.append((e0, e1))
+            done[j].record(comp)
+        e1.record(comp)
         torch.cuda.synchronize()
-        ms2 = sum(e0.elapsed_time(e1) for e0, e1 in evs2)
+        ms2 = e0.elapsed_time(e1)
         if world > 1:
             t = torch.tensor([ms2], dtype=torch.float64, device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms2 = float(t.item())
         e2e = {"value": world * SOLVES_PER_STEP * a.steps / (ms2 / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "pipeline": "two input sets; the H2D copy of step i+1 overlaps step i; one event pair around the "
+                           "K steps (flushes included)"}
 
     # precision form: RT-tSVD alone, float32 vs TF32 sketch, device time and
     # error against the oracle's stored solution samples for this workload
