@@ -13,6 +13,8 @@
 // A thread always handles the same tube (DFT_THREADS is a multiple of
 // DFT_TILE), so its tube offset is computed once; squares are summed per
 // thread in the working precision and combined in float64 across the CTA.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -122,6 +124,125 @@ k_rdft_pow2(const T* __restrict__ X, cplx<T>* __restrict__ Xh, int n, int logn, 
         Xh[(long)s * tubes + t] = o;
     }
     store_partial<T>(acc, sumsq);
+}
+
+// ---- n = 256 as 16 x 16 ------------------------------------------------------
+// The packed sequences of a CTA (16 of them, two real tubes each) are
+// transformed by the 16 x 16 split of the DFT (x_n, n = 16 n1 + n2): sixteen
+// 16-point DFTs over n1 in registers, the twiddles exp(-2 pi i n2 k1 / 256),
+// sixteen 16-point DFTs over n2; thread (seq, j) does the j-th of each for
+// its sequence.  Three barriers instead of the eight of the radix-2 stages.
+template <typename T>
+__device__ __forceinline__ void dft4f(cplx<T>& x0, cplx<T>& x1, cplx<T>& x2, cplx<T>& x3) {
+    // forward 4-point DFT in place: X_k = sum_n x_n exp(-2 pi i n k / 4)
+    const cplx<T> t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = csub(x1, x3);
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = mk<T>(t1.x + t3.y, t1.y - t3.x);  // t1 - i t3
+    x3 = mk<T>(t1.x - t3.y, t1.y + t3.x);  // t1 + i t3
+}
+
+// forward 16-point DFT of v in place, natural order in and out (4 x 4 split)
+template <typename T>
+__device__ __forceinline__ void dft16f(cplx<T> (&v)[16]) {
+    const T c8 = (T)0.92387953251128675613, s8 = (T)0.38268343236508977173, h2 = (T)0.70710678118654752440;
+    // step 1: for each n2, the 4-point DFT over n1 of v[4 n1 + n2] -> a[k1][n2] kept at v[4 k1 + n2]
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4f<T>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // step 2: twiddles exp(-2 pi i n2 k1 / 16), n2 k1 in {1, 2, 3, 2, 4, 6, 3, 6, 9}
+    auto tw = [](cplx<T> a, T c, T s) { return mk<T>(a.x * c - a.y * s, a.x * s + a.y * c); };  // a (c + i s)
+    v[4 * 1 + 1] = tw(v[5], c8, -s8);
+    v[4 * 1 + 2] = tw(v[6], h2, -h2);
+    v[4 * 1 + 3] = tw(v[7], s8, -c8);
+    v[4 * 2 + 1] = tw(v[9], h2, -h2);
+    v[4 * 2 + 2] = mk<T>(v[10].y, -v[10].x);  // times -i
+    v[4 * 2 + 3] = tw(v[11], -h2, -h2);
+    v[4 * 3 + 1] = tw(v[13], s8, -c8);
+    v[4 * 3 + 2] = tw(v[14], -h2, -h2);
+    v[4 * 3 + 3] = tw(v[15], -c8, s8);
+    // step 3: for each k1, the 4-point DFT over n2 -> X[k1 + 4 k2]
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4f<T>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 index
+    cplx<T> o[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = o[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DFT_THREADS)
+k_rdft_256(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int cols, long ld, long ss, double* sumsq,
+           const int* skip) {
+    if (skip && *skip) return;
+    constexpr int n = 256, XS = DFT_TILE + 1, TS = 17;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = (cplx<T>*)smraw;                 // 256 roots exp(-2 pi i m / 256)
+    cplx<T>* zt = tw + n;                          // [seq][k1][n2], row stride 17: 16 * 16 * 17
+    T* zx = (T*)(zt + 16 * 16 * TS);               // real input [k][tube], row stride 33; later the
+    cplx<T>* z = (cplx<T>*)zx;                     // packed spectrum [k][seq], row stride 17
+    const long t0 = (long)blockIdx.x * DFT_TILE;
+    fill_roots<T>(tw, n, n, (T)-1);
+    const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
+    const bool live = t0 + tt < tubes;
+    const T* xt = X + (live ? tube_off(t0 + tt, cols, ld) : 0);
+    T acc = 0;
+    {
+        constexpr int LB = n / (DFT_THREADS / DFT_TILE);  // 32 loads in flight per thread
+        T v[LB];
+#pragma unroll
+        for (int j = 0; j < LB; ++j) v[j] = live ? __ldcs(xt + (long)(k0 + j * kst) * ss) : (T)0;
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            acc = fma(v[j], v[j], acc);
+            zx[(k0 + j * kst) * XS + tt] = v[j];
+        }
+    }
+    __syncthreads();
+    const int seq = threadIdx.x >> 4, j = threadIdx.x & 15;
+    {
+        // 16-point DFTs over n1 of x[16 n1 + j] (sequence seq: tubes seq and seq + 16 as re, im)
+        cplx<T> v[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) v[n1] = mk<T>(zx[(16 * n1 + j) * XS + seq], zx[(16 * n1 + j) * XS + seq + 16]);
+        dft16f<T>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) zt[(seq * 16 + k1) * TS + j] = cmul(v[k1], tw[(j * k1) & (n - 1)]);
+    }
+    __syncthreads();
+    {
+        // 16-point DFTs over n2 for k1 = j: X[j + 16 k2]
+        cplx<T> v[16];
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) v[n2] = zt[(seq * 16 + j) * TS + n2];
+        dft16f<T>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) z[(j + 16 * k2) * TS + seq] = v[k2];
+    }
+    __syncthreads();
+    const int h = n / 2 + 1;
+    for (int e = threadIdx.x; e < h * DFT_TILE; e += blockDim.x) {
+        const int s = e >> 5, tq = e & 31;
+        const long t = t0 + tq;
+        if (t >= tubes) continue;
+        const int p = tq & 15;
+        const cplx<T> zs = z[s * TS + p];
+        const cplx<T> zc = cconj(z[((n - s) & (n - 1)) * TS + p]);
+        cplx<T> o;
+        if (tq < 16) o = mk<T>((zs.x + zc.x) * (T)0.5, (zs.y + zc.y) * (T)0.5);
+        else o = mk<T>((zs.y - zc.y) * (T)0.5, -(zs.x - zc.x) * (T)0.5);
+        Xh[(long)s * tubes + t] = o;
+    }
+    store_partial<T>(acc, sumsq);
+}
+
+static size_t rdft256_smem(size_t elem) {
+    const size_t c = 2 * elem;
+    const size_t zx = std::max((size_t)256 * (DFT_TILE + 1) * elem, (size_t)256 * 17 * c);
+    return (size_t)256 * c + (size_t)16 * 16 * 17 * c + zx;
 }
 
 template <typename T>
@@ -276,7 +397,12 @@ tp_status rdft(const T* X, void* Xh, int n, int rows, int cols, long ld, long ss
     if (tubes == 0) return TP_OK;
     const unsigned grid = (unsigned)((tubes + DFT_TILE - 1) / DFT_TILE);
     const size_t smem = rdft_smem(n, sizeof(T));
-    if (is_pow2(n)) {
+    if (n == 256) {
+        const size_t sm256 = rdft256_smem(sizeof(T));
+        if (prep(k_rdft_256<T>, sm256) != TP_OK) return TP_ERR_CUDA;
+        prof_begin(TP_KC_DFT, st);
+        k_rdft_256<T><<<grid, DFT_THREADS, sm256, st>>>(X, (cplx<T>*)Xh, tubes, cols, ld, ss, sumsq, skip);
+    } else if (is_pow2(n)) {
         if (prep(k_rdft_pow2<T>, smem) != TP_OK) return TP_ERR_CUDA;
         prof_begin(TP_KC_DFT, st);
         k_rdft_pow2<T><<<grid, DFT_THREADS, smem, st>>>(X, (cplx<T>*)Xh, n, ilog2(n), tubes, cols, ld, ss,
