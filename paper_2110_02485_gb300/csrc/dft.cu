@@ -239,6 +239,78 @@ k_rdft_256(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int co
     store_partial<T>(acc, sumsq);
 }
 
+// Inverse for n = 256: the half spectra of 32 tubes become 16 packed full
+// spectra Z = X_a + i X_b, transformed back by the 16 x 16 split with
+// conjugated roots (the inverse DFT is conj(DFT(conj(Z)))), scaled by 1/n.
+template <typename T>
+__global__ void __launch_bounds__(DFT_THREADS)
+k_irdft_256(const cplx<T>* __restrict__ Xh, T* __restrict__ X, long tubes, int cols, long ld, long ss,
+            const int* skip) {
+    if (skip && *skip) return;
+    constexpr int n = 256, TS = 17;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = (cplx<T>*)smraw;          // 256 roots exp(-2 pi i m / 256)
+    cplx<T>* zt = tw + n;                   // [seq][k1][n2], row stride 17
+    cplx<T>* z = zt + 16 * 16 * TS;         // conj of the packed spectrum, then the packed signal: [k][seq]
+    const long t0 = (long)blockIdx.x * DFT_TILE;
+    fill_roots<T>(tw, n, n, (T)-1);
+    const int h = n / 2 + 1;
+    constexpr int LB = sizeof(T) == 4 ? 8 : 4;
+    for (int e0 = threadIdx.x; e0 < h * 16; e0 += LB * blockDim.x) {
+        cplx<T> xa[LB], xb[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int s = e >> 4, p = e & 15;
+            const long ta = t0 + p, tb = t0 + p + 16;
+            xa[u] = (e < h * 16 && ta < tubes) ? Xh[(long)s * tubes + ta] : mk<T>(0, 0);
+            xb[u] = (e < h * 16 && tb < tubes) ? Xh[(long)s * tubes + tb] : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= h * 16) break;
+            const int s = e >> 4, p = e & 15;
+            cplx<T> a = xa[u], b = xb[u];
+            const bool self = (s == 0) || (2 * s == n);
+            if (self) { a.y = 0; b.y = 0; }
+            // conj(Z[s]) and conj(Z[n - s]), Z = X_a + i X_b with X(n - s) = conj(X(s))
+            z[s * TS + p] = mk<T>(a.x - b.y, -(a.y + b.x));
+            if (!self) z[(n - s) * TS + p] = mk<T>(a.x + b.y, -(b.x - a.y));
+        }
+    }
+    __syncthreads();
+    const int seq = threadIdx.x >> 4, j = threadIdx.x & 15;
+    {
+        cplx<T> v[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) v[n1] = z[(16 * n1 + j) * TS + seq];
+        dft16f<T>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) zt[(seq * 16 + k1) * TS + j] = cmul(v[k1], tw[(j * k1) & (n - 1)]);
+    }
+    __syncthreads();
+    {
+        cplx<T> v[16];
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) v[n2] = zt[(seq * 16 + j) * TS + n2];
+        dft16f<T>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) z[(j + 16 * k2) * TS + seq] = v[k2];  // conj of the packed signal
+    }
+    __syncthreads();
+    const T inv = (T)1 / (T)n;
+    const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
+    if (t0 + tt < tubes) {
+        T* xt = X + tube_off(t0 + tt, cols, ld);
+#pragma unroll 8
+        for (int k = k0; k < n; k += kst) {
+            const cplx<T> v = z[k * TS + (tt & 15)];
+            xt[(long)k * ss] = (tt < 16 ? v.x : -v.y) * inv;
+        }
+    }
+}
+
 static size_t rdft256_smem(size_t elem) {
     const size_t c = 2 * elem;
     const size_t zx = std::max((size_t)256 * (DFT_TILE + 1) * elem, (size_t)256 * 17 * c);
@@ -422,7 +494,12 @@ tp_status irdft(const void* Xh, T* X, int n, int rows, int cols, long ld, long s
     if (tubes == 0) return TP_OK;
     const unsigned grid = (unsigned)((tubes + DFT_TILE - 1) / DFT_TILE);
     const size_t smem = rdft_smem(n, sizeof(T));
-    if (is_pow2(n)) {
+    if (n == 256) {
+        const size_t sm256 = (size_t)(256 + 2 * 16 * 16 * 17) * 2 * sizeof(T);
+        if (prep(k_irdft_256<T>, sm256) != TP_OK) return TP_ERR_CUDA;
+        prof_begin(TP_KC_DFT, st);
+        k_irdft_256<T><<<grid, DFT_THREADS, sm256, st>>>((const cplx<T>*)Xh, X, tubes, cols, ld, ss, skip);
+    } else if (is_pow2(n)) {
         if (prep(k_irdft_pow2<T>, smem) != TP_OK) return TP_ERR_CUDA;
         prof_begin(TP_KC_DFT, st);
         k_irdft_pow2<T><<<grid, DFT_THREADS, smem, st>>>((const cplx<T>*)Xh, X, n, ilog2(n), tubes, cols, ld,
