@@ -146,6 +146,46 @@ k_cgemm(int M, int N, int K, const int* dM, const int* dN, const int* dK, cplx<T
     }
 }
 
+// Products with at most four right-hand columns and A read by rows (op N or
+// R): a warp per row of C, the lanes striding the reduction (coalesced rows of
+// A), a warp sum per column.  Rows past the run-time count are not written.
+constexpr int ROWDOT_NB = 4;
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rowdot(int M, int N, int K, const int* dM, const int* dN, const int* dK, cplx<T> alpha,
+         const cplx<T>* __restrict__ A, long lda, long sA, int conjA, const cplx<T>* __restrict__ B, long ldb,
+         long sB, cplx<T>* __restrict__ C, long ldc, long sC, const int* skip) {
+    typedef cplx<T> V;
+    if (skip && *skip) return;
+    int Me = M, Ne = N, Ke = K;
+    if (dM) Me = min(Me, *dM);
+    if (dN) Ne = min(Ne, *dN);
+    if (dK) Ke = min(Ke, *dK);
+    const int lane = threadIdx.x & 31, row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= Me) return;
+    const long s = blockIdx.y;
+    const V* a = A + s * sA + (long)row * lda;
+    B += s * sB;
+    V acc[ROWDOT_NB];
+#pragma unroll
+    for (int c = 0; c < ROWDOT_NB; ++c) acc[c] = mk<T>(0, 0);
+#pragma unroll 4
+    for (int k = lane; k < Ke; k += 32) {
+        V x = a[k];
+        if (conjA) x.y = -x.y;
+#pragma unroll
+        for (int c = 0; c < ROWDOT_NB; ++c)
+            if (c < Ne) cfma(acc[c], x, B[(long)k * ldb + c]);
+    }
+#pragma unroll
+    for (int c = 0; c < ROWDOT_NB; ++c) {
+        acc[c].x = warp_sum(acc[c].x);
+        acc[c].y = warp_sum(acc[c].y);
+    }
+    if (lane == 0)
+        for (int c = 0; c < Ne; ++c) C[s * sC + (long)row * ldc + c] = cmul(alpha, acc[c]);
+}
+
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 static tp_status launch(int batch, int M, int N, int K, const int* dM, const int* dN, const int* dK,
                         cplx<T> alpha, const void* A, long lda, long sA, int opA, const void* B, long ldb,
@@ -176,6 +216,13 @@ tp_status cgemm(int batch, int M, int N, int K, const int* dM, const int* dN, co
         if (e != TP_ERR_UNSUPPORTED) return e;
     }
     const cplx<T> al = mk<T>((T)alpha_re, (T)alpha_im), be = mk<T>((T)beta_re, (T)beta_im);
+    if (N <= ROWDOT_NB && (opA == OP_N || opA == OP_R) && opB == OP_N && beta_re == 0.0 && beta_im == 0.0) {
+        dim3 grid((unsigned)((M + 7) / 8), (unsigned)batch);
+        prof_begin(TP_KC_GEMM, st);
+        k_rowdot<T><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, al, (const cplx<T>*)A, lda, sA, opA == OP_R ? 1 : 0,
+                                          (const cplx<T>*)B, ldb, sB, (cplx<T>*)C, ldc, sC, skip);
+        return launched(TP_KC_GEMM, st);
+    }
     if (N <= 16)
         return launch<T, 128, 16, (sizeof(T) == 4 ? 16 : 8), 4, 2>(batch, M, N, K, dM, dN, dK, al, A, lda, sA, opA,
                                                                     B, ldb, sB, opB, be, C, ldc, sC, skip, st);
