@@ -418,6 +418,11 @@ def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
         out[name] = rec
     out["note"] = ("TF32: sketch and power-iteration products with one tf32 tensor-core product; "
                    "re-projection and the rest float32")
+    if gold is not None and "fp32_error_prediction" in gold["rtsvd"]:
+        # first-order float32 error of the truncated solution, u32 kappa_k sqrt(N), from the oracle's
+        # singular values (kappa_k = max sigma_1 / min sigma_k over the Fourier slices)
+        out["oracle_kappa_k"] = gold["rtsvd"]["kappa_k"]
+        out["fp32_error_prediction"] = gold["rtsvd"]["fp32_error_prediction"]
     return out
 
 

@@ -44,8 +44,13 @@ def main() -> None:
 
     r1 = O.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.eps_rel * np.sqrt(O.fro2(A)), cfg.p_over, cfg.block,
                        cfg.q_power, cfg.r_max)
+    # FP32 feasibility: kappa_k = max_s sigma_1 / min_s sigma_k of the factorisation's singular values, and the
+    # first-order float32 error of the truncated solution, u32 kappa_k sqrt(N)
+    S = r1["S"]
+    kappa = float(S[:, 0].max() / S[:, r1["k"] - 1].min())
     out["rtsvd"] = pack(r1, {"r": int(r1["r"]), "residual": float(r1["res"][r1["k"]]), "margin": float(r1["margin"]),
-                             "res": {str(k): v for k, v in r1["res"].items()}})
+                             "res": {str(k): v for k, v in r1["res"].items()}, "kappa_k": kappa,
+                             "fp32_error_prediction": float(np.finfo(np.float32).eps * kappa * np.sqrt(cfg.N))})
     r2 = O.tgkb_solve(A, B, P["delta"], cfg.tau, cfg.k_max)
     out["tgkb"] = pack(r2, {"residual": float(r2["res"][r2["k"]]), "margin": float(r2["margin"]),
                             "res": {str(k): v for k, v in r2["res"].items()}})
