@@ -710,6 +710,8 @@ template <> struct JacobiSweeps<float> {
                                : jacobi_sweeps_reg<12, false>(Rs, dp, np, r, max_sweeps, tol);
         if (r <= 128) return v2 ? jacobi_sweeps_reg<16, true>(Rs, dp, np, r, max_sweeps, tol)
                                 : jacobi_sweeps_reg<16, false>(Rs, dp, np, r, max_sweeps, tol);
+        if (r <= 160) return v2 ? jacobi_sweeps_reg<20, true>(Rs, dp, np, r, max_sweeps, tol)
+                                : jacobi_sweeps_reg<20, false>(Rs, dp, np, r, max_sweeps, tol);
         return jacobi_sweeps_smem<float>(Rs, dp, np, r, max_sweeps, tol);
     }
 };

@@ -115,6 +115,29 @@ def synthetic_image(rows: int, cols: int, n_bumps: int, n_rects: int,
     return np.clip(img, 0.0, 1.0)
 
 
+def synthetic_video(rows: int, cols: int, frames: int, n_bumps: int, n_rects: int,
+                    rng: np.random.Generator) -> np.ndarray:
+    """`frames` images of one scene whose bumps move by one pixel per frame
+    along the columns (the rectangles stay); (frames, rows, cols) in [0, 1]."""
+    N = max(rows, cols)
+    ii = np.arange(rows, dtype=np.float64)[:, None]
+    jj = np.arange(cols, dtype=np.float64)[None, :]
+    bumps = [(rng.uniform(0, rows), rng.uniform(0, cols), rng.uniform(N / 32.0, N / 8.0), rng.uniform(0.3, 1.0))
+             for _ in range(n_bumps)]
+    still = np.zeros((rows, cols))
+    for _ in range(n_rects):
+        r0, r1 = np.sort(rng.integers(0, rows, size=2))
+        c0, c1 = np.sort(rng.integers(0, cols, size=2))
+        still[r0:r1 + 1, c0:c1 + 1] += rng.uniform(0.2, 1.0)
+    out = np.empty((frames, rows, cols))
+    for f in range(frames):
+        img = still.copy()
+        for ci, cj, w, amp in bumps:
+            img += amp * np.exp(-((ii - ci) ** 2 + (jj - cj - f) ** 2) / (2.0 * w * w))
+        out[f] = np.clip(img, 0.0, 1.0)
+    return out
+
+
 def forward_blur(T: np.ndarray, c: np.ndarray, img: np.ndarray) -> np.ndarray:
     """B_img = T @ img @ Circ(c)^T with Circ[k, k'] = c[(k - k') mod n].
 
@@ -144,7 +167,7 @@ def gaussian_tensor(shape, seed: int, dtype=np.float32) -> np.ndarray:
 
 
 def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | None = None,
-                 general: float = 0.0, with_omega: bool = True, frames: int = 1) -> dict:
+                 general: float = 0.0, with_omega: bool = True, frames: int = 1, video: bool = False) -> dict:
     """Build one deblurring problem.
 
     general > 0 adds a dense Gaussian perturbation of relative size `general`
@@ -152,7 +175,8 @@ def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | 
     multiples of one matrix.  B is always made from the unperturbed operator.
     frames > 1 blurs that many independent images with the same operator and
     stacks them as lateral slices (the several-right-hand-side problem (I6));
-    the noise level and delta then refer to all frames together.
+    the noise level and delta then refer to all frames together.  video=True
+    makes the frames one moving scene (synthetic_video) instead.
     Returns float32 arrays A (n,N,N), B (n,N,frames), X_true (n,N,frames),
     Omega (n,N,r_max) and float64 scalars delta, norm_A.
     """
@@ -167,7 +191,10 @@ def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | 
     if general > 0.0:
         P = rng.standard_normal(A.shape)
         A = (A.astype(np.float64) + general * P / np.linalg.norm(P) * np.linalg.norm(A)).astype(np.float32)
-    imgs = [synthetic_image(N, N, cfg.bumps, cfg.rects, rng) for _ in range(frames)]
+    if video:
+        imgs = list(synthetic_video(N, N, frames, cfg.bumps, cfg.rects, rng))
+    else:
+        imgs = [synthetic_image(N, N, cfg.bumps, cfg.rects, rng) for _ in range(frames)]
     B_true = np.stack([forward_blur(T, c, img) for img in imgs])
     B, delta = add_noise(B_true if frames > 1 else B_true[0], noise, rng)
     B = B.reshape(frames, N, N)

@@ -495,6 +495,25 @@ def test_tgkb_cap_reports_not_converged(tp, dtype):
     assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype] * 10
 
 
+@pytest.mark.parametrize("N,r_max", [(144, 144), (160, 150)])
+def test_rtsvd_large_rank_matches_oracle(tp, N, r_max):
+    """Float32 RT-tSVD whose rank passes 128 (the small SVD's register form
+    with twenty entries per lane), against the oracle on a few Fourier slices."""
+    A, B, delta = problem(N, 4, seed=N, noise=1e-4, general=0.05)
+    Om = rnd((4, N, r_max), 17).astype(np.float32)
+    tau, eps_rel = 1.1, 1e-6
+    ref = O.rtsvd_solve(A.astype(np.float64), B.astype(np.float64), Om.astype(np.float64), delta, tau,
+                        eps_rel * np.sqrt(O.fro2(A.astype(np.float64))), 200, 16, 1, r_max=r_max)
+    X, info, hist = tp.rtsvd_solve(dev(A, torch.float32), dev(B, torch.float32), dev(Om, torch.float32), delta, tau,
+                                   200, 16, 1, r_max=r_max, eps_rel=eps_rel, res_hist=True)
+    assert ref["r"] > 128 and info["r"] == ref["r"]
+    for k, rk in ref["res"].items():
+        assert abs(hist[k] - rk) <= res_tol(rk, B, torch.float32) * 10, k
+    if exact_k_required(ref, torch.float32):
+        assert info["k"] == ref["k"]
+        assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[torch.float32] * 10
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_rtsvd_rmax_cap_reports_not_converged(tp, dtype):
     A, B, delta = problem(16, 8)
