@@ -77,3 +77,26 @@ def test_rtsvd_lateral_slice_limits(lib):
     P.r_max = 160
     assert L.rtsvd_workspace_bytes(256, 256, 256, 1, ctypes.byref(P), tprod.TP_FP32) > 0
     assert L.rtsvd_workspace_bytes(256, 256, 256, 64, ctypes.byref(P), tprod.TP_FP32) == 0
+
+
+def test_workspace_queries_refuse_out_of_range_requests(lib):
+    """The host-only workspace queries of the later entry points: zero (the
+    refusal) outside each documented limit, positive inside it."""
+    from paper_2110_02485_gb300 import build, tprod
+    L = tprod.load(build.build())
+    T = tprod.TtsvdParams(1.0, 1.1, None)
+    assert L.ttsvd_workspace_bytes(64, 64, 32, 1, ctypes.byref(T), tprod.TP_FP32) > 0
+    assert L.ttsvd_workspace_bytes(200, 200, 32, 1, ctypes.byref(T), tprod.TP_FP32) == 0   # min(l, m) > 160
+    assert L.ttsvd_workspace_bytes(120, 120, 32, 1, ctypes.byref(T), tprod.TP_FP64) == 0   # > 112 in FP64
+    assert L.tgkb_triplets_workspace_bytes(64, 64, 32, 20, tprod.TP_FP32) > 0
+    assert L.tgkb_triplets_workspace_bytes(256, 256, 32, 200, tprod.TP_FP32) == 0           # (k+1)^2 too large
+    assert L.tgkb_triplets_workspace_bytes(16, 16, 8, 17, tprod.TP_FP32) == 0               # k > min(l, m)
+    G = tprod.TgkbParams(1.0, 1.1, 10, None, None)
+    assert L.nested_tgkb_workspace_bytes(64, 64, 32, 5, ctypes.byref(G), tprod.TP_FP32) > 0
+    assert L.nested_tgkb_workspace_bytes(64, 64, 32, 0, ctypes.byref(G), tprod.TP_FP32) == 0
+    assert L.tgkb_workspace_bytes(64, 64, 32, 1025, ctypes.byref(G), tprod.TP_FP32) == 0    # p > 1024
+    d = (ctypes.c_double * 2)(1.0, -1.0)                                                    # a negative bound
+    Gd = tprod.TgkbParams(1.0, 1.1, 10, None, ctypes.cast(d, ctypes.c_void_p))
+    assert L.tgkb_workspace_bytes(64, 64, 32, 2, ctypes.byref(Gd), tprod.TP_FP32) == 0
+    K = tprod.TikParams(G, 1e-2, 1e2, 0.0)
+    assert L.tgkb_tikhonov_workspace_bytes(64, 64, 32, 2, ctypes.byref(K), tprod.TP_FP32) == 0  # p = 1 only
