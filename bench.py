@@ -79,6 +79,7 @@ def args_():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-precision", action="store_true", help="skip the TF32-vs-FP32 RT-tSVD comparison")
     p.add_argument("--no-batched", action="store_true", help="skip the several-frames RT-tSVD measurement")
+    p.add_argument("--no-uneven", action="store_true", help="skip the uneven-size batch of problems")
     p.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
     return p.parse_args()
 
@@ -333,6 +334,9 @@ def run_ours(a, rank, world, local):
     batched = None
     if not a.no_batched and rank == 0:
         batched = batched_form(a, cfg, flush, tprod, torch)
+    uneven = None
+    if not a.no_uneven and rank == 0:
+        uneven = uneven_form(a, flush, tprod, torch)
 
     hbm, bf16, src = peaks()
     work = class_work(cfg, infos)
@@ -366,7 +370,7 @@ def run_ours(a, rank, world, local):
                       f"CUDA graph of the step ({graph.launches} kernels) captured once, replayed per step",
                       "parallelism": f"replicas x{world}"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
-           "precision_form": prec_form, "batched_form": batched,
+           "precision_form": prec_form, "batched_form": batched, "uneven_form": uneven,
            "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
            "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
                           "tgkb": {k: infos[1][k] for k in ("k", "status")},
@@ -505,6 +509,64 @@ def batched_form(a, cfg, flush, tprod, torch, frames=32):
                      "all_ok": all(g["status"] == 0 for g in ginfo),
                      "dp_met": all(ghist[j, ks[j]] <= cfg.tau * dj[j] for j in range(frames))}
     return out
+
+
+def uneven_form(a, flush, tprod, torch, count=16):
+    """Config 4b: 16 independent problems of seeded uneven sizes N (one
+    right-hand side each, noise 1e-2), one RT-tSVD and one tGKB solve each,
+    all 32 solves recorded as one CUDA graph and replayed: solves per second
+    (L2 flushed between replays, CUDA events), with each solve's status."""
+    from paper_2110_02485_gb300 import synth
+    probs = synth.uneven_problems(count)
+    dev = [{k: torch.from_numpy(p[k]).cuda() for k in ("A", "B", "Omega")} for p in probs]
+    tau, p_over, q, b, eps_rel, k_max = 1.1, 10, 1, 16, 3e-2, 100
+
+    def solve(p, d):
+        _, i1, _ = tprod.rtsvd_solve(d["A"], d["B"], d["Omega"], p["delta"], tau, p_over, b, q, p["r_max"],
+                                     eps_rel=eps_rel, sync=False)
+        _, i2, _ = tprod.tgkb_solve(d["A"], d["B"], p["delta"], tau, min(k_max, p["N"]), sync=False)
+        return i1, i2
+
+    nstreams = 4
+    side = [torch.cuda.Stream() for _ in range(nstreams)]
+
+    def all_solves():
+        # the problems are independent: four streams, joined at the end, so that small problems (few
+        # Fourier slices, few CTAs) run side by side
+        main = torch.cuda.current_stream()
+        infos = [None] * len(probs)
+        for st in side:
+            st.wait_stream(main)
+        for i, (p, d) in enumerate(zip(probs, dev)):
+            with torch.cuda.stream(side[i % nstreams]):
+                infos[i] = solve(p, d)
+        for st in side:
+            main.wait_stream(st)
+        return infos
+
+    for p, d in zip(probs, dev):  # first-use setup of every shape outside the capture
+        solve(p, d)
+    torch.cuda.synchronize()
+    g = tprod.Captured(all_solves, warmup=0)
+    reps = max(3, min(a.steps, 10))
+    g.replay()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    infos = [(tprod._info_dict(i1), tprod._info_dict(i2)) for i1, i2 in g.outputs]
+    return {"problems": count, "sizes": [p["N"] for p in probs], "solves_per_s": 2 * count * reps / (ms / 1e3),
+            "ms_per_replay": ms / reps, "kernels_per_replay": g.launches, "streams": nstreams,
+            "rtsvd_status": [i1["status"] for i1, _ in infos], "rtsvd_k": [i1["k"] for i1, _ in infos],
+            "tgkb_status": [i2["status"] for _, i2 in infos], "tgkb_k": [i2["k"] for _, i2 in infos],
+            "workload": "16 problems, N drawn from {64,96,128,192,256,320,384}, blur sigma 2.5 band 8 s 3, "
+                        "noise 1e-2; RT-tSVD p=10 q=1 b=16 r_max=min(N,96) eps_rel=3e-2, tGKB k_max=min(N,100)"}
 
 
 def oracle_solve(method, cfg, P):

@@ -206,3 +206,26 @@ def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | 
         out["Omega"] = rng.standard_normal((N, N, cfg.r_max)).astype(np.float32)
     out["norm_A"] = float(np.sqrt(np.sum(A.astype(np.float64) ** 2)))
     return out
+
+
+UNEVEN_SIZES = (64, 96, 128, 192, 256, 320, 384)
+
+
+def uneven_problems(count: int = 16, seed: int = 46, noise: float = 1e-2, r_cap: int = 96) -> list:
+    """`count` independent deblurring problems of seeded sizes N drawn from
+    UNEVEN_SIZES (blur law sigma 2.5, band 8, s = 3; one image each with 20
+    bumps and 4 rectangles; white noise of relative level `noise`).  Each entry:
+    float32 A (N,N,N), B (N,N,1), Omega (N,N,r_max) with r_max = min(N, r_cap),
+    and N, r_max, delta."""
+    rng = rng_for(seed)
+    out = []
+    for N in rng.choice(UNEVEN_SIZES, size=count):
+        N = int(N)
+        T, c = blur_factors(N, 2.5, 8, 3.0)
+        img = synthetic_image(N, N, 20, 4, rng)
+        B, delta = add_noise(forward_blur(T, c, img), noise, rng)
+        r_max = min(N, r_cap)
+        out.append(dict(N=N, r_max=r_max, delta=delta, A=blur_tensor(T, c), B=lateral(B).astype(np.float32),
+                        Omega=rng.standard_normal((N, N, r_max)).astype(np.float32)))
+    return out
+
