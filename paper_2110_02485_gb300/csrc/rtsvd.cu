@@ -127,6 +127,143 @@ __device__ void chol16_reg(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shif
     __syncwarp();
 }
 
+// ---- float32 deflation on the tensor cores (mma.sync m16n8k8, tf32) ----------
+// The two products of a classical Gram-Schmidt pass, C = Q^H Y and
+// Y <- Y - Q^T C (Q's rows are the basis vectors), written as real products
+// with interleaved (re, im) reduction indices, each operand split as
+// x = hi + lo in tf32 and the products summed as hi*hi + hi*lo + lo*hi
+// (float32-level accuracy, as the 3xTF32 products of zgemm_tc).  Within every
+// 8-deep k step lane quad member t takes the real indices 2t and 2t+1 (the re
+// and im of one complex entry) in the fragment slots t and t+4, the same
+// permutation on both operands.
+__device__ __forceinline__ uint32_t tf32_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ void split_tf(float x, uint32_t& hi, uint32_t& lo) {
+    hi = tf32_bits(x);
+    lo = tf32_bits(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// d += A * [b0; b1] with both split: hi*hi + hi*lo + lo*hi
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t b0h,
+                                     uint32_t b0l, uint32_t b1h, uint32_t b1l) {
+    mma_tf32_16x8x8(d, ah, b0h, b1h);
+    mma_tf32_16x8x8(d, ah, b0l, b1l);
+    mma_tf32_16x8x8(d, al, b0h, b1h);
+}
+
+// Cp (r_prev x 16) = conj(Q) Y for 16 columns of Y (Ys column-major, L a
+// multiple of 16).  Warps take (16-row tile, k range) items; the partial
+// tiles meet in `part` (at most 16 x 16 x 32 floats) and are summed over the
+// k ranges in a fixed order.  Ends with a barrier.
+__device__ void orth_coef_mma(const float2* __restrict__ Q, const float2* Ys, int L, int r_prev, float2* Cp,
+                              float* part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int mt = (r_prev + 15) / 16, nks = L / 4;
+    int KC = nw / mt;
+    KC = KC < 1 ? 1 : (KC > nks ? nks : KC);
+    constexpr uint32_t SGN = 0x80000000u;
+    for (int it = warp; it < mt * KC; it += nw) {
+        const int mtile = it / KC, kc = it - mtile * KC;
+        const int ks0 = kc * nks / KC, ks1 = (kc + 1) * nks / KC;
+        const int i0 = mtile * 16 + g, i1 = i0 + 8;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int ks = ks0; ks < ks1; ++ks) {
+            const int e = ks * 4 + t;
+            const float2 q0 = i0 < r_prev ? __ldcg(Q + (long)i0 * L + e) : make_float2(0.f, 0.f);
+            const float2 q1 = i1 < r_prev ? __ldcg(Q + (long)i1 * L + e) : make_float2(0.f, 0.f);
+            uint32_t ah[4], al[4];
+            split_tf(q0.x, ah[0], al[0]);
+            split_tf(q1.x, ah[1], al[1]);
+            split_tf(q0.y, ah[2], al[2]);
+            split_tf(q1.y, ah[3], al[3]);
+#pragma unroll
+            for (int jh = 0; jh < 2; ++jh) {
+                const float2 y = Ys[(jh * 8 + g) * L + e];
+                uint32_t xh, xl, yh, yl;
+                split_tf(y.x, xh, xl);
+                split_tf(y.y, yh, yl);
+                mma3(acc[jh], ah, al, xh, xl, yh, yl);                    // Re: sum Qr Yr + Qi Yi
+                mma3(acc[2 + jh], ah, al, yh, yl, xh ^ SGN, xl ^ SGN);    // Im: sum Qr Yi - Qi Yr
+            }
+        }
+        float* P = part + (size_t)kc * mt * 16 * 32;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = mtile * 16 + g + (c >> 1) * 8, col = nt * 8 + 2 * t + (c & 1);
+                P[row * 32 + col] = acc[nt][c];
+            }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < r_prev * 16; idx += blockDim.x) {
+        const int i = idx >> 4, j = idx & 15;
+        float sr = 0.f, si = 0.f;
+        for (int kc = 0; kc < KC; ++kc) {
+            const float* P = part + (size_t)kc * mt * 16 * 32 + i * 32;
+            sr += P[j];
+            si += P[16 + j];
+        }
+        Cp[i * 16 + j] = make_float2(sr, si);
+    }
+    __syncthreads();
+}
+
+// Ys (L x 16, column-major) -= Q^T Cp (Q's rows are the basis vectors; no
+// conjugation): a warp per 16-row tile of Y.  L a multiple of 16.
+__device__ void orth_update_mma(const float2* __restrict__ Q, float2* Ys, int L, int r_prev, const float2* Cp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int mt = L / 16, nks = (r_prev + 3) / 4;
+    constexpr uint32_t SGN = 0x80000000u;
+    for (int mtile = warp; mtile < mt; mtile += nw) {
+        const int e0 = mtile * 16 + g, e1 = e0 + 8;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int ks = 0; ks < nks; ++ks) {
+            const int i = ks * 4 + t;
+            const bool ok = i < r_prev;
+            const float2 q0 = ok ? __ldcg(Q + (long)i * L + e0) : make_float2(0.f, 0.f);
+            const float2 q1 = ok ? __ldcg(Q + (long)i * L + e1) : make_float2(0.f, 0.f);
+            uint32_t ah[4], al[4];
+            split_tf(q0.x, ah[0], al[0]);
+            split_tf(q1.x, ah[1], al[1]);
+            split_tf(q0.y, ah[2], al[2]);
+            split_tf(q1.y, ah[3], al[3]);
+#pragma unroll
+            for (int jh = 0; jh < 2; ++jh) {
+                const float2 c = ok ? Cp[i * 16 + jh * 8 + g] : make_float2(0.f, 0.f);
+                uint32_t xh, xl, yh, yl;
+                split_tf(c.x, xh, xl);
+                split_tf(c.y, yh, yl);
+                mma3(acc[jh], ah, al, xh, xl, yh ^ SGN, yl ^ SGN);  // Re: sum Qr Cr - Qi Ci
+                mma3(acc[2 + jh], ah, al, yh, yl, xh, xl);          // Im: sum Qr Ci + Qi Cr
+            }
+        }
+#pragma unroll
+        for (int jh = 0; jh < 2; ++jh)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = (c >> 1) ? e1 : e0, j = jh * 8 + 2 * t + (c & 1);
+                float2* y = Ys + j * L + row;
+                *y = make_float2(y->x - acc[jh][c], y->y - acc[2 + jh][c]);
+            }
+    }
+}
+
 template <typename T, int BB>
 __global__ void __launch_bounds__(OrthThreads<T, BB>::v)
 k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev, cplx<T>* Qout,
@@ -141,6 +278,7 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
     V* Rk = G + BB * BB;                    // this pass's R
     V* Ra = Rk + BB * BB;                   // accumulated in-block R
     V* Rt = Ra + BB * BB;                   // scratch for the product
+    float* part = (float*)(Rt + BB * BB);   // tensor-core deflation: partial coefficient tiles
     __shared__ double red[33];
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = OrthThreads<T, BB>::v / 32;
@@ -163,7 +301,12 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
     if (r_prev > 0) {
         const V* Q = Qb + (long)s * sQ;
         const int dpasses = final_pass ? 2 : 1;
+        const bool tc = sizeof(T) == 4 && BB == 16 && (L & 15) == 0 && r_prev <= 256;  // part: 16 row tiles
         for (int pass = 0; pass < dpasses; ++pass) {
+          if (tc) {
+            orth_coef_mma((const float2*)Q, (const float2*)Ys, L, r_prev, (float2*)Cp, part);
+            orth_update_mma((const float2*)Q, (float2*)Ys, L, r_prev, (const float2*)Cp);
+          } else {
             // two basis vectors per warp share every shared-memory read of Y
             for (int i0 = 2 * warp; i0 < r_prev; i0 += 2 * NW) {
                 const bool two = i0 + 1 < r_prev;
@@ -233,6 +376,7 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                     *y = csub(*y, acc[c]);
                 }
             }
+          }
             for (int e = tid; e < r_prev * BB; e += blockDim.x) Cs[e] = pass ? cadd(Cs[e], Cp[e]) : Cp[e];
             __syncthreads();
         }
@@ -378,7 +522,8 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
 
 static size_t orth_smem(int L, int b, int r_prev, size_t c) {
     const size_t BB = b <= 16 ? 16 : 32;
-    return ((size_t)BB * L + 2 * (size_t)r_prev * BB + 4 * BB * BB) * c;
+    const size_t part = (c == 8 && BB == 16) ? (size_t)16 * 16 * 32 * sizeof(float) : 0;  // tensor-core deflation
+    return ((size_t)BB * L + 2 * (size_t)r_prev * BB + 4 * BB * BB) * c + part;
 }
 
 template <typename T>
