@@ -408,7 +408,10 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
 
     const double td2n = (double)n * tau_delta * tau_delta;
     // Givens state (thread 0): phibar, previous rotation, orphan residual
-    double phibar = z1, cs_prev = 1.0, sn_prev = 0.0, orphan = 0.0;
+    // The rotations run in the working precision: the bidiagonal entries are
+    // working-precision norms, and a float64 square root and division on one
+    // thread cost thousands of cycles per step on this GPU (1/64-rate float64).
+    T phibar = z1, cs_prev = 1, sn_prev = 0, orphan = 0;
     T zprev = z1;
     int k = k_max;
     // Step i publishes its residual and goes on; the discrepancy test of step
@@ -480,26 +483,26 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
             zs_[i] = zi;
             // Givens QR of the lower-bidiagonal slice: column i has c_i on the
             // diagonal, z_{i+1} below it.
-            const double cid = ci, zid = zi;
-            const double rhobar = (i == 1) ? cid : cs_prev * cid;
-            S.theta[i - 1] = (i == 1) ? 0.0 : sn_prev * cid;   // R(i-1, i)
-            const double rho = givens_norm<T>(rhobar, zid);
-            double c = 1.0, sn = 0.0;
-            if (rho > 0.0) {
-                const double irho = 1.0 / rho;
+            const T cid = ci, zid = zi;
+            const T rhobar = (i == 1) ? cid : cs_prev * cid;
+            S.theta[i - 1] = (i == 1) ? 0.0 : (double)(sn_prev * cid);   // R(i-1, i)
+            const T rho = sqrt(fma(rhobar, rhobar, zid * zid));  // norms of working-precision vectors
+            T c = 1, sn = 0;
+            if (rho > (T)0) {
+                const T irho = (T)1 / rho;
                 c = rhobar * irho;
                 sn = zid * irho;
-                S.phi[i - 1] = c * phibar;
+                S.phi[i - 1] = (double)(c * phibar);
                 phibar = -sn * phibar;
             } else {  // zero column: its right-hand side entry stays unmatched
                 S.phi[i - 1] = 0.0;
                 orphan += phibar * phibar;
-                phibar = 0.0;
+                phibar = 0;
             }
             S.rho[i - 1] = rho;
             cs_prev = c;
             sn_prev = sn;
-            res2[(long)i * h + s] = ws * (orphan + phibar * phibar);
+            res2[(long)i * h + s] = ws * (double)(orphan + phibar * phibar);
             // step i done here (release: the residual above is visible first); the test comes after the next product
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&counters[i]) : "memory");
         }
