@@ -280,9 +280,10 @@ __global__ void __launch_bounds__(NT, 1) k_gkb_multi(const GkmArgs a) {
     normalize_multi<T, PB>(u, lu, l, q, lq, Qg, (long)(k_max + 1) * l, act, nrm, inv, invd, mode);
     // Givens state of lateral slice tid (threads 0..PB-1): phibar, previous
     // rotation, orphan residual
-    double phibar = 0.0, cs_prev = 1.0, sn_prev = 0.0, orphan = 0.0;
+    // (rotations in the working precision, as in the single-slice kernel)
+    T phibar = 0, cs_prev = 1, sn_prev = 0, orphan = 0;
     if (tid < PB) {
-        phibar = act[tid] ? (double)nrm[tid] : 0.0;
+        phibar = act[tid] ? nrm[tid] : (T)0;
         zprev[tid] = act[tid] ? nrm[tid] : (T)0;
     }
     __syncthreads();
@@ -344,26 +345,26 @@ __global__ void __launch_bounds__(NT, 1) k_gkb_multi(const GkmArgs a) {
             // Givens QR of lateral slice tid's lower-bidiagonal slice: column i
             // has c_i on the diagonal and z_{i+1} below it
             double* gj = gv + (long)tid * 3 * k_max;
-            const double cid = cj[tid], zid = zj[tid];
-            const double rhobar = (i == 1) ? cid : cs_prev * cid;
-            gj[k_max + i - 1] = (i == 1) ? 0.0 : sn_prev * cid;  // theta: R(i-1, i)
-            const double rho = givens_norm<T>(rhobar, zid);
-            double c = 1.0, sn = 0.0;
-            if (rho > 0.0) {
-                const double irho = 1.0 / rho;
+            const T cid = cj[tid], zid = zj[tid];
+            const T rhobar = (i == 1) ? cid : cs_prev * cid;
+            gj[k_max + i - 1] = (i == 1) ? 0.0 : (double)(sn_prev * cid);  // theta: R(i-1, i)
+            const T rho = sqrt(fma(rhobar, rhobar, zid * zid));
+            T c = 1, sn = 0;
+            if (rho > (T)0) {
+                const T irho = (T)1 / rho;
                 c = rhobar * irho;
                 sn = zid * irho;
-                gj[2 * k_max + i - 1] = c * phibar;
+                gj[2 * k_max + i - 1] = (double)(c * phibar);
                 phibar = -sn * phibar;
             } else {  // zero column: its right-hand side entry stays unmatched
                 gj[2 * k_max + i - 1] = 0.0;
                 orphan += phibar * phibar;
-                phibar = 0.0;
+                phibar = 0;
             }
             gj[i - 1] = rho;
             cs_prev = c;
             sn_prev = sn;
-            a.res2[((long)i * PB + tid) * h + s] = ws * (orphan + phibar * phibar);
+            a.res2[((long)i * PB + tid) * h + s] = ws * (double)(orphan + phibar * phibar);
             zprev[tid] = zj[tid];
             __threadfence();
         }
