@@ -52,52 +52,37 @@ template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
 
 // Cholesky factor of a 16 x 16 Hermitian Gram matrix (upper triangle of G in
-// shared memory) by one warp, the matrix in registers: lanes j and j + 16
-// hold the even and the odd rows of column j.  The step loop is not unrolled
-// (a one-shot straight-line body would be bound by instruction fetch); at
-// step k the lanes pick an entry by a select tree on the bits of k / 2, the
-// lane holding row k of the column passes it on by a shuffle, the pivot comes
-// from lane k (its reciprocal square root Newton-refined), row k of R is
-// formed lane-wise and the entries each lane needs are broadcast by shuffles
-// for the trailing update.  Rows k >= b and zero pivots give zero
-// rows (a zero column stays zero).  On the first pass (may_shift) a pivot
-// below 100 u of the largest diagonal entry restarts on G + shift I and asks
-// for one more pass (shifted CholQR3).  Writes R (row-major) and 1/diag.
+// shared memory) by one warp, the matrix in registers: lane j (and its twin
+// j + 16) holds column j, so with the step loop unrolled every entry has a
+// fixed register.  At step k the pivot comes from lane k (its reciprocal
+// square root Newton-refined), the lanes form row k of R, store it (R is an
+// output) and read back the entries R[k][i] they need for the trailing update
+// from shared memory.  The next pivot is formed ahead of that update: at lane
+// k + 1 the updated diagonal entry needs only that lane's own R[k][k+1], so
+// one shuffle per step lies on the pivot chain.  Rows k >= b and zero pivots
+// give zero rows (a zero column stays zero).  On the first pass (may_shift) a
+// pivot below 100 u of the largest diagonal entry restarts on G + shift I and
+// asks for one more pass (shifted CholQR3).  Writes R (row-major) and 1/diag.
 template <typename T>
 __device__ void chol16_reg(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shift, bool may_shift,
                            int* need_shift, int* passes) {
     typedef cplx<T> V;
-    // lane = 16 h + j holds the entries i = 2 t + h (t < 8) of column j: the
-    // two half-warps split the rows by parity, so each lane selects from and
-    // updates eight entries and fetches eight entries of row k of R
-    const int lane = threadIdx.x & 31, j = lane & 15, hpar = lane >> 4;
+    const int lane = threadIdx.x & 31, j = lane & 15;
     T dmax = G[j * 16 + j].x;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
 #pragma unroll 1
     for (int attempt = 0; attempt < 2; ++attempt) {
-        V col[8];
+        V col[16];  // entries i > j are never read
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int i = 2 * t + hpar;
-            col[t] = i <= j ? G[i * 16 + j] : mk<T>(0, 0);
-            if (attempt == 1 && i == j) col[t].x += shift;
+        for (int i = 0; i < 16; ++i) {
+            col[i] = i <= j ? G[i * 16 + j] : mk<T>(0, 0);
+            if (attempt == 1 && i == j) col[i].x += shift;
         }
         bool bad = false;
-#pragma unroll 1
+        T d2 = __shfl_sync(0xffffffffu, col[0].x, 0);
+#pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const int tk = k >> 1;
-            V t4[4], t2[2];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) t4[i] = (tk & 1) ? col[2 * i + 1] : col[2 * i];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) t2[i] = (tk & 2) ? t4[2 * i + 1] : t4[2 * i];
-            const V mine = (tk & 4) ? t2[1] : t2[0];  // entry 2 tk + hpar of column j
-            const int src = ((k & 1) << 4) + j;        // the lane of this column that holds entry k
-            V ck;
-            ck.x = __shfl_sync(0xffffffffu, mine.x, src);
-            ck.y = __shfl_sync(0xffffffffu, mine.y, src);
-            const T d2 = __shfl_sync(0xffffffffu, ck.x, k);
             if (k < b && d2 < (T)(100.0 * Eps<T>::v) * dmax) bad = true;
             T d = 0, id = 0;
             if (k < b && d2 > (T)0) {
@@ -105,20 +90,22 @@ __device__ void chol16_reg(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shif
                 d = d2 * id;
             }
             V r = mk<T>(0, 0);
-            if (j > k) r = cscale(ck, id);
+            if (j > k) r = cscale(col[k], id);
             else if (j == k) r = mk<T>(d, 0);
+            T d2n = 0;
+            if (k < 15) {
+                const V nd = csub(col[k + 1], cmul(cconj(r), r));
+                d2n = __shfl_sync(0xffffffffu, nd.x, k + 1);
+            }
             if (lane < 16) Rk[k * 16 + j] = r;
             if (lane == 0) invd[k] = id;
+            __syncwarp();
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int i = 2 * t + hpar;
-                V ri;
-                ri.x = __shfl_sync(0xffffffffu, r.x, i);
-                ri.y = __shfl_sync(0xffffffffu, r.y, i);
-                if (i > k && i <= j) col[t] = csub(col[t], cmul(cconj(ri), r));
-            }
+            for (int i = k + 1; i < 16; ++i) col[i] = csub(col[i], cmul(cconj(Rk[k * 16 + i]), r));
+            d2 = d2n;
         }
         if (!may_shift || attempt == 1 || !bad || dmax == (T)0) break;
+        __syncwarp();
         if (lane == 0) {
             *need_shift = 1;
             *passes += 1;
