@@ -45,11 +45,11 @@ NCU_TRAFFIC = {
     "gkb": {"bytes": 70.92e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
             "sha256": "d870f70df2645457074ff1a32126269cad12bdf24da97001ad3b36cd3d6e70cb",
             "profile": "profiles/k_gkb_n256.md"},
-    "orth": {"bytes": 7.49e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
-             "sha256": "286744a79768d6d74bae9a2a65603dc05ff86db805f83a213ecda381bfce4346",
+    "orth": {"bytes": 7.51e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
+             "sha256": "feeb15bdaf81e95a14cbfa0d5a591dc312caa9173344d7c5342b4d608a6ec9c0",
              "profile": "profiles/k_orth_n256.md"},
-    "svd": {"bytes": 9.68e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
-            "sha256": "286744a79768d6d74bae9a2a65603dc05ff86db805f83a213ecda381bfce4346",
+    "svd": {"bytes": 9.69e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
+            "sha256": "feeb15bdaf81e95a14cbfa0d5a591dc312caa9173344d7c5342b4d608a6ec9c0",
             "profile": "profiles/k_jacobi_n256.md"},
 }
 
