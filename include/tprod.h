@@ -310,6 +310,48 @@ tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n,
                               const tp_tik_params* params, void* X, tp_info* d_info, int prec,
                               void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------ gradients in the tube weights -------
+ * For a separable operator A(:,:,k) = c_k T (one fixed l x m matrix T, tube
+ * weights c: the blur law of the synthetic problems), every Fourier slice is
+ * c-hat_s T (c-hat = fft(c)), and the subspaces the solvers build from a
+ * slice (the RT-tSVD sketch with its power iterations for a fixed Omega, the
+ * tGKB Krylov space, the singular vectors) are those of T.  With the discrete
+ * choices of a solve held fixed (k, the sketch rank r, mu) its solution is
+ * therefore X-hat_s = M_s B-hat_s / c-hat_s with M_s free of c for the
+ * truncated methods, and z(lam / |c-hat_s|^2) / c-hat_s for the projected
+ * Tikhonov solution with damping lam = 1/mu (z the solution for T).  For a
+ * loss L with G = dL/dX, Parseval gives
+ *   dL/dc_k = -(1/n) sum_{s<n} Re( (gamma_s + t_s) / c-hat_s * w^{sk} ),
+ *   gamma_s = <G-hat_s, X-hat_s>,  w = exp(-2 pi i / n),
+ * with t_s = 0 for the truncated methods and t_s = 2 lam Re<G-hat_s,
+ * dX-hat_s/dlam> for the Tikhonov-tGKB solution.  A slice with c-hat_s = 0
+ * contributes nothing.  The paper has no counterpart; these are services for
+ * gradient-based use.  c and dc are float64 device arrays of n entries.
+ * Limits: n <= 1024.
+ *
+ * sep_grad_c: for a solution X of rtsvd_truncated_solve, ttsvd_solve,
+ * tgkb_solve or nested_tgkb_solve with such an operator.
+ *   X, G : real (n, m, p);  m, p <= 4096.
+ * Workspace: sep_grad_c_workspace_bytes(m, n, p, prec) (0: invalid sizes).
+ */
+size_t sep_grad_c_workspace_bytes(int m, int n, int p, int prec);
+tp_status sep_grad_c(const void* X, const void* G, const double* c, int m, int n, int p, double* dc, int prec,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* tgkb_tikhonov_grad_c: the same for the solution of the last
+ * tgkb_tikhonov_solve made with solve_ws and the same (l, m, n, params,
+ * prec), at the k and mu it chose, read from that workspace (untouched since;
+ * this call does not modify it, so it can be repeated).  Per slice the
+ * projected solution is y = M^{-1} P_k^T z_1 e_1 with M = P_k^T P_k + lam I,
+ * so dX-hat/dlam = -W_k M^{-1} y, formed in float64 from the bidiagonal.
+ *   G : real (n, m, 1)
+ * Workspace: tgkb_tikhonov_grad_c_workspace_bytes(l, m, n, params, prec).
+ */
+size_t tgkb_tikhonov_grad_c_workspace_bytes(int l, int m, int n, const tp_tik_params* params, int prec);
+tp_status tgkb_tikhonov_grad_c(const void* G, const double* c, int l, int m, int n, const tp_tik_params* params,
+                               const void* solve_ws, size_t solve_ws_bytes, double* dc, int prec, void* ws,
+                               size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------ misc -------- */
 const char* tp_status_string(int status);
 int tp_version(void);                 /* 100 * major + minor                        */

@@ -482,6 +482,60 @@ def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, max_iter=20
 
 
 # --------------------------------------------------------------------------
+# Gradients with respect to the tube weights of a separable operator.
+# --------------------------------------------------------------------------
+
+def tikhonov_rho(g, mu, G):
+    """rho_s = <G-hat_s, dX-hat_s/d lam> (lam = 1/mu) for the projected
+    Tikhonov solution of tikhonov_fixed_mu with the same g and mu: per slice
+    y = V diag(S / (S^2 + lam)) U1 z1 from the SVD of the bidiagonal P_k, so
+    dy/dlam = -V diag(S / (S^2 + lam)^2) U1 z1 and dX-hat/dlam = W_k dy/dlam.
+    Returns the n complex values (full spectrum)."""
+    n = g["c"].shape[0]
+    k = g["c"].shape[1]
+    U1, S, Vs = _bidiag_svds(g["c"], g["z"], k)
+    z1 = g["z"][:, 0]
+    lam = 1.0 / mu
+    Gh = fft3(G)[:, :, 0]
+    rho = np.zeros(n, complex)
+    for s in range(n):
+        dy = Vs[s] @ (-S[s] / (S[s] ** 2 + lam) ** 2 * z1[s] * U1[s])
+        xi = g["W"][s] @ dy
+        rho[s] = np.vdot(Gh[s], xi)
+    return rho
+
+
+def grad_c_separable(X, G, c, lam=0.0, rho=None):
+    """dL/dc for a solution X (n, m, p) of a solve with the separable operator
+    A(:,:,k) = c_k T, for G = dL/dX, with the discrete choices of the solve (k,
+    the sketch rank r) held fixed.
+
+    Each Fourier slice of A is c-hat_s T, and the subspaces every method builds
+    from a slice (the RT-tSVD sketch with its power iterations, the tGKB
+    Krylov space, the singular vectors) are those of T, so the truncated
+    solutions are X-hat_s = M_s B-hat_s / c-hat_s with M_s free of c:
+    dX-hat_s = -X-hat_s dc-hat_s / c-hat_s.  The projected Tikhonov solution
+    with damping lam is z(lam / |c-hat_s|^2) / c-hat_s, z the solution for T,
+    which adds -(2 lam / |c-hat_s|^2) xi_s Re(conj(c-hat_s) dc-hat_s) with
+    xi_s = dX-hat_s/dlam (rho_s = <G-hat_s, xi_s> from tikhonov_rho).  With
+    dL = (1/n) sum_s Re<G-hat_s, dX-hat_s> (Parseval) and dc-hat_s =
+    sum_k dc_k w^{sk}, w = exp(-2 pi i / n):
+        dL/dc_k = -(1/n) sum_s Re( (gamma_s + 2 lam Re rho_s) / c-hat_s * w^{sk} ),
+    gamma_s = <G-hat_s, X-hat_s>.  The paper has no counterpart; the sum over
+    s is written out over the full spectrum."""
+    n = c.shape[0]
+    Xh, Gh = fft3(X), fft3(G)
+    ch = fft3(np.asarray(c, float)[:, None, None])[:, 0, 0]
+    gam = np.einsum("sij,sij->s", np.conj(Gh), Xh)
+    if rho is not None:
+        gam = gam + 2.0 * lam * np.real(rho)
+    a = -gam / ch
+    idx = np.arange(n)
+    w = np.exp(-2j * np.pi * np.outer(idx, idx) / n)
+    return np.real(a @ w) / n
+
+
+# --------------------------------------------------------------------------
 # t-Lanczos (Algorithm t-Lanc) and the t-Lanczos method (Eq. (9t)); symmetric A.
 # --------------------------------------------------------------------------
 

@@ -307,6 +307,41 @@ tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n,
     return TP_ERR_ARG;
 }
 
+size_t sep_grad_c_workspace_bytes(int m, int n, int p, int prec) {
+    if (prec == TP_FP32) return sep_ws_bytes<float>(m, n, p);
+    if (prec == TP_FP64) return sep_ws_bytes<double>(m, n, p);
+    return 0;
+}
+
+tp_status sep_grad_c(const void* X, const void* G, const double* c, int m, int n, int p, double* dc, int prec,
+                     void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return sep_grad<float>((const float*)X, (const float*)G, c, m, n, p, dc, ws, ws_bytes, st);
+    if (prec == TP_FP64)
+        return sep_grad<double>((const double*)X, (const double*)G, c, m, n, p, dc, ws, ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+size_t tgkb_tikhonov_grad_c_workspace_bytes(int l, int m, int n, const tp_tik_params* params, int prec) {
+    if (prec == TP_FP32) return tik_grad_ws_bytes<float>(l, m, n, params);
+    if (prec == TP_FP64) return tik_grad_ws_bytes<double>(l, m, n, params);
+    return 0;
+}
+
+tp_status tgkb_tikhonov_grad_c(const void* G, const double* c, int l, int m, int n, const tp_tik_params* params,
+                               const void* solve_ws, size_t solve_ws_bytes, double* dc, int prec, void* ws,
+                               size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return tik_grad_c<float>((const float*)G, c, l, m, n, params, solve_ws, solve_ws_bytes, dc, ws, ws_bytes,
+                                 st);
+    if (prec == TP_FP64)
+        return tik_grad_c<double>((const double*)G, c, l, m, n, params, solve_ws, solve_ws_bytes, dc, ws,
+                                  ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
 const char* tp_status_string(int status) {
     switch (status) {
         case TP_OK: return "ok";

@@ -1616,6 +1616,122 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     return TP_OK;
 }
 
+// Tikhonov term of the tube-weight gradient, per slice s: with lam = 1/mu of
+// the solve (mu = 10^t) and M = P^T P + lam I (P the (k+1) x k lower
+// bidiagonal of the slice: c on the diagonal, z_1..z_k below it; M is
+// tridiagonal with M_jj = c_j^2 + z_{j+1}^2 + lam, M_{j-1,j} = z_j c_j), the
+// projected solution is y = M^{-1} P^T z_0 e_1 = M^{-1} (z_0 c_0) e_1 and
+// dy/dlam = -M^{-1} y.  Then dX-hat/dlam = W_k dy/dlam and
+//   add[s] = 2 lam Re<G-hat_s, W_k dy/dlam> = 2 lam sum_j dy_j Re(h_j),
+// h_j = <w_j, G-hat_s>.  Warps form Re(h_j); one thread factors M = L D L^T
+// (float64, positive pivots since lam > 0) and solves both systems.
+// scr: per slice 3 k_max doubles.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tik_rho(const T* cc, const T* zz, int k_max, const cplx<T>* Wb, int m,
+                                                 const State* st, const TikState* ts, const cplx<T>* Gh,
+                                                 double* scr, double* add) {
+    __shared__ double hre[GKB_KMAX];
+    const int s = blockIdx.x, k = st->k, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const cplx<T>* W = Wb + (long)s * k_max * m;
+    const cplx<T>* g = Gh + (long)s * m;
+    for (int j = warp; j < k; j += nw) {
+        double a = 0.0;
+        for (int e = lane; e < m; e += 32) {
+            const cplx<T> w = W[(long)j * m + e], x = g[e];
+            a += (double)(w.x * x.x + w.y * x.y);
+        }
+        a = warp_sum(a);
+        if (lane == 0) hre[j] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double lam = pow(10.0, -ts->t);
+    const T* c = cc + (long)s * k_max;
+    const T* z = zz + (long)s * (k_max + 1);
+    double* dd = scr + (long)s * 3 * k_max;  // pivots of D
+    double* ll = dd + k_max;                 // subdiagonal of L
+    double* y = ll + k_max;
+    for (int j = 0; j < k; ++j) {
+        const double cj = (double)c[j], zj1 = (double)z[j + 1];
+        const double mjj = cj * cj + zj1 * zj1 + lam;
+        if (j == 0) {
+            dd[0] = mjj;
+        } else {
+            const double off = (double)z[j] * cj;  // M_{j-1,j}
+            ll[j] = off / dd[j - 1];
+            dd[j] = mjj - ll[j] * off;
+        }
+    }
+    // y = M^{-1} (z_0 c_0 e_1): forward with L, scale by D, back with L^T
+    for (int j = 0; j < k; ++j) y[j] = j == 0 ? (double)z[0] * (double)c[0] : -ll[j] * y[j - 1];
+    for (int j = 0; j < k; ++j) y[j] /= dd[j];
+    for (int j = k - 2; j >= 0; --j) y[j] -= ll[j + 1] * y[j + 1];
+    // dy = -M^{-1} y, accumulated into sum_j dy_j Re(h_j) on the way back
+    double prev = 0.0;
+    for (int j = 0; j < k; ++j) {
+        const double u = -y[j] - (j > 0 ? ll[j] * prev : 0.0);
+        prev = u;
+        y[j] = u / dd[j];  // y now holds D^{-1} L^{-1} (-y)
+    }
+    double acc = 0.0, next = 0.0;
+    for (int j = k - 1; j >= 0; --j) {
+        const double dy = y[j] - (j + 1 < k ? ll[j + 1] * next : 0.0);
+        next = dy;
+        acc += dy * hre[j];
+    }
+    add[s] = 2.0 * lam * acc;
+}
+
+template <typename T>
+static size_t tik_grad_carve(void* base, int m, int n, int k_max, cplx<T>** Gh, double2** gamma, double** add,
+                             double** scr) {
+    const size_t h = n / 2 + 1;
+    Carver cv(base, 0);
+    *Gh = cv.take<cplx<T>>(h * m);
+    *gamma = cv.take<double2>(h);
+    *add = cv.take<double>(h);
+    *scr = cv.take<double>(h * 3 * (size_t)k_max);
+    return cv.off;
+}
+
+template <typename T>
+size_t tik_grad_ws_bytes(int l, int m, int n, const tp_tik_params* P) {
+    if (!P || gk_check<T>(l, m, n, 1, &P->gkb) != TP_OK || n > GRAD_MAX_N) return 0;
+    cplx<T>* Gh;
+    double2* gamma;
+    double *add, *scr;
+    return tik_grad_carve<T>(nullptr, m, n, P->gkb.k_max, &Gh, &gamma, &add, &scr);
+}
+
+template <typename T>
+tp_status tik_grad_c(const T* G, const double* c, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,
+                     size_t solve_ws_bytes, double* dc, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!P || !G || !c || !dc || n > GRAD_MAX_N) return TP_ERR_ARG;
+    TRY(gk_check<T>(l, m, n, 1, &P->gkb));
+    const int k_max = P->gkb.k_max, h = n / 2 + 1;
+    GkWs<T> w = gk_carve<T>((void*)solve_ws, l, m, n, k_max, 1);
+    if (!solve_ws || ((size_t)solve_ws & 255) || solve_ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
+    cplx<T>* Gh;
+    double2* gamma;
+    double *add, *scr;
+    const size_t need = tik_grad_carve<T>(ws, m, n, k_max, &Gh, &gamma, &add, &scr);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < need) return TP_ERR_WORKSPACE;
+    TRY(rdft<T>(G, Gh, n, m, 1, 1, m, nullptr, nullptr, st));
+    prof_begin(TP_KC_MISC, st);
+    k_tik_rho<T><<<h, 256, 0, st>>>(w.cc, w.zz, k_max, w.W, m, w.st, w.ts, Gh, scr, add);
+    TRY(launched(TP_KC_MISC, st));
+    TRY(sep_gamma<T>(w.Xhat, Gh, h, m, gamma, st));
+    return grad_c(c, n, gamma, add, dc, st);
+}
+
+template size_t tik_grad_ws_bytes<float>(int, int, int, const tp_tik_params*);
+template size_t tik_grad_ws_bytes<double>(int, int, int, const tp_tik_params*);
+template tp_status tik_grad_c<float>(const float*, const double*, int, int, int, const tp_tik_params*, const void*,
+                                     size_t, double*, void*, size_t, cudaStream_t);
+template tp_status tik_grad_c<double>(const double*, const double*, int, int, int, const tp_tik_params*, const void*,
+                                      size_t, double*, void*, size_t, cudaStream_t);
+
 template size_t gk_ws_bytes<float>(int, int, int, int, const tp_tgkb_params*);
 template size_t gk_ws_bytes<double>(int, int, int, int, const tp_tgkb_params*);
 template size_t gkn_ws_bytes<float>(int, int, int, int, const tp_tgkb_params*);

@@ -136,4 +136,21 @@ struct Carver {
     }
 };
 
+// Gradients with respect to the tube weights of a separable operator
+// (grad.cu).  sep_gamma: gamma[s] = <Gh[s], Xh[s]> over `per` complex entries
+// per slice; grad_c: dc_k = -(1/n) sum_s Re((gamma_s + add_s) / c-hat_s w^{sk})
+// over the half spectrum (add optional, device, h entries).
+constexpr int GRAD_MAX_N = 1024;
+template <typename T>
+tp_status sep_gamma(const void* Xh, const void* Gh, int h, long per, double2* gamma, cudaStream_t st);
+tp_status grad_c(const double* c, int n, const double2* gamma, const double* add, double* dc, cudaStream_t st);
+template <typename T> size_t sep_ws_bytes(int m, int n, int p);
+template <typename T>
+tp_status sep_grad(const T* X, const T* G, const double* c, int m, int n, int p, double* dc, void* ws,
+                   size_t ws_bytes, cudaStream_t st);
+template <typename T> size_t tik_grad_ws_bytes(int l, int m, int n, const tp_tik_params* P);
+template <typename T>
+tp_status tik_grad_c(const T* G, const double* c, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,
+                     size_t solve_ws_bytes, double* dc, void* ws, size_t ws_bytes, cudaStream_t st);
+
 }  // namespace tp

@@ -52,7 +52,8 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
            "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
            "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve", "tgkb_triplets_workspace_bytes",
-           "tgkb_triplets")
+           "tgkb_triplets", "sep_grad_c_workspace_bytes", "sep_grad_c", "tgkb_tikhonov_grad_c_workspace_bytes",
+           "tgkb_tikhonov_grad_c")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -108,8 +109,14 @@ def load(path: str | None = None):
     L.tp_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), i]
     L.tp_timing_read.restype = i
     L.tprod_gemm_noalloc.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]
+    L.sep_grad_c_workspace_bytes.argtypes = [i, i, i, i]
+    L.sep_grad_c_workspace_bytes.restype = sz
+    L.sep_grad_c.argtypes = [vp, vp, vp, i, i, i, vp, i, vp, sz, vp]
+    L.tgkb_tikhonov_grad_c_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(TikParams), i]
+    L.tgkb_tikhonov_grad_c_workspace_bytes.restype = sz
+    L.tgkb_tikhonov_grad_c.argtypes = [vp, vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, i, vp, sz, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
-              "tgkb_tikhonov_solve", "tprod_gemm_noalloc"):
+              "tgkb_tikhonov_solve", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -515,8 +522,63 @@ def tgkb_triplets(A, B, k):
     return U, S, V
 
 
-def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True):
-    """Tikhonov-tGKB (Section 5).  Returns (X, info)."""
+class TgktFactor:
+    """What tgkt_solve(..., keep=True) leaves for tgkt_grad_c: the solve's
+    workspace (basis, bidiagonal, k, mu, X-hat) and its arguments."""
+
+    def __init__(self, ws, P, l, m, n, prec, device, dtype):
+        self.ws, self.P = ws, P
+        self.l, self.m, self.n = l, m, n
+        self.prec, self.device, self.dtype = prec, device, dtype
+
+
+def sep_grad_c(X: torch.Tensor, G: torch.Tensor, c: torch.Tensor) -> torch.Tensor:
+    """dL/dc for a solution X (n, m, p) of a truncated solve (T-tSVD, RT-tSVD,
+    tGKB, nested tGKB) with the separable operator A(:,:,k) = c_k T, at the
+    solve's k, for G = dL/dX.  c: float64 CUDA tensor (n,).  Returns dc
+    (float64, n)."""
+    _dev(X, G, c)
+    if tuple(G.shape) != tuple(X.shape) or G.dtype != X.dtype or c.dtype != torch.float64:
+        raise ValueError("G must match X; c must be float64")
+    n, m, p = X.shape
+    if tuple(c.shape) != (n,):
+        raise ValueError("c must hold n tube weights")
+    prec = _prec(X)
+    L = load()
+    nb = L.sep_grad_c_workspace_bytes(m, n, p, prec)
+    if nb == 0:
+        raise TprodError("sep_grad_c_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, X.device)
+    wp, wn = _aligned(ws)
+    dc = torch.empty(n, dtype=torch.float64, device=X.device)
+    _check("sep_grad_c", L.sep_grad_c(_ptr(X), _ptr(G), _ptr(c), m, n, p, _ptr(dc), prec, wp, wn, _stream()))
+    return dc
+
+
+def tgkt_grad_c(fac: "TgktFactor", G: torch.Tensor, c: torch.Tensor) -> torch.Tensor:
+    """dL/dc for the Tikhonov-tGKB solution that made `fac` (k and mu fixed),
+    operator A(:,:,k) = c_k T, for G = dL/dX (n, m, 1).  Returns dc (float64, n)."""
+    _dev(G, c)
+    if tuple(G.shape) != (fac.n, fac.m, 1) or G.dtype != fac.dtype or c.dtype != torch.float64:
+        raise ValueError("G must match the solution X of the solve; c must be float64")
+    if tuple(c.shape) != (fac.n,):
+        raise ValueError("c must hold n tube weights")
+    L = load()
+    nb = L.tgkb_tikhonov_grad_c_workspace_bytes(fac.l, fac.m, fac.n, ctypes.byref(fac.P), fac.prec)
+    if nb == 0:
+        raise TprodError("tgkb_tikhonov_grad_c_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, G.device)
+    wp, wn = _aligned(ws)
+    sp, sn = _aligned(fac.ws)
+    dc = torch.empty(fac.n, dtype=torch.float64, device=G.device)
+    _check("tgkb_tikhonov_grad_c", L.tgkb_tikhonov_grad_c(_ptr(G), _ptr(c), fac.l, fac.m, fac.n, ctypes.byref(fac.P),
+                                                          sp, sn, _ptr(dc), fac.prec, wp, wn, _stream()))
+    return dc
+
+
+def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True, keep=False):
+    """Tikhonov-tGKB (Section 5).  Returns (X, info[, factor]); keep=True also
+    returns the solve's workspace for tgkt_grad_c."""
     _dev(A, B)
     n, l, m = A.shape
     prec = _prec(A)
@@ -532,6 +594,9 @@ def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True):
     info = _info_buf(A.device)
     _check("tgkb_tikhonov_solve", L.tgkb_tikhonov_solve(_ptr(A), _ptr(B), l, m, n, 1, ctypes.byref(P), _ptr(X),
                                                         _ptr(info), prec, wp, wn, _stream()))
+    if keep:
+        fac = TgktFactor(ws, P, l, m, n, prec, A.device, A.dtype)
+        return (X, info, fac) if not sync else (X, _info_dict(info), fac)
     if not sync:
         return X, info
     return X, _info_dict(info)

@@ -100,3 +100,27 @@ def test_workspace_queries_refuse_out_of_range_requests(lib):
     assert L.tgkb_workspace_bytes(64, 64, 32, 2, ctypes.byref(Gd), tprod.TP_FP32) == 0
     K = tprod.TikParams(G, 1e-2, 1e2, 0.0)
     assert L.tgkb_tikhonov_workspace_bytes(64, 64, 32, 2, ctypes.byref(K), tprod.TP_FP32) == 0  # p = 1 only
+
+
+def test_tube_weight_gradient_queries_and_argument_checks(lib):
+    """Workspace queries of the separable-operator gradients, and their
+    argument errors, answered on the host (no GPU needed)."""
+    from paper_2110_02485_gb300 import tprod
+    L = tprod.load()
+    assert L.sep_grad_c_workspace_bytes(256, 256, 1, tprod.TP_FP32) > 0
+    assert L.sep_grad_c_workspace_bytes(256, 256, 32, tprod.TP_FP64) > L.sep_grad_c_workspace_bytes(
+        256, 256, 32, tprod.TP_FP32)
+    assert L.sep_grad_c_workspace_bytes(256, 2048, 1, tprod.TP_FP32) == 0                   # n > 1024
+    assert L.sep_grad_c_workspace_bytes(0, 16, 1, tprod.TP_FP32) == 0
+    assert L.sep_grad_c_workspace_bytes(16, 16, 1, 9) == 0                                  # bad precision
+    G = tprod.TgkbParams(1.0, 1.1, 10, None)
+    K = tprod.TikParams(G, 1e-2, 1e2, 0.0)
+    assert L.tgkb_tikhonov_grad_c_workspace_bytes(64, 64, 32, ctypes.byref(K), tprod.TP_FP32) > 0
+    assert L.tgkb_tikhonov_grad_c_workspace_bytes(64, 64, 2048, ctypes.byref(K), tprod.TP_FP32) == 0
+    assert L.tgkb_tikhonov_grad_c_workspace_bytes(8, 8, 32, ctypes.byref(K), tprod.TP_FP32) == 0  # k_max > 8
+    # null pointers are rejected before any CUDA call
+    p = ctypes.c_void_p(256)
+    assert L.sep_grad_c(None, p, p, 16, 16, 1, p, tprod.TP_FP32, p, 1 << 20, None) == -1
+    assert L.sep_grad_c(p, p, None, 16, 16, 1, p, tprod.TP_FP32, p, 1 << 20, None) == -1
+    assert L.tgkb_tikhonov_grad_c(None, p, 64, 64, 32, ctypes.byref(K), p, 1 << 30, p, tprod.TP_FP32, p, 1 << 20,
+                                  None) == -1

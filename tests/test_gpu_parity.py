@@ -583,3 +583,116 @@ def test_captured_graph_replay_matches_plain_calls(tp):
         assert all(torch.equal(a, b) for a, b in zip(Xs, ref))
         assert [tp._info_dict(i) for i in infos] == rinfo
 
+
+
+# ------------------------------------- gradients in the tube weights c ----
+
+def separable_problem(N, n, seed, p=1, noise=1e-2):
+    """A(:,:,k) = c_k T exactly (float64), p blurred images plus noise."""
+    T, c = synth.blur_factors(N, 1.3, 3, 1.5, n=n)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    g = np.random.default_rng(seed)
+    Xt = np.concatenate([synth.lateral(synth.synthetic_image(N, n, 3, 1, g)) for _ in range(p)], axis=2)
+    Bt = O.tprod_bcirc(A, Xt)
+    E = g.standard_normal(Bt.shape)
+    E = noise * E / np.linalg.norm(E) * np.linalg.norm(Bt)
+    return T, c, A, Bt + E, float(np.linalg.norm(E))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,p", [(16, 9, 1), (20, 16, 2), (24, 12, 1)])
+def test_sep_grad_c_rtsvd_matches_oracle(tp, dtype, N, n, p):
+    """dL/dc of the RT-tSVD solution (k fixed) for L = <W, X_k>, against the
+    oracle's gradient of its own solve on the same inputs."""
+    T, c, A, B, delta = separable_problem(N, n, 40 + N, p=p)
+    if dtype == torch.float32:
+        A, B = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+    Om = rnd((n, N, N), 41).astype(np.float32).astype(np.float64)
+    ref = O.rtsvd_solve(A, B, Om, delta, 1.1, 0.01 * np.sqrt(O.fro2(A)), 3, 4, 1, r_max=N)
+    X, info = tp.rtsvd_solve(dev(A, dtype), dev(B, dtype), dev(Om, dtype), delta, 1.1, 3, 4, 1, r_max=N,
+                             eps_rel=0.01)
+    if not exact_k_required(ref, dtype):
+        pytest.skip("truncation index inside the rounding band")
+    assert info["k"] == ref["k"]
+    W = rnd((n, N, p), 42)
+    dc = tp.sep_grad_c(X, dev(W, dtype), dev(c, torch.float64)).cpu().numpy()
+    want = O.grad_c_separable(ref["X"], W, c)
+    assert dc.shape == (n,)
+    assert rel(dc, want) <= (1e-8 if dtype == torch.float64 else 5e-3)
+
+
+def test_sep_grad_c_rtsvd_central_differences(tp):
+    """Float64 central differences of L(c) = ||X_k(c) - W||^2 through the GPU
+    solve (k and the sketch rank unchanged under the perturbation) against
+    the GPU gradient.  The sketch stops at rank 20 < 24 by the eta test."""
+    N, n = 24, 10
+    T, c, A, B, delta = separable_problem(N, n, 50)
+    Om = rnd((n, N, N), 51)
+    dt = torch.float64
+    kw = dict(r_max=N, eps_rel=0.01)
+    X, info = tp.rtsvd_solve(dev(A, dt), dev(B, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, **kw)
+    W = rnd((n, N, 1), 52)
+    G = 2.0 * (X - dev(W, dt))
+    dc = tp.sep_grad_c(X, G, dev(c, dt)).cpu().numpy()
+    g = np.random.default_rng(53)
+    h = 1e-6 * np.linalg.norm(c)
+    loss = lambda Xs: float(np.sum((Xs.cpu().numpy() - W) ** 2))
+    for _ in range(8):
+        e = g.standard_normal(n)
+        e /= np.linalg.norm(e)
+        Ap = synth.blur_tensor(T, c + h * e, dtype=np.float64)
+        Am = synth.blur_tensor(T, c - h * e, dtype=np.float64)
+        Xp, ip = tp.rtsvd_solve(dev(Ap, dt), dev(B, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, **kw)
+        Xm, im = tp.rtsvd_solve(dev(Am, dt), dev(B, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, **kw)
+        assert ip["k"] == im["k"] == info["k"] and ip["r"] == im["r"] == info["r"] == 20
+        fd = (loss(Xp) - loss(Xm)) / (2 * h)
+        assert abs(fd - dc @ e) <= 1e-6 * max(abs(fd), np.linalg.norm(dc))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,k_max", [(12, 8, 12), (16, 17, 16)])
+def test_tgkt_grad_c_matches_oracle(tp, dtype, N, n, k_max):
+    """dL/dc of the Tikhonov-tGKB solution (k and mu fixed), damping term
+    included, against the oracle's gradient of its own solve."""
+    T, c, A, B, delta = separable_problem(N, n, 60 + N)
+    if dtype == torch.float32:
+        A, B = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+    ref = O.tgkt_solve(A, B, delta, 1.1, k_max, 1e-3, 1e9)
+    X, info, fac = tp.tgkt_solve(dev(A, dtype), dev(B, dtype), delta, 1.1, k_max, 1e-3, 1e9, keep=True)
+    if not exact_k_required(ref["gkb"], dtype):
+        pytest.skip("truncation index inside the rounding band")
+    assert info["k"] == ref["k"] and info["status"] == ref["status"] == O.STATUS_OK
+    W = rnd((n, N, 1), 61)
+    Wd = dev(W, dtype)
+    dc = tp.tgkt_grad_c(fac, Wd, dev(c, torch.float64)).cpu().numpy()
+    want = O.grad_c_separable(ref["X"], W, c, lam=1.0 / ref["mu"], rho=O.tikhonov_rho(ref["gkb"], ref["mu"], W))
+    assert rel(dc, want) <= (1e-6 if dtype == torch.float64 else 3e-2)
+    # repeatable: the solve's workspace is only read
+    assert np.array_equal(dc, tp.tgkt_grad_c(fac, Wd, dev(c, torch.float64)).cpu().numpy())
+
+
+def test_tgkt_grad_c_central_differences(tp):
+    """Float64 central differences through the GPU Tikhonov-tGKB solve at a
+    fixed mu (a search interval whose upper end still leaves the residual
+    above tau*delta, so the solve returns mu = mu_hi) against the GPU
+    gradient; k unchanged under the perturbation."""
+    N, n = 16, 12
+    T, c, A, B, delta = separable_problem(N, n, 70)
+    dt = torch.float64
+    _, free = tp.tgkt_solve(dev(A, dt), dev(B, dt), delta, 1.1, 16, 1e-3, 1e9)
+    mu0 = free["mu"] / 20.0
+    args = (delta, 1.1, 16, mu0 / 4.0, mu0)
+    X, info, fac = tp.tgkt_solve(dev(A, dt), dev(B, dt), *args, keep=True)
+    assert info["status"] == O.STATUS_NOT_CONVERGED and abs(info["mu"] / mu0 - 1.0) <= 1e-12
+    W = rnd((n, N, 1), 71)
+    dc = tp.tgkt_grad_c(fac, dev(W, dt), dev(c, dt)).cpu().numpy()
+    g = np.random.default_rng(72)
+    h = 1e-6 * np.linalg.norm(c)
+    for _ in range(8):
+        e = g.standard_normal(n)
+        e /= np.linalg.norm(e)
+        Xp, ip = tp.tgkt_solve(dev(synth.blur_tensor(T, c + h * e, dtype=np.float64), dt), dev(B, dt), *args)
+        Xm, im = tp.tgkt_solve(dev(synth.blur_tensor(T, c - h * e, dtype=np.float64), dt), dev(B, dt), *args)
+        assert ip["k"] == im["k"] == info["k"]
+        fd = (float(np.sum(W * Xp.cpu().numpy())) - float(np.sum(W * Xm.cpu().numpy()))) / (2 * h)
+        assert abs(fd - dc @ e) <= 1e-6 * max(abs(fd), np.linalg.norm(dc))
