@@ -43,7 +43,7 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # hash is renewed only when the file changed elsewhere).
 NCU_TRAFFIC = {
     "gkb": {"bytes": 70.92e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
-            "sha256": "d870f70df2645457074ff1a32126269cad12bdf24da97001ad3b36cd3d6e70cb",
+            "sha256": "e5b60671570d3ef0b36e00a53d70932906826c31e0a86789484f58848fcfa887",
             "profile": "profiles/k_gkb_n256.md"},
     "orth": {"bytes": 7.51e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
              "sha256": "feeb15bdaf81e95a14cbfa0d5a591dc312caa9173344d7c5342b4d608a6ec9c0",
