@@ -80,6 +80,7 @@ def args_():
     p.add_argument("--no-precision", action="store_true", help="skip the TF32-vs-FP32 RT-tSVD comparison")
     p.add_argument("--no-batched", action="store_true", help="skip the several-frames RT-tSVD measurement")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven-size batch of problems")
+    p.add_argument("--no-grad", action="store_true", help="skip the differentiation form")
     p.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
     return p.parse_args()
 
@@ -337,6 +338,9 @@ def run_ours(a, rank, world, local):
     uneven = None
     if not a.no_uneven and rank == 0:
         uneven = uneven_form(a, flush, tprod, torch)
+    grad = None
+    if not a.no_grad and rank == 0:
+        grad = differentiation_form(a, cfg, P, A, B, Om, flush, tprod, torch)
 
     hbm, bf16, src = peaks()
     work = class_work(cfg, infos)
@@ -371,6 +375,7 @@ def run_ours(a, rank, world, local):
                       "parallelism": f"replicas x{world}"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
            "precision_form": prec_form, "batched_form": batched, "uneven_form": uneven,
+           "differentiation_form": grad,
            "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
            "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
                           "tgkb": {k: infos[1][k] for k in ("k", "status")},
@@ -428,6 +433,51 @@ def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
         out["oracle_kappa_k"] = gold["rtsvd"]["kappa_k"]
         out["fp32_error_prediction"] = gold["rtsvd"]["fp32_error_prediction"]
     return out
+
+
+def differentiation_form(a, cfg, P, A, B, Om, flush, tprod, torch):
+    """Gradients of L = ||X - X_true||_F^2 for the workload's blur (A(:,:,k) =
+    c_k T): dL/dB and dL/dc of the RT-tSVD solution at its k, and dL/dc of the
+    Tikhonov-tGKB solution at its k and mu.  Device time of the forward solve
+    and of the backward calls (L2 flushed before each, CUDA events)."""
+    Xt = torch.from_numpy(P["X_true"]).cuda()
+    c = torch.from_numpy(np.asarray(P["c"], dtype=np.float64)).cuda()
+    reps = max(3, min(a.steps, 10))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms, out = 0.0, None
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / reps, out
+
+    def rt_fwd():
+        return tprod.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                                 eps_rel=cfg.eps_rel, sync=False, keep=True)
+
+    ms_f, (X, _, _, fac) = timed(rt_fwd)
+    G = 2.0 * (X - Xt)
+    ms_b, (dB, dc) = timed(lambda: (tprod.rtsvd_adjoint(fac, G), tprod.sep_grad_c(X, G, c)))
+    rt = {"ms_forward": ms_f, "ms_backward": ms_b, "backward_over_forward": ms_b / ms_f,
+          "norm_dB": float(dB.double().norm()), "norm_dc": float(dc.norm())}
+
+    def tk_fwd():
+        return tprod.tgkt_solve(A, B, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False, keep=True)
+
+    ms_f, (X, _, tfac) = timed(tk_fwd)
+    G = 2.0 * (X - Xt)
+    ms_b, dc = timed(lambda: tprod.tgkt_grad_c(tfac, G, c))
+    tk = {"ms_forward": ms_f, "ms_backward": ms_b, "backward_over_forward": ms_b / ms_f,
+          "norm_dc": float(dc.norm())}
+    return {"loss": "||X - X_true||_F^2", "rtsvd_dB_and_dc": rt, "tgkt_dc": tk,
+            "note": "k (and mu) held at the forward values; dc by the separable-operator identity"}
 
 
 def batched_form(a, cfg, flush, tprod, torch, frames=32):

@@ -696,3 +696,44 @@ def test_tgkt_grad_c_central_differences(tp):
         assert ip["k"] == im["k"] == info["k"]
         fd = (float(np.sum(W * Xp.cpu().numpy())) - float(np.sum(W * Xm.cpu().numpy()))) / (2 * h)
         assert abs(fd - dc @ e) <= 1e-6 * max(abs(fd), np.linalg.norm(dc))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_sep_grad_c_tgkb_p_matches_oracle(tp, dtype):
+    """dL/dc of the tGKB_p solution (every lateral slice with its own k_j)."""
+    N, n, p = 16, 10, 3
+    T, c = synth.blur_factors(N, 1.3, 3, 1.5, n=n)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    g = np.random.default_rng(80)
+    Xt = np.concatenate([synth.lateral(synth.synthetic_image(N, n, 3, 1, g)) for _ in range(p)], axis=2)
+    Bt = O.tprod_bcirc(A, Xt)
+    E = g.standard_normal(Bt.shape)
+    E = 1e-2 * E / np.linalg.norm(E) * np.linalg.norm(Bt)
+    deltas = [float(np.linalg.norm(E[:, :, j])) for j in range(p)]
+    B = Bt + E
+    if dtype == torch.float32:
+        A, B = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+    ref = O.tgkb_p_solve(A, B, deltas, 1.1, 12)
+    X, infos = tp.tgkb_solve(dev(A, dtype), dev(B, dtype), 0.0, 1.1, 12, deltas=deltas)
+    if not all(exact_k_required(o, dtype) for o in ref["per_slice"]):
+        pytest.skip("a truncation index inside the rounding band")
+    assert [i["k"] for i in infos] == ref["k"]
+    W = rnd((n, N, p), 81)
+    dc = tp.sep_grad_c(X, dev(W, dtype), dev(c, torch.float64)).cpu().numpy()
+    assert rel(dc, O.grad_c_separable(ref["X"], W, c)) <= (1e-8 if dtype == torch.float64 else 5e-3)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 64])
+def test_sep_grad_c_ttsvd_tube_lengths(tp, n):
+    """dL/dc of the T-tSVD solution for short tubes (one slice; the Nyquist
+    slice present or absent) and a longer one, float64."""
+    N = 12
+    T, c, A, B, delta = separable_problem(N, n, 90 + n)
+    ref = O.ttsvd_solve(A, B, delta, 1.1)
+    X, info = tp.ttsvd_solve(dev(A, torch.float64), dev(B, torch.float64), delta, 1.1)
+    if not exact_k_required(ref, torch.float64):
+        pytest.skip("truncation index inside the rounding band")
+    assert info["k"] == ref["k"]
+    W = rnd((n, N, 1), 91)
+    dc = tp.sep_grad_c(X, dev(W, torch.float64), dev(c, torch.float64)).cpu().numpy()
+    assert rel(dc, O.grad_c_separable(ref["X"], W, c)) <= 1e-8

@@ -120,3 +120,44 @@ def test_grad_c_fails_for_a_non_separable_operator():
                                                     k_fixed=t["k"])["X"]))
     fd = (fwd(c + h * e) - fwd(c - h * e)) / (2 * h)
     assert abs(fd - grad @ e) > 1e-3 * abs(fd)
+
+
+def test_grad_c_tgkb_p_central_differences():
+    """tGKB_p: every lateral slice has its own Krylov space and k_j, and each
+    is a separable solve, so the same formula holds for all p at once."""
+    N, n, p = 10, 6, 3
+    T, c = synth.blur_factors(N, 1.3, 3, 1.5, n=n)
+    g = np.random.default_rng(21)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    Xt = np.concatenate([synth.lateral(synth.synthetic_image(N, n, 3, 1, g)) for _ in range(p)], axis=2)
+    Bt = O.tprod_bcirc(A, Xt)
+    E = g.standard_normal(Bt.shape)
+    E = 1e-2 * E / np.linalg.norm(E) * np.linalg.norm(Bt)
+    deltas = [float(np.linalg.norm(E[:, :, j])) for j in range(p)]
+    B = Bt + E
+    out = O.tgkb_p_solve(A, B, deltas, 1.1, 8)
+    W = g.standard_normal((n, N, p))
+
+    def loss(cc):
+        o = O.tgkb_p_solve(synth.blur_tensor(T, cc, dtype=np.float64), B, deltas, 1.1, 8)
+        assert o["k"] == out["k"]
+        return float(np.sum(W * o["X"]))
+
+    fd_check(loss, c, O.grad_c_separable(out["X"], W, c), 22)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_grad_c_short_tubes(n):
+    """n = 1 (one slice, dL/dc = -gamma_0 / c), n = 2 and 3 (the Nyquist slice
+    and its absence) against central differences of the T-tSVD."""
+    N = 8
+    T, c, B, delta, Xt = separable(N, n, 23 + n)
+    A = synth.blur_tensor(T, c, dtype=np.float64)
+    t = O.ttsvd_solve(A, B, delta, 1.1)
+    W = np.random.default_rng(24).standard_normal((n, N, 1))
+    fwd = lambda cc: float(np.sum(W * O.ttsvd_solve(synth.blur_tensor(T, cc, dtype=np.float64), B, delta, 1.1,
+                                                    k_fixed=t["k"])["X"]))
+    grad = O.grad_c_separable(t["X"], W, c)
+    fd_check(fwd, c, grad, 25, count=4)
+    if n == 1:
+        assert np.isclose(grad[0], -np.sum(W * t["X"]) / c[0], rtol=1e-12)
