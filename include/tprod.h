@@ -334,6 +334,14 @@ tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n,
  *   X, G : real (n, m, p);  m, p <= 4096.
  * Workspace: sep_grad_c_workspace_bytes(m, n, p, prec) (0: invalid sizes).
  */
+/* sep_operator: forms the separable operator A(:,:,k) = c_k T on the device
+ * (the product in float64, rounded once to the working precision), for
+ * callers that differentiate in c.
+ *   T : real (l, m)      c : device float64 (n)      A : real (n, l, m)
+ * No workspace.
+ */
+tp_status sep_operator(const void* T, const double* c, int l, int m, int n, void* A, int prec, void* stream);
+
 size_t sep_grad_c_workspace_bytes(int m, int n, int p, int prec);
 tp_status sep_grad_c(const void* X, const void* G, const double* c, int m, int n, int p, double* dc, int prec,
                      void* ws, size_t ws_bytes, void* stream);

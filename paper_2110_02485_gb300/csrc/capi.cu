@@ -307,6 +307,13 @@ tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n,
     return TP_ERR_ARG;
 }
 
+tp_status sep_operator(const void* T, const double* c, int l, int m, int n, void* A, int prec, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32) return sep_operator<float>((const float*)T, c, l, m, n, (float*)A, st);
+    if (prec == TP_FP64) return sep_operator<double>((const double*)T, c, l, m, n, (double*)A, st);
+    return TP_ERR_ARG;
+}
+
 size_t sep_grad_c_workspace_bytes(int m, int n, int p, int prec) {
     if (prec == TP_FP32) return sep_ws_bytes<float>(m, n, p);
     if (prec == TP_FP64) return sep_ws_bytes<double>(m, n, p);

@@ -13,6 +13,8 @@
 // n - s contribute complex conjugates).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -96,6 +98,29 @@ tp_status grad_c(const double* c, int n, const double2* gamma, const double* add
     k_grad_c<<<1, 256, smem, st>>>(c, n, gamma, add, dc);
     return launched(TP_KC_MISC, st);
 }
+
+// A(:,:,k) = c_k T, the product formed in float64 and rounded once.
+template <typename T>
+__global__ void k_sep_operator(const T* Tm, const double* c, long lm, int n, T* A) {
+    const long total = (long)n * lm;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long k = e / lm, ij = e - k * lm;
+        A[e] = (T)(c[k] * (double)Tm[ij]);
+    }
+}
+
+template <typename T>
+tp_status sep_operator(const T* Tm, const double* c, int l, int m, int n, T* A, cudaStream_t st) {
+    if (!Tm || !c || !A || l < 1 || m < 1 || n < 1) return TP_ERR_ARG;
+    const long total = (long)n * l * m;
+    const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+    prof_begin(TP_KC_MISC, st);
+    k_sep_operator<T><<<blocks, 256, 0, st>>>(Tm, c, (long)l * m, n, A);
+    return launched(TP_KC_MISC, st);
+}
+
+template tp_status sep_operator<float>(const float*, const double*, int, int, int, float*, cudaStream_t);
+template tp_status sep_operator<double>(const double*, const double*, int, int, int, double*, cudaStream_t);
 
 template tp_status sep_gamma<float>(const void*, const void*, int, long, double2*, cudaStream_t);
 template tp_status sep_gamma<double>(const void*, const void*, int, long, double2*, cudaStream_t);

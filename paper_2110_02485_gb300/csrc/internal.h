@@ -148,6 +148,8 @@ template <typename T> size_t sep_ws_bytes(int m, int n, int p);
 template <typename T>
 tp_status sep_grad(const T* X, const T* G, const double* c, int m, int n, int p, double* dc, void* ws,
                    size_t ws_bytes, cudaStream_t st);
+template <typename T>
+tp_status sep_operator(const T* Tm, const double* c, int l, int m, int n, T* A, cudaStream_t st);
 template <typename T> size_t tik_grad_ws_bytes(int l, int m, int n, const tp_tik_params* P);
 template <typename T>
 tp_status tik_grad_c(const T* G, const double* c, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,

@@ -53,7 +53,7 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
            "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve", "tgkb_triplets_workspace_bytes",
            "tgkb_triplets", "sep_grad_c_workspace_bytes", "sep_grad_c", "tgkb_tikhonov_grad_c_workspace_bytes",
-           "tgkb_tikhonov_grad_c")
+           "tgkb_tikhonov_grad_c", "sep_operator")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -109,6 +109,7 @@ def load(path: str | None = None):
     L.tp_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), i]
     L.tp_timing_read.restype = i
     L.tprod_gemm_noalloc.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]
+    L.sep_operator.argtypes = [vp, vp, i, i, i, vp, i, vp]
     L.sep_grad_c_workspace_bytes.argtypes = [i, i, i, i]
     L.sep_grad_c_workspace_bytes.restype = sz
     L.sep_grad_c.argtypes = [vp, vp, vp, i, i, i, vp, i, vp, sz, vp]
@@ -116,7 +117,7 @@ def load(path: str | None = None):
     L.tgkb_tikhonov_grad_c_workspace_bytes.restype = sz
     L.tgkb_tikhonov_grad_c.argtypes = [vp, vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, i, vp, sz, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
-              "tgkb_tikhonov_solve", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c"):
+              "tgkb_tikhonov_solve", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -530,6 +531,75 @@ class TgktFactor:
         self.ws, self.P = ws, P
         self.l, self.m, self.n = l, m, n
         self.prec, self.device, self.dtype = prec, device, dtype
+
+
+def sep_operator(T: torch.Tensor, c: torch.Tensor) -> torch.Tensor:
+    """A(:,:,k) = c_k T, formed on the device: T (l, m) in the working
+    precision, c float64 (n,).  Returns A (n, l, m)."""
+    _dev(T, c)
+    if T.dim() != 2 or c.dim() != 1 or c.dtype != torch.float64:
+        raise ValueError("T must be (l, m) and c a float64 vector")
+    l, m = T.shape
+    n = c.shape[0]
+    A = torch.empty((n, l, m), dtype=T.dtype, device=T.device)
+    _check("sep_operator", load().sep_operator(_ptr(T), _ptr(c), l, m, n, _ptr(A), _prec(T), _stream()))
+    return A
+
+
+class SepRtsvdSolve(torch.autograd.Function):
+    """X_k = RT-tSVD solution for the separable operator A(:,:,k) = c_k T,
+    differentiable in B (rtsvd_adjoint) and in c (sep_grad_c), with k and the
+    sketch rank held at the values the solve chose."""
+
+    @staticmethod
+    def forward(ctx, B, c, T, Omega, kw):
+        A = sep_operator(T, c.detach())
+        X, _, _, fac = rtsvd_solve(A, B, Omega, sync=False, keep=True, **kw)
+        ctx.fac = fac
+        ctx.save_for_backward(X, c)
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        if ctx.needs_input_grad[2]:
+            raise NotImplementedError("dL/dT is not provided")
+        X, c = ctx.saved_tensors
+        G = G.contiguous()
+        dB = rtsvd_adjoint(ctx.fac, G) if ctx.needs_input_grad[0] else None
+        dc = sep_grad_c(X, G, c.detach().contiguous()) if ctx.needs_input_grad[1] else None
+        return dB, dc, None, None, None
+
+
+def rtsvd_solve_sep_ad(c, T, B, Omega, delta, tau, p_over, **kw):
+    """Differentiable (in B and c) RT-tSVD solve for A(:,:,k) = c_k T: returns X."""
+    return SepRtsvdSolve.apply(B, c, T, Omega, dict(delta=delta, tau=tau, p_over=p_over, **kw))
+
+
+class SepTgktSolve(torch.autograd.Function):
+    """Tikhonov-tGKB solution for A(:,:,k) = c_k T, differentiable in c
+    (tgkt_grad_c) with k and mu held at the values the solve chose.  dL/dB is
+    not provided: the Krylov space depends on B."""
+
+    @staticmethod
+    def forward(ctx, B, c, T, kw):
+        A = sep_operator(T, c.detach())
+        X, _, fac = tgkt_solve(A, B, sync=False, keep=True, **kw)
+        ctx.fac = fac
+        ctx.save_for_backward(c)
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        if ctx.needs_input_grad[0] or ctx.needs_input_grad[2]:
+            raise NotImplementedError("only dL/dc is provided for the Tikhonov-tGKB solution")
+        (c,) = ctx.saved_tensors
+        return None, tgkt_grad_c(ctx.fac, G.contiguous(), c.detach().contiguous()), None, None
+
+
+def tgkt_solve_sep_ad(c, T, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12):
+    """Differentiable (in c) Tikhonov-tGKB solve for A(:,:,k) = c_k T: returns X."""
+    return SepTgktSolve.apply(B, c, T, dict(delta=delta, tau=tau, k_max=k_max, mu_lo=mu_lo, mu_hi=mu_hi,
+                                            log_tol=log_tol))
 
 
 def sep_grad_c(X: torch.Tensor, G: torch.Tensor, c: torch.Tensor) -> torch.Tensor:

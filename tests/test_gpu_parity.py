@@ -737,3 +737,43 @@ def test_sep_grad_c_ttsvd_tube_lengths(tp, n):
     W = rnd((n, N, 1), 91)
     dc = tp.sep_grad_c(X, dev(W, torch.float64), dev(c, torch.float64)).cpu().numpy()
     assert rel(dc, O.grad_c_separable(ref["X"], W, c)) <= 1e-8
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_sep_operator_is_the_blur_tensor(tp, dtype):
+    """A(:,:,k) = c_k T with the product in float64 and one rounding: the
+    generator's tensor for the T the device holds."""
+    T, c = synth.blur_factors(20, 1.3, 3, 1.5, n=9)
+    Td = dev(T, dtype)
+    A = tp.sep_operator(Td, dev(c, torch.float64)).cpu().numpy()
+    assert np.array_equal(A, synth.blur_tensor(Td.cpu().double().numpy(), c, dtype=A.dtype))
+
+
+def test_sep_rtsvd_autograd_gradcheck(tp):
+    """torch.autograd.gradcheck of the RT-tSVD solve in B and c together
+    (float64; k = 6 and r = 8 < 10 stay fixed under the perturbations)."""
+    T, c, A, B, delta = separable_problem(10, 6, 101)
+    Om = dev(rnd((6, 10, 10), 102), torch.float64)
+    Td = dev(T, torch.float64)
+    Bd = dev(B, torch.float64).requires_grad_()
+    cd = dev(c, torch.float64).requires_grad_()
+    f = lambda Bx, cx: tp.rtsvd_solve_sep_ad(cx, Td, Bx, Om, delta, 1.1, 3, block=4, q_power=1, r_max=10,
+                                             eps_rel=0.01)
+    assert torch.autograd.gradcheck(f, (Bd, cd), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def test_sep_tgkt_autograd_gradcheck(tp):
+    """gradcheck of the Tikhonov-tGKB solve in c at a fixed mu (the search
+    interval ends below the discrepancy root, so mu = mu_hi); asking for dL/dB
+    raises."""
+    T, c, A, B, delta = separable_problem(10, 6, 101)
+    Td = dev(T, torch.float64)
+    Bd = dev(B, torch.float64)
+    _, free = tp.tgkt_solve(dev(A, torch.float64), Bd, delta, 1.1, 10, 1e-3, 1e9)
+    mu0 = free["mu"] / 20.0
+    cd = dev(c, torch.float64).requires_grad_()
+    f = lambda cx: tp.tgkt_solve_sep_ad(cx, Td, Bd, delta, 1.1, 10, mu0 / 4.0, mu0)
+    assert torch.autograd.gradcheck(f, (cd,), eps=1e-6, atol=1e-7, rtol=1e-5)
+    X = tp.tgkt_solve_sep_ad(cd.detach(), Td, Bd.clone().requires_grad_(), delta, 1.1, 10, mu0 / 4.0, mu0)
+    with pytest.raises((NotImplementedError, RuntimeError), match="only dL/dc"):
+        X.sum().backward()
