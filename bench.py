@@ -89,6 +89,29 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms, world, device):
+    """The job's time: the slowest rank's (all-reduce MAX over the process
+    group); the rank's own time when it runs alone."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, ms):
+    """Solves per second of the whole job: every rank solves its own problem
+    each step, and the job takes the slowest rank's time."""
+    return world * SOLVES_PER_STEP * steps / (ms / 1e3)
+
+
+def replica_seed(cfg, rank):
+    """Each rank's independent problem (weak scaling, no data-path collective)."""
+    return cfg.seed + rank
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -190,7 +213,7 @@ def run_ours(a, rank, world, local):
     build.build()
     tprod.load()
     cfg = synth.CONFIGS[a.config]
-    P = synth.blur_problem(cfg, seed=cfg.seed + rank)
+    P = synth.blur_problem(cfg, seed=replica_seed(cfg, rank))
     dev = lambda x: torch.from_numpy(x).cuda()
     A, B, Om = dev(P["A"]), dev(P["B"]), dev(P["Omega"])
     delta = P["delta"]
@@ -258,12 +281,8 @@ def run_ours(a, rank, world, local):
     tprod.timing_enable([])
     clk = clocks.stop()
     launches = graph.launches * a.steps if graph else tprod.kernel_launches() - launches0
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * SOLVES_PER_STEP * a.steps / (ms / 1e3)
+    ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in evs), world, "cuda")
+    value = job_throughput(world, a.steps, ms)
 
     # end to end through the public API: pinned host inputs in, solutions out.
     # Two sets of device inputs: the copy of step i+1's inputs (a second
@@ -317,11 +336,8 @@ def run_ours(a, rank, world, local):
         e1.record(comp)
         torch.cuda.synchronize()
         ms2 = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms2], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms2 = float(t.item())
-        e2e = {"value": world * SOLVES_PER_STEP * a.steps / (ms2 / 1e3), "unit": UNIT,
+        ms2 = max_over_ranks(ms2, world, "cuda")
+        e2e = {"value": job_throughput(world, a.steps, ms2), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "pipeline": "two input sets; the H2D copy of step i+1 overlaps step i; one event pair around the "
                            "K steps (flushes included)"}
