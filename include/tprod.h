@@ -214,6 +214,18 @@ tp_status ttsvd_solve(const void* A, const void* B, int l, int m, int n, int p,
                       const tp_ttsvd_params* params, void* X, tp_info* d_info, int prec,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* ttsvd_adjoint: the adjoint of the map B -> X_s of the last ttsvd_solve made
+ * with this workspace and the same (l, m, n, p, params, prec).  With s held
+ * at the value that solve chose, X_s is linear in B and for G = dL/dX_s
+ *   dL/dB = U_s * S_s^{-1} * V_s^T * G
+ * (as rtsvd_adjoint, on the factorisation the solve left in the workspace).
+ *   G : real (n, m, p)      dB : real (n, l, p)
+ * The workspace must be untouched since that solve; the call can be repeated.
+ * The paper has no counterpart; it is a service for gradient-based use.
+ */
+tp_status ttsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_ttsvd_params* params, void* dB, int prec,
+                        void* ws, size_t ws_bytes, void* stream);
+
 /* -------------------------------------------------------------- tGKB ------
  * tgkb_solve: the tGKB method (Algorithm 4 with both reorthogonalisation
  * steps done as two classical Gram-Schmidt passes).  After step i the

@@ -93,6 +93,19 @@ def ttsvd_solve(A, B, delta, tau, k_fixed=None):
                 margin=_margin(res, k, td), S=S)
 
 
+def ttsvd_adjoint(A, out: dict, G: np.ndarray) -> np.ndarray:
+    """Adjoint of the linear map B -> X_s of a ttsvd_solve result at its s:
+    X_s = V_s S_s^{-1} U_s^T * B (Eq. (14)), so dL/dB = U_s S_s^{-1} V_s^T * G,
+    slice by slice from the full tSVD of A; singular values the solve dropped
+    (_inv_sigma) are dropped here too."""
+    n, l, m = A.shape
+    k = out["k"]
+    U, S, V = tsvd_hat(fft3(A))
+    inv = _inv_sigma(S, max(l, m))[:, :k]
+    t = _ct(V[:, :, :k]) @ fft3(G)
+    return ifft3_real(U[:, :, :k] @ (inv[:, :, None] * t))
+
+
 # --------------------------------------------------------------------------
 # R-tSVD, Algorithm 3 exactly as printed (one Gaussian slice per step).
 # --------------------------------------------------------------------------

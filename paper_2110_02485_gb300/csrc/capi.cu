@@ -84,6 +84,8 @@ template <typename T>
 tp_status rt_adjoint(const T*, int, int, int, int, const tp_rtsvd_params*, T*, void*, size_t, cudaStream_t);
 template <typename T> size_t tt_ws_bytes(int, int, int, int, const tp_ttsvd_params*);
 template <typename T>
+tp_status tt_adjoint(const T*, int, int, int, int, const tp_ttsvd_params*, T*, void*, size_t, cudaStream_t);
+template <typename T>
 tp_status tt_solve(const T*, const T*, int, int, int, int, const tp_ttsvd_params*, T*, tp_info*, void*, size_t,
                    cudaStream_t);
 template <typename T> size_t gk_ws_bytes(int, int, int, int, const tp_tgkb_params*);
@@ -214,6 +216,15 @@ tp_status rtsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_rtsv
     if (prec == TP_FP32 || prec == TP_TF32)
         return rt_adjoint<float>((const float*)G, l, m, n, p, params, (float*)dB, ws, ws_bytes, st);
     if (prec == TP_FP64) return rt_adjoint<double>((const double*)G, l, m, n, p, params, (double*)dB, ws, ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
+tp_status ttsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_ttsvd_params* params, void* dB, int prec,
+                        void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32) return tt_adjoint<float>((const float*)G, l, m, n, p, params, (float*)dB, ws, ws_bytes, st);
+    if (prec == TP_FP64)
+        return tt_adjoint<double>((const double*)G, l, m, n, p, params, (double*)dB, ws, ws_bytes, st);
     return TP_ERR_ARG;
 }
 

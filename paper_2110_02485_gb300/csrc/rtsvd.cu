@@ -1284,9 +1284,9 @@ tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int
 //   dB-hat = Q Q^H K_k S_k^{-2} V_k^H G-hat
 // (U-tilde_k = B-tilde V_k S_k^{-1} = Q^H K_k S_k^{-1}).
 template <typename T>
-tp_status rt_adjoint(const T* G, int l, int m, int n, int p, const tp_rtsvd_params* P, T* dB, void* ws,
-                     size_t ws_bytes, cudaStream_t st) {
-    TRY(rt_check<T>(l, m, n, p, P));
+static tp_status rt_adjoint_impl(const T* G, int l, int m, int n, int p, const tp_rtsvd_params* P, T* dB, void* ws,
+                                 size_t ws_bytes, cudaStream_t st, bool full) {
+    TRY(rt_check<T>(l, m, n, p, P, full));
     if (!G || !dB) return TP_ERR_ARG;
     const int r_max = P->r_max, h = n / 2 + 1;
     RtWs<T> w = rt_carve<T>(ws, l, m, n, P->block, r_max, p);
@@ -1309,6 +1309,12 @@ tp_status rt_adjoint(const T* G, int l, int m, int n, int p, const tp_rtsvd_para
     TRY(cgemm<T>(h, l, p, r_max, 0, 0, dr, 1, 0, w.Q, l, (long)r_max * l, OP_T, w.d, p, rp, OP_N, 0, 0, w.Bhat, p,
                  (long)l * p, nullptr, st));
     return irdft<T>(w.Bhat, dB, n, l, p, p, (long)l * p, nullptr, st);
+}
+
+template <typename T>
+tp_status rt_adjoint(const T* G, int l, int m, int n, int p, const tp_rtsvd_params* P, T* dB, void* ws,
+                     size_t ws_bytes, cudaStream_t st) {
+    return rt_adjoint_impl<T>(G, l, m, n, p, P, dB, ws, ws_bytes, st, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -1369,6 +1375,24 @@ tp_status tt_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_
     return rt_solve_impl<T>(A, B, Om, l, m, n, p, &R, X, info, ws, rb, st, 3, true);
 }
 
+// Adjoint of B -> X_s of the last tt_solve made with ws: the RT-tSVD adjoint
+// on the factorisation the solve left in the workspace's RT-tSVD part
+// (X_s = V_s S_s^{-1} U_s^T * B, Eq. (14), is linear in B at the chosen s).
+template <typename T>
+tp_status tt_adjoint(const T* G, int l, int m, int n, int p, const tp_ttsvd_params* P, T* dB, void* ws,
+                     size_t ws_bytes, cudaStream_t st) {
+    if (!P) return TP_ERR_ARG;
+    const tp_rtsvd_params R = tt_params<T>(l, m, P);
+    TRY(rt_check<T>(l, m, n, p, &R, true));
+    const size_t rb = align256(rt_carve<T>(nullptr, l, m, n, R.block, R.r_max, p).bytes);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < rb) return TP_ERR_WORKSPACE;
+    return rt_adjoint_impl<T>(G, l, m, n, p, &R, dB, ws, rb, st, true);
+}
+
+template tp_status tt_adjoint<float>(const float*, int, int, int, int, const tp_ttsvd_params*, float*, void*, size_t,
+                                     cudaStream_t);
+template tp_status tt_adjoint<double>(const double*, int, int, int, int, const tp_ttsvd_params*, double*, void*,
+                                      size_t, cudaStream_t);
 template size_t tt_ws_bytes<float>(int, int, int, int, const tp_ttsvd_params*);
 template size_t tt_ws_bytes<double>(int, int, int, int, const tp_ttsvd_params*);
 template tp_status tt_solve<float>(const float*, const float*, int, int, int, int, const tp_ttsvd_params*, float*,

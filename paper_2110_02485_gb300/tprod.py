@@ -53,7 +53,7 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
            "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve", "tgkb_triplets_workspace_bytes",
            "tgkb_triplets", "sep_grad_c_workspace_bytes", "sep_grad_c", "tgkb_tikhonov_grad_c_workspace_bytes",
-           "tgkb_tikhonov_grad_c", "sep_operator")
+           "tgkb_tikhonov_grad_c", "sep_operator", "ttsvd_adjoint")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -110,6 +110,7 @@ def load(path: str | None = None):
     L.tp_timing_read.restype = i
     L.tprod_gemm_noalloc.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]
     L.sep_operator.argtypes = [vp, vp, i, i, i, vp, i, vp]
+    L.ttsvd_adjoint.argtypes = [vp, i, i, i, i, ctypes.POINTER(TtsvdParams), vp, i, vp, sz, vp]
     L.sep_grad_c_workspace_bytes.argtypes = [i, i, i, i]
     L.sep_grad_c_workspace_bytes.restype = sz
     L.sep_grad_c.argtypes = [vp, vp, vp, i, i, i, vp, i, vp, sz, vp]
@@ -117,7 +118,8 @@ def load(path: str | None = None):
     L.tgkb_tikhonov_grad_c_workspace_bytes.restype = sz
     L.tgkb_tikhonov_grad_c.argtypes = [vp, vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, i, vp, sz, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
-              "tgkb_tikhonov_solve", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator"):
+              "tgkb_tikhonov_solve", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator",
+              "ttsvd_adjoint"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -412,8 +414,29 @@ def rtsvd_solve_ad(A, B, Omega, delta, tau, p_over, **kw):
     return RtsvdSolve.apply(B, A, Omega, dict(delta=delta, tau=tau, p_over=p_over, **kw))
 
 
-def ttsvd_solve(A, B, delta, tau, res_hist=False, sync=True):
-    """T-tSVD method (Section 4.1).  Returns (X, info[, res_hist])."""
+class TtsvdFactor:
+    """What ttsvd_solve(..., keep=True) leaves for ttsvd_adjoint."""
+
+    def __init__(self, ws, P, hist, l, m, n, p, prec, device, dtype):
+        self.ws, self.P, self.hist = ws, P, hist
+        self.l, self.m, self.n, self.p = l, m, n, p
+        self.prec, self.device, self.dtype = prec, device, dtype
+
+
+def ttsvd_adjoint(fac: TtsvdFactor, G: torch.Tensor) -> torch.Tensor:
+    """dL/dB = U_s S_s^{-1} V_s^T * G for the T-tSVD solve that made `fac` (s fixed)."""
+    _dev(G)
+    if tuple(G.shape) != (fac.n, fac.m, fac.p) or G.dtype != fac.dtype:
+        raise ValueError("G must match the solution X of the solve")
+    dB = torch.empty((fac.n, fac.l, fac.p), dtype=fac.dtype, device=fac.device)
+    wp, wn = _aligned(fac.ws)
+    _check("ttsvd_adjoint", load().ttsvd_adjoint(_ptr(G), fac.l, fac.m, fac.n, fac.p, ctypes.byref(fac.P), _ptr(dB),
+                                                 fac.prec, wp, wn, _stream()))
+    return dB
+
+
+def ttsvd_solve(A, B, delta, tau, res_hist=False, sync=True, keep=False):
+    """T-tSVD method (Section 4.1).  Returns (X, info[, res_hist][, factor])."""
     _dev(A, B)
     n, l, m = A.shape
     p = B.shape[2]
@@ -430,10 +453,11 @@ def ttsvd_solve(A, B, delta, tau, res_hist=False, sync=True):
     info = _info_buf(A.device)
     _check("ttsvd_solve", L.ttsvd_solve(_ptr(A), _ptr(B), l, m, n, p, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp,
                                         wn, _stream()))
+    fac = (TtsvdFactor(ws, P, hist, l, m, n, p, prec, A.device, A.dtype),) if keep else ()
     if not sync:
-        return X, info, hist
+        return (X, info, hist) + fac
     out = (X, _info_dict(info))
-    return out + ((hist.cpu().numpy(),) if res_hist else ())
+    return out + ((hist.cpu().numpy(),) if res_hist else ()) + fac
 
 
 def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None):

@@ -777,3 +777,22 @@ def test_sep_tgkt_autograd_gradcheck(tp):
     X = tp.tgkt_solve_sep_ad(cd.detach(), Td, Bd.clone().requires_grad_(), delta, 1.1, 10, mu0 / 4.0, mu0)
     with pytest.raises((NotImplementedError, RuntimeError), match="only dL/dc"):
         X.sum().backward()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,p", [(12, 8, 1), (16, 9, 2)])
+def test_ttsvd_adjoint_matches_oracle(tp, dtype, N, n, p):
+    """dL/dB = U_s S_s^{-1} V_s^T * G of the GPU T-tSVD solve against the
+    oracle's, at the same s; repeatable (the factorisation is only read)."""
+    A, B, delta = problem(N, n, seed=50 + p, p=p)
+    ref = O.ttsvd_solve(A.astype(np.float64), B.astype(np.float64), delta, 1.1)
+    X, info, fac = tp.ttsvd_solve(dev(A, dtype), dev(B, dtype), delta, 1.1, keep=True)
+    if not exact_k_required(ref, dtype):
+        pytest.skip("truncation index inside the rounding band")
+    assert info["k"] == ref["k"]
+    G = rnd((n, N, p), 60 + p)
+    dB = tp.ttsvd_adjoint(fac, dev(G, dtype)).cpu().numpy()
+    want = O.ttsvd_adjoint(A.astype(np.float64), ref, dev(G, dtype).cpu().double().numpy())
+    assert dB.shape == (n, N, p)
+    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 2e-3)
+    assert np.array_equal(dB, tp.ttsvd_adjoint(fac, dev(G, dtype)).cpu().numpy())

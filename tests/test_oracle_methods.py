@@ -181,6 +181,26 @@ def test_rtsvd_adjoint_satisfies_the_adjoint_identity():
     assert np.allclose(adj[:, :, 1:2], one, rtol=0, atol=1e-12 * np.abs(one).max())
 
 
+def test_ttsvd_adjoint_satisfies_the_adjoint_identity():
+    """<G, X_s(E)> = <adjoint(G), E> with X_s(E) from ttsvd_solve itself at
+    the chosen s, and at full rank the adjoint of B -> A^{-1} * B is
+    A^{-T} * G (the t-transpose of the inverse)."""
+    A, B, delta = small_blur_multi(p=2)
+    n, l, m = A.shape
+    out = O.ttsvd_solve(A, B, delta, 1.1)
+    g = np.random.default_rng(78)
+    for _ in range(3):
+        E = g.standard_normal((n, l, 2))
+        G = g.standard_normal((n, m, 2))
+        XE = O.ttsvd_solve(A, E, delta, 1.1, k_fixed=out["k"])["X"]
+        assert np.isclose(np.sum(G * XE), np.sum(O.ttsvd_adjoint(A, out, G) * E), rtol=1e-10)
+    full = dict(out, k=min(l, m))
+    G = g.standard_normal((n, m, 1))
+    Ainv = O.ifft3_real(np.linalg.inv(O.fft3(A)))
+    want = O.tprod_bcirc(O.ttranspose(Ainv), G)
+    assert np.allclose(O.ttsvd_adjoint(A, full, G), want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+
 def test_ttsvd_discrepancy_bracket_with_brute_force_residual():
     A, B, delta = small_blur()
     tau = 1.1
