@@ -60,6 +60,14 @@ def test_product_path_has_no_cpu_fallback():
     from paper_2110_02485_gb300 import tprod
     with pytest.raises(TypeError):
         tprod.fft(torch.zeros(4, 3, 3))
+    X = torch.zeros(4, 3, 1)
+    c = torch.ones(4, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        tprod.sep_grad_c(X, X, c)
+    with pytest.raises(TypeError):
+        tprod.sep_operator(torch.zeros(3, 3), c)
+    with pytest.raises(TypeError):
+        tprod.rtsvd_solve(torch.zeros(4, 3, 3), X, torch.zeros(4, 3, 3), 1.0, 1.1, 1, r_max=3, eps_rel=0.1)
 
 
 def test_rtsvd_lateral_slice_limits(lib):
