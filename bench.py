@@ -46,10 +46,10 @@ NCU_TRAFFIC = {
             "sha256": "e5b60671570d3ef0b36e00a53d70932906826c31e0a86789484f58848fcfa887",
             "profile": "profiles/k_gkb_n256.md"},
     "orth": {"bytes": 7.51e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
-             "sha256": "feeb15bdaf81e95a14cbfa0d5a591dc312caa9173344d7c5342b4d608a6ec9c0",
+             "sha256": "47fa331650bf1c81124819a99904104b53b31327888072e3033922ea1a00b465",
              "profile": "profiles/k_orth_n256.md"},
     "svd": {"bytes": 9.69e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
-            "sha256": "feeb15bdaf81e95a14cbfa0d5a591dc312caa9173344d7c5342b4d608a6ec9c0",
+            "sha256": "47fa331650bf1c81124819a99904104b53b31327888072e3033922ea1a00b465",
             "profile": "profiles/k_jacobi_n256.md"},
 }
 
