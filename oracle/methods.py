@@ -54,10 +54,14 @@ def _dp_pick(res: dict, tau_delta: float, k_lo: int, k_hi: int):
 
 
 def _margin(res: dict, k: int, tau_delta: float) -> float:
-    """Relative distance of the DP test from a tie at the chosen k and at k-1."""
+    """Relative distance of the DP test from a tie at the chosen k and at k-1.
+    With delta = 0 the bound tau*delta is 0: residuals are compared with 0
+    exactly, so the margin is infinite unless a residual is exactly 0."""
     vals = [abs(res[k] - tau_delta)]
     if (k - 1) in res:
         vals.append(abs(res[k - 1] - tau_delta))
+    if tau_delta == 0.0:
+        return float("inf") if min(vals) > 0.0 else 0.0
     return float(min(vals) / tau_delta)
 
 

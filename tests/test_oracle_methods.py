@@ -474,3 +474,41 @@ def test_small_workload_end_to_end():
         assert out["status"] == O.STATUS_OK
         assert err(out["X"]) < 0.3
     assert g["k"] < t["k"]                  # tGKB needs fewer steps than T-tSVD's k (Section 5)
+
+
+def test_zero_right_hand_side_gives_the_zero_solution():
+    """B = 0: Normalize breaks down on every slice (zero vector substitute),
+    the residual is 0 at the first admissible k, and X = 0 exactly."""
+    A, B, delta = small_blur()
+    n, l, m = A.shape
+    Z = np.zeros_like(B)
+    Om = rnd((n, m, m), 30)
+    eps = 0.02 * np.sqrt(O.fro2(A))
+    g = O.tgkb_solve(A, Z, delta, 1.1, 6)
+    r = O.rtsvd_solve(A, Z, Om, delta, 1.1, eps, 3, 2, 1, r_max=m)
+    t = O.ttsvd_solve(A, Z, delta, 1.1)
+    k = O.tgkt_solve(A, Z, delta, 1.1, 6, 1e-3, 1e5)
+    assert (g["k"], t["k"], k["k"]) == (1, 1, 1) and r["k"] == max(1, r["r"] - 3)
+    for o in (g, r, t, k):
+        assert o["status"] == O.STATUS_OK
+        assert not np.any(o["X"])
+
+
+def test_zero_delta_runs_to_the_cap():
+    """delta = 0: the discrepancy bound is 0, so the iterative methods stop at
+    their caps with NOT_CONVERGED, while the T-tSVD reaches full rank, where
+    the residual of a square nonsingular A is exactly 0 (captured energy
+    clamped at ||B||^2)."""
+    A, B, delta = small_blur()
+    n, l, m = A.shape
+    Om = rnd((n, m, m), 31)
+    eps = 0.02 * np.sqrt(O.fro2(A))
+    g = O.tgkb_solve(A, B, 0.0, 1.1, 6)
+    r = O.rtsvd_solve(A, B, Om, 0.0, 1.1, eps, 3, 2, 1, r_max=m)
+    k = O.tgkt_solve(A, B, 0.0, 1.1, 6, 1e-3, 1e5)
+    t = O.ttsvd_solve(A, B, 0.0, 1.1)
+    assert g["k"] == 6 and g["status"] == O.STATUS_NOT_CONVERGED
+    assert r["k"] == r["r"] and r["status"] == O.STATUS_NOT_CONVERGED
+    assert k["status"] == O.STATUS_NOT_CONVERGED and k["mu"] == 1e5
+    assert t["k"] == min(l, m) and t["status"] == O.STATUS_OK
+    assert np.isclose(np.sqrt(O.fro2(B - O.tprod(A, t["X"]))), 0.0, atol=1e-10 * np.sqrt(O.fro2(B)))
