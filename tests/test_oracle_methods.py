@@ -470,10 +470,15 @@ def test_small_workload_end_to_end():
     r = O.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.eps_rel * P["norm_A"], cfg.p_over,
                       cfg.block, cfg.q_power, cfg.r_max)
     g = O.tgkb_solve(A, B, P["delta"], cfg.tau, cfg.k_max)
-    for out in (t, r, g):
+    tk = O.tgkt_solve(A, B, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)
+    for out in (t, r, g, tk):
         assert out["status"] == O.STATUS_OK
         assert err(out["X"]) < 0.3
-    assert g["k"] < t["k"]                  # tGKB needs fewer steps than T-tSVD's k (Section 5)
+    # the qualitative findings of Section 5's tables on this synthetic workload
+    assert g["k"] < t["k"]                  # tGKB needs fewer steps than T-tSVD's k
+    assert r["k"] == r["r"] - cfg.p_over    # RT-tSVD stops at k_init = r - rho (Eq. (kinit))
+    assert abs(err(r["X"]) - err(t["X"])) < 0.01 * err(t["X"])   # RT-tSVD as accurate as T-tSVD
+    assert err(tk["X"]) <= err(g["X"])      # the Tikhonov variant at least as accurate as tGKB
 
 
 def test_zero_right_hand_side_gives_the_zero_solution():
