@@ -7,7 +7,11 @@
  *   - the RT-tSVD method (Algorithm 3, Section 4.2, Eq. (kinit)),
  *   - the tGKB method (Algorithm 4, Eqs. (t-gkb), (9tt), (solgkb)),
  *   - Tikhonov regularisation of the tGKB-projected problem (tGKT, Section 5),
- * each with the discrepancy principle of Eq. (disp).
+ *   - the T-tSVD method (Section 4.1), tGKB_p and nested_tGKB_p (Algorithm 6),
+ *     and the t-singular triplets of k tGKB steps (Section 4.3),
+ * each with the discrepancy principle of Eq. (disp); and, with no counterpart
+ * in the paper, gradients: the t-product's adjoint, dL/dB of the truncated
+ * solutions, and dL/dc in the tube weights of a separable operator.
  *
  * Layouts (all row-major, all pointers DEVICE pointers owned by the caller):
  *   real tensor  l x m x n   : array (n, l, m); element (i,j,k) at [k*l*m + i*m + j]
