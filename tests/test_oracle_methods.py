@@ -258,6 +258,35 @@ def test_tgkb_solution_is_the_krylov_least_squares_solution(k):
     assert np.allclose(out["X"], spatial(Xh), atol=1e-8 * np.abs(out["X"]).max())
 
 
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_tgkb_solution_is_the_cgls_iterate(k):
+    """Per Fourier slice, X_k is the k-th iterate of textbook CGLS on
+    (A-hat_s, b-hat_s) from x = 0 (the same Krylov least-squares problem,
+    reached by a different recurrence: short-term, no reorthogonalisation)."""
+    A, B, delta = small_blur(N=9, n=5, general=0.3)
+    out = O.tgkb_solve(A, B, delta, 1.1, 50, k_fixed=k)
+    Ah, Bh = O.fft3(A), O.fft3(B)
+    Xh = np.zeros((A.shape[0], A.shape[2], 1), complex)
+    for s in range(A.shape[0]):
+        M, b = Ah[s], Bh[s, :, 0]
+        x = np.zeros(M.shape[1], complex)
+        r = b.copy()
+        g = M.conj().T @ r
+        d = g.copy()
+        gg = np.vdot(g, g).real
+        for _ in range(k):
+            q = M @ d
+            alpha = gg / np.vdot(q, q).real
+            x = x + alpha * d
+            r = r - alpha * q
+            g = M.conj().T @ r
+            gg_new = np.vdot(g, g).real
+            d = g + (gg_new / gg) * d
+            gg = gg_new
+        Xh[s, :, 0] = x
+    assert np.allclose(out["X"], spatial(Xh), atol=1e-8 * np.abs(out["X"]).max())
+
+
 def test_tgkb_full_space_solves_the_system():
     n, m = 4, 5
     A = rnd((n, m, m), 10) + 3 * O.tidentity(m, n)
