@@ -123,7 +123,9 @@ tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m
  * every GPU that loads the library until the process exits.  A problem whose
  * three spectra need more than that returns TP_ERR_WORKSPACE and enqueues
  * nothing; the need is align256(h*l*kk*c) + align256(h*kk*m*c) +
- * align256(h*l*m*c) bytes, h = n/2+1, c = 8 (FP32) or 16 (FP64).
+ * align256(h*l*m*c) bytes, h = n/2+1, c = 8 (FP32) or 16 (FP64).  Sizes
+ * that tprod_gemm refuses (an operand of 2^40 elements or more, l above
+ * 65535*128) return TP_ERR_ARG, also before anything is enqueued.
  * The first call on each device looks up the array's device address (with
  * that device current); make it before any stream capture.  Calls share the
  * array, so calls that overlap on the GPU race; nothing needs clearing

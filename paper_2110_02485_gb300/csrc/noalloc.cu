@@ -43,7 +43,10 @@ tp_status scratch_for_current_device(void** out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TP_ERR_CUDA;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();  // leave no stale error for the next call on this thread
+            return TP_ERR_CUDA;
+        }
         g_scratch_addr[dev] = p;
     }
     *out = g_scratch_addr[dev];
@@ -78,6 +81,11 @@ extern "C" tp_status tprod_gemm_noalloc(const void* A, const void* B, void* C, i
     if (prec != TP_FP32 && prec != TP_FP64) return TP_ERR_ARG;
     if (transA != 0 && transA != 1) return TP_ERR_ARG;
     if (n > (prec == TP_FP32 ? 1024 : 512)) return TP_ERR_ARG;
+    // the size limits of tprod_gemm: with every operand below 2^40 elements the
+    // byte counts below cannot wrap
+    const long lim = 1L << 40;
+    if ((long)l * kk * n >= lim || (long)kk * m * n >= lim || (long)l * m * n >= lim) return TP_ERR_ARG;
+    if (l > 65535 * 128) return TP_ERR_ARG;
     const size_t c = prec == TP_FP32 ? 8 : 16;
     const size_t h = (size_t)n / 2 + 1;
     const size_t need = tp::align256(h * l * kk * c) + tp::align256(h * kk * m * c) + tp::align256(h * l * m * c);

@@ -54,6 +54,21 @@ def test_argument_errors_are_synchronous_and_enqueue_nothing(lib):
     assert lib.tp_status_string(-5).decode().startswith("discrepancy")
 
 
+def test_noalloc_refuses_sizes_whose_scratch_need_would_wrap(lib):
+    """Sizes whose byte count would wrap size_t are argument errors, returned
+    before any CUDA call (on a host without a GPU a CUDA call would give -2)."""
+    f = lib.tprod_gemm_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 6 + [ctypes.c_void_p]
+    p = ctypes.c_void_p(256)
+    big = 1 << 30
+    for prec in (0, 1):
+        assert f(p, p, p, big, big, big, 1, 0, prec, None) == -1
+        assert f(p, p, p, big, big, 1, 1, 1, prec, None) == -1
+        assert f(p, p, p, 1, big, big, 1, 0, prec, None) == -1
+    assert f(p, p, p, 65535 * 128 + 1, 1, 1, 1, 0, 0, None) == -1
+
+
 def test_product_path_has_no_cpu_fallback():
     """The binding refuses CPU tensors instead of computing on the host."""
     import torch

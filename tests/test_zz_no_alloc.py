@@ -5,8 +5,11 @@ hand over) use this entry point; it computes in a fixed 16 MiB scratch array
 inside the library.  The test calls it through the C ABI twice in a row, so
 the second call runs on the scratch the first left behind, and checks both
 results against tprod_gemm with a caller workspace, within the FP32/FP64
-t-product tolerances of the parity tests.  It also checks that a problem too
-large for the scratch is refused before anything is written.
+t-product tolerances of the parity tests, and one FP64 result against a
+t-product the test forms itself (FFT along the tubes, a product per slice,
+inverse FFT).  It also checks the edge of the 16 MiB scratch: the largest
+cube that fits is computed correctly and the next size up is refused before
+anything is written.
 
 This file sorts last so that a run stopping at the first failure has run every
 other test first; it also passes on its own in a fresh process.
@@ -63,5 +66,42 @@ def test_noalloc_rejects_problems_beyond_the_scratch(lib):
     B = torch.zeros((64, 256, 256), device="cuda")
     C = torch.full((64, 256, 256), 3.0, device="cuda")
     assert call_noalloc(L, A, B, C, False, 0) == tprod.TP_ERR_WORKSPACE
+    torch.cuda.synchronize()
+    assert bool(torch.all(C == 3.0))
+
+
+def test_noalloc_matches_an_independent_fp64_tproduct(lib):
+    tprod, L = lib
+    g = np.random.default_rng(11)
+    A64 = torch.from_numpy(g.standard_normal((10, 13, 7)))
+    B64 = torch.from_numpy(g.standard_normal((10, 7, 6)))
+    # facewise product of the Fourier slices (Section 2), formed here with torch.fft on the host
+    ref = torch.fft.ifft(torch.fft.fft(A64, dim=0) @ torch.fft.fft(B64, dim=0), dim=0).real
+    A, B = A64.to("cuda"), B64.to("cuda")
+    C = torch.full((10, 13, 6), float("nan"), device="cuda", dtype=torch.float64)
+    assert call_noalloc(L, A, B, C, False, 1) == 0
+    torch.cuda.synchronize()
+    assert float(torch.linalg.norm(C.cpu() - ref) / torch.linalg.norm(ref)) <= 1e-12
+
+
+def test_noalloc_at_the_edge_of_the_scratch(lib):
+    """n = 16 (9 spectral slices), FP32, cubes of side L: three spectra of
+    align256(9 L^2 8) bytes each.  L = 278 needs 16,694,016 bytes (fits in
+    16 MiB = 16,777,216); L = 279 needs 16,813,824 (refused)."""
+    tprod, L = lib
+    g = np.random.default_rng(5)
+    side = 278
+    A = torch.from_numpy(g.standard_normal((16, side, side))).to("cuda", torch.float32)
+    B = torch.from_numpy(g.standard_normal((16, side, side))).to("cuda", torch.float32)
+    ref = tprod.tprod(A, B)
+    C = torch.full_like(ref, float("nan"))
+    assert call_noalloc(L, A, B, C, False, 0) == 0
+    torch.cuda.synchronize()
+    err = float(torch.linalg.norm(C - ref) / torch.linalg.norm(ref))
+    assert err <= 5e-6 * np.sqrt(side)
+    side = 279
+    A = torch.zeros((16, side, side), device="cuda")
+    C = torch.full((16, side, side), 3.0, device="cuda")
+    assert call_noalloc(L, A, A, C, False, 0) == tprod.TP_ERR_WORKSPACE
     torch.cuda.synchronize()
     assert bool(torch.all(C == 3.0))
