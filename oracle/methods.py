@@ -201,11 +201,22 @@ def rtsvd_block(A, Omega, eps, b, q, r_max):
 # RT-tSVD method (Section 4.2 and Eq. (kinit)).
 # --------------------------------------------------------------------------
 
+def rtsvd_prefix(fac: dict, r: int, block: int) -> dict:
+    """The block-form factorisation stopped after its first r columns (r a
+    multiple of the block size, or the full r): the blocks are built one after
+    another, so this is what rtsvd_block returns when eta falls below eps^2
+    right after column r."""
+    nb = -(-r // block)
+    return dict(Q=fac["Q"][:, :, :r], Bt=fac["Bt"][:, :r, :], r=r, eta=fac["etas"][nb], etas=fac["etas"][:nb + 1])
+
+
 def rtsvd_solve(A, B, Omega, delta, tau, eps, p_over, block=16, q_power=1,
-                r_max=None, form="block", k_fixed=None):
+                r_max=None, form="block", k_fixed=None, fac=None):
     n, l, m = A.shape
     r_max = min(l, m) if r_max is None else r_max
-    if form == "alg3":
+    if fac is not None:
+        pass  # a factorisation made earlier (rtsvd_block / rtsvd_prefix) with this eps
+    elif form == "alg3":
         fac = rtsvd_alg3(A, Omega, eps, r_max)
     else:
         fac = rtsvd_block(A, Omega, eps, block, q_power, r_max)

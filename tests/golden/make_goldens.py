@@ -1,11 +1,16 @@
-"""Write n256_oracle.json: the FP64 oracle's results on the 256^3 deblurring
-workload that bench.py times (synth.CONFIGS["n256"], the seed of rank 0), for
-the full-size GPU parity test (tests/test_gpu_full_size.py).
+"""Write <config>_oracle.json and <config>_oracle_X.npz: the FP64 oracle's
+results on a full-size deblurring workload that bench.py times
+(synth.CONFIGS[config], the seed of rank 0), for the full-size GPU parity tests
+(tests/test_gpu_full_size.py) and the bench's error figures.
 
-Calls only the oracle and the seeded input generator.  About a minute and a
-half of CPU:
+The .json holds the scalars (truncation indices, statuses, margins, residual
+histories, mu, the float32 feasibility figures); the .npz holds the complete
+float64 solutions X (n, N, 1) of the RT-tSVD, tGKB and Tikhonov-tGKB solves.
 
-    python tests/golden/make_n256.py
+Calls only the oracle and the seeded input generator:
+
+    python tests/golden/make_goldens.py n256      # about a minute and a half
+    python tests/golden/make_goldens.py n512      # several minutes
 """
 import json
 import os
@@ -27,20 +32,21 @@ def sample_index(N: int) -> np.ndarray:
     return np.random.default_rng(2024).choice(N * N, size=N_SAMPLES, replace=False)
 
 
-def main() -> None:
-    cfg = synth.CONFIGS["n256"]
+def main(name: str) -> None:
+    cfg = synth.CONFIGS[name]
     P = synth.blur_problem(cfg, seed=cfg.seed)
     A, B, Om = (P[k].astype(np.float64) for k in ("A", "B", "Omega"))
     idx = sample_index(cfg.N)
-    out = {"config": "n256", "seed": cfg.seed, "delta": P["delta"], "sample_index": idx.tolist()}
+    out = {"config": name, "seed": cfg.seed, "delta": P["delta"], "sample_index": idx.tolist()}
+    sols = {}
 
-    def pack(r, extra):
+    def pack(method, r, extra):
         X = r["X"].reshape(-1)
+        sols[method] = r["X"]
         d = {"k": int(r["k"]), "status": int(r["status"]), "tau_delta": float(r["tau_delta"]),
-             "x_norm": float(np.linalg.norm(X)),
-             "x_samples": X[idx].tolist()}
+             "x_norm": float(np.linalg.norm(X)), "x_samples": X[idx].tolist()}
         d.update(extra)
-        return d
+        out[method] = d
 
     r1 = O.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.eps_rel * np.sqrt(O.fro2(A)), cfg.p_over, cfg.block,
                        cfg.q_power, cfg.r_max)
@@ -48,18 +54,19 @@ def main() -> None:
     # first-order float32 error of the truncated solution, u32 kappa_k sqrt(N)
     S = r1["S"]
     kappa = float(S[:, 0].max() / S[:, r1["k"] - 1].min())
-    out["rtsvd"] = pack(r1, {"r": int(r1["r"]), "residual": float(r1["res"][r1["k"]]), "margin": float(r1["margin"]),
-                             "res": {str(k): v for k, v in r1["res"].items()}, "kappa_k": kappa,
-                             "fp32_error_prediction": float(np.finfo(np.float32).eps * kappa * np.sqrt(cfg.N))})
+    pack("rtsvd", r1, {"r": int(r1["r"]), "residual": float(r1["res"][r1["k"]]), "margin": float(r1["margin"]),
+                       "res": {str(k): v for k, v in r1["res"].items()}, "kappa_k": kappa,
+                       "fp32_error_prediction": float(np.finfo(np.float32).eps * kappa * np.sqrt(cfg.N))})
     r2 = O.tgkb_solve(A, B, P["delta"], cfg.tau, cfg.k_max)
-    out["tgkb"] = pack(r2, {"residual": float(r2["res"][r2["k"]]), "margin": float(r2["margin"]),
-                            "res": {str(k): v for k, v in r2["res"].items()}})
+    pack("tgkb", r2, {"residual": float(r2["res"][r2["k"]]), "margin": float(r2["margin"]),
+                      "res": {str(k): v for k, v in r2["res"].items()}})
     r3 = O.tgkt_solve(A, B, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)
-    out["tgkt"] = pack(r3, {"mu": float(r3["mu"]), "residual": float(r3["residual"])})
-    with open(os.path.join(HERE, "n256_oracle.json"), "w") as f:
+    pack("tgkt", r3, {"mu": float(r3["mu"]), "residual": float(r3["residual"])})
+    with open(os.path.join(HERE, f"{name}_oracle.json"), "w") as f:
         json.dump(out, f)
-    print({m: {k: out[m].get(k) for k in ("k", "status", "margin", "mu")} for m in ("rtsvd", "tgkb", "tgkt")})
+    np.savez(os.path.join(HERE, f"{name}_oracle_X.npz"), **sols)
+    print({m: {k: out[m].get(k) for k in ("k", "status", "margin", "mu", "r")} for m in ("rtsvd", "tgkb", "tgkt")})
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1] if len(sys.argv) > 1 else "n256")

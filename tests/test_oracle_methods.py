@@ -105,6 +105,29 @@ def test_rtsvd_discrepancy_residual_and_bracket():
     assert all(out["res"][j] > tau * delta for j in range(out["k_init"], k))
 
 
+def test_rtsvd_prefix_is_the_sketch_stopped_by_its_eta_test():
+    """A prefix of a factorisation sketched to r_max is what the block sketch
+    returns when eta falls below eps^2 right after that many columns: the same
+    Q, Bt, r and eta, and the same solve."""
+    A, B, delta = small_blur(N=10, n=8, general=0.02)
+    n, l, m = A.shape
+    Om = rnd((n, m, m), 9)
+    full = O.rtsvd_block(A, Om, 0.0, 2, 1, m)
+    etas = full["etas"]
+    for nb in (2, 3):
+        # an eps between eta after nb blocks and eta after nb - 1 stops the sketch at r = 2 nb
+        eps = np.sqrt(np.sqrt(etas[nb] * etas[nb - 1]))
+        ref = O.rtsvd_block(A, Om, eps, 2, 1, m)
+        pre = O.rtsvd_prefix(full, 2 * nb, 2)
+        assert ref["r"] == pre["r"] == 2 * nb
+        assert np.allclose(ref["Q"], pre["Q"], atol=1e-13) and np.allclose(ref["Bt"], pre["Bt"], atol=1e-13)
+        assert np.isclose(ref["eta"], pre["eta"], rtol=1e-12)
+        a = O.rtsvd_solve(A, B, Om, delta, 1.1, eps, 1, 2, 1, r_max=m)
+        b = O.rtsvd_solve(A, B, Om, delta, 1.1, eps, 1, 2, 1, r_max=m, fac=pre)
+        assert a["k"] == b["k"] and a["status"] == b["status"]
+        assert np.allclose(a["X"], b["X"], atol=1e-12)
+
+
 def small_blur_multi(p=3, N=10, n=8, seed=13, noise=1e-2, general=0.02):
     """p lateral slices (different images) blurred by one operator, with noise
     of total relative level `noise` (delta = ||E||_F over all slices)."""
