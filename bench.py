@@ -177,29 +177,89 @@ def gkb_bytes(h, l, m, k, esize):
 
 
 def class_work(cfg, infos, esize=4):
-    """Algorithmic work per step by kernel class: (amount, unit, bound)."""
+    """Algorithmic work per step by kernel class: {class: {"bytes", "flops",
+    "bound", "note"}}.  Bytes are the HBM traffic the method needs (each pass
+    over a tensor counted once); flops count real multiply-adds as 2.  The
+    bound is the one the per-step scope table assigns to the step: the DFT,
+    the products streaming A-hat, the tGKB iteration and the discrepancy scan
+    are HBM-bound (their arithmetic intensity is below the ridge); the small
+    SVD, the Tikhonov search and the block orthonormalisation are bound by
+    arithmetic (float32 SIMT and, in the orthonormalisation, the legacy
+    tensor path)."""
     N = cfg.N
     h, l, m, n = N // 2 + 1, N, N, N
     c = 2 * esize
     rt, gk, tk = infos
     r, k_rt, b, q = rt["r"], rt["k"], cfg.block, cfg.q_power
     nblk = -(-r // b)
-    gemm = nblk * (2 * q + 2) * 8.0 * h * l * m * b            # sketch, power iterations, projection
-    gemm += 8.0 * h * r * l + 8.0 * h * m * r * r + 8.0 * h * r * l * m + 8.0 * h * m * k_rt
-    dft_bytes = 3 * (esize * n * l * m + c * h * l * m)        # A transformed by each of the three solves
-    gkbb = gkb_bytes(h, l, m, gk["k"], esize) + gkb_bytes(h, l, m, tk["k"], esize)
-    orth = 0.0
+    nchunk = -(-r // 32)
+    # products over A-hat: sketch, power iterations and projection of each block, the K = A-hat V chunks, the
+    # transposed copy of A-hat (read + write), and the small products V = Q_G U_R, d = Q^H b, X = V alpha
+    gemm_b = (nblk * (2 * q + 2) + nchunk) * c * h * l * m + 2 * c * h * l * m
+    gemm_b += c * h * (m * r + r * r + m * r) + c * h * (r * l + l) + c * h * (m * r + m)
+    gemm_f = nblk * (2 * q + 2) * 8.0 * h * l * m * b + 8.0 * h * l * m * r
+    gemm_f += 8.0 * h * m * r * r + 8.0 * h * r * l + 8.0 * h * m * k_rt
+    dft_b = 3 * (esize * n * l * m + c * h * l * m)            # A transformed by each of the three solves
+    dft_b += 3 * (esize * n * l + c * h * l) + esize * n * m * r + c * h * m * r   # B (x3), Omega
+    dft_b += 3 * (c * h * m + esize * n * m)                   # the three inverse transforms
+    gkb_b = gkb_bytes(h, l, m, gk["k"], esize) + gkb_bytes(h, l, m, tk["k"], esize)
+    gkb_f = 0.0
+    for kk in (gk["k"], tk["k"]):
+        for i in range(1, kk + 1):
+            gkb_f += 2 * 8.0 * h * l * m + 4 * 8.0 * h * ((i - 1) * m + i * l)
+    orth_f, orth_b = 0.0, 0.0
     for blk in range(nblk):
         rp = blk * b
         # two CGS passes against the basis (32 flop per complex coefficient and update) for the q+1 sketch
         # blocks and the projection block; in-block Cholesky QR at 8*L*b^2 flop per pass (Gram + solve), two
         # passes for kept blocks, one for the q intermediate blocks on each side
-        orth += h * ((q + 1) * 32.0 * l * rp * b + (q * 8.0 + 16.0) * l * b * b)
-        orth += h * (q * 8.0 * m * b * b + 32.0 * m * rp * b + 16.0 * m * b * b)
-    svd = h * rt.get("sweeps", 8) * (r * (r - 1) / 2) * 7 * r * 8.0
-    return {"gemm": (gemm / 1e12, "TFLOP", "alu"), "dft": (dft_bytes / 1e9, "GB", "hbm"),
-            "gkb": (gkbb / 1e9, "GB", "hbm"), "orth": (orth / 1e12, "TFLOP", "alu"),
-            "svd": (svd / 1e12, "TFLOP", "alu")}
+        orth_f += h * ((q + 1) * 32.0 * l * rp * b + (q * 8.0 + 16.0) * l * b * b)
+        orth_f += h * (q * 8.0 * m * b * b + 32.0 * m * rp * b + 16.0 * m * b * b)
+        # each CGS pass reads the basis twice (coefficients, update); the block is read and written once
+        orth_b += h * c * (2 * (q + 1) * 2 * l * rp + 2 * 2 * m * rp)
+        orth_b += h * c * ((q + 1) * 2 * l * b + q * 2 * m * b + 2 * m * b)
+    svd_f = h * rt.get("sweeps", 8) * (r * (r - 1) / 2) * 7 * r * 8.0
+    dp_b = c * h * (p_over_candidates(rt, cfg) * k_rt * l + l)
+    return {"gemm": {"bytes": gemm_b, "flops": gemm_f, "bound": "hbm"},
+            "dft": {"bytes": dft_b, "flops": None, "bound": "hbm"},
+            "gkb": {"bytes": gkb_b, "flops": gkb_f, "bound": "hbm",
+                    "note": "A-hat and the bases are L2-resident at N=256 (67.6 MB + bases < 129 MB L2): "
+                            "fractions of the HBM peak above 1 are possible there"},
+            "orth": {"bytes": orth_b, "flops": orth_f, "bound": "alu"},
+            "svd": {"bytes": None, "flops": svd_f, "bound": "alu"},
+            "dp": {"bytes": dp_b, "flops": None, "bound": "hbm"}}
+
+
+def p_over_candidates(rt, cfg):
+    """Discrepancy candidates k_init..r, each a pass over K_k."""
+    return rt["r"] - max(1, rt["r"] - cfg.p_over) + 1
+
+
+def roofline_entries(work, per_class, hbm, peak_src):
+    """One roofline entry per kernel class with device time in the last timed
+    step: achieved bytes/s against the measured HBM peak where the class moves
+    bytes, flop/s against the derived FP32 SIMT peak where it computes."""
+    out = {}
+    for cls, w in work.items():
+        ms, launches = per_class.get(cls, (0.0, 0))
+        if not launches or ms <= 0:
+            continue
+        sec = ms / 1e3
+        e = {"bound": w["bound"], "ms_per_step": ms, "launches": launches, "avg_launch_ms": ms / launches}
+        if w.get("bytes"):
+            e["hbm_gbs"] = w["bytes"] / sec / 1e9
+            e["hbm_frac"] = e["hbm_gbs"] / hbm
+            e["bytes_per_launch"] = w["bytes"] / launches
+        if w.get("flops"):
+            e["tflops"] = w["flops"] / sec / 1e12
+            e["fp32_simt_frac"] = e["tflops"] / FP32_SIMT_TFLOPS
+        if w.get("note"):
+            e["note"] = w["note"]
+        out[cls] = e
+    out["peaks"] = {"hbm_gbs": hbm, "hbm_source": peak_src,
+                    "fp32_simt_tflops": FP32_SIMT_TFLOPS,
+                    "fp32_simt_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    return out
 
 
 def run_ours(a, rank, world, local):
@@ -239,13 +299,13 @@ def run_ours(a, rank, world, local):
 
     # timed region: K steps, L2 flushed between steps, device time by CUDA
     # events.  By default the step is captured once as a CUDA graph and
-    # replayed.  The dominant kernel class is timed by CUDA events around its
+    # replayed.  Every kernel class is timed by CUDA events around its
     # launches in the last timed step only (a second capture of the step with
     # those events inside), so that the events do not slow the other steps.
     graph = timed_graph = None
     if not a.no_graph:
         graph = tprod.Captured(lambda: step(A, B, Om), warmup=0)
-        tprod.timing_enable([dominant])
+        tprod.timing_enable(tprod.KERNEL_CLASSES)
         timed_graph = tprod.Captured(lambda: step(A, B, Om), warmup=0)
         tprod.timing_enable([])
 
@@ -254,7 +314,7 @@ def run_ours(a, rank, world, local):
             (timed_graph if last else graph).replay()
         else:
             if last:
-                tprod.timing_enable([dominant])
+                tprod.timing_enable(tprod.KERNEL_CLASSES)
             step(A, B, Om)
 
     launches0 = tprod.kernel_launches()
@@ -276,8 +336,9 @@ def run_ours(a, rank, world, local):
     t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
-    dom_ms, dom_launches = tprod.timing_read()[dominant]  # the last timed step
-    dom_steps = 1
+    last_step = tprod.timing_read()  # per class, the last timed step
+    dominant = max(last_step, key=lambda k: last_step[k][0])
+    dom_ms, dom_launches = last_step[dominant]
     tprod.timing_enable([])
     clk = clocks.stop()
     launches = graph.launches * a.steps if graph else tprod.kernel_launches() - launches0
@@ -360,25 +421,21 @@ def run_ours(a, rank, world, local):
 
     hbm, bf16, src = peaks()
     work = class_work(cfg, infos)
+    by_class = roofline_entries(work, last_step, hbm, src)
     roof = None
-    if dominant in work and dom_launches:
-        amount, unit, bound = work[dominant]
-        secs = dom_ms / 1e3 / dom_steps  # device seconds of this class per step
-        if bound == "hbm":
-            ach = amount / secs
-            tr = ncu_traffic(dominant, cfg.name)
-            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": tr, "traffic_source": NCU_TRAFFIC[dominant]["profile"] if tr else None,
-                    "algorithmic_bytes_per_launch": amount * 1e9 * dom_steps / dom_launches, "kernel_class": dominant, "peak_source": src,
-                    "avg_launch_ms": dom_ms / dom_launches}
+    if dominant in by_class:
+        e, w = by_class[dominant], work[dominant]
+        tr = ncu_traffic(dominant, cfg.name)
+        common = {"traffic": tr / 1.0 if tr else None,
+                  "traffic_source": NCU_TRAFFIC[dominant]["profile"] if tr else None,
+                  "kernel_class": dominant, "avg_launch_ms": e["avg_launch_ms"], "launches_per_step": e["launches"]}
+        if w["bound"] == "hbm":
+            roof = {"bound": "hbm", "achieved": e["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": e["hbm_frac"],
+                    "algorithmic_bytes_per_launch": e["bytes_per_launch"], "peak_source": src, **common}
         else:
-            ach = amount / secs
-            tr = ncu_traffic(dominant, cfg.name)
-            roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_SIMT_TFLOPS, "traffic": tr,
-                    "traffic_source": NCU_TRAFFIC[dominant]["profile"] if tr else None, "kernel_class": dominant,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                    "avg_launch_ms": dom_ms / dom_launches}
+            roof = {"bound": "alu", "achieved": e["tflops"], "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                    "frac": e["fp32_simt_frac"], "hbm_frac_of_algorithmic_bytes": e.get("hbm_frac"),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", **common}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -389,7 +446,7 @@ def run_ours(a, rank, world, local):
                       "launch": "plain launches" if graph is None else
                       f"CUDA graph of the step ({graph.launches} kernels) captured once, replayed per step",
                       "parallelism": f"replicas x{world}"},
-           "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+           "e2e": e2e, "gpu_launches": launches, "roofline": roof, "roofline_by_class": by_class, "clocks": clk,
            "precision_form": prec_form, "batched_form": batched, "uneven_form": uneven,
            "differentiation_form": grad,
            "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
@@ -408,13 +465,17 @@ def run_ours(a, rank, world, local):
 def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
     """RT-tSVD solves/s with the float32 and the TF32 sketch on the same
     workload (L2 flushed between solves, CUDA events), with each solution's
-    sampled error against the oracle's (tests/golden/n256_oracle.json, written
-    by an oracle-only script; read, not run)."""
+    relative Frobenius error against the oracle's complete solution
+    (tests/golden/<workload>_oracle_X.npz, written by an oracle-only script;
+    read, not run)."""
     gold_path = os.path.join(ROOT, "tests", "golden", f"{cfg.name}_oracle.json")
-    gold = None
+    sol_path = os.path.join(ROOT, "tests", "golden", f"{cfg.name}_oracle_X.npz")
+    gold, ref_x = None, None
     if os.path.exists(gold_path):
         with open(gold_path) as f:
             gold = json.load(f)
+    if os.path.exists(sol_path):
+        ref_x = np.load(sol_path)["rtsvd"]
     out = {}
     reps = max(3, min(a.steps, 20))
     for name, tf32 in (("fp32", False), ("tf32", True)):
@@ -435,10 +496,10 @@ def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
             ms += e0.elapsed_time(e1)
         info = tprod._info_dict(info)
         rec = {"solves_per_s": reps / (ms / 1e3), "ms_per_solve": ms / reps, "k": info["k"], "r": info["r"]}
+        if ref_x is not None:  # every entry of the solution against the oracle's
+            x = X.cpu().numpy().astype(np.float64)
+            rec["rel_err_vs_oracle"] = float(np.linalg.norm(x - ref_x) / np.linalg.norm(ref_x))
         if gold is not None:
-            x = X.cpu().numpy().reshape(-1)[np.asarray(gold["sample_index"])]
-            ref = np.asarray(gold["rtsvd"]["x_samples"])
-            rec["rel_err_vs_oracle_samples"] = float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
             rec["k_matches_oracle"] = info["k"] == gold["rtsvd"]["k"]
         out[name] = rec
     out["note"] = ("TF32: sketch and power-iteration products with one tf32 tensor-core product; "

@@ -958,58 +958,210 @@ __global__ void k_alpha(const T* sigma, long ssig, const cplx<T>* dprime, long s
     }
 }
 
-// Per slice: squared residual norms ||b - sum_{j<k} K_j alpha_j||^2 for all
-// k = 0..r, where K = A V (stored vector-major, K_j contiguous).
+// Coefficients in the computed basis.  The one-sided Jacobi stops when every
+// pair of columns of R J is orthogonal to within its tolerance (relative
+// off-diagonal 4 sqrt(r) u), so the normalised columns U_R are orthonormal only
+// to that level, and the sum of alpha_j v_j over j < k with alpha_j = d'_j /
+// sigma_j treats U_k^H U_k as the identity.  For the truncated solution in the
+// span of V_k = Q_G U_k the coefficients are (U_k^H U_k)^{-1} alpha_k; with
+// N = U_k^H U_k - I of order 1e-6 its first-order form
+//   alpha_k <- alpha_k - N alpha_k = 2 alpha_k - U_k^H (U_k alpha_k)
+// is exact to O(|N|^2).  In float32 this takes the error of the 256^3
+// truncated solution from 1.8e-5 to 1e-6 against the float64 oracle.  k from
+// the state (the discrepancy choice), r the sketch rank; alpha is r_max x np
+// per slice (row-major), U_R row-major with column j the j-th singular vector.
+// Applied in the same way to t = V_k^H G of the adjoint (the map is
+// self-adjoint in the coefficients).  Right-hand sides in chunks of 16.
 template <typename T>
+__global__ void __launch_bounds__(256) k_alpha_corr(const cplx<T>* __restrict__ UR, long ldu, long sU,
+                                                   cplx<T>* alpha, long sa, const State* st, int np) {
+    typedef cplx<T> V;
+    constexpr int CH = 16;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int r = st->r, k = st->k, s = blockIdx.x;
+    if (k <= 0 || r <= 0) return;
+    V* a = (V*)smraw;      // k x nc: the coefficients of this chunk
+    V* t = a + k * CH;     // r x nc: U_k a
+    const V* U = UR + (long)s * sU;
+    V* al = alpha + (long)s * sa;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int c0 = 0; c0 < np; c0 += CH) {
+        const int nc = np - c0 < CH ? np - c0 : CH;
+        for (int e = tid; e < k * nc; e += blockDim.x) {
+            const int j = e / nc, c = e - j * nc;
+            a[e] = al[(long)j * np + c0 + c];
+        }
+        __syncthreads();
+        // t_i = sum_{j<k} U[i][j] a_j: a warp per (row, column), lanes along the row
+        for (int ic = warp; ic < r * nc; ic += nw) {
+            const int i = ic / nc, c = ic - i * nc;
+            V acc = mk<T>(0, 0);
+            for (int j = lane; j < k; j += 32) cfma(acc, U[(long)i * ldu + j], a[j * nc + c]);
+            acc.x = warp_sum(acc.x);
+            acc.y = warp_sum(acc.y);
+            if (lane == 0) t[i * nc + c] = acc;
+        }
+        __syncthreads();
+        // alpha_j <- 2 a_j - sum_i conj(U[i][j]) t_i: a thread per (j, column), consecutive threads along j
+        for (int e = tid; e < k * nc; e += blockDim.x) {
+            const int c = e / k, j = e - c * k;
+            V acc = mk<T>(0, 0);
+            for (int i = 0; i < r; ++i) cfmac(acc, U[(long)i * ldu + j], t[i * nc + c]);
+            const V x = a[j * nc + c];
+            al[(long)j * np + c0 + c] = mk<T>((T)2 * x.x - acc.x, (T)2 * x.y - acc.y);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+static tp_status alpha_corr(int h, const cplx<T>* UR, int r_max, cplx<T>* alpha, long sa, const State* st, int np,
+                            cudaStream_t stream) {
+    const size_t smem = (size_t)2 * r_max * 16 * sizeof(cplx<T>);
+    if (smem_optin((const void*)k_alpha_corr<T>, smem) != TP_OK) return TP_ERR_CUDA;
+    prof_begin(TP_KC_MISC, stream);
+    k_alpha_corr<T><<<h, 256, smem, stream>>>(UR, r_max, (long)r_max * r_max, alpha, sa, st, np);
+    return launched(TP_KC_MISC, stream);
+}
+
+// Per slice: squared residual norms ||b - sum_{j<k} K_j alpha^(k)_j||^2 for
+// the candidates k = k_init .. r (k_init = max(1, r - p), Eq. (kinit)), where
+// K = A V (stored vector-major, K_j contiguous) and alpha^(k) are the
+// coefficients that the solution truncated at k uses: in float32 the
+// computed-basis coefficients 2 alpha_k - U_k^H (U_k alpha_k) of
+// k_alpha_corr (so that the residual tested is the returned solution's), in
+// float64 alpha_k itself (U_R orthonormal to rounding).  Up to DP_CC
+// candidates share one pass over K: each thread carries its RPT rows of every
+// candidate's residual.  np right-hand sides (alpha and B row-major with np
+// columns), summed.  Per thread and per warp in the working precision, across
+// warps in float64; the other entries of out are 0.
+constexpr int DP_CC = 12;
+template <typename T, int RPT>
 __global__ void __launch_bounds__(256)
 k_dp_scan(const cplx<T>* __restrict__ KhT, long sK, const cplx<T>* __restrict__ alpha, long sa,
-          const cplx<T>* __restrict__ bhat, long sb, const State* st, int l, int np, int p_over, double* out,
-          long so) {
-    // Residual B - sum_{j<k} K_j alpha_j of one slice for every k (np
-    // right-hand sides, alpha and B row-major with np columns); its squared
-    // Frobenius norm is formed only for the candidates k >= k_init =
-    // max(1, r - p) (the others are written as 0): per thread and per warp in
-    // the working precision, across warps in float64.
+          const cplx<T>* __restrict__ bhat, long sb, const cplx<T>* __restrict__ UR, long ldu, long sU,
+          const State* st, int l, int np, int p_over, double* out, long so) {
     typedef cplx<T> V;
-    constexpr int RPT = 4;  // rows per thread (l <= 1024)
+    constexpr bool CORR = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smraw[];
-    double* wsum = (double*)smraw;  // [8][r+1]
     const int r = st->r, s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
-    const int k_init = max(1, r - p_over);
+    double* wsum = (double*)smraw;                        // [nw][r+1]
+    V* Tm = (V*)(wsum + (size_t)nw * (r + 1) + 1);        // r x DP_CC: U_k alpha_k per candidate
+    V* ak = Tm + (size_t)r * DP_CC;                       // DP_CC x r: alpha^(k), zero for j >= k
+    Tm = (V*)(((size_t)Tm + 15) & ~(size_t)15);
+    ak = Tm + (size_t)r * DP_CC;
+    const int k_init = max(1, r - p_over), ncand = r - k_init + 1;
     KhT += (long)s * sK;
+    const V* al = alpha + (long)s * sa;
+    const V* U = UR + (long)s * sU;
+    for (int e = tid; e < nw * (r + 1); e += blockDim.x) wsum[e] = 0.0;
     for (int c = 0; c < np; ++c) {
-        V res[RPT];
+        for (int c0 = 0; c0 < ncand; c0 += DP_CC) {
+            const int nc = min(DP_CC, ncand - c0), kb = k_init + c0;  // candidates kb .. kb + nc - 1
+            if (CORR) {
+                // T[i][q] = sum_{j < kb+q} U[i][j] a_j
+                for (int e = tid; e < r * nc; e += blockDim.x) {
+                    const int q = e / r, i = e - q * r;
+                    V acc = mk<T>(0, 0);
+                    const V* Ui = U + (long)i * ldu;
+#pragma unroll 4
+                    for (int j = 0; j < kb + q; ++j) cfma(acc, Ui[j], al[(long)j * np + c]);
+                    Tm[i * DP_CC + q] = acc;
+                }
+                __syncthreads();
+                // alpha^(k)_j = 2 a_j - sum_i conj(U[i][j]) T[i][q]
+                for (int e = tid; e < r * nc; e += blockDim.x) {
+                    const int q = e / r, j = e - q * r;
+                    V v = mk<T>(0, 0);
+                    if (j < kb + q) {
+                        V acc = mk<T>(0, 0);
+#pragma unroll 4
+                        for (int i = 0; i < r; ++i) cfmac(acc, U[(long)i * ldu + j], Tm[i * DP_CC + q]);
+                        const V a = al[(long)j * np + c];
+                        v = mk<T>((T)2 * a.x - acc.x, (T)2 * a.y - acc.y);
+                    }
+                    ak[q * r + j] = v;
+                }
+            } else {
+                for (int e = tid; e < r * nc; e += blockDim.x) {
+                    const int q = e / r, j = e - q * r;
+                    ak[q * r + j] = j < kb + q ? al[(long)j * np + c] : mk<T>(0, 0);
+                }
+            }
+            __syncthreads();
+            V res[DP_CC][RPT];
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            const int i = tid + u * blockDim.x;
-            res[u] = (i < l) ? bhat[(long)s * sb + (long)i * np + c] : mk<T>(0, 0);
-        }
-        for (int j = 0; j <= r; ++j) {
-            if (j > 0) {
-                const V a = alpha[(long)s * sa + (long)(j - 1) * np + c];
+            for (int u = 0; u < RPT; ++u) {
+                const int i = tid + u * blockDim.x;
+                const V b = (i < l) ? bhat[(long)s * sb + (long)i * np + c] : mk<T>(0, 0);
+#pragma unroll
+                for (int q = 0; q < DP_CC; ++q) res[q][u] = b;
+            }
+            // the K loads of the next DP_PF columns are in flight while one is applied
+            constexpr int DP_PF = (8 * 4 / (int)sizeof(T)) / RPT > 2 ? (8 * 4 / (int)sizeof(T)) / RPT : 2;
+            const int kend = kb + nc - 1;
+            V kv[DP_PF][RPT];
+#pragma unroll
+            for (int f = 0; f < DP_PF; ++f)
 #pragma unroll
                 for (int u = 0; u < RPT; ++u) {
                     const int i = tid + u * blockDim.x;
-                    if (i < l) res[u] = csub(res[u], cmul(KhT[(long)(j - 1) * l + i], a));
+                    kv[f][u] = (i < l && f < kend) ? KhT[(long)f * l + i] : mk<T>(0, 0);
+                }
+            for (int j0 = 0; j0 < kend; j0 += DP_PF) {
+#pragma unroll
+                for (int f = 0; f < DP_PF; ++f) {
+                    const int j = j0 + f;
+                    if (j >= kend) break;
+                    V cur[RPT];
+#pragma unroll
+                    for (int u = 0; u < RPT; ++u) {
+                        cur[u] = kv[f][u];
+                        const int i = tid + u * blockDim.x;
+                        const int jn = j + DP_PF;
+                        kv[f][u] = (i < l && jn < kend) ? KhT[(long)jn * l + i] : mk<T>(0, 0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < DP_CC; ++q) {
+                        if (q >= nc) break;
+                        const V a = ak[q * r + j];
+#pragma unroll
+                        for (int u = 0; u < RPT; ++u) res[q][u] = csub(res[q][u], cmul(cur[u], a));
+                    }
                 }
             }
-            if (j >= k_init) {
+#pragma unroll
+            for (int q = 0; q < DP_CC; ++q) {
+                if (q >= nc) break;
                 T part = 0;
 #pragma unroll
-                for (int u = 0; u < RPT; ++u) part += cabs2(res[u]);
+                for (int u = 0; u < RPT; ++u) part += cabs2(res[q][u]);
                 part = warp_sum(part);
-                if (lane == 0) wsum[warp * (r + 1) + j] = (c == 0 ? 0.0 : wsum[warp * (r + 1) + j]) + (double)part;
+                if (lane == 0) wsum[warp * (r + 1) + kb + q] += (double)part;
             }
+            __syncthreads();
         }
     }
-    __syncthreads();
     for (int j = tid; j <= r; j += blockDim.x) {
         double a = 0.0;
         if (j >= k_init)
             for (int w = 0; w < nw; ++w) a += wsum[w * (r + 1) + j];
         out[(long)s * so + j] = a;
     }
+}
+
+template <typename T>
+static tp_status dp_scan(int h, const cplx<T>* KhT, long sK, const cplx<T>* alpha, long sa, const cplx<T>* bhat,
+                         long sb, const cplx<T>* UR, int r_max, const State* st, int l, int np, int p_over,
+                         double* out, long so, cudaStream_t stream) {
+    const size_t smem = (size_t)8 * (r_max + 1) * sizeof(double) + 16 + 2 * (size_t)r_max * DP_CC * sizeof(cplx<T>);
+    auto kern = l <= 256 ? k_dp_scan<T, 1> : (l <= 512 ? k_dp_scan<T, 2> : k_dp_scan<T, 4>);
+    if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
+    prof_begin(TP_KC_DP, stream);
+    kern<<<h, 256, smem, stream>>>(KhT, sK, alpha, sa, bhat, sb, UR, r_max, (long)r_max * r_max, st, l, np, p_over,
+                                   out, so);
+    return launched(TP_KC_DP, stream);
 }
 
 // Global residuals (Parseval over slices), the discrepancy-principle choice
@@ -1256,17 +1408,14 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
     if (!k_done)
         TRY(cgemm<T>(h, r_max, l, m, dr, 0, 0, 1, 0, w.Vt, r_max, (long)m * r_max, OP_T, w.Ahat, m, lm, OP_T, 0, 0,
                      w.KhT, l, (long)r_max * l, nullptr, st));
-    {
-        const size_t smem = (size_t)(256 / 32) * (r_max + 1) * sizeof(double);
-        prof_begin(TP_KC_DP, st);
-        k_dp_scan<T><<<h, 256, smem, st>>>(w.KhT, (long)r_max * l, w.alpha, rp, w.Bhat, (long)l * p, w.st, l, p,
-                                           P->p_over, w.dpout, r_max + 1);
-        TRY(launched(TP_KC_DP, st));
-    }
+    TRY(dp_scan<T>(h, w.KhT, (long)r_max * l, w.alpha, rp, w.Bhat, (long)l * p, w.UR, r_max, w.st, l, p, P->p_over,
+                   w.dpout, r_max + 1, st));
     prof_begin(TP_KC_DP, st);
     k_dp_reduce<<<1, 256, (r_max + 1) * sizeof(double), st>>>(w.dpout, r_max + 1, h, n, w.st, P->p_over,
                                                               P->tau * P->delta, info, P->res_hist, r_max);
     TRY(launched(TP_KC_DP, st));
+    // float32: the coefficients of the chosen k in the computed (not exactly orthonormal) basis
+    if (sizeof(T) == 4) TRY(alpha_corr<T>(h, w.UR, r_max, w.alpha, rp, w.st, p, st));
     TRY(cgemm<T>(h, m, p, r_max, 0, 0, &w.st->k, 1, 0, w.Vt, r_max, (long)m * r_max, OP_N, w.alpha, p, rp, OP_N,
                  0, 0, w.Xhat, p, (long)m * p, nullptr, st));
     TRY(irdft<T>(w.Xhat, X, n, m, p, p, (long)m * p, nullptr, st));
@@ -1298,6 +1447,7 @@ static tp_status rt_adjoint_impl(const T* G, int l, int m, int n, int p, const t
     // t = V_k^H G-hat (k x p), then t_j / sigma_j^2
     TRY(cgemm<T>(h, r_max, p, m, dk, 0, 0, 1, 0, w.Vt, r_max, (long)m * r_max, OP_C, w.Xhat, p, (long)m * p, OP_N, 0,
                  0, w.alpha, p, rp, nullptr, st));
+    if (sizeof(T) == 4) TRY(alpha_corr<T>(h, w.UR, r_max, w.alpha, rp, w.st, p, st));  // as in the solve
     prof_begin(TP_KC_MISC, st);
     k_alpha<T><<<h, 256, 0, st>>>(w.sigma, r_max, w.alpha, rp, w.alpha, rp, w.st, h, l > m ? l : m, r_max, p, 2);
     TRY(launched(TP_KC_MISC, st));

@@ -1,8 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Every case feeds both sides the same seeded inputs.  The GPU runs in FP64
-(to show it computes the same algorithm: agreement to ~1e-10) and in FP32
-(the product precision: tolerances derived in the design notes).  Truncation
+(to show it computes the same algorithm: agreement to 1e-10) and in FP32
+(the product precision: solutions within 1e-5 relative Frobenius error).  Truncation
 indices are integers decided by a floating-point threshold; they must match
 exactly unless the oracle's margin puts the decision inside the rounding
 band of the GPU precision.
@@ -16,8 +16,10 @@ from paper_2110_02485_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# relative Frobenius tolerances on X against the FP64 oracle
-TOL_X = {torch.float64: 1e-9, torch.float32: 2e-4}
+# relative Frobenius tolerances on X against the FP64 oracle: the stated bound for
+# float32 solutions (every case measures below 8e-6), and float64 agreement to
+# rounding (measured below 1e-13)
+TOL_X = {torch.float64: 1e-10, torch.float32: 1e-5}
 # decisions closer than this (relative) to tau*delta may legitimately differ
 TIE = {torch.float64: 1e-9, torch.float32: 1e-4}
 
@@ -134,7 +136,7 @@ def test_rtsvd_adjoint_matches_oracle(tp, dtype, N, n, p):
     dB = tp.rtsvd_adjoint(fac, dev(G, dtype)).cpu().numpy()
     want = O.rtsvd_adjoint(ref, dev(G, dtype).cpu().double().numpy())
     assert dB.shape == (n, N, p)
-    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 2e-3)
+    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 1e-4)
     # repeatable: the factorisation is not overwritten
     dB2 = tp.rtsvd_adjoint(fac, dev(G, dtype)).cpu().numpy()
     assert np.array_equal(dB, dB2)
@@ -263,7 +265,7 @@ def test_rtsvd_matches_oracle(tp, dtype, N, n, block, q, p_over, eps_rel):
     if exact_k_required(ref, dtype):
         assert info["k"] == ref["k"]
         assert info["status"] == ref["status"]
-        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+        assert rel(X, ref["X"]) <= TOL_X[dtype]
     for k, rk in ref["res"].items():
         assert abs(hist[k] - rk) <= res_tol(rk, B, dtype)
     assert np.isclose(info["norm_a2"], O.fro2(A.astype(np.float64)), rtol=1e-6 if dtype == torch.float32 else 1e-12)
@@ -291,13 +293,13 @@ def test_rtsvd_several_lateral_slices_match_oracle(tp, dtype, N, n, block, p, r_
     if exact_k_required(ref, dtype):
         assert info["k"] == ref["k"]
         assert info["status"] == ref["status"]
-        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+        assert rel(X, ref["X"]) <= TOL_X[dtype]
         # slice j of the joint solve is the k-term filtered solution of slice j alone
         j = p // 2
         Xj = O.rtsvd_solve(A.astype(np.float64), B[:, :, j:j + 1].astype(np.float64), Om.astype(np.float64),
                            delta, tau, eps_rel * np.sqrt(O.fro2(A.astype(np.float64))), p_over, block, 1,
                            r_max=r_max, k_fixed=ref["k"])["X"]
-        assert rel(X[:, :, j:j + 1], Xj) <= TOL_X[dtype] * 10
+        assert rel(X[:, :, j:j + 1], Xj) <= TOL_X[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -323,7 +325,7 @@ def test_ttsvd_matches_oracle(tp, dtype, N, n, l, p):
     if exact_k_required(ref, dtype):
         assert info["k"] == ref["k"]
         assert info["status"] == ref["status"]
-        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+        assert rel(X, ref["X"]) <= TOL_X[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -337,7 +339,7 @@ def test_tgkb_matches_oracle(tp, dtype, N, n, k_max, l):
     if exact_k_required(ref, dtype):
         assert info["k"] == ref["k"]
         assert info["status"] == ref["status"]
-        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+        assert rel(X, ref["X"]) <= TOL_X[dtype]
     for i, ri in ref["res"].items():
         if i <= info["k"]:
             assert abs(hist[i] - ri) <= res_tol(ri, B, dtype)
@@ -386,7 +388,7 @@ def test_tgkb_p_matches_oracle(tp, dtype, N, n, p, k_max):
         if exact_k_required(r, dtype):
             assert info["k"] == r["k"], j
             assert info["status"] == r["status"]
-            assert rel(X[:, :, j], r["X"][:, :, 0]) <= TOL_X[dtype] * 10
+            assert rel(X[:, :, j], r["X"][:, :, 0]) <= TOL_X[dtype]
             assert abs(info["residual"] - r["res"][r["k"]]) <= res_tol(r["res"][r["k"]], B[:, :, j:j + 1], dtype)
 
 
@@ -411,7 +413,7 @@ def test_nested_tgkb_p_matches_oracle(tp, dtype, N, n, p, k_max, levels):
             break
         assert infos[j]["k"] == ref["k"][j], j
         assert infos[j]["status"] == ref["status"][j]
-        assert rel(X[:, :, j], ref["X"][:, :, j]) <= TOL_X[dtype] * 10
+        assert rel(X[:, :, j], ref["X"][:, :, j]) <= TOL_X[dtype]
         for k, rk in ref["res"][j].items():
             assert abs(hist[j, k] - rk) <= res_tol(rk, B[:, :, j:j + 1], dtype)
         untested = [k for k in range(k_max + 1) if k not in ref["res"][j]]
@@ -435,7 +437,7 @@ def test_tgkb_p_common_delta_and_cap(tp, dtype):
         r = ref["per_slice"][j]
         if exact_k_required(r, dtype):
             assert infos[j]["k"] == r["k"] and infos[j]["status"] == r["status"]
-            assert rel(X[:, :, j], r["X"][:, :, 0]) <= TOL_X[dtype] * 10
+            assert rel(X[:, :, j], r["X"][:, :, 0]) <= TOL_X[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -479,7 +481,7 @@ def test_tgkt_matches_oracle(tp, dtype, N, n, k_max, lo, hi):
         assert info["k"] == ref["k"]
         assert info["status"] == ref["status"]
         assert abs(np.log10(info["mu"]) - np.log10(ref["mu"])) <= (1e-9 if dtype == torch.float64 else 1e-3)
-        assert rel(X, ref["X"]) <= TOL_X[dtype] * 10
+        assert rel(X, ref["X"]) <= TOL_X[dtype]
         assert abs(info["residual"] - ref["residual"]) <= (1e-9 if dtype == torch.float64 else 1e-4) * ref["residual"]
 
 
@@ -492,7 +494,7 @@ def test_tgkb_cap_reports_not_converged(tp, dtype):
     ref = O.tgkb_solve(A.astype(np.float64), B.astype(np.float64), delta * 1e-6, 1.1, 3)
     assert info["status"] == O.STATUS_NOT_CONVERGED == ref["status"]
     assert info["k"] == 3 == ref["k"]
-    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype] * 10
+    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype]
 
 
 @pytest.mark.parametrize("N,r_max", [(144, 144), (160, 150)])
@@ -511,7 +513,7 @@ def test_rtsvd_large_rank_matches_oracle(tp, N, r_max):
         assert abs(hist[k] - rk) <= res_tol(rk, B, torch.float32) * 10, k
     if exact_k_required(ref, torch.float32):
         assert info["k"] == ref["k"]
-        assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[torch.float32] * 10
+        assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[torch.float32]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -525,7 +527,7 @@ def test_rtsvd_rmax_cap_reports_not_converged(tp, dtype):
     assert info["r"] == 6 == ref["r"]
     assert info["status"] == O.STATUS_NOT_CONVERGED == ref["status"]
     assert info["k"] == ref["k"]
-    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype] * 10
+    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -539,13 +541,13 @@ def test_zero_fourier_slices_break_down_cleanly(tp, dtype):
     ref = O.tgkb_solve(A, B, 1e-3, 1.1, N)
     X, info = tp.tgkb_solve(dev(A, dtype), dev(B, dtype), 1e-3, 1.1, N)
     assert info["k"] == ref["k"]
-    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype] * 10
+    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[dtype]
     Om = rnd((n, N, N), 23)
     refr = O.rtsvd_solve(A, B, Om, 1e-3, 1.1, 1e-3 * np.sqrt(O.fro2(A)), 2, 2, 1, r_max=N)
     Xr, infor = tp.rtsvd_solve(dev(A, dtype), dev(B, dtype), dev(Om, dtype), 1e-3, 1.1, 2, 2, 1, r_max=N,
                                eps_rel=1e-3)
     assert infor["r"] == refr["r"] and infor["k"] == refr["k"]
-    assert rel(Xr.cpu().numpy(), refr["X"]) <= TOL_X[dtype] * 10
+    assert rel(Xr.cpu().numpy(), refr["X"]) <= TOL_X[dtype]
 
 
 def test_invalid_arguments_raise(tp):
@@ -794,5 +796,5 @@ def test_ttsvd_adjoint_matches_oracle(tp, dtype, N, n, p):
     dB = tp.ttsvd_adjoint(fac, dev(G, dtype)).cpu().numpy()
     want = O.ttsvd_adjoint(A.astype(np.float64), ref, dev(G, dtype).cpu().double().numpy())
     assert dB.shape == (n, N, p)
-    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 2e-3)
+    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 1e-4)
     assert np.array_equal(dB, tp.ttsvd_adjoint(fac, dev(G, dtype)).cpu().numpy())
