@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "RT-tSVD / tGKB solves/s at N=256,512 on 1 GB300; % roofline; BF16 vs FP32 at rel-err"
 UNIT = "solves/s"
 SOLVES_PER_STEP = 3
+VIDEO_TAU = 1.2  # Section 5 uses 1.2 for the video and the multi-frame examples
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 SIMT peak derived from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -81,6 +82,8 @@ def args_():
     p.add_argument("--no-batched", action="store_true", help="skip the several-frames RT-tSVD measurement")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven-size batch of problems")
     p.add_argument("--no-grad", action="store_true", help="skip the differentiation form")
+    p.add_argument("--no-n512", action="store_true", help="skip the 512^3 workload")
+    p.add_argument("--no-hat", action="store_true", help="skip the solves from a precomputed A-hat")
     p.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
     return p.parse_args()
 
@@ -418,6 +421,12 @@ def run_ours(a, rank, world, local):
     grad = None
     if not a.no_grad and rank == 0:
         grad = differentiation_form(a, cfg, P, A, B, Om, flush, tprod, torch)
+    hat = None
+    if not a.no_hat and rank == 0:
+        hat = hat_form(a, cfg, P, A, B, Om, flush, tprod, torch)
+    n512 = None
+    if not a.no_n512 and rank == 0 and cfg.name != "n512":
+        n512 = full_size_form(a, "n512", flush, tprod, torch)
 
     hbm, bf16, src = peaks()
     work = class_work(cfg, infos)
@@ -448,7 +457,7 @@ def run_ours(a, rank, world, local):
                       "parallelism": f"replicas x{world}"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "roofline_by_class": by_class, "clocks": clk,
            "precision_form": prec_form, "batched_form": batched, "uneven_form": uneven,
-           "differentiation_form": grad,
+           "differentiation_form": grad, "n512_form": n512, "b_only_form": hat,
            "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
            "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
                           "tgkb": {k: infos[1][k] for k in ("k", "status")},
@@ -510,6 +519,110 @@ def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
         out["oracle_kappa_k"] = gold["rtsvd"]["kappa_k"]
         out["fp32_error_prediction"] = gold["rtsvd"]["fp32_error_prediction"]
     return out
+
+
+def full_size_form(a, name, flush, tprod, torch, steps=10):
+    """The same three-solve step on another full-size workload (the 512^3
+    precision-form size by default): CUDA-graph replays with L2 flushes and
+    CUDA events, device time per kernel class from one instrumented plain
+    step, every solution's relative Frobenius error against the oracle's
+    complete solution (tests/golden/<name>_oracle_X.npz, written by an
+    oracle-only script; read, not run) and the truncation indices against the
+    oracle's; and the RT-tSVD alone in float32 and in the TF32 form."""
+    from paper_2110_02485_gb300 import synth
+    cfg = synth.CONFIGS[name]
+    P = synth.blur_problem(cfg, seed=cfg.seed)
+    A, B, Om = (torch.from_numpy(P[k]).cuda() for k in ("A", "B", "Omega"))
+    delta = P["delta"]
+
+    def step():
+        X1, i1, _ = tprod.rtsvd_solve(A, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                                      eps_rel=cfg.eps_rel, sync=False)
+        X2, i2, _ = tprod.tgkb_solve(A, B, delta, cfg.tau, cfg.k_max, sync=False)
+        X3, i3 = tprod.tgkt_solve(A, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False)
+        return (X1, X2, X3), (i1, i2, i3)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    tprod.timing_enable(tprod.KERNEL_CLASSES)
+    Xs, infos = step()
+    per_class = tprod.timing_read()
+    tprod.timing_enable([])
+    infos = [tprod._info_dict(x) for x in infos]
+    g = tprod.Captured(step, warmup=0)
+    g.replay()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    Xs, _ = g.outputs
+    out = {"workload": f"{name}: {cfg.N}x{cfg.N}x{cfg.N} blur (sigma {cfg.sigma:g}, band {cfg.band}, s {cfg.s:g}), "
+                       f"1 RHS, noise {cfg.noise:g}; one RT-tSVD + one tGKB + one Tikhonov-tGKB solve per step",
+           "solves_per_s": SOLVES_PER_STEP * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+           "kernels_per_step": g.launches,
+           "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
+           "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
+                          "tgkb": {k: infos[1][k] for k in ("k", "status")},
+                          "tgkt": {k: infos[2][k] for k in ("k", "status", "mu")}}}
+    gold_path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
+    sol_path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle_X.npz")
+    if os.path.exists(gold_path) and os.path.exists(sol_path):
+        with open(gold_path) as f:
+            gold = json.load(f)
+        sols = np.load(sol_path)
+        for m, X, inf in zip(("rtsvd", "tgkb", "tgkt"), Xs, infos):
+            x = X.cpu().numpy().astype(np.float64)
+            out["solve_info"][m]["rel_err_vs_oracle"] = float(np.linalg.norm(x - sols[m]) / np.linalg.norm(sols[m]))
+            out["solve_info"][m]["k_matches_oracle"] = inf["k"] == gold[m]["k"]
+    prec = precision_form(a, cfg, P, A, B, Om, flush, tprod, torch)
+    out["precision_form"] = prec
+    return out
+
+
+def hat_form(a, cfg, P, A, B, Om, flush, tprod, torch, steps=20):
+    """The "B-only" figure: the three solves of the step through the *_hat
+    entry points, with A-hat transformed once (tprod_fft) outside the timed
+    replays, so each solve starts from B (and Omega).  CUDA-graph replays, L2
+    flushed between them, CUDA events."""
+    n = A.shape[0]
+    Ah = tprod.fft(A)
+    delta = P["delta"]
+
+    def step():
+        X1, i1, _ = tprod.rtsvd_solve(None, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                                      eps_rel=cfg.eps_rel, sync=False, Ahat=Ah, n=n)
+        X2, i2, _ = tprod.tgkb_solve(None, B, delta, cfg.tau, cfg.k_max, sync=False, Ahat=Ah, n=n)
+        X3, i3 = tprod.tgkt_solve(None, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False, Ahat=Ah, n=n)
+        return (X1, X2, X3), (i1, i2, i3)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    g = tprod.Captured(step, warmup=0)
+    g.replay()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    infos = [tprod._info_dict(x) for x in g.outputs[1]]
+    return {"solves_per_s": SOLVES_PER_STEP * steps / (ms / 1e3), "ms_per_step": ms / steps,
+            "entry_points": "rtsvd_truncated_solve_hat, tgkb_solve_hat, tgkb_tikhonov_solve_hat",
+            "k": [i["k"] for i in infos], "status": [i["status"] for i in infos],
+            "note": "A-hat from one tprod_fft before the timed replays; every DFT of B and Omega, the sketch and "
+                    "every other step inside"}
 
 
 def differentiation_form(a, cfg, P, A, B, Om, flush, tprod, torch):
@@ -589,13 +702,15 @@ def batched_form(a, cfg, flush, tprod, torch, frames=32):
     r_max = min(cfg.r_max, 128)
     Om = Om[:, :, :r_max].contiguous()
 
+    tau = VIDEO_TAU
+
     def joint():
-        return tprod.rtsvd_solve(A, B, Om, Pm["delta"], cfg.tau, cfg.p_over, cfg.block, cfg.q_power, r_max,
+        return tprod.rtsvd_solve(A, B, Om, Pm["delta"], tau, cfg.p_over, cfg.block, cfg.q_power, r_max,
                                  eps_rel=cfg.eps_rel, res_hist=True, sync=False)
 
     def per_frame():
         d1 = Pm["delta"] / np.sqrt(frames)  # each frame's share of the noise norm
-        return [tprod.rtsvd_solve(A, b, Om, d1, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, r_max,
+        return [tprod.rtsvd_solve(A, b, Om, d1, tau, cfg.p_over, cfg.block, cfg.q_power, r_max,
                                   eps_rel=cfg.eps_rel, sync=False) for b in Bs]
 
     ms_j, (X, info, hist) = timed(joint)
@@ -606,15 +721,15 @@ def batched_form(a, cfg, flush, tprod, torch, frames=32):
                                          f"1 px per frame) as lateral slices, noise {cfg.noise:g} over all frames"}
     out["rtsvd"] = {"rhs_per_s": frames / (ms_j / 1e3), "ms_per_call": ms_j,
                     "per_frame_calls_rhs_per_s": frames / (ms_s / 1e3), "k": info["k"], "r": info["r"],
-                    "status": info["status"], "dp_met": bool(hist[info["k"]] <= cfg.tau * Pm["delta"])}
+                    "status": info["status"], "dp_met": bool(hist[info["k"]] <= tau * Pm["delta"])}
     # tGKB_p: every frame with its own bound delta_j = ||E_j||_F and its own k_j
     dj = [float(np.linalg.norm(Pm["B"][:, :, j].astype(np.float64) - Pm["B_true"][:, :, j])) for j in range(frames)]
 
     def gkb_joint():
-        return tprod.tgkb_solve(A, B, 0.0, cfg.tau, cfg.k_max, deltas=dj, res_hist=True, sync=False)
+        return tprod.tgkb_solve(A, B, 0.0, tau, cfg.k_max, deltas=dj, res_hist=True, sync=False)
 
     def gkb_per_frame():
-        return [tprod.tgkb_solve(A, b, d, cfg.tau, cfg.k_max, sync=False) for b, d in zip(Bs, dj)]
+        return [tprod.tgkb_solve(A, b, d, tau, cfg.k_max, sync=False) for b, d in zip(Bs, dj)]
 
     ms_gj, (_, ginfo, ghist) = timed(gkb_joint)
     ms_gs, _ = timed(gkb_per_frame)
@@ -622,7 +737,7 @@ def batched_form(a, cfg, flush, tprod, torch, frames=32):
     ghist = ghist.cpu().numpy()
     ks = [g["k"] for g in ginfo]
     def nested():
-        return tprod.nested_tgkb_solve(A, B, dj, cfg.tau, cfg.k_max, res_hist=True, sync=False)
+        return tprod.nested_tgkb_solve(A, B, dj, tau, cfg.k_max, res_hist=True, sync=False)
 
     ms_n, (_, ninfo, nhist) = timed(nested)
     ninfo = tprod._info_list(ninfo, frames)
@@ -630,11 +745,11 @@ def batched_form(a, cfg, flush, tprod, torch, frames=32):
     nk = [g["k"] for g in ninfo]
     out["nested_tgkb_p"] = {"rhs_per_s": frames / (ms_n / 1e3), "ms_per_call": ms_n, "k_final": max(nk),
                             "all_ok": all(g["status"] == 0 for g in ninfo),
-                            "projected_dp_met": all(nhist[j, nk[j]] < cfg.tau * dj[j] for j in range(frames))}
+                            "projected_dp_met": all(nhist[j, nk[j]] < tau * dj[j] for j in range(frames))}
     out["tgkb_p"] = {"rhs_per_s": frames / (ms_gj / 1e3), "ms_per_call": ms_gj,
                      "per_frame_calls_rhs_per_s": frames / (ms_gs / 1e3), "k_min": min(ks), "k_max": max(ks),
                      "all_ok": all(g["status"] == 0 for g in ginfo),
-                     "dp_met": all(ghist[j, ks[j]] <= cfg.tau * dj[j] for j in range(frames))}
+                     "dp_met": all(ghist[j, ks[j]] <= tau * dj[j] for j in range(frames))}
     return out
 
 
@@ -646,11 +761,12 @@ def uneven_form(a, flush, tprod, torch, count=16):
     from paper_2110_02485_gb300 import synth
     probs = synth.uneven_problems(count)
     dev = [{k: torch.from_numpy(p[k]).cuda() for k in ("A", "B", "Omega")} for p in probs]
-    tau, p_over, q, b, eps_rel, k_max = 1.1, 10, 1, 16, 3e-2, 100
+    tau, p_over, q, b, k_max = synth.UNEVEN_TAU, synth.UNEVEN_P_OVER, synth.UNEVEN_Q, synth.UNEVEN_BLOCK, \
+        synth.UNEVEN_KMAX
 
     def solve(p, d):
         _, i1, _ = tprod.rtsvd_solve(d["A"], d["B"], d["Omega"], p["delta"], tau, p_over, b, q, p["r_max"],
-                                     eps_rel=eps_rel, sync=False)
+                                     eps_rel=p["eps_rel"], sync=False)
         _, i2, _ = tprod.tgkb_solve(d["A"], d["B"], p["delta"], tau, min(k_max, p["N"]), sync=False)
         return i1, i2
 
@@ -693,7 +809,11 @@ def uneven_form(a, flush, tprod, torch, count=16):
             "rtsvd_status": [i1["status"] for i1, _ in infos], "rtsvd_k": [i1["k"] for i1, _ in infos],
             "tgkb_status": [i2["status"] for _, i2 in infos], "tgkb_k": [i2["k"] for _, i2 in infos],
             "workload": "16 problems, N drawn from {64,96,128,192,256,320,384}, blur sigma 2.5 band 8 s 3, "
-                        "noise 1e-2; RT-tSVD p=10 q=1 b=16 r_max=min(N,96) eps_rel=3e-2, tGKB k_max=min(N,100)"}
+                        "noise 1e-2; RT-tSVD p=10 q=1 b=16 r_max=min(N,160), eps_rel per problem (the largest "
+                        "grid value 10^(-j/10) meeting the discrepancy principle within [r-p, r]), "
+                        "tGKB k_max=min(N,100)",
+            "rtsvd_all_converged": all(i1["status"] == 0 for i1, _ in infos),
+            "tgkb_all_converged": all(i2["status"] == 0 for _, i2 in infos)}
 
 
 def oracle_solve(method, cfg, P):

@@ -51,7 +51,9 @@ typedef enum {
     TP_ERR_BREAKDOWN = -4,      /* reserved: exact breakdown reported by a solver      */
     TP_ERR_NOT_CONVERGED = -5,  /* discrepancy principle not met within r_max / k_max  */
     TP_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up                  */
-    TP_ERR_UNSUPPORTED = -7     /* valid request outside what this build supports      */
+    TP_ERR_UNSUPPORTED = -7,    /* valid request outside what this build supports      */
+    TP_ERR_NONFINITE = -8       /* A or B holds a NaN or an infinity (from the norms    */
+                                /* the DFTs form); the solution is then meaningless     */
 } tp_status;
 
 /* Arithmetic precision of a call.
@@ -175,6 +177,20 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
                                 int l, int m, int n, int p, const tp_rtsvd_params* params,
                                 void* X, tp_info* d_info, int prec,
                                 void* ws, size_t ws_bytes, void* stream);
+/* rtsvd_truncated_solve_hat: the same solve from a precomputed half spectrum of A
+ * (Section 2: every t-operation acts on the Fourier slices A-hat^(s)), so
+ * that several solves with one operator transform it once (tprod_fft).
+ * Ahat: device, (h = n/2+1, l, m) interleaved complex (complex64 for FP32 and
+ * TF32, complex128 for FP64), 16-byte aligned, the layout tprod_fft writes;
+ * read only, owned by the caller, and valid until the solve's work on the
+ * stream is done.  Every other argument, the workspace size (the
+ * *_workspace_bytes query) and the results are those of the plain call; the
+ * solve forms ||A||_F^2 from A-hat by Parseval where it needs it (one
+ * reduction over A-hat).  A null Ahat returns TP_ERR_ARG. */
+tp_status rtsvd_truncated_solve_hat(const void* Ahat, const void* B, const void* Omega,
+                                    int l, int m, int n, int p, const tp_rtsvd_params* params,
+                                    void* X, tp_info* d_info, int prec,
+                                    void* ws, size_t ws_bytes, void* stream);
 
 /* rtsvd_adjoint: the adjoint of the map B -> X_k of the last
  * rtsvd_truncated_solve made with this workspace and the same arguments
@@ -267,6 +283,19 @@ size_t tgkb_workspace_bytes(int l, int m, int n, int p, const tp_tgkb_params* pa
 tp_status tgkb_solve(const void* A, const void* B, int l, int m, int n, int p,
                      const tp_tgkb_params* params, void* X, tp_info* d_info, int prec,
                      void* ws, size_t ws_bytes, void* stream);
+/* tgkb_solve_hat: the same solve from a precomputed half spectrum of A
+ * (Section 2: every t-operation acts on the Fourier slices A-hat^(s)), so
+ * that several solves with one operator transform it once (tprod_fft).
+ * Ahat: device, (h = n/2+1, l, m) interleaved complex (complex64 for FP32 and
+ * TF32, complex128 for FP64), 16-byte aligned, the layout tprod_fft writes;
+ * read only, owned by the caller, and valid until the solve's work on the
+ * stream is done.  Every other argument, the workspace size (the
+ * *_workspace_bytes query) and the results are those of the plain call; the
+ * solve forms ||A||_F^2 from A-hat by Parseval where it needs it (one
+ * reduction over A-hat).  A null Ahat returns TP_ERR_ARG. */
+tp_status tgkb_solve_hat(const void* Ahat, const void* B, int l, int m, int n, int p,
+                         const tp_tgkb_params* params, void* X, tp_info* d_info, int prec,
+                         void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------ nested_tGKB_p ----
  * nested_tgkb_solve: the nested_tGKB_p method (Algorithm 6) for p lateral
@@ -327,6 +356,19 @@ size_t tgkb_tikhonov_workspace_bytes(int l, int m, int n, int p, const tp_tik_pa
 tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n, int p,
                               const tp_tik_params* params, void* X, tp_info* d_info, int prec,
                               void* ws, size_t ws_bytes, void* stream);
+/* tgkb_tikhonov_solve_hat: the same solve from a precomputed half spectrum of A
+ * (Section 2: every t-operation acts on the Fourier slices A-hat^(s)), so
+ * that several solves with one operator transform it once (tprod_fft).
+ * Ahat: device, (h = n/2+1, l, m) interleaved complex (complex64 for FP32 and
+ * TF32, complex128 for FP64), 16-byte aligned, the layout tprod_fft writes;
+ * read only, owned by the caller, and valid until the solve's work on the
+ * stream is done.  Every other argument, the workspace size (the
+ * *_workspace_bytes query) and the results are those of the plain call; the
+ * solve forms ||A||_F^2 from A-hat by Parseval where it needs it (one
+ * reduction over A-hat).  A null Ahat returns TP_ERR_ARG. */
+tp_status tgkb_tikhonov_solve_hat(const void* Ahat, const void* B, int l, int m, int n, int p,
+                                  const tp_tik_params* params, void* X, tp_info* d_info, int prec,
+                                  void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------ gradients in the tube weights -------
  * For a separable operator A(:,:,k) = c_k T (one fixed l x m matrix T, tube
@@ -382,6 +424,25 @@ tp_status tgkb_tikhonov_grad_c(const void* G, const double* c, int l, int m, int
 const char* tp_status_string(int status);
 int tp_version(void);                 /* 100 * major + minor                        */
 int tp_kernel_launches(void);         /* kernels enqueued by this library so far    */
+/* tp_wait_budget: the bound, in SM clock cycles, of every device-side wait for
+ * progress in kernels launched after the call: the grid-wide waits of the
+ * persistent tGKB kernels (Algorithm 4; default about 2 s) and the mbarrier
+ * waits of the tensor-core product (default about 1 s).  0 restores the
+ * defaults; a negative value returns TP_ERR_ARG.  A wait that runs out makes
+ * its kernel stop its loop, drain the copies and tensor-core operations it
+ * has in flight (those drains keep their own bound) and report TP_ERR_TIMEOUT
+ * in the solve's tp_info; the context stays usable.  It exists for
+ * failure-detection tests: a budget of a few cycles makes the waits run out
+ * on purpose.  Process-wide; not meant to change while launches are being
+ * enqueued from other threads. */
+int tp_wait_budget(long long cycles);
+/* tp_wait_stall: with on = 1, the grid-wide waits of the persistent tGKB
+ * kernels launched after the call wait for one arrival more than their grid
+ * makes, so that every such wait runs out after its budget (an arrival that
+ * nothing makes); on = 0 restores normal waits.  For failure-detection tests
+ * only, together with a short tp_wait_budget; the kernels then stop, report
+ * TP_ERR_TIMEOUT and leave the context usable.  Process-wide. */
+int tp_wait_stall(int on);
 
 /* Optional device timing per kernel class, for benchmarks (off by default).
  * tp_timing_enable(mask): bit c of mask enables class c; every later launch

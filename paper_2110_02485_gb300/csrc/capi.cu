@@ -1,3 +1,4 @@
+#include <atomic>
 // extern "C" entry points of libtprod (declared in include/tprod.h).
 #include "common.cuh"
 #include "internal.h"
@@ -7,6 +8,37 @@
 #include <vector>
 
 namespace tp {
+
+std::atomic<long long> g_wait_budget{0};
+std::atomic<int> g_wait_stall{0};
+
+long long wait_budget(long long dflt) {
+    const long long v = g_wait_budget.load();
+    return v > 0 ? v : dflt;
+}
+
+int wait_stall() { return g_wait_stall.load(); }
+
+__global__ void k_info_nonfinite(const double* pa, int na, const double* pb, int nb, tp_info* info, int cnt) {
+    __shared__ double red[33];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < na; i += blockDim.x) a += pa[i];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += pb[i];
+    a = block_sum_t(a, red);
+    if (isfinite(a)) return;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        info[j].status = TP_ERR_NONFINITE;
+        info[j].residual = __longlong_as_double(0x7ff8000000000000LL);  // NaN
+    }
+}
+
+tp_status info_nonfinite(const double* partsA, int nA, const double* partsB, int nB, tp_info* info, int cnt,
+                         cudaStream_t st) {
+    prof_begin(TP_KC_MISC, st);
+    k_info_nonfinite<<<1, 256, 0, st>>>(partsA, nA, partsB, nB, info, cnt);
+    return launched(TP_KC_MISC, st);
+}
+
 
 int g_launches = 0;
 
@@ -79,7 +111,7 @@ tp_status smem_optin(const void* kern, size_t bytes) {
 template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_params*);
 template <typename T>
 tp_status rt_solve(const T*, const T*, const T*, int, int, int, int, const tp_rtsvd_params*, T*, tp_info*, void*,
-                   size_t, cudaStream_t, int);
+                   size_t, cudaStream_t, int, const void*);
 template <typename T>
 tp_status rt_adjoint(const T*, int, int, int, int, const tp_rtsvd_params*, T*, void*, size_t, cudaStream_t);
 template <typename T> size_t tt_ws_bytes(int, int, int, int, const tp_ttsvd_params*);
@@ -91,7 +123,7 @@ tp_status tt_solve(const T*, const T*, int, int, int, int, const tp_ttsvd_params
 template <typename T> size_t gk_ws_bytes(int, int, int, int, const tp_tgkb_params*);
 template <typename T>
 tp_status gk_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
-                   cudaStream_t);
+                   cudaStream_t, const void*);
 template <typename T> size_t gkn_ws_bytes(int, int, int, int, const tp_tgkb_params*);
 template <typename T>
 tp_status gkn_solve(const T*, const T*, int, int, int, int, const tp_tgkb_params*, T*, tp_info*, void*, size_t,
@@ -102,7 +134,7 @@ tp_status tri_solve(const T*, const T*, int, int, int, int, T*, T*, T*, void*, s
 template <typename T> size_t tik_ws_bytes(int, int, int, int, const tp_tik_params*);
 template <typename T>
 tp_status tik_solve(const T*, const T*, int, int, int, int, const tp_tik_params*, T*, tp_info*, void*, size_t,
-                    cudaStream_t);
+                    cudaStream_t, const void*);
 
 static bool dims_ok(int l, int m, int n, int prec) {
     if (l < 1 || m < 1 || n < 1) return false;
@@ -203,10 +235,25 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == TP_FP32 || prec == TP_TF32)
         return rt_solve<float>((const float*)A, (const float*)B, (const float*)Omega, l, m, n, p, params, (float*)X,
-                               d_info, ws, ws_bytes, st, prec == TP_TF32 ? 1 : 3);
+                               d_info, ws, ws_bytes, st, prec == TP_TF32 ? 1 : 3, nullptr);
     if (prec == TP_FP64)
         return rt_solve<double>((const double*)A, (const double*)B, (const double*)Omega, l, m, n, p, params,
-                                (double*)X, d_info, ws, ws_bytes, st, 3);
+                                (double*)X, d_info, ws, ws_bytes, st, 3, nullptr);
+    return TP_ERR_ARG;
+}
+
+
+tp_status rtsvd_truncated_solve_hat(const void* Ahat, const void* B, const void* Omega, int l, int m, int n, int p,
+                                    const tp_rtsvd_params* params, void* X, tp_info* d_info, int prec, void* ws,
+                                    size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!Ahat) return TP_ERR_ARG;
+    if (prec == TP_FP32 || prec == TP_TF32)
+        return rt_solve<float>(nullptr, (const float*)B, (const float*)Omega, l, m, n, p, params, (float*)X, d_info,
+                               ws, ws_bytes, st, prec == TP_TF32 ? 1 : 3, Ahat);
+    if (prec == TP_FP64)
+        return rt_solve<double>(nullptr, (const double*)B, (const double*)Omega, l, m, n, p, params, (double*)X,
+                                d_info, ws, ws_bytes, st, 3, Ahat);
     return TP_ERR_ARG;
 }
 
@@ -257,10 +304,23 @@ tp_status tgkb_solve(const void* A, const void* B, int l, int m, int n, int p, c
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == TP_FP32)
         return gk_solve<float>((const float*)A, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws, ws_bytes,
-                               st);
+                               st, nullptr);
     if (prec == TP_FP64)
         return gk_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
-                                ws_bytes, st);
+                                ws_bytes, st, nullptr);
+    return TP_ERR_ARG;
+}
+
+tp_status tgkb_solve_hat(const void* Ahat, const void* B, int l, int m, int n, int p, const tp_tgkb_params* params,
+                         void* X, tp_info* d_info, int prec, void* ws, size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!Ahat) return TP_ERR_ARG;
+    if (prec == TP_FP32)
+        return gk_solve<float>(nullptr, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws, ws_bytes, st,
+                               Ahat);
+    if (prec == TP_FP64)
+        return gk_solve<double>(nullptr, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws, ws_bytes, st,
+                                Ahat);
     return TP_ERR_ARG;
 }
 
@@ -311,10 +371,24 @@ tp_status tgkb_tikhonov_solve(const void* A, const void* B, int l, int m, int n,
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == TP_FP32)
         return tik_solve<float>((const float*)A, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws,
-                                ws_bytes, st);
+                                ws_bytes, st, nullptr);
     if (prec == TP_FP64)
         return tik_solve<double>((const double*)A, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws,
-                                 ws_bytes, st);
+                                 ws_bytes, st, nullptr);
+    return TP_ERR_ARG;
+}
+
+tp_status tgkb_tikhonov_solve_hat(const void* Ahat, const void* B, int l, int m, int n, int p,
+                                  const tp_tik_params* params, void* X, tp_info* d_info, int prec, void* ws,
+                                  size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!Ahat) return TP_ERR_ARG;
+    if (prec == TP_FP32)
+        return tik_solve<float>(nullptr, (const float*)B, l, m, n, p, params, (float*)X, d_info, ws, ws_bytes, st,
+                                Ahat);
+    if (prec == TP_FP64)
+        return tik_solve<double>(nullptr, (const double*)B, l, m, n, p, params, (double*)X, d_info, ws, ws_bytes, st,
+                                 Ahat);
     return TP_ERR_ARG;
 }
 
@@ -370,6 +444,7 @@ const char* tp_status_string(int status) {
         case TP_ERR_NOT_CONVERGED: return "discrepancy principle not met within the cap";
         case TP_ERR_TIMEOUT: return "bounded device-side wait gave up";
         case TP_ERR_UNSUPPORTED: return "request not supported by this build or device";
+        case TP_ERR_NONFINITE: return "input holds a NaN or an infinity";
         default: return "unknown status";
     }
 }
@@ -377,6 +452,18 @@ const char* tp_status_string(int status) {
 int tp_version(void) { return 100; }
 
 int tp_kernel_launches(void) { return g_launches; }
+
+int tp_wait_budget(long long cycles) {
+    if (cycles < 0) return TP_ERR_ARG;
+    tp::g_wait_budget.store(cycles);
+    return TP_OK;
+}
+
+int tp_wait_stall(int on) {
+    if (on != 0 && on != 1) return TP_ERR_ARG;
+    tp::g_wait_stall.store(on);
+    return TP_OK;
+}
 
 int tp_timing_enable(int class_mask) {
     g_mask = class_mask & ((1 << TP_KC_COUNT) - 1);

@@ -512,6 +512,38 @@ tp_status irdft(const void* Xh, T* X, int n, int rows, int cols, long ld, long s
     return launched(TP_KC_DFT, st);
 }
 
+// ||X||_F^2 from a half spectrum (h = n/2 + 1 slices of rows x cols), in the
+// same rdft_parts(rows, cols) partial sums the forward transform writes:
+// Parseval, (1/n) sum_s w_s ||X-hat_s||^2.  Partial b covers the entries
+// DFT_TILE b .. DFT_TILE (b+1) - 1 of every slice; the 256 threads of its CTA
+// take the 32 entries of eight slices at a time (their loads independent), and
+// the sum runs in a fixed order (per thread in the working precision, across
+// threads in float64).
+template <typename T>
+__global__ void __launch_bounds__(256) k_norm2_hat(const cplx<T>* __restrict__ Xh, int n, int h, long rc, int nparts,
+                                                   double* parts) {
+    __shared__ double red[33];
+    const int b = blockIdx.x, t = threadIdx.x & (DFT_TILE - 1), g = threadIdx.x / DFT_TILE;
+    const int ng = blockDim.x / DFT_TILE;
+    const long e = (long)b * DFT_TILE + t;
+    double acc = 0.0;
+    if (e < rc)
+#pragma unroll 4
+        for (int s = g; s < h; s += ng) acc += parseval_w(s, n) * (double)cabs2(__ldg(Xh + (long)s * rc + e));
+    acc = block_sum_t(acc, red);
+    if (threadIdx.x == 0) parts[b] = acc / (double)n;
+}
+
+template <typename T>
+tp_status norm2_hat(const void* Xh, int n, int rows, int cols, double* parts, cudaStream_t st) {
+    const int np = rdft_parts(rows, cols), h = n / 2 + 1;
+    prof_begin(TP_KC_DFT, st);
+    k_norm2_hat<T><<<np, 256, 0, st>>>((const cplx<T>*)Xh, n, h, (long)rows * cols, np, parts);
+    return launched(TP_KC_DFT, st);
+}
+template tp_status norm2_hat<float>(const void*, int, int, int, double*, cudaStream_t);
+template tp_status norm2_hat<double>(const void*, int, int, int, double*, cudaStream_t);
+
 template tp_status rdft<float>(const float*, void*, int, int, int, long, long, double*, const int*, cudaStream_t);
 template tp_status rdft<double>(const double*, void*, int, int, int, long, long, double*, const int*, cudaStream_t);
 template tp_status irdft<float>(const void*, float*, int, int, int, long, long, const int*, cudaStream_t);

@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2)
 k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l, int m, int n, int h, int k_max,
       double tau_delta, cplx<T>* Wb, cplx<T>* Qb, T* cc, T* zz, double* res2, unsigned* counters,
       cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info, int kc,
-      int bs) {
+      int bs, int extra) {
     // bs: column stride of Bhat and Xhat (the lateral slice count of B; the
     // pointers already point at this slice's column)
     typedef cplx<T> V;
@@ -434,7 +434,7 @@ k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l,
             if (tid == 0) {
                 // wait for every slice to finish step i-1 (bounded)
                 const long long t0 = clock64();
-                while (ld_acquire(&counters[i - 1]) < (unsigned)h) {
+                while (ld_acquire(&counters[i - 1]) < (unsigned)(h + extra)) {
                     if (clock64() - t0 > spin_cycles) {
                         flag_timeout = 1;
                         break;
@@ -583,6 +583,7 @@ struct GknArgs {
     tp_info* info;        // p records
     double* res_hist;     // optional (p, k_max+1)
     long long spin;
+    int extra;            // arrivals awaited beyond the grid (0; 1 under tp_wait_stall)
     int l, m, n, h, k_max, p, k_init;
 };
 
@@ -740,7 +741,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2) k_gkb_nested(const Gkn
                 a.res2[(long)S.e * h + s] = ws * (S.orphan + pb.x * pb.x + pb.y * pb.y);
                 asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.counters[S.e]) : "memory");
                 const long long t0 = clock64();
-                while (ld_acquire(&a.counters[S.e]) < (unsigned)h) {
+                while (ld_acquire(&a.counters[S.e]) < (unsigned)(h + a.extra)) {
                     if (clock64() - t0 > a.spin) {
                         S.timeout = 1;
                         break;
@@ -1169,6 +1170,8 @@ struct GkWs {
     double *res2, *fout;
     T *cc, *zz, *tout, *lam, *tscr;
     double* gv;  // Givens data of the batched kernel (p > 1)
+    double *partsA, *partsB;  // squared-norm partials of the DFTs of A and B (non-finite input check)
+    int nA, nB;
     cplx<T> *Ahat, *Bhat, *W, *Q, *Xhat;
     size_t bytes;
 };
@@ -1193,6 +1196,10 @@ static GkWs<T> gk_carve(void* base, int l, int m, int n, int k_max, int p) {
     w.lam = c.take<T>(TIK_P);
     w.tscr = c.take<T>((long)TIK_P * h * 4 * k_max);
     w.gv = p > 1 ? c.take<double>(h * pb * 3 * k_max) : nullptr;
+    w.nA = rdft_parts(l, m);
+    w.nB = rdft_parts(l, p);
+    w.partsA = c.take<double>(w.nA);
+    w.partsB = c.take<double>(w.nB);
     w.Ahat = c.take<V>(h * l * m);
     w.Bhat = c.take<V>(h * l * p);
     w.W = c.take<V>(h * pb * k_max * m);
@@ -1226,6 +1233,18 @@ size_t gk_ws_bytes(int l, int m, int n, int p, const tp_tgkb_params* P) {
         tp_status _e = (x);         \
         if (_e != TP_OK) return _e; \
     } while (0)
+
+// A-hat for a tGKB solve: the DFT of A into the workspace, or the caller's
+// half spectrum (read only; ||A||^2 from it by Parseval for the non-finite
+// input check).
+template <typename T>
+static tp_status gk_ahat(const T* A, const void* Ahat_in, int l, int m, int n, GkWs<T>& w, cudaStream_t st) {
+    if (Ahat_in) {
+        w.Ahat = (cplx<T>*)Ahat_in;
+        return norm2_hat<T>(Ahat_in, n, l, m, w.partsA, st);
+    }
+    return rdft<T>(A, w.Ahat, n, l, m, m, (long)l * m, w.partsA, nullptr, st);
+}
 
 // One single-slice tGKB launch: column bs-strided B-hat of one lateral slice
 // (Bhat_j, already offset) to its X-hat column (Xhat_j).
@@ -1264,11 +1283,11 @@ static tp_status gk_single(const GkWs<T>& w, const cplx<T>* Bhat_j, cplx<T>* Xha
     if (!coop || (long)per_sm * nsm < h) return TP_ERR_UNSUPPORTED;
     const cplx<T>* Ahat = w.Ahat;
     int l_ = l, m_ = m, n_ = n, h_ = h, k_ = k_max, wi = write_info, bs_ = bs;
-    long long spin = 4000000000LL;  // ~2 s at the GB300 SM clock
-    int kc_ = kc;
+    long long spin = wait_budget(4000000000LL);  // ~2 s at the GB300 SM clock
+    int kc_ = kc, extra_ = wait_stall();
     void* args[] = {(void*)&Ahat, (void*)&Bhat_j, &l_, &m_, &n_, &h_, &k_, &td, (void*)&w.W, (void*)&w.Q,
                     (void*)&w.cc, (void*)&w.zz, (void*)&w.res2, (void*)&w.counters, (void*)&Xhat_j,
-                    (void*)&w.st, (void*)&info, (void*)&res_hist, &spin, &wi, &kc_, &bs_};
+                    (void*)&w.st, (void*)&info, (void*)&res_hist, &spin, &wi, &kc_, &bs_, &extra_};
     prof_begin(TP_KC_GKB, st);
     if (cudaLaunchCooperativeKernel(kern, dim3(h), dim3(nt), args, smem, st) != cudaSuccess)
         return TP_ERR_CUDA;
@@ -1277,10 +1296,9 @@ static tp_status gk_single(const GkWs<T>& w, const cplx<T>* Bhat_j, cplx<T>* Xha
 
 template <typename T>
 static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tgkb_params* P, GkWs<T>& w,
-                        tp_info* info, int write_info, cudaStream_t st) {
-    const long lm = (long)l * m;
-    TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, nullptr, nullptr, st));
-    TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, nullptr, nullptr, st));
+                        tp_info* info, int write_info, cudaStream_t st, const void* Ahat_in = nullptr) {
+    TRY(gk_ahat<T>(A, Ahat_in, l, m, n, w, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, 1, 1, l, w.partsB, nullptr, st));
     return gk_single<T>(w, w.Bhat, w.Xhat, 1, l, m, n, P->k_max, P->tau * P->delta, info, P->res_hist, write_info,
                         st);
 }
@@ -1290,10 +1308,10 @@ static tp_status gk_run(const T* A, const T* B, int l, int m, int n, const tp_tg
 // the batched kernel does not take run one single-slice launch per slice.
 template <typename T>
 static tp_status gk_run_p(const T* A, const T* B, int l, int m, int n, int p, const tp_tgkb_params* P, GkWs<T>& w,
-                          tp_info* info, cudaStream_t st) {
+                          tp_info* info, cudaStream_t st, const void* Ahat_in = nullptr) {
     const int h = n / 2 + 1, k_max = P->k_max;
-    TRY(rdft<T>(A, w.Ahat, n, l, m, m, (long)l * m, nullptr, nullptr, st));
-    TRY(rdft<T>(B, w.Bhat, n, l, p, p, (long)l * p, nullptr, nullptr, st));
+    TRY(gk_ahat<T>(A, Ahat_in, l, m, n, w, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, p, p, (long)l * p, w.partsB, nullptr, st));
     auto td_of = [&](int j) { return P->tau * (P->delta_p ? P->delta_p[j] : P->delta); };
     int nt = 0;
     size_t smem = 0;
@@ -1311,7 +1329,8 @@ static tp_status gk_run_p(const T* A, const T* B, int l, int m, int n, int p, co
             a.counters = w.counters;
             a.info = info;
             a.res_hist = P->res_hist;
-            a.spin = 4000000000LL;  // ~2 s at the GB300 SM clock
+            a.spin = wait_budget(4000000000LL);  // ~2 s at the GB300 SM clock
+            a.extra = wait_stall();
             a.l = l;
             a.m = m;
             a.n = n;
@@ -1340,13 +1359,14 @@ static tp_status gk_run_p(const T* A, const T* B, int l, int m, int n, int p, co
 
 template <typename T>
 tp_status gk_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_tgkb_params* P, T* X,
-                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st, const void* Ahat) {
     TRY(gk_check<T>(l, m, n, p, P));
-    if (!A || !B || !X || !info) return TP_ERR_ARG;
+    if ((!A && !Ahat) || !B || !X || !info || ((size_t)Ahat & 15)) return TP_ERR_ARG;
     GkWs<T> w = gk_carve<T>(ws, l, m, n, P->k_max, p);
     if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
-    if (p == 1) TRY(gk_run<T>(A, B, l, m, n, P, w, info, 1, st));
-    else TRY(gk_run_p<T>(A, B, l, m, n, p, P, w, info, st));
+    if (p == 1) TRY(gk_run<T>(A, B, l, m, n, P, w, info, 1, st, Ahat));
+    else TRY(gk_run_p<T>(A, B, l, m, n, p, P, w, info, st, Ahat));
+    TRY(info_nonfinite(w.partsA, w.nA, w.partsB, w.nB, info, p, st));
     TRY(irdft<T>(w.Xhat, X, n, m, p, p, (long)m * p, nullptr, st));
     return TP_OK;
 }
@@ -1356,6 +1376,8 @@ template <typename T>
 struct GknWs {
     unsigned* counters;
     double *res2, *phi, *rot, *td;
+    double *partsA, *partsB;  // squared-norm partials of the DFTs (non-finite input check)
+    int nA, nB;
     cplx<T> *Ahat, *Bhat, *W, *Q, *Xhat;
     size_t bytes;
 };
@@ -1371,6 +1393,10 @@ static GknWs<T> gkn_carve(void* base, int l, int m, int n, int k_max, int p) {
     w.phi = c.take<double>(h * k_max * 2);
     w.rot = c.take<double>(h * k_max * 3);
     w.td = c.take<double>(p);
+    w.nA = rdft_parts(l, m);
+    w.nB = rdft_parts(l, p);
+    w.partsA = c.take<double>(w.nA);
+    w.partsB = c.take<double>(w.nB);
     w.Ahat = c.take<V>(h * l * m);
     w.Bhat = c.take<V>(h * l * p);
     w.W = c.take<V>(h * (long)k_max * m);
@@ -1426,8 +1452,8 @@ tp_status gkn_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
         k_fill_td<<<1, 128, 0, st>>>(w.td + j0, c, cnt);
         TRY(launched(TP_KC_MISC, st));
     }
-    TRY(rdft<T>(A, w.Ahat, n, l, m, m, (long)l * m, nullptr, nullptr, st));
-    TRY(rdft<T>(B, w.Bhat, n, l, p, p, (long)l * p, nullptr, nullptr, st));
+    TRY(rdft<T>(A, w.Ahat, n, l, m, m, (long)l * m, w.partsA, nullptr, st));
+    TRY(rdft<T>(B, w.Bhat, n, l, p, p, (long)l * p, w.partsB, nullptr, st));
     GknArgs g;
     g.Ahat = w.Ahat;
     g.Bhat = w.Bhat;
@@ -1441,7 +1467,8 @@ tp_status gkn_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     g.td = w.td;
     g.info = info;
     g.res_hist = P->res_hist;
-    g.spin = 4000000000LL;  // ~2 s at the GB300 SM clock
+    g.spin = wait_budget(4000000000LL);  // ~2 s at the GB300 SM clock
+    g.extra = wait_stall();
     g.l = l;
     g.m = m;
     g.n = n;
@@ -1453,6 +1480,7 @@ tp_status gkn_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     prof_begin(TP_KC_GKB, st);
     if (cudaLaunchCooperativeKernel(kern, dim3(h), dim3(nt), args, smem, st) != cudaSuccess) return TP_ERR_CUDA;
     TRY(launched(TP_KC_GKB, st));
+    TRY(info_nonfinite(w.partsA, w.nA, w.partsB, w.nB, info, p, st));
     return irdft<T>(w.Xhat, X, n, m, p, p, (long)m * p, nullptr, st);
 }
 
@@ -1579,14 +1607,14 @@ size_t tik_ws_bytes(int l, int m, int n, int p, const tp_tik_params* P) {
 
 template <typename T>
 tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp_tik_params* P, T* X,
-                    tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+                    tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st, const void* Ahat) {
     if (!P || p != 1) return TP_ERR_ARG;
     TRY(gk_check<T>(l, m, n, p, &P->gkb));
     if (!(P->mu_lo > 0.0) || !(P->mu_hi > P->mu_lo)) return TP_ERR_ARG;
-    if (!A || !B || !X || !info) return TP_ERR_ARG;
+    if ((!A && !Ahat) || !B || !X || !info || ((size_t)Ahat & 15)) return TP_ERR_ARG;
     GkWs<T> w = gk_carve<T>(ws, l, m, n, P->gkb.k_max, 1);
     if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
-    TRY(gk_run<T>(A, B, l, m, n, &P->gkb, w, info, 0, st));
+    TRY(gk_run<T>(A, B, l, m, n, &P->gkb, w, info, 0, st, Ahat));
     const int h = n / 2 + 1, k_max = P->gkb.k_max;
     const double lo = log10(P->mu_lo), hi = log10(P->mu_hi);
     const double tol = P->log_tol > 0.0 ? P->log_tol : 1e-12;
@@ -1612,6 +1640,7 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     prof_begin(TP_KC_TIK, st);
     k_tik_info<<<1, 32, 0, st>>>(w.fout, h, n, w.st, w.ts, td, info);
     TRY(launched(TP_KC_TIK, st));
+    TRY(info_nonfinite(w.partsA, w.nA, w.partsB, w.nB, info, 1, st));
     TRY(irdft<T>(w.Xhat, X, n, m, 1, 1, m, nullptr, st));
     return TP_OK;
 }
@@ -1743,12 +1772,12 @@ template tp_status gkn_solve<double>(const double*, const double*, int, int, int
 template size_t tik_ws_bytes<float>(int, int, int, int, const tp_tik_params*);
 template size_t tik_ws_bytes<double>(int, int, int, int, const tp_tik_params*);
 template tp_status gk_solve<float>(const float*, const float*, int, int, int, int, const tp_tgkb_params*, float*,
-                                   tp_info*, void*, size_t, cudaStream_t);
+                                   tp_info*, void*, size_t, cudaStream_t, const void*);
 template tp_status gk_solve<double>(const double*, const double*, int, int, int, int, const tp_tgkb_params*,
-                                    double*, tp_info*, void*, size_t, cudaStream_t);
+                                    double*, tp_info*, void*, size_t, cudaStream_t, const void*);
 template tp_status tik_solve<float>(const float*, const float*, int, int, int, int, const tp_tik_params*, float*,
-                                    tp_info*, void*, size_t, cudaStream_t);
+                                    tp_info*, void*, size_t, cudaStream_t, const void*);
 template tp_status tik_solve<double>(const double*, const double*, int, int, int, int, const tp_tik_params*,
-                                     double*, tp_info*, void*, size_t, cudaStream_t);
+                                     double*, tp_info*, void*, size_t, cudaStream_t, const void*);
 
 }  // namespace tp

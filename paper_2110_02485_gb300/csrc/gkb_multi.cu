@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(NT, 1) k_gkb_multi(const GkmArgs a) {
         if (i >= 2) {
             if (tid == 0) {
                 const long long t0 = clock64();
-                while (ld_acquire(&a.counters[i - 1]) < (unsigned)h) {
+                while (ld_acquire(&a.counters[i - 1]) < (unsigned)(h + a.extra)) {
                     if (clock64() - t0 > a.spin) {
                         flag_timeout = 1;
                         break;

@@ -20,6 +20,19 @@ void prof_end(int cls, cudaStream_t st);
 // Opt a kernel into `bytes` of dynamic shared memory.  Always needed when
 // static + dynamic shared memory exceeds 48 KB; cached per kernel.
 tp_status smem_optin(const void* kern, size_t bytes);
+// Bound of the waits for progress (grid-wide waits of the persistent tGKB
+// kernels, mbarrier waits of the tensor-core product), in SM clock cycles:
+// `dflt` unless tp_wait_budget set another.  Drains of work already in flight
+// keep their own bound.
+long long wait_budget(long long dflt);
+// 1 when tp_wait_stall asked the grid-wide waits to wait for one arrival more
+// than the grid makes (failure-detection tests), else 0.
+int wait_stall();
+// After a solve whose DFTs wrote norm partials of A and B: a NaN or infinity
+// in either sum marks every one of the cnt info records TP_ERR_NONFINITE
+// (residual NaN).  One small launch.
+tp_status info_nonfinite(const double* partsA, int nA, const double* partsB, int nB, tp_info* info, int cnt,
+                         cudaStream_t st);
 
 inline tp_status launched(int cls, cudaStream_t st) {
     ++g_launches;
@@ -38,6 +51,10 @@ template <typename T>
 tp_status irdft(const void* Xh, T* X, int n, int rows, int cols, long ld, long ss,
                 const int* skip, cudaStream_t st);
 int rdft_parts(int rows, int cols);
+// ||X||_F^2 of the tensor whose half spectrum (n/2+1, rows, cols) is Xh, as the
+// rdft_parts(rows, cols) partial sums that rdft writes for X (Parseval).
+template <typename T>
+tp_status norm2_hat(const void* Xh, int n, int rows, int cols, double* parts, cudaStream_t st);
 size_t rdft_smem(int n, size_t elem);
 
 // Batched complex matrix product over slices:
@@ -87,6 +104,7 @@ struct GkmArgs {
     tp_info* info;
     double* res_hist;
     long long spin;  // bound of each grid-wide wait, in SM clock cycles
+    int extra;       // arrivals awaited beyond the grid (0; 1 under tp_wait_stall)
     int l, m, n, h, k_max, p, j0, pb;
     double td[GKM_PB];    // tau * delta_j
     double td2n[GKM_PB];  // n (tau delta_j)^2, compared with the Parseval sums
@@ -109,7 +127,8 @@ struct State {
     int k;            // truncation index
     int status;
     int sweeps;
-    int pad[3];
+    int nonfinite;    // 1 when the norms of A or B are not finite
+    int pad[2];
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -143,12 +143,15 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], con
     mma_tf32_16x8x8(d, al, b0h, b1h);
 }
 
-// Cp (r_prev x 16) = conj(Q) Y for 16 columns of Y (Ys column-major, L a
-// multiple of 16).  Warps take (16-row tile, k range) items; the partial
-// tiles meet in `part` (at most 16 x 16 x 32 floats) and are summed over the
-// k ranges in a fixed order.  Ends with a barrier.
-__device__ void orth_coef_mma(const float2* __restrict__ Q, const float2* Ys, int L, int r_prev, float2* Cp,
-                              float* part) {
+// Cp (r_prev x 16) = conj(Q) Y for 16 columns of Y (Ys column-major with
+// column stride LP, L a multiple of 16); row i of Q starts at Q + i QS, in
+// global memory (GQ, read with cache-global loads) or in shared memory.
+// Warps take (16-row tile, k range) items; the partial tiles meet in `part`
+// (at most 16 x 16 x 32 floats) and are summed over the k ranges in a fixed
+// order.  Ends with a barrier.
+template <bool GQ>
+__device__ void orth_coef_mma(const float2* __restrict__ Q, int QS, const float2* Ys, int L, int LP, int r_prev,
+                              float2* Cp, float* part) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int mt = (r_prev + 15) / 16, nks = L / 4;
@@ -166,8 +169,9 @@ __device__ void orth_coef_mma(const float2* __restrict__ Q, const float2* Ys, in
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
         for (int ks = ks0; ks < ks1; ++ks) {
             const int e = ks * 4 + t;
-            const float2 q0 = i0 < r_prev ? __ldcg(Q + (long)i0 * L + e) : make_float2(0.f, 0.f);
-            const float2 q1 = i1 < r_prev ? __ldcg(Q + (long)i1 * L + e) : make_float2(0.f, 0.f);
+            const float2 z = make_float2(0.f, 0.f);
+            const float2 q0 = i0 < r_prev ? (GQ ? __ldcg(Q + (long)i0 * QS + e) : Q[(long)i0 * QS + e]) : z;
+            const float2 q1 = i1 < r_prev ? (GQ ? __ldcg(Q + (long)i1 * QS + e) : Q[(long)i1 * QS + e]) : z;
             uint32_t ah[4], al[4];
             split_tf(q0.x, ah[0], al[0]);
             split_tf(q1.x, ah[1], al[1]);
@@ -175,7 +179,7 @@ __device__ void orth_coef_mma(const float2* __restrict__ Q, const float2* Ys, in
             split_tf(q1.y, ah[3], al[3]);
 #pragma unroll
             for (int jh = 0; jh < 2; ++jh) {
-                const float2 y = Ys[(jh * 8 + g) * L + e];
+                const float2 y = Ys[(jh * 8 + g) * LP + e];
                 uint32_t xh, xl, yh, yl;
                 split_tf(y.x, xh, xl);
                 split_tf(y.y, yh, yl);
@@ -206,9 +210,11 @@ __device__ void orth_coef_mma(const float2* __restrict__ Q, const float2* Ys, in
     __syncthreads();
 }
 
-// Ys (L x 16, column-major) -= Q^T Cp (Q's rows are the basis vectors; no
-// conjugation): a warp per 16-row tile of Y.  L a multiple of 16.
-__device__ void orth_update_mma(const float2* __restrict__ Q, float2* Ys, int L, int r_prev, const float2* Cp) {
+// Ys (L x 16, column-major, column stride LP) -= Q^T Cp (Q's rows are the
+// basis vectors; no conjugation): a warp per 16-row tile of Y.  L a multiple
+// of 16.
+__device__ void orth_update_mma(const float2* __restrict__ Q, float2* Ys, int L, int LP, int r_prev,
+                                const float2* Cp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int mt = L / 16, nks = (r_prev + 3) / 4;
@@ -245,10 +251,20 @@ __device__ void orth_update_mma(const float2* __restrict__ Q, float2* Ys, int L,
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int row = (c >> 1) ? e1 : e0, j = jh * 8 + 2 * t + (c & 1);
-                float2* y = Ys + j * L + row;
+                float2* y = Ys + j * LP + row;
                 *y = make_float2(y->x - acc[jh][c], y->y - acc[2 + jh][c]);
             }
     }
+}
+
+// Shared-memory extents of k_orth beyond its matrices: the partial tiles of
+// the tensor-core deflation (float32, 16 columns) and the Gram partials (one
+// per thread, at least one per upper-triangle entry).
+template <typename T, int BB> constexpr size_t orth_part_bytes() {
+    return (sizeof(T) == 4 && BB == 16) ? (size_t)16 * 16 * 32 * sizeof(float) : 0;
+}
+template <typename T, int BB> constexpr size_t orth_gram_elems() {
+    return (size_t)(BB * (BB + 1) / 2 > OrthThreads<T, BB>::v ? BB * (BB + 1) / 2 : OrthThreads<T, BB>::v);
 }
 
 template <typename T, int BB>
@@ -258,26 +274,39 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
     typedef cplx<T> V;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* Ys = (V*)smraw;                      // Ys[j*L + row], BB columns (unused ones zero)
-    V* Cs = Ys + (size_t)BB * L;            // r_prev x BB, summed over both passes
+    // Ys[j*LP + row], BB columns (unused ones zero); the odd column stride LP = L + 1
+    // keeps the column-parallel accesses (load, write-back, tensor-core operand
+    // reads) free of shared-memory bank conflicts
+    const int LP = L + 1;
+    V* Ys = (V*)smraw;
+    V* Cs = Ys + (size_t)BB * LP;           // r_prev x BB, summed over both passes
     V* Cp = Cs + (size_t)r_prev * BB;       // r_prev x BB, this pass
     V* G = Cp + (size_t)r_prev * BB;        // BB x BB Gram / Cholesky work
     V* Rk = G + BB * BB;                    // this pass's R
     V* Ra = Rk + BB * BB;                   // accumulated in-block R
     V* Rt = Ra + BB * BB;                   // scratch for the product
     float* part = (float*)(Rt + BB * BB);   // tensor-core deflation: partial coefficient tiles
+    V* gpart = (V*)((unsigned char*)part + orth_part_bytes<T, BB>());  // Gram partials
     __shared__ double red[33];
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = OrthThreads<T, BB>::v / 32;
     Y += (long)s * sY;
 
+    __shared__ int passes, need_shift;
+    if (tid == 0) {  // published by the barriers of the norm below
+        passes = final_pass ? 2 : 1;
+        need_shift = 0;
+    }
     T nn = 0;
-    for (int e = tid; e < L * BB; e += blockDim.x) {
-        const int j = e / L, row = e - j * L;
-        V v = mk<T>(0, 0);
-        if (j < b) v = Y[(long)row * b + j];
-        Ys[e] = v;
+    for (int e = tid; e < L * b; e += blockDim.x) {  // Y row-major L x b: coalesced reads
+        const int row = e / b, j = e - row * b;
+        const V v = Y[e];
+        Ys[j * LP + row] = v;
         nn += cabs2(v);
+    }
+    for (int e = tid; e < L * (BB - b); e += blockDim.x) {
+        const int j = b + e / L, row = e - (j - b) * L;
+        Ys[j * LP + row] = mk<T>(0, 0);
     }
     for (int e = tid; e < BB * BB; e += blockDim.x) Ra[e] = mk<T>((e / BB) == (e % BB) ? (T)1 : (T)0, 0);
     const double nnd = block_sum_t(nn, red);
@@ -291,8 +320,8 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
         const bool tc = sizeof(T) == 4 && BB == 16 && (L & 15) == 0 && r_prev <= 256;  // part: 16 row tiles
         for (int pass = 0; pass < dpasses; ++pass) {
           if (tc) {
-            orth_coef_mma((const float2*)Q, (const float2*)Ys, L, r_prev, (float2*)Cp, part);
-            orth_update_mma((const float2*)Q, (float2*)Ys, L, r_prev, (const float2*)Cp);
+            orth_coef_mma<true>((const float2*)Q, L, (const float2*)Ys, L, LP, r_prev, (float2*)Cp, part);
+            orth_update_mma((const float2*)Q, (float2*)Ys, L, LP, r_prev, (const float2*)Cp);
           } else {
             // two basis vectors per warp share every shared-memory read of Y
             for (int i0 = 2 * warp; i0 < r_prev; i0 += 2 * NW) {
@@ -309,7 +338,7 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                     if (!two) b0 = b1 = mk<T>(0, 0);
 #pragma unroll
                     for (int j = 0; j < BB; ++j) {
-                        const V y0 = Ys[j * L + row], y1 = Ys[j * L + row + 32];
+                        const V y0 = Ys[j * LP + row], y1 = Ys[j * LP + row + 32];
                         cfmac(acc0[j], a0, y0);
                         cfmac(acc1[j], b0, y0);
                         cfmac(acc0[j], a1, y1);
@@ -321,7 +350,7 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                     const V b0 = two ? qb[row] : mk<T>(0, 0);
 #pragma unroll
                     for (int j = 0; j < BB; ++j) {
-                        const V y0 = Ys[j * L + row];
+                        const V y0 = Ys[j * LP + row];
                         cfmac(acc0[j], a0, y0);
                         cfmac(acc1[j], b0, y0);
                     }
@@ -359,7 +388,7 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                 }
 #pragma unroll
                 for (int c = 0; c < CPG; ++c) {
-                    V* y = Ys + (g * CPG + c) * L + row;
+                    V* y = Ys + (g * CPG + c) * LP + row;
                     *y = csub(*y, acc[c]);
                 }
             }
@@ -373,34 +402,58 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
     //    conditioned, otherwise shifted CholQR3 (a shifted first pass, then two
     //    plain passes).  G holds the Gram matrix, Rk this pass's R, Rt = Rk^-1,
     //    Ra the accumulated in-block R (only when R is an output).
-    __shared__ int passes, need_shift;
     __shared__ T invd[BB];
     // Intermediate blocks (inside the power iteration) only need a
-    // well-conditioned basis of the right subspace: one Cholesky QR pass.
-    // Blocks that are kept (Q, QG, R) get two.
-    if (tid == 0) {
-        passes = final_pass ? 2 : 1;
-        need_shift = 0;
-    }
-    T y2p = 0;
-    for (int e = tid; e < L * BB; e += blockDim.x) y2p += cabs2(Ys[e]);
-    const double y2 = block_sum_t(y2p, red);  // its barriers also publish `passes`
-    // the Cholesky warp alone needs the shift (float64 arithmetic is slow here)
-    const double shift = warp == 0 ? 11.0 * ((double)L * b + (double)b * (b + 1)) * Eps<T>::v * y2 : 0.0;
+    // well-conditioned basis of the right subspace: one Cholesky QR pass
+    // (`passes` set at the start).  Blocks that are kept (Q, QG, R) get two.
+    T shift = 0;  // the shifted first pass's shift (Cholesky warp only)
     for (int pass = 0; pass < passes; ++pass) {
-        // Gram matrix (upper triangle incl. diagonal)
-        for (int p = warp; p < BB * BB; p += NW) {
-            const int i = p / BB, j = p - i * BB;
-            if (i > j) continue;
-            V acc = mk<T>(0, 0);
-            for (int row = lane; row < L; row += 32) cfmac(acc, Ys[i * L + row], Ys[j * L + row]);
-            acc.x = warp_sum(acc.x);
-            acc.y = warp_sum(acc.y);
-            if (lane == 0) G[i * BB + j] = acc;
+        // Gram matrix: float32 with 16 columns on the tensor cores (the
+        // coefficient product with the block's own columns as the basis, the
+        // full 16 x 16, 3xTF32); otherwise the upper triangle incl. diagonal by
+        // a thread per (entry, chunk of rows), the chunk sums meeting in gpart
+        if (sizeof(T) == 4 && BB == 16 && (L & 15) == 0) {
+            orth_coef_mma<false>((const float2*)Ys, LP, (const float2*)Ys, L, LP, 16, (float2*)G, part);
+        } else {
+            constexpr int NE = BB * (BB + 1) / 2;
+            const int nch = (int)blockDim.x / NE > 1 ? (int)blockDim.x / NE : 1;
+            const int rpc = (L + nch - 1) / nch;
+            for (int it = tid; it < NE * nch; it += blockDim.x) {
+                const int c = it / NE, e = it - c * NE;
+                int i = 0, rest = e;
+                while (rest >= BB - i) {
+                    rest -= BB - i;
+                    ++i;
+                }
+                const V* yi = Ys + i * LP;
+                const V* yj = Ys + (i + rest) * LP;
+                const int r0 = c * rpc, r1 = min(L, r0 + rpc);
+                V acc = mk<T>(0, 0);
+#pragma unroll 4
+                for (int row = r0; row < r1; ++row) cfmac(acc, yi[row], yj[row]);
+                gpart[it] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < NE; e += blockDim.x) {
+                int i = 0, rest = e;
+                while (rest >= BB - i) {
+                    rest -= BB - i;
+                    ++i;
+                }
+                V acc = gpart[e];
+                for (int c = 1; c < nch; ++c) acc = cadd(acc, gpart[c * NE + e]);
+                G[i * BB + i + rest] = acc;
+            }
         }
         __syncthreads();
+        if (pass == 0 && warp == 0) {
+            // 11 (L b + b(b+1)) u ||Y||_F^2, ||Y||_F^2 the trace of the Gram matrix
+            T y2 = lane < BB ? G[lane * BB + lane].x : (T)0;
+            y2 = warp_sum(y2);
+            shift = (T)(11.0 * ((double)L * b + (double)b * (b + 1)) * Eps<T>::v) * y2;
+        }
         if (warp == 0 && BB == 16 && sizeof(T) == 4) {
-            chol16_reg<T>(G, Rk, invd, b, (T)shift, pass == 0, &need_shift, &passes);
+            chol16_reg<T>(G, Rk, invd, b, shift, pass == 0, &need_shift, &passes);
         } else if (warp == 0) {
             // Cholesky G (+ shift) = R^H R by the first warp: at step k the
             // lanes form row k of R, then update the trailing Gram entries as
@@ -447,7 +500,7 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
                     }
                     __syncwarp();
                 }
-                if (pass > 0 || shifted || !bad || y2 == 0.0) break;
+                if (pass > 0 || shifted || !bad || dmax == (T)0) break;
                 if (lane == 0) {
                     need_shift = 1;
                     passes += 1;
@@ -462,13 +515,13 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
             V x[BB];
 #pragma unroll
             for (int jj = 0; jj < BB; ++jj) {
-                V y = Ys[jj * L + row];
+                V y = Ys[jj * LP + row];
 #pragma unroll
                 for (int i = 0; i < jj; ++i) y = csub(y, cmul(x[i], Rk[i * BB + jj]));
                 x[jj] = cscale(y, invd[jj]);
             }
 #pragma unroll
-            for (int jj = 0; jj < BB; ++jj) Ys[jj * L + row] = x[jj];
+            for (int jj = 0; jj < BB; ++jj) Ys[jj * LP + row] = x[jj];
         }
         if (R) {
             const int nthr = (int)blockDim.x, t0 = L < nthr ? L : 0;  // threads idle in the solve when L < blockDim
@@ -489,11 +542,14 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
 
     for (int e = tid; e < L * b; e += blockDim.x) {
         const int row = e / b, j = e - row * b;
-        Y[e] = Ys[j * L + row];
+        Y[e] = Ys[j * LP + row];
     }
     if (Qout) {
         V* Qo = Qout + (long)s * sQ + (long)r_prev * L;
-        for (int e = tid; e < L * b; e += blockDim.x) Qo[e] = Ys[e];
+        for (int e = tid; e < L * b; e += blockDim.x) {
+            const int j = e / L, row = e - j * L;
+            Qo[e] = Ys[j * LP + row];
+        }
     }
     if (R) {
         V* Rs = R + (long)s * sR;
@@ -509,8 +565,11 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
 
 static size_t orth_smem(int L, int b, int r_prev, size_t c) {
     const size_t BB = b <= 16 ? 16 : 32;
-    const size_t part = (c == 8 && BB == 16) ? (size_t)16 * 16 * 32 * sizeof(float) : 0;  // tensor-core deflation
-    return ((size_t)BB * L + 2 * (size_t)r_prev * BB + 4 * BB * BB) * c + part;
+    const size_t part = c == 8 ? (BB == 16 ? orth_part_bytes<float, 16>() : orth_part_bytes<float, 32>())
+                               : (BB == 16 ? orth_part_bytes<double, 16>() : orth_part_bytes<double, 32>());
+    const size_t gram = c == 8 ? (BB == 16 ? orth_gram_elems<float, 16>() : orth_gram_elems<float, 32>())
+                               : (BB == 16 ? orth_gram_elems<double, 16>() : orth_gram_elems<double, 32>());
+    return ((size_t)BB * (L + 1) + 2 * (size_t)r_prev * BB + 4 * BB * BB + gram) * c + part;
 }
 
 template <typename T>
@@ -554,6 +613,7 @@ __global__ void k_rt_init(State* st, const double* partsA, int nA, const double*
         st->status = TP_OK;
         st->sweeps = 0;
         st->sigma_max = 0.0;
+        st->nonfinite = (isfinite(a2) && isfinite(b2)) ? 0 : 1;
     }
 }
 
@@ -1191,6 +1251,7 @@ __global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st,
         }
     if (st->eps2 >= 0.0 && st->eta >= st->eps2) status = TP_ERR_NOT_CONVERGED;
     if (st->status == TP_ERR_TIMEOUT) status = TP_ERR_TIMEOUT;  // a bounded wait of a product ran out
+    if (st->nonfinite) status = TP_ERR_NONFINITE;
     double margin = fabs(res[k] - tau_delta) / tau_delta;
     if (k - 1 >= k_init) margin = fmin(margin, fabs(res[k - 1] - tau_delta) / tau_delta);
     st->k = k;
@@ -1202,7 +1263,7 @@ __global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st,
     o.k = k;
     o.r = r;
     o.sweeps = st->sweeps;
-    o.residual = res[k];
+    o.residual = st->nonfinite ? __longlong_as_double(0x7ff8000000000000LL) : res[k];  // NaN
     o.tau_delta = tau_delta;
     o.eta = st->eta;
     o.mu = 0.0;
@@ -1314,16 +1375,22 @@ size_t rt_ws_bytes(int l, int m, int n, int p, const tp_rtsvd_params* P) {
 template <typename T>
 static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m, int n, int p,
                                const tp_rtsvd_params* P, T* X, tp_info* info, void* ws, size_t ws_bytes,
-                               cudaStream_t st, int tc_passes, bool full) {
+                               cudaStream_t st, int tc_passes, bool full, const void* Ahat_in = nullptr) {
     TRY(rt_check<T>(l, m, n, p, P, full));
-    if (!A || !B || !Om || !X || !info) return TP_ERR_ARG;
+    if ((!A && !Ahat_in) || !B || !Om || !X || !info) return TP_ERR_ARG;
+    if (Ahat_in && ((size_t)Ahat_in & 15)) return TP_ERR_ARG;
     const int b = P->block, r_max = P->r_max, h = n / 2 + 1;
     RtWs<T> w = rt_carve<T>(ws, l, m, n, b, r_max, p);
     if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
     const long lm = (long)l * m;
     const int* done = &w.st->done;
 
-    TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, w.partsA, nullptr, st));
+    if (Ahat_in) {  // the caller's half spectrum of A (read only); ||A||^2 by Parseval
+        w.Ahat = (cplx<T>*)Ahat_in;
+        TRY(norm2_hat<T>(Ahat_in, n, l, m, w.partsA, st));
+    } else {
+        TRY(rdft<T>(A, w.Ahat, n, l, m, m, lm, w.partsA, nullptr, st));
+    }
     if (w.AhT) {
         prof_begin(TP_KC_GEMM, st);
         k_ctranspose<T><<<dim3((unsigned)((m + 31) / 32), (unsigned)((l + 31) / 32), (unsigned)h), 256, 0, st>>>(
@@ -1424,8 +1491,8 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
 
 template <typename T>
 tp_status rt_solve(const T* A, const T* B, const T* Om, int l, int m, int n, int p, const tp_rtsvd_params* P, T* X,
-                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st, int tc_passes) {
-    return rt_solve_impl<T>(A, B, Om, l, m, n, p, P, X, info, ws, ws_bytes, st, tc_passes, false);
+                   tp_info* info, void* ws, size_t ws_bytes, cudaStream_t st, int tc_passes, const void* Ahat) {
+    return rt_solve_impl<T>(A, B, Om, l, m, n, p, P, X, info, ws, ws_bytes, st, tc_passes, false, Ahat);
 }
 
 // Adjoint of B -> X_k for the factorisation and k that the last rt_solve
@@ -1556,8 +1623,10 @@ template tp_status rt_adjoint<double>(const double*, int, int, int, int, const t
 template size_t rt_ws_bytes<float>(int, int, int, int, const tp_rtsvd_params*);
 template size_t rt_ws_bytes<double>(int, int, int, int, const tp_rtsvd_params*);
 template tp_status rt_solve<float>(const float*, const float*, const float*, int, int, int, int,
-                                   const tp_rtsvd_params*, float*, tp_info*, void*, size_t, cudaStream_t, int);
+                                   const tp_rtsvd_params*, float*, tp_info*, void*, size_t, cudaStream_t, int,
+                                   const void*);
 template tp_status rt_solve<double>(const double*, const double*, const double*, int, int, int, int,
-                                    const tp_rtsvd_params*, double*, tp_info*, void*, size_t, cudaStream_t, int);
+                                    const tp_rtsvd_params*, double*, tp_info*, void*, size_t, cudaStream_t, int,
+                                    const void*);
 
 }  // namespace tp

@@ -121,20 +121,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity.  False on timeout (which
-// also raises *abort) or when another role has raised *abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
+// Bounded wait for the phase with the given parity (at most `spin` cycles).
+// False on timeout (which also raises *abort) or when another role has raised
+// *abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort, long long spin) {
     const long long t0 = clock64();
     while (!mbar_try(a, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > TC_SPIN) {
+        if (clock64() - t0 > spin) {
             *abort = 1;
             return false;
         }
     }
     return true;
 }
-// Bounded wait that ignores the abort flag (used to drain work in flight).
+// Bounded wait that ignores the abort flag (used to drain work in flight: TMA
+// writes and MMAs already issued, which complete whatever the other roles do;
+// its bound is fixed, never the progress budget).
 __device__ __forceinline__ void mbar_drain(uint32_t a, uint32_t parity) {
     const long long t0 = clock64();
     while (!mbar_try(a, parity))
@@ -203,11 +206,13 @@ template <int OPA, int NCP, int NP> struct TcCfg {
     static constexpr int B_OP = B_RAW + B_RAW_BYTES;
     static constexpr int STAGE = B_OP + NB * TC_KT * 4;  // a multiple of 1024
     // two CTAs per SM when two stages fit in half the shared memory (the TMA
-    // stream of one CTA does not fill an SM's share of L2 bandwidth), else one
-    // CTA with up to four stages
-    static constexpr int NS = 2 * STAGE + 1024 <= TC_SMEM_LIMIT / 2
-                                  ? 2
-                                  : ((TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE);
+    // stream of one CTA does not fill an SM's share of L2 bandwidth), with as
+    // many stages as fit there (up to four: each CTA's tiles are latency-bound,
+    // about 1,900 cycles per 16 KB tile with two in flight), else one CTA with
+    // up to four stages
+    static constexpr int NS2 = (TC_SMEM_LIMIT / 2 - 1024) / STAGE;
+    static constexpr int NS = NS2 >= 2 ? (NS2 > 4 ? 4 : NS2)
+                                       : ((TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE);
     static constexpr size_t SMEM = (size_t)NS * STAGE + 1024;  // + alignment slack
     static constexpr uint32_t TX = TC_A_BYTES + B_RAW_BYTES;   // bytes the two TMA boxes deliver
     static constexpr uint32_t NCOLS = NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
@@ -292,7 +297,7 @@ template <int OPA, bool CONJ, int NCP, int NP>
 __global__ void __launch_bounds__(TC_THREADS, 2)
 k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            float2* __restrict__ C, long ldc, long sC, int Mc, int Nc, int Kc, const int* skip, int* err,
-           int trans_out, const int* ncap, int c0) {
+           int trans_out, const int* ncap, int c0, long long spin) {
     typedef TcCfg<OPA, NCP, NP> G;
     if (skip && *skip) return;
     if (ncap && c0 >= *ncap) return;  // a column chunk past the run-time column count
@@ -337,7 +342,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             int issued = 0;
             for (int kt = 0; kt < nkt; ++kt) {
                 const int st = kt % G::NS;
-                if (kt >= G::NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((kt / G::NS - 1) & 1), abort)) break;
+                if (kt >= G::NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((kt / G::NS - 1) & 1), abort, spin)) break;
                 const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
                 const uint32_t fb = smem_u32(&full[st]);
                 mbar_expect_tx(fb, G::TX);
@@ -356,7 +361,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             int issued = 0;
             for (int kt = 0; kt < nkt; ++kt) {
                 const int st = kt % G::NS;
-                if (!mbar_wait(smem_u32(&conv[st]), (uint32_t)((kt / G::NS) & 1), abort)) break;
+                if (!mbar_wait(smem_u32(&conv[st]), (uint32_t)((kt / G::NS) & 1), abort, spin)) break;
                 tc_fence_after();
                 const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
 #pragma unroll
@@ -386,13 +391,13 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         // warps 0-7: split each stage, then the epilogue
         for (int kt = 0; kt < nkt; ++kt) {
             const int st = kt % G::NS;
-            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / G::NS) & 1), abort)) break;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / G::NS) & 1), abort, spin)) break;
             split_stage<OPA, CONJ, NCP, NP>(sgen + st * G::STAGE);
             fence_async_smem();  // generic-proxy writes -> tensor-core reads
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&conv[st]));
         }
-        const bool ok = mbar_wait(smem_u32(&accf), 0u, abort);
+        const bool ok = mbar_wait(smem_u32(&accf), 0u, abort, spin);
         if (__all_sync(0xffffffffu, ok)) {
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -477,7 +482,8 @@ tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, lon
     const int Mr = OPA == OP_N ? M : 2 * M;
     dim3 grid((unsigned)((Mr + TC_M - 1) / TC_M), (unsigned)batch);
     prof_begin(TP_KC_GEMM, st);
-    kern<<<grid, TC_THREADS, G::SMEM, st>>>(ma, mb, (float2*)C, ldc, sC, M, N, K, skip, err, trans_out, ncap, c0);
+    kern<<<grid, TC_THREADS, G::SMEM, st>>>(ma, mb, (float2*)C, ldc, sC, M, N, K, skip, err, trans_out, ncap, c0,
+                                             wait_budget(TC_SPIN));
     return launched(TP_KC_GEMM, st);
 }
 

@@ -68,8 +68,9 @@ class BlurConfig:
 # the third is the 512^3 precision-form size.  eps_rel (the tolerance of
 # Algorithm 3 relative to ||A||_F; the paper tunes the absolute eps per example
 # by experiment, Table 0) is the largest value on the grid 10^(-j/10) for which
-# the oracle's RT-tSVD meets the discrepancy principle within [r - p, r]; at
-# 256^3 this gives r = 96, close to the paper's r = 99 for its 256^3 image.
+# the oracle's RT-tSVD meets the discrepancy principle within [r - p, r]
+# (tests/golden/calibrate_eps.py); at 256^3 this gives r = 96, close to the
+# paper's r = 99 for its 256^3 image, and at 512^3 10^(-1.2): r = 128, k = 120.
 CONFIGS = {
     "n32": BlurConfig("n32", 32, 1.5, 4, 2.0, 5, 2, 1e-2, 1.01, 5, 1, 1, 32,
                       3e-2, 32, 1e1, 1e7, 43),
@@ -78,7 +79,7 @@ CONFIGS = {
     "n256_hi": BlurConfig("n256_hi", 256, 2.5, 8, 3.0, 20, 4, 1e-2, 1.1, 10, 1,
                           16, 160, 3e-2, 100, 1e1, 1e7, 44),
     "n512": BlurConfig("n512", 512, 3.0, 12, 4.0, 20, 4, 1e-3, 1.1, 10, 1, 16,
-                       160, 3e-3, 100, 1e1, 1e7, 45),
+                       160, 10 ** -1.2, 100, 1e1, 1e7, 45),
 }
 
 
@@ -209,23 +210,35 @@ def blur_problem(cfg: BlurConfig | str, noise: float | None = None, seed: int | 
 
 
 UNEVEN_SIZES = (64, 96, 128, 192, 256, 320, 384)
+# solver parameters of the uneven batch (RT-tSVD and tGKB per problem)
+UNEVEN_TAU, UNEVEN_P_OVER, UNEVEN_Q, UNEVEN_BLOCK, UNEVEN_KMAX = 1.1, 10, 1, 16, 100
+UNEVEN_R_CAP = 160
+# eps_rel = 10^(-j/10) per problem of uneven_problems(16, 46): the largest grid
+# value for which the oracle's RT-tSVD meets the discrepancy principle within
+# [r - p, r] (tests/golden/calibrate_eps.py uneven)
+UNEVEN_EPS_J = (6, 6, 5, 8, 6, 6, 5, 7, 7, 5, 5, 5, 7, 7, 6, 6)
 
 
-def uneven_problems(count: int = 16, seed: int = 46, noise: float = 1e-2, r_cap: int = 96) -> list:
+def uneven_problems(count: int = 16, seed: int = 46, noise: float = 1e-2, r_cap: int = UNEVEN_R_CAP,
+                    calibrated: bool = True) -> list:
     """`count` independent deblurring problems of seeded sizes N drawn from
     UNEVEN_SIZES (blur law sigma 2.5, band 8, s = 3; one image each with 20
     bumps and 4 rectangles; white noise of relative level `noise`).  Each entry:
     float32 A (N,N,N), B (N,N,1), Omega (N,N,r_max) with r_max = min(N, r_cap),
-    and N, r_max, delta."""
+    and N, r_max, delta, and eps_rel (the calibrated tolerance of Algorithm 3,
+    for the default batch)."""
     rng = rng_for(seed)
     out = []
-    for N in rng.choice(UNEVEN_SIZES, size=count):
+    for i, N in enumerate(rng.choice(UNEVEN_SIZES, size=count)):
         N = int(N)
         T, c = blur_factors(N, 2.5, 8, 3.0)
         img = synthetic_image(N, N, 20, 4, rng)
         B, delta = add_noise(forward_blur(T, c, img), noise, rng)
         r_max = min(N, r_cap)
-        out.append(dict(N=N, r_max=r_max, delta=delta, A=blur_tensor(T, c), B=lateral(B).astype(np.float32),
+        eps_rel = None
+        if calibrated and UNEVEN_EPS_J is not None and (count, seed, noise, r_cap) == (16, 46, 1e-2, UNEVEN_R_CAP):
+            eps_rel = 10.0 ** (-UNEVEN_EPS_J[i] / 10.0)
+        out.append(dict(N=N, r_max=r_max, delta=delta, eps_rel=eps_rel, A=blur_tensor(T, c),
+                        B=lateral(B).astype(np.float32),
                         Omega=rng.standard_normal((N, N, r_max)).astype(np.float32)))
     return out
-

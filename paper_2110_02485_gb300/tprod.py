@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 TP_OK, TP_ERR_ARG, TP_ERR_CUDA, TP_ERR_WORKSPACE = 0, -1, -2, -3
 TP_ERR_BREAKDOWN, TP_ERR_NOT_CONVERGED, TP_ERR_TIMEOUT, TP_ERR_UNSUPPORTED = -4, -5, -6, -7
+TP_ERR_NONFINITE = -8
 TP_FP32, TP_FP64, TP_TF32 = 0, 1, 2
 
 
@@ -50,10 +51,11 @@ class TikParams(ctypes.Structure):
 EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm", "rtsvd_workspace_bytes",
            "rtsvd_truncated_solve", "tgkb_workspace_bytes", "tgkb_solve", "tgkb_tikhonov_workspace_bytes",
            "tgkb_tikhonov_solve", "tp_status_string", "tp_version", "tp_kernel_launches", "tp_timing_enable",
-           "tp_timing_read", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
+           "tp_timing_read", "tp_wait_budget", "tp_wait_stall", "tprod_gemm_noalloc", "rtsvd_adjoint", "nested_tgkb_workspace_bytes",
            "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve", "tgkb_triplets_workspace_bytes",
            "tgkb_triplets", "sep_grad_c_workspace_bytes", "sep_grad_c", "tgkb_tikhonov_grad_c_workspace_bytes",
-           "tgkb_tikhonov_grad_c", "sep_operator", "ttsvd_adjoint")
+           "tgkb_tikhonov_grad_c", "sep_operator", "ttsvd_adjoint",
+           "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -100,11 +102,18 @@ def load(path: str | None = None):
     L.tgkb_tikhonov_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(TikParams), i]
     L.tgkb_tikhonov_workspace_bytes.restype = sz
     L.tgkb_tikhonov_solve.argtypes = [vp, vp, i, i, i, i, ctypes.POINTER(TikParams), vp, vp, i, vp, sz, vp]
+    L.tgkb_tikhonov_solve_hat.argtypes = L.tgkb_tikhonov_solve.argtypes
+    L.rtsvd_truncated_solve_hat.argtypes = L.rtsvd_truncated_solve.argtypes
+    L.tgkb_solve_hat.argtypes = L.tgkb_solve.argtypes
     L.tp_status_string.argtypes = [i]
     L.tp_status_string.restype = ctypes.c_char_p
     L.tp_version.restype = i
     L.tp_kernel_launches.restype = i
     L.tp_timing_enable.argtypes = [i]
+    L.tp_wait_budget.argtypes = [ctypes.c_longlong]
+    L.tp_wait_budget.restype = i
+    L.tp_wait_stall.argtypes = [i]
+    L.tp_wait_stall.restype = i
     L.tp_timing_enable.restype = i
     L.tp_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), i]
     L.tp_timing_read.restype = i
@@ -118,7 +127,7 @@ def load(path: str | None = None):
     L.tgkb_tikhonov_grad_c_workspace_bytes.restype = sz
     L.tgkb_tikhonov_grad_c.argtypes = [vp, vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, i, vp, sz, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
-              "tgkb_tikhonov_solve", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator",
+              "tgkb_tikhonov_solve", "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator",
               "ttsvd_adjoint"):
         getattr(L, f).restype = i
     _lib = L
@@ -131,6 +140,20 @@ def status_string(st: int) -> str:
 
 def kernel_launches() -> int:
     return int(load().tp_kernel_launches())
+
+
+def wait_budget(cycles: int) -> None:
+    """Bound (SM clock cycles) of the device-side waits for progress in later
+    launches; 0 restores the defaults (about 1-2 s).  For failure-detection
+    tests: a budget of a few cycles makes those waits run out on purpose."""
+    _check("tp_wait_budget", load().tp_wait_budget(int(cycles)))
+
+
+def wait_stall(on: bool) -> None:
+    """With on, the grid-wide waits of the persistent tGKB kernels wait for an
+    arrival that nothing makes, so each runs out after its budget
+    (failure-detection tests; pair with a short wait_budget)."""
+    _check("tp_wait_stall", load().tp_wait_stall(1 if on else 0))
 
 
 def timing_enable(classes) -> None:
@@ -171,6 +194,35 @@ def _dev(*ts: torch.Tensor):
             raise TypeError("tprod works on CUDA tensors only (no CPU path)")
         if not t.is_contiguous():
             raise ValueError("tensors must be contiguous")
+
+
+class _Op:
+    """The operator of a solve: the real tensor A (n, l, m) or its half
+    spectrum A-hat (n/2+1, l, m) complex with n given (the *_hat entry
+    points).  Shape, dtype and device as the solve needs them."""
+
+    def __init__(self, A, Ahat, n):
+        if (A is None) == (Ahat is None):
+            raise ValueError("give exactly one of A and Ahat")
+        if A is not None:
+            _dev(A)
+            self.t, self.hat = A, False
+            self.n, self.l, self.m = A.shape
+            self.dtype = A.dtype
+        else:
+            _dev(Ahat)
+            if n is None or Ahat.shape[0] != int(n) // 2 + 1:
+                raise ValueError("Ahat needs n with Ahat.shape[0] == n // 2 + 1")
+            if Ahat.dtype not in (torch.complex64, torch.complex128):
+                raise TypeError("Ahat must be complex64 or complex128")
+            self.t, self.hat = Ahat, True
+            self.n, (self.l, self.m) = int(n), Ahat.shape[1:]
+            self.dtype = torch.float32 if Ahat.dtype == torch.complex64 else torch.float64
+        self.device = self.t.device
+        self.prec = TP_FP32 if self.dtype == torch.float32 else TP_FP64
+
+    def entry(self, L, name):
+        return getattr(L, name + "_hat") if self.hat else getattr(L, name)
 
 
 def _stream() -> ctypes.c_void_p:
@@ -357,37 +409,38 @@ def rtsvd_adjoint(fac: RtsvdFactor, G: torch.Tensor) -> torch.Tensor:
 
 
 def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None, eps=0.0, eps_rel=0.0,
-                res_hist=False, sync=True, tf32=False, keep=False):
+                res_hist=False, sync=True, tf32=False, keep=False, Ahat=None, n=None):
     """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist][, factor]).
 
     B is (n, l, p): p > 1 lateral slices share one factorisation and one k
     (problem (I6)).  tf32=True (float32 only): the TP_TF32 precision form of
     the block sketch and projection products.  keep=True also returns an
-    RtsvdFactor for rtsvd_adjoint."""
-    _dev(A, B, Omega)
-    n, l, m = A.shape
+    RtsvdFactor for rtsvd_adjoint.  With A=None, Ahat (the half spectrum
+    from fft(A)) and n: the rtsvd_truncated_solve_hat entry point."""
+    op = _Op(A, Ahat, n)
+    _dev(B, Omega)
+    n, l, m = op.n, op.l, op.m
     p = B.shape[2]
     r_max = min(l, m) if r_max is None else r_max
-    prec = _prec(A)
+    prec = op.prec
     if tf32:
         if prec != TP_FP32:
             raise TypeError("tf32 needs float32 tensors")
         prec = TP_TF32
-    X = torch.empty((n, m, p), dtype=A.dtype, device=A.device)
-    hist = torch.empty(r_max + 1, dtype=torch.float64, device=A.device) if res_hist else None
+    X = torch.empty((n, m, p), dtype=op.dtype, device=op.device)
+    hist = torch.empty(r_max + 1, dtype=torch.float64, device=op.device) if res_hist else None
     P = RtsvdParams(float(delta), float(tau), float(eps), float(eps_rel), int(p_over), int(q_power), int(block),
                     int(r_max), hist.data_ptr() if hist is not None else None)
     L = load()
     nb = L.rtsvd_workspace_bytes(l, m, n, p, ctypes.byref(P), prec)
     if nb == 0:
         raise TprodError("rtsvd_workspace_bytes", TP_ERR_ARG)
-    ws = _workspace(nb, A.device)
+    ws = _workspace(nb, op.device)
     wp, wn = _aligned(ws)
-    info = _info_buf(A.device)
-    _check("rtsvd_truncated_solve", L.rtsvd_truncated_solve(_ptr(A), _ptr(B), _ptr(Omega), l, m, n, p,
-                                                            ctypes.byref(P), _ptr(X), _ptr(info), prec, wp, wn,
-                                                            _stream()))
-    fac = (RtsvdFactor(ws, P, hist, l, m, n, p, prec, A.device, A.dtype),) if keep else ()
+    info = _info_buf(op.device)
+    _check("rtsvd_truncated_solve", op.entry(L, "rtsvd_truncated_solve")(
+        _ptr(op.t), _ptr(B), _ptr(Omega), l, m, n, p, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp, wn, _stream()))
+    fac = (RtsvdFactor(ws, P, hist, l, m, n, p, prec, op.device, op.dtype),) if keep else ()
     if not sync:
         return (X, info, hist) + fac
     out = (X, _info_dict(info))
@@ -460,18 +513,20 @@ def ttsvd_solve(A, B, delta, tau, res_hist=False, sync=True, keep=False):
     return out + ((hist.cpu().numpy(),) if res_hist else ()) + fac
 
 
-def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None):
+def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None, Ahat=None, n=None):
     """tGKB method (Algorithm 4 + Eq. (solgkb)).  Returns (X, info[, res_hist]).
 
     B is (n, l, p); p > 1 is the tGKB_p method: every lateral slice j is
     solved on its own with bound deltas[j] (default: delta for all) and its own
-    k_j; info is then a list of p records and res_hist a (p, k_max+1) array."""
-    _dev(A, B)
-    n, l, m = A.shape
+    k_j; info is then a list of p records and res_hist a (p, k_max+1) array.
+    With A=None, Ahat and n: the tgkb_solve_hat entry point."""
+    op = _Op(A, Ahat, n)
+    _dev(B)
+    n, l, m = op.n, op.l, op.m
     p = B.shape[2]
-    prec = _prec(A)
-    X = torch.empty((n, m, p), dtype=A.dtype, device=A.device)
-    hist = torch.empty((p, k_max + 1), dtype=torch.float64, device=A.device) if res_hist else None
+    prec = op.prec
+    X = torch.empty((n, m, p), dtype=op.dtype, device=op.device)
+    hist = torch.empty((p, k_max + 1), dtype=torch.float64, device=op.device) if res_hist else None
     dp = None
     if deltas is not None:
         dl = [float(d) for d in deltas]
@@ -484,11 +539,11 @@ def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None):
     nb = L.tgkb_workspace_bytes(l, m, n, p, ctypes.byref(P), prec)
     if nb == 0:
         raise TprodError("tgkb_workspace_bytes", TP_ERR_ARG)
-    ws = _workspace(nb, A.device)
+    ws = _workspace(nb, op.device)
     wp, wn = _aligned(ws)
-    info = _info_buf(A.device, p)
-    _check("tgkb_solve", L.tgkb_solve(_ptr(A), _ptr(B), l, m, n, p, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp,
-                                      wn, _stream()))
+    info = _info_buf(op.device, p)
+    _check("tgkb_solve", op.entry(L, "tgkb_solve")(_ptr(op.t), _ptr(B), l, m, n, p, ctypes.byref(P), _ptr(X),
+                                                   _ptr(info), prec, wp, wn, _stream()))
     if p == 1 and hist is not None:
         hist = hist[0]
     if not sync:
@@ -670,26 +725,28 @@ def tgkt_grad_c(fac: "TgktFactor", G: torch.Tensor, c: torch.Tensor) -> torch.Te
     return dc
 
 
-def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True, keep=False):
+def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True, keep=False, Ahat=None, n=None):
     """Tikhonov-tGKB (Section 5).  Returns (X, info[, factor]); keep=True also
-    returns the solve's workspace for tgkt_grad_c."""
-    _dev(A, B)
-    n, l, m = A.shape
-    prec = _prec(A)
-    X = torch.empty((n, m, 1), dtype=A.dtype, device=A.device)
+    returns the solve's workspace for tgkt_grad_c.  With A=None, Ahat and n:
+    the tgkb_tikhonov_solve_hat entry point."""
+    op = _Op(A, Ahat, n)
+    _dev(B)
+    n, l, m = op.n, op.l, op.m
+    prec = op.prec
+    X = torch.empty((n, m, 1), dtype=op.dtype, device=op.device)
     P = TikParams(TgkbParams(float(delta), float(tau), int(k_max), None), float(mu_lo), float(mu_hi),
                   float(log_tol))
     L = load()
     nb = L.tgkb_tikhonov_workspace_bytes(l, m, n, 1, ctypes.byref(P), prec)
     if nb == 0:
         raise TprodError("tgkb_tikhonov_workspace_bytes", TP_ERR_ARG)
-    ws = _workspace(nb, A.device)
+    ws = _workspace(nb, op.device)
     wp, wn = _aligned(ws)
-    info = _info_buf(A.device)
-    _check("tgkb_tikhonov_solve", L.tgkb_tikhonov_solve(_ptr(A), _ptr(B), l, m, n, 1, ctypes.byref(P), _ptr(X),
-                                                        _ptr(info), prec, wp, wn, _stream()))
+    info = _info_buf(op.device)
+    _check("tgkb_tikhonov_solve", op.entry(L, "tgkb_tikhonov_solve")(
+        _ptr(op.t), _ptr(B), l, m, n, 1, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp, wn, _stream()))
     if keep:
-        fac = TgktFactor(ws, P, l, m, n, prec, A.device, A.dtype)
+        fac = TgktFactor(ws, P, l, m, n, prec, op.device, op.dtype)
         return (X, info, fac) if not sync else (X, _info_dict(info), fac)
     if not sync:
         return X, info

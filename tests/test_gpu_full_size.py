@@ -1,8 +1,9 @@
-"""Parity at the full 256^3 bench workload, in the launch configuration that
-bench.py times (the same generator, seed, parameters and float32 path).
+"""Parity at the full-size workloads that bench.py times: the 256^3 image
+deblur and the 512^3 precision-form size, in the launch configuration of the
+bench (the same generator, seed, parameters and float32 path).
 
-The oracle's results on this workload are stored in tests/golden/n256_oracle.json
-(scalars) and n256_oracle_X.npz (the complete float64 solutions) by
+The oracle's results on each workload are stored in tests/golden/<name>_oracle.json
+(scalars) and <name>_oracle_X.npz (the complete float64 solutions) by
 tests/golden/make_goldens.py, which calls only the oracle.  The GPU must pick
 the same truncation indices (the stored margins are far from the tie band),
 match the oracle's whole solution within 1e-5 relative Frobenius error in
@@ -39,14 +40,15 @@ def tp():
 TOL_FP32 = 1e-5
 
 
-@pytest.fixture(scope="module")
-def work():
-    with open(os.path.join(HERE, "golden", "n256_oracle.json")) as f:
+@pytest.fixture(scope="module", params=["n256", "n512"])
+def work(request):
+    name = request.param
+    with open(os.path.join(HERE, "golden", f"{name}_oracle.json")) as f:
         gold = json.load(f)
-    sols = np.load(os.path.join(HERE, "golden", "n256_oracle_X.npz"))
+    sols = np.load(os.path.join(HERE, "golden", f"{name}_oracle_X.npz"))
     for m in ("rtsvd", "tgkb", "tgkt"):
         gold[m]["X"] = sols[m]
-    cfg = synth.CONFIGS["n256"]
+    cfg = synth.CONFIGS[name]
     P = synth.blur_problem(cfg, seed=gold["seed"])
     assert abs(P["delta"] - gold["delta"]) <= 1e-12 * gold["delta"]
     return cfg, P, gold
@@ -76,10 +78,10 @@ def check(info, X, ref, P, tol_x):
     assert abs(info["residual"] - res) <= 1e-4 * res         # and the reported residual is the true one
 
 
-def test_rtsvd_n256(tp, work):
+def test_rtsvd_full_size(tp, work):
     cfg, P, gold = work
     ref = gold["rtsvd"]
-    assert ref["margin"] > 1e-3
+    assert ref["margin"] > 1e-4          # outside the float32 tie band: k must match
     X, info = tp.rtsvd_solve(dev(P["A"]), dev(P["B"]), dev(P["Omega"]), P["delta"], cfg.tau, cfg.p_over, cfg.block,
                              cfg.q_power, cfg.r_max, eps_rel=cfg.eps_rel)
     X = X.cpu().numpy()
@@ -87,7 +89,7 @@ def test_rtsvd_n256(tp, work):
     check(info, X, ref, P, TOL_FP32)
 
 
-def test_rtsvd_n256_tf32_form(tp, work):
+def test_rtsvd_full_size_tf32_form(tp, work):
     cfg, P, gold = work
     ref = gold["rtsvd"]
     X, info = tp.rtsvd_solve(dev(P["A"]), dev(P["B"]), dev(P["Omega"]), P["delta"], cfg.tau, cfg.p_over, cfg.block,
@@ -98,15 +100,15 @@ def test_rtsvd_n256_tf32_form(tp, work):
     assert true_residual(P, X) <= ref["tau_delta"] * (1 + 1e-3)
 
 
-def test_tgkb_n256(tp, work):
+def test_tgkb_full_size(tp, work):
     cfg, P, gold = work
     ref = gold["tgkb"]
-    assert ref["margin"] > 1e-3
+    assert ref["margin"] > 1e-4
     X, info = tp.tgkb_solve(dev(P["A"]), dev(P["B"]), P["delta"], cfg.tau, cfg.k_max)
     check(info, X.cpu().numpy(), ref, P, TOL_FP32)
 
 
-def test_tgkt_n256(tp, work):
+def test_tgkt_full_size(tp, work):
     cfg, P, gold = work
     ref = gold["tgkt"]
     X, info = tp.tgkt_solve(dev(P["A"]), dev(P["B"]), P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)

@@ -798,3 +798,43 @@ def test_ttsvd_adjoint_matches_oracle(tp, dtype, N, n, p):
     assert dB.shape == (n, N, p)
     assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 1e-4)
     assert np.array_equal(dB, tp.ttsvd_adjoint(fac, dev(G, dtype)).cpu().numpy())
+
+
+# ------------------------------------------------ precomputed A-hat ----
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_hat_entry_points_match_the_plain_solves_and_the_oracle(tp, dtype):
+    """rtsvd_truncated_solve_hat, tgkb_solve_hat and tgkb_tikhonov_solve_hat
+    with A-hat from tprod_fft: the plain calls' truncation indices and the
+    oracle's solutions (||A||^2 for Algorithm 3 comes from A-hat by Parseval)."""
+    A, B, delta = problem(20, 16, seed=21)
+    n = A.shape[0]
+    Om = rnd((n, 20, 20), 23).astype(np.float32)
+    Ad, Bd, Omd = dev(A, dtype), dev(B, dtype), dev(Om, dtype)
+    Ah = tp.fft(Ad)
+    A64, B64 = (x.astype(np.float64) for x in (A, B))
+    eps_rel = 0.02
+    ref = O.rtsvd_solve(A64, B64, Om.astype(np.float64), delta, 1.1, eps_rel * np.sqrt(O.fro2(A64)), 3, 4, 1, r_max=20)
+    X0, i0 = tp.rtsvd_solve(Ad, Bd, Omd, delta, 1.1, 3, 4, 1, r_max=20, eps_rel=eps_rel)
+    X1, i1 = tp.rtsvd_solve(None, Bd, Omd, delta, 1.1, 3, 4, 1, r_max=20, eps_rel=eps_rel, Ahat=Ah, n=n)
+    assert (i1["r"], i1["k"], i1["status"]) == (i0["r"], i0["k"], i0["status"]) == (ref["r"], ref["k"], ref["status"])
+    assert np.isclose(i1["norm_a2"], O.fro2(A64), rtol=1e-6 if dtype == torch.float32 else 1e-12)
+    assert rel(X1.cpu().numpy(), ref["X"]) <= TOL_X[dtype]
+    ref = O.tgkb_solve(A64, B64, delta, 1.1, 16)
+    X1, i1 = tp.tgkb_solve(None, Bd, delta, 1.1, 16, Ahat=Ah, n=n)
+    assert (i1["k"], i1["status"]) == (ref["k"], ref["status"])
+    assert rel(X1.cpu().numpy(), ref["X"]) <= TOL_X[dtype]
+    ref = O.tgkt_solve(A64, B64, delta, 1.1, 16, 1e-2, 1e8)
+    X1, i1 = tp.tgkt_solve(None, Bd, delta, 1.1, 16, 1e-2, 1e8, Ahat=Ah, n=n)
+    assert i1["k"] == ref["k"]
+    assert rel(X1.cpu().numpy(), ref["X"]) <= TOL_X[dtype]
+
+
+def test_hat_entry_points_refuse_a_missing_or_mismatched_spectrum(tp):
+    A, B, delta = problem(8, 6, seed=2)
+    Bd = dev(B, torch.float32)
+    Ah = tp.fft(dev(A, torch.float32))
+    with pytest.raises(ValueError):
+        tp.tgkb_solve(None, Bd, delta, 1.1, 4, Ahat=Ah, n=8)   # 8 // 2 + 1 != 4 slices
+    with pytest.raises(ValueError):
+        tp.tgkb_solve(None, Bd, delta, 1.1, 4)                 # neither A nor A-hat

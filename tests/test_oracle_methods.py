@@ -569,3 +569,15 @@ def test_zero_delta_runs_to_the_cap():
     assert k["status"] == O.STATUS_NOT_CONVERGED and k["mu"] == 1e5
     assert t["k"] == min(l, m) and t["status"] == O.STATUS_OK
     assert np.isclose(np.sqrt(O.fro2(B - O.tprod(A, t["X"]))), 0.0, atol=1e-10 * np.sqrt(O.fro2(B)))
+
+
+def test_uneven_batch_carries_a_calibrated_tolerance_per_problem():
+    """The bench's uneven batch: every problem has r_max = min(N, 160) and the
+    eps_rel its calibration chose (synth.UNEVEN_EPS_J, written from
+    tests/golden/calibrate_eps.py); a smaller or reseeded batch has none."""
+    probs = synth.uneven_problems()
+    assert len(probs) == 16 and len(synth.UNEVEN_EPS_J) == 16
+    for p, j in zip(probs, synth.UNEVEN_EPS_J):
+        assert p["r_max"] == min(p["N"], 160)
+        assert p["eps_rel"] == 10.0 ** (-j / 10.0)
+    assert all(p["eps_rel"] is None for p in synth.uneven_problems(count=3))
