@@ -84,6 +84,7 @@ def args_():
     p.add_argument("--no-grad", action="store_true", help="skip the differentiation form")
     p.add_argument("--no-n512", action="store_true", help="skip the 512^3 workload")
     p.add_argument("--no-hat", action="store_true", help="skip the solves from a precomputed A-hat")
+    p.add_argument("--no-ttsvd", action="store_true", help="skip the full-tSVD comparison method")
     p.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
     return p.parse_args()
 
@@ -421,6 +422,9 @@ def run_ours(a, rank, world, local):
     grad = None
     if not a.no_grad and rank == 0:
         grad = differentiation_form(a, cfg, P, A, B, Om, flush, tprod, torch)
+    tts = None
+    if not a.no_ttsvd and rank == 0 and cfg.N <= 256:
+        tts = ttsvd_form(a, cfg, P, A, B, flush, tprod, torch)
     hat = None
     if not a.no_hat and rank == 0:
         hat = hat_form(a, cfg, P, A, B, Om, flush, tprod, torch)
@@ -457,7 +461,7 @@ def run_ours(a, rank, world, local):
                       "parallelism": f"replicas x{world}"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "roofline_by_class": by_class, "clocks": clk,
            "precision_form": prec_form, "batched_form": batched, "uneven_form": uneven,
-           "differentiation_form": grad, "n512_form": n512, "b_only_form": hat,
+           "differentiation_form": grad, "n512_form": n512, "b_only_form": hat, "ttsvd_form": tts,
            "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
            "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
                           "tgkb": {k: infos[1][k] for k in ("k", "status")},
@@ -487,10 +491,10 @@ def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
         ref_x = np.load(sol_path)["rtsvd"]
     out = {}
     reps = max(3, min(a.steps, 20))
-    for name, tf32 in (("fp32", False), ("tf32", True)):
+    for name in ("fp32", "tf32", "bf16"):
         def solve():
             return tprod.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
-                                     eps_rel=cfg.eps_rel, sync=False, tf32=tf32)
+                                     eps_rel=cfg.eps_rel, sync=False, tf32=name == "tf32", bf16=name == "bf16")
         for _ in range(2):
             solve()
         torch.cuda.synchronize()
@@ -511,7 +515,8 @@ def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
         if gold is not None:
             rec["k_matches_oracle"] = info["k"] == gold["rtsvd"]["k"]
         out[name] = rec
-    out["note"] = ("TF32: sketch and power-iteration products with one tf32 tensor-core product; "
+    out["note"] = ("TF32: sketch and power-iteration products with one tf32 tensor-core product; BF16: the same "
+                   "products on bfloat16 copies of A-hat and A-hat^T (float32 accumulation); in both the "
                    "re-projection and the rest float32")
     if gold is not None and "fp32_error_prediction" in gold["rtsvd"]:
         # first-order float32 error of the truncated solution, u32 kappa_k sqrt(N), from the oracle's
@@ -623,6 +628,46 @@ def hat_form(a, cfg, P, A, B, Om, flush, tprod, torch, steps=20):
             "k": [i["k"] for i in infos], "status": [i["status"] for i in infos],
             "note": "A-hat from one tprod_fft before the timed replays; every DFT of B and Omega, the sketch and "
                     "every other step inside"}
+
+
+def ttsvd_form(a, cfg, P, A, B, flush, tprod, torch, reps=5):
+    """The T-tSVD (Section 4.1: full tSVD of A, truncation by the discrepancy
+    principle from s = 1), the paper's slow comparison method, at full size:
+    solves per second (graph replays, L2 flushed, CUDA events), k and the
+    relative error against the oracle's solution when the golden holds it."""
+    def solve():
+        X, info, _ = tprod.ttsvd_solve(A, B, P["delta"], cfg.tau, sync=False)
+        return X, info
+
+    solve()
+    torch.cuda.synchronize()
+    g = tprod.Captured(solve, warmup=0)
+    g.replay()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    X, info = g.outputs
+    info = tprod._info_dict(info)
+    out = {"solves_per_s": reps / (ms / 1e3), "ms_per_solve": ms / reps, "k": info["k"], "r": info["r"],
+           "status": info["status"], "sweeps": info["sweeps"]}
+    gold_path = os.path.join(ROOT, "tests", "golden", f"{cfg.name}_oracle.json")
+    sol_path = os.path.join(ROOT, "tests", "golden", f"{cfg.name}_oracle_X.npz")
+    if os.path.exists(gold_path) and os.path.exists(sol_path):
+        with open(gold_path) as f:
+            gold = json.load(f)
+        sols = np.load(sol_path)
+        if "ttsvd" in sols.files:
+            x = X.cpu().numpy().astype(np.float64)
+            out["rel_err_vs_oracle"] = float(np.linalg.norm(x - sols["ttsvd"]) / np.linalg.norm(sols["ttsvd"]))
+            out["k_matches_oracle"] = info["k"] == gold["ttsvd"]["k"]
+    return out
 
 
 def differentiation_form(a, cfg, P, A, B, Om, flush, tprod, torch):

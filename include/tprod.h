@@ -68,8 +68,17 @@ typedef enum {
  *            everything else stay as TP_FP32.  The reduced-precision form of
  *            the RT-tSVD sketch (Algorithm 3's products), accepted by
  *            tprod_gemm, rtsvd_truncated_solve and their workspace queries;
- *            any other entry point rejects it with TP_ERR_ARG (or returns 0). */
-typedef enum { TP_FP32 = 0, TP_FP64 = 1, TP_TF32 = 2 } tp_precision;
+ *            any other entry point rejects it with TP_ERR_ARG (or returns 0).
+ *   TP_BF16: float data; the block sketch and power-iteration products of
+ *            rtsvd_truncated_solve[_hat] run on bfloat16 copies of A-hat and
+ *            A-hat^T (made once per solve, in the workspace: its query with
+ *            TP_BF16 counts them) and a bfloat16 right-hand side, as
+ *            tensor-core products with float32 accumulation; the
+ *            re-projection and everything else stay as TP_FP32.  Shapes the
+ *            bfloat16 products do not take (l or m not a multiple of 4)
+ *            return TP_ERR_ARG.  Accepted by the RT-tSVD entry points and
+ *            their workspace query only. */
+typedef enum { TP_FP32 = 0, TP_FP64 = 1, TP_TF32 = 2, TP_BF16 = 3 } tp_precision;
 
 /* Result record of a solve, written to device memory. */
 typedef struct {
@@ -155,9 +164,12 @@ tp_status tprod_gemm_noalloc(const void* A, const void* B, void* C, int l, int k
  * residual over all slices (delta then bounds the norm of all of E).
  *   A     : real (n, l, m)       B : real (n, l, p)     X : real (n, m, p)
  *   Omega : real (n, m, r_max)   (Gaussian test slices, supplied by the caller)
- * Limits: 1 <= block <= 32; r_max <= min(l, m); r_max <= 160 (FP32) or
- * 112 (FP64); l, m <= 1024; 1 <= p <= 64, and the small SVD's working set,
- * (r_max^2 + r_max p) complex entries, must fit in 227 KB of shared memory.
+ * Limits: 1 <= block <= 32; r_max <= min(l, m) and r_max <= 256; l, m <=
+ * 1024; 1 <= p <= 64.  The small SVD keeps R's working copy in shared memory
+ * while (r_max^2 + r_max p) complex entries fit in 227 KB, else in the
+ * workspace (global memory, L2-resident); its r_max p right-hand sides must
+ * fit in shared memory in either case; and the block orthonormalisation's
+ * working set (about (l + 1) b + 2 r_max b complex entries) must fit too.
  */
 typedef struct {
     double delta;       /* noise bound of Eq. (errbd)                                 */
@@ -223,7 +235,7 @@ tp_status rtsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_rtsv
  * iterations, the scan of Eq. (disp) from s = 1.  Singular values at or below
  * max(l,m)*eps*sigma_max are treated as zero.  B (n, l, p), X (n, m, p); p > 1
  * slices share one s (as rtsvd_truncated_solve).
- * Limits: min(l, m) <= 160 (FP32) or 112 (FP64), and as rtsvd_truncated_solve.
+ * Limits: min(l, m) <= 256, and as rtsvd_truncated_solve (with r_max = min(l, m)).
  */
 typedef struct {
     double delta;       /* noise bound of Eq. (errbd)                                 */

@@ -108,7 +108,7 @@ tp_status smem_optin(const void* kern, size_t bytes) {
     return TP_OK;
 }
 
-template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_params*);
+template <typename T> size_t rt_ws_bytes(int, int, int, int, const tp_rtsvd_params*, bool);
 template <typename T>
 tp_status rt_solve(const T*, const T*, const T*, int, int, int, int, const tp_rtsvd_params*, T*, tp_info*, void*,
                    size_t, cudaStream_t, int, const void*);
@@ -224,8 +224,9 @@ tp_status tprod_gemm(const void* A, const void* B, void* C, int l, int kk, int m
 
 size_t rtsvd_workspace_bytes(int l, int m, int n, int p, const tp_rtsvd_params* params, int prec) {
     prec = data_prec(prec);
-    if (prec == TP_FP32) return rt_ws_bytes<float>(l, m, n, p, params);
-    if (prec == TP_FP64) return rt_ws_bytes<double>(l, m, n, p, params);
+    if (prec == TP_BF16) return rt_ws_bytes<float>(l, m, n, p, params, true);
+    if (prec == TP_FP32) return rt_ws_bytes<float>(l, m, n, p, params, false);
+    if (prec == TP_FP64) return rt_ws_bytes<double>(l, m, n, p, params, false);
     return 0;
 }
 
@@ -233,9 +234,9 @@ tp_status rtsvd_truncated_solve(const void* A, const void* B, const void* Omega,
                                 const tp_rtsvd_params* params, void* X, tp_info* d_info, int prec, void* ws,
                                 size_t ws_bytes, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == TP_FP32 || prec == TP_TF32)
+    if (prec == TP_FP32 || prec == TP_TF32 || prec == TP_BF16)
         return rt_solve<float>((const float*)A, (const float*)B, (const float*)Omega, l, m, n, p, params, (float*)X,
-                               d_info, ws, ws_bytes, st, prec == TP_TF32 ? 1 : 3, nullptr);
+                               d_info, ws, ws_bytes, st, prec == TP_TF32 ? 1 : (prec == TP_BF16 ? 0 : 3), nullptr);
     if (prec == TP_FP64)
         return rt_solve<double>((const double*)A, (const double*)B, (const double*)Omega, l, m, n, p, params,
                                 (double*)X, d_info, ws, ws_bytes, st, 3, nullptr);
@@ -248,9 +249,9 @@ tp_status rtsvd_truncated_solve_hat(const void* Ahat, const void* B, const void*
                                     size_t ws_bytes, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!Ahat) return TP_ERR_ARG;
-    if (prec == TP_FP32 || prec == TP_TF32)
+    if (prec == TP_FP32 || prec == TP_TF32 || prec == TP_BF16)
         return rt_solve<float>(nullptr, (const float*)B, (const float*)Omega, l, m, n, p, params, (float*)X, d_info,
-                               ws, ws_bytes, st, prec == TP_TF32 ? 1 : 3, Ahat);
+                               ws, ws_bytes, st, prec == TP_TF32 ? 1 : (prec == TP_BF16 ? 0 : 3), Ahat);
     if (prec == TP_FP64)
         return rt_solve<double>(nullptr, (const double*)B, (const double*)Omega, l, m, n, p, params, (double*)X,
                                 d_info, ws, ws_bytes, st, 3, Ahat);

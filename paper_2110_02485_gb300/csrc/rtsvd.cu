@@ -11,6 +11,8 @@
 // one-sided Jacobi on R gives R J = U_R S, hence U = J and V = QG U_R.
 // Only U^H (Q^H b) is needed, so J itself is never stored: the rotations are
 // applied to d = Q^H b as they are made.
+#include <algorithm>
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -912,14 +914,17 @@ template <typename T>
 __global__ void __launch_bounds__(JAC_THREADS)
 k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, const cplx<T>* __restrict__ d, long sd,
          int np, T* sigma, long ssig, cplx<T>* UR, long ldu, long sU, cplx<T>* dprime, long sdp, int max_sweeps,
-         int* sweeps_out) {
-    // d and d' are r x np (np right-hand sides, row-major) per slice
+         int* sweeps_out, cplx<T>* gR, long sG) {
+    // d and d' are r x np (np right-hand sides, row-major) per slice.  The
+    // working copy of R (column-major) lives in shared memory, or, when gR is
+    // given (factors too large for shared memory: the full T-tSVD), in gR +
+    // s sG in global memory (the slices' copies stay in L2).
     typedef cplx<T> V;
     const int r = st->r;
     if (r <= 0) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* Rs = (V*)smraw;                       // column j at Rs[j*r]
-    V* dp = Rs + (size_t)r * r;
+    V* Rs = gR ? gR + (long)blockIdx.x * sG : (V*)smraw;  // column j at Rs[j*r]
+    V* dp = gR ? (V*)smraw : Rs + (size_t)r * r;
     T* sg = (T*)(dp + (size_t)r * np);  // column norms (sigma), working precision
     int* perm = (int*)(sg + r);
     __shared__ T tol_s;
@@ -964,8 +969,9 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     if (tid == 0) atomicMax(sweeps_out, sweep);
 }
 
-static size_t jacobi_smem(int r, size_t c, int np) {
-    return (size_t)r * r * c + (size_t)r * np * c + (size_t)r * sizeof(double) + (size_t)r * sizeof(int);
+static size_t jacobi_smem(int r, size_t c, int np, bool global_r = false) {
+    return (global_r ? 0 : (size_t)r * r * c) + (size_t)r * np * c + (size_t)r * sizeof(double) +
+           (size_t)r * sizeof(int);
 }
 
 // The one-sided Jacobi SVD of h square r x r factors (r from st->r, at most
@@ -979,7 +985,8 @@ tp_status jacobi_svd(int h, const void* R, long ldr, long sR, const State* st, c
     if (smem_optin((const void*)k_jacobi<T>, smem) != TP_OK) return TP_ERR_CUDA;
     prof_begin(TP_KC_SVD, stream);
     k_jacobi<T><<<h, JAC_THREADS, smem, stream>>>((const cplx<T>*)R, ldr, sR, st, (const cplx<T>*)d, sd, np, sigma,
-                                                  ssig, (cplx<T>*)UR, ldu, sU, (cplx<T>*)dprime, sdp, 60, sweeps);
+                                                  ssig, (cplx<T>*)UR, ldu, sU, (cplx<T>*)dprime, sdp, 60, sweeps,
+                                                  nullptr, 0);
     return launched(TP_KC_SVD, stream);
 }
 template tp_status jacobi_svd<float>(int, const void*, long, long, const State*, const void*, long, int, float*, long,
@@ -1093,8 +1100,11 @@ static tp_status alpha_corr(int h, const cplx<T>* UR, int r_max, cplx<T>* alpha,
 // float64 alpha_k itself (U_R orthonormal to rounding).  Up to DP_CC
 // candidates share one pass over K: each thread carries its RPT rows of every
 // candidate's residual.  np right-hand sides (alpha and B row-major with np
-// columns), summed.  Per thread and per warp in the working precision, across
-// warps in float64; the other entries of out are 0.
+// columns): a CTA per (slice, column, candidate group), column c writing its
+// squared norms to out + c h so (the reduction sums the columns); the
+// candidates are split evenly over gridDim.z CTAs, each writing its own
+// entries (the first also the zeros).  Per thread and per warp in the working
+// precision, across warps in float64.
 constexpr int DP_CC = 12;
 template <typename T, int RPT>
 __global__ void __launch_bounds__(256)
@@ -1105,29 +1115,37 @@ k_dp_scan(const cplx<T>* __restrict__ KhT, long sK, const cplx<T>* __restrict__ 
     constexpr bool CORR = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int r = st->r, s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = blockDim.x >> 5;
+    const int nw = blockDim.x >> 5, c = blockIdx.y;
+    out += (long)c * gridDim.x * so;
     double* wsum = (double*)smraw;                        // [nw][r+1]
     V* Tm = (V*)(wsum + (size_t)nw * (r + 1) + 1);        // r x DP_CC: U_k alpha_k per candidate
     V* ak = Tm + (size_t)r * DP_CC;                       // DP_CC x r: alpha^(k), zero for j >= k
     Tm = (V*)(((size_t)Tm + 15) & ~(size_t)15);
     ak = Tm + (size_t)r * DP_CC;
     const int k_init = max(1, r - p_over), ncand = r - k_init + 1;
+    const int per = (ncand + gridDim.z - 1) / gridDim.z;
+    const int q_lo = blockIdx.z * per, q_hi = min(ncand, q_lo + per);  // this CTA's candidates k_init + q
     KhT += (long)s * sK;
     const V* al = alpha + (long)s * sa;
     const V* U = UR + (long)s * sU;
     for (int e = tid; e < nw * (r + 1); e += blockDim.x) wsum[e] = 0.0;
-    for (int c = 0; c < np; ++c) {
-        for (int c0 = 0; c0 < ncand; c0 += DP_CC) {
-            const int nc = min(DP_CC, ncand - c0), kb = k_init + c0;  // candidates kb .. kb + nc - 1
+    {
+        for (int c0 = q_lo; c0 < q_hi; c0 += DP_CC) {
+            const int nc = min(DP_CC, q_hi - c0), kb = k_init + c0;  // candidates kb .. kb + nc - 1
             if (CORR) {
-                // T[i][q] = sum_{j < kb+q} U[i][j] a_j
-                for (int e = tid; e < r * nc; e += blockDim.x) {
-                    const int q = e / r, i = e - q * r;
+                // T[i][q] = sum_{j < kb+q} U[i][j] a_j: the first column in full, the others by one more
+                // term each (a thread per row i)
+                for (int i = tid; i < r; i += blockDim.x) {
                     V acc = mk<T>(0, 0);
                     const V* Ui = U + (long)i * ldu;
 #pragma unroll 4
-                    for (int j = 0; j < kb + q; ++j) cfma(acc, Ui[j], al[(long)j * np + c]);
-                    Tm[i * DP_CC + q] = acc;
+                    for (int j = 0; j < kb; ++j) cfma(acc, Ui[j], al[(long)j * np + c]);
+                    Tm[i * DP_CC] = acc;
+                    for (int q = 1; q < nc; ++q) {
+                        const int j = kb + q - 1;
+                        cfma(acc, Ui[j], al[(long)j * np + c]);
+                        Tm[i * DP_CC + q] = acc;
+                    }
                 }
                 __syncthreads();
                 // alpha^(k)_j = 2 a_j - sum_i conj(U[i][j]) T[i][q]
@@ -1204,8 +1222,11 @@ k_dp_scan(const cplx<T>* __restrict__ KhT, long sK, const cplx<T>* __restrict__ 
         }
     }
     for (int j = tid; j <= r; j += blockDim.x) {
+        const int q = j - k_init;
+        const bool mine = q >= q_lo && q < q_hi;
+        if (!mine && !(blockIdx.z == 0 && q < 0)) continue;  // other CTAs' candidates
         double a = 0.0;
-        if (j >= k_init)
+        if (mine)
             for (int w = 0; w < nw; ++w) a += wsum[w * (r + 1) + j];
         out[(long)s * so + j] = a;
     }
@@ -1219,15 +1240,17 @@ static tp_status dp_scan(int h, const cplx<T>* KhT, long sK, const cplx<T>* alph
     auto kern = l <= 256 ? k_dp_scan<T, 1> : (l <= 512 ? k_dp_scan<T, 2> : k_dp_scan<T, 4>);
     if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
     prof_begin(TP_KC_DP, stream);
-    kern<<<h, 256, smem, stream>>>(KhT, sK, alpha, sa, bhat, sb, UR, r_max, (long)r_max * r_max, st, l, np, p_over,
-                                   out, so);
+    // the candidates k_init..r (at most p + 1) over up to four CTAs per slice and column
+    const int nz = std::min(4, std::max(1, (std::min(p_over, r_max - 1) + 1 + 3) / 4));
+    kern<<<dim3((unsigned)h, (unsigned)np, (unsigned)nz), 256, smem, stream>>>(
+        KhT, sK, alpha, sa, bhat, sb, UR, r_max, (long)r_max * r_max, st, l, np, p_over, out, so);
     return launched(TP_KC_DP, stream);
 }
 
 // Global residuals (Parseval over slices), the discrepancy-principle choice
 // of k in [max(1, r-p), r], and the info record.
-__global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st, int p_over, double tau_delta,
-                            tp_info* info, double* res_hist, int r_max) {
+__global__ void k_dp_reduce(const double* out, long so, int h, int np, int n, State* st, int p_over,
+                            double tau_delta, tp_info* info, double* res_hist, int r_max) {
     extern __shared__ double res[];
     const int r = st->r;
     const int k_init = max(1, r - p_over);  // only the candidates k_init..r are needed
@@ -1236,7 +1259,8 @@ __global__ void k_dp_reduce(const double* out, long so, int h, int n, State* st,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = k_init + warp; k <= r; k += nw) {
         double a = 0.0;
-        for (int s = lane; s < h; s += 32) a += parseval_w(s, n) * out[(long)s * so + k];
+        for (int c = 0; c < np; ++c)  // the right-hand sides' partials, in a fixed order
+            for (int s = lane; s < h; s += 32) a += parseval_w(s, n) * out[((long)c * h + s) * so + k];
         a = warp_sum(a);
         if (lane == 0) res[k] = sqrt(fmax(a, 0.0) / (double)n);
     }
@@ -1281,14 +1305,17 @@ struct RtWs {
     double *partsA, *partsB, *normsq, *dpout;
     cplx<T> *Ahat, *AhT, *Bhat, *G, *Y, *Z, *Q, *BHb, *QG, *R, *d, *UR, *dprime, *alpha, *Vt, *KhT, *Xhat;
     T* sigma;
+    __nv_bfloat162 *Abf, *ATbf;
     size_t bytes;
 };
 
 // A-hat^T per slice (m x l), so that the float32 products A-hat^H Y read rows
 // (conj(A-hat^T) Y) on the tensor cores.  32 x 32 tiles through shared memory.
+// In the BF16 form (Abf, ATbf not null) the same pass also writes bfloat16
+// copies of A-hat and A-hat^T (re, im rounded to nearest, 4 bytes per entry).
 template <typename T>
 __global__ void __launch_bounds__(256) k_ctranspose(const cplx<T>* __restrict__ A, cplx<T>* __restrict__ AT, int l,
-                                                    int m) {
+                                                    int m, __nv_bfloat162* Abf, __nv_bfloat162* ATbf) {
     __shared__ cplx<T> tile[32][33];
     const long s = blockIdx.z;
     const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -1296,17 +1323,25 @@ __global__ void __launch_bounds__(256) k_ctranspose(const cplx<T>* __restrict__ 
     AT += s * l * m;
     for (int y = ty; y < 32; y += 8) {
         const int i = i0 + y, j = j0 + tx;
-        if (i < l && j < m) tile[y][tx] = A[(long)i * m + j];
+        if (i < l && j < m) {
+            const cplx<T> v = A[(long)i * m + j];
+            tile[y][tx] = v;
+            if (Abf) Abf[s * l * m + (long)i * m + j] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+        }
     }
     __syncthreads();
     for (int y = ty; y < 32; y += 8) {
         const int j = j0 + y, i = i0 + tx;
-        if (i < l && j < m) AT[(long)j * l + i] = tile[tx][y];
+        if (i < l && j < m) {
+            const cplx<T> v = tile[tx][y];
+            AT[(long)j * l + i] = v;
+            if (ATbf) ATbf[s * l * m + (long)j * l + i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+        }
     }
 }
 
 template <typename T>
-static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max, int p) {
+static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max, int p, bool bf16 = false) {
     typedef cplx<T> V;
     const long h = n / 2 + 1;
     Carver c(base, 0);
@@ -1315,7 +1350,7 @@ static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max, int p
     w.partsA = c.take<double>(rdft_parts(l, m));
     w.partsB = c.take<double>(rdft_parts(l, p));
     w.normsq = c.take<double>(h);
-    w.dpout = c.take<double>(h * (r_max + 1));
+    w.dpout = c.take<double>(h * (r_max + 1) * p);  // per right-hand side
     w.Ahat = c.take<V>(h * l * m);
     w.AhT = sizeof(T) == 4 ? c.take<V>(h * l * m) : nullptr;  // float32 only: tensor-core products
     w.Bhat = c.take<V>(h * l * p);
@@ -1334,6 +1369,10 @@ static RtWs<T> rt_carve(void* base, int l, int m, int n, int b, int r_max, int p
     w.KhT = c.take<V>(h * r_max * l);
     w.Xhat = c.take<V>(h * m * p);
     w.sigma = c.take<T>(h * r_max);
+    // BF16 form only, after everything else (the other layouts do not move):
+    // bfloat16 copies of A-hat and A-hat^T for the sketch and power products
+    w.Abf = bf16 ? c.take<__nv_bfloat162>(h * l * m) : nullptr;
+    w.ATbf = bf16 ? c.take<__nv_bfloat162>(h * l * m) : nullptr;
     w.bytes = c.off;
     return w;
 }
@@ -1345,14 +1384,19 @@ static int jac_rmax(size_t elem, int p) {
     return r;
 }
 
-constexpr int RT_MAX_RHS = 64;  // lateral slices of B per RT-tSVD call
+constexpr int RT_MAX_RHS = 64;    // lateral slices of B per RT-tSVD call
+constexpr int RT_MAX_RANK = 256;  // sketch rank (the small SVD of rank above jac_rmax runs from global memory)
 
 template <typename T>
 static tp_status rt_check(int l, int m, int n, int p, const tp_rtsvd_params* P, bool full = false) {
     if (!P || l < 1 || m < 1 || n < 1 || p < 1 || p > RT_MAX_RHS) return TP_ERR_ARG;
     if (l > 1024 || m > 1024 || n > (sizeof(T) == 4 ? 1024 : 512)) return TP_ERR_ARG;
     if (P->block < 1 || P->block > MAX_BLOCK || P->r_max < 1 || P->r_max > (l < m ? l : m)) return TP_ERR_ARG;
-    if (P->r_max > (sizeof(T) == 4 ? 160 : 112) || P->r_max > jac_rmax(sizeof(T), p)) return TP_ERR_ARG;
+    // the small SVD: in shared memory up to jac_rmax, beyond it (up to 256) with R's working copy in global
+    // memory and only the p right-hand sides in shared memory
+    if (P->r_max > RT_MAX_RANK) return TP_ERR_ARG;
+    if (P->r_max > jac_rmax(sizeof(T), p) && jacobi_smem(P->r_max, 2 * sizeof(T), p, true) > 227 * 1024)
+        return TP_ERR_ARG;
     if (!(P->tau > 0.0) || !(P->delta >= 0.0) || P->p_over < 0 || P->q_power < 0) return TP_ERR_ARG;
     if (!full && !(P->eps > 0.0) && !(P->eps_rel > 0.0)) return TP_ERR_ARG;
     const int Lmax = l > m ? l : m;
@@ -1361,9 +1405,10 @@ static tp_status rt_check(int l, int m, int n, int p, const tp_rtsvd_params* P, 
 }
 
 template <typename T>
-size_t rt_ws_bytes(int l, int m, int n, int p, const tp_rtsvd_params* P) {
+size_t rt_ws_bytes(int l, int m, int n, int p, const tp_rtsvd_params* P, bool bf16) {
     if (rt_check<T>(l, m, n, p, P) != TP_OK) return 0;
-    return rt_carve<T>(nullptr, l, m, n, P->block, P->r_max, p).bytes;
+    if (bf16 && sizeof(T) != 4) return 0;
+    return rt_carve<T>(nullptr, l, m, n, P->block, P->r_max, p, bf16).bytes;
 }
 
 #define TRY(x)                              \
@@ -1380,7 +1425,12 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
     if ((!A && !Ahat_in) || !B || !Om || !X || !info) return TP_ERR_ARG;
     if (Ahat_in && ((size_t)Ahat_in & 15)) return TP_ERR_ARG;
     const int b = P->block, r_max = P->r_max, h = n / 2 + 1;
-    RtWs<T> w = rt_carve<T>(ws, l, m, n, b, r_max, p);
+    // tc_passes: 3 = float32-accurate products, 1 = the TF32 form, 0 = the BF16
+    // form (sketch and power products on bfloat16 copies of A-hat)
+    const bool bf16 = tc_passes == 0;
+    // the bfloat16 products read 16-byte multiples per row (4 complex entries): refused before anything runs
+    if (bf16 && (sizeof(T) != 4 || (l & 3) || (m & 3))) return TP_ERR_ARG;
+    RtWs<T> w = rt_carve<T>(ws, l, m, n, b, r_max, p, bf16);
     if (!ws || ((size_t)ws & 255) || ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
     const long lm = (long)l * m;
     const int* done = &w.st->done;
@@ -1394,7 +1444,7 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
     if (w.AhT) {
         prof_begin(TP_KC_GEMM, st);
         k_ctranspose<T><<<dim3((unsigned)((m + 31) / 32), (unsigned)((l + 31) / 32), (unsigned)h), 256, 0, st>>>(
-            w.Ahat, w.AhT, l, m);
+            w.Ahat, w.AhT, l, m, w.Abf, w.ATbf);
         TRY(launched(TP_KC_GEMM, st));
     }
     // A-hat^H Y: conj(A-hat^T) Y from the transposed copy when there is one
@@ -1410,21 +1460,34 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
     // reaches are transformed too; one full launch beats a latency-bound
     // launch per block)
     TRY(rdft<T>(Om, w.G, n, m, r_max, r_max, (long)m * r_max, nullptr, nullptr, st));
+    // the sketch and power-iteration products: A-hat (op N) or conj(A-hat^T) (op R); in the BF16 form on the
+    // bfloat16 copies, tensor cores only (a shape they do not take is refused, never run on other data)
+    auto sketch = [&](int M, int N, int K, const void* Af, const void* Ab, long lda, int op, const cplx<T>* Bm,
+                      long ldb, long sB, cplx<T>* C, long ldc, long sC) -> tp_status {
+        if (!bf16)
+            return cgemm<T>(h, M, N, K, 0, 0, 0, 1, 0, Af, lda, lm, op, Bm, ldb, sB, OP_N, 0, 0, C, ldc, sC, done, st,
+                            &w.st->status, tc_passes);
+        // a right-hand side that does not start on a 16-byte boundary (the columns of an odd block of Omega)
+        // cannot be a TMA source: that product runs float32-accurate on the float32 A-hat instead
+        if (((uintptr_t)Bm & 15) || (ldb & 1) || (sB & 1))
+            return cgemm<T>(h, M, N, K, 0, 0, 0, 1, 0, Af, lda, lm, op, Bm, ldb, sB, OP_N, 0, 0, C, ldc, sC, done,
+                            st, &w.st->status, 3);
+        const tp_status e = zgemm_tc(h, M, N, K, Ab, lda, lm, op, Bm, ldb, sB, C, ldc, sC, done, &w.st->status, 0,
+                                     st);
+        return e == TP_ERR_UNSUPPORTED ? TP_ERR_ARG : e;
+    };
     const int nblk = (r_max + b - 1) / b;
     for (int blk = 0; blk < nblk; ++blk) {
         const int r0 = blk * b, bb = (b < r_max - r0) ? b : r_max - r0;
         // sketch, power iterations, orthonormalise
-        TRY(cgemm<T>(h, l, bb, m, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_N, w.G + r0, r_max, (long)m * r_max, OP_N, 0, 0,
-                     w.Y, bb, (long)l * bb, done, st, &w.st->status, tc_passes));
+        TRY(sketch(l, bb, m, w.Ahat, w.Abf, m, OP_N, w.G + r0, r_max, (long)m * r_max, w.Y, bb, (long)l * bb));
         const bool last_y = (P->q_power == 0);
         TRY(orth<T>(h, w.Y, (long)l * bb, l, bb, w.Q, (long)r_max * l, r0, last_y ? w.Q : nullptr, nullptr, 0, 0, 0,
                     nullptr, done, st));
         for (int it = 0; it < P->q_power; ++it) {
-            TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, AH, ldah, lm, op_h, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.Z, bb,
-                         (long)m * bb, done, st, &w.st->status, tc_passes));
+            TRY(sketch(m, bb, l, AH, w.ATbf, ldah, op_h, w.Y, bb, (long)l * bb, w.Z, bb, (long)m * bb));
             TRY(orth<T>(h, w.Z, (long)m * bb, m, bb, nullptr, 0, 0, nullptr, nullptr, 0, 0, 0, nullptr, done, st));
-            TRY(cgemm<T>(h, l, bb, m, 0, 0, 0, 1, 0, w.Ahat, m, lm, OP_N, w.Z, bb, (long)m * bb, OP_N, 0, 0, w.Y, bb,
-                         (long)l * bb, done, st, &w.st->status, tc_passes));
+            TRY(sketch(l, bb, m, w.Ahat, w.Abf, m, OP_N, w.Z, bb, (long)m * bb, w.Y, bb, (long)l * bb));
             const bool last = (it + 1 == P->q_power);
             TRY(orth<T>(h, w.Y, (long)l * bb, l, bb, w.Q, (long)r_max * l, r0, last ? w.Q : nullptr, nullptr, 0, 0,
                         0, nullptr, done, st));
@@ -1444,12 +1507,14 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
     TRY(cgemm<T>(h, r_max, p, l, dr, 0, 0, 1, 0, w.Q, l, (long)r_max * l, OP_R, w.Bhat, p, (long)l * p, OP_N, 0, 0,
                  w.d, p, rp, nullptr, st));
     {
-        const size_t smem = jacobi_smem(r_max, sizeof(cplx<T>), p);
+        // factors too large for shared memory: the working copy in Vt (free until V = Q_G U_R is formed)
+        const bool gmode = r_max > jac_rmax(sizeof(T), p);
+        const size_t smem = jacobi_smem(r_max, sizeof(cplx<T>), p, gmode);
         if (smem_optin((const void*)k_jacobi<T>, smem) != TP_OK) return TP_ERR_CUDA;
         prof_begin(TP_KC_SVD, st);
         k_jacobi<T><<<h, JAC_THREADS, smem, st>>>(w.R, r_max, (long)r_max * r_max, w.st, w.d, rp, p, w.sigma, r_max,
                                                     w.UR, r_max, (long)r_max * r_max, w.dprime, rp, 60,
-                                                    &w.st->sweeps);
+                                                    &w.st->sweeps, gmode ? w.Vt : nullptr, (long)m * r_max);
         TRY(launched(TP_KC_SVD, st));
     }
     prof_begin(TP_KC_MISC, st);
@@ -1478,7 +1543,7 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
     TRY(dp_scan<T>(h, w.KhT, (long)r_max * l, w.alpha, rp, w.Bhat, (long)l * p, w.UR, r_max, w.st, l, p, P->p_over,
                    w.dpout, r_max + 1, st));
     prof_begin(TP_KC_DP, st);
-    k_dp_reduce<<<1, 256, (r_max + 1) * sizeof(double), st>>>(w.dpout, r_max + 1, h, n, w.st, P->p_over,
+    k_dp_reduce<<<1, 256, (r_max + 1) * sizeof(double), st>>>(w.dpout, r_max + 1, h, p, n, w.st, P->p_over,
                                                               P->tau * P->delta, info, P->res_hist, r_max);
     TRY(launched(TP_KC_DP, st));
     // float32: the coefficients of the chosen k in the computed (not exactly orthonormal) basis
@@ -1620,8 +1685,8 @@ template tp_status rt_adjoint<float>(const float*, int, int, int, int, const tp_
                                      cudaStream_t);
 template tp_status rt_adjoint<double>(const double*, int, int, int, int, const tp_rtsvd_params*, double*, void*,
                                       size_t, cudaStream_t);
-template size_t rt_ws_bytes<float>(int, int, int, int, const tp_rtsvd_params*);
-template size_t rt_ws_bytes<double>(int, int, int, int, const tp_rtsvd_params*);
+template size_t rt_ws_bytes<float>(int, int, int, int, const tp_rtsvd_params*, bool);
+template size_t rt_ws_bytes<double>(int, int, int, int, const tp_rtsvd_params*, bool);
 template tp_status rt_solve<float>(const float*, const float*, const float*, int, int, int, int,
                                    const tp_rtsvd_params*, float*, tp_info*, void*, size_t, cudaStream_t, int,
                                    const void*);

@@ -38,9 +38,15 @@
 // op = R (conj(A) B, A row-major) uses the op = N kernel with the signs of
 // the right-hand side flipped; the RT-tSVD forms A-hat^H Y this way from a
 // transposed copy of A-hat, so every large product takes the swizzled path.
+// BF16 form (NP = 0): A is a bfloat16 copy of the complex matrix (interleaved
+// re, im; 4 bytes per entry), the right-hand side is rounded to bfloat16 as it
+// is expanded, and the MMAs are kind::f16 with float32 accumulation: a stage
+// holds 64 real reduction entries (the same 128-byte swizzled rows), one MMA
+// per 16-entry step, no lo tile.  Relative error of a product term about 2^-8.
 // Every wait is bounded; on a timeout the kernel records TP_ERR_TIMEOUT,
 // waits (bounded) for its MMAs, frees its tensor memory and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
@@ -98,11 +104,23 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor, kind::f16: D float32, A and B bfloat16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        :
+        : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
         :
         : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
@@ -186,25 +204,33 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, uint32_t lbo) {
     return (uint32_t)(k >> 2) * lbo + (uint32_t)(row >> 3) * TC_SBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
 }
 
+// The same for 2-byte elements: 8 per 16-byte core-matrix row.
+__device__ __forceinline__ uint32_t kmaj_off16(int row, int k, uint32_t lbo) {
+    return (uint32_t)(k >> 3) * lbo + (uint32_t)(row >> 3) * TC_SBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
 __device__ __forceinline__ float pick4(const float4& v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
 
 // Stage buffers: raw A (TMA), hi A (op C only; op N uses the raw tile), lo A
 // (3xTF32 only), raw B rows (TMA), and the real right-hand side B_op.  NP = 3
-// (hi*hi + hi*lo + lo*hi, float32 accuracy) or 1 (hi*hi, the TF32 precision
-// form).
+// (hi*hi + hi*lo + lo*hi, float32 accuracy), 1 (hi*hi, the TF32 precision
+// form) or 0 (bfloat16 A and B_op, the BF16 form; op N only).  KT real
+// reduction entries per stage: 32 in tf32, 64 in bfloat16 (the same 128-byte
+// rows).
 template <int OPA, int NCP, int NP> struct TcCfg {
+    static constexpr int KT = NP == 0 ? 2 * TC_KT : TC_KT;
     static constexpr int NB = (NP == 3 ? 4 : 2) * NCP;  // B_op rows: (re, im) x (hi[, lo])
     static constexpr uint32_t LBO_B = (NB / 8) * 128;
-    static constexpr int KB = OPA == OP_N ? TC_KT / 2 : TC_KT;  // B rows per stage
+    static constexpr int KB = OPA == OP_N ? KT / 2 : KT;  // B rows per stage
     static constexpr int A_RAW = 0;
     static constexpr int A_HI = OPA == OP_N ? 0 : TC_A_BYTES;
     static constexpr int A_LO = A_HI + TC_A_BYTES;  // used when NP == 3
     static constexpr int B_RAW = (NP == 3 ? A_LO : A_HI) + TC_A_BYTES;
     static constexpr int B_RAW_BYTES = KB * NCP * 8;
     static constexpr int B_OP = B_RAW + B_RAW_BYTES;
-    static constexpr int STAGE = B_OP + NB * TC_KT * 4;  // a multiple of 1024
+    static constexpr int STAGE = B_OP + NB * KT * (NP == 0 ? 2 : 4);  // a multiple of 1024
     // two CTAs per SM when two stages fit in half the shared memory (the TMA
     // stream of one CTA does not fill an SM's share of L2 bandwidth), with as
     // many stages as fit there (up to four: each CTA's tiles are latency-bound,
@@ -226,6 +252,19 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
     const float2* rb = (const float2*)(st + G::B_RAW);
     float* Bs = (float*)(st + G::B_OP);
     constexpr int RS = (NCP / 8) * TC_SBO;  // rows c, NCP + c, ...: NCP / 8 core matrices apart
+    if (NP == 0) {
+        // bfloat16: A is used as loaded; the right-hand side's re and im rows
+        // (signs as below) rounded to bfloat16, two entries per 4-byte store
+        const float sa = CONJ ? 1.f : -1.f, sb = CONJ ? -1.f : 1.f;
+        for (int e = t; e < G::KB * NCP; e += TC_CONV_THREADS) {
+            const int jj = e / NCP, c = e - jj * NCP;
+            const float2 x = rb[e];
+            char* q = (char*)Bs + kmaj_off16(c, 2 * jj, G::LBO_B);
+            *(__nv_bfloat162*)(q) = __floats2bfloat162_rn(x.x, sa * x.y);
+            *(__nv_bfloat162*)(q + RS) = __floats2bfloat162_rn(x.y, sb * x.x);
+        }
+        return;
+    }
     if (OPA == OP_N) {
         if (NP == 3) {
             // element-wise on the swizzled tile: hi is the tile itself, lo at the same offset
@@ -311,7 +350,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     C += (long)sl * sC;
     const int Mr = OPA == OP_N ? Mc : 2 * Mc;
     const int Kr = OPA == OP_N ? 2 * Kc : Kc;
-    const int nkt = (Kr + TC_KT - 1) / TC_KT;
+    const int nkt = (Kr + G::KT - 1) / G::KT;
     // stage ring at a 1024-byte boundary (the 128-byte swizzle repeats every 1024 bytes)
     const uint32_t sbase = (smem_u32(sm_raw) + 1023u) & ~1023u;
     unsigned char* sgen = sm_raw + (sbase - smem_u32(sm_raw));
@@ -346,7 +385,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
                 const uint32_t fb = smem_u32(&full[st]);
                 mbar_expect_tx(fb, G::TX);
-                if (OPA == OP_N) tma_load_3d(buf + G::A_RAW, &tmA, kt * TC_KT, row0, sl, fb);
+                if (OPA == OP_N) tma_load_3d(buf + G::A_RAW, &tmA, kt * G::KT, row0, sl, fb);
                 else tma_load_3d(buf + G::A_RAW, &tmA, row0, kt * TC_KT, sl, fb);
                 tma_load_3d(buf + G::B_RAW, &tmB, 0, kt * G::KB, sl, fb);
                 issued = kt + 1;
@@ -357,7 +396,8 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         }
     } else if (warp == TC_MMA_WARP) {
         if (lane == 0) {
-            const uint32_t id_full = idesc_tf32(TC_M, G::NB), id_half = idesc_tf32(TC_M, 2 * NCP);
+            const uint32_t id_full = NP == 0 ? idesc_bf16(TC_M, G::NB) : idesc_tf32(TC_M, G::NB);
+            const uint32_t id_half = idesc_tf32(TC_M, 2 * NCP);
             int issued = 0;
             for (int kt = 0; kt < nkt; ++kt) {
                 const int st = kt % G::NS;
@@ -375,6 +415,10 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                         dal = sdesc(buf + G::A_LO + ks * 2 * TC_LBO_A, TC_LBO_A, TC_SBO);
                     }
                     const uint64_t db = sdesc(buf + G::B_OP + ks * 2 * G::LBO_B, G::LBO_B, TC_SBO);
+                    if (NP == 0) {  // 16 bfloat16 reduction entries per step (32 bytes, as 8 tf32)
+                        mma_bf16(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);
+                        continue;
+                    }
                     mma_tf32(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);  // hi*hi [| hi*lo]
                     if (NP == 3) mma_tf32(tmem, dal, db, id_half, 1u);              // += lo*hi
                 }
@@ -449,16 +493,18 @@ EncodeFn encode_fn() {
     return fn;
 }
 
-// 3-D float32 tensor map over (columns, rows, slices) with the given box.
+// 3-D tensor map over (columns, rows, slices) with the given box; float32
+// elements, or bfloat16 when bf16.
 bool make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t slices, uint64_t row_bytes,
-              uint64_t slice_bytes, uint32_t box_c, uint32_t box_r, bool swz) {
+              uint64_t slice_bytes, uint32_t box_c, uint32_t box_r, bool swz, bool bf16 = false) {
     EncodeFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {cols, rows, slices};
     const cuuint64_t strides[2] = {row_bytes, slice_bytes};
     const cuuint32_t box[3] = {box_c, box_r, 1};
     const cuuint32_t es[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+    return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+              const_cast<void*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -469,9 +515,11 @@ tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, lon
                     int c0, cudaStream_t st) {
     typedef TcCfg<OPA, NCP, NP> G;
     CUtensorMap ma, mb;
-    // A: op N rows i of 2K floats (box 32 x 128, swizzled); op C rows i of 2M floats (box 128 x 32)
-    const bool oka = OPA == OP_N ? make_map(&ma, A, 2 * (uint64_t)K, M, batch, 8 * (uint64_t)lda,
-                                            8 * (uint64_t)sA, TC_KT, TC_M, true)
+    // A: op N rows i of 2K floats (box 32 x 128, swizzled; bfloat16: 2K entries of 2 bytes, box 64 x 128);
+    // op C rows i of 2M floats (box 128 x 32)
+    const uint64_t ab = NP == 0 ? 4 : 8;  // bytes per complex entry of A
+    const bool oka = OPA == OP_N ? make_map(&ma, A, 2 * (uint64_t)K, M, batch, ab * (uint64_t)lda,
+                                            ab * (uint64_t)sA, G::KT, TC_M, true, NP == 0)
                                  : make_map(&ma, A, 2 * (uint64_t)M, K, batch, 8 * (uint64_t)lda,
                                             8 * (uint64_t)sA, TC_M, TC_KT, false);
     const bool okb =
@@ -495,7 +543,9 @@ tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long
                    long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes, cudaStream_t st,
                    int trans_out, const int* ncap, int c0) {
     if (opA != OP_N && opA != OP_R && opA != OP_C) return TP_ERR_UNSUPPORTED;
-    if (passes != 1 && passes != 3) return TP_ERR_UNSUPPORTED;
+    if (passes != 0 && passes != 1 && passes != 3) return TP_ERR_UNSUPPORTED;
+    // bfloat16 A (passes 0): op N or R only, rows and slices 16-byte multiples (4 complex entries)
+    if (passes == 0 && (opA == OP_C || (lda & 3) || (sA & 3))) return TP_ERR_UNSUPPORTED;
     if (trans_out && opA == OP_C) return TP_ERR_UNSUPPORTED;
     if (batch < 1 || batch > 65535 || M < 1 || N < 1 || N > 32 || K < 1) return TP_ERR_UNSUPPORTED;
     // tensor maps: 16-byte aligned bases and 16-byte multiples for the row and slice strides
@@ -517,6 +567,10 @@ tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long
         if (opA == OP_N) TC_SWITCH(OP_N, false, 3)
         if (opA == OP_R) TC_SWITCH(OP_N, true, 3)
         TC_SWITCH(OP_C, false, 3)
+    }
+    if (passes == 0) {
+        if (opA == OP_N) TC_SWITCH(OP_N, false, 0)
+        TC_SWITCH(OP_N, true, 0)
     }
     if (opA == OP_N) TC_SWITCH(OP_N, false, 1)
     if (opA == OP_R) TC_SWITCH(OP_N, true, 1)

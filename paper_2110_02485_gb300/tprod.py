@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 TP_OK, TP_ERR_ARG, TP_ERR_CUDA, TP_ERR_WORKSPACE = 0, -1, -2, -3
 TP_ERR_BREAKDOWN, TP_ERR_NOT_CONVERGED, TP_ERR_TIMEOUT, TP_ERR_UNSUPPORTED = -4, -5, -6, -7
 TP_ERR_NONFINITE = -8
-TP_FP32, TP_FP64, TP_TF32 = 0, 1, 2
+TP_FP32, TP_FP64, TP_TF32, TP_BF16 = 0, 1, 2, 3
 
 
 class TpInfo(ctypes.Structure):
@@ -409,24 +409,28 @@ def rtsvd_adjoint(fac: RtsvdFactor, G: torch.Tensor) -> torch.Tensor:
 
 
 def rtsvd_solve(A, B, Omega, delta, tau, p_over, block=16, q_power=1, r_max=None, eps=0.0, eps_rel=0.0,
-                res_hist=False, sync=True, tf32=False, keep=False, Ahat=None, n=None):
+                res_hist=False, sync=True, tf32=False, keep=False, Ahat=None, n=None, bf16=False):
     """RT-tSVD method (Section 4.2).  Returns (X, info[, res_hist][, factor]).
 
     B is (n, l, p): p > 1 lateral slices share one factorisation and one k
     (problem (I6)).  tf32=True (float32 only): the TP_TF32 precision form of
     the block sketch and projection products.  keep=True also returns an
     RtsvdFactor for rtsvd_adjoint.  With A=None, Ahat (the half spectrum
-    from fft(A)) and n: the rtsvd_truncated_solve_hat entry point."""
+    from fft(A)) and n: the rtsvd_truncated_solve_hat entry point.
+    bf16=True (float32 only): the TP_BF16 form (sketch and power products on
+    bfloat16 copies of A-hat)."""
     op = _Op(A, Ahat, n)
     _dev(B, Omega)
     n, l, m = op.n, op.l, op.m
     p = B.shape[2]
     r_max = min(l, m) if r_max is None else r_max
     prec = op.prec
-    if tf32:
+    if tf32 and bf16:
+        raise ValueError("tf32 and bf16 are two different forms")
+    if tf32 or bf16:
         if prec != TP_FP32:
-            raise TypeError("tf32 needs float32 tensors")
-        prec = TP_TF32
+            raise TypeError("tf32 and bf16 need float32 tensors")
+        prec = TP_TF32 if tf32 else TP_BF16
     X = torch.empty((n, m, p), dtype=op.dtype, device=op.device)
     hist = torch.empty(r_max + 1, dtype=torch.float64, device=op.device) if res_hist else None
     P = RtsvdParams(float(delta), float(tau), float(eps), float(eps_rel), int(p_over), int(q_power), int(block),

@@ -5,7 +5,8 @@ results on a full-size deblurring workload that bench.py times
 
 The .json holds the scalars (truncation indices, statuses, margins, residual
 histories, mu, the float32 feasibility figures); the .npz holds the complete
-float64 solutions X (n, N, 1) of the RT-tSVD, tGKB and Tikhonov-tGKB solves.
+float64 solutions X (n, N, 1) of the RT-tSVD, tGKB and Tikhonov-tGKB solves
+(and, up to N = 256, of the T-tSVD).
 
 Calls only the oracle and the seeded input generator:
 
@@ -62,10 +63,13 @@ def main(name: str) -> None:
                       "res": {str(k): v for k, v in r2["res"].items()}})
     r3 = O.tgkt_solve(A, B, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)
     pack("tgkt", r3, {"mu": float(r3["mu"]), "residual": float(r3["residual"])})
+    if cfg.N <= 256:  # the full tSVD (Section 4.1) of the comparison tables
+        r4 = O.ttsvd_solve(A, B, P["delta"], cfg.tau)
+        pack("ttsvd", r4, {"residual": float(r4["res"][r4["k"]]), "margin": float(r4["margin"])})
     with open(os.path.join(HERE, f"{name}_oracle.json"), "w") as f:
         json.dump(out, f)
     np.savez(os.path.join(HERE, f"{name}_oracle_X.npz"), **sols)
-    print({m: {k: out[m].get(k) for k in ("k", "status", "margin", "mu", "r")} for m in ("rtsvd", "tgkb", "tgkt")})
+    print({m: {k: out[m].get(k) for k in ("k", "status", "margin", "mu", "r")} for m in sols})
 
 
 if __name__ == "__main__":

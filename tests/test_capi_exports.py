@@ -87,8 +87,9 @@ def test_product_path_has_no_cpu_fallback():
 
 def test_rtsvd_lateral_slice_limits(lib):
     """Workspace sizing (host only) accepts 1 <= p <= 64 lateral slices of B,
-    grows with p, and refuses an r_max whose small SVD working set
-    (r_max^2 + r_max p complex entries) would not fit in shared memory."""
+    grows with p, and refuses r_max beyond 256 or one whose right-hand sides
+    (r_max p complex entries, kept in shared memory by the small SVD also when
+    R's working copy moves to global memory) would not fit."""
     from paper_2110_02485_gb300 import build, tprod
     L = tprod.load(build.build())
     P = tprod.RtsvdParams(1.0, 1.1, 0.1, 0.0, 2, 1, 16, 64, None)
@@ -96,10 +97,16 @@ def test_rtsvd_lateral_slice_limits(lib):
     assert all(s > 0 for s in sizes) and sizes == sorted(sizes) and sizes[0] < sizes[-1]
     for p in (0, 65, -1):
         assert L.rtsvd_workspace_bytes(256, 256, 256, p, ctypes.byref(P), tprod.TP_FP32) == 0
-    # FP32 at r_max = 160: 160^2 + 160 p complex64 entries fit for p = 1, not for p = 64
-    P.r_max = 160
-    assert L.rtsvd_workspace_bytes(256, 256, 256, 1, ctypes.byref(P), tprod.TP_FP32) > 0
-    assert L.rtsvd_workspace_bytes(256, 256, 256, 64, ctypes.byref(P), tprod.TP_FP32) == 0
+    # FP32 at r_max = 160 and 256: R in shared memory for p = 1, in global memory for p = 64 (160 x 64 and
+    # 256 x 64 complex64 right-hand sides fit); FP64 at r_max = 256, p = 64: 256 x 64 complex128 do not
+    for r in (160, 256):
+        P.r_max = r
+        assert L.rtsvd_workspace_bytes(256, 256, 256, 1, ctypes.byref(P), tprod.TP_FP32) > 0
+        assert L.rtsvd_workspace_bytes(256, 256, 256, 64, ctypes.byref(P), tprod.TP_FP32) > 0
+    assert L.rtsvd_workspace_bytes(256, 256, 256, 64, ctypes.byref(P), tprod.TP_FP64) == 0
+    assert L.rtsvd_workspace_bytes(256, 256, 256, 8, ctypes.byref(P), tprod.TP_FP64) > 0
+    P.r_max = 257
+    assert L.rtsvd_workspace_bytes(512, 512, 256, 1, ctypes.byref(P), tprod.TP_FP32) == 0
 
 
 def test_workspace_queries_refuse_out_of_range_requests(lib):
@@ -109,8 +116,9 @@ def test_workspace_queries_refuse_out_of_range_requests(lib):
     L = tprod.load(build.build())
     T = tprod.TtsvdParams(1.0, 1.1, None)
     assert L.ttsvd_workspace_bytes(64, 64, 32, 1, ctypes.byref(T), tprod.TP_FP32) > 0
-    assert L.ttsvd_workspace_bytes(200, 200, 32, 1, ctypes.byref(T), tprod.TP_FP32) == 0   # min(l, m) > 160
-    assert L.ttsvd_workspace_bytes(120, 120, 32, 1, ctypes.byref(T), tprod.TP_FP64) == 0   # > 112 in FP64
+    assert L.ttsvd_workspace_bytes(256, 256, 32, 1, ctypes.byref(T), tprod.TP_FP32) > 0    # R in global memory
+    assert L.ttsvd_workspace_bytes(256, 256, 32, 1, ctypes.byref(T), tprod.TP_FP64) > 0
+    assert L.ttsvd_workspace_bytes(300, 300, 32, 1, ctypes.byref(T), tprod.TP_FP32) == 0   # min(l, m) > 256
     assert L.tgkb_triplets_workspace_bytes(64, 64, 32, 20, tprod.TP_FP32) > 0
     assert L.tgkb_triplets_workspace_bytes(256, 256, 32, 200, tprod.TP_FP32) == 0           # (k+1)^2 too large
     assert L.tgkb_triplets_workspace_bytes(16, 16, 8, 17, tprod.TP_FP32) == 0               # k > min(l, m)

@@ -46,8 +46,9 @@ def work(request):
     with open(os.path.join(HERE, "golden", f"{name}_oracle.json")) as f:
         gold = json.load(f)
     sols = np.load(os.path.join(HERE, "golden", f"{name}_oracle_X.npz"))
-    for m in ("rtsvd", "tgkb", "tgkt"):
-        gold[m]["X"] = sols[m]
+    for m in ("rtsvd", "tgkb", "tgkt", "ttsvd"):
+        if m in sols.files:
+            gold[m]["X"] = sols[m]
     cfg = synth.CONFIGS[name]
     P = synth.blur_problem(cfg, seed=gold["seed"])
     assert abs(P["delta"] - gold["delta"]) <= 1e-12 * gold["delta"]
@@ -98,6 +99,35 @@ def test_rtsvd_full_size_tf32_form(tp, work):
     assert info["status"] == 0
     assert rel(X, ref) <= 3e-3
     assert true_residual(P, X) <= ref["tau_delta"] * (1 + 1e-3)
+
+
+def test_rtsvd_full_size_bf16_form(tp, work):
+    """The BF16 form of the RT-tSVD (bfloat16 sketch and power products,
+    float32 re-projection) at full size: within the reduced-precision bound
+    3e-3 of the oracle, and the discrepancy principle holds for the returned
+    solution (the bfloat16 tie band, 100 u_bf16 = 0.4 in the margin, covers
+    both stored margins, so k need not equal the oracle's)."""
+    cfg, P, gold = work
+    ref = gold["rtsvd"]
+    X, info = tp.rtsvd_solve(dev(P["A"]), dev(P["B"]), dev(P["Omega"]), P["delta"], cfg.tau, cfg.p_over, cfg.block,
+                             cfg.q_power, cfg.r_max, eps_rel=cfg.eps_rel, bf16=True)
+    X = X.cpu().numpy()
+    assert info["status"] == 0
+    assert rel(X, ref) <= 3e-3
+    assert true_residual(P, X) <= ref["tau_delta"] * (1 + 1e-3)
+
+
+def test_ttsvd_full_size(tp, work):
+    """The T-tSVD (Section 4.1, the full tSVD of A, rank 256 at 256^3: the
+    small SVD beyond shared memory) where the golden holds the oracle's."""
+    cfg, P, gold = work
+    if "ttsvd" not in gold or "X" not in gold["ttsvd"]:
+        pytest.skip("no T-tSVD golden for this workload")
+    ref = gold["ttsvd"]
+    assert ref["margin"] > 1e-4
+    X, info = tp.ttsvd_solve(dev(P["A"]), dev(P["B"]), P["delta"], cfg.tau)
+    assert info["r"] == cfg.N
+    check(info, X.cpu().numpy(), ref, P, TOL_FP32)
 
 
 def test_tgkb_full_size(tp, work):

@@ -304,11 +304,20 @@ def test_rtsvd_several_lateral_slices_match_oracle(tp, dtype, N, n, block, p, r_
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("N,n,l,p", [(12, 8, None, 1), (16, 9, None, 1), (20, 16, 28, 1), (24, 6, None, 3),
-                                     (40, 8, None, 1)])
+                                     (40, 8, None, 1), (192, 4, None, 1), (256, 3, None, 2)])
 def test_ttsvd_matches_oracle(tp, dtype, N, n, l, p):
     """T-tSVD (Section 4.1) through the RT-tSVD path with the t-identity sketch
     against the oracle's full tSVD: the truncation index, the solution and the
-    residual at every s."""
+    residual at every s.  N = 192 and 256 take ranks beyond the shared-memory
+    small SVD (its working copy in global memory).
+
+    At N >= 160 the leading singular values of each Fourier slice cluster
+    (relative gaps 5e-4 to 1e-3 against 1e-2 at N = 40): a cut inside the
+    cluster separates singular vectors that float32 rounding mixes, so
+    single-index residuals there move by about u sqrt(r) / gap (2e-3 at
+    N = 256); those are held to twice that bound, computed from the operator's
+    own gaps, while the cuts the discrepancy principle weighs (k - 2 .. k + 2)
+    and the solution are held to the usual bounds."""
     A, B, delta = problem(N, n, seed=11 + N, l=l, p=p)
     tau = 1.1
     ref = O.ttsvd_solve(A.astype(np.float64), B.astype(np.float64), delta, tau)
@@ -319,9 +328,15 @@ def test_ttsvd_matches_oracle(tp, dtype, N, n, l, p):
     # the oracle forms the residual as sqrt(||B||^2 - ||U_s^T B||^2), which
     # cancels to about sqrt(u) ||B|| near full rank: compare above that floor
     floor = 1e-6 * np.linalg.norm(B)
+    clustered = dtype == torch.float32 and N >= 160
+    if clustered:  # twice the first-order bound u sqrt(r) / gap, gap the smallest leading relative gap
+        S = np.linalg.svd(O.fft3(A.astype(np.float64)), compute_uv=False)
+        gap = float(((S[:, :8] - S[:, 1:9]) / S[:, :1]).min())
+        loose = float(np.finfo(np.float32).eps) * np.sqrt(info["r"]) / gap
     for k, rk in ref["res"].items():
         if k >= 1 and rk > floor:
-            assert abs(hist[k] - rk) <= res_tol(rk, B, dtype), k
+            tol = loose * rk if clustered and abs(k - ref["k"]) > 2 else res_tol(rk, B, dtype)
+            assert abs(hist[k] - rk) <= tol, k
     if exact_k_required(ref, dtype):
         assert info["k"] == ref["k"]
         assert info["status"] == ref["status"]
@@ -838,3 +853,37 @@ def test_hat_entry_points_refuse_a_missing_or_mismatched_spectrum(tp):
         tp.tgkb_solve(None, Bd, delta, 1.1, 4, Ahat=Ah, n=8)   # 8 // 2 + 1 != 4 slices
     with pytest.raises(ValueError):
         tp.tgkb_solve(None, Bd, delta, 1.1, 4)                 # neither A nor A-hat
+
+
+# ------------------------------------------------------ BF16 sketch form ----
+
+def test_rtsvd_bf16_form_matches_oracle_within_its_bound(tp):
+    """The TP_BF16 form (sketch and power products on bfloat16 copies of A-hat,
+    float32 accumulation, float32 re-projection) on the oracle-sized workload
+    (config n32): the oracle's sketch rank and truncation index, and the
+    solution within the reduced-precision bound 3e-3 (measured 4.9e-5 by a
+    bfloat16 emulation of the sketch in float64; on small blur problems whose
+    sketch stops just past k + p the bfloat16 error reaches 3e-3 to 1.5e-2, so
+    the bound is a property of the workload, not of the products)."""
+    P = synth.blur_problem("n32")
+    cfg = P["cfg"]
+    A64, B64, Om64 = (P[k].astype(np.float64) for k in ("A", "B", "Omega"))
+    ref = O.rtsvd_solve(A64, B64, Om64, P["delta"], cfg.tau, cfg.eps_rel * np.sqrt(O.fro2(A64)), cfg.p_over,
+                        cfg.block, cfg.q_power, cfg.r_max)
+    f = torch.float32
+    A, B, Om = dev(P["A"], f), dev(P["B"], f), dev(P["Omega"], f)
+    X, info = tp.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                             eps_rel=cfg.eps_rel, bf16=True)
+    assert info["r"] == ref["r"] and info["k"] == ref["k"]
+    assert rel(X.cpu().numpy(), ref["X"]) <= 3e-3
+    Xh, ih = tp.rtsvd_solve(None, B, Om, P["delta"], cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                            eps_rel=cfg.eps_rel, bf16=True, Ahat=tp.fft(A), n=cfg.N)
+    assert ih["k"] == info["k"] and rel(Xh.cpu().numpy(), ref["X"]) <= 3e-3
+
+
+def test_rtsvd_bf16_form_refuses_shapes_its_products_do_not_take(tp):
+    A, B, delta = problem(18, 8, seed=2)     # 18 complex entries a row: not a multiple of 4
+    Om = rnd((8, 18, 18), 3).astype(np.float32)
+    f = torch.float32
+    with pytest.raises(tp.TprodError):
+        tp.rtsvd_solve(dev(A, f), dev(B, f), dev(Om, f), delta, 1.1, 3, 4, 1, r_max=18, eps_rel=0.02, bf16=True)
