@@ -20,4 +20,4 @@ from .talgebra import (fft3, ifft3, ifft3_real, dft3_naive, fro2, fro2_hat, tpro
 from .methods import (STATUS_OK, STATUS_NOT_CONVERGED, ttsvd_solve, ttsvd_adjoint, rtsvd_alg3, rtsvd_block, rtsvd_prefix,
                       rtsvd_solve, rtsvd_adjoint, tgkb_hat, tgkb_solve, tgkb_p_solve, ritz_triplets, nested_tgkb_p_solve, bidiag, tgkt_solve, tikhonov_fixed_mu,
                       tikhonov_residual, tlanczos_hat, tlanczos_solve, tridiag,
-                      tikhonov_rho, grad_c_separable)
+                      tikhonov_rho, grad_c_separable, tgkt_fixed, tgkt_adjoint)

@@ -564,6 +564,123 @@ def grad_c_separable(X, G, c, lam=0.0, rho=None):
 
 
 # --------------------------------------------------------------------------
+# Gradient with respect to B of the Tikhonov-tGKB solution (Section 5) at a
+# fixed number of steps k and a fixed mu.
+# --------------------------------------------------------------------------
+
+def tgkt_fixed(A, B, k, mu):
+    """The Tikhonov-tGKB solution for one lateral slice B after k steps of
+    Algorithm 4, at the given mu (no discrepancy choice of k or mu)."""
+    g = tgkb_solve(A, B, 0.0, 1.0, k, k_fixed=k)
+    X, _ = tikhonov_fixed_mu(g, mu)
+    return X
+
+
+def _gkb_slice_taped(a: np.ndarray, b: np.ndarray, k: int) -> dict:
+    """k steps of Algorithm 4 on one Fourier slice (a: l x m, b: l) with the
+    intermediate vectors kept for the reverse sweep; reorthogonalisation by
+    two classical Gram-Schmidt passes, as tgkb_hat."""
+    l, m = a.shape
+    U = np.zeros((l, k + 1), complex)
+    V = np.zeros((m, k), complex)
+    al = np.zeros(k)
+    be = np.zeros(k + 1)
+    tape = []
+    be[0] = np.linalg.norm(b)
+    U[:, 0] = b / be[0]
+    for j in range(k):
+        w0 = a.conj().T @ U[:, j]
+        if j > 0:
+            w0 = w0 - be[j] * V[:, j - 1]
+        w1 = w0 - V[:, :j] @ (V[:, :j].conj().T @ w0)
+        w2 = w1 - V[:, :j] @ (V[:, :j].conj().T @ w1)
+        al[j] = np.linalg.norm(w2)
+        V[:, j] = w2 / al[j]
+        t0 = a @ V[:, j] - al[j] * U[:, j]
+        t1 = t0 - U[:, :j + 1] @ (U[:, :j + 1].conj().T @ t0)
+        t2 = t1 - U[:, :j + 1] @ (U[:, :j + 1].conj().T @ t1)
+        be[j + 1] = np.linalg.norm(t2)
+        U[:, j + 1] = t2 / be[j + 1]
+        tape.append((w0, w1, t0, t1))
+    return dict(U=U, V=V, al=al, be=be, tape=tape)
+
+
+def _unproject_bar(fbar: np.ndarray, x_in: np.ndarray, Q: np.ndarray, Qbar: np.ndarray) -> np.ndarray:
+    """Reverse of f = x - Q (Q^H x) for a real loss: returns x-bar and adds
+    the contribution to Q-bar (in place).  Bars follow dL = Re<bar, d.>."""
+    if Q.shape[1] == 0:
+        return fbar
+    c = Q.conj().T @ x_in
+    qf = Q.conj().T @ fbar
+    Qbar -= np.outer(fbar, c.conj()) + np.outer(x_in, qf.conj())
+    return fbar - Q @ qf
+
+
+def _unnormalize_bar(ubar: np.ndarray, nbar: float, u: np.ndarray, nrm: float) -> np.ndarray:
+    """Reverse of (u, nrm) = (t / ||t||, ||t||): t-bar from u-bar and nrm-bar."""
+    return ubar / nrm + (nbar - np.real(np.vdot(u, ubar)) / nrm) * u
+
+
+def tgkt_adjoint(A, B, k, mu, G):
+    """dL/dB for L with dL/dX = G, X = tgkt_fixed(A, B, k, mu): the reverse
+    (adjoint) sweep through the k steps of Algorithm 4 per Fourier slice, the
+    reorthogonalisation and normalisations included, and through the
+    projected Tikhonov solve y = (P_k^T P_k + I/mu)^{-1} P_k^T z_1 e_1.
+    Returns (dB, X), both (n, l, 1) and (n, m, 1) real."""
+    n, l, m = A.shape
+    lam = 1.0 / mu
+    Ah, Bh, Gh = fft3(A), fft3(B)[:, :, 0], fft3(G)[:, :, 0]
+    Xh = np.zeros((n, m), complex)
+    Yh = np.zeros((n, l), complex)
+    for s in range(n):
+        a = Ah[s]
+        f = _gkb_slice_taped(a, Bh[s], k)
+        U, V, al, be = f["U"], f["V"], f["al"], f["be"]
+        P = bidiag(al, be, k)
+        M = P.T @ P + lam * np.eye(k)
+        y = np.linalg.solve(M, P.T @ (be[0] * np.eye(k + 1)[:, 0]))
+        Xh[s] = V @ y
+        # x = V y;  y = M^{-1} P^T be_0 e_1
+        xbar = Gh[s]
+        Vbar = np.outer(xbar, y)
+        ybar = np.real(V.conj().T @ xbar)
+        sv = np.linalg.solve(M, ybar)
+        Pbar = np.outer(be[0] * np.eye(k + 1)[:, 0], sv) - P @ (np.outer(sv, y) + np.outer(y, sv))
+        albar = np.array([Pbar[j, j] for j in range(k)])
+        bebar = np.zeros(k + 1)
+        bebar[0] = sv @ (P.T @ np.eye(k + 1)[:, 0])
+        for j in range(k):
+            bebar[j + 1] += Pbar[j + 1, j]
+        Ubar = np.zeros_like(U)
+        for j in range(k - 1, -1, -1):
+            w0, w1, t0, t1 = f["tape"][j]
+            t2bar = _unnormalize_bar(Ubar[:, j + 1], bebar[j + 1], U[:, j + 1], be[j + 1])
+            Uj = U[:, :j + 1]
+            Ujbar = np.zeros_like(Uj)
+            t1bar = _unproject_bar(t2bar, t1, Uj, Ujbar)
+            t0bar = _unproject_bar(t1bar, t0, Uj, Ujbar)
+            Ubar[:, :j + 1] += Ujbar
+            # t0 = a v_j - al_j u_j
+            Vbar[:, j] += a.conj().T @ t0bar
+            albar[j] -= np.real(np.vdot(U[:, j], t0bar))
+            Ubar[:, j] -= al[j] * t0bar
+            w2bar = _unnormalize_bar(Vbar[:, j], albar[j], V[:, j], al[j])
+            Vj = V[:, :j]
+            Vjbar = np.zeros_like(Vj)
+            w1bar = _unproject_bar(w2bar, w1, Vj, Vjbar)
+            w0bar = _unproject_bar(w1bar, w0, Vj, Vjbar)
+            Vbar[:, :j] += Vjbar
+            # w0 = a^H u_j - be_j v_{j-1}
+            Ubar[:, j] += a @ w0bar
+            if j > 0:
+                bebar[j] -= np.real(np.vdot(V[:, j - 1], w0bar))
+                Vbar[:, j - 1] -= be[j] * w0bar
+        Yh[s] = _unnormalize_bar(Ubar[:, 0], bebar[0], U[:, 0], be[0])
+    # dL = (1/n) sum_s Re<Gh_s, dXh_s> = (1/n) sum_s Re<Yh_s, dBh_s>, so dL/dB = Re(ifft(Yh))
+    return ifft3_real(Yh[:, :, None]), ifft3_real(Xh[:, :, None])
+
+
+# --------------------------------------------------------------------------
 # t-Lanczos (Algorithm t-Lanc) and the t-Lanczos method (Eq. (9t)); symmetric A.
 # --------------------------------------------------------------------------
 

@@ -481,6 +481,44 @@ def test_tgkt_residual_monotone_limit_and_root():
     assert np.isclose(np.sqrt(O.fro2(B - O.tprod_bcirc(A, out["X"]))), out["residual"], rtol=1e-7)
 
 
+def test_tgkt_adjoint_matches_central_differences_on_64_directions():
+    """dL/dB of the Tikhonov-tGKB solution at fixed k and mu (the reverse
+    sweep through Algorithm 4) against FP64 central differences of the
+    forward map, L = ||X - X_true||_F^2, on 64 seeded directions."""
+    A, B, _ = small_blur(N=10, n=8, general=0.02)
+    k, mu = 5, 300.0
+    g = np.random.default_rng(41)
+    Xt = g.standard_normal((8, 10, 1))
+    X = O.tgkt_fixed(A, B, k, mu)
+    dB, Xa = O.tgkt_adjoint(A, B, k, mu, 2.0 * (X - Xt))
+    assert np.allclose(Xa, X, atol=1e-13 * np.abs(X).max())
+    loss = lambda Bv: float(np.sum((O.tgkt_fixed(A, Bv, k, mu) - Xt) ** 2))
+    h = 1e-6
+    for _ in range(64):
+        D = g.standard_normal(B.shape)
+        D *= np.linalg.norm(B) / np.linalg.norm(D)
+        fd = (loss(B + h * D) - loss(B - h * D)) / (2 * h)
+        assert abs(fd - np.sum(dB * D)) <= 1e-7 * np.linalg.norm(dB) * np.linalg.norm(D)
+
+
+def test_tgkt_adjoint_on_the_full_space_is_the_dense_tikhonov_adjoint():
+    """With k = m the Krylov space is all of C^m and the solution is the dense
+    Tikhonov solution X-hat_s = (A_s^H A_s + I/mu)^{-1} A_s^H B-hat_s, linear in
+    B: its adjoint applied to G is A_s (A_s^H A_s + I/mu)^{-1} G-hat_s per
+    slice (the subspace terms of the reverse sweep must cancel)."""
+    A, B, _ = small_blur(N=6, n=4, general=0.2)
+    n, l, m = A.shape
+    mu = 20.0
+    G = rnd((n, m, 1), 42)
+    dB, _ = O.tgkt_adjoint(A, B, m, mu, G)
+    Ah, Gh = O.fft3(A), O.fft3(G)
+    Yh = np.zeros((n, l, 1), complex)
+    for s in range(n):
+        M = Ah[s]
+        Yh[s] = M @ np.linalg.solve(M.conj().T @ M + np.eye(m) / mu, Gh[s])
+    assert np.allclose(dB, spatial(Yh), atol=1e-8 * np.abs(dB).max())
+
+
 # ---------------------------------------------------------- t-Lanczos ----
 
 def test_tlanczos_decomposition_on_a_symmetric_tensor():
