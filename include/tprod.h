@@ -432,6 +432,34 @@ tp_status tgkb_tikhonov_grad_c(const void* G, const double* c, int l, int m, int
                                const void* solve_ws, size_t solve_ws_bytes, double* dc, int prec, void* ws,
                                size_t ws_bytes, void* stream);
 
+/* --------------------------------- gradient of the Tikhonov-tGKB solution in B
+ * tgkb_tikhonov_adjoint: dL/dB for a loss L of the solution X of the last
+ * tgkb_tikhonov_solve (or _hat) made with solve_ws and the same (l, m, n,
+ * params, prec), with the number of steps k and mu held at the values that
+ * solve chose (Section 5: per Fourier slice the minimiser of ||A x - b||^2 +
+ * mu^{-1} ||x||^2 over the Krylov space that k steps of Algorithm 4 build from
+ * b).  The Krylov space moves with B and its motion is part of the gradient:
+ * the call runs the reverse (adjoint) sweep through the k steps of Algorithm
+ * 4 per slice, the two Gram-Schmidt passes and the Normalize steps included,
+ * and through the projected Tikhonov solve, recomputing each step's vectors
+ * from the two bases the solve kept (four products with A-hat per step; one
+ * CTA per slice).  The paper has no counterpart; it is a service for
+ * gradient-based use.
+ *   G     : real (n, m, 1), dL/dX         dB : real (n, l, 1), written
+ *   Ahat  : null when the solve transformed A itself; otherwise the same
+ *           half spectrum (n/2+1, l, m) that was given to the _hat solve
+ *           (read only, 16-byte aligned)
+ * solve_ws is read, never modified (the call can be repeated).  Asynchronous
+ * on the stream.  TP_ERR_ARG for null pointers or a misaligned Ahat;
+ * TP_ERR_WORKSPACE when solve_ws or ws is too small or not 256-byte aligned.
+ * Workspace: tgkb_tikhonov_adjoint_workspace_bytes(l, m, n, params, prec)
+ * (0: invalid sizes).
+ */
+size_t tgkb_tikhonov_adjoint_workspace_bytes(int l, int m, int n, const tp_tik_params* params, int prec);
+tp_status tgkb_tikhonov_adjoint(const void* G, int l, int m, int n, const tp_tik_params* params,
+                                const void* solve_ws, size_t solve_ws_bytes, const void* Ahat, void* dB, int prec,
+                                void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------ misc -------- */
 const char* tp_status_string(int status);
 int tp_version(void);                 /* 100 * major + minor                        */

@@ -1754,6 +1754,325 @@ tp_status tik_grad_c(const T* G, const double* c, int l, int m, int n, const tp_
     return grad_c(c, n, gamma, add, dc, st);
 }
 
+// ---------------------------------------------------------------------------
+// dL/dB of the Tikhonov-tGKB solution at the k and mu of its solve: the
+// reverse (adjoint) sweep through the k steps of Algorithm 4 per Fourier
+// slice, with the two Gram-Schmidt passes and the Normalize steps, and
+// through the projected Tikhonov solve y = M^{-1} P^T z_0 e_1 (M = P^T P +
+// lam I, lam = 1/mu, P the (k+1) x k lower bidiagonal: c on the diagonal, z
+// below).  The forward keeps the bases U (Q: u_0 .. u_k) and V (W: v_0 ..
+// v_{k-1}); each step's intermediate vectors are recomputed from them (four
+// products with A-hat per step).  Bars follow dL = Re<bar, d.> with dL/dx =
+// G-hat_s; the sweep returns dL/db-hat_s, and dL/dB = irdft of those (the
+// Parseval argument of the t-product's adjoint).  Float64 scalars; vectors
+// and products in the working precision (the forward's); dot products summed
+// in float64 across lanes.
+// ---------------------------------------------------------------------------
+constexpr int TIKADJ_THREADS = 512;
+
+// out[i] = <Q_i, x> for i < cnt (Q_i = Q + i ld, length len): a warp per vector.
+template <typename T>
+__device__ void tadj_dots(const cplx<T>* Q, long ld, int cnt, const cplx<T>* x, int len, double2* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < cnt; i += nw) {
+        const cplx<T>* q = Q + (long)i * ld;
+        T ar = 0, ai = 0;
+        for (int e = lane; e < len; e += 32) {
+            const cplx<T> a = q[e], v = x[e];
+            ar += a.x * v.x + a.y * v.y;
+            ai += a.x * v.y - a.y * v.x;
+        }
+        const double r = warp_sum((double)ar), im = warp_sum((double)ai);
+        if (lane == 0) out[i] = make_double2(r, im);
+    }
+    __syncthreads();
+}
+
+// Re<q, x> over len entries, every thread gets it (two barriers).
+template <typename T>
+__device__ double tadj_redot(const cplx<T>* q, const cplx<T>* x, int len, double* red) {
+    T a = 0;
+    for (int e = threadIdx.x; e < len; e += blockDim.x) a += q[e].x * x[e].x + q[e].y * x[e].y;
+    return block_sum_t(a, red);
+}
+
+// Reverse of f = x - Q (Q^H x) over cnt basis vectors (c = Q^H x given):
+// qf = Q^H fbar; Qbar_i -= fbar conj(c_i) + x conj(qf_i); xbar = fbar - Q qf
+// (xbar may alias fbar).
+template <typename T>
+__device__ void tadj_unproj(const cplx<T>* Q, cplx<T>* Qbar, long ld, int cnt, int len, const double2* c,
+                            double2* qf, const cplx<T>* fbar, const cplx<T>* x, cplx<T>* xbar) {
+    tadj_dots<T>(Q, ld, cnt, fbar, len, qf);
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const cplx<T> fb = fbar[e], xv = x[e];
+        double sr = 0.0, si = 0.0;
+        for (int i = 0; i < cnt; ++i) {
+            const double2 ci = c[i], qi = qf[i];
+            cplx<T>* qb = Qbar + (long)i * ld + e;
+            // fb conj(c_i) + x conj(qf_i)
+            const double ur = (double)fb.x * ci.x + (double)fb.y * ci.y + (double)xv.x * qi.x + (double)xv.y * qi.y;
+            const double ui = (double)fb.y * ci.x - (double)fb.x * ci.y + (double)xv.y * qi.x - (double)xv.x * qi.y;
+            *qb = mk<T>((T)((double)qb->x - ur), (T)((double)qb->y - ui));
+            const cplx<T> q = Q[(long)i * ld + e];
+            sr += (double)q.x * qi.x - (double)q.y * qi.y;
+            si += (double)q.x * qi.y + (double)q.y * qi.x;
+        }
+        xbar[e] = mk<T>((T)((double)fb.x - sr), (T)((double)fb.y - si));
+    }
+    __syncthreads();
+}
+
+// y[i] = sum_e a[i][e] v[e] - alpha u[i] (rows i < l of the l x m slice; a warp per row).
+template <typename T>
+__device__ void tadj_mv_n(const cplx<T>* a, int l, int m, const cplx<T>* v, double alpha, const cplx<T>* u,
+                          cplx<T>* y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < l; i += nw) {
+        cplx<T> acc = mk<T>(0, 0);
+        for (int e = lane; e < m; e += 32) cfma(acc, a[(long)i * m + e], v[e]);
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        if (lane == 0) {
+            if (u) acc = csub(acc, cscale(u[i], (T)alpha));
+            y[i] = acc;
+        }
+    }
+    __syncthreads();
+}
+
+// y[e] = sum_i conj(a[i][e]) t[i] - beta v[e] (columns e < m; a thread per column).
+template <typename T>
+__device__ void tadj_mv_c(const cplx<T>* a, int l, int m, const cplx<T>* t, double beta, const cplx<T>* v,
+                          cplx<T>* y) {
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        cplx<T> acc = mk<T>(0, 0);
+        for (int i = 0; i < l; ++i) cfmac(acc, a[(long)i * m + e], t[i]);
+        if (v) acc = csub(acc, cscale(v[e], (T)beta));
+        y[e] = acc;
+    }
+    __syncthreads();
+}
+
+// Reverse of (u, nrm) = (t / ||t||, ||t||): tbar = ubar / nrm + (nbar - Re<u, ubar> / nrm) u.
+template <typename T>
+__device__ void tadj_unnorm(const cplx<T>* ubar, double nbar, const cplx<T>* u, double nrm, int len, cplx<T>* tbar,
+                            double* red) {
+    const double ru = tadj_redot<T>(u, ubar, len, red);
+    const double f = nbar - ru / nrm;
+    for (int e = threadIdx.x; e < len; e += blockDim.x)
+        tbar[e] = mk<T>((T)(ubar[e].x / nrm + f * u[e].x), (T)(ubar[e].y / nrm + f * u[e].y));
+    __syncthreads();
+}
+
+template <typename T>
+struct TadjArgs {
+    const cplx<T>* Ahat;
+    const cplx<T>* Ub;   // forward's Q: (h, k_max + 1, l)
+    const cplx<T>* Vb;   // forward's W: (h, k_max, m)
+    const T* cc;
+    const T* zz;
+    const State* st;
+    const TikState* ts;
+    const cplx<T>* Gh;   // (h, m)
+    cplx<T>* Ubar;       // (h, k_max + 1, l)
+    cplx<T>* Vbar;       // (h, k_max, m)
+    cplx<T>* vec;        // (h, 3 l + 3 m): t0 t1 tb | w0 w1 wb
+    double* sc;          // (h, 4 k_max + 2): y, s, albar, bebar
+    cplx<T>* Yh;         // (h, l): dL/db-hat
+    int l, m, k_max;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TIKADJ_THREADS) k_tikadj_rev(const TadjArgs<T> g) {
+    typedef cplx<T> V;
+    // first-pass coefficients (U^H t0, V^H w0), second-pass ones (U^H t1, V^H w1), and Q^H fbar
+    __shared__ double2 cdot[GKB_KMAX + 1], c2[GKB_KMAX + 1], qf[GKB_KMAX + 1];
+    __shared__ double red[33];
+    const int s = blockIdx.x, tid = threadIdx.x, l = g.l, m = g.m, k_max = g.k_max;
+    const int k = min(max(g.st->k, 0), k_max);  // a workspace that holds no solve cannot send the sweep out of bounds
+    const V* a = g.Ahat + (long)s * l * m;
+    const V* U = g.Ub + (long)s * (k_max + 1) * l;
+    const V* Vv = g.Vb + (long)s * k_max * m;
+    const T* c = g.cc + (long)s * k_max;
+    const T* z = g.zz + (long)s * (k_max + 1);
+    const V* G = g.Gh + (long)s * m;
+    V* Ub = g.Ubar + (long)s * (k_max + 1) * l;
+    V* Vb = g.Vbar + (long)s * k_max * m;
+    V* t0 = g.vec + (long)s * (3 * l + 3 * m);
+    V *t1 = t0 + l, *tb = t1 + l, *w0 = tb + l, *w1 = w0 + m, *wb = w1 + m;
+    double* y = g.sc + (long)s * (4 * k_max + 2);
+    double *sv = y + k_max, *albar = sv + k_max, *bebar = albar + k_max;
+    const double lam = pow(10.0, -g.ts->t);
+
+    // x = V y, y = M^{-1} P^T z_0 e_1:  ybar = Re(V^H G),  s = M^{-1} ybar,
+    // Pbar = z_0 e_1 s^T - P (s y^T + y s^T),  Vbar = G y^T
+    tadj_dots<T>(Vv, m, k, G, m, cdot);
+    if (tid == 0) {
+        double* dd = albar;  // scratch for the LDL^T pivots and multipliers (overwritten below)
+        double* ll = bebar;
+        for (int j = 0; j < k; ++j) {
+            const double cj = (double)c[j], zj1 = (double)z[j + 1];
+            const double mjj = cj * cj + zj1 * zj1 + lam;
+            if (j == 0) {
+                dd[0] = mjj;
+            } else {
+                const double off = (double)z[j] * cj;
+                ll[j] = off / dd[j - 1];
+                dd[j] = mjj - ll[j] * off;
+            }
+        }
+        double py = 0.0, ps = 0.0;
+        for (int j = 0; j < k; ++j) {
+            const double fy = (j == 0 ? (double)z[0] * (double)c[0] : 0.0) - (j > 0 ? ll[j] * py : 0.0);
+            const double fs = cdot[j].x - (j > 0 ? ll[j] * ps : 0.0);
+            py = fy;
+            ps = fs;
+            y[j] = fy / dd[j];
+            sv[j] = fs / dd[j];
+        }
+        for (int j = k - 2; j >= 0; --j) {
+            y[j] -= ll[j + 1] * y[j + 1];
+            sv[j] -= ll[j + 1] * sv[j + 1];
+        }
+        // the bars of the bidiagonal entries c_j = P[j][j] and z_{j+1} = P[j+1][j], and of z_0
+        for (int j = 0; j < k; ++j) {
+            double ab = -2.0 * (double)c[j] * sv[j] * y[j];
+            if (j > 0) ab -= (double)z[j] * (sv[j - 1] * y[j] + y[j - 1] * sv[j]);
+            if (j == 0) ab += (double)z[0] * sv[0];
+            albar[j] = ab;
+        }
+        bebar[0] = sv[0] * (double)c[0];
+        for (int j = 0; j < k; ++j) {
+            double bb = -2.0 * (double)z[j + 1] * sv[j] * y[j];
+            if (j + 1 < k) bb -= (double)c[j + 1] * (sv[j + 1] * y[j] + y[j + 1] * sv[j]);
+            bebar[j + 1] = bb;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < k * m; e += blockDim.x) {
+        const int j = e / m, i = e - j * m;
+        Vb[e] = cscale(G[i], (T)y[j]);
+    }
+    for (int e = tid; e < (k + 1) * l; e += blockDim.x) Ub[e] = mk<T>(0, 0);
+    __syncthreads();
+
+    for (int j = k - 1; j >= 0; --j) {
+        const V* uj = U + (long)j * l;
+        const V* vj = Vv + (long)j * m;
+        const double aj = (double)c[j], bj1 = (double)z[j + 1];
+        // forward of the step, recomputed: t0 = a v_j - c_j u_j, t1 = t0 - U (U^H t0) over u_0 .. u_j
+        tadj_mv_n<T>(a, l, m, vj, aj, uj, t0);
+        tadj_dots<T>(U, l, j + 1, t0, l, cdot);
+        for (int e = tid; e < l; e += blockDim.x) {
+            double sr = 0.0, si = 0.0;
+            for (int i = 0; i <= j; ++i) {
+                const V q = U[(long)i * l + e];
+                sr += (double)q.x * cdot[i].x - (double)q.y * cdot[i].y;
+                si += (double)q.x * cdot[i].y + (double)q.y * cdot[i].x;
+            }
+            t1[e] = mk<T>((T)((double)t0[e].x - sr), (T)((double)t0[e].y - si));
+        }
+        __syncthreads();
+        // u_{j+1} = t2 / z_{j+1};  t2 = t1 - U (U^H t1);  t1 = t0 - U (U^H t0)
+        tadj_unnorm<T>(Ub + (long)(j + 1) * l, bebar[j + 1], U + (long)(j + 1) * l, bj1, l, tb, red);
+        tadj_dots<T>(U, l, j + 1, t1, l, c2);
+        tadj_unproj<T>(U, Ub, l, j + 1, l, c2, qf, tb, t1, tb);
+        tadj_unproj<T>(U, Ub, l, j + 1, l, cdot, qf, tb, t0, tb);
+        // t0 = a v_j - c_j u_j
+        tadj_mv_c<T>(a, l, m, tb, 0.0, nullptr, w0);  // a^H t0bar into w0 (scratch)
+        const double ru = tadj_redot<T>(uj, tb, l, red);
+        for (int e = tid; e < m; e += blockDim.x) Vb[(long)j * m + e] = cadd(Vb[(long)j * m + e], w0[e]);
+        for (int e = tid; e < l; e += blockDim.x) Ub[(long)j * l + e] = csub(Ub[(long)j * l + e], cscale(tb[e], (T)aj));
+        if (tid == 0) albar[j] -= ru;
+        __syncthreads();
+        // forward, recomputed: w0 = a^H u_j - z_j v_{j-1}, w1 = w0 - V (V^H w0) over v_0 .. v_{j-1}
+        tadj_mv_c<T>(a, l, m, uj, j > 0 ? (double)z[j] : 0.0, j > 0 ? Vv + (long)(j - 1) * m : nullptr, w0);
+        tadj_dots<T>(Vv, m, j, w0, m, cdot);
+        for (int e = tid; e < m; e += blockDim.x) {
+            double sr = 0.0, si = 0.0;
+            for (int i = 0; i < j; ++i) {
+                const V q = Vv[(long)i * m + e];
+                sr += (double)q.x * cdot[i].x - (double)q.y * cdot[i].y;
+                si += (double)q.x * cdot[i].y + (double)q.y * cdot[i].x;
+            }
+            w1[e] = mk<T>((T)((double)w0[e].x - sr), (T)((double)w0[e].y - si));
+        }
+        __syncthreads();
+        // v_j = w2 / c_j;  w2 = w1 - V (V^H w1);  w1 = w0 - V (V^H w0)
+        tadj_unnorm<T>(Vb + (long)j * m, albar[j], vj, aj, m, wb, red);
+        tadj_dots<T>(Vv, m, j, w1, m, c2);
+        tadj_unproj<T>(Vv, Vb, m, j, m, c2, qf, wb, w1, wb);
+        tadj_unproj<T>(Vv, Vb, m, j, m, cdot, qf, wb, w0, wb);
+        // w0 = a^H u_j - z_j v_{j-1}
+        tadj_mv_n<T>(a, l, m, wb, 0.0, nullptr, t1);  // a w0bar into t1 (scratch)
+        double rv = 0.0;
+        if (j > 0) rv = tadj_redot<T>(Vv + (long)(j - 1) * m, wb, m, red);
+        for (int e = tid; e < l; e += blockDim.x) Ub[(long)j * l + e] = cadd(Ub[(long)j * l + e], t1[e]);
+        if (j > 0)
+            for (int e = tid; e < m; e += blockDim.x)
+                Vb[(long)(j - 1) * m + e] = csub(Vb[(long)(j - 1) * m + e], cscale(wb[e], (T)z[j]));
+        if (tid == 0 && j > 0) bebar[j] -= rv;
+        __syncthreads();
+    }
+    // u_0 = b / z_0
+    tadj_unnorm<T>(Ub, bebar[0], U, (double)z[0], l, g.Yh + (long)s * l, red);
+}
+
+template <typename T>
+static size_t tik_adj_carve(void* base, int l, int m, int n, int k_max, TadjArgs<T>* a) {
+    const size_t h = n / 2 + 1;
+    Carver cv(base, 0);
+    a->Gh = cv.take<cplx<T>>(h * m);
+    a->Ubar = cv.take<cplx<T>>(h * (k_max + 1) * (size_t)l);
+    a->Vbar = cv.take<cplx<T>>(h * (size_t)k_max * m);
+    a->vec = cv.take<cplx<T>>(h * (3 * (size_t)l + 3 * (size_t)m));
+    a->Yh = cv.take<cplx<T>>(h * (size_t)l);
+    a->sc = cv.take<double>(h * (4 * (size_t)k_max + 2));
+    return cv.off;
+}
+
+template <typename T>
+size_t tik_adj_ws_bytes(int l, int m, int n, const tp_tik_params* P) {
+    if (!P || gk_check<T>(l, m, n, 1, &P->gkb) != TP_OK) return 0;
+    TadjArgs<T> a;
+    return tik_adj_carve<T>(nullptr, l, m, n, P->gkb.k_max, &a);
+}
+
+template <typename T>
+tp_status tik_adjoint(const T* G, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,
+                      size_t solve_ws_bytes, const void* Ahat, T* dB, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!P || !G || !dB || ((size_t)Ahat & 15)) return TP_ERR_ARG;
+    TRY(gk_check<T>(l, m, n, 1, &P->gkb));
+    const int k_max = P->gkb.k_max, h = n / 2 + 1;
+    GkWs<T> w = gk_carve<T>((void*)solve_ws, l, m, n, k_max, 1);
+    if (!solve_ws || ((size_t)solve_ws & 255) || solve_ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
+    TadjArgs<T> a;
+    const size_t need = tik_adj_carve<T>(ws, l, m, n, k_max, &a);
+    if (!ws || ((size_t)ws & 255) || ws_bytes < need) return TP_ERR_WORKSPACE;
+    a.Ahat = Ahat ? (const cplx<T>*)Ahat : w.Ahat;  // the half spectrum the solve used
+    a.Ub = w.Q;
+    a.Vb = w.W;
+    a.cc = w.cc;
+    a.zz = w.zz;
+    a.st = w.st;
+    a.ts = w.ts;
+    a.l = l;
+    a.m = m;
+    a.k_max = k_max;
+    TRY(rdft<T>(G, (void*)a.Gh, n, m, 1, 1, m, nullptr, nullptr, st));
+    prof_begin(TP_KC_MISC, st);
+    k_tikadj_rev<T><<<h, TIKADJ_THREADS, 0, st>>>(a);
+    TRY(launched(TP_KC_MISC, st));
+    return irdft<T>(a.Yh, dB, n, l, 1, 1, l, nullptr, st);
+}
+
+template size_t tik_adj_ws_bytes<float>(int, int, int, const tp_tik_params*);
+template size_t tik_adj_ws_bytes<double>(int, int, int, const tp_tik_params*);
+template tp_status tik_adjoint<float>(const float*, int, int, int, const tp_tik_params*, const void*, size_t,
+                                      const void*, float*, void*, size_t, cudaStream_t);
+template tp_status tik_adjoint<double>(const double*, int, int, int, const tp_tik_params*, const void*, size_t,
+                                       const void*, double*, void*, size_t, cudaStream_t);
+
 template size_t tik_grad_ws_bytes<float>(int, int, int, const tp_tik_params*);
 template size_t tik_grad_ws_bytes<double>(int, int, int, const tp_tik_params*);
 template tp_status tik_grad_c<float>(const float*, const double*, int, int, int, const tp_tik_params*, const void*,

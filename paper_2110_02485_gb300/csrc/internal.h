@@ -169,6 +169,13 @@ tp_status sep_grad(const T* X, const T* G, const double* c, int m, int n, int p,
                    size_t ws_bytes, cudaStream_t st);
 template <typename T>
 tp_status sep_operator(const T* Tm, const double* c, int l, int m, int n, T* A, cudaStream_t st);
+// dL/dB of the Tikhonov-tGKB solution left in solve_ws (k and mu held): the
+// reverse sweep through Algorithm 4, one CTA per slice.  Ahat: null, or the
+// caller's half spectrum when the solve was given one.
+template <typename T> size_t tik_adj_ws_bytes(int l, int m, int n, const tp_tik_params* P);
+template <typename T>
+tp_status tik_adjoint(const T* G, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,
+                      size_t solve_ws_bytes, const void* Ahat, T* dB, void* ws, size_t ws_bytes, cudaStream_t st);
 template <typename T> size_t tik_grad_ws_bytes(int l, int m, int n, const tp_tik_params* P);
 template <typename T>
 tp_status tik_grad_c(const T* G, const double* c, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,

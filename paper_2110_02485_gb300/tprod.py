@@ -55,7 +55,8 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "nested_tgkb_solve", "ttsvd_workspace_bytes", "ttsvd_solve", "tgkb_triplets_workspace_bytes",
            "tgkb_triplets", "sep_grad_c_workspace_bytes", "sep_grad_c", "tgkb_tikhonov_grad_c_workspace_bytes",
            "tgkb_tikhonov_grad_c", "sep_operator", "ttsvd_adjoint",
-           "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat")
+           "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat",
+           "tgkb_tikhonov_adjoint_workspace_bytes", "tgkb_tikhonov_adjoint")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -126,9 +127,12 @@ def load(path: str | None = None):
     L.tgkb_tikhonov_grad_c_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(TikParams), i]
     L.tgkb_tikhonov_grad_c_workspace_bytes.restype = sz
     L.tgkb_tikhonov_grad_c.argtypes = [vp, vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, i, vp, sz, vp]
+    L.tgkb_tikhonov_adjoint_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(TikParams), i]
+    L.tgkb_tikhonov_adjoint_workspace_bytes.restype = sz
+    L.tgkb_tikhonov_adjoint.argtypes = [vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, vp, i, vp, sz, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
               "tgkb_tikhonov_solve", "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator",
-              "ttsvd_adjoint"):
+              "ttsvd_adjoint", "tgkb_tikhonov_adjoint"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -607,13 +611,16 @@ def tgkb_triplets(A, B, k):
 
 
 class TgktFactor:
-    """What tgkt_solve(..., keep=True) leaves for tgkt_grad_c: the solve's
-    workspace (basis, bidiagonal, k, mu, X-hat) and its arguments."""
+    """What tgkt_solve(..., keep=True) leaves for tgkt_grad_c and
+    tgkt_adjoint: the solve's workspace (A-hat, B-hat, basis, bidiagonal, k,
+    mu, X-hat), its arguments, and the caller's A-hat when the solve was
+    given one (None otherwise)."""
 
-    def __init__(self, ws, P, l, m, n, prec, device, dtype):
+    def __init__(self, ws, P, l, m, n, prec, device, dtype, ahat=None):
         self.ws, self.P = ws, P
         self.l, self.m, self.n = l, m, n
         self.prec, self.device, self.dtype = prec, device, dtype
+        self.ahat = ahat
 
 
 def sep_operator(T: torch.Tensor, c: torch.Tensor) -> torch.Tensor:
@@ -659,9 +666,9 @@ def rtsvd_solve_sep_ad(c, T, B, Omega, delta, tau, p_over, **kw):
 
 
 class SepTgktSolve(torch.autograd.Function):
-    """Tikhonov-tGKB solution for A(:,:,k) = c_k T, differentiable in c
-    (tgkt_grad_c) with k and mu held at the values the solve chose.  dL/dB is
-    not provided: the Krylov space depends on B."""
+    """Tikhonov-tGKB solution for A(:,:,k) = c_k T, differentiable in B
+    (tgkt_adjoint: the Krylov space moves with B) and in c (tgkt_grad_c),
+    with k and mu held at the values the solve chose."""
 
     @staticmethod
     def forward(ctx, B, c, T, kw):
@@ -673,14 +680,17 @@ class SepTgktSolve(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, G):
-        if ctx.needs_input_grad[0] or ctx.needs_input_grad[2]:
-            raise NotImplementedError("only dL/dc is provided for the Tikhonov-tGKB solution")
+        if ctx.needs_input_grad[2]:
+            raise NotImplementedError("dL/dT is not provided")
         (c,) = ctx.saved_tensors
-        return None, tgkt_grad_c(ctx.fac, G.contiguous(), c.detach().contiguous()), None, None
+        G = G.contiguous()
+        dB = tgkt_adjoint(ctx.fac, G) if ctx.needs_input_grad[0] else None
+        dc = tgkt_grad_c(ctx.fac, G, c.detach().contiguous()) if ctx.needs_input_grad[1] else None
+        return dB, dc, None, None
 
 
 def tgkt_solve_sep_ad(c, T, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12):
-    """Differentiable (in c) Tikhonov-tGKB solve for A(:,:,k) = c_k T: returns X."""
+    """Differentiable (in B and c) Tikhonov-tGKB solve for A(:,:,k) = c_k T: returns X."""
     return SepTgktSolve.apply(B, c, T, dict(delta=delta, tau=tau, k_max=k_max, mu_lo=mu_lo, mu_hi=mu_hi,
                                             log_tol=log_tol))
 
@@ -729,6 +739,27 @@ def tgkt_grad_c(fac: "TgktFactor", G: torch.Tensor, c: torch.Tensor) -> torch.Te
     return dc
 
 
+def tgkt_adjoint(fac: "TgktFactor", G: torch.Tensor) -> torch.Tensor:
+    """dL/dB of the Tikhonov-tGKB solution that made `fac` (k and mu held at
+    the solve's values; the Krylov space moves with B) for G = dL/dX (n, m,
+    1): the reverse sweep through the solve's tGKB steps.  Returns dB (n, l, 1)."""
+    _dev(G)
+    if tuple(G.shape) != (fac.n, fac.m, 1) or G.dtype != fac.dtype:
+        raise ValueError("G must match the solution X of the solve")
+    G = G.contiguous()
+    L = load()
+    nb = L.tgkb_tikhonov_adjoint_workspace_bytes(fac.l, fac.m, fac.n, ctypes.byref(fac.P), fac.prec)
+    if nb == 0:
+        raise TprodError("tgkb_tikhonov_adjoint_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, G.device)
+    wp, wn = _aligned(ws)
+    sp, sn = _aligned(fac.ws)
+    dB = torch.empty((fac.n, fac.l, 1), dtype=fac.dtype, device=G.device)
+    _check("tgkb_tikhonov_adjoint", L.tgkb_tikhonov_adjoint(_ptr(G), fac.l, fac.m, fac.n, ctypes.byref(fac.P), sp, sn,
+                                                            _ptr(fac.ahat), _ptr(dB), fac.prec, wp, wn, _stream()))
+    return dB
+
+
 def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True, keep=False, Ahat=None, n=None):
     """Tikhonov-tGKB (Section 5).  Returns (X, info[, factor]); keep=True also
     returns the solve's workspace for tgkt_grad_c.  With A=None, Ahat and n:
@@ -750,7 +781,7 @@ def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True, 
     _check("tgkb_tikhonov_solve", op.entry(L, "tgkb_tikhonov_solve")(
         _ptr(op.t), _ptr(B), l, m, n, 1, ctypes.byref(P), _ptr(X), _ptr(info), prec, wp, wn, _stream()))
     if keep:
-        fac = TgktFactor(ws, P, l, m, n, prec, op.device, op.dtype)
+        fac = TgktFactor(ws, P, l, m, n, prec, op.device, op.dtype, op.t if op.hat else None)
         return (X, info, fac) if not sync else (X, _info_dict(info), fac)
     if not sync:
         return X, info

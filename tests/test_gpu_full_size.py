@@ -9,7 +9,9 @@ the same truncation indices (the stored margins are far from the tie band),
 match the oracle's whole solution within 1e-5 relative Frobenius error in
 float32, and report residuals that an independent float64 evaluation of
 ||B - A*X|| reproduces.  The TF32 precision form of the RT-tSVD is held to the
-bound for the reduced-precision sketch (3e-3 relative).
+bound for the reduced-precision sketch (3e-3 relative).  The gradient of the
+Tikhonov-tGKB solution in B is checked at 256^3 against the oracle's reverse
+sweep and by central differences.
 """
 import json
 import os
@@ -148,3 +150,53 @@ def test_tgkt_full_size(tp, work):
     assert rel(X, ref) <= TOL_FP32
     res = true_residual(P, X)
     assert abs(res - ref["tau_delta"]) <= 1e-3 * ref["tau_delta"]   # mu puts the residual on tau*delta
+
+
+@pytest.mark.parametrize("name", ["n256_hi", "n256"])
+def test_tgkt_adjoint_full_size(tp, name):
+    """Differentiation form at 256^3 (noise 1e-2, and the bench's 1e-3): dL/dB
+    of L = ||X - X_true||_F^2 for the Tikhonov-tGKB solution with k and mu held
+    at the solve's values.  The float32 gradient against the oracle's reverse
+    sweep through Algorithm 4 at the same k and mu (every entry); the float64
+    GPU gradient against central differences (h = 1e-6 relative) of the
+    float64 GPU solve with k and mu pinned (k_max = k; a mu interval ending
+    0.1% below the discrepancy root, so that the search returns mu = mu_hi
+    exactly under every perturbation), on 64 seeded directions."""
+    cfg = synth.CONFIGS[name]
+    P = synth.blur_problem(cfg, seed=cfg.seed)
+    A32, B32, Xt = dev(P["A"]), dev(P["B"]), P["X_true"].astype(np.float64)
+    X, info, fac = tp.tgkt_solve(A32, B32, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, keep=True)
+    k, mu = info["k"], info["mu"]
+    G = 2.0 * (X.cpu().double().numpy() - Xt)
+    dB = tp.tgkt_adjoint(fac, dev(G.astype(np.float32))).cpu().double().numpy()
+    want, Xo = O.tgkt_adjoint(P["A"].astype(np.float64), P["B"].astype(np.float64), k, mu,
+                              G.astype(np.float32).astype(np.float64))
+    assert float(np.linalg.norm(X.cpu().numpy() - Xo) / np.linalg.norm(Xo)) <= TOL_FP32
+    assert float(np.linalg.norm(dB - want) / np.linalg.norm(want)) <= 1e-5
+    # float64 end to end on the device (mu pinned just below the free solve's root), against the oracle at the
+    # same k and mu and against central differences of the device's own float64 solve
+    A64, B64 = A32.double(), B32.double()
+    _, i64 = tp.tgkt_solve(A64, B64, P["delta"], cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi)
+    k64, mu_pin = i64["k"], i64["mu"] * 0.999
+    X64, ip, f64 = tp.tgkt_solve(A64, B64, P["delta"], cfg.tau, k64, mu_pin / 2, mu_pin, keep=True)
+    assert ip["k"] == k64 and abs(ip["mu"] / mu_pin - 1) <= 1e-12
+    G64 = 2.0 * (X64.cpu().numpy() - Xt)
+    dB64 = tp.tgkt_adjoint(f64, dev(G64)).cpu().numpy()
+    want64, _ = O.tgkt_adjoint(P["A"].astype(np.float64), P["B"].astype(np.float64), k64, ip["mu"], G64)
+    assert float(np.linalg.norm(dB64 - want64) / np.linalg.norm(want64)) <= 1e-9
+
+    def loss(Bv):
+        Xv, iv = tp.tgkt_solve(A64, Bv, P["delta"], cfg.tau, k64, mu_pin / 2, mu_pin)
+        assert iv["k"] == k64 and iv["mu"] == ip["mu"]
+        return float(((Xv.cpu().double() - torch.from_numpy(Xt)) ** 2).sum())
+
+    g = np.random.default_rng(91)
+    h = 1e-6
+    nb = float(B64.norm())
+    scale = float(np.linalg.norm(dB64)) * nb / np.sqrt(dB64.size)  # typical size of a directional derivative
+    for _ in range(64):
+        D = torch.from_numpy(g.standard_normal(P["B"].shape)).cuda()
+        D *= nb / float(D.norm())
+        fd = (loss(B64 + h * D) - loss(B64 - h * D)) / (2 * h)
+        an = float((torch.from_numpy(dB64).cuda() * D).sum())
+        assert abs(fd - an) <= 1e-5 * scale

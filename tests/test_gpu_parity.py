@@ -780,20 +780,75 @@ def test_sep_rtsvd_autograd_gradcheck(tp):
 
 
 def test_sep_tgkt_autograd_gradcheck(tp):
-    """gradcheck of the Tikhonov-tGKB solve in c at a fixed mu (the search
-    interval ends below the discrepancy root, so mu = mu_hi); asking for dL/dB
-    raises."""
+    """gradcheck of the Tikhonov-tGKB solve in B and c together at a fixed mu
+    (the search interval ends below the discrepancy root, so mu = mu_hi under
+    every perturbation; k = the discrepancy index stays fixed too)."""
     T, c, A, B, delta = separable_problem(10, 6, 101)
     Td = dev(T, torch.float64)
     Bd = dev(B, torch.float64)
     _, free = tp.tgkt_solve(dev(A, torch.float64), Bd, delta, 1.1, 10, 1e-3, 1e9)
     mu0 = free["mu"] / 20.0
     cd = dev(c, torch.float64).requires_grad_()
-    f = lambda cx: tp.tgkt_solve_sep_ad(cx, Td, Bd, delta, 1.1, 10, mu0 / 4.0, mu0)
-    assert torch.autograd.gradcheck(f, (cd,), eps=1e-6, atol=1e-7, rtol=1e-5)
-    X = tp.tgkt_solve_sep_ad(cd.detach(), Td, Bd.clone().requires_grad_(), delta, 1.1, 10, mu0 / 4.0, mu0)
-    with pytest.raises((NotImplementedError, RuntimeError), match="only dL/dc"):
-        X.sum().backward()
+    Bg = Bd.clone().requires_grad_()
+    f = lambda Bx, cx: tp.tgkt_solve_sep_ad(cx, Td, Bx, delta, 1.1, 10, mu0 / 4.0, mu0)
+    assert torch.autograd.gradcheck(f, (Bg, cd), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,l", [(12, 8, None), (16, 9, None), (20, 16, 28), (32, 32, None)])
+def test_tgkt_adjoint_matches_oracle(tp, dtype, N, n, l):
+    """dL/dB of the Tikhonov-tGKB solution (Section 5) at the k and mu of the
+    GPU solve against the oracle's reverse sweep through Algorithm 4 at the
+    same k and mu; repeatable (the solve's workspace is only read)."""
+    A, B, delta = problem(N, n, seed=70 + N, l=l)
+    Ad, Bd = dev(A, dtype), dev(B, dtype)
+    A64, B64 = (x.cpu().double().numpy() for x in (Ad, Bd))
+    X, info, fac = tp.tgkt_solve(Ad, Bd, delta, 1.1, min(12, N), 1e-3, 1e9, keep=True)
+    k, mu = info["k"], info["mu"]
+    ref = O.tgkt_solve(A64, B64, delta, 1.1, min(12, N), 1e-3, 1e9)
+    if exact_k_required(ref["gkb"], dtype):
+        assert k == ref["k"]
+    G = rnd((n, N, 1), 71)
+    dB = tp.tgkt_adjoint(fac, dev(G, dtype)).cpu().numpy()
+    want, Xo = O.tgkt_adjoint(A64, B64, k, mu, dev(G, dtype).cpu().double().numpy())
+    assert dB.shape == (n, A.shape[1], 1)
+    assert rel(X.cpu().numpy(), Xo) <= (1e-10 if dtype == torch.float64 else 1e-5)
+    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 1e-5)
+    assert np.array_equal(dB, tp.tgkt_adjoint(fac, dev(G, dtype)).cpu().numpy())
+
+
+def test_tgkt_adjoint_central_differences_64_directions(tp):
+    """The GPU dL/dB (float64) of L = ||X - X_true||_F^2 against FP64 central
+    differences (h = 1e-6 relative) of the oracle's Tikhonov-tGKB map at the
+    solve's fixed k and mu, on 64 seeded directions."""
+    A, B, delta = problem(12, 8, seed=77)
+    g = np.random.default_rng(78)
+    Xt = g.standard_normal((8, 12, 1))
+    X, info, fac = tp.tgkt_solve(dev(A, torch.float64), dev(B, torch.float64), delta, 1.1, 12, 1e-3, 1e9,
+                                 keep=True)
+    k, mu = info["k"], info["mu"]
+    dB = tp.tgkt_adjoint(fac, dev(2.0 * (X.cpu().numpy() - Xt), torch.float64)).cpu().numpy()
+    loss = lambda Bv: float(np.sum((O.tgkt_fixed(A, Bv, k, mu) - Xt) ** 2))
+    h = 1e-6
+    for _ in range(64):
+        D = g.standard_normal(B.shape)
+        D *= np.linalg.norm(B) / np.linalg.norm(D)
+        fd = (loss(B + h * D) - loss(B - h * D)) / (2 * h)
+        assert abs(fd - np.sum(dB * D)) <= 1e-7 * np.linalg.norm(dB) * np.linalg.norm(D)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_tgkt_adjoint_after_the_hat_solve(tp, dtype):
+    """The adjoint of a solve given A-hat (tgkb_tikhonov_solve_hat) reads that
+    half spectrum and equals the adjoint of the plain solve."""
+    A, B, delta = problem(16, 9, seed=79)
+    Ad, Bd = dev(A, dtype), dev(B, dtype)
+    G = dev(rnd((9, 16, 1), 80), dtype)
+    _, i1, f1 = tp.tgkt_solve(Ad, Bd, delta, 1.1, 12, 1e-3, 1e9, keep=True)
+    _, i2, f2 = tp.tgkt_solve(None, Bd, delta, 1.1, 12, 1e-3, 1e9, keep=True, Ahat=tp.fft(Ad), n=9)
+    assert i1["k"] == i2["k"]
+    d1, d2 = tp.tgkt_adjoint(f1, G).cpu().numpy(), tp.tgkt_adjoint(f2, G).cpu().numpy()
+    assert rel(d2, d1) <= (1e-12 if dtype == torch.float64 else 1e-5)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
