@@ -460,6 +460,19 @@ tp_status tgkb_tikhonov_adjoint(const void* G, int l, int m, int n, const tp_tik
                                 const void* solve_ws, size_t solve_ws_bytes, const void* Ahat, void* dB, int prec,
                                 void* ws, size_t ws_bytes, void* stream);
 
+/* tgkb_adjoint: the same for the solution of the last tgkb_solve (or _hat)
+ * with one lateral slice (p = 1) made with solve_ws and the same (l, m, n,
+ * params, prec), at the k it chose (Algorithm 4 and Eq. (solgkb): the least-
+ * squares solution over the Krylov space, the Tikhonov case with mu^{-1} = 0).
+ * Arguments, ownership and errors as tgkb_tikhonov_adjoint; a workspace of a
+ * tGKB_p solve (p > 1) is laid out differently and must not be passed.
+ * Workspace: tgkb_adjoint_workspace_bytes(l, m, n, params, prec).
+ */
+size_t tgkb_adjoint_workspace_bytes(int l, int m, int n, const tp_tgkb_params* params, int prec);
+tp_status tgkb_adjoint(const void* G, int l, int m, int n, const tp_tgkb_params* params, const void* solve_ws,
+                       size_t solve_ws_bytes, const void* Ahat, void* dB, int prec, void* ws, size_t ws_bytes,
+                       void* stream);
+
 /* ------------------------------------------------------------ misc -------- */
 const char* tp_status_string(int status);
 int tp_version(void);                 /* 100 * major + minor                        */

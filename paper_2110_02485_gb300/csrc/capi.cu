@@ -435,6 +435,25 @@ tp_status tgkb_tikhonov_grad_c(const void* G, const double* c, int l, int m, int
     return TP_ERR_ARG;
 }
 
+size_t tgkb_adjoint_workspace_bytes(int l, int m, int n, const tp_tgkb_params* params, int prec) {
+    if (prec == TP_FP32) return gk_adj_ws_bytes<float>(l, m, n, params);
+    if (prec == TP_FP64) return gk_adj_ws_bytes<double>(l, m, n, params);
+    return 0;
+}
+
+tp_status tgkb_adjoint(const void* G, int l, int m, int n, const tp_tgkb_params* params, const void* solve_ws,
+                       size_t solve_ws_bytes, const void* Ahat, void* dB, int prec, void* ws, size_t ws_bytes,
+                       void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == TP_FP32)
+        return gk_adjoint<float>((const float*)G, l, m, n, params, solve_ws, solve_ws_bytes, Ahat, (float*)dB, ws,
+                                 ws_bytes, st);
+    if (prec == TP_FP64)
+        return gk_adjoint<double>((const double*)G, l, m, n, params, solve_ws, solve_ws_bytes, Ahat, (double*)dB,
+                                  ws, ws_bytes, st);
+    return TP_ERR_ARG;
+}
+
 size_t tgkb_tikhonov_adjoint_workspace_bytes(int l, int m, int n, const tp_tik_params* params, int prec) {
     if (prec == TP_FP32) return tik_adj_ws_bytes<float>(l, m, n, params);
     if (prec == TP_FP64) return tik_adj_ws_bytes<double>(l, m, n, params);

@@ -1880,6 +1880,7 @@ struct TadjArgs {
     double* sc;          // (h, 4 k_max + 2): y, s, albar, bebar
     cplx<T>* Yh;         // (h, l): dL/db-hat
     int l, m, k_max;
+    int tik;             // 1: the Tikhonov solution (lam = 1/mu of the solve); 0: the tGKB solution (lam = 0)
 };
 
 template <typename T>
@@ -1902,7 +1903,7 @@ __global__ void __launch_bounds__(TIKADJ_THREADS) k_tikadj_rev(const TadjArgs<T>
     V *t1 = t0 + l, *tb = t1 + l, *w0 = tb + l, *w1 = w0 + m, *wb = w1 + m;
     double* y = g.sc + (long)s * (4 * k_max + 2);
     double *sv = y + k_max, *albar = sv + k_max, *bebar = albar + k_max;
-    const double lam = pow(10.0, -g.ts->t);
+    const double lam = g.tik ? pow(10.0, -g.ts->t) : 0.0;
 
     // x = V y, y = M^{-1} P^T z_0 e_1:  ybar = Re(V^H G),  s = M^{-1} ybar,
     // Pbar = z_0 e_1 s^T - P (s y^T + y s^T),  Vbar = G y^T
@@ -2032,18 +2033,20 @@ static size_t tik_adj_carve(void* base, int l, int m, int n, int k_max, TadjArgs
 }
 
 template <typename T>
-size_t tik_adj_ws_bytes(int l, int m, int n, const tp_tik_params* P) {
-    if (!P || gk_check<T>(l, m, n, 1, &P->gkb) != TP_OK) return 0;
+static size_t tadj_ws(int l, int m, int n, const tp_tgkb_params* P) {
+    if (!P || gk_check<T>(l, m, n, 1, P) != TP_OK) return 0;
     TadjArgs<T> a;
-    return tik_adj_carve<T>(nullptr, l, m, n, P->gkb.k_max, &a);
+    return tik_adj_carve<T>(nullptr, l, m, n, P->k_max, &a);
 }
 
+// The reverse sweep for the solution left in solve_ws by a single-slice tGKB
+// (tik = 0) or Tikhonov-tGKB (tik = 1) solve with the same sizes and k_max.
 template <typename T>
-tp_status tik_adjoint(const T* G, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,
-                      size_t solve_ws_bytes, const void* Ahat, T* dB, void* ws, size_t ws_bytes, cudaStream_t st) {
+static tp_status tadj_run(const T* G, int l, int m, int n, const tp_tgkb_params* P, int tik, const void* solve_ws,
+                          size_t solve_ws_bytes, const void* Ahat, T* dB, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (!P || !G || !dB || ((size_t)Ahat & 15)) return TP_ERR_ARG;
-    TRY(gk_check<T>(l, m, n, 1, &P->gkb));
-    const int k_max = P->gkb.k_max, h = n / 2 + 1;
+    TRY(gk_check<T>(l, m, n, 1, P));
+    const int k_max = P->k_max, h = n / 2 + 1;
     GkWs<T> w = gk_carve<T>((void*)solve_ws, l, m, n, k_max, 1);
     if (!solve_ws || ((size_t)solve_ws & 255) || solve_ws_bytes < w.bytes) return TP_ERR_WORKSPACE;
     TadjArgs<T> a;
@@ -2059,6 +2062,7 @@ tp_status tik_adjoint(const T* G, int l, int m, int n, const tp_tik_params* P, c
     a.l = l;
     a.m = m;
     a.k_max = k_max;
+    a.tik = tik;
     TRY(rdft<T>(G, (void*)a.Gh, n, m, 1, 1, m, nullptr, nullptr, st));
     prof_begin(TP_KC_MISC, st);
     k_tikadj_rev<T><<<h, TIKADJ_THREADS, 0, st>>>(a);
@@ -2066,6 +2070,35 @@ tp_status tik_adjoint(const T* G, int l, int m, int n, const tp_tik_params* P, c
     return irdft<T>(a.Yh, dB, n, l, 1, 1, l, nullptr, st);
 }
 
+template <typename T>
+size_t tik_adj_ws_bytes(int l, int m, int n, const tp_tik_params* P) {
+    return P ? tadj_ws<T>(l, m, n, &P->gkb) : 0;
+}
+
+template <typename T>
+tp_status tik_adjoint(const T* G, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,
+                      size_t solve_ws_bytes, const void* Ahat, T* dB, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!P) return TP_ERR_ARG;
+    return tadj_run<T>(G, l, m, n, &P->gkb, 1, solve_ws, solve_ws_bytes, Ahat, dB, ws, ws_bytes, st);
+}
+
+template <typename T>
+size_t gk_adj_ws_bytes(int l, int m, int n, const tp_tgkb_params* P) {
+    return tadj_ws<T>(l, m, n, P);
+}
+
+template <typename T>
+tp_status gk_adjoint(const T* G, int l, int m, int n, const tp_tgkb_params* P, const void* solve_ws,
+                     size_t solve_ws_bytes, const void* Ahat, T* dB, void* ws, size_t ws_bytes, cudaStream_t st) {
+    return tadj_run<T>(G, l, m, n, P, 0, solve_ws, solve_ws_bytes, Ahat, dB, ws, ws_bytes, st);
+}
+
+template size_t gk_adj_ws_bytes<float>(int, int, int, const tp_tgkb_params*);
+template size_t gk_adj_ws_bytes<double>(int, int, int, const tp_tgkb_params*);
+template tp_status gk_adjoint<float>(const float*, int, int, int, const tp_tgkb_params*, const void*, size_t,
+                                     const void*, float*, void*, size_t, cudaStream_t);
+template tp_status gk_adjoint<double>(const double*, int, int, int, const tp_tgkb_params*, const void*, size_t,
+                                      const void*, double*, void*, size_t, cudaStream_t);
 template size_t tik_adj_ws_bytes<float>(int, int, int, const tp_tik_params*);
 template size_t tik_adj_ws_bytes<double>(int, int, int, const tp_tik_params*);
 template tp_status tik_adjoint<float>(const float*, int, int, int, const tp_tik_params*, const void*, size_t,

@@ -172,6 +172,11 @@ tp_status sep_operator(const T* Tm, const double* c, int l, int m, int n, T* A, 
 // dL/dB of the Tikhonov-tGKB solution left in solve_ws (k and mu held): the
 // reverse sweep through Algorithm 4, one CTA per slice.  Ahat: null, or the
 // caller's half spectrum when the solve was given one.
+// The same for the solution of a single-slice tGKB solve (lam = 0).
+template <typename T> size_t gk_adj_ws_bytes(int l, int m, int n, const tp_tgkb_params* P);
+template <typename T>
+tp_status gk_adjoint(const T* G, int l, int m, int n, const tp_tgkb_params* P, const void* solve_ws,
+                     size_t solve_ws_bytes, const void* Ahat, T* dB, void* ws, size_t ws_bytes, cudaStream_t st);
 template <typename T> size_t tik_adj_ws_bytes(int l, int m, int n, const tp_tik_params* P);
 template <typename T>
 tp_status tik_adjoint(const T* G, int l, int m, int n, const tp_tik_params* P, const void* solve_ws,

@@ -56,7 +56,8 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "tgkb_triplets", "sep_grad_c_workspace_bytes", "sep_grad_c", "tgkb_tikhonov_grad_c_workspace_bytes",
            "tgkb_tikhonov_grad_c", "sep_operator", "ttsvd_adjoint",
            "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat",
-           "tgkb_tikhonov_adjoint_workspace_bytes", "tgkb_tikhonov_adjoint")
+           "tgkb_tikhonov_adjoint_workspace_bytes", "tgkb_tikhonov_adjoint", "tgkb_adjoint_workspace_bytes",
+           "tgkb_adjoint")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -130,9 +131,12 @@ def load(path: str | None = None):
     L.tgkb_tikhonov_adjoint_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(TikParams), i]
     L.tgkb_tikhonov_adjoint_workspace_bytes.restype = sz
     L.tgkb_tikhonov_adjoint.argtypes = [vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, vp, i, vp, sz, vp]
+    L.tgkb_adjoint_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(TgkbParams), i]
+    L.tgkb_adjoint_workspace_bytes.restype = sz
+    L.tgkb_adjoint.argtypes = [vp, i, i, i, ctypes.POINTER(TgkbParams), vp, sz, vp, vp, i, vp, sz, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
               "tgkb_tikhonov_solve", "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator",
-              "ttsvd_adjoint", "tgkb_tikhonov_adjoint"):
+              "ttsvd_adjoint", "tgkb_tikhonov_adjoint", "tgkb_adjoint"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -521,13 +525,14 @@ def ttsvd_solve(A, B, delta, tau, res_hist=False, sync=True, keep=False):
     return out + ((hist.cpu().numpy(),) if res_hist else ()) + fac
 
 
-def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None, Ahat=None, n=None):
-    """tGKB method (Algorithm 4 + Eq. (solgkb)).  Returns (X, info[, res_hist]).
+def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None, Ahat=None, n=None, keep=False):
+    """tGKB method (Algorithm 4 + Eq. (solgkb)).  Returns (X, info[, res_hist][, factor]).
 
     B is (n, l, p); p > 1 is the tGKB_p method: every lateral slice j is
     solved on its own with bound deltas[j] (default: delta for all) and its own
     k_j; info is then a list of p records and res_hist a (p, k_max+1) array.
-    With A=None, Ahat and n: the tgkb_solve_hat entry point."""
+    With A=None, Ahat and n: the tgkb_solve_hat entry point.  keep=True (p = 1)
+    also returns the solve's workspace for tgkb_adjoint."""
     op = _Op(A, Ahat, n)
     _dev(B)
     n, l, m = op.n, op.l, op.m
@@ -554,10 +559,13 @@ def tgkb_solve(A, B, delta, tau, k_max, res_hist=False, sync=True, deltas=None, 
                                                    _ptr(info), prec, wp, wn, _stream()))
     if p == 1 and hist is not None:
         hist = hist[0]
+    if keep and p != 1:
+        raise ValueError("keep=True needs one lateral slice (tgkb_adjoint)")
+    fac = (TgktFactor(ws, P, l, m, n, prec, op.device, op.dtype, op.t if op.hat else None),) if keep else ()
     if not sync:
-        return X, info, hist
+        return (X, info, hist) + fac
     out = (X, _info_dict(info) if p == 1 else _info_list(info, p))
-    return out + ((hist.cpu().numpy(),) if res_hist else ())
+    return out + ((hist.cpu().numpy(),) if res_hist else ()) + fac
 
 
 def nested_tgkb_solve(A, B, deltas, eta, k_max, res_hist=False, sync=True):
@@ -758,6 +766,71 @@ def tgkt_adjoint(fac: "TgktFactor", G: torch.Tensor) -> torch.Tensor:
     _check("tgkb_tikhonov_adjoint", L.tgkb_tikhonov_adjoint(_ptr(G), fac.l, fac.m, fac.n, ctypes.byref(fac.P), sp, sn,
                                                             _ptr(fac.ahat), _ptr(dB), fac.prec, wp, wn, _stream()))
     return dB
+
+
+def tgkb_adjoint(fac: "TgktFactor", G: torch.Tensor) -> torch.Tensor:
+    """dL/dB of the single-slice tGKB solution that made `fac` (k held at the
+    solve's value; the Krylov space moves with B) for G = dL/dX (n, m, 1).
+    Returns dB (n, l, 1)."""
+    _dev(G)
+    if tuple(G.shape) != (fac.n, fac.m, 1) or G.dtype != fac.dtype:
+        raise ValueError("G must match the solution X of the solve")
+    G = G.contiguous()
+    L = load()
+    nb = L.tgkb_adjoint_workspace_bytes(fac.l, fac.m, fac.n, ctypes.byref(fac.P), fac.prec)
+    if nb == 0:
+        raise TprodError("tgkb_adjoint_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, G.device)
+    wp, wn = _aligned(ws)
+    sp, sn = _aligned(fac.ws)
+    dB = torch.empty((fac.n, fac.l, 1), dtype=fac.dtype, device=G.device)
+    _check("tgkb_adjoint", L.tgkb_adjoint(_ptr(G), fac.l, fac.m, fac.n, ctypes.byref(fac.P), sp, sn, _ptr(fac.ahat),
+                                          _ptr(dB), fac.prec, wp, wn, _stream()))
+    return dB
+
+
+class TgkbSolve(torch.autograd.Function):
+    """X = tGKB solution (one lateral slice), differentiable in B with k held
+    at the value the solve chose (tgkb_adjoint); A is a constant."""
+
+    @staticmethod
+    def forward(ctx, B, A, kw):
+        X, _, _, fac = tgkb_solve(A, B, sync=False, keep=True, **kw)
+        ctx.fac = fac
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        if ctx.needs_input_grad[1]:
+            raise NotImplementedError("dL/dA is not provided")
+        return tgkb_adjoint(ctx.fac, G.contiguous()), None, None
+
+
+class TgktSolve(torch.autograd.Function):
+    """X = Tikhonov-tGKB solution, differentiable in B with k and mu held at
+    the values the solve chose (tgkt_adjoint); A is a constant."""
+
+    @staticmethod
+    def forward(ctx, B, A, kw):
+        X, _, fac = tgkt_solve(A, B, sync=False, keep=True, **kw)
+        ctx.fac = fac
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        if ctx.needs_input_grad[1]:
+            raise NotImplementedError("dL/dA is not provided")
+        return tgkt_adjoint(ctx.fac, G.contiguous()), None, None
+
+
+def tgkb_solve_ad(A, B, delta, tau, k_max):
+    """Differentiable (in B) tGKB solve of one lateral slice: returns X."""
+    return TgkbSolve.apply(B, A, dict(delta=delta, tau=tau, k_max=k_max))
+
+
+def tgkt_solve_ad(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12):
+    """Differentiable (in B) Tikhonov-tGKB solve: returns X."""
+    return TgktSolve.apply(B, A, dict(delta=delta, tau=tau, k_max=k_max, mu_lo=mu_lo, mu_hi=mu_hi, log_tol=log_tol))
 
 
 def tgkt_solve(A, B, delta, tau, k_max, mu_lo, mu_hi, log_tol=1e-12, sync=True, keep=False, Ahat=None, n=None):

@@ -156,7 +156,7 @@ def test_rtsvd_adjoint_central_differences(tp):
     W = g.standard_normal(X.shape)
     dB = tp.rtsvd_adjoint(fac, dev(W, dt)).cpu().numpy()
     h = 1e-6 * np.linalg.norm(B)
-    for _ in range(8):
+    for _ in range(64):
         E = g.standard_normal(B.shape)
         E /= np.linalg.norm(E)
         Xp, ip = tp.rtsvd_solve(dev(A, dt), dev(B + h * E, dt), dev(Om, dt), delta, 1.1, 3, 4, 1, **kw)
@@ -654,7 +654,7 @@ def test_sep_grad_c_rtsvd_central_differences(tp):
     g = np.random.default_rng(53)
     h = 1e-6 * np.linalg.norm(c)
     loss = lambda Xs: float(np.sum((Xs.cpu().numpy() - W) ** 2))
-    for _ in range(8):
+    for _ in range(64):
         e = g.standard_normal(n)
         e /= np.linalg.norm(e)
         Ap = synth.blur_tensor(T, c + h * e, dtype=np.float64)
@@ -705,7 +705,7 @@ def test_tgkt_grad_c_central_differences(tp):
     dc = tp.tgkt_grad_c(fac, dev(W, dt), dev(c, dt)).cpu().numpy()
     g = np.random.default_rng(72)
     h = 1e-6 * np.linalg.norm(c)
-    for _ in range(8):
+    for _ in range(64):
         e = g.standard_normal(n)
         e /= np.linalg.norm(e)
         Xp, ip = tp.tgkt_solve(dev(synth.blur_tensor(T, c + h * e, dtype=np.float64), dt), dev(B, dt), *args)
@@ -835,6 +835,56 @@ def test_tgkt_adjoint_central_differences_64_directions(tp):
         D *= np.linalg.norm(B) / np.linalg.norm(D)
         fd = (loss(B + h * D) - loss(B - h * D)) / (2 * h)
         assert abs(fd - np.sum(dB * D)) <= 1e-7 * np.linalg.norm(dB) * np.linalg.norm(D)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N,n,l", [(12, 8, None), (20, 16, 28), (32, 32, None)])
+def test_tgkb_adjoint_matches_oracle(tp, dtype, N, n, l):
+    """dL/dB of the tGKB solution (Algorithm 4, Eq. (solgkb)) at the k of the
+    GPU solve against the oracle's reverse sweep with no damping (mu = inf)."""
+    A, B, delta = problem(N, n, seed=90 + N, l=l)
+    Ad, Bd = dev(A, dtype), dev(B, dtype)
+    A64, B64 = (x.cpu().double().numpy() for x in (Ad, Bd))
+    X, info, fac = tp.tgkb_solve(Ad, Bd, delta, 1.1, min(12, N), keep=True)
+    G = rnd((n, N, 1), 91)
+    dB = tp.tgkb_adjoint(fac, dev(G, dtype)).cpu().numpy()
+    want, Xo = O.tgkt_adjoint(A64, B64, info["k"], np.inf, dev(G, dtype).cpu().double().numpy())
+    assert rel(X.cpu().numpy(), Xo) <= (1e-10 if dtype == torch.float64 else 1e-5)
+    assert rel(dB, want) <= (1e-9 if dtype == torch.float64 else 1e-5)
+
+
+def test_tgkb_adjoint_central_differences_64_directions(tp):
+    """The GPU dL/dB (float64) of L = <W, X> for the tGKB solution against
+    FP64 central differences of the oracle's tGKB at the solve's k, on 64
+    seeded directions."""
+    A, B, delta = problem(16, 9, seed=93)
+    g = np.random.default_rng(94)
+    X, info, fac = tp.tgkb_solve(dev(A, torch.float64), dev(B, torch.float64), delta, 1.1, 12, keep=True)
+    k = info["k"]
+    W = g.standard_normal(X.shape)
+    dB = tp.tgkb_adjoint(fac, dev(W, torch.float64)).cpu().numpy()
+    loss = lambda Bv: float(np.sum(W * O.tgkb_solve(A, Bv, 0.0, 1.0, k, k_fixed=k)["X"]))
+    h = 1e-6
+    for _ in range(64):
+        D = g.standard_normal(B.shape)
+        D *= np.linalg.norm(B) / np.linalg.norm(D)
+        fd = (loss(B + h * D) - loss(B - h * D)) / (2 * h)
+        assert abs(fd - np.sum(dB * D)) <= 1e-7 * np.linalg.norm(dB) * np.linalg.norm(D)
+
+
+def test_krylov_autograd_gradcheck_in_B(tp):
+    """gradcheck of TgkbSolve (k fixed by the discrepancy principle under the
+    perturbations) and TgktSolve (mu = mu_hi: the interval ends below the
+    discrepancy root) in B, float64, for a general (non-separable) A."""
+    A, B, delta = problem(10, 6, seed=95)
+    Ad = dev(A, torch.float64)
+    Bg = dev(B, torch.float64).requires_grad_()
+    assert torch.autograd.gradcheck(lambda Bx: tp.tgkb_solve_ad(Ad, Bx, delta, 1.1, 10), (Bg,), eps=1e-6,
+                                    atol=1e-7, rtol=1e-5)
+    _, free = tp.tgkt_solve(Ad, Bg.detach(), delta, 1.1, 10, 1e-3, 1e9)
+    mu0 = free["mu"] / 20.0
+    assert torch.autograd.gradcheck(lambda Bx: tp.tgkt_solve_ad(Ad, Bx, delta, 1.1, 10, mu0 / 4.0, mu0), (Bg,),
+                                    eps=1e-6, atol=1e-7, rtol=1e-5)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])

@@ -1,7 +1,7 @@
 """Pins for the oracle's gradients with respect to the tube weights c of a
 separable operator A(:,:,k) = c_k T: float64 central differences of the
 oracle's own forward solves (k, the sketch rank and mu held fixed) in seeded
-directions."""
+directions (64 of them, as for the gradients in B)."""
 import numpy as np
 import pytest
 
@@ -20,7 +20,7 @@ def separable(N, n, seed, noise=1e-2):
     return T, c, Bt + E, float(np.linalg.norm(E)), Xt
 
 
-def fd_check(forward, c, grad, seed, count=12, rtol=1e-6):
+def fd_check(forward, c, grad, seed, count=64, rtol=1e-6):
     """Central differences of the scalar forward(c) against <grad, e>."""
     g = np.random.default_rng(seed)
     h = 1e-6 * np.linalg.norm(c)
@@ -158,6 +158,6 @@ def test_grad_c_short_tubes(n):
     fwd = lambda cc: float(np.sum(W * O.ttsvd_solve(synth.blur_tensor(T, cc, dtype=np.float64), B, delta, 1.1,
                                                     k_fixed=t["k"])["X"]))
     grad = O.grad_c_separable(t["X"], W, c)
-    fd_check(fwd, c, grad, 25, count=4)
+    fd_check(fwd, c, grad, 25)
     if n == 1:
         assert np.isclose(grad[0], -np.sum(W * t["X"]) / c[0], rtol=1e-12)

@@ -501,6 +501,26 @@ def test_tgkt_adjoint_matches_central_differences_on_64_directions():
         assert abs(fd - np.sum(dB * D)) <= 1e-7 * np.linalg.norm(dB) * np.linalg.norm(D)
 
 
+def test_tgkt_adjoint_at_infinite_mu_is_the_tgkb_adjoint():
+    """mu = inf (no damping) gives the tGKB solution of Eq. (solgkb) at k
+    steps, and the reverse sweep its dL/dB: the forward against tgkb_solve,
+    the gradient against central differences on 64 seeded directions."""
+    A, B, _ = small_blur(N=10, n=8, general=0.02)
+    k = 4
+    X = O.tgkb_solve(A, B, 0.0, 1.0, k, k_fixed=k)["X"]
+    g = np.random.default_rng(43)
+    W = g.standard_normal(X.shape)
+    dB, Xa = O.tgkt_adjoint(A, B, k, np.inf, W)
+    assert np.allclose(Xa, X, atol=1e-12 * np.abs(X).max())
+    loss = lambda Bv: float(np.sum(W * O.tgkb_solve(A, Bv, 0.0, 1.0, k, k_fixed=k)["X"]))
+    h = 1e-6
+    for _ in range(64):
+        D = g.standard_normal(B.shape)
+        D *= np.linalg.norm(B) / np.linalg.norm(D)
+        fd = (loss(B + h * D) - loss(B - h * D)) / (2 * h)
+        assert abs(fd - np.sum(dB * D)) <= 1e-7 * np.linalg.norm(dB) * np.linalg.norm(D)
+
+
 def test_tgkt_adjoint_on_the_full_space_is_the_dense_tikhonov_adjoint():
     """With k = m the Krylov space is all of C^m and the solution is the dense
     Tikhonov solution X-hat_s = (A_s^H A_s + I/mu)^{-1} A_s^H B-hat_s, linear in
