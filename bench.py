@@ -42,16 +42,24 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel class from the
 # ncu capture summarised in profiles/; reported only while the source file holds the captured kernel (the
 # hash is renewed only when the file changed elsewhere).
+_SRC = "paper_2110_02485_gb300/csrc/"
+_SHA = {"zgemm_tc.cu": "56f1d158d7f719457c959a0bdd7f2a98ec99e76fc4770b96dc1ff60d7498717f",
+        "cgemm.cu": "160c7ca14d3faf7dd4ef4bda9bf3a4435e971cc84f4c617e4de456181981a416",
+        "rtsvd.cu": "27e95429992605511894878a78bc607743abc816f3923b69910d9ce750988b15",
+        "gkb.cu": "6a0b36658f1d1cdb518dedc4ad5594c0aeda196fcbe5a6bd70a308f52da9027d",
+        "dft.cu": "34991122ba0a27140057f2ba353df138d786aba820f9833122ba67d4d0e0d876"}
+# DRAM bytes (read + write) per launch of each kernel class, averaged over the class's launches in one plain
+# step of the n256 workload (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum over the whole step,
+# profiles/launches_n256_bench_step.md), with the sha256 of every source the class's kernels come from: a record
+# whose sources changed since the capture reads as null.
 NCU_TRAFFIC = {
-    "gkb": {"bytes": 70.92e6, "source": "paper_2110_02485_gb300/csrc/gkb.cu",
-            "sha256": "e5b60671570d3ef0b36e00a53d70932906826c31e0a86789484f58848fcfa887",
-            "profile": "profiles/k_gkb_n256.md"},
-    "orth": {"bytes": 7.51e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
-             "sha256": "47fa331650bf1c81124819a99904104b53b31327888072e3033922ea1a00b465",
-             "profile": "profiles/k_orth_n256.md"},
-    "svd": {"bytes": 9.69e6, "source": "paper_2110_02485_gb300/csrc/rtsvd.cu",
-            "sha256": "47fa331650bf1c81124819a99904104b53b31327888072e3033922ea1a00b465",
-            "profile": "profiles/k_jacobi_n256.md"},
+    "gemm": {"bytes": 43.68e6, "sources": ["zgemm_tc.cu", "cgemm.cu", "rtsvd.cu"],
+             "profile": "profiles/k_zgemm_tc_n256.md"},
+    "gkb": {"bytes": 69.00e6, "sources": ["gkb.cu"], "profile": "profiles/k_gkb_n256.md"},
+    "orth": {"bytes": 7.38e6, "sources": ["rtsvd.cu"], "profile": "profiles/k_orth_n256.md"},
+    "svd": {"bytes": 9.72e6, "sources": ["rtsvd.cu"], "profile": "profiles/k_jacobi_n256.md"},
+    "dft": {"bytes": 26.84e6, "sources": ["dft.cu"], "profile": "profiles/k_rdft_256_n256.md"},
+    "dp": {"bytes": 17.66e6, "sources": ["rtsvd.cu"], "profile": "profiles/launches_n256_bench_step.md"},
 }
 
 
@@ -60,12 +68,13 @@ def ncu_traffic(cls, config="n256"):
     rec = NCU_TRAFFIC.get(cls)
     if not rec or config != "n256":  # the captures summarised in profiles/ are of the n256 workload
         return None
-    try:
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
-                return None
-    except OSError:
-        return None
+    for src in rec["sources"]:
+        try:
+            with open(os.path.join(ROOT, _SRC + src), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != _SHA[src]:
+                    return None
+        except OSError:
+            return None
     return rec["bytes"]
 
 
@@ -77,6 +86,9 @@ def args_():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="n256")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-step", action="store_true",
+                   help="after the warm-ups run one plain step between cudaProfilerStart and cudaProfilerStop "
+                        "and exit without a bench line (for ncu --profile-from-start off)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-precision", action="store_true", help="skip the TF32-vs-FP32 RT-tSVD comparison")
     p.add_argument("--no-batched", action="store_true", help="skip the several-frames RT-tSVD measurement")
@@ -293,6 +305,14 @@ def run_ours(a, rank, world, local):
     for _ in range(a.warmup):
         step(A, B, Om)
     torch.cuda.synchronize()
+    if a.profile_step:  # one plain step inside the profiler's capture range, L2 flushed before it
+        flush.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step(A, B, Om)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
     # one instrumented step: device time per kernel class, and the solve records
     tprod.timing_enable(tprod.KERNEL_CLASSES)
     _, infos_dev = step(A, B, Om)
@@ -435,6 +455,9 @@ def run_ours(a, rank, world, local):
     hbm, bf16, src = peaks()
     work = class_work(cfg, infos)
     by_class = roofline_entries(work, last_step, hbm, src)
+    for c_, e_ in by_class.items():  # DRAM bytes per launch from the ncu capture of one step, where current
+        if isinstance(e_, dict) and c_ in NCU_TRAFFIC:
+            e_["traffic_per_launch"] = ncu_traffic(c_, cfg.name)
     roof = None
     if dominant in by_class:
         e, w = by_class[dominant], work[dominant]
