@@ -86,6 +86,8 @@ def args_():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="n256")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the built-in stage counts of the tensor-core products (no tuning before timing)")
     p.add_argument("--profile-step", action="store_true",
                    help="after the warm-ups run one plain step between cudaProfilerStart and cudaProfilerStop "
                         "and exit without a bench line (for ncu --profile-from-start off)")
@@ -302,6 +304,10 @@ def run_ours(a, rank, world, local):
         return (X1, X2, X3), (i1, i2, i3)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    # stage counts of the tensor-core products for this problem's shapes (outside every timed region; the
+    # results do not depend on them)
+    tprod.autotune_clear()
+    tuned = tprod.rtsvd_autotune(cfg.N, cfg.N, cfg.N, 1, cfg.block, cfg.r_max, "fp32") if not a.no_autotune else []
     for _ in range(a.warmup):
         step(A, B, Om)
     torch.cuda.synchronize()
@@ -485,6 +491,10 @@ def run_ours(a, rank, world, local):
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "roofline_by_class": by_class, "clocks": clk,
            "precision_form": prec_form, "batched_form": batched, "uneven_form": uneven,
            "differentiation_form": grad, "n512_form": n512, "b_only_form": hat, "ttsvd_form": tts,
+           "autotune": {"what": "stage count of the tensor-core products' TMA ring per product shape, timed before "
+                                "the warm-ups (results independent of it)",
+                        "shapes": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in e.items()}
+                                   for e in tuned]},
            "per_class_ms_one_step": {k: round(v[0], 4) for k, v in per_class.items()},
            "solve_info": {"rtsvd": {k: infos[0][k] for k in ("k", "r", "status", "sweeps")},
                           "tgkb": {k: infos[1][k] for k in ("k", "status")},
@@ -515,6 +525,9 @@ def precision_form(a, cfg, P, A, B, Om, flush, tprod, torch):
     out = {}
     reps = max(3, min(a.steps, 20))
     for name in ("fp32", "tf32", "bf16"):
+        if not a.no_autotune:  # the form's own product shapes
+            tprod.rtsvd_autotune(cfg.N, cfg.N, cfg.N, 1, cfg.block, cfg.r_max, name)
+
         def solve():
             return tprod.rtsvd_solve(A, B, Om, P["delta"], cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
                                      eps_rel=cfg.eps_rel, sync=False, tf32=name == "tf32", bf16=name == "bf16")
@@ -570,6 +583,8 @@ def full_size_form(a, name, flush, tprod, torch, steps=10):
         X3, i3 = tprod.tgkt_solve(A, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False)
         return (X1, X2, X3), (i1, i2, i3)
 
+    if not a.no_autotune:
+        tprod.rtsvd_autotune(cfg.N, cfg.N, cfg.N, 1, cfg.block, cfg.r_max, "fp32")
     for _ in range(3):
         step()
     torch.cuda.synchronize()
@@ -843,6 +858,10 @@ def uneven_form(a, flush, tprod, torch, count=16):
 
     nstreams = 4
     side = [torch.cuda.Stream() for _ in range(nstreams)]
+
+    if not a.no_autotune:  # every size's product shapes, before the capture
+        for n_, r_ in sorted({(int(p["N"]), int(p["r_max"])) for p in probs}):
+            tprod.rtsvd_autotune(n_, n_, n_, 1, b, r_, "fp32")
 
     def all_solves():
         # the problems are independent: four streams, joined at the end, so that small problems (few

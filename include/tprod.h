@@ -473,6 +473,42 @@ tp_status tgkb_adjoint(const void* G, int l, int m, int n, const tp_tgkb_params*
                        size_t solve_ws_bytes, const void* Ahat, void* dB, int prec, void* ws, size_t ws_bytes,
                        void* stream);
 
+/* --------------------------------------------------------- autotuner -------
+ * rtsvd_autotune: picks, for every tensor-core product that an
+ * rtsvd_truncated_solve with these sizes, params (block, r_max) and prec
+ * launches, the stage count of the product's TMA ring (2 up to what one CTA's
+ * shared memory holds; two CTAs per SM at two stages, one above) by timing
+ * each candidate with CUDA events on scratch operands, and records the
+ * fastest in a process-wide table that every later launch of that shape
+ * consults.  Results do not depend on the stage count (the same MMAs in the
+ * same order), only the time does.  The shapes: the sketch and power-iteration
+ * products (A-hat Omega_b, A-hat Z; A-hat^H Y from the transposed copy) in the
+ * sketch precision, the re-projection A-hat^H Y and the 32-column chunks of K
+ * = A-hat V.  No counterpart in the paper.
+ *   ws : device scratch, 256-byte aligned, at least rtsvd_workspace_bytes for
+ *        the same arguments (its contents are overwritten)
+ * Synchronises the stream (not for CUDA graph capture).  TP_FP64 tunes nothing
+ * (the float64 products run on the SIMT kernel) and returns TP_OK.
+ * TP_ERR_ARG for invalid sizes or precision; TP_ERR_WORKSPACE for a missing,
+ * misaligned or too small ws.
+ * tp_autotune_table: up to max entries of the table, entry i as ints[8 i ..
+ *   8 i + 7] = (op: 0 A, 2 conj(A); passes: 3 float32-accurate, 1 tf32, 0
+ *   bfloat16; columns rounded up to 8; M; K; batch; stages chosen; the
+ *   built-in rule's stages) and flts[2 i .. 2 i + 1] = (ms of the choice, ms
+ *   of the built-in rule); returns the number of entries written.
+ * tp_autotune_clear: empties the table (every shape back to the built-in rule).
+ * tp_autotune_set: puts one shape's stage count into the table (a stored
+ *   tuning, or a test): op 0 (A), 2 (conj(A), from the transposed copy) or 3
+ *   (A^H), passes, columns (1..32), M, K, batch as above; TP_ERR_ARG for a
+ *   shape the tensor-core product does not take or a stage count outside 2 ..
+ *   what fits.  Host only.
+ */
+tp_status rtsvd_autotune(int l, int m, int n, int p, const tp_rtsvd_params* params, int prec, void* ws,
+                         size_t ws_bytes, void* stream);
+int tp_autotune_table(int* ints, float* flts, int max);
+void tp_autotune_clear(void);
+tp_status tp_autotune_set(int op, int passes, int columns, int M, int K, int batch, int stages);
+
 /* ------------------------------------------------------------ misc -------- */
 const char* tp_status_string(int status);
 int tp_version(void);                 /* 100 * major + minor                        */

@@ -1,5 +1,7 @@
 #include <atomic>
 // extern "C" entry points of libtprod (declared in include/tprod.h).
+#include <stdint.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -471,6 +473,44 @@ tp_status tgkb_tikhonov_adjoint(const void* G, int l, int m, int n, const tp_tik
         return tik_adjoint<double>((const double*)G, l, m, n, params, solve_ws, solve_ws_bytes, Ahat, (double*)dB,
                                    ws, ws_bytes, st);
     return TP_ERR_ARG;
+}
+
+tp_status rtsvd_autotune(int l, int m, int n, int p, const tp_rtsvd_params* params, int prec, void* ws,
+                         size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!params || l < 1 || m < 1 || n < 1 || p < 1 || params->block < 1 || params->r_max < 1) return TP_ERR_ARG;
+    if (prec == TP_FP64) return TP_OK;  // the float64 products run on the SIMT kernel: nothing to tune
+    if (prec != TP_FP32 && prec != TP_TF32 && prec != TP_BF16) return TP_ERR_ARG;
+    if (!ws || ((uintptr_t)ws & 255)) return TP_ERR_WORKSPACE;
+    const int h = n / 2 + 1, b = params->block < params->r_max ? params->block : params->r_max;
+    const int sk = prec == TP_FP32 ? 3 : (prec == TP_TF32 ? 1 : 0);
+    // the products of a solve: sketch A-hat Omega_b and the power iteration's A-hat Z (op N), A-hat^H Y from
+    // the transposed copy (op R) in the sketch precision, the re-projection A-hat^H Y (float32-accurate) and
+    // the column chunks of K = A-hat V (float32-accurate, 32 columns, written transposed)
+    struct Shape { int op, M, N, K, passes, trans; } shapes[4] = {
+        {OP_N, l, b, m, sk, 0}, {OP_R, m, b, l, sk, 0}, {OP_R, m, b, l, 3, 0},
+        {OP_N, l, params->r_max < 32 ? params->r_max : 32, m, 3, 1}};
+    for (const Shape& sh : shapes) {
+        if (sh.passes == 0 && ((l & 3) || (m & 3))) continue;  // the BF16 form refuses these shapes
+        const tp_status e = zgemm_tc_tune(h, sh.M, sh.N, sh.K, sh.op, sh.passes, sh.trans, ws, ws_bytes, st, nullptr,
+                                          nullptr, nullptr);
+        if (e != TP_OK && e != TP_ERR_UNSUPPORTED) return e;
+    }
+    return TP_OK;
+}
+
+int tp_autotune_table(int* ints, float* flts, int max) {
+    if (!ints || !flts || max < 0) return 0;
+    return zgemm_tc_tuned(ints, flts, max);
+}
+
+void tp_autotune_clear(void) { zgemm_tc_untune(); }
+
+tp_status tp_autotune_set(int op, int passes, int columns, int M, int K, int batch, int stages) {
+    if ((op != OP_N && op != OP_R && op != OP_C) || (passes != 0 && passes != 1 && passes != 3) || columns < 1 ||
+        columns > 32 || M < 1 || K < 1 || batch < 1)
+        return TP_ERR_ARG;
+    return zgemm_tc_set(op, passes, columns, M, K, batch, stages) == TP_OK ? TP_OK : TP_ERR_ARG;
 }
 
 const char* tp_status_string(int status) {

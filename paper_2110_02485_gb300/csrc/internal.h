@@ -85,6 +85,14 @@ tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long
                    long ldb, long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes,
                    cudaStream_t st, int trans_out = 0, const int* ncap = nullptr, int c0 = 0);
 
+// The tensor-core product's stage-count tuner (a per-shape table consulted by
+// every zgemm_tc launch; results do not depend on the stage count).
+tp_status zgemm_tc_tune(int batch, int M, int N, int K, int opA, int passes, int trans_out, void* scratch,
+                        size_t scratch_bytes, cudaStream_t st, int* ns_out, float* ms_out, float* ms_dflt);
+int zgemm_tc_tuned(int* ints, float* flts, int max);
+tp_status zgemm_tc_set(int op, int passes, int N, int M, int K, int batch, int ns);
+void zgemm_tc_untune();
+
 // Batched tGKB (tGKB_p): one cooperative launch carries GKM_PB lateral
 // slices of B (columns j0 .. j0+pb-1) through Algorithm 4 in lockstep.
 // Complex arrays are cplx<T>: Ahat (h, l, m), Bhat (h, l, p), Wb (h, PB,

@@ -50,7 +50,9 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "internal.h"
@@ -70,6 +72,7 @@ constexpr uint32_t TC_SBO = 128;                  // no-swizzle: next core matri
 constexpr uint32_t TC_SBO_SW = 1024;              // 128-byte swizzle: next 8-row group
 constexpr int TC_SMEM_LIMIT = 225 * 1024;
 constexpr long long TC_SPIN = 2000000000LL;       // ~1 s at the GB300 SM clock
+constexpr int TC_NS_CAP = 6;                      // stages of the ring at most (barrier arrays)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -240,6 +243,10 @@ template <int OPA, int NCP, int NP> struct TcCfg {
     static constexpr int NS = NS2 >= 2 ? (NS2 > 4 ? 4 : NS2)
                                        : ((TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE);
     static constexpr size_t SMEM = (size_t)NS * STAGE + 1024;  // + alignment slack
+    // the most stages one CTA can hold (the autotuner's range is 2 .. NS_FIT)
+    static constexpr int NS_FIT = (TC_SMEM_LIMIT - 1024) / STAGE > TC_NS_CAP ? TC_NS_CAP
+                                                                            : (TC_SMEM_LIMIT - 1024) / STAGE;
+    static size_t smem(int ns) { return (size_t)ns * STAGE + 1024; }
     static constexpr uint32_t TX = TC_A_BYTES + B_RAW_BYTES;   // bytes the two TMA boxes deliver
     static constexpr uint32_t NCOLS = NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
 };
@@ -336,12 +343,12 @@ template <int OPA, bool CONJ, int NCP, int NP>
 __global__ void __launch_bounds__(TC_THREADS, 2)
 k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            float2* __restrict__ C, long ldc, long sC, int Mc, int Nc, int Kc, const int* skip, int* err,
-           int trans_out, const int* ncap, int c0, long long spin) {
+           int trans_out, const int* ncap, int c0, long long spin, int ns) {
     typedef TcCfg<OPA, NCP, NP> G;
     if (skip && *skip) return;
     if (ncap && c0 >= *ncap) return;  // a column chunk past the run-time column count
     extern __shared__ unsigned char sm_raw[];
-    __shared__ __align__(8) uint64_t full[G::NS], conv[G::NS], empty[G::NS], accf;
+    __shared__ __align__(8) uint64_t full[TC_NS_CAP], conv[TC_NS_CAP], empty[TC_NS_CAP], accf;
     __shared__ uint32_t tmem_s;
     __shared__ int abort_s;
     volatile int* abort = &abort_s;
@@ -356,7 +363,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     unsigned char* sgen = sm_raw + (sbase - smem_u32(sm_raw));
 
     if (tid == 0) {
-        for (int i = 0; i < G::NS; ++i) {
+        for (int i = 0; i < ns; ++i) {
             mbar_init_n(smem_u32(&full[i]), 1);
             mbar_init_n(smem_u32(&conv[i]), TC_CONV_WARPS);
             mbar_init_n(smem_u32(&empty[i]), 1);
@@ -380,8 +387,8 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         if (lane == 0) {
             int issued = 0;
             for (int kt = 0; kt < nkt; ++kt) {
-                const int st = kt % G::NS;
-                if (kt >= G::NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((kt / G::NS - 1) & 1), abort, spin)) break;
+                const int st = kt % ns;
+                if (kt >= ns && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((kt / ns - 1) & 1), abort, spin)) break;
                 const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
                 const uint32_t fb = smem_u32(&full[st]);
                 mbar_expect_tx(fb, G::TX);
@@ -391,8 +398,8 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 issued = kt + 1;
             }
             // drain: every TMA write lands before the CTA can end
-            for (int kt = issued - G::NS > 0 ? issued - G::NS : 0; kt < issued; ++kt)
-                mbar_drain(smem_u32(&full[kt % G::NS]), (uint32_t)((kt / G::NS) & 1));
+            for (int kt = issued - ns > 0 ? issued - ns : 0; kt < issued; ++kt)
+                mbar_drain(smem_u32(&full[kt % ns]), (uint32_t)((kt / ns) & 1));
         }
     } else if (warp == TC_MMA_WARP) {
         if (lane == 0) {
@@ -400,8 +407,8 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             const uint32_t id_half = idesc_tf32(TC_M, 2 * NCP);
             int issued = 0;
             for (int kt = 0; kt < nkt; ++kt) {
-                const int st = kt % G::NS;
-                if (!mbar_wait(smem_u32(&conv[st]), (uint32_t)((kt / G::NS) & 1), abort, spin)) break;
+                const int st = kt % ns;
+                if (!mbar_wait(smem_u32(&conv[st]), (uint32_t)((kt / ns) & 1), abort, spin)) break;
                 tc_fence_after();
                 const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
 #pragma unroll
@@ -428,14 +435,14 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             if (issued == nkt) {
                 mma_commit(smem_u32(&accf));
             } else if (issued > 0) {  // aborted: let the MMAs in flight finish
-                mbar_drain(smem_u32(&empty[(issued - 1) % G::NS]), (uint32_t)(((issued - 1) / G::NS) & 1));
+                mbar_drain(smem_u32(&empty[(issued - 1) % ns]), (uint32_t)(((issued - 1) / ns) & 1));
             }
         }
     } else {
         // warps 0-7: split each stage, then the epilogue
         for (int kt = 0; kt < nkt; ++kt) {
-            const int st = kt % G::NS;
-            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / G::NS) & 1), abort, spin)) break;
+            const int st = kt % ns;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / ns) & 1), abort, spin)) break;
             split_stage<OPA, CONJ, NCP, NP>(sgen + st * G::STAGE);
             fence_async_smem();  // generic-proxy writes -> tensor-core reads
             __syncwarp();
@@ -512,8 +519,11 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, 
 template <int OPA, bool CONJ, int NCP, int NP>
 tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, const void* B, long ldb,
                     long sB, void* C, long ldc, long sC, const int* skip, int* err, int trans_out, const int* ncap,
-                    int c0, cudaStream_t st) {
+                    int c0, cudaStream_t st, int ns) {
     typedef TcCfg<OPA, NCP, NP> G;
+    if (ns <= 0) ns = G::NS;                       // the built-in rule
+    if (ns < 2 || ns > G::NS_FIT) return TP_ERR_UNSUPPORTED;
+    const size_t smem = G::smem(ns);
     CUtensorMap ma, mb;
     // A: op N rows i of 2K floats (box 32 x 128, swizzled; bfloat16: 2K entries of 2 bytes, box 64 x 128);
     // op C rows i of 2M floats (box 128 x 32)
@@ -526,22 +536,94 @@ tp_status launch_tc(int batch, int M, int N, int K, const void* A, long lda, lon
         make_map(&mb, B, 2 * (uint64_t)N, K, batch, 8 * (uint64_t)ldb, 8 * (uint64_t)sB, 2 * NCP, G::KB, false);
     if (!oka || !okb) return TP_ERR_UNSUPPORTED;
     auto kern = k_zgemm_tc<OPA, CONJ, NCP, NP>;
-    if (smem_optin((const void*)kern, G::SMEM) != TP_OK) return TP_ERR_CUDA;
+    if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
     const int Mr = OPA == OP_N ? M : 2 * M;
     dim3 grid((unsigned)((Mr + TC_M - 1) / TC_M), (unsigned)batch);
     prof_begin(TP_KC_GEMM, st);
-    kern<<<grid, TC_THREADS, G::SMEM, st>>>(ma, mb, (float2*)C, ldc, sC, M, N, K, skip, err, trans_out, ncap, c0,
-                                             wait_budget(TC_SPIN));
+    kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, (float2*)C, ldc, sC, M, N, K, skip, err, trans_out, ncap, c0,
+                                          wait_budget(TC_SPIN), ns);
     return launched(TP_KC_GEMM, st);
+}
+
+// Deterministic scratch operands for the tuner (values of order one, no denormals).
+__global__ void k_tune_fill(float* x, long cnt, float f) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) x[i] = __sinf(f * (float)(i % 8191) + 0.3f);
+}
+__global__ void k_tune_fill_bf16(__nv_bfloat16* x, long cnt, float f) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) x[i] = __float2bfloat16(__sinf(f * (float)(i % 8191) + 0.3f));
+}
+
+// Stage counts picked by the tuner, per product shape.
+struct TuneKey {
+    int op, passes, ncp, M, K, batch;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(op, passes, ncp, M, K, batch) < std::tie(o.op, o.passes, o.ncp, o.M, o.K, o.batch);
+    }
+};
+struct TuneVal {
+    int ns;
+    float ms, ms_default;
+    int ns_default;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+int tuned_ns(int op, int passes, int ncp, int M, int K, int batch) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(TuneKey{op, passes, ncp, M, K, batch});
+    return it == g_tune.end() ? 0 : it->second.ns;
+}
+
+// The kernel's default stage count and the largest one for a shape (0 when the kernel does not take it).
+void ns_range(int opA, int passes, int ncp, int* dflt, int* fit) {
+    *dflt = *fit = 0;
+#define TC_R(OP, P, NC)                     \
+    {                                       \
+        typedef TcCfg<OP, NC, P> G;         \
+        *dflt = G::NS;                      \
+        *fit = G::NS_FIT;                   \
+    }
+#define TC_RS(OP, P)                                   \
+    switch (ncp) {                                     \
+        case 8: TC_R(OP, P, 8) break;                  \
+        case 16: TC_R(OP, P, 16) break;                \
+        case 24: TC_R(OP, P, 24) break;                \
+        default: TC_R(OP, P, 32) break;                \
+    }
+    const int op = opA == OP_C ? OP_C : OP_N;
+    if (passes == 3) {
+        if (op == OP_N) TC_RS(OP_N, 3) else TC_RS(OP_C, 3)
+    } else if (passes == 1) {
+        if (op == OP_N) TC_RS(OP_N, 1) else TC_RS(OP_C, 1)
+    } else if (op == OP_N) {
+        TC_RS(OP_N, 0)
+    }
+#undef TC_RS
+#undef TC_R
 }
 
 }  // namespace
 
+tp_status zgemm_tc_ns(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B,
+                      long ldb, long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes,
+                      cudaStream_t st, int trans_out, const int* ncap, int c0, int ns);
+
 // Returns TP_ERR_UNSUPPORTED (nothing enqueued) when the shape or alignment
-// does not fit this kernel; the caller then uses the SIMT product.
+// does not fit this kernel; the caller then uses the SIMT product.  The stage
+// count is the tuner's for this shape when it has one, else the built-in rule.
 tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B, long ldb,
                    long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes, cudaStream_t st,
                    int trans_out, const int* ncap, int c0) {
+    const int ns = tuned_ns(opA, passes, (N + 7) & ~7, M, K, batch);
+    return zgemm_tc_ns(batch, M, N, K, A, lda, sA, opA, B, ldb, sB, C, ldc, sC, skip, err, passes, st, trans_out, ncap,
+                       c0, ns);
+}
+
+tp_status zgemm_tc_ns(int batch, int M, int N, int K, const void* A, long lda, long sA, int opA, const void* B,
+                      long ldb, long sB, void* C, long ldc, long sC, const int* skip, int* err, int passes,
+                      cudaStream_t st, int trans_out, const int* ncap, int c0, int ns) {
     if (opA != OP_N && opA != OP_R && opA != OP_C) return TP_ERR_UNSUPPORTED;
     if (passes != 0 && passes != 1 && passes != 3) return TP_ERR_UNSUPPORTED;
     // bfloat16 A (passes 0): op N or R only, rows and slices 16-byte multiples (4 complex entries)
@@ -555,7 +637,7 @@ tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long
     const int ncp = (N + 7) & ~7;
 #define TC_GO(OP, CJ, NC, P)                                                                                  \
     launch_tc<OP, CJ, NC, P>(batch, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, skip, err, trans_out, ncap, \
-                             c0, st)
+                             c0, st, ns)
 #define TC_SWITCH(OP, CJ, P)                          \
     switch (ncp) {                                    \
         case 8: return TC_GO(OP, CJ, 8, P);           \
@@ -577,6 +659,112 @@ tp_status zgemm_tc(int batch, int M, int N, int K, const void* A, long lda, long
     TC_SWITCH(OP_C, false, 1)
 #undef TC_SWITCH
 #undef TC_GO
+}
+
+// Times every stage count from 2 to the largest that fits for one product
+// shape on scratch operands (filled here; A is M x K, B K x N, C M x N per
+// slice, row-major, bfloat16 A for passes 0) and records the fastest.
+// Synchronises the stream.  TP_ERR_UNSUPPORTED when the kernel does not take
+// the shape, TP_ERR_WORKSPACE when the scratch is too small.
+tp_status zgemm_tc_tune(int batch, int M, int N, int K, int opA, int passes, int trans_out, void* scratch,
+                        size_t scratch_bytes, cudaStream_t st, int* ns_out, float* ms_out, float* ms_dflt) {
+    const int ncp = (N + 7) & ~7;
+    int dflt = 0, fit = 0;
+    ns_range(opA, passes, ncp, &dflt, &fit);
+    if (dflt == 0) return TP_ERR_UNSUPPORTED;
+    const long rows = opA == OP_C ? K : M, cols = opA == OP_C ? M : K;  // A stored rows x cols complex
+    const size_t ab = passes == 0 ? 4 : 8;
+    const size_t a_bytes = (((size_t)batch * rows * cols * ab) + 255) & ~(size_t)255;
+    const size_t b_bytes = (((size_t)batch * K * N * 8) + 255) & ~(size_t)255;
+    const size_t c_bytes = (size_t)batch * M * N * 8;
+    if (!scratch || ((uintptr_t)scratch & 255) || scratch_bytes < a_bytes + b_bytes + c_bytes) return TP_ERR_WORKSPACE;
+    unsigned char* base = (unsigned char*)scratch;
+    void *A = base, *B = base + a_bytes, *C = base + a_bytes + b_bytes;
+    const long na = (long)batch * rows * cols * 2, nb = (long)batch * K * N * 2;
+    if (passes == 0) k_tune_fill_bf16<<<(unsigned)((na + 255) / 256), 256, 0, st>>>((__nv_bfloat16*)A, na, 0.37f);
+    else k_tune_fill<<<(unsigned)((na + 255) / 256), 256, 0, st>>>((float*)A, na, 0.37f);
+    k_tune_fill<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>((float*)B, nb, 0.71f);
+    if (cudaGetLastError() != cudaSuccess) return TP_ERR_CUDA;
+    const long ldc = trans_out ? M : N;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TP_ERR_CUDA;
+    int best = 0;
+    float best_ms = 0.f, d_ms = 0.f;
+    tp_status err = TP_OK;
+    for (int ns = 2; ns <= fit && err == TP_OK; ++ns) {
+        auto run = [&]() {
+            return zgemm_tc_ns(batch, M, N, K, A, cols, rows * cols, opA, B, N, (long)K * N, C, ldc, (long)M * N,
+                               nullptr, nullptr, passes, st, trans_out, nullptr, 0, ns);
+        };
+        for (int w = 0; w < 2 && err == TP_OK; ++w) err = run();
+        if (err != TP_OK) break;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 5 && err == TP_OK; ++rep) {  // the fastest of five launches
+            cudaEventRecord(e0, st);
+            err = run();
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) err = TP_ERR_CUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = t < ms ? t : ms;
+        }
+        if (ns == dflt) d_ms = ms;
+        if (best == 0 || ms < best_ms) {
+            best = ns;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != TP_OK) return err;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[TuneKey{opA, passes, ncp, M, K, batch}] = TuneVal{best, best_ms, d_ms, dflt};
+    }
+    if (ns_out) *ns_out = best;
+    if (ms_out) *ms_out = best_ms;
+    if (ms_dflt) *ms_dflt = d_ms;
+    return TP_OK;
+}
+
+// The tuner's table: up to max entries (op, passes, columns, M, K, batch, stages, ms, default stages,
+// default ms) into out as ints and floats; returns the number of entries.
+int zgemm_tc_tuned(int* ints, float* flts, int max) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    int i = 0;
+    for (const auto& kv : g_tune) {
+        if (i >= max) break;
+        int* o = ints + 8 * i;
+        o[0] = kv.first.op;
+        o[1] = kv.first.passes;
+        o[2] = kv.first.ncp;
+        o[3] = kv.first.M;
+        o[4] = kv.first.K;
+        o[5] = kv.first.batch;
+        o[6] = kv.second.ns;
+        o[7] = kv.second.ns_default;
+        flts[2 * i] = kv.second.ms;
+        flts[2 * i + 1] = kv.second.ms_default;
+        ++i;
+    }
+    return i;
+}
+
+// Sets the stage count of one product shape (op as zgemm_tc takes it, columns
+// before rounding); TP_ERR_UNSUPPORTED outside 2 .. the largest that fits.
+tp_status zgemm_tc_set(int op, int passes, int N, int M, int K, int batch, int ns) {
+    const int ncp = (N + 7) & ~7;
+    int dflt = 0, fit = 0;
+    ns_range(op, passes, ncp, &dflt, &fit);
+    if (dflt == 0 || ns < 2 || ns > fit) return TP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[TuneKey{op, passes, ncp, M, K, batch}] = TuneVal{ns, 0.f, 0.f, dflt};
+    return TP_OK;
+}
+
+void zgemm_tc_untune() {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
 }
 
 }  // namespace tp

@@ -57,7 +57,7 @@ EXPORTS = ("tprod_fft", "tprod_ifft", "tprod_gemm_workspace_bytes", "tprod_gemm"
            "tgkb_tikhonov_grad_c", "sep_operator", "ttsvd_adjoint",
            "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat",
            "tgkb_tikhonov_adjoint_workspace_bytes", "tgkb_tikhonov_adjoint", "tgkb_adjoint_workspace_bytes",
-           "tgkb_adjoint")
+           "tgkb_adjoint", "rtsvd_autotune", "tp_autotune_table", "tp_autotune_clear", "tp_autotune_set")
 
 KERNEL_CLASSES = ("dft", "gemm", "orth", "svd", "gkb", "dp", "tik", "misc")
 
@@ -131,12 +131,19 @@ def load(path: str | None = None):
     L.tgkb_tikhonov_adjoint_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(TikParams), i]
     L.tgkb_tikhonov_adjoint_workspace_bytes.restype = sz
     L.tgkb_tikhonov_adjoint.argtypes = [vp, i, i, i, ctypes.POINTER(TikParams), vp, sz, vp, vp, i, vp, sz, vp]
+    L.rtsvd_autotune.argtypes = [i, i, i, i, ctypes.POINTER(RtsvdParams), i, vp, sz, vp]
+    L.tp_autotune_table.argtypes = [vp, vp, i]
+    L.tp_autotune_table.restype = i
+    L.tp_autotune_clear.argtypes = []
+    L.tp_autotune_clear.restype = None
+    L.tp_autotune_set.argtypes = [i, i, i, i, i, i, i]
+    L.tp_autotune_set.restype = i
     L.tgkb_adjoint_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(TgkbParams), i]
     L.tgkb_adjoint_workspace_bytes.restype = sz
     L.tgkb_adjoint.argtypes = [vp, i, i, i, ctypes.POINTER(TgkbParams), vp, sz, vp, vp, i, vp, sz, vp]
     for f in ("tprod_fft", "tprod_ifft", "tprod_gemm", "rtsvd_truncated_solve", "tgkb_solve",
               "tgkb_tikhonov_solve", "rtsvd_truncated_solve_hat", "tgkb_solve_hat", "tgkb_tikhonov_solve_hat", "tprod_gemm_noalloc", "sep_grad_c", "tgkb_tikhonov_grad_c", "sep_operator",
-              "ttsvd_adjoint", "tgkb_tikhonov_adjoint", "tgkb_adjoint"):
+              "ttsvd_adjoint", "tgkb_tikhonov_adjoint", "tgkb_adjoint", "rtsvd_autotune"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -766,6 +773,54 @@ def tgkt_adjoint(fac: "TgktFactor", G: torch.Tensor) -> torch.Tensor:
     _check("tgkb_tikhonov_adjoint", L.tgkb_tikhonov_adjoint(_ptr(G), fac.l, fac.m, fac.n, ctypes.byref(fac.P), sp, sn,
                                                             _ptr(fac.ahat), _ptr(dB), fac.prec, wp, wn, _stream()))
     return dB
+
+
+_FORMS = {"fp32": TP_FP32, "tf32": TP_TF32, "bf16": TP_BF16, "fp64": TP_FP64}
+
+
+def rtsvd_autotune(n, l, m, p=1, block=16, r_max=160, form="fp32", device="cuda") -> list:
+    """Pick the stage counts of the tensor-core products that an rtsvd_solve
+    of these sizes and form (fp32, tf32, bf16; fp64 tunes nothing) launches,
+    by timing each candidate (rtsvd_autotune; synchronises the stream).  Later
+    solves of these shapes use the choices; results do not change.  Returns
+    the whole table (autotune_table)."""
+    prec = _FORMS[form]
+    P = RtsvdParams(1.0, 1.1, 0.1, 0.0, 1, 1, int(block), int(r_max), None)
+    L = load()
+    nb = L.rtsvd_workspace_bytes(l, m, n, p, ctypes.byref(P), prec)
+    if nb == 0:
+        raise TprodError("rtsvd_workspace_bytes", TP_ERR_ARG)
+    ws = _workspace(nb, torch.device(device))
+    wp, wn = _aligned(ws)
+    _check("rtsvd_autotune", L.rtsvd_autotune(l, m, n, p, ctypes.byref(P), prec, wp, wn, _stream()))
+    return autotune_table()
+
+
+def autotune_table() -> list:
+    """The tuner's table: one dict per tuned product shape."""
+    L = load()
+    cap = 256
+    ints = (ctypes.c_int * (8 * cap))()
+    flts = (ctypes.c_float * (2 * cap))()
+    cnt = L.tp_autotune_table(ctypes.cast(ints, ctypes.c_void_p), ctypes.cast(flts, ctypes.c_void_p), cap)
+    ops = {0: "A", 2: "conj(A)", 3: "A^H"}
+    forms = {3: "fp32", 1: "tf32", 0: "bf16"}
+    return [{"op": ops.get(ints[8 * k], ints[8 * k]), "form": forms.get(ints[8 * k + 1], ints[8 * k + 1]),
+             "columns": ints[8 * k + 2], "M": ints[8 * k + 3], "K": ints[8 * k + 4], "batch": ints[8 * k + 5],
+             "stages": ints[8 * k + 6], "stages_default": ints[8 * k + 7], "ms": flts[2 * k],
+             "ms_default": flts[2 * k + 1]} for k in range(cnt)]
+
+
+def autotune_clear() -> None:
+    """Every product shape back to the built-in stage-count rule."""
+    load().tp_autotune_clear()
+
+
+def autotune_set(op: int, form: str, columns: int, M: int, K: int, batch: int, stages: int) -> None:
+    """Put one product shape's stage count into the table (op 0: A, 2: conj(A)
+    from the transposed copy, 3: A^H)."""
+    passes = {"fp32": 3, "tf32": 1, "bf16": 0}[form]
+    _check("tp_autotune_set", load().tp_autotune_set(op, passes, columns, M, K, batch, stages))
 
 
 def tgkb_adjoint(fac: "TgktFactor", G: torch.Tensor) -> torch.Tensor:

@@ -155,3 +155,24 @@ def test_tube_weight_gradient_queries_and_argument_checks(lib):
     assert L.sep_grad_c(p, p, None, 16, 16, 1, p, tprod.TP_FP32, p, 1 << 20, None) == -1
     assert L.tgkb_tikhonov_grad_c(None, p, 64, 64, 32, ctypes.byref(K), p, 1 << 30, p, tprod.TP_FP32, p, 1 << 20,
                                   None) == -1
+
+
+def test_autotune_table_host_checks(lib):
+    """tp_autotune_set answers on the host: shapes the tensor-core product
+    does not take and stage counts outside its range are refused, accepted
+    entries appear in the table, and clearing empties it."""
+    from paper_2110_02485_gb300 import tprod
+    L = tprod.load()
+    L.tp_autotune_clear()
+    assert L.tp_autotune_set(1, 3, 16, 256, 256, 129, 2) == -1        # op T is not a tensor-core form
+    assert L.tp_autotune_set(0, 2, 16, 256, 256, 129, 2) == -1        # passes 2 does not exist
+    assert L.tp_autotune_set(0, 3, 33, 256, 256, 129, 2) == -1        # more than 32 columns
+    assert L.tp_autotune_set(0, 3, 16, 256, 256, 129, 1) == -1        # one stage is no ring
+    assert L.tp_autotune_set(0, 3, 16, 256, 256, 129, 7) == -1        # more stages than any CTA holds
+    assert L.tp_autotune_set(3, 0, 16, 256, 256, 129, 2) == -1        # the bfloat16 form takes no A^H
+    assert L.tp_autotune_set(0, 3, 16, 256, 256, 129, 3) == 0
+    assert L.tp_autotune_set(2, 0, 16, 256, 256, 129, 4) == 0
+    table = tprod.autotune_table()
+    assert {(e["op"], e["form"], e["stages"]) for e in table} == {("A", "fp32", 3), ("conj(A)", "bf16", 4)}
+    tprod.autotune_clear()
+    assert tprod.autotune_table() == []
