@@ -1805,19 +1805,19 @@ __device__ void tadj_unproj(const cplx<T>* Q, cplx<T>* Qbar, long ld, int cnt, i
     tadj_dots<T>(Q, ld, cnt, fbar, len, qf);
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
         const cplx<T> fb = fbar[e], xv = x[e];
-        double sr = 0.0, si = 0.0;
+        T sr = 0, si = 0;  // the working precision (float64 arithmetic is 1/64 of the float32 rate)
         for (int i = 0; i < cnt; ++i) {
-            const double2 ci = c[i], qi = qf[i];
+            const T cr = (T)c[i].x, ci = (T)c[i].y, qr = (T)qf[i].x, qi = (T)qf[i].y;
             cplx<T>* qb = Qbar + (long)i * ld + e;
             // fb conj(c_i) + x conj(qf_i)
-            const double ur = (double)fb.x * ci.x + (double)fb.y * ci.y + (double)xv.x * qi.x + (double)xv.y * qi.y;
-            const double ui = (double)fb.y * ci.x - (double)fb.x * ci.y + (double)xv.y * qi.x - (double)xv.x * qi.y;
-            *qb = mk<T>((T)((double)qb->x - ur), (T)((double)qb->y - ui));
+            const T ur = fb.x * cr + fb.y * ci + xv.x * qr + xv.y * qi;
+            const T ui = fb.y * cr - fb.x * ci + xv.y * qr - xv.x * qi;
+            *qb = mk<T>(qb->x - ur, qb->y - ui);
             const cplx<T> q = Q[(long)i * ld + e];
-            sr += (double)q.x * qi.x - (double)q.y * qi.y;
-            si += (double)q.x * qi.y + (double)q.y * qi.x;
+            sr += q.x * qr - q.y * qi;
+            si += q.x * qi + q.y * qr;
         }
-        xbar[e] = mk<T>((T)((double)fb.x - sr), (T)((double)fb.y - si));
+        xbar[e] = mk<T>(fb.x - sr, fb.y - si);
     }
     __syncthreads();
 }
@@ -1844,13 +1844,35 @@ __device__ void tadj_mv_n(const cplx<T>* a, int l, int m, const cplx<T>* v, doub
 template <typename T>
 __device__ void tadj_mv_c(const cplx<T>* a, int l, int m, const cplx<T>* t, double beta, const cplx<T>* v,
                           cplx<T>* y) {
-    for (int e = threadIdx.x; e < m; e += blockDim.x) {
-        cplx<T> acc = mk<T>(0, 0);
-        for (int i = 0; i < l; ++i) cfmac(acc, a[(long)i * m + e], t[i]);
-        if (v) acc = csub(acc, cscale(v[e], (T)beta));
-        y[e] = acc;
+    // columns e < m, the rows split into blockDim / m (at most 4) interleaved shares whose partial sums meet in
+    // the shared array (fixed order); two accumulators per thread
+    __shared__ cplx<T> part[3 * (TIKADJ_THREADS / 4)];  // (shares - 1) x span <= 3 x blockDim / 4
+    int sh = (int)blockDim.x / m;
+    sh = sh < 1 ? 1 : (sh > 4 ? 4 : sh);
+    const int span = (int)blockDim.x / sh;  // threads per share
+    const int share = (int)threadIdx.x / span, c0 = (int)threadIdx.x - share * span;
+    for (int e0 = 0; e0 < m; e0 += span) {
+        const int e = e0 + c0;
+        cplx<T> acc0 = mk<T>(0, 0), acc1 = mk<T>(0, 0);
+        if (share < sh && e < m) {
+            int i = share;
+            for (; i + sh < l; i += 2 * sh) {
+                cfmac(acc0, a[(long)i * m + e], t[i]);
+                cfmac(acc1, a[(long)(i + sh) * m + e], t[i + sh]);
+            }
+            if (i < l) cfmac(acc0, a[(long)i * m + e], t[i]);
+        }
+        const cplx<T> acc = cadd(acc0, acc1);
+        if (share > 0 && share < sh && e < m) part[(share - 1) * span + c0] = acc;
+        __syncthreads();
+        if (share == 0 && e < m) {
+            cplx<T> sum = acc;
+            for (int q = 1; q < sh; ++q) sum = cadd(sum, part[(q - 1) * span + c0]);
+            if (v) sum = csub(sum, cscale(v[e], (T)beta));
+            y[e] = sum;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // Reverse of (u, nrm) = (t / ||t||, ||t||): tbar = ubar / nrm + (nbar - Re<u, ubar> / nrm) u.
@@ -1858,9 +1880,9 @@ template <typename T>
 __device__ void tadj_unnorm(const cplx<T>* ubar, double nbar, const cplx<T>* u, double nrm, int len, cplx<T>* tbar,
                             double* red) {
     const double ru = tadj_redot<T>(u, ubar, len, red);
-    const double f = nbar - ru / nrm;
+    const T f = (T)(nbar - ru / nrm), in = (T)(1.0 / nrm);
     for (int e = threadIdx.x; e < len; e += blockDim.x)
-        tbar[e] = mk<T>((T)(ubar[e].x / nrm + f * u[e].x), (T)(ubar[e].y / nrm + f * u[e].y));
+        tbar[e] = mk<T>(ubar[e].x * in + f * u[e].x, ubar[e].y * in + f * u[e].y);
     __syncthreads();
 }
 
@@ -1965,13 +1987,14 @@ __global__ void __launch_bounds__(TIKADJ_THREADS) k_tikadj_rev(const TadjArgs<T>
         tadj_mv_n<T>(a, l, m, vj, aj, uj, t0);
         tadj_dots<T>(U, l, j + 1, t0, l, cdot);
         for (int e = tid; e < l; e += blockDim.x) {
-            double sr = 0.0, si = 0.0;
+            T sr = 0, si = 0;
             for (int i = 0; i <= j; ++i) {
                 const V q = U[(long)i * l + e];
-                sr += (double)q.x * cdot[i].x - (double)q.y * cdot[i].y;
-                si += (double)q.x * cdot[i].y + (double)q.y * cdot[i].x;
+                const T cr = (T)cdot[i].x, ci = (T)cdot[i].y;
+                sr += q.x * cr - q.y * ci;
+                si += q.x * ci + q.y * cr;
             }
-            t1[e] = mk<T>((T)((double)t0[e].x - sr), (T)((double)t0[e].y - si));
+            t1[e] = mk<T>(t0[e].x - sr, t0[e].y - si);
         }
         __syncthreads();
         // u_{j+1} = t2 / z_{j+1};  t2 = t1 - U (U^H t1);  t1 = t0 - U (U^H t0)
@@ -1990,13 +2013,14 @@ __global__ void __launch_bounds__(TIKADJ_THREADS) k_tikadj_rev(const TadjArgs<T>
         tadj_mv_c<T>(a, l, m, uj, j > 0 ? (double)z[j] : 0.0, j > 0 ? Vv + (long)(j - 1) * m : nullptr, w0);
         tadj_dots<T>(Vv, m, j, w0, m, cdot);
         for (int e = tid; e < m; e += blockDim.x) {
-            double sr = 0.0, si = 0.0;
+            T sr = 0, si = 0;
             for (int i = 0; i < j; ++i) {
                 const V q = Vv[(long)i * m + e];
-                sr += (double)q.x * cdot[i].x - (double)q.y * cdot[i].y;
-                si += (double)q.x * cdot[i].y + (double)q.y * cdot[i].x;
+                const T cr = (T)cdot[i].x, ci = (T)cdot[i].y;
+                sr += q.x * cr - q.y * ci;
+                si += q.x * ci + q.y * cr;
             }
-            w1[e] = mk<T>((T)((double)w0[e].x - sr), (T)((double)w0[e].y - si));
+            w1[e] = mk<T>(w0[e].x - sr, w0[e].y - si);
         }
         __syncthreads();
         // v_j = w2 / c_j;  w2 = w1 - V (V^H w1);  w1 = w0 - V (V^H w0)
