@@ -278,7 +278,11 @@ tp_status ttsvd_adjoint(const void* G, int l, int m, int n, int p, const tp_ttsv
  * data with odd m, or too little shared memory) run one launch per slice.
  *   A : real (n, l, m)     B : real (n, l, p)     X : real (n, m, p)
  *   d_info : p device records, record j for slice j
- * Limits: k_max <= min(l, m, 512); l, m <= 1024; 1 <= p <= 1024.
+ * Limits: k_max <= min(l, m, 512); l, m <= 1024; 1 <= p <= 1024; n <= 1024
+ * (float32) or 512 (float64).  The persistent launch holds the CTAs of all
+ * n/2 + 1 Fourier slices at once (one, two or four per SM: 1024, 512 or 256
+ * threads each); a shape whose CTAs do not all fit returns
+ * TP_ERR_UNSUPPORTED before anything is enqueued.
  */
 typedef struct {
     double delta;       /* noise bound of Eq. (errbd); with p > 1, the bound of every

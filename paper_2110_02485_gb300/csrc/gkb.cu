@@ -359,7 +359,7 @@ __device__ T normalize_into(const cplx<T>* u, int L, T p, double* red, NormBc<T>
 // Persistent tGKB.  Outputs per slice: W (k_max x m), Q (k_max+1 x l),
 // c (k_max), z (k_max+1), Xhat (m) for the chosen k; State k/status; info.
 template <typename T, bool VEC, int NT>
-__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2)
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : (NT >= 512 ? 2 : 4))
 k_gkb(const cplx<T>* __restrict__ Ahat, const cplx<T>* __restrict__ Bhat, int l, int m, int n, int h, int k_max,
       double tau_delta, cplx<T>* Wb, cplx<T>* Qb, T* cc, T* zz, double* res2, unsigned* counters,
       cplx<T>* Xhat, State* st, tp_info* info, double* res_hist, long long spin_cycles, int write_info, int kc,
@@ -619,7 +619,7 @@ __device__ double2 block_dot(const cplx<T>* q, const cplx<T>* b, int L, double* 
 }
 
 template <typename T, bool VEC, int NT>
-__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2) k_gkb_nested(const GknArgs a) {
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : (NT >= 512 ? 2 : 4)) k_gkb_nested(const GknArgs a) {
     typedef cplx<T> V;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int l = a.l, m = a.m, n = a.n, h = a.h, k_max = a.k_max, p = a.p;
@@ -1259,11 +1259,12 @@ static tp_status gk_single(const GkWs<T>& w, const cplx<T>* Bhat_j, cplx<T>* Xha
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return TP_ERR_CUDA;
     // One CTA per Fourier slice, all resident (cooperative launch): 1024
-    // threads when one CTA per SM suffices, else 512.  Vector loads need
+    // threads when one CTA per SM suffices, else 512 (two per SM) or 256
+    // (four per SM, up to n = 1214 on 152 SMs).  Vector loads need
     // 16-byte aligned rows.  Spare shared memory caches the first kc vectors
     // of both Krylov bases.
     const size_t vb = sizeof(cplx<T>);
-    const int nt = (h <= nsm) ? 1024 : 512;
+    const int nt = (h <= nsm) ? 1024 : (h <= 2 * nsm ? 512 : 256);  // 1, 2 or 4 CTAs per SM
     const bool vec = ((size_t)m * vb) % 16 == 0 && (size_t)m * vb / 16 <= (size_t)nt;
     const size_t part_n = std::max<size_t>(4 * (size_t)L, 16 / vb * (size_t)nt);
     const size_t base_bytes = ((size_t)l + m + L + k_max + 1 + part_n) * vb;
@@ -1276,7 +1277,8 @@ static tp_status gk_single(const GkWs<T>& w, const cplx<T>* Bhat_j, cplx<T>* Xha
     const size_t smem = base_bytes + (size_t)kc * ((size_t)l + m) * vb;
     const void* kern;
     if (nt == 1024) kern = vec ? (const void*)k_gkb<T, true, 1024> : (const void*)k_gkb<T, false, 1024>;
-    else kern = vec ? (const void*)k_gkb<T, true, 512> : (const void*)k_gkb<T, false, 512>;
+    else if (nt == 512) kern = vec ? (const void*)k_gkb<T, true, 512> : (const void*)k_gkb<T, false, 512>;
+    else kern = vec ? (const void*)k_gkb<T, true, 256> : (const void*)k_gkb<T, false, 256>;
     if (smem_optin(kern, smem) != TP_OK) return TP_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess)
         return TP_ERR_CUDA;
@@ -1432,13 +1434,14 @@ tp_status gkn_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return TP_ERR_CUDA;
     const size_t vb = sizeof(cplx<T>);
-    const int nt = (h <= nsm) ? 1024 : 512;
+    const int nt = (h <= nsm) ? 1024 : (h <= 2 * nsm ? 512 : 256);  // 1, 2 or 4 CTAs per SM
     const bool vec = ((size_t)m * vb) % 16 == 0 && (size_t)m * vb / 16 <= (size_t)nt;
     const size_t part_n = std::max<size_t>(4 * (size_t)L, 16 / vb * (size_t)nt);
     const size_t smem = ((size_t)l + m + L + l + k_max + 1 + part_n) * vb;
     const void* kern;
     if (nt == 1024) kern = vec ? (const void*)k_gkb_nested<T, true, 1024> : (const void*)k_gkb_nested<T, false, 1024>;
-    else kern = vec ? (const void*)k_gkb_nested<T, true, 512> : (const void*)k_gkb_nested<T, false, 512>;
+    else if (nt == 512) kern = vec ? (const void*)k_gkb_nested<T, true, 512> : (const void*)k_gkb_nested<T, false, 512>;
+    else kern = vec ? (const void*)k_gkb_nested<T, true, 256> : (const void*)k_gkb_nested<T, false, 256>;
     if (smem_optin(kern, smem) != TP_OK) return TP_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess) return TP_ERR_CUDA;
     if (!coop || (long)per_sm * nsm < h) return TP_ERR_UNSUPPORTED;
