@@ -126,12 +126,7 @@ k_rdft_pow2(const T* __restrict__ X, cplx<T>* __restrict__ Xh, int n, int logn, 
     store_partial<T>(acc, sumsq);
 }
 
-// ---- n = 256 as 16 x 16 ------------------------------------------------------
-// The packed sequences of a CTA (16 of them, two real tubes each) are
-// transformed by the 16 x 16 split of the DFT (x_n, n = 16 n1 + n2): sixteen
-// 16-point DFTs over n1 in registers, the twiddles exp(-2 pi i n2 k1 / 256),
-// sixteen 16-point DFTs over n2; thread (seq, j) does the j-th of each for
-// its sequence.  Three barriers instead of the eight of the radix-2 stages.
+// ---- register DFTs of 4, 16 and 32 points (the n = 16 Q kernels below) --------
 template <typename T>
 __device__ __forceinline__ void dft4f(cplx<T>& x0, cplx<T>& x1, cplx<T>& x2, cplx<T>& x3) {
     // forward 4-point DFT in place: X_k = sum_n x_n exp(-2 pi i n k / 4)
@@ -173,17 +168,72 @@ __device__ __forceinline__ void dft16f(cplx<T> (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = o[i];
 }
 
+// forward 32-point DFT of v in place, natural order in and out: the 16-point
+// DFTs of the even and odd entries, combined with exp(-2 pi i k / 32)
 template <typename T>
+__device__ __forceinline__ void dft32f(cplx<T> (&v)[32]) {
+    // cos and sin of 2 pi k / 32, k = 0 .. 7
+    const T c1 = (T)0.98078528040323044913, s1 = (T)0.19509032201612826785;
+    const T c2 = (T)0.92387953251128675613, s2 = (T)0.38268343236508977173;
+    const T c3 = (T)0.83146961230254523708, s3 = (T)0.55557023301960222474, h2 = (T)0.70710678118654752440;
+    const T C[8] = {(T)1, c1, c2, c3, h2, s3, s2, s1}, S[8] = {(T)0, s1, s2, s3, h2, c3, c2, c1};
+    cplx<T> e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+    }
+    dft16f<T>(e);
+    dft16f<T>(o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        // exp(-2 pi i k / 32) = c - i s; k >= 8 turns by a further -pi / 2
+        const T c = k < 8 ? C[k] : -S[k - 8], sn = k < 8 ? S[k] : C[k - 8];
+        const cplx<T> t = mk<T>(o[k].x * c + o[k].y * sn, o[k].y * c - o[k].x * sn);
+        v[k] = cadd(e[k], t);
+        v[k + 16] = csub(e[k], t);
+    }
+}
+template <typename T, int Q> struct DftQ;
+template <typename T> struct DftQ<T, 16> {
+    static __device__ __forceinline__ void run(cplx<T> (&v)[16]) { dft16f<T>(v); }
+};
+template <typename T> struct DftQ<T, 32> {
+    static __device__ __forceinline__ void run(cplx<T> (&v)[32]) { dft32f<T>(v); }
+};
+
+// ---- n = 16 Q (Q = 16: n = 256; Q = 32: n = 512) ------------------------------
+// x_t with t = Q t1 + t2 (t1 < 16, t2 < Q), X_k with k = k1 + 16 k2:
+//   X[k1 + 16 k2] = sum_t2 exp(-2 pi i t2 k2 / Q) exp(-2 pi i t2 k1 / n)
+//                   sum_t1 exp(-2 pi i t1 k1 / 16) x[Q t1 + t2].
+// Thread (seq, j) of the 16 per packed sequence does the 16-point DFTs over t1
+// for t2 = j, j + 16, ... (Q / 16 of them), applies the twiddles, and then the
+// Q-point DFT over t2 for k1 = j, all in registers.  The three shared-memory
+// phases (real input [t][tube], twiddled partial DFTs [seq][k1][t2], packed
+// spectrum [k][seq]) share one buffer, each read into registers behind a
+// barrier before the next is written, so that several CTAs fit on an SM.
+template <int Q> struct Rdft16Q {
+    static constexpr int n = 16 * Q, XS = DFT_TILE + 1, TS = Q + 1, ZS = 17;
+    template <typename T> static constexpr size_t region() {
+        const size_t a = (size_t)n * XS * sizeof(T), b = (size_t)256 * TS * 2 * sizeof(T),
+                     c = (size_t)n * ZS * 2 * sizeof(T);
+        return a > b ? (a > c ? a : c) : (b > c ? b : c);
+    }
+    template <typename T> static constexpr size_t smem() { return (size_t)n * 2 * sizeof(T) + region<T>(); }
+};
+
+template <typename T, int Q>
 __global__ void __launch_bounds__(DFT_THREADS)
-k_rdft_256(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int cols, long ld, long ss, double* sumsq,
+k_rdft_16q(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int cols, long ld, long ss, double* sumsq,
            const int* skip) {
     if (skip && *skip) return;
-    constexpr int n = 256, XS = DFT_TILE + 1, TS = 17;
+    typedef Rdft16Q<Q> R;
+    constexpr int n = R::n, XS = R::XS, TS = R::TS, ZS = R::ZS;
     extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* tw = (cplx<T>*)smraw;                 // 256 roots exp(-2 pi i m / 256)
-    cplx<T>* zt = tw + n;                          // [seq][k1][n2], row stride 17: 16 * 16 * 17
-    T* zx = (T*)(zt + 16 * 16 * TS);               // real input [k][tube], row stride 33; later the
-    cplx<T>* z = (cplx<T>*)zx;                     // packed spectrum [k][seq], row stride 17
+    cplx<T>* tw = (cplx<T>*)smraw;                 // n roots exp(-2 pi i m / n)
+    T* zx = (T*)(tw + n);                          // phase 1: real input [t][tube], row stride 33
+    cplx<T>* zt = (cplx<T>*)zx;                    // phase 2: [seq][k1][t2], row stride Q + 1
+    cplx<T>* z = (cplx<T>*)zx;                     // phase 3: packed spectrum [k][seq], row stride 17
     const long t0 = (long)blockIdx.x * DFT_TILE;
     fill_roots<T>(tw, n, n, (T)-1);
     const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
@@ -191,36 +241,50 @@ k_rdft_256(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int co
     const T* xt = X + (live ? tube_off(t0 + tt, cols, ld) : 0);
     T acc = 0;
     {
-        constexpr int LB = n / (DFT_THREADS / DFT_TILE);  // 32 loads in flight per thread
-        T v[LB];
+        constexpr int LB = n / (DFT_THREADS / DFT_TILE) > 32 ? 32 : n / (DFT_THREADS / DFT_TILE);
+#pragma unroll 1
+        for (int kb = 0; kb < n / (DFT_THREADS / DFT_TILE); kb += LB) {
+            T v[LB];  // LB loads in flight per thread
 #pragma unroll
-        for (int j = 0; j < LB; ++j) v[j] = live ? __ldcs(xt + (long)(k0 + j * kst) * ss) : (T)0;
+            for (int j = 0; j < LB; ++j) v[j] = live ? __ldcs(xt + (long)(k0 + (kb + j) * kst) * ss) : (T)0;
 #pragma unroll
-        for (int j = 0; j < LB; ++j) {
-            acc = fma(v[j], v[j], acc);
-            zx[(k0 + j * kst) * XS + tt] = v[j];
+            for (int j = 0; j < LB; ++j) {
+                acc = fma(v[j], v[j], acc);
+                zx[(k0 + (kb + j) * kst) * XS + tt] = v[j];
+            }
         }
     }
     __syncthreads();
     const int seq = threadIdx.x >> 4, j = threadIdx.x & 15;
     {
-        // 16-point DFTs over n1 of x[16 n1 + j] (sequence seq: tubes seq and seq + 16 as re, im)
-        cplx<T> v[16];
+        // 16-point DFTs over t1 of x[Q t1 + t2], t2 = j + 16 u (sequence seq: tubes seq and seq + 16 as re, im)
+        cplx<T> v[Q / 16][16];
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[n1] = mk<T>(zx[(16 * n1 + j) * XS + seq], zx[(16 * n1 + j) * XS + seq + 16]);
-        dft16f<T>(v);
+        for (int u = 0; u < Q / 16; ++u)
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) zt[(seq * 16 + k1) * TS + j] = cmul(v[k1], tw[(j * k1) & (n - 1)]);
+            for (int t1 = 0; t1 < 16; ++t1) {
+                const int t = Q * t1 + j + 16 * u;
+                v[u][t1] = mk<T>(zx[t * XS + seq], zx[t * XS + seq + 16]);
+            }
+        __syncthreads();  // the real input is read: the buffer takes the partial DFTs
+#pragma unroll
+        for (int u = 0; u < Q / 16; ++u) {
+            const int t2 = j + 16 * u;
+            dft16f<T>(v[u]);
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) zt[(seq * 16 + k1) * TS + t2] = cmul(v[u][k1], tw[(t2 * k1) & (n - 1)]);
+        }
     }
     __syncthreads();
     {
-        // 16-point DFTs over n2 for k1 = j: X[j + 16 k2]
-        cplx<T> v[16];
+        // Q-point DFT over t2 for k1 = j: X[j + 16 k2]
+        cplx<T> v[Q];
 #pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2) v[n2] = zt[(seq * 16 + j) * TS + n2];
-        dft16f<T>(v);
+        for (int t2 = 0; t2 < Q; ++t2) v[t2] = zt[(seq * 16 + j) * TS + t2];
+        __syncthreads();  // the partial DFTs are read: the buffer takes the spectrum
+        DftQ<T, Q>::run(v);
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) z[(j + 16 * k2) * TS + seq] = v[k2];
+        for (int k2 = 0; k2 < Q; ++k2) z[(j + 16 * k2) * ZS + seq] = v[k2];
     }
     __syncthreads();
     const int h = n / 2 + 1;
@@ -229,8 +293,8 @@ k_rdft_256(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int co
         const long t = t0 + tq;
         if (t >= tubes) continue;
         const int p = tq & 15;
-        const cplx<T> zs = z[s * TS + p];
-        const cplx<T> zc = cconj(z[((n - s) & (n - 1)) * TS + p]);
+        const cplx<T> zs = z[s * ZS + p];
+        const cplx<T> zc = cconj(z[((n - s) & (n - 1)) * ZS + p]);
         cplx<T> o;
         if (tq < 16) o = mk<T>((zs.x + zc.x) * (T)0.5, (zs.y + zc.y) * (T)0.5);
         else o = mk<T>((zs.y - zc.y) * (T)0.5, -(zs.x - zc.x) * (T)0.5);
@@ -309,12 +373,6 @@ k_irdft_256(const cplx<T>* __restrict__ Xh, T* __restrict__ X, long tubes, int c
             xt[(long)k * ss] = (tt < 16 ? v.x : -v.y) * inv;
         }
     }
-}
-
-static size_t rdft256_smem(size_t elem) {
-    const size_t c = 2 * elem;
-    const size_t zx = std::max((size_t)256 * (DFT_TILE + 1) * elem, (size_t)256 * 17 * c);
-    return (size_t)256 * c + (size_t)16 * 16 * 17 * c + zx;
 }
 
 template <typename T>
@@ -469,11 +527,12 @@ tp_status rdft(const T* X, void* Xh, int n, int rows, int cols, long ld, long ss
     if (tubes == 0) return TP_OK;
     const unsigned grid = (unsigned)((tubes + DFT_TILE - 1) / DFT_TILE);
     const size_t smem = rdft_smem(n, sizeof(T));
-    if (n == 256) {
-        const size_t sm256 = rdft256_smem(sizeof(T));
-        if (prep(k_rdft_256<T>, sm256) != TP_OK) return TP_ERR_CUDA;
+    if (n == 256 || n == 512) {
+        const size_t sm = n == 256 ? Rdft16Q<16>::smem<T>() : Rdft16Q<32>::smem<T>();
+        auto kern = n == 256 ? k_rdft_16q<T, 16> : k_rdft_16q<T, 32>;
+        if (prep(kern, sm) != TP_OK) return TP_ERR_CUDA;
         prof_begin(TP_KC_DFT, st);
-        k_rdft_256<T><<<grid, DFT_THREADS, sm256, st>>>(X, (cplx<T>*)Xh, tubes, cols, ld, ss, sumsq, skip);
+        kern<<<grid, DFT_THREADS, sm, st>>>(X, (cplx<T>*)Xh, tubes, cols, ld, ss, sumsq, skip);
     } else if (is_pow2(n)) {
         if (prep(k_rdft_pow2<T>, smem) != TP_OK) return TP_ERR_CUDA;
         prof_begin(TP_KC_DFT, st);

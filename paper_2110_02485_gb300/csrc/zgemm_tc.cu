@@ -27,13 +27,15 @@
 //        (3-D tensor maps: columns, rows, slices; zero fill past the edges);
 //   warps 0-7: the hi/lo split.  For op = N the TMA writes A with the 128-byte
 //        swizzle, which is the tensor core's K-major SWIZZLE_128B layout, so
-//        the split is element-wise in place (hi) plus a lo copy; for op = C the
+//        hi is the tile in place and lo is written to tensor memory (one lane
+//        per row; the lo*hi MMA reads its A operand from there); for op = C the
 //        raw tile (rows i) is transposed into the no-swizzle K-major layout
 //        (8 rows x 16 bytes per core matrix).  The real right-hand side is
 //        built from the raw B rows;
 //   warp 9 (one thread): the MMAs of a stage, committed to the stage's
 //        "empty" barrier, which hands the buffers back to the TMA thread.
-// The accumulator (128 lanes x 4 b' float32 columns) lives in tensor memory;
+// The accumulator (128 lanes x 4 b' float32 columns) lives in tensor memory,
+// followed by the lo tiles of the stages (op = N, 3xTF32);
 // warps 0-7 read it back with tcgen05.ld once the last commit lands.
 // op = R (conj(A) B, A row-major) uses the op = N kernel with the signs of
 // the right-hand side flipped; the RT-tSVD forms A-hat^H Y this way from a
@@ -128,6 +130,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+// A from tensor memory (columns of one lane per row), B from shared memory.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+        :
+        : "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                  : "memory");
@@ -201,6 +212,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive 32-bit columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Byte offset of element (row, k) in a K-major no-swizzle tile whose core
 // matrices advance by `lbo` along K and by 128 bytes along the rows.
 __device__ __forceinline__ uint32_t kmaj_off(int row, int k, uint32_t lbo) {
@@ -217,43 +239,62 @@ __device__ __forceinline__ float pick4(const float4& v, int e) {
 }
 
 // Stage buffers: raw A (TMA), hi A (op C only; op N uses the raw tile), lo A
-// (3xTF32 only), raw B rows (TMA), and the real right-hand side B_op.  NP = 3
-// (hi*hi + hi*lo + lo*hi, float32 accuracy), 1 (hi*hi, the TF32 precision
-// form) or 0 (bfloat16 A and B_op, the BF16 form; op N only).  KT real
-// reduction entries per stage: 32 in tf32, 64 in bfloat16 (the same 128-byte
-// rows).
+// (3xTF32 with op C only), raw B rows (TMA), and the real right-hand side
+// B_op.  NP = 3 (hi*hi + hi*lo + lo*hi, float32 accuracy), 1 (hi*hi, the TF32
+// precision form) or 0 (bfloat16 A and B_op, the BF16 form; op N only).  KT
+// real reduction entries per stage: 32 in tf32, 64 in bfloat16 (the same
+// 128-byte rows).  With op N and NP = 3 (LO_TM) the lo tile of A lives in
+// tensor memory instead (32 columns per stage after the accumulator's, one
+// lane per row), which is what the MMA's A operand may also be read from:
+// a stage then takes 16 KB less shared memory, so two CTAs per SM keep four
+// tiles each in flight.
 template <int OPA, int NCP, int NP> struct TcCfg {
     static constexpr int KT = NP == 0 ? 2 * TC_KT : TC_KT;
     static constexpr int NB = (NP == 3 ? 4 : 2) * NCP;  // B_op rows: (re, im) x (hi[, lo])
+    static constexpr bool LO_TM = NP == 3 && OPA == OP_N;
     static constexpr uint32_t LBO_B = (NB / 8) * 128;
     static constexpr int KB = OPA == OP_N ? KT / 2 : KT;  // B rows per stage
     static constexpr int A_RAW = 0;
     static constexpr int A_HI = OPA == OP_N ? 0 : TC_A_BYTES;
-    static constexpr int A_LO = A_HI + TC_A_BYTES;  // used when NP == 3
-    static constexpr int B_RAW = (NP == 3 ? A_LO : A_HI) + TC_A_BYTES;
+    static constexpr int A_LO = A_HI + TC_A_BYTES;  // used when NP == 3 and not LO_TM
+    static constexpr int B_RAW = (NP == 3 && !LO_TM ? A_LO : A_HI) + TC_A_BYTES;
     static constexpr int B_RAW_BYTES = KB * NCP * 8;
     static constexpr int B_OP = B_RAW + B_RAW_BYTES;
-    static constexpr int STAGE = B_OP + NB * KT * (NP == 0 ? 2 : 4);  // a multiple of 1024
+    static constexpr int STAGE = B_OP + NB * KT * (NP == 0 ? 2 : 4);
+    static_assert(STAGE % 1024 == 0, "stages start on the 128-byte swizzle's 1024-byte period");
+    // tensor-memory columns: the accumulator (NB, at least 32), then the lo tiles
+    static constexpr int ACC = NB < 32 ? 32 : NB;
+    static constexpr int tm_need(int ns) { return ACC + (LO_TM ? 32 * ns : 0); }
     // two CTAs per SM when two stages fit in half the shared memory (the TMA
     // stream of one CTA does not fill an SM's share of L2 bandwidth), with as
-    // many stages as fit there (up to four: each CTA's tiles are latency-bound,
-    // about 1,900 cycles per 16 KB tile with two in flight), else one CTA with
-    // up to four stages
-    static constexpr int NS2 = (TC_SMEM_LIMIT / 2 - 1024) / STAGE;
-    static constexpr int NS = NS2 >= 2 ? (NS2 > 4 ? 4 : NS2)
-                                       : ((TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE);
-    static constexpr size_t SMEM = (size_t)NS * STAGE + 1024;  // + alignment slack
+    // many stages as fit there (up to four: each CTA's tiles are latency-bound)
+    // and in half the tensor memory, else one CTA with up to four stages
+    static constexpr int NS2S = (TC_SMEM_LIMIT / 2 - 1024) / STAGE;
+    static constexpr int NS2 = NS2S >= 2 && tm_need(NS2S > 4 ? 4 : NS2S) > 256 ? (256 - ACC) / 32 : NS2S;
+    static constexpr int NS1 = (TC_SMEM_LIMIT - 1024) / STAGE >= 4 ? 4 : (TC_SMEM_LIMIT - 1024) / STAGE;
+    static constexpr int NS = NS2 >= 2 ? (NS2 > 4 ? 4 : NS2) : NS1;
     // the most stages one CTA can hold (the autotuner's range is 2 .. NS_FIT)
-    static constexpr int NS_FIT = (TC_SMEM_LIMIT - 1024) / STAGE > TC_NS_CAP ? TC_NS_CAP
+    static constexpr int NSF_SM = (TC_SMEM_LIMIT - 1024) / STAGE > TC_NS_CAP ? TC_NS_CAP
                                                                             : (TC_SMEM_LIMIT - 1024) / STAGE;
-    static size_t smem(int ns) { return (size_t)ns * STAGE + 1024; }
+    static constexpr int NS_FIT = tm_need(NSF_SM) > 512 ? (512 - ACC) / 32 : NSF_SM;
+    // a stage count whose tensor memory exceeds half of it reserves more than
+    // half the shared memory, so that a second CTA never waits in tcgen05.alloc
+    static size_t smem(int ns) {
+        const size_t s = (size_t)ns * STAGE + 1024;  // + alignment slack
+        return tm_need(ns) > 256 && s <= (size_t)TC_SMEM_LIMIT / 2 ? (size_t)TC_SMEM_LIMIT / 2 + 1024 : s;
+    }
     static constexpr uint32_t TX = TC_A_BYTES + B_RAW_BYTES;   // bytes the two TMA boxes deliver
-    static constexpr uint32_t NCOLS = NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
+    static uint32_t __host__ __device__ ncols(int ns) {       // power of two, at least 32
+        uint32_t c = 32;
+        while ((int)c < tm_need(ns)) c <<= 1;
+        return c;
+    }
 };
 
 // Split one stage (warps 0-7).  CONJ (op = R): right-hand side signs of conj(A) B.
+// LO_TM: tlo is the tensor-memory address (lane 0) of this stage's lo tile.
 template <int OPA, bool CONJ, int NCP, int NP>
-__device__ __forceinline__ void split_stage(unsigned char* st) {
+__device__ __forceinline__ void split_stage(unsigned char* st, uint32_t tlo) {
     typedef TcCfg<OPA, NCP, NP> G;
     const int t = threadIdx.x;
     const float2* rb = (const float2*)(st + G::B_RAW);
@@ -274,14 +315,23 @@ __device__ __forceinline__ void split_stage(unsigned char* st) {
     }
     if (OPA == OP_N) {
         if (NP == 3) {
-            // element-wise on the swizzled tile: hi is the tile itself, lo at the same offset
-            const float4* a = (const float4*)(st + G::A_RAW);
-            float4* alo = (float4*)(st + G::A_LO);
-#pragma unroll 4
-            for (int i = t; i < TC_A_BYTES / 16; i += TC_CONV_THREADS) {
-                const float4 v = a[i];
-                alo[i] = make_float4(tf32_rest(v.x), tf32_rest(v.y), tf32_rest(v.z), tf32_rest(v.w));
+            // hi is the swizzled tile itself; lo goes to tensor memory, one lane per
+            // row: warp w takes rows 32 (w % 4) .. (its lanes) and reduction entries
+            // 16 (w / 4) .. + 15, i.e. four 16-byte chunks of its row, chunk c of
+            // row r sitting at chunk c ^ (r % 8) of the 128-byte line
+            static_assert(TC_CONV_WARPS == 8 && TC_KT == 32, "two warps per lane quarter, 16 entries each");
+            const int w = t >> 5, q = w & 3, hh = w >> 2, r = 32 * q + (t & 31);
+            const unsigned char* row = st + G::A_RAW + (r >> 3) * 1024 + (r & 7) * 128;
+            uint32_t v[16];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 x = *(const float4*)(row + (((4 * hh + j) ^ (r & 7)) << 4));
+                v[4 * j] = __float_as_uint(tf32_rest(x.x));
+                v[4 * j + 1] = __float_as_uint(tf32_rest(x.y));
+                v[4 * j + 2] = __float_as_uint(tf32_rest(x.z));
+                v[4 * j + 3] = __float_as_uint(tf32_rest(x.w));
             }
+            tmem_st16(tlo + ((uint32_t)(32 * q) << 16) + 16u * hh, v);
         }
         // A B:       re row (Br, -Bi), im row (Bi,  Br)
         // conj(A) B: re row (Br,  Bi), im row (Bi, -Br)
@@ -374,7 +424,7 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
-                     "r"(G::NCOLS)
+                     "r"(G::ncols(ns))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -427,7 +477,10 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                         continue;
                     }
                     mma_tf32(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);  // hi*hi [| hi*lo]
-                    if (NP == 3) mma_tf32(tmem, dal, db, id_half, 1u);              // += lo*hi
+                    if (G::LO_TM)                                                    // += lo*hi
+                        mma_tf32_ta(tmem, tmem + (uint32_t)(G::ACC + 32 * st + 8 * ks), db, id_half, 1u);
+                    else if (NP == 3)
+                        mma_tf32(tmem, dal, db, id_half, 1u);
                 }
                 mma_commit(smem_u32(&empty[st]));
                 issued = kt + 1;
@@ -443,8 +496,12 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         for (int kt = 0; kt < nkt; ++kt) {
             const int st = kt % ns;
             if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / ns) & 1), abort, spin)) break;
-            split_stage<OPA, CONJ, NCP, NP>(sgen + st * G::STAGE);
+            split_stage<OPA, CONJ, NCP, NP>(sgen + st * G::STAGE, tmem + (uint32_t)(G::ACC + 32 * st));
             fence_async_smem();  // generic-proxy writes -> tensor-core reads
+            if (G::LO_TM) {      // the lo tile's tensor-memory stores complete before the MMA thread reads it
+                tmem_st_wait();
+                tc_fence_before();
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&conv[st]));
         }
@@ -480,7 +537,8 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     if (tid == 0 && abort_s && err) atomicExch(err, (int)TP_ERR_TIMEOUT);
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::NCOLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::ncols(ns))
+                     : "memory");
     }
 }
 
