@@ -213,60 +213,75 @@ template <typename T> struct DftQ<T, 32> {
 // spectrum [k][seq]) share one buffer, each read into registers behind a
 // barrier before the next is written, so that several CTAs fit on an SM.
 template <int Q> struct Rdft16Q {
-    static constexpr int n = 16 * Q, XS = DFT_TILE + 1, TS = Q + 1, ZS = 17;
+    static constexpr int n = 16 * Q, TS = Q + 1, ZS = 17;
     template <typename T> static constexpr size_t region() {
-        const size_t a = (size_t)n * XS * sizeof(T), b = (size_t)256 * TS * 2 * sizeof(T),
-                     c = (size_t)n * ZS * 2 * sizeof(T);
-        return a > b ? (a > c ? a : c) : (b > c ? b : c);
+        const size_t b = (size_t)256 * TS * 2 * sizeof(T), c = (size_t)n * ZS * 2 * sizeof(T);
+        return b > c ? b : c;
     }
     template <typename T> static constexpr size_t smem() { return (size_t)n * 2 * sizeof(T) + region<T>(); }
 };
 
 template <typename T, int Q>
-__global__ void __launch_bounds__(DFT_THREADS)
+__global__ void __launch_bounds__(DFT_THREADS, sizeof(T) == 4 ? (Q == 16 ? 5 : 3) : 1)
 k_rdft_16q(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int cols, long ld, long ss, double* sumsq,
            const int* skip) {
     if (skip && *skip) return;
     typedef Rdft16Q<Q> R;
-    constexpr int n = R::n, XS = R::XS, TS = R::TS, ZS = R::ZS;
+    constexpr int n = R::n, TS = R::TS, ZS = R::ZS, h = n / 2 + 1;
+    constexpr int NT = DFT_THREADS;  // compile-time strides: the index arithmetic folds into constants
+    static_assert(NT == 256, "16 packed sequences x 16 threads");
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* tw = (cplx<T>*)smraw;                 // n roots exp(-2 pi i m / n)
-    T* zx = (T*)(tw + n);                          // phase 1: real input [t][tube], row stride 33
-    cplx<T>* zt = (cplx<T>*)zx;                    // phase 2: [seq][k1][t2], row stride Q + 1
-    cplx<T>* z = (cplx<T>*)zx;                     // phase 3: packed spectrum [k][seq], row stride 17
+    cplx<T>* zp = tw + n;                          // phase 1: packed input [t][seq], row stride 17
+    cplx<T>* zt = zp;                              // phase 2: [seq][k1][t2], row stride Q + 1
+    cplx<T>* z = zp;                               // phase 3: packed spectrum [k][seq], row stride 17
+    const int tid = threadIdx.x;
     const long t0 = (long)blockIdx.x * DFT_TILE;
-    fill_roots<T>(tw, n, n, (T)-1);
-    const int tt = threadIdx.x & (DFT_TILE - 1), k0 = threadIdx.x / DFT_TILE, kst = blockDim.x / DFT_TILE;
-    const bool live = t0 + tt < tubes;
-    const T* xt = X + (live ? tube_off(t0 + tt, cols, ld) : 0);
+    {
+        const T step = (T)2 / (T)n;  // exact for a power of two: the argument 2 m / n without a division
+        for (int m = tid; m < n; m += NT) {
+            T sn, cs;
+            sincospi_t<T>((T)m * step, &sn, &cs);
+            tw[m] = mk<T>(cs, -sn);
+        }
+    }
+    // phase 1: thread (row group kr, pair p) loads tubes p and p + 16 (the real and imaginary parts of packed
+    // sequence p) at rows kr, kr + 16, ...; a half-warp reads 16 consecutive tubes of one row
+    const int p = tid & 15, kr = tid >> 4;
     T acc = 0;
     {
-        constexpr int LB = n / (DFT_THREADS / DFT_TILE) > 32 ? 32 : n / (DFT_THREADS / DFT_TILE);
+        const bool la = t0 + p < tubes, lb = t0 + p + 16 < tubes;
+        const T* xa = X + (la ? tube_off(t0 + p, cols, ld) : 0);
+        const T* xb = X + (lb ? tube_off(t0 + p + 16, cols, ld) : 0);
+        constexpr int RPT = n / 16;                  // rows per thread
+        constexpr int LB = RPT > 16 ? 16 : RPT;      // row pairs in flight per thread
 #pragma unroll 1
-        for (int kb = 0; kb < n / (DFT_THREADS / DFT_TILE); kb += LB) {
-            T v[LB];  // LB loads in flight per thread
+        for (int rb = 0; rb < RPT; rb += LB) {
+            T va[LB], vb[LB];
 #pragma unroll
-            for (int j = 0; j < LB; ++j) v[j] = live ? __ldcs(xt + (long)(k0 + (kb + j) * kst) * ss) : (T)0;
+            for (int i = 0; i < LB; ++i) {
+                const long off = (long)(kr + 16 * (rb + i)) * ss;
+                va[i] = la ? __ldcs(xa + off) : (T)0;
+                vb[i] = lb ? __ldcs(xb + off) : (T)0;
+            }
 #pragma unroll
-            for (int j = 0; j < LB; ++j) {
-                acc = fma(v[j], v[j], acc);
-                zx[(k0 + (kb + j) * kst) * XS + tt] = v[j];
+            for (int i = 0; i < LB; ++i) {
+                acc = fma(va[i], va[i], acc);
+                acc = fma(vb[i], vb[i], acc);
+                zp[(kr + 16 * (rb + i)) * ZS + p] = mk<T>(va[i], vb[i]);
             }
         }
     }
     __syncthreads();
-    const int seq = threadIdx.x >> 4, j = threadIdx.x & 15;
+    const int seq = tid >> 4, j = tid & 15;
     {
-        // 16-point DFTs over t1 of x[Q t1 + t2], t2 = j + 16 u (sequence seq: tubes seq and seq + 16 as re, im)
+        // 16-point DFTs over t1 of x[Q t1 + t2], t2 = j + 16 u
         cplx<T> v[Q / 16][16];
 #pragma unroll
         for (int u = 0; u < Q / 16; ++u)
 #pragma unroll
-            for (int t1 = 0; t1 < 16; ++t1) {
-                const int t = Q * t1 + j + 16 * u;
-                v[u][t1] = mk<T>(zx[t * XS + seq], zx[t * XS + seq + 16]);
-            }
-        __syncthreads();  // the real input is read: the buffer takes the partial DFTs
+            for (int t1 = 0; t1 < 16; ++t1) v[u][t1] = zp[(Q * t1 + j + 16 * u) * ZS + seq];
+        __syncthreads();  // the input is read: the buffer takes the partial DFTs
 #pragma unroll
         for (int u = 0; u < Q / 16; ++u) {
             const int t2 = j + 16 * u;
@@ -287,18 +302,24 @@ k_rdft_16q(const T* __restrict__ X, cplx<T>* __restrict__ Xh, long tubes, int co
         for (int k2 = 0; k2 < Q; ++k2) z[(j + 16 * k2) * ZS + seq] = v[k2];
     }
     __syncthreads();
-    const int h = n / 2 + 1;
-    for (int e = threadIdx.x; e < h * DFT_TILE; e += blockDim.x) {
-        const int s = e >> 5, tq = e & 31;
+    {
+        // separate the two real tubes of each packed sequence: thread (row group, tube tq) writes
+        // slices s = tid / 32 + 8 i of tube tq; tq < 16 takes (Z_s + conj Z_{n-s}) / 2, the others
+        // (Z_s - conj Z_{n-s}) / 2i, branch-free
+        const int tq = tid & 31, q = tq & 15, s0 = tid >> 5;
         const long t = t0 + tq;
-        if (t >= tubes) continue;
-        const int p = tq & 15;
-        const cplx<T> zs = z[s * ZS + p];
-        const cplx<T> zc = cconj(z[((n - s) & (n - 1)) * ZS + p]);
-        cplx<T> o;
-        if (tq < 16) o = mk<T>((zs.x + zc.x) * (T)0.5, (zs.y + zc.y) * (T)0.5);
-        else o = mk<T>((zs.y - zc.y) * (T)0.5, -(zs.x - zc.x) * (T)0.5);
-        Xh[(long)s * tubes + t] = o;
+        const T sg = tq < 16 ? (T)1 : (T)-1;
+        if (t < tubes) {
+            cplx<T>* dst = Xh + t + (long)s0 * tubes;
+            const long dstep = 8 * tubes;
+#pragma unroll 4
+            for (int s = s0; s < h; s += NT / 32, dst += dstep) {
+                const cplx<T> zs = z[s * ZS + q];
+                const cplx<T> zc = z[((n - s) & (n - 1)) * ZS + q];
+                const T ux = fma(sg, zc.x, zs.x), uy = fma(-sg, zc.y, zs.y);  // Z_s +- conj Z_{n-s}
+                *dst = tq < 16 ? mk<T>(ux * (T)0.5, uy * (T)0.5) : mk<T>(uy * (T)0.5, -ux * (T)0.5);
+            }
+        }
     }
     store_partial<T>(acc, sumsq);
 }
