@@ -136,7 +136,8 @@ struct State {
     int status;
     int sweeps;
     int nonfinite;    // 1 when the norms of A or B are not finite
-    int pad[2];
+    unsigned arrived; // CTAs of the current block orthonormalisation that have finished (0 between launches)
+    int pad;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -272,7 +272,8 @@ template <typename T, int BB> constexpr size_t orth_gram_elems() {
 template <typename T, int BB>
 __global__ void __launch_bounds__(OrthThreads<T, BB>::v)
 k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev, cplx<T>* Qout,
-       cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip, int final_pass) {
+       cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip, int final_pass, State* eta,
+       int n_dft, int r_new) {
     typedef cplx<T> V;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -563,6 +564,30 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
             Rs[(long)i * ldr + r_prev + j] = v;
         }
     }
+    if (eta) {
+        // the last CTA to finish takes the eta update of Algorithm 3 for the
+        // block (eta <- eta - ||Bt(block)||_F^2, Parseval-weighted over the
+        // slices, in the fixed order of 256 partial sums), sets r and the stop
+        // flag, and resets the arrival count for the next block
+        __shared__ int last;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) last = atomicAdd(&eta->arrived, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            double a = 0.0;
+            if (tid < 256)
+                for (int s2 = tid; s2 < (int)gridDim.x; s2 += 256) a += parseval_w(s2, n_dft) * __ldcg(&normsq[s2]);
+            a = block_sum(a, red);
+            if (tid == 0) {
+                eta->eta -= a / (double)n_dft;
+                eta->r = r_new;
+                if (eta->eta < eta->eps2) eta->done = 1;
+                eta->arrived = 0;
+            }
+        }
+    }
 }
 
 static size_t orth_smem(int L, int b, int r_prev, size_t c) {
@@ -577,20 +602,21 @@ static size_t orth_smem(int L, int b, int r_prev, size_t c) {
 template <typename T>
 static tp_status orth(int h, cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev,
                       cplx<T>* Qout, cplx<T>* R, long ldr, long sR, int r_rows, double* normsq, const int* skip,
-                      cudaStream_t st) {
+                      cudaStream_t st, State* eta = nullptr, int n_dft = 0, int r_new = 0) {
     const int final_pass = (Qout != nullptr || R != nullptr) ? 1 : 0;
     const size_t smem = orth_smem(L, b, r_prev, sizeof(cplx<T>));
     auto kern = b <= 16 ? k_orth<T, 16> : k_orth<T, 32>;
     const int nt = b <= 16 ? OrthThreads<T, 16>::v : OrthThreads<T, 32>::v;
     if (smem_optin((const void*)kern, smem) != TP_OK) return TP_ERR_CUDA;
     prof_begin(TP_KC_ORTH, st);
-    kern<<<h, nt, smem, st>>>(Y, sY, L, b, Qb, sQ, r_prev, Qout, R, ldr, sR, r_rows, normsq, skip, final_pass);
+    kern<<<h, nt, smem, st>>>(Y, sY, L, b, Qb, sQ, r_prev, Qout, R, ldr, sR, r_rows, normsq, skip, final_pass, eta,
+                              n_dft, r_new);
     return launched(TP_KC_ORTH, st);
 }
 
 // ---------------------------------------------------------------------------
-// Scalars: ||A||^2 from the DFT partials, eps^2, and the eta update of
-// Algorithm 3 (eta <- eta - ||Bt(block)||_F^2, Parseval-weighted over slices).
+// Scalars: ||A||^2 from the DFT partials and eps^2 (the eta update of
+// Algorithm 3 is taken by the last CTA of each block's k_orth launch).
 // ---------------------------------------------------------------------------
 __device__ double fixed_order_sum(const double* v, int count, double* red) {
     double a = 0.0;
@@ -615,20 +641,8 @@ __global__ void k_rt_init(State* st, const double* partsA, int nA, const double*
         st->status = TP_OK;
         st->sweeps = 0;
         st->sigma_max = 0.0;
+        st->arrived = 0;
         st->nonfinite = (isfinite(a2) && isfinite(b2)) ? 0 : 1;
-    }
-}
-
-__global__ void k_eta_update(State* st, const double* normsq, int h, int n, int r_new) {
-    if (st->done) return;
-    __shared__ double red[32];
-    double a = 0.0;
-    for (int s = threadIdx.x; s < h; s += blockDim.x) a += parseval_w(s, n) * normsq[s];
-    a = block_sum(a, red);
-    if (threadIdx.x == 0) {
-        st->eta -= a / (double)n;
-        st->r = r_new;
-        if (st->eta < st->eps2) st->done = 1;
     }
 }
 
@@ -1495,11 +1509,9 @@ static tp_status rt_solve_impl(const T* A, const T* B, const T* Om, int l, int m
         // Bt(block)^H = A^H Y; its QR against the earlier columns extends QG and R
         TRY(cgemm<T>(h, m, bb, l, 0, 0, 0, 1, 0, AH, ldah, lm, op_h, w.Y, bb, (long)l * bb, OP_N, 0, 0, w.BHb, bb,
                      (long)m * bb, done, st, &w.st->status, 3));  // the re-projection stays float32-accurate
+        // its last CTA also takes the block's eta update
         TRY(orth<T>(h, w.BHb, (long)m * bb, m, bb, w.QG, (long)r_max * m, r0, w.QG, w.R, r_max,
-                    (long)r_max * r_max, r_max, w.normsq, done, st));
-        prof_begin(TP_KC_MISC, st);
-        k_eta_update<<<1, 256, 0, st>>>(w.st, w.normsq, h, n, r0 + bb);
-        TRY(launched(TP_KC_MISC, st));
+                    (long)r_max * r_max, r_max, w.normsq, done, st, w.st, n, r0 + bb));
     }
     const int* dr = &w.st->r;
     // d = Q^H B (r_max x p per slice)
