@@ -63,6 +63,38 @@ NCU_TRAFFIC = {
 }
 
 
+_SIDE_STREAMS = []
+
+
+def concurrent(fns, torch):
+    """Call fns (independent solves that only enqueue work) on one stream each,
+    forked from the current stream and joined back to it at the end; their
+    results in order."""
+    main = torch.cuda.current_stream()
+    while len(_SIDE_STREAMS) < len(fns):
+        _SIDE_STREAMS.append(torch.cuda.Stream())
+    out = []
+    for fn, st in zip(fns, _SIDE_STREAMS):
+        st.wait_stream(main)
+        with torch.cuda.stream(st):
+            out.append(fn())
+    for st in _SIDE_STREAMS[:len(fns)]:
+        main.wait_stream(st)
+    return out
+
+
+def three_solves(tprod, cfg, A, B, Om, delta, torch, serial):
+    """One step: an RT-tSVD, a tGKB and a Tikhonov-tGKB solve of the same
+    problem.  They are independent, so unless serial they run on three
+    streams (joined at the end of the step)."""
+    fns = [lambda: tprod.rtsvd_solve(A, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                                     eps_rel=cfg.eps_rel, sync=False)[:2],
+           lambda: tprod.tgkb_solve(A, B, delta, cfg.tau, cfg.k_max, sync=False)[:2],
+           lambda: tprod.tgkt_solve(A, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False)]
+    res = [f() for f in fns] if serial else concurrent(fns, torch)
+    return tuple(r[0] for r in res), tuple(r[1] for r in res)
+
+
 def ncu_traffic(cls, config="n256"):
     import hashlib
     rec = NCU_TRAFFIC.get(cls)
@@ -100,6 +132,7 @@ def args_():
     p.add_argument("--no-hat", action="store_true", help="skip the solves from a precomputed A-hat")
     p.add_argument("--no-ttsvd", action="store_true", help="skip the full-tSVD comparison method")
     p.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
+    p.add_argument("--serial", action="store_true", help="the three solves of a step on one stream")
     return p.parse_args()
 
 
@@ -296,12 +329,8 @@ def run_ours(a, rank, world, local):
     A, B, Om = dev(P["A"]), dev(P["B"]), dev(P["Omega"])
     delta = P["delta"]
 
-    def step(A, B, Om):
-        X1, i1, _ = tprod.rtsvd_solve(A, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
-                                      eps_rel=cfg.eps_rel, sync=False)
-        X2, i2, _ = tprod.tgkb_solve(A, B, delta, cfg.tau, cfg.k_max, sync=False)
-        X3, i3 = tprod.tgkt_solve(A, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False)
-        return (X1, X2, X3), (i1, i2, i3)
+    def step(A, B, Om, serial=a.serial):
+        return three_solves(tprod, cfg, A, B, Om, delta, torch, serial)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     # stage counts of the tensor-core products for this problem's shapes (outside every timed region; the
@@ -315,13 +344,13 @@ def run_ours(a, rank, world, local):
         flush.zero_()
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        step(A, B, Om)
+        step(A, B, Om, serial=True)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         return
     # one instrumented step: device time per kernel class, and the solve records
     tprod.timing_enable(tprod.KERNEL_CLASSES)
-    _, infos_dev = step(A, B, Om)
+    _, infos_dev = step(A, B, Om, serial=True)
     per_class = tprod.timing_read()
     tprod.timing_enable([])
     infos = [tprod._info_dict(x) for x in infos_dev]
@@ -331,12 +360,14 @@ def run_ours(a, rank, world, local):
     # events.  By default the step is captured once as a CUDA graph and
     # replayed.  Every kernel class is timed by CUDA events around its
     # launches in the last timed step only (a second capture of the step with
-    # those events inside), so that the events do not slow the other steps.
+    # those events inside, its three solves on one stream so that each
+    # kernel's time is its own), so that the events do not slow the other
+    # steps.
     graph = timed_graph = None
     if not a.no_graph:
         graph = tprod.Captured(lambda: step(A, B, Om), warmup=0)
         tprod.timing_enable(tprod.KERNEL_CLASSES)
-        timed_graph = tprod.Captured(lambda: step(A, B, Om), warmup=0)
+        timed_graph = tprod.Captured(lambda: step(A, B, Om, serial=True), warmup=0)
         tprod.timing_enable([])
 
     def run_step(last):
@@ -345,7 +376,7 @@ def run_ours(a, rank, world, local):
         else:
             if last:
                 tprod.timing_enable(tprod.KERNEL_CLASSES)
-            step(A, B, Om)
+            step(A, B, Om, serial=last or a.serial)
 
     launches0 = tprod.kernel_launches()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -487,6 +518,9 @@ def run_ours(a, rank, world, local):
                       "N": cfg.N, "solves_per_step": SOLVES_PER_STEP, "l2": "flushed between steps (512 MB write)",
                       "launch": "plain launches" if graph is None else
                       f"CUDA graph of the step ({graph.launches} kernels) captured once, replayed per step",
+                      "concurrency": "one stream" if a.serial else
+                      "the three independent solves of a step on three streams, joined at its end; the last timed "
+                      "step on one stream with CUDA events around every launch (per-class times)",
                       "parallelism": f"replicas x{world}"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "roofline_by_class": by_class, "clocks": clk,
            "precision_form": prec_form, "batched_form": batched, "uneven_form": uneven,
@@ -576,12 +610,8 @@ def full_size_form(a, name, flush, tprod, torch, steps=10):
     A, B, Om = (torch.from_numpy(P[k]).cuda() for k in ("A", "B", "Omega"))
     delta = P["delta"]
 
-    def step():
-        X1, i1, _ = tprod.rtsvd_solve(A, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
-                                      eps_rel=cfg.eps_rel, sync=False)
-        X2, i2, _ = tprod.tgkb_solve(A, B, delta, cfg.tau, cfg.k_max, sync=False)
-        X3, i3 = tprod.tgkt_solve(A, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False)
-        return (X1, X2, X3), (i1, i2, i3)
+    def step(serial=a.serial):
+        return three_solves(tprod, cfg, A, B, Om, delta, torch, serial)
 
     if not a.no_autotune:
         tprod.rtsvd_autotune(cfg.N, cfg.N, cfg.N, 1, cfg.block, cfg.r_max, "fp32")
@@ -589,7 +619,7 @@ def full_size_form(a, name, flush, tprod, torch, steps=10):
         step()
     torch.cuda.synchronize()
     tprod.timing_enable(tprod.KERNEL_CLASSES)
-    Xs, infos = step()
+    Xs, infos = step(serial=True)
     per_class = tprod.timing_read()
     tprod.timing_enable([])
     infos = [tprod._info_dict(x) for x in infos]
@@ -639,11 +669,13 @@ def hat_form(a, cfg, P, A, B, Om, flush, tprod, torch, steps=20):
     delta = P["delta"]
 
     def step():
-        X1, i1, _ = tprod.rtsvd_solve(None, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
-                                      eps_rel=cfg.eps_rel, sync=False, Ahat=Ah, n=n)
-        X2, i2, _ = tprod.tgkb_solve(None, B, delta, cfg.tau, cfg.k_max, sync=False, Ahat=Ah, n=n)
-        X3, i3 = tprod.tgkt_solve(None, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False, Ahat=Ah, n=n)
-        return (X1, X2, X3), (i1, i2, i3)
+        fns = [lambda: tprod.rtsvd_solve(None, B, Om, delta, cfg.tau, cfg.p_over, cfg.block, cfg.q_power, cfg.r_max,
+                                         eps_rel=cfg.eps_rel, sync=False, Ahat=Ah, n=n)[:2],
+               lambda: tprod.tgkb_solve(None, B, delta, cfg.tau, cfg.k_max, sync=False, Ahat=Ah, n=n)[:2],
+               lambda: tprod.tgkt_solve(None, B, delta, cfg.tau, cfg.k_max, cfg.mu_lo, cfg.mu_hi, sync=False,
+                                        Ahat=Ah, n=n)]
+        res = [f() for f in fns] if a.serial else concurrent(fns, torch)
+        return tuple(r[0] for r in res), tuple(r[1] for r in res)
 
     for _ in range(3):
         step()
