@@ -774,16 +774,31 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 // one per round (no integer division), and the per-round "any rotation" flag
 // rides on the round's barrier.
 template <int EPL, bool V2, int GL = 8>
-__device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol) {
+__device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol, float* cn) {
     __shared__ int max_off2;  // bit pattern of the largest (|g|^2 / (a b)) of a sweep
     const int tid = threadIdx.x, lane = tid & 31, hl = tid & (GL - 1), slot = tid / GL, nslots = blockDim.x / GL;
     const int rr = r + (r & 1), npair = rr / 2;
     const float tol2 = tol * tol;
     // element e of this lane: index hl + GL e, or with pairs (V2) 2 (hl + GL (e / 2)) + e % 2
     auto idx = [&](int e) { return V2 ? 2 * (hl + GL * (e >> 1)) + (e & 1) : hl + GL * e; };
+    // squared column norms: recomputed from the columns at the start of every
+    // sweep and carried through its rotations (a rotation by t = tan(theta)
+    // with |g| the off-diagonal entry leaves |x|^2 - t |g| and |y|^2 + t |g|),
+    // so a round forms only g = x^H y (cn: r floats of shared memory)
+    const int warp = tid >> 5, nw = blockDim.x >> 5;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (tid == 0) max_off2 = 0;
+        for (int j = warp; j < r; j += nw) {
+            float sq = 0.f;
+            for (int i = lane; i < r; i += 32) {
+                const float2 v = Rs[(size_t)j * r + i];
+                sq = fmaf(v.x, v.x, fmaf(v.y, v.y, sq));
+            }
+            sq = warp_sum(sq);
+            if (lane == 0) cn[j] = sq;
+        }
+        __syncthreads();
         int any = 0;
         float mo2 = 0.f;
         for (int base = 0; base < npair; base += nslots) {
@@ -824,18 +839,12 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
                         }
                     }
                 }
-                float a = 0.f, b = 0.f;
+                const float a = valid ? cn[p] : 0.f, b = valid ? cn[q] : 0.f;
                 float2 g = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int e = 0; e < EPL; ++e) {
-                    a = fmaf(x[e].x, x[e].x, fmaf(x[e].y, x[e].y, a));
-                    b = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, b));
-                    cfmac(g, x[e], y[e]);
-                }
+                for (int e = 0; e < EPL; ++e) cfmac(g, x[e], y[e]);
 #pragma unroll
                 for (int o = GL / 2; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
                     g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
                     g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
                 }
@@ -848,6 +857,11 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
                     const float zeta = (b - a) * 0.5f * rg;
                     const float tt = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
                     const float c = rsqrt_nr(fmaf(tt, tt, 1.f)), sn = c * tt;
+                    if (hl == 0) {
+                        const float tg = tt * (ag2 * rg);  // t |g|
+                        cn[p] = fmaxf(a - tg, 0.f);
+                        cn[q] = fmaxf(b + tg, 0.f);
+                    }
                     float2 xn[EPL], yn[EPL];
 #pragma unroll
                     for (int e = 0; e < EPL; ++e) {
@@ -903,23 +917,23 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
 }
 
 template <typename T> struct JacobiSweeps {
-    static __device__ int run(cplx<T>* Rs, cplx<T>* dp, int np, int r, int max_sweeps, T tol) {
+    static __device__ int run(cplx<T>* Rs, cplx<T>* dp, int np, int r, int max_sweeps, T tol, T*) {
         return jacobi_sweeps_smem<T>(Rs, dp, np, r, max_sweeps, tol);
     }
 };
 template <> struct JacobiSweeps<float> {
-    static __device__ int run(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol) {
+    static __device__ int run(float2* Rs, float2* dp, int np, int r, int max_sweeps, float tol, float* cn) {
         const bool v2 = (r & 1) == 0;  // 16-byte pairs of entries need an even column length
-        if (r <= 32) return v2 ? jacobi_sweeps_reg<4, true>(Rs, dp, np, r, max_sweeps, tol)
-                               : jacobi_sweeps_reg<4, false>(Rs, dp, np, r, max_sweeps, tol);
-        if (r <= 64) return v2 ? jacobi_sweeps_reg<8, true>(Rs, dp, np, r, max_sweeps, tol)
-                               : jacobi_sweeps_reg<8, false>(Rs, dp, np, r, max_sweeps, tol);
-        if (r <= 96) return v2 ? jacobi_sweeps_reg<12, true>(Rs, dp, np, r, max_sweeps, tol)
-                               : jacobi_sweeps_reg<12, false>(Rs, dp, np, r, max_sweeps, tol);
-        if (r <= 128) return v2 ? jacobi_sweeps_reg<16, true>(Rs, dp, np, r, max_sweeps, tol)
-                                : jacobi_sweeps_reg<16, false>(Rs, dp, np, r, max_sweeps, tol);
-        if (r <= 160) return v2 ? jacobi_sweeps_reg<20, true>(Rs, dp, np, r, max_sweeps, tol)
-                                : jacobi_sweeps_reg<20, false>(Rs, dp, np, r, max_sweeps, tol);
+        if (r <= 32) return v2 ? jacobi_sweeps_reg<4, true>(Rs, dp, np, r, max_sweeps, tol, cn)
+                               : jacobi_sweeps_reg<4, false>(Rs, dp, np, r, max_sweeps, tol, cn);
+        if (r <= 64) return v2 ? jacobi_sweeps_reg<8, true>(Rs, dp, np, r, max_sweeps, tol, cn)
+                               : jacobi_sweeps_reg<8, false>(Rs, dp, np, r, max_sweeps, tol, cn);
+        if (r <= 96) return v2 ? jacobi_sweeps_reg<12, true>(Rs, dp, np, r, max_sweeps, tol, cn)
+                               : jacobi_sweeps_reg<12, false>(Rs, dp, np, r, max_sweeps, tol, cn);
+        if (r <= 128) return v2 ? jacobi_sweeps_reg<16, true>(Rs, dp, np, r, max_sweeps, tol, cn)
+                                : jacobi_sweeps_reg<16, false>(Rs, dp, np, r, max_sweeps, tol, cn);
+        if (r <= 160) return v2 ? jacobi_sweeps_reg<20, true>(Rs, dp, np, r, max_sweeps, tol, cn)
+                                : jacobi_sweeps_reg<20, false>(Rs, dp, np, r, max_sweeps, tol, cn);
         return jacobi_sweeps_smem<float>(Rs, dp, np, r, max_sweeps, tol);
     }
 };
@@ -951,7 +965,7 @@ k_jacobi(const cplx<T>* __restrict__ R, long ldr, long sR, const State* st, cons
     for (int i = tid; i < r * np; i += blockDim.x) dp[i] = d[(long)s * sd + i];
     if (tid == 0) tol_s = (T)(4.0 * sqrt((double)r) * Eps<T>::v);
     __syncthreads();
-    const int sweep = JacobiSweeps<T>::run(Rs, dp, np, r, max_sweeps, tol_s);
+    const int sweep = JacobiSweeps<T>::run(Rs, dp, np, r, max_sweeps, tol_s, sg);  // sg: the sweeps' norm scratch
     for (int j = warp; j < r; j += nw) {
         T a = 0;  // column norms in the working precision (float64 only on lane 0)
         for (int i = lane; i < r; i += 32) a += cabs2(Rs[(size_t)j * r + i]);
