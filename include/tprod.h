@@ -365,7 +365,8 @@ tp_status tgkb_triplets(const void* A, const void* B, int l, int m, int n, int k
 typedef struct {
     tp_tgkb_params gkb;
     double mu_lo, mu_hi;   /* search interval, 0 < mu_lo < mu_hi                       */
-    double log_tol;        /* bracket width in log10(mu); <= 0 selects 1e-12           */
+    double log_tol;        /* bracket width in log10(mu); <= 0 selects 1e-12; float32
+                              stops at 1e-7, the spacing of float32 mu^(-1/2)           */
 } tp_tik_params;
 
 size_t tgkb_tikhonov_workspace_bytes(int l, int m, int n, int p, const tp_tik_params* params, int prec);

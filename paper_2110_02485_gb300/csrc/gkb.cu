@@ -933,29 +933,24 @@ struct TikState {
 };
 
 constexpr int TIK_P = 256;
-static_assert(TIK_P <= 256, "fill_lam forms p-th powers from eight squarings");
-
 // lam_p = 10^(-t_p / 2) at the TIK_P points t_p = lo + (hi - lo) p / (TIK_P - 1)
-// of the current bracket: 10^(-lo/2) times the p-th power of
-// 10^(-(hi - lo) / (2 (TIK_P - 1))), the power from the binary digits of p
-// (float64, then rounded to the working precision).  All TIK_P threads call it.
+// of the current bracket, each thread its own point: x = -t_p log2(10) / 2 in
+// float64, split as x = e + f (e an integer, 0 <= f < 1), lam = 2^f 2^e with
+// 2^f in the working precision (a relative error of a few units in its last
+// place, the precision lam is used in).  All TIK_P threads call it.
+template <typename R> __device__ __forceinline__ R exp2_split(double x);
+template <> __device__ __forceinline__ float exp2_split<float>(double x) {
+    const double e = floor(x);
+    return ldexpf(exp2f((float)(x - e)), (int)e);
+}
+template <> __device__ __forceinline__ double exp2_split<double>(double x) { return exp2(x); }
+
 template <typename R>
 __device__ void fill_lam(const TikState* ts, R* lam) {
-    __shared__ double pw[9];
-    if (threadIdx.x == 0) {
-        pw[8] = pow(10.0, -0.5 * ts->lo);
-        double b = pow(10.0, -0.5 * (ts->hi - ts->lo) / (double)(TIK_P - 1));
-        for (int i = 0; i < 8; ++i) {
-            pw[i] = b;
-            b *= b;
-        }
-    }
-    __syncthreads();
     const int p = threadIdx.x;
-    double v = pw[8];
-    for (int i = 0; i < 8; ++i)
-        if ((p >> i) & 1) v *= pw[i];
-    lam[p] = (R)v;
+    const double lo = ts->lo, hi = ts->hi;
+    const double t = p == TIK_P - 1 ? hi : lo + (hi - lo) * ((double)p * (1.0 / (TIK_P - 1)));
+    lam[p] = exp2_split<R>(-1.66096404744368117393 * t);  // -log2(10) / 2
 }
 
 // New bracket from the residuals at the TIK_P points (one CTA of TIK_P
@@ -1620,7 +1615,10 @@ tp_status tik_solve(const T* A, const T* B, int l, int m, int n, int p, const tp
     TRY(gk_run<T>(A, B, l, m, n, &P->gkb, w, info, 0, st, Ahat));
     const int h = n / 2 + 1, k_max = P->gkb.k_max;
     const double lo = log10(P->mu_lo), hi = log10(P->mu_hi);
-    const double tol = P->log_tol > 0.0 ? P->log_tol : 1e-12;
+    // the bracket is narrowed to log_tol, but no further than the spacing of
+    // working-precision lam = mu^(-1/2) (float32: adjacent values differ by
+    // 1e-7 in log10(mu), so narrower brackets hold one lam and change nothing)
+    const double tol = std::max(P->log_tol > 0.0 ? P->log_tol : 1e-12, sizeof(T) == 4 ? 1e-7 : 0.0);
     const double td = P->gkb.tau * P->gkb.delta;
     const T thr = (T)((double)n * td * td);
     prof_begin(TP_KC_TIK, st);
