@@ -455,30 +455,35 @@ k_zgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         if (lane == 0) {
             const uint32_t id_full = NP == 0 ? idesc_bf16(TC_M, G::NB) : idesc_tf32(TC_M, G::NB);
             const uint32_t id_half = idesc_tf32(TC_M, 2 * NCP);
+            // the shared-memory descriptors of stage 0, k-step 0; a stage or k-step
+            // only moves the start address (bits 0-13, in 16-byte units), and every
+            // operand address is below 228 KB, so the offsets add without a carry
+            // out of that field
+            const uint64_t da0 = OPA == OP_N ? sdesc(sbase + G::A_HI, 16, TC_SBO_SW, 2)
+                                             : sdesc(sbase + G::A_HI, TC_LBO_A, TC_SBO);
+            const uint64_t dl0 = OPA == OP_N ? sdesc(sbase + G::A_LO, 16, TC_SBO_SW, 2)
+                                             : sdesc(sbase + G::A_LO, TC_LBO_A, TC_SBO);
+            const uint64_t db0 = sdesc(sbase + G::B_OP, G::LBO_B, TC_SBO);
+            constexpr uint64_t A_KS = OPA == OP_N ? 32 / 16 : 2 * TC_LBO_A / 16;  // per k-step, 16-byte units
+            constexpr uint64_t B_KS = 2 * G::LBO_B / 16;
             int issued = 0;
             for (int kt = 0; kt < nkt; ++kt) {
                 const int st = kt % ns;
                 if (!mbar_wait(smem_u32(&conv[st]), (uint32_t)((kt / ns) & 1), abort, spin)) break;
                 tc_fence_after();
-                const uint32_t buf = sbase + (uint32_t)(st * G::STAGE);
+                const uint64_t so = (uint64_t)(st * (G::STAGE / 16));
+                const uint32_t tlo = tmem + (uint32_t)(G::ACC + 32 * st);
 #pragma unroll
                 for (int ks = 0; ks < TC_KT / 8; ++ks) {
-                    uint64_t dah, dal;
-                    if (OPA == OP_N) {  // 128-byte swizzled K-major: K advances 32 bytes inside the atom
-                        dah = sdesc(buf + G::A_HI + ks * 32, 16, TC_SBO_SW, 2);
-                        dal = sdesc(buf + G::A_LO + ks * 32, 16, TC_SBO_SW, 2);
-                    } else {
-                        dah = sdesc(buf + G::A_HI + ks * 2 * TC_LBO_A, TC_LBO_A, TC_SBO);
-                        dal = sdesc(buf + G::A_LO + ks * 2 * TC_LBO_A, TC_LBO_A, TC_SBO);
-                    }
-                    const uint64_t db = sdesc(buf + G::B_OP + ks * 2 * G::LBO_B, G::LBO_B, TC_SBO);
+                    const uint64_t dah = da0 + so + A_KS * ks, dal = dl0 + so + A_KS * ks;
+                    const uint64_t db = db0 + so + B_KS * ks;
                     if (NP == 0) {  // 16 bfloat16 reduction entries per step (32 bytes, as 8 tf32)
                         mma_bf16(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);
                         continue;
                     }
                     mma_tf32(tmem, dah, db, id_full, (kt > 0 || ks > 0) ? 1u : 0u);  // hi*hi [| hi*lo]
                     if (G::LO_TM)                                                    // += lo*hi
-                        mma_tf32_ta(tmem, tmem + (uint32_t)(G::ACC + 32 * st + 8 * ks), db, id_half, 1u);
+                        mma_tf32_ta(tmem, tlo + (uint32_t)(8 * ks), db, id_half, 1u);
                     else if (NP == 3)
                         mma_tf32(tmem, dal, db, id_half, 1u);
                 }
