@@ -15,9 +15,9 @@
 // keeps hi*hi + hi*lo + lo*hi (the "3xTF32" scheme).  The tensor core reads a
 // float32 operand as tf32 by ignoring its 13 low mantissa bits, so for the
 // large operand (A) with op = N or R hi is the float32 tile itself, left in
-// place, and lo = rna(x - trunc(x)) is the only value written; otherwise
-// hi = rna(x), lo = rna(x - hi).  Relative error of a term: at most about
-// 2^-21, the order of float32 products.  The right-hand
+// place, and lo = x - trunc(x) (read as tf32, i.e. truncated) is the only
+// value written; otherwise hi = rna(x), lo = rna(x - hi).  Relative error of
+// a term: at most about 2^-20, the order of float32 products.  The right-hand
 // side's hi and lo rows are stacked, so one MMA of N = 4 b' forms hi*hi and
 // hi*lo and a second of N = 2 b' adds lo*hi (b' = b rounded up to 8).
 //
@@ -94,9 +94,14 @@ __device__ __forceinline__ void split3(float4 x, float4& hi, float4& lo) {
     split3(x.z, hi.z, lo.z);
     split3(x.w, hi.w, lo.w);
 }
-// The part of x below its tf32 truncation, rounded to tf32.
+// The part of x below its tf32 truncation (exact in float32).  It is left
+// unrounded: the tensor core reads it as tf32 by dropping its low bits, an
+// error of at most 2^-20 |x|, the size of the lo*lo term the split already
+// neglects (an emulation of the product over Gaussian data: 7.7e-9 mean and
+// 3.9e-8 largest error relative to |A||B|, against 6.0e-9 and 3.4e-8 with lo
+// rounded to nearest).
 __device__ __forceinline__ float tf32_rest(float x) {
-    return tf32_rna(x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u));
+    return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
 // Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
