@@ -13,6 +13,7 @@
 // applied to d = Q^H b as they are made.
 #include <algorithm>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -54,77 +55,92 @@ template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
 
 // Cholesky factor of a 16 x 16 Hermitian Gram matrix (upper triangle of G in
-// shared memory) by one warp, the matrix in registers: lane j (and its twin
-// j + 16) holds column j, so with the step loop unrolled every entry has a
-// fixed register.  At step k the pivot comes from lane k (its reciprocal
-// square root Newton-refined), the lanes form row k of R, store it (R is an
-// output) and read back the entries R[k][i] they need for the trailing update
-// from shared memory.  The next pivot is formed ahead of that update: at lane
-// k + 1 the updated diagonal entry needs only that lane's own R[k][k+1], so
-// one shuffle per step lies on the pivot chain.  Rows k >= b and zero pivots
-// give zero rows (a zero column stays zero).  On the first pass (may_shift) a
-// pivot below 100 u of the largest diagonal entry restarts on G + shift I and
-// asks for one more pass (shifted CholQR3).  Writes R (row-major) and 1/diag.
+// shared memory) by the first 160 threads (warps 0-4, named barrier 1): thread
+// e < 136 holds the upper-triangle entry (i, j), i <= j, in registers.  At step
+// k the owner of (k, k) forms the pivot (its reciprocal square root
+// Newton-refined), the owners of row k scale it into R[k][.], and every entry
+// below row k takes its trailing update from that row.  Each entry sees the
+// same operations in the same order as in a column-per-lane Cholesky, with far
+// less code per step (the kernel's instruction footprint is what a cold launch
+// pays for).  Rows k >= b and zero pivots give zero rows (a zero column stays
+// zero).  On the first pass (may_shift) a pivot below 100 u of the largest
+// diagonal entry restarts on G + shift I and asks for one more pass (shifted
+// CholQR3).  Writes R (row-major, lower part zero) and 1/diag.
+__device__ __forceinline__ void bar_chol() { asm volatile("bar.sync 1, 160;" ::: "memory"); }
+
 template <typename T>
-__device__ void chol16_reg(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shift, bool may_shift,
+__device__ void chol16_par(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shift, bool may_shift,
                            int* need_shift, int* passes) {
     typedef cplx<T> V;
-    const int lane = threadIdx.x & 31, j = lane & 15;
-    T dmax = G[j * 16 + j].x;
+    __shared__ T s_id;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x;
+    const bool own = tid < 136;
+    int i = 0, j = 0;
+    if (own) {
+        int rest = tid;
+        while (rest >= 16 - i) {
+            rest -= 16 - i;
+            ++i;
+        }
+        j = i + rest;
+    }
+    T dmax = 0;
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    for (int kk = 0; kk < 16; ++kk) dmax = fmax(dmax, G[kk * 16 + kk].x);
 #pragma unroll 1
     for (int attempt = 0; attempt < 2; ++attempt) {
-        V col[16];  // entries i > j are never read
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            col[i] = i <= j ? G[i * 16 + j] : mk<T>(0, 0);
-            if (attempt == 1 && i == j) col[i].x += shift;
+        V g = mk<T>(0, 0);
+        if (own) {
+            g = G[i * 16 + j];
+            if (attempt == 1 && i == j) g.x += shift;
+            if (i < j) Rk[j * 16 + i] = mk<T>(0, 0);
         }
-        bool bad = false;
-        T d2 = __shfl_sync(0xffffffffu, col[0].x, 0);
-#pragma unroll
+        if (tid == 0) s_bad = 0;
+        bar_chol();
+#pragma unroll 1
         for (int k = 0; k < 16; ++k) {
-            if (k < b && d2 < (T)(100.0 * Eps<T>::v) * dmax) bad = true;
-            T d = 0, id = 0;
-            if (k < b && d2 > (T)0) {
-                id = rsqrt_t<T>(d2);
-                d = d2 * id;
+            if (own && i == k && j == k) {
+                const T d2 = g.x;
+                T d = 0, id = 0;
+                if (k < b && d2 < (T)(100.0 * Eps<T>::v) * dmax) s_bad = 1;
+                if (k < b && d2 > (T)0) {
+                    id = rsqrt_t<T>(d2);
+                    d = d2 * id;
+                }
+                Rk[k * 16 + k] = mk<T>(d, 0);
+                invd[k] = id;
+                s_id = id;
             }
-            V r = mk<T>(0, 0);
-            if (j > k) r = cscale(col[k], id);
-            else if (j == k) r = mk<T>(d, 0);
-            T d2n = 0;
-            if (k < 15) {
-                const V nd = csub(col[k + 1], cmul(cconj(r), r));
-                d2n = __shfl_sync(0xffffffffu, nd.x, k + 1);
+            bar_chol();
+            if (own && i == k && j > k) {
+                g = cscale(g, s_id);
+                Rk[k * 16 + j] = g;
             }
-            if (lane < 16) Rk[k * 16 + j] = r;
-            if (lane == 0) invd[k] = id;
-            __syncwarp();
-#pragma unroll
-            for (int i = k + 1; i < 16; ++i) col[i] = csub(col[i], cmul(cconj(Rk[k * 16 + i]), r));
-            d2 = d2n;
+            bar_chol();
+            if (own && i > k) g = csub(g, cmul(cconj(Rk[k * 16 + i]), Rk[k * 16 + j]));
         }
+        const bool bad = s_bad != 0;
         if (!may_shift || attempt == 1 || !bad || dmax == (T)0) break;
-        __syncwarp();
-        if (lane == 0) {
+        bar_chol();
+        if (tid == 0) {
             *need_shift = 1;
             *passes += 1;
         }
     }
-    __syncwarp();
 }
 
-// ---- float32 deflation on the tensor cores (mma.sync m16n8k8, tf32) ----------
-// The two products of a classical Gram-Schmidt pass, C = Q^H Y and
-// Y <- Y - Q^T C (Q's rows are the basis vectors), written as real products
-// with interleaved (re, im) reduction indices, each operand split as
-// x = hi + lo in tf32 and the products summed as hi*hi + hi*lo + lo*hi
-// (float32-level accuracy, as the 3xTF32 products of zgemm_tc).  Within every
-// 8-deep k step lane quad member t takes the real indices 2t and 2t+1 (the re
-// and im of one complex entry) in the fragment slots t and t+4, the same
-// permutation on both operands.
+
+// ---- float32 Gram matrix on the tensor cores (mma.sync m16n8k8, tf32) -------
+// The Gram matrix of a block, C = Y^H Y (a coefficient product with the
+// block's own columns as the basis rows), written as a real product with
+// interleaved (re, im) reduction indices, each operand split as x = hi + lo in
+// tf32 and the products summed as hi*hi + hi*lo + lo*hi (float32-level
+// accuracy, as the 3xTF32 products of zgemm_tc; tf32 keeps float32's exponent
+// range, so the operands need no scaling).  Within every 8-deep k step lane
+// quad member t takes the real indices 2t and 2t+1 (the re and im of one
+// complex entry) in the fragment slots t and t+4, the same permutation on both
+// operands.
 __device__ __forceinline__ uint32_t tf32_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 __device__ __forceinline__ void split_tf(float x, uint32_t& hi, uint32_t& lo) {
     hi = tf32_bits(x);
@@ -212,40 +228,181 @@ __device__ void orth_coef_mma(const float2* __restrict__ Q, int QS, const float2
     __syncthreads();
 }
 
-// Ys (L x 16, column-major, column stride LP) -= Q^T Cp (Q's rows are the
-// basis vectors; no conjugation): a warp per 16-row tile of Y.  L a multiple
-// of 16.
-__device__ void orth_update_mma(const float2* __restrict__ Q, float2* Ys, int L, int LP, int r_prev,
-                                const float2* Cp) {
+// ---- float32 deflation on binary16 tensor cores (mma.sync m16n8k16) -------
+// The two products of a classical Gram-Schmidt pass against the basis, with
+// every operand split as x = hi + lo in binary16 (11 significant bits each)
+// and the products summed as hi*hi + hi*lo + lo*hi in float32: the same
+// 22-bit operands as the 3xTF32 split, in half the MMAs (the m16n8k16 form
+// takes twice the reduction depth per instruction at the same issue rate).
+// binary16 has a narrow exponent range, so both operands are scaled by powers
+// of two (exact) before the split and the product scaled back: the basis rows
+// are unit vectors (every entry at most 1: x 2^14), the other operand by its
+// largest component m, x 2^(13 - floor(log2 m)), which the phase before
+// measured.  Components below 2^-17 m keep a subnormal lo part, whose absolute
+// error (2^-25 of the scaled unit) is far below the float32 level of the sum.
+// Within every 16-deep k step lane quad member t takes the complex entries
+// 8s + t (fragment slots 2t, 2t+1: re, im) and 8s + t + 4 (slots 2t+8, 2t+9).
+constexpr float H16_QSCALE = 16384.f;  // 2^14
+
+// 2^(13 - floor(log2 m)): m times it lies in [2^13, 2^14); 1 for m = 0 (or NaN)
+__device__ __forceinline__ float h16_scale(float m) {
+    if (!(m > 0.f)) return 1.f;
+    int e = (int)((__float_as_uint(m) >> 23) & 255u) - 127;
+    e = e < -100 ? -100 : (e > 113 ? 113 : e);
+    return __uint_as_float((unsigned)(127 + 13 - e) << 23);
+}
+// (a, b) -> binary16 pairs hi = rn(a, b), lo = rn(a - hi_a, b - hi_b); a in the low half
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+__device__ __forceinline__ void mma_f16_16x8x16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// d += A * [b0; b1] with both split: hi*hi + hi*lo + lo*hi
+__device__ __forceinline__ void mmah3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t b0h,
+                                      uint32_t b0l, uint32_t b1h, uint32_t b1l) {
+    mma_f16_16x8x16(d, ah, b0h, b1h);
+    mma_f16_16x8x16(d, ah, b0l, b1l);
+    mma_f16_16x8x16(d, al, b0h, b1h);
+}
+// the packed pair (lo16, hi16) -> (hi16, lo16) with the sign of the given half flipped
+__device__ __forceinline__ uint32_t swap_neg(uint32_t x, uint32_t sign) { return __byte_perm(x, 0, 0x1032) ^ sign; }
+// largest value of v over the warp, written to wmax[warp] by lane 0
+__device__ __forceinline__ void warp_max_to(float v, float* wmax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+}
+__device__ __forceinline__ float max_of(const float* wmax, int n) {
+    float m = 0.f;
+    for (int w = 0; w < n; ++w) m = fmaxf(m, wmax[w]);
+    return m;
+}
+
+// Cp (r_prev x 16) = conj(Q) Y for the 16 columns of Y (Ys column-major with
+// column stride LP, L a multiple of 16); row i of Q (a unit vector) starts at
+// Q + i L in global memory (cache-global loads).  ymax: the largest component
+// of Y.  Warps take (16-row tile, k range) items; the partial tiles, scaled
+// back, meet in `part` and are summed over the k ranges in a fixed order.
+// The largest component of Cp goes to cmax_w (one entry per warp).  Ends with
+// a barrier.
+__device__ void orth_coef_h16(const float2* __restrict__ Q, const float2* Ys, int L, int LP, int r_prev, float ymax,
+                              float2* Cp, float* part, float* cmax_w) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int mt = L / 16, nks = (r_prev + 3) / 4;
-    constexpr uint32_t SGN = 0x80000000u;
+    const int mt = (r_prev + 15) / 16, nks = L / 8;
+    int KC = nw / mt;
+    KC = KC < 1 ? 1 : (KC > nks ? nks : KC);
+    const float sy = h16_scale(ymax), back = 1.f / (H16_QSCALE * sy);
+    constexpr uint32_t HI = 0x80000000u;
+    for (int it = warp; it < mt * KC; it += nw) {
+        const int mtile = it / KC, kc = it - mtile * KC;
+        const int ks0 = kc * nks / KC, ks1 = (kc + 1) * nks / KC;
+        const int i0 = mtile * 16 + g, i1 = i0 + 8;
+        const bool ok0 = i0 < r_prev, ok1 = i1 < r_prev;
+        const float2* q0 = Q + (long)i0 * L;
+        const float2* q1 = Q + (long)i1 * L;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+        for (int ks = ks0; ks < ks1; ++ks) {
+            const int e0 = ks * 8 + t, e1 = e0 + 4;
+            const float2 z = make_float2(0.f, 0.f);
+            const float2 a0 = ok0 ? __ldcg(q0 + e0) : z, a1 = ok1 ? __ldcg(q1 + e0) : z;
+            const float2 a2 = ok0 ? __ldcg(q0 + e1) : z, a3 = ok1 ? __ldcg(q1 + e1) : z;
+            uint32_t ah[4], al[4];
+            split_h2(a0.x * H16_QSCALE, a0.y * H16_QSCALE, ah[0], al[0]);
+            split_h2(a1.x * H16_QSCALE, a1.y * H16_QSCALE, ah[1], al[1]);
+            split_h2(a2.x * H16_QSCALE, a2.y * H16_QSCALE, ah[2], al[2]);
+            split_h2(a3.x * H16_QSCALE, a3.y * H16_QSCALE, ah[3], al[3]);
+#pragma unroll
+            for (int jh = 0; jh < 2; ++jh) {
+                const float2 y0 = Ys[(jh * 8 + g) * LP + e0], y1 = Ys[(jh * 8 + g) * LP + e1];
+                uint32_t r0h, r0l, r1h, r1l;
+                split_h2(y0.x * sy, y0.y * sy, r0h, r0l);
+                split_h2(y1.x * sy, y1.y * sy, r1h, r1l);
+                // Re: sum qr yr + qi yi with (yr, yi); Im: sum qr yi - qi yr with (yi, -yr)
+                mmah3(acc[jh], ah, al, r0h, r0l, r1h, r1l);
+                mmah3(acc[2 + jh], ah, al, swap_neg(r0h, HI), swap_neg(r0l, HI), swap_neg(r1h, HI),
+                      swap_neg(r1l, HI));
+            }
+        }
+        float* P = part + (size_t)kc * mt * 16 * 32;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = mtile * 16 + g + (c >> 1) * 8, col = nt * 8 + 2 * t + (c & 1);
+                P[row * 32 + col] = acc[nt][c] * back;
+            }
+    }
+    __syncthreads();
+    float cm = 0.f;
+    for (int idx = threadIdx.x; idx < r_prev * 16; idx += blockDim.x) {
+        const int i = idx >> 4, j = idx & 15;
+        float sr = 0.f, si = 0.f;
+        for (int kc = 0; kc < KC; ++kc) {
+            const float* P = part + (size_t)kc * mt * 16 * 32 + i * 32;
+            sr += P[j];
+            si += P[16 + j];
+        }
+        Cp[i * 16 + j] = make_float2(sr, si);
+        cm = fmaxf(cm, fmaxf(fabsf(sr), fabsf(si)));
+    }
+    warp_max_to(cm, cmax_w);
+    __syncthreads();
+}
+
+// Ys (L x 16, column-major, column stride LP) -= Q^T Cp (Q's rows are the
+// basis vectors; no conjugation): a warp per 16-row tile of Y.  L a multiple
+// of 16; cmax: the largest component of Cp.  The largest component of the
+// updated Y goes to ymax_w (one entry per warp).
+__device__ void orth_update_h16(const float2* __restrict__ Q, float2* Ys, int L, int LP, int r_prev,
+                                const float2* Cp, float cmax, float* ymax_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int mt = L / 16, nks = (r_prev + 7) / 8;
+    const float sc = h16_scale(cmax), back = 1.f / (H16_QSCALE * sc);
+    constexpr uint32_t LO = 0x00008000u;
+    float ym = 0.f;
     for (int mtile = warp; mtile < mt; mtile += nw) {
         const int e0 = mtile * 16 + g, e1 = e0 + 8;
         float acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+            for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
         for (int ks = 0; ks < nks; ++ks) {
-            const int i = ks * 4 + t;
-            const bool ok = i < r_prev;
-            const float2 q0 = ok ? __ldcg(Q + (long)i * L + e0) : make_float2(0.f, 0.f);
-            const float2 q1 = ok ? __ldcg(Q + (long)i * L + e1) : make_float2(0.f, 0.f);
+            const int i0 = ks * 8 + t, i1 = i0 + 4;
+            const bool ok0 = i0 < r_prev, ok1 = i1 < r_prev;
+            const float2 z = make_float2(0.f, 0.f);
+            const float2 a0 = ok0 ? __ldcg(Q + (long)i0 * L + e0) : z, a1 = ok0 ? __ldcg(Q + (long)i0 * L + e1) : z;
+            const float2 a2 = ok1 ? __ldcg(Q + (long)i1 * L + e0) : z, a3 = ok1 ? __ldcg(Q + (long)i1 * L + e1) : z;
             uint32_t ah[4], al[4];
-            split_tf(q0.x, ah[0], al[0]);
-            split_tf(q1.x, ah[1], al[1]);
-            split_tf(q0.y, ah[2], al[2]);
-            split_tf(q1.y, ah[3], al[3]);
+            split_h2(a0.x * H16_QSCALE, a0.y * H16_QSCALE, ah[0], al[0]);
+            split_h2(a1.x * H16_QSCALE, a1.y * H16_QSCALE, ah[1], al[1]);
+            split_h2(a2.x * H16_QSCALE, a2.y * H16_QSCALE, ah[2], al[2]);
+            split_h2(a3.x * H16_QSCALE, a3.y * H16_QSCALE, ah[3], al[3]);
 #pragma unroll
             for (int jh = 0; jh < 2; ++jh) {
-                const float2 c = ok ? Cp[i * 16 + jh * 8 + g] : make_float2(0.f, 0.f);
-                uint32_t xh, xl, yh, yl;
-                split_tf(c.x, xh, xl);
-                split_tf(c.y, yh, yl);
-                mma3(acc[jh], ah, al, xh, xl, yh ^ SGN, yl ^ SGN);  // Re: sum Qr Cr - Qi Ci
-                mma3(acc[2 + jh], ah, al, yh, yl, xh, xl);          // Im: sum Qr Ci + Qi Cr
+                const float2 c0 = ok0 ? Cp[i0 * 16 + jh * 8 + g] : z, c1 = ok1 ? Cp[i1 * 16 + jh * 8 + g] : z;
+                uint32_t r0h, r0l, r1h, r1l;
+                split_h2(c0.x * sc, -c0.y * sc, r0h, r0l);
+                split_h2(c1.x * sc, -c1.y * sc, r1h, r1l);
+                // Re: sum qr cr - qi ci with (cr, -ci); Im: sum qr ci + qi cr with (ci, cr)
+                mmah3(acc[jh], ah, al, r0h, r0l, r1h, r1l);
+                mmah3(acc[2 + jh], ah, al, swap_neg(r0h, LO), swap_neg(r0l, LO), swap_neg(r1h, LO),
+                      swap_neg(r1l, LO));
             }
         }
 #pragma unroll
@@ -254,9 +411,12 @@ __device__ void orth_update_mma(const float2* __restrict__ Q, float2* Ys, int L,
             for (int c = 0; c < 4; ++c) {
                 const int row = (c >> 1) ? e1 : e0, j = jh * 8 + 2 * t + (c & 1);
                 float2* y = Ys + j * LP + row;
-                *y = make_float2(y->x - acc[jh][c], y->y - acc[2 + jh][c]);
+                const float2 v = make_float2(y->x - acc[jh][c] * back, y->y - acc[2 + jh][c] * back);
+                *y = v;
+                ym = fmaxf(ym, fmaxf(fabsf(v.x), fabsf(v.y)));
             }
     }
+    warp_max_to(ym, ymax_w);
 }
 
 // Shared-memory extents of k_orth beyond its matrices: the partial tiles of
@@ -301,17 +461,37 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
         need_shift = 0;
     }
     T nn = 0;
-    for (int e = tid; e < L * b; e += blockDim.x) {  // Y row-major L x b: coalesced reads
-        const int row = e / b, j = e - row * b;
-        const V v = Y[e];
-        Ys[j * LP + row] = v;
-        nn += cabs2(v);
+    float ymax = 0.f;  // largest component of the block (binary16 deflation scale)
+    {
+        // Y row-major L x b: coalesced reads, eight per thread in flight
+        constexpr int U = 8;
+        const int tot = L * b, nt = blockDim.x;
+        for (int e0 = tid; e0 < tot; e0 += U * nt) {
+            V v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nt;
+                v[u] = e < tot ? Y[e] : mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nt;
+                if (e < tot) {
+                    const int row = e / b, j = e - row * b;
+                    Ys[j * LP + row] = v[u];
+                    nn += cabs2(v[u]);
+                    ymax = fmaxf(ymax, fmaxf(fabsf((float)v[u].x), fabsf((float)v[u].y)));
+                }
+            }
+        }
     }
     for (int e = tid; e < L * (BB - b); e += blockDim.x) {
         const int j = b + e / L, row = e - (j - b) * L;
         Ys[j * LP + row] = mk<T>(0, 0);
     }
     for (int e = tid; e < BB * BB; e += blockDim.x) Ra[e] = mk<T>((e / BB) == (e % BB) ? (T)1 : (T)0, 0);
+    __shared__ float wmax_y[32], wmax_c[32];  // per-warp maxima of |Y| and |Cp| components
+    warp_max_to(ymax, wmax_y);                 // published by the barriers of the norm
     const double nnd = block_sum_t(nn, red);
     if (normsq && tid == 0) normsq[s] = nnd;
 
@@ -323,8 +503,10 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
         const bool tc = sizeof(T) == 4 && BB == 16 && (L & 15) == 0 && r_prev <= 256;  // part: 16 row tiles
         for (int pass = 0; pass < dpasses; ++pass) {
           if (tc) {
-            orth_coef_mma<true>((const float2*)Q, L, (const float2*)Ys, L, LP, r_prev, (float2*)Cp, part);
-            orth_update_mma((const float2*)Q, (float2*)Ys, L, LP, r_prev, (const float2*)Cp);
+            orth_coef_h16((const float2*)Q, (const float2*)Ys, L, LP, r_prev, max_of(wmax_y, NW), (float2*)Cp,
+                          part, wmax_c);
+            orth_update_h16((const float2*)Q, (float2*)Ys, L, LP, r_prev, (const float2*)Cp, max_of(wmax_c, NW),
+                            wmax_y);
           } else {
             // two basis vectors per warp share every shared-memory read of Y
             for (int i0 = 2 * warp; i0 < r_prev; i0 += 2 * NW) {
@@ -449,14 +631,19 @@ k_orth(cplx<T>* Y, long sY, int L, int b, const cplx<T>* Qb, long sQ, int r_prev
             }
         }
         __syncthreads();
+        __shared__ T s_shift;
         if (pass == 0 && warp == 0) {
             // 11 (L b + b(b+1)) u ||Y||_F^2, ||Y||_F^2 the trace of the Gram matrix
             T y2 = lane < BB ? G[lane * BB + lane].x : (T)0;
             y2 = warp_sum(y2);
             shift = (T)(11.0 * ((double)L * b + (double)b * (b + 1)) * Eps<T>::v) * y2;
+            if (lane == 0) s_shift = shift;
         }
-        if (warp == 0 && BB == 16 && sizeof(T) == 4) {
-            chol16_reg<T>(G, Rk, invd, b, shift, pass == 0, &need_shift, &passes);
+        if (BB == 16 && sizeof(T) == 4) {
+            if (tid < 160) {
+                bar_chol();  // s_shift
+                chol16_par<T>(G, Rk, invd, b, s_shift, pass == 0, &need_shift, &passes);
+            }
         } else if (warp == 0) {
             // Cholesky G (+ shift) = R^H R by the first warp: at step k the
             // lanes form row k of R, then update the trailing Gram entries as
