@@ -131,6 +131,11 @@ __device__ void chol16_par(const cplx<T>* G, cplx<T>* Rk, T* invd, int b, T shif
 }
 
 
+// Row stride (floats) of the partial coefficient tiles of the tensor-core
+// products: 32 re/im entries padded to 40, so that the (row g, columns 2t, 2t+1)
+// pairs of a half-warp's float2 stores fall on 32 distinct banks.
+constexpr int PART_LD = 40;
+
 // ---- float32 Gram matrix on the tensor cores (mma.sync m16n8k8, tf32) -------
 // The Gram matrix of a block, C = Y^H Y (a coefficient product with the
 // block's own columns as the basis rows), written as a real product with
@@ -165,7 +170,7 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], con
 // column stride LP, L a multiple of 16); row i of Q starts at Q + i QS, in
 // global memory (GQ, read with cache-global loads) or in shared memory.
 // Warps take (16-row tile, k range) items; the partial tiles meet in `part`
-// (at most 16 x 16 x 32 floats) and are summed over the k ranges in a fixed
+// (at most 16 x 16 x PART_LD floats) and are summed over the k ranges in a fixed
 // order.  Ends with a barrier.
 template <bool GQ>
 __device__ void orth_coef_mma(const float2* __restrict__ Q, int QS, const float2* Ys, int L, int LP, int r_prev,
@@ -205,13 +210,13 @@ __device__ void orth_coef_mma(const float2* __restrict__ Q, int QS, const float2
                 mma3(acc[2 + jh], ah, al, yh, yl, xh ^ SGN, xl ^ SGN);    // Im: sum Qr Yi - Qi Yr
             }
         }
-        float* P = part + (size_t)kc * mt * 16 * 32;
+        float* P = part + (size_t)kc * mt * 16 * PART_LD;
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int row = mtile * 16 + g + (c >> 1) * 8, col = nt * 8 + 2 * t + (c & 1);
-                P[row * 32 + col] = acc[nt][c];
+            for (int h = 0; h < 2; ++h) {
+                const int row = mtile * 16 + g + h * 8, col = nt * 8 + 2 * t;
+                *(float2*)(P + row * PART_LD + col) = make_float2(acc[nt][2 * h], acc[nt][2 * h + 1]);
             }
     }
     __syncthreads();
@@ -219,7 +224,7 @@ __device__ void orth_coef_mma(const float2* __restrict__ Q, int QS, const float2
         const int i = idx >> 4, j = idx & 15;
         float sr = 0.f, si = 0.f;
         for (int kc = 0; kc < KC; ++kc) {
-            const float* P = part + (size_t)kc * mt * 16 * 32 + i * 32;
+            const float* P = part + (size_t)kc * mt * 16 * PART_LD + i * PART_LD;
             sr += P[j];
             si += P[16 + j];
         }
@@ -337,13 +342,13 @@ __device__ void orth_coef_h16(const float2* __restrict__ Q, const float2* Ys, in
                       swap_neg(r1l, HI));
             }
         }
-        float* P = part + (size_t)kc * mt * 16 * 32;
+        float* P = part + (size_t)kc * mt * 16 * PART_LD;
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int row = mtile * 16 + g + (c >> 1) * 8, col = nt * 8 + 2 * t + (c & 1);
-                P[row * 32 + col] = acc[nt][c] * back;
+            for (int h = 0; h < 2; ++h) {
+                const int row = mtile * 16 + g + h * 8, col = nt * 8 + 2 * t;
+                *(float2*)(P + row * PART_LD + col) = make_float2(acc[nt][2 * h] * back, acc[nt][2 * h + 1] * back);
             }
     }
     __syncthreads();
@@ -352,7 +357,7 @@ __device__ void orth_coef_h16(const float2* __restrict__ Q, const float2* Ys, in
         const int i = idx >> 4, j = idx & 15;
         float sr = 0.f, si = 0.f;
         for (int kc = 0; kc < KC; ++kc) {
-            const float* P = part + (size_t)kc * mt * 16 * 32 + i * 32;
+            const float* P = part + (size_t)kc * mt * 16 * PART_LD + i * PART_LD;
             sr += P[j];
             si += P[16 + j];
         }
@@ -423,7 +428,7 @@ __device__ void orth_update_h16(const float2* __restrict__ Q, float2* Ys, int L,
 // the tensor-core deflation (float32, 16 columns) and the Gram partials (one
 // per thread, at least one per upper-triangle entry).
 template <typename T, int BB> constexpr size_t orth_part_bytes() {
-    return (sizeof(T) == 4 && BB == 16) ? (size_t)16 * 16 * 32 * sizeof(float) : 0;
+    return (sizeof(T) == 4 && BB == 16) ? (size_t)16 * 16 * PART_LD * sizeof(float) : 0;
 }
 template <typename T, int BB> constexpr size_t orth_gram_elems() {
     return (size_t)(BB * (BB + 1) / 2 > OrthThreads<T, BB>::v ? BB * (BB + 1) / 2 : OrthThreads<T, BB>::v);
@@ -998,6 +1003,10 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
             for (int t = 0; t < rr - 1; ++t) {
                 const int p = min(pa, pb), q = max(pa, pb);
                 const bool valid = kp < npair && q < r && p != q;
+                // a warp whose slots all lie beyond the round's pairs (r = 96: 48 pairs
+                // for 64 slots) skips to the barrier instead of issuing the round on zeros
+                // (up to r = 96; the longer columns leave no register for the test)
+                if (EPL > 12 || base + (tid >> 5) * (32 / GL) < npair) {
                 float2* cp = Rs + (size_t)p * r;
                 float2* cq = Rs + (size_t)q * r;
                 float2 x[EPL], y[EPL];
@@ -1085,6 +1094,7 @@ __device__ int jacobi_sweeps_reg(float2* Rs, float2* dp, int np, int r, int max_
                     }
                 }
                 any |= rot ? 1 : 0;
+                }
                 any = __syncthreads_or(any);
                 // next round: both indices of a slot advance by one (kp = 0 keeps p = 0)
                 if (kp != 0) pa = pa == rr - 1 ? 1 : pa + 1;
