@@ -170,6 +170,10 @@ tp_status tprod_gemm_noalloc(const void* A, const void* B, void* C, int l, int k
  * workspace (global memory, L2-resident); its r_max p right-hand sides must
  * fit in shared memory in either case; and the block orthonormalisation's
  * working set (about (l + 1) b + 2 r_max b complex entries) must fit too.
+ * Float32 range: the small SVD forms squared inner products of the factor
+ * (fourth powers of the data's magnitude), so float32 data far from unit
+ * scale (entries of A near 1e-13, say) can end in TP_ERR_NOT_CONVERGED;
+ * rescale such data, or use TP_FP64.
  */
 typedef struct {
     double delta;       /* noise bound of Eq. (errbd)                                 */

@@ -271,6 +271,31 @@ def test_rtsvd_matches_oracle(tp, dtype, N, n, block, q, p_over, eps_rel):
     assert np.isclose(info["norm_a2"], O.fro2(A.astype(np.float64)), rtol=1e-6 if dtype == torch.float32 else 1e-12)
 
 
+@pytest.mark.parametrize("s", [-12, 12])
+def test_rtsvd_float32_scaled_problem(tp, s):
+    """A and B scaled by 2^s (delta with them): the solution of A X = B is
+    unchanged.  The float32 path at l = m = 32 deflates its second block on the
+    binary16 tensor-core split, whose operands the kernel rescales by powers of
+    two from their measured magnitudes; the scaled solve must still pick the
+    oracle's r and k and match the unscaled oracle solution within 1e-5.  At
+    2^-12 unscaled binary16 operands would sit in its subnormal range, at 2^12
+    the sketch columns pass its largest value.  (The scale stays inside the
+    float32 path's range: the small SVD works with squared inner products of
+    the factor, fourth powers of the data's magnitude.)"""
+    N, n = 32, 8
+    A, B, delta = problem(N, n)
+    Om = rnd((n, N, N), 11).astype(np.float32)
+    ref = O.rtsvd_solve(A.astype(np.float64), B.astype(np.float64), Om.astype(np.float64), delta, 1.1,
+                        0.02 * np.sqrt(O.fro2(A.astype(np.float64))), 3, 16, 1, r_max=N)
+    assert exact_k_required(ref, torch.float32)
+    f = 2.0 ** s
+    X, info = tp.rtsvd_solve(dev(A * np.float32(f), torch.float32), dev(B * np.float32(f), torch.float32),
+                             dev(Om, torch.float32), delta * f, 1.1, 3, 16, 1, r_max=N, eps_rel=0.02)
+    assert info["status"] == 0
+    assert info["r"] == ref["r"] and info["k"] == ref["k"]
+    assert rel(X.cpu().numpy(), ref["X"]) <= TOL_X[torch.float32]
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("N,n,block,p,r_max", [(12, 8, 4, 2, 12), (16, 9, 3, 5, 16), (20, 16, 8, 17, 20),
                                                (24, 6, 16, 64, 24)])
